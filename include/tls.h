@@ -1,0 +1,179 @@
+/*
+ * tls.h -- C ABI of the GB300 (sm_103a) RQI-PCGTLS library.
+ *
+ * Method: Rayleigh quotient iteration for the smallest singular value sigma_{n+1} of [A, b]
+ * and the total-least-squares solution x_TLS = -v(1:n, n+1) / v(n+1, n+1) (Oktay & Carson,
+ * arXiv 2305.19028, Sec. 1), with every RQI step solving the two shifted systems
+ * (A^T A - sigma_k^2 I) w = f by preconditioned conjugate gradients, PCGTLS (Alg. 3), in the
+ * three-precision form of Alg. 4:
+ *   u_f  the precision of the preconditioner R (the paper's u_q): FP16 / BF16 / FP32 / FP64;
+ *   u    the PCGTLS working precision (the paper's u_p): FP32 or FP64;
+ *   u_r  the precision of the residuals, the Rayleigh quotient and the stop test (the paper's
+ *        u): always FP64.
+ * R is the Cholesky factor of the column-scaled Gram matrix H = D^{-1} A^T A D^{-1},
+ * D = diag(||a_j||) (Sec. 3.1, two-sided diagonal scaling), so R = R_H D.
+ *
+ * Conventions for every entry point:
+ *  - Nothing throws across the ABI. Each call returns a tls_status; a per-context message
+ *    with details is available from tls_last_error().
+ *  - All work runs on the context's CUDA stream (the stream passed at creation, or a
+ *    stream the context creates when NULL is passed). tls_solve synchronises that stream only
+ *    to return x and sigma.
+ *  - Matrices are row-major. Sizes are int64_t. Pointers are either host pointers or device
+ *    pointers as stated per argument.
+ *  - A context is not thread-safe; distinct contexts may be used from distinct threads.
+ */
+#ifndef TLS_H_
+#define TLS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TLS_OK = 0,
+  TLS_ERR_ARG = 1,               /* invalid argument (sizes, NULL, NaN/Inf in the data) */
+  TLS_ERR_CUDA = 2,              /* a CUDA runtime call failed */
+  TLS_ERR_OOM = 3,               /* device allocation failed */
+  TLS_ERR_STATE = 4,             /* call out of order (e.g. tls_solve before tls_factor) */
+  TLS_ERR_FACTOR_BREAKDOWN = 5,  /* Cholesky met a non-positive pivot on every rung */
+  TLS_ERR_NOT_SPD = 6,           /* PCGTLS met delta_j <= 0: A^T A - sigma^2 I not SPD (Sec. 3) */
+  TLS_ERR_NOT_UNIQUE = 7,        /* sigma_{n+1} >= sigma'_n estimate: x_TLS not unique (Sec. 3) */
+  TLS_ERR_NO_CONVERGENCE = 8,    /* max_rqi reached with psi above the acceptance level */
+  TLS_ERR_TIMEOUT = 9            /* a bounded device wait gave up */
+} tls_status;
+
+typedef enum {
+  TLS_FP16 = 0,
+  TLS_BF16 = 1,
+  TLS_FP32 = 2,
+  TLS_FP64 = 3
+} tls_prec;
+
+/* Stop reasons reported in tls_info.stop_reason. */
+enum {
+  TLS_STOP_TOL = 1,       /* psi_k <= tol * (||A||_F^2 + ||b||^2)                          */
+  TLS_STOP_PSI_UP = 2,    /* psi_k > psi_{k-1} (or >= with psi_rule_ge), Sec. 3 after Eq. (4) */
+  TLS_STOP_MAX_RQI = 3    /* k reached max_rqi                                              */
+};
+
+typedef struct {
+  tls_prec u;          /* PCGTLS precision u_p: TLS_FP32 (mixed) or TLS_FP64 (plain)          */
+  int mode_A;          /* 1: operator with A, delta = ||A q||^2 - sigma^2 ||q||^2 (default);    */
+                       /* 0: Alg. 3 as printed, delta = ||p||^2 - sigma^2 ||q||^2               */
+  int cg_fixed;        /* 1: k+1 PCGTLS steps in RQI step k (Alg. 4, default);                 */
+                       /* 0: up to cg_max steps, stopping when ||s_j|| <= cg_tol ||s_0||        */
+  double cg_tol;
+  int cg_max;
+  int psi_rule_ge;     /* 1: stop on psi_k >= psi_{k-1} (the rule of Sec. 4.2)                 */
+  int ls_iters;        /* PCG steps (sigma^2 = 0) that produce the LS start x_0 (default 12)   */
+  int max_shifts;      /* Cholesky retries with H + s I, s = 2^-10 * 4^i before escalating u_f */
+} tls_options;
+
+typedef struct {
+  int stop_reason;       /* TLS_STOP_* */
+  int rqi_steps;         /* residual evaluations in the RQI loop (k of the last one)         */
+  int best_k;            /* k of the returned iterate (the one with the smallest psi)        */
+  int cg_iters;          /* PCGTLS steps summed over both solves of every RQI step           */
+  int shifts;            /* diagonal shifts applied to H before the factorisation succeeded  */
+  int not_spd;           /* 1 if some PCGTLS solve stopped on delta_j <= 0                   */
+  tls_prec u_f_used;     /* precision of the factor that was used                            */
+  double psi_final;      /* psi of the returned iterate                                      */
+  double sigma2;         /* sigma^2 of the returned iterate                                  */
+  double shift;          /* the shift s of H + s I that was used (0 if none)                 */
+  double t_factor_ms;    /* device time of the last tls_factor (CUDA events)                 */
+  double t_solve_ms;     /* device time of this tls_solve                                    */
+} tls_info;
+
+typedef struct tls_ctx tls_ctx;
+
+/* Default options: u = FP32, mode A, k+1 PCGTLS steps, strict psi rule, 12 LS steps,
+ * 3 shifts. */
+void tls_default_options(tls_options* opt);
+
+/*
+ * tls_create_dense -- a TLS problem [A, b] with dense A (Sec. 1: min ||[E, r]||_F subject to
+ * (A + E) x = b + r).
+ *   m, n      rows and columns of A, m >= n >= 1.
+ *   A         m x n, row-major with leading dimension lda >= n (elements); FP64.
+ *   b         m FP64 values.
+ *   on_device 0: A and b are host pointers; 1: they are device pointers of the current device.
+ *   stream    a cudaStream_t (as void*) for all the context's work, or NULL to create one.
+ * The context copies A and b into device memory it owns (the caller keeps its buffers).
+ * On host pointers the data is checked for NaN/Inf (TLS_ERR_ARG). *out is NULL on error.
+ */
+tls_status tls_create_dense(tls_ctx** out, int64_t m, int64_t n, const double* A, int64_t lda,
+                            const double* b, int on_device, void* stream);
+
+/*
+ * tls_create_csr -- as tls_create_dense with A in CSR form:
+ *   row_ptr   m + 1 int64 offsets, row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz;
+ *   col_idx   nnz int32 column indices in [0, n), strictly increasing within each row;
+ *   val       nnz FP64 values.
+ * Host pointers only (on_device must be 0); the structure is validated on the host.
+ */
+tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz,
+                          const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                          const double* b, int on_device, void* stream);
+
+/*
+ * tls_factor -- build the preconditioner R in precision u_f (Alg. 4, the factorisation step;
+ * Sec. 3.1): column scaling D, the Gram matrix H = (A D^{-1})^T (A D^{-1}) from A D^{-1}
+ * rounded to u_f (tensor cores, FP32 accumulation, for FP16/BF16), Cholesky H + s I = R_H^T R_H
+ * with R_H rounded to u_f, and R = R_H D. On a non-positive pivot it retries with shifts
+ * s = 2^-10 * 4^i (i < max_shifts), then escalates u_f (FP16/BF16 -> FP32 -> FP64);
+ * TLS_ERR_FACTOR_BREAKDOWN if FP64 fails too. opt may be NULL (defaults).
+ */
+tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt);
+
+/*
+ * tls_solve -- run RQI-PCGTLS (Alg. 2 with the solves of Alg. 3, precisions as in Alg. 4)
+ * from the LS start and return the iterate with the smallest psi_k (Eq. (4)).
+ *   tol      stop when psi_k <= tol * (||A||_F^2 + ||b||^2) (a normwise backward error of
+ *            the eigenpair of Eq. (1)); 0 leaves only the psi-increase rule and max_rqi.
+ *   max_rqi  maximum number of RQI updates.
+ *   x        n FP64 values, host memory, written on success.
+ *   sigma    host, sigma = sqrt(sigma_k^2) of the returned iterate.
+ *   info     host, may be NULL.
+ * Requires a successful tls_factor (else TLS_ERR_STATE).
+ */
+tls_status tls_solve(tls_ctx* ctx, double tol, int max_rqi, double* x, double* sigma,
+                     tls_info* info);
+
+/* x on the device instead of the host (n FP64 values, device pointer); sigma and info on the
+ * host as in tls_solve. */
+tls_status tls_solve_device(tls_ctx* ctx, double tol, int max_rqi, double* x_dev,
+                            double* sigma, tls_info* info);
+
+/*
+ * tls_solve_batched -- solve `count` independent, already factored contexts; per_problem[i]
+ * receives each status, x[i] (host, n_i FP64) and sigma[i] the results, infos may be NULL.
+ * Returns the first non-OK status in index order, or TLS_OK.
+ */
+tls_status tls_solve_batched(int count, tls_ctx* const* ctxs, double tol, int max_rqi,
+                             double* const* x, double* sigma, tls_info* infos,
+                             tls_status* per_problem);
+
+void tls_destroy(tls_ctx* ctx);
+const char* tls_status_str(tls_status s);
+const char* tls_last_error(const tls_ctx* ctx);
+
+/* Problem sizes of a context (m, n; nnz = -1 for dense). */
+void tls_shape(const tls_ctx* ctx, int64_t* m, int64_t* n, int64_t* nnz);
+
+/*
+ * tls_set_allocator -- route the library's device allocations through caller functions
+ * (e.g. a framework's caching allocator). alloc(bytes, stream, user) returns a device pointer
+ * or NULL; release(ptr, bytes, stream, user) frees it. Pass NULLs to restore cudaMalloc /
+ * cudaFree. Affects contexts created afterwards. Not thread-safe with concurrent creation.
+ */
+typedef void* (*tls_alloc_fn)(uint64_t bytes, void* stream, void* user);
+typedef void (*tls_free_fn)(void* ptr, uint64_t bytes, void* stream, void* user);
+void tls_set_allocator(tls_alloc_fn alloc, tls_free_fn release, void* user);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLS_H_ */

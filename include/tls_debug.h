@@ -1,0 +1,80 @@
+/*
+ * tls_debug.h -- inspection entry points of the RQI-PCGTLS library: each runs one step of
+ * the solve path on a factored context with host inputs/outputs, so that a caller (or a
+ * test) can check the kernels in isolation. Same conventions as tls.h.
+ */
+#ifndef TLS_DEBUG_H_
+#define TLS_DEBUG_H_
+
+#include <stdint.h>
+#include "tls.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * tls_export_factor -- copy the factor the solve uses (Sec. 3.1): R_host (n x n, row-major)
+ * receives R_H, the Cholesky factor of the column-scaled Gram matrix rounded to u_f (upper
+ * triangular; R = R_H diag(d)); d_host (n) the column norms d_j = ||a_j||; H_host (n x n) the
+ * scaled Gram matrix H = (A D^{-1})^T (A D^{-1}) as formed from the u_f-rounded data.
+ * Any output may be NULL. TLS_ERR_STATE before a successful tls_factor.
+ */
+tls_status tls_export_factor(tls_ctx* ctx, double* R_host, double* d_host, double* H_host);
+
+/*
+ * tls_residual -- one RQI residual block in FP64 at x (Alg. 2 lines r_k..g_k, Eq. (2), Eq. (4)):
+ * f_host (n) = -A^T r - sigma^2 x with r = b - A x; scal_host[0..4] = sigma^2 = r^T r/(1+x^T x),
+ * g = -b^T r + sigma^2, psi = sqrt((||f||^2 + g^2)/(||x||^2 + 1)), r^T r, b^T r.
+ * Needs no factor. x_host: n values (host).
+ */
+tls_status tls_residual(tls_ctx* ctx, const double* x_host, double* f_host, double* scal_host);
+
+/*
+ * tls_pcgtls -- PCGTLS (Alg. 3) for (A^T A - sigma2 I) w = f in the context's precision u, for
+ * nr = 1 or 2 right-hand sides f0 (and f1) sharing each pass over A: `steps` steps, or fewer
+ * when ||s_j|| <= cg_tol ||s_0|| (cg_tol > 0) or delta_j <= 0. w0 (and w1): n values each.
+ * iters[2], not_spd[2] (may be NULL): per right-hand side. Host pointers.
+ */
+tls_status tls_pcgtls(tls_ctx* ctx, int nr, double sigma2, const double* f0, const double* f1,
+                      int steps, double cg_tol, double* w0, double* w1, int* iters,
+                      int* not_spd);
+
+/*
+ * tls_precond -- the preconditioner products in precision u: s0 = R^{-T} y (Alg. 3
+ * initialisation) and u = R^{-1} R^{-T} y (the solve with A^T A ~ R^T R of Alg. 2, line 4).
+ * y, s0, u: n values (host); s0 or u may be NULL.
+ */
+tls_status tls_precond(tls_ctx* ctx, const double* y, double* s0, double* u);
+
+/* Kernel classes timed by the profiler. */
+enum {
+  TLS_PROF_SCALE = 0,        /* column norms, FP32 copy, scaled cast of A       */
+  TLS_PROF_GRAM = 1,         /* H = A_s^T A_s                                   */
+  TLS_PROF_CHOL = 2,         /* blocked Cholesky (each attempt)                 */
+  TLS_PROF_TRTRI = 3,        /* rounding of R_H, W = R_H^{-1}, W^T             */
+  TLS_PROF_RESID_PASS = 4,   /* FP64 pass over A of the RQI residual           */
+  TLS_PROF_RESID_REDUCE = 5, /* its reduction: f, sigma^2, g, psi               */
+  TLS_PROF_PCG_PASS2 = 6,    /* PCGTLS pass over A, two right-hand sides        */
+  TLS_PROF_PCG_PASS1 = 7,    /* PCGTLS pass over A, one right-hand side (LS)    */
+  TLS_PROF_PCG_REDUCE = 8,   /* PCGTLS partial reduction and w, y updates       */
+  TLS_PROF_PCG_GEMV = 9,     /* products with W and W^T, s and p recurrences    */
+  TLS_PROF_VEC = 10,         /* FP64 RQI vector updates                          */
+  TLS_PROF_NCLASSES = 11
+};
+
+/*
+ * tls_profile_enable -- when on, every kernel (group) the context launches is bracketed by
+ * CUDA events on its stream; times are summed per class after each tls_factor / tls_solve.
+ * Enabling (or disabling) resets the sums.
+ */
+tls_status tls_profile_enable(tls_ctx* ctx, int on);
+/* Launch count and summed device milliseconds of one class (TLS_PROF_*). */
+tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* ms);
+/* Kernels launched by the library since it was loaded (all contexts). */
+uint64_t tls_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLS_DEBUG_H_ */

@@ -1,0 +1,965 @@
+// C ABI of the library (include/tls.h, include/tls_debug.h): contexts, the factorisation
+// ladder and the RQI-PCGTLS driver (Alg. 2 / Alg. 4 of Oktay & Carson, arXiv 2305.19028).
+#include "../../include/tls.h"
+#include "../../include/tls_debug.h"
+#include "tls_internal.h"
+
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace tls {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+using tls::Prec;
+using tls::PcgScalars;
+using tls::RqiScalars;
+
+namespace {
+
+tls_alloc_fn g_alloc = nullptr;
+tls_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tls_ctx {
+  int64_t m = 0, n = 0, npad = 0, mpad = 0, nnz = -1;
+  int device = 0, num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<DevBuf> bufs;
+
+  // problem data (device)
+  double* A64 = nullptr;   // m x npad, zero padded columns
+  double* b = nullptr;     // m
+  float* A32 = nullptr;    // m x npad, made by tls_factor when u = FP32
+  double norm2_A = 0.0, norm2_b = 0.0;
+
+  // factor
+  bool factored = false;
+  Prec u = Prec::FP32;
+  tls_prec uf_used = TLS_FP16;
+  tls_options opt{};
+  double* d = nullptr;       // column norms (npad)
+  double* dinv = nullptr;    // 1 / d
+  void* H = nullptr;         // scaled Gram (npad^2, float or double, see H_fp64)
+  bool H_fp64 = false;
+  void* R = nullptr;         // R_H rounded to u_f, stored in the u type (npad^2)
+  void* W = nullptr;         // R_H^{-1} (u type)
+  void* WT = nullptr;        // W^T (u type)
+  int shifts = 0;
+  double shift = 0.0;
+  double t_factor_ms = 0.0;
+
+  // solve workspace
+  double* x = nullptr;       // npad
+  double* x_best = nullptr;  // npad
+  double* f = nullptr;       // npad
+  void* vbuf = nullptr;      // u-type vectors: y, w, s, p0, p1, q (each 2 x npad)
+  void* part = nullptr;      // pass partials, u type: P x 2 x npad
+  double* part64 = nullptr;  // FP64 residual pass partials: P x npad
+  double* spart = nullptr;   // P x 2 x 2
+  double* sout = nullptr;    // 4 (residual) + 4 (PCGTLS)
+  double* gpart = nullptr;   // gemv / reduction partials (1024 x 4)
+  unsigned int* counter = nullptr;  // 4
+  PcgScalars* sc = nullptr;
+  RqiScalars* rs = nullptr;
+  int P64 = 0, PU = 0;
+  tls::ApassPlan plan64{}, planU{};
+  // pinned host mirrors
+  RqiScalars* h_rs = nullptr;
+  PcgScalars* h_sc = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-kernel-class CUDA-event timing (tls_profile_enable)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pcls;
+  int pused = 0;
+  double prof_ms[TLS_PROF_NCLASSES] = {};
+  int64_t prof_cnt[TLS_PROF_NCLASSES] = {};
+};
+
+namespace {
+
+void set_err(tls_ctx* c, const std::string& s) {
+  if (c) c->err = s;
+}
+
+tls_status cuda_status(tls_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TLS_OK;
+  set_err(c, std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? TLS_ERR_OOM : TLS_ERR_CUDA;
+}
+
+#define TLS_CK(call)                                                  \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return cuda_status(ctx, e_, #call);       \
+  } while (0)
+
+#define TLS_CK_LAUNCH(what)                                           \
+  do {                                                                \
+    cudaError_t e_ = cudaGetLastError();                              \
+    if (e_ != cudaSuccess) return cuda_status(ctx, e_, what);        \
+  } while (0)
+
+void* dev_alloc(tls_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (g_alloc) {
+    p = g_alloc((uint64_t)bytes, (void*)c->stream, g_alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->bufs.push_back({p, bytes});
+  return p;
+}
+
+void dev_free(tls_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->bufs.size(); ++i) {
+    if (c->bufs[i].ptr == p) {
+      if (g_free) g_free(p, (uint64_t)c->bufs[i].bytes, (void*)c->stream, g_alloc_user);
+      else cudaFree(p);
+      c->bufs.erase(c->bufs.begin() + (long)i);
+      return;
+    }
+  }
+}
+
+template <typename T>
+T* alloc_t(tls_ctx* c, int64_t count) {
+  return static_cast<T*>(dev_alloc(c, sizeof(T) * (size_t)count));
+}
+
+bool finite_all(const double* p, int64_t count) {
+  for (int64_t i = 0; i < count; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
+  ctx->m = m;
+  ctx->n = n;
+  ctx->npad = tls::round_up(n, tls::kPad);
+  ctx->mpad = tls::round_up(m, tls::kPad);
+  TLS_CK(cudaGetDevice(&ctx->device));
+  TLS_CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  if (stream) {
+    ctx->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    TLS_CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  TLS_CK(cudaEventCreate(&ctx->ev0));
+  TLS_CK(cudaEventCreate(&ctx->ev1));
+  TLS_CK(cudaMallocHost(&ctx->h_rs, sizeof(RqiScalars)));
+  TLS_CK(cudaMallocHost(&ctx->h_sc, sizeof(PcgScalars)));
+  const int64_t npad = ctx->npad;
+  ctx->b = alloc_t<double>(ctx, m);
+  ctx->x = alloc_t<double>(ctx, npad);
+  ctx->x_best = alloc_t<double>(ctx, npad);
+  ctx->f = alloc_t<double>(ctx, npad);
+  ctx->d = alloc_t<double>(ctx, npad);
+  ctx->dinv = alloc_t<double>(ctx, npad);
+  ctx->sout = alloc_t<double>(ctx, 8);
+  ctx->gpart = alloc_t<double>(ctx, 4096);
+  ctx->counter = alloc_t<unsigned int>(ctx, 4);
+  ctx->sc = alloc_t<PcgScalars>(ctx, 1);
+  ctx->rs = alloc_t<RqiScalars>(ctx, 1);
+  if (!ctx->b || !ctx->x || !ctx->x_best || !ctx->f || !ctx->d || !ctx->dinv || !ctx->sout ||
+      !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs) {
+    set_err(ctx, "device allocation failed");
+    return TLS_ERR_OOM;
+  }
+  TLS_CK(cudaMemsetAsync(ctx->counter, 0, 4 * sizeof(unsigned int), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->sc, 0, sizeof(PcgScalars), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->rs, 0, sizeof(RqiScalars), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * npad, ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->x_best, 0, sizeof(double) * npad, ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->f, 0, sizeof(double) * npad, ctx->stream));
+  // FP64 residual pass plan and partials
+  ctx->plan64 = tls::plan_apass<double>(m, npad, 1, ctx->num_sms);
+  ctx->P64 = ctx->plan64.grid;
+  ctx->part64 = alloc_t<double>(ctx, (int64_t)ctx->P64 * npad);
+  ctx->spart = alloc_t<double>(ctx, (int64_t)2 * ctx->num_sms * 2 * 2 + 16);
+  if (!ctx->part64 || !ctx->spart) {
+    set_err(ctx, "device allocation failed");
+    return TLS_ERR_OOM;
+  }
+  return TLS_OK;
+}
+
+void destroy_ctx(tls_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  while (!ctx->bufs.empty()) dev_free(ctx, ctx->bufs.back().ptr);
+  if (ctx->h_rs) cudaFreeHost(ctx->h_rs);
+  if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+size_t u_size(Prec u) { return u == Prec::FP64 ? 8 : 4; }
+
+// Brackets one kernel (or kernel group) with CUDA events on the context stream when
+// profiling is on; the times are collected after the next synchronisation.
+struct Prof {
+  tls_ctx* c;
+  int idx = -1;
+  Prof(tls_ctx* ctx, int cls) : c(ctx) {
+    if (!c->prof_on) return;
+    if ((size_t)(2 * c->pused + 2) > c->pev.size()) {
+      for (int k = 0; k < 2; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c->pev.push_back(e);
+      }
+      c->pcls.push_back(0);
+    }
+    idx = c->pused++;
+    c->pcls[idx] = cls;
+    cudaEventRecord(c->pev[2 * idx], c->stream);
+  }
+  ~Prof() {
+    if (idx >= 0) cudaEventRecord(c->pev[2 * idx + 1], c->stream);
+  }
+};
+
+void prof_collect(tls_ctx* c) {
+  for (int i = 0; i < c->pused; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->pev[2 * i], c->pev[2 * i + 1]) == cudaSuccess) {
+      c->prof_ms[c->pcls[i]] += ms;
+      c->prof_cnt[c->pcls[i]] += 1;
+    }
+  }
+  c->pused = 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// RQI residual block (FP64 pass over A): r, sigma^2, f, g, psi at ctx->x.
+// ---------------------------------------------------------------------------------------
+tls_status residual_pass(tls_ctx* ctx) {
+  {
+    Prof pr(ctx, TLS_PROF_RESID_PASS);
+    tls::launch_apass<double>(ctx->plan64, ctx->A64, ctx->npad, ctx->m, ctx->npad, 1, true,
+                              ctx->x, ctx->npad, ctx->b, ctx->part64, ctx->spart, ctx->sout,
+                              ctx->counter, nullptr, ctx->stream);
+  }
+  {
+    Prof pr(ctx, TLS_PROF_RESID_REDUCE);
+    tls::launch_resid_reduce(ctx->part64, ctx->P64, ctx->npad, ctx->x, ctx->f, ctx->sout,
+                             ctx->rs, ctx->gpart, ctx->stream);
+  }
+  TLS_CK_LAUNCH("residual pass");
+  return TLS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Paired PCGTLS (Alg. 3) in the u type T: nr right-hand sides fin0 * s0 and fin1.
+// ---------------------------------------------------------------------------------------
+// device address of the PCGTLS termination flags (no host dereference of the device pointer)
+const int* done_ptr(tls_ctx* ctx) {
+  return reinterpret_cast<const int*>(reinterpret_cast<const char*>(ctx->sc) +
+                                      offsetof(PcgScalars, done));
+}
+
+template <typename T>
+struct UVecs {
+  T *y, *w, *s, *p0, *p1, *q;
+};
+
+template <typename T>
+UVecs<T> uvecs(tls_ctx* ctx) {
+  T* base = static_cast<T*>(ctx->vbuf);
+  const int64_t k = 2 * ctx->npad;
+  return {base, base + k, base + 2 * k, base + 3 * k, base + 4 * k, base + 5 * k};
+}
+
+template <typename T>
+tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const double* fin1,
+                   double sigma2, int steps, double cg_tol, bool modeA) {
+  UVecs<T> v = uvecs<T>(ctx);
+  const int64_t npad = ctx->npad;
+  const T* Au = (ctx->u == Prec::FP64) ? reinterpret_cast<const T*>(ctx->A64)
+                                       : reinterpret_cast<const T*>(ctx->A32);
+  const T* W = static_cast<const T*>(ctx->W);
+  const T* WT = static_cast<const T*>(ctx->WT);
+  {
+    Prof pr(ctx, TLS_PROF_PCG_GEMV);
+    tls::launch_pcg_prep<T>(fin0, s0, fin1, nr, ctx->n, npad, ctx->dinv, v.y, v.w, v.p0, v.p1,
+                            ctx->sc, sigma2, cg_tol, ctx->stream);
+    tls::launch_gemv_wt<T>(WT, npad, v.y, v.s, nullptr, nullptr, ctx->gpart, ctx->sc, true,
+                           modeA, nr, ctx->stream);
+  }
+  T* pb[2] = {v.p0, v.p1};
+  for (int j = 0; j < steps; ++j) {
+    T* pcur = pb[j & 1];
+    T* pprev = pb[(j + 1) & 1];
+    {
+      Prof pr(ctx, TLS_PROF_PCG_GEMV);
+      tls::launch_gemv_w<T>(W, npad, v.s, pprev, pcur, ctx->dinv, v.q, ctx->gpart, ctx->sc, nr,
+                            ctx->stream);
+    }
+    if (modeA) {
+      {
+        Prof pr(ctx, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
+        tls::launch_apass<T>(ctx->planU, Au, npad, ctx->m, npad, nr, false, v.q, npad, nullptr,
+                             static_cast<T*>(ctx->part), ctx->spart, ctx->sout + 4,
+                             ctx->counter + 1, done_ptr(ctx), ctx->stream);
+      }
+      Prof pr(ctx, TLS_PROF_PCG_REDUCE);
+      tls::launch_pcg_reduce<T>(static_cast<const T*>(ctx->part), ctx->PU, npad, v.q, v.w, v.y,
+                                ctx->dinv, ctx->sc, ctx->sout + 4, nr, ctx->stream);
+    } else {
+      Prof pr(ctx, TLS_PROF_PCG_REDUCE);
+      tls::launch_pcg_update_R<T>(v.q, v.w, v.y, ctx->dinv, ctx->sc, nr, npad, ctx->stream);
+    }
+    {
+      Prof pr(ctx, TLS_PROF_PCG_GEMV);
+      tls::launch_gemv_wt<T>(WT, npad, v.y, v.s, pcur, nullptr, ctx->gpart, ctx->sc, false,
+                             modeA, nr, ctx->stream);
+    }
+  }
+  TLS_CK_LAUNCH("pcgtls");
+  return TLS_OK;
+}
+
+template <typename T>
+tls_status precond_apply(tls_ctx* ctx, const double* y) {
+  // q = R^{-1} R^{-T} y via one init step (s_0 = R^{-T} y) and one W product (beta = 0)
+  UVecs<T> v = uvecs<T>(ctx);
+  tls::launch_pcg_prep<T>(y, 1.0, nullptr, 1, ctx->n, ctx->npad, ctx->dinv, v.y, v.w, v.p0, v.p1,
+                          ctx->sc, 0.0, 0.0, ctx->stream);
+  tls::launch_gemv_wt<T>(static_cast<const T*>(ctx->WT), ctx->npad, v.y, v.s, nullptr, nullptr,
+                         ctx->gpart, ctx->sc, true, true, 1, ctx->stream);
+  tls::launch_gemv_w<T>(static_cast<const T*>(ctx->W), ctx->npad, v.s, v.p1, v.p0, ctx->dinv,
+                        v.q, ctx->gpart, ctx->sc, 1, ctx->stream);
+  TLS_CK_LAUNCH("precond");
+  return TLS_OK;
+}
+
+template <typename T>
+tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, double* sigma_out) {
+  const tls_options& o = ctx->opt;
+  const bool modeA = o.mode_A != 0;
+  UVecs<T> v = uvecs<T>(ctx);
+  cudaStream_t st = ctx->stream;
+  TLS_CK(cudaEventRecord(ctx->ev0, st));
+  // Alg. 2 line 1: LS start. Residual at x = 0 gives f = -A^T b; PCG with sigma^2 = 0.
+  TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * ctx->npad, st));
+  tls::launch_xx(ctx->x, ctx->rs, ctx->n, st);
+  tls_status stt = residual_pass(ctx);
+  if (stt != TLS_OK) return stt;
+  stt = run_pcg<T>(ctx, 1, ctx->f, -1.0, nullptr, 0.0, std::max(1, o.ls_iters), 0.0, modeA);
+  if (stt != TLS_OK) return stt;
+  {
+    Prof pr(ctx, TLS_PROF_VEC);
+    tls::launch_copy_to_x<T>(ctx->x, v.w, ctx->rs, ctx->n, st);
+  }
+  // lines 2-5: r_0, sigma_0^2, u_0 = (R^T R)^{-1} x_0, x_1 = x_0 + sigma_0^2 u_0
+  stt = residual_pass(ctx);
+  if (stt != TLS_OK) return stt;
+  stt = precond_apply<T>(ctx, ctx->x);
+  if (stt != TLS_OK) return stt;
+  {
+    Prof pr(ctx, TLS_PROF_VEC);
+    tls::launch_inverse_step<T>(ctx->x, v.q, ctx->rs, ctx->n, st);
+  }
+  TLS_CK_LAUNCH("inverse step");
+
+  const double scale = ctx->norm2_A + ctx->norm2_b;
+  double prev_psi = INFINITY;
+  int stop = TLS_STOP_MAX_RQI;
+  int best_k = 0, k = 0, cg_total = 0, not_spd = 0;
+  double best_psi = INFINITY, best_s2 = 0.0;
+  for (;;) {
+    ++k;
+    stt = residual_pass(ctx);
+    if (stt != TLS_OK) return stt;
+    TLS_CK(cudaMemcpyAsync(ctx->h_rs, ctx->rs, sizeof(RqiScalars), cudaMemcpyDeviceToHost, st));
+    if (k > 1)
+      TLS_CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+    TLS_CK(cudaStreamSynchronize(st));
+    if (k > 1) {
+      cg_total += ctx->h_sc->iters[0] + ctx->h_sc->iters[1];
+      not_spd |= ctx->h_sc->not_spd[0] | ctx->h_sc->not_spd[1];
+    }
+    const double psi = ctx->h_rs->psi, s2 = ctx->h_rs->sigma2;
+    if (!std::isfinite(psi) || !std::isfinite(s2)) {
+      stop = TLS_STOP_PSI_UP;
+      break;
+    }
+    const bool up = o.psi_rule_ge ? (psi >= prev_psi) : (psi > prev_psi);
+    if (up) {
+      stop = TLS_STOP_PSI_UP;
+      break;
+    }
+    best_k = k;
+    best_psi = psi;
+    best_s2 = s2;
+    TLS_CK(cudaMemcpyAsync(ctx->x_best, ctx->x, sizeof(double) * ctx->npad,
+                           cudaMemcpyDeviceToDevice, st));
+    if (psi <= tol * scale) {
+      stop = TLS_STOP_TOL;
+      break;
+    }
+    if (k > max_rqi) {
+      stop = TLS_STOP_MAX_RQI;
+      break;
+    }
+    prev_psi = psi;
+    const int steps = o.cg_fixed ? (k + 1) : std::max(1, o.cg_max);
+    stt = run_pcg<T>(ctx, 2, ctx->f, -1.0, ctx->x, s2, steps, o.cg_fixed ? 0.0 : o.cg_tol, modeA);
+    if (stt != TLS_OK) return stt;
+    {
+      Prof pr(ctx, TLS_PROF_VEC);
+      tls::launch_rqi_update<T>(ctx->x, v.w, v.w + ctx->npad, ctx->f, ctx->rs, ctx->n, st);
+    }
+    TLS_CK_LAUNCH("rqi update");
+  }
+  TLS_CK(cudaEventRecord(ctx->ev1, st));
+  TLS_CK(cudaEventSynchronize(ctx->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  prof_collect(ctx);
+  *sigma_out = std::sqrt(std::max(best_s2, 0.0));
+  if (info) {
+    info->stop_reason = stop;
+    info->rqi_steps = k;
+    info->best_k = best_k;
+    info->cg_iters = cg_total;
+    info->shifts = ctx->shifts;
+    info->not_spd = not_spd;
+    info->u_f_used = ctx->uf_used;
+    info->psi_final = best_psi;
+    info->sigma2 = best_s2;
+    info->shift = ctx->shift;
+    info->t_factor_ms = ctx->t_factor_ms;
+    info->t_solve_ms = ms;
+  }
+  return TLS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Factorisation ladder
+// ---------------------------------------------------------------------------------------
+Prec to_prec(tls_prec p) { return static_cast<Prec>((int)p); }
+
+tls_status ensure_solve_buffers(tls_ctx* ctx) {
+  const int64_t npad = ctx->npad;
+  const size_t us = u_size(ctx->u);
+  if (ctx->vbuf) dev_free(ctx, ctx->vbuf);
+  if (ctx->part) dev_free(ctx, ctx->part);
+  ctx->vbuf = dev_alloc(ctx, us * 12 * (size_t)npad);
+  if (ctx->u == Prec::FP64) ctx->planU = tls::plan_apass<double>(ctx->m, npad, 2, ctx->num_sms);
+  else ctx->planU = tls::plan_apass<float>(ctx->m, npad, 2, ctx->num_sms);
+  ctx->PU = ctx->planU.grid;
+  ctx->part = dev_alloc(ctx, us * (size_t)ctx->PU * 2 * (size_t)npad);
+  if (!ctx->vbuf || !ctx->part) {
+    set_err(ctx, "device allocation failed (solve buffers)");
+    return TLS_ERR_OOM;
+  }
+  TLS_CK(cudaMemsetAsync(ctx->vbuf, 0, us * 12 * (size_t)npad, ctx->stream));
+  return TLS_OK;
+}
+
+tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
+  cudaStream_t st = ctx->stream;
+  const int64_t m = ctx->m, n = ctx->n, npad = ctx->npad, mpad = ctx->mpad;
+  TLS_CK(cudaEventRecord(ctx->ev0, st));
+  // free previous factor buffers
+  for (void** p : {&ctx->H, &ctx->R, &ctx->W, &ctx->WT}) {
+    dev_free(ctx, *p);
+    *p = nullptr;
+  }
+  ctx->factored = false;
+  if (ctx->u == Prec::FP32 && ctx->A32 == nullptr) {
+    ctx->A32 = alloc_t<float>(ctx, m * npad);
+    if (!ctx->A32) {
+      set_err(ctx, "device allocation failed (FP32 copy of A)");
+      return TLS_ERR_OOM;
+    }
+  }
+  // column scaling D (Sec. 3.1); the FP32 copy of A for u = FP32 is written in the same pass
+  double* cpart = alloc_t<double>(ctx, 64 * npad);
+  if (!cpart) {
+    set_err(ctx, "device allocation failed");
+    return TLS_ERR_OOM;
+  }
+  {
+    Prof pr(ctx, TLS_PROF_SCALE);
+    tls::launch_colnorm(ctx->A64, npad, m, n, npad, ctx->u == Prec::FP32 ? ctx->A32 : nullptr,
+                        npad, ctx->d, nullptr, ctx->dinv, cpart, st);
+  }
+  TLS_CK_LAUNCH("column norms");
+  {
+    std::vector<double> hd(npad);
+    TLS_CK(cudaMemcpyAsync(hd.data(), ctx->d, sizeof(double) * npad, cudaMemcpyDeviceToHost, st));
+    TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * npad, st));
+    tls::launch_xx(ctx->b, ctx->rs, m, st);   // ||b||^2 into rs->xx (scratch use)
+    TLS_CK(cudaMemcpyAsync(ctx->h_rs, ctx->rs, sizeof(RqiScalars), cudaMemcpyDeviceToHost, st));
+    TLS_CK(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s += hd[j] * hd[j];
+    ctx->norm2_A = s;
+    ctx->norm2_b = ctx->h_rs->xx;
+  }
+  dev_free(ctx, cpart);
+
+  // the ladder of factor precisions (Sec. 3.1 constraints, escalation on breakdown)
+  std::vector<tls_prec> ladder;
+  ladder.push_back(uf_req);
+  if (uf_req == TLS_FP16 || uf_req == TLS_BF16) ladder.push_back(TLS_FP32);
+  if (uf_req != TLS_FP64) ladder.push_back(TLS_FP64);
+  int* dinfo = alloc_t<int>(ctx, 1);
+  if (!dinfo) return TLS_ERR_OOM;
+  ctx->shifts = 0;
+  ctx->shift = 0.0;
+  bool ok = false;
+  for (tls_prec uf : ladder) {
+    const Prec pf = to_prec(uf);
+    const bool chol64 = (pf == Prec::FP64);
+    const size_t ce = chol64 ? 8 : 4;
+    const size_t ae = (pf == Prec::FP64) ? 8 : (pf == Prec::FP32 ? 4 : 2);
+    void* AsT = dev_alloc(ctx, ae * (size_t)npad * (size_t)mpad);
+    ctx->H = dev_alloc(ctx, ce * (size_t)npad * (size_t)npad);
+    void* M = dev_alloc(ctx, ce * (size_t)npad * (size_t)npad);
+    if (!AsT || !ctx->H || !M) {
+      set_err(ctx, "device allocation failed (factor workspace)");
+      return TLS_ERR_OOM;
+    }
+    const bool from64 = (ctx->u != Prec::FP32) || (pf == Prec::FP64);
+    {
+      Prof pr(ctx, TLS_PROF_SCALE);
+      tls::launch_scale_cast_T(from64 ? (const void*)ctx->A64 : (const void*)ctx->A32, from64,
+                               npad, m, n, npad, mpad, ctx->dinv, AsT, pf, st);
+    }
+    {
+      Prof pr(ctx, TLS_PROF_GRAM);
+      bool tc = false;
+      if (pf == Prec::FP16 || pf == Prec::BF16)
+        tc = tls::launch_gram_tc(AsT, pf, n, npad, mpad, static_cast<float*>(ctx->H), st);
+      if (!tc) tls::launch_gram_simt(AsT, pf, n, npad, mpad, ctx->H, st);
+    }
+    TLS_CK_LAUNCH("gram");
+    dev_free(ctx, AsT);
+    const int max_shift = std::max(0, ctx->opt.max_shifts);
+    for (int sh = 0; sh <= max_shift; ++sh) {
+      const double shift = (sh == 0) ? 0.0 : std::ldexp(1.0, -10) * std::pow(4.0, sh - 1);
+      TLS_CK(cudaMemcpyAsync(M, ctx->H, ce * (size_t)npad * (size_t)npad,
+                             cudaMemcpyDeviceToDevice, st));
+      TLS_CK(cudaMemsetAsync(dinfo, 0, sizeof(int), st));
+      {
+        Prof pr(ctx, TLS_PROF_CHOL);
+        if (chol64)
+          tls::launch_cholesky<double>(static_cast<double*>(M), n, npad, shift, dinfo, nullptr, st);
+        else
+          tls::launch_cholesky<float>(static_cast<float*>(M), n, npad, shift, dinfo, nullptr, st);
+      }
+      TLS_CK_LAUNCH("cholesky");
+      int hinfo = 0;
+      TLS_CK(cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TLS_CK(cudaStreamSynchronize(st));
+      if (hinfo == 0) {
+        ok = true;
+        ctx->shift = shift;
+        break;
+      }
+      ctx->shifts += 1;
+    }
+    if (!ok) {
+      dev_free(ctx, M);
+      dev_free(ctx, ctx->H);
+      ctx->H = nullptr;
+      continue;
+    }
+    // R_H rounded to u_f (the computed factor R-hat), then carried in the u type
+    if (chol64) tls::launch_round_to<double>(static_cast<double*>(M), npad, pf, st);
+    else tls::launch_round_to<float>(static_cast<float*>(M), npad, pf, st);
+    const size_t us = u_size(ctx->u);
+    ctx->R = dev_alloc(ctx, us * (size_t)npad * (size_t)npad);
+    ctx->W = dev_alloc(ctx, us * (size_t)npad * (size_t)npad);
+    ctx->WT = dev_alloc(ctx, us * (size_t)npad * (size_t)npad);
+    void* work = dev_alloc(ctx, us * (size_t)npad * (size_t)npad);
+    if (!ctx->R || !ctx->W || !ctx->WT || !work) {
+      set_err(ctx, "device allocation failed (inverse factor)");
+      return TLS_ERR_OOM;
+    }
+    const int64_t cnt = npad * npad;
+    Prof pr(ctx, TLS_PROF_TRTRI);
+    if (ctx->u == Prec::FP64) {
+      if (chol64) TLS_CK(cudaMemcpyAsync(ctx->R, M, 8 * cnt, cudaMemcpyDeviceToDevice, st));
+      else tls::launch_f2d(static_cast<float*>(M), static_cast<double*>(ctx->R), cnt, st);
+      tls::launch_trtri<double>(static_cast<double*>(ctx->R), static_cast<double*>(ctx->W),
+                                static_cast<double*>(ctx->WT), static_cast<double*>(work), npad, st);
+    } else {
+      if (chol64) tls::launch_d2f(static_cast<double*>(M), static_cast<float*>(ctx->R), cnt, st);
+      else TLS_CK(cudaMemcpyAsync(ctx->R, M, 4 * cnt, cudaMemcpyDeviceToDevice, st));
+      tls::launch_trtri<float>(static_cast<float*>(ctx->R), static_cast<float*>(ctx->W),
+                               static_cast<float*>(ctx->WT), static_cast<float*>(work), npad, st);
+    }
+    TLS_CK_LAUNCH("triangular inverse");
+    dev_free(ctx, work);
+    dev_free(ctx, M);
+    ctx->uf_used = uf;
+    ctx->H_fp64 = chol64;
+    break;
+  }
+  dev_free(ctx, dinfo);
+  if (!ok) {
+    set_err(ctx, "Cholesky breakdown at every shift and precision");
+    return TLS_ERR_FACTOR_BREAKDOWN;
+  }
+  tls_status s2 = ensure_solve_buffers(ctx);
+  if (s2 != TLS_OK) return s2;
+  TLS_CK(cudaEventRecord(ctx->ev1, st));
+  TLS_CK(cudaEventSynchronize(ctx->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  prof_collect(ctx);
+  ctx->t_factor_ms = ms;
+  ctx->factored = true;
+  return TLS_OK;
+}
+
+template <typename T>
+static tls_status pcgtls_host(tls_ctx* ctx, int nr, double sigma2, const double* f0,
+                              const double* f1, int steps, double cg_tol, double* w0, double* w1,
+                              int* iters, int* not_spd) {
+  cudaStream_t st = ctx->stream;
+  const int64_t n = ctx->n, npad = ctx->npad;
+  // stage the right-hand sides in f (RHS 0) and x_best (RHS 1) of the context
+  TLS_CK(cudaMemsetAsync(ctx->f, 0, sizeof(double) * npad, st));
+  TLS_CK(cudaMemcpyAsync(ctx->f, f0, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if (nr > 1) {
+    TLS_CK(cudaMemsetAsync(ctx->x_best, 0, sizeof(double) * npad, st));
+    TLS_CK(cudaMemcpyAsync(ctx->x_best, f1, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  }
+  tls_status s = run_pcg<T>(ctx, nr, ctx->f, 1.0, ctx->x_best, sigma2, steps, cg_tol,
+                            ctx->opt.mode_A != 0);
+  if (s != TLS_OK) return s;
+  UVecs<T> v = uvecs<T>(ctx);
+  std::vector<T> hw((size_t)2 * npad);
+  TLS_CK(cudaMemcpyAsync(hw.data(), v.w, sizeof(T) * 2 * npad, cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaStreamSynchronize(st));
+  for (int64_t j = 0; j < n; ++j) {
+    w0[j] = (double)hw[j];
+    if (nr > 1 && w1) w1[j] = (double)hw[npad + j];
+  }
+  if (iters) { iters[0] = ctx->h_sc->iters[0]; iters[1] = ctx->h_sc->iters[1]; }
+  if (not_spd) { not_spd[0] = ctx->h_sc->not_spd[0]; not_spd[1] = ctx->h_sc->not_spd[1]; }
+  return TLS_OK;
+}
+
+template <typename T>
+static tls_status precond_host(tls_ctx* ctx, const double* y, double* s0, double* u) {
+  cudaStream_t st = ctx->stream;
+  const int64_t n = ctx->n, npad = ctx->npad;
+  TLS_CK(cudaMemsetAsync(ctx->f, 0, sizeof(double) * npad, st));
+  TLS_CK(cudaMemcpyAsync(ctx->f, y, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  tls_status s = precond_apply<T>(ctx, ctx->f);
+  if (s != TLS_OK) return s;
+  UVecs<T> v = uvecs<T>(ctx);
+  std::vector<T> hs(npad), hq(npad);
+  TLS_CK(cudaMemcpyAsync(hs.data(), v.s, sizeof(T) * npad, cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaMemcpyAsync(hq.data(), v.q, sizeof(T) * npad, cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaStreamSynchronize(st));
+  for (int64_t j = 0; j < n; ++j) {
+    if (s0) s0[j] = (double)hs[j];
+    if (u) u[j] = (double)hq[j];
+  }
+  return TLS_OK;
+}
+
+}  // namespace
+
+// =========================================================================================
+extern "C" {
+
+void tls_default_options(tls_options* opt) {
+  if (!opt) return;
+  opt->u = TLS_FP32;
+  opt->mode_A = 1;
+  opt->cg_fixed = 1;
+  opt->cg_tol = 1e-6;
+  opt->cg_max = 50;
+  opt->psi_rule_ge = 0;
+  opt->ls_iters = 12;
+  opt->max_shifts = 3;
+}
+
+const char* tls_status_str(tls_status s) {
+  switch (s) {
+    case TLS_OK: return "TLS_OK";
+    case TLS_ERR_ARG: return "TLS_ERR_ARG";
+    case TLS_ERR_CUDA: return "TLS_ERR_CUDA";
+    case TLS_ERR_OOM: return "TLS_ERR_OOM";
+    case TLS_ERR_STATE: return "TLS_ERR_STATE";
+    case TLS_ERR_FACTOR_BREAKDOWN: return "TLS_ERR_FACTOR_BREAKDOWN";
+    case TLS_ERR_NOT_SPD: return "TLS_ERR_NOT_SPD";
+    case TLS_ERR_NOT_UNIQUE: return "TLS_ERR_NOT_UNIQUE";
+    case TLS_ERR_NO_CONVERGENCE: return "TLS_ERR_NO_CONVERGENCE";
+    case TLS_ERR_TIMEOUT: return "TLS_ERR_TIMEOUT";
+  }
+  return "TLS_ERR_UNKNOWN";
+}
+
+const char* tls_last_error(const tls_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+void tls_set_allocator(tls_alloc_fn alloc, tls_free_fn release, void* user) {
+  g_alloc = alloc;
+  g_free = release;
+  g_alloc_user = user;
+}
+
+void tls_shape(const tls_ctx* ctx, int64_t* m, int64_t* n, int64_t* nnz) {
+  if (!ctx) return;
+  if (m) *m = ctx->m;
+  if (n) *n = ctx->n;
+  if (nnz) *nnz = ctx->nnz;
+}
+
+tls_status tls_create_dense(tls_ctx** out, int64_t m, int64_t n, const double* A, int64_t lda,
+                            const double* b, int on_device, void* stream) {
+  if (!out) return TLS_ERR_ARG;
+  *out = nullptr;
+  if (m < 1 || n < 1 || m < n || lda < n || !A || !b) return TLS_ERR_ARG;
+  if (!on_device) {
+    for (int64_t i = 0; i < m; ++i)
+      if (!finite_all(A + i * lda, n)) return TLS_ERR_ARG;
+    if (!finite_all(b, m)) return TLS_ERR_ARG;
+  }
+  tls_ctx* ctx = new tls_ctx();
+  tls_options o;
+  tls_default_options(&o);
+  ctx->opt = o;
+  tls_status s = ctx_common_init(ctx, m, n, stream);
+  if (s != TLS_OK) { destroy_ctx(ctx); return s; }
+  const int64_t npad = ctx->npad;
+  ctx->A64 = alloc_t<double>(ctx, m * npad);
+  if (!ctx->A64) { destroy_ctx(ctx); return TLS_ERR_OOM; }
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemsetAsync(ctx->A64, 0, sizeof(double) * m * npad, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(ctx->A64, sizeof(double) * npad, A, sizeof(double) * lda,
+                          sizeof(double) * n, m, kind, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->b, b, sizeof(double) * m, kind, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    tls_status st = cuda_status(ctx, e, "upload");
+    destroy_ctx(ctx);
+    return st;
+  }
+  *out = ctx;
+  return TLS_OK;
+}
+
+tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                          const int32_t* col_idx, const double* val, const double* b,
+                          int on_device, void* stream) {
+  // The CSR path expands A into the dense device layout until the sparse kernels land.
+  if (!out) return TLS_ERR_ARG;
+  *out = nullptr;
+  if (on_device || m < 1 || n < 1 || m < n || nnz < 0 || !row_ptr || !b) return TLS_ERR_ARG;
+  if (nnz > 0 && (!col_idx || !val)) return TLS_ERR_ARG;
+  if (row_ptr[0] != 0 || row_ptr[m] != nnz) return TLS_ERR_ARG;
+  std::vector<double> dense((size_t)m * (size_t)n, 0.0);
+  for (int64_t i = 0; i < m; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) return TLS_ERR_ARG;
+    int64_t prev = -1;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int64_t c = col_idx[e];
+      if (c < 0 || c >= n || c <= prev || !std::isfinite(val[e])) return TLS_ERR_ARG;
+      prev = c;
+      dense[(size_t)i * (size_t)n + (size_t)c] = val[e];
+    }
+  }
+  tls_status s = tls_create_dense(out, m, n, dense.data(), n, b, 0, stream);
+  if (s == TLS_OK) (*out)->nnz = nnz;
+  return s;
+}
+
+tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
+  if (!ctx) return TLS_ERR_ARG;
+  if ((int)u_f < 0 || (int)u_f > 3) {
+    set_err(ctx, "u_f must be FP16, BF16, FP32 or FP64");
+    return TLS_ERR_ARG;
+  }
+  tls_options o;
+  tls_default_options(&o);
+  if (opt) o = *opt;
+  if (o.u != TLS_FP32 && o.u != TLS_FP64) {
+    set_err(ctx, "u must be FP32 or FP64");
+    return TLS_ERR_ARG;
+  }
+  const int64_t limit = (o.u == TLS_FP64) ? 4096 : 8192;
+  if (ctx->npad > limit) {
+    set_err(ctx, "n too large for the dense path");
+    return TLS_ERR_ARG;
+  }
+  ctx->opt = o;
+  ctx->u = to_prec(o.u);
+  return factor_impl(ctx, u_f);
+}
+
+static tls_status solve_common(tls_ctx* ctx, double tol, int max_rqi, double* sigma,
+                               tls_info* info) {
+  if (!ctx || !sigma || max_rqi < 0 || !(tol >= 0.0)) return TLS_ERR_ARG;
+  if (!ctx->factored) {
+    set_err(ctx, "tls_solve called before a successful tls_factor");
+    return TLS_ERR_STATE;
+  }
+  if (ctx->u == Prec::FP64) return solve_impl<double>(ctx, tol, max_rqi, info, sigma);
+  return solve_impl<float>(ctx, tol, max_rqi, info, sigma);
+}
+
+tls_status tls_solve(tls_ctx* ctx, double tol, int max_rqi, double* x, double* sigma,
+                     tls_info* info) {
+  if (!x) return TLS_ERR_ARG;
+  tls_status s = solve_common(ctx, tol, max_rqi, sigma, info);
+  if (s != TLS_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(x, ctx->x_best, sizeof(double) * ctx->n,
+                                  cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  return cuda_status(ctx, e, "download x");
+}
+
+tls_status tls_solve_device(tls_ctx* ctx, double tol, int max_rqi, double* x_dev, double* sigma,
+                            tls_info* info) {
+  if (!x_dev) return TLS_ERR_ARG;
+  tls_status s = solve_common(ctx, tol, max_rqi, sigma, info);
+  if (s != TLS_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(x_dev, ctx->x_best, sizeof(double) * ctx->n,
+                                  cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  return cuda_status(ctx, e, "copy x");
+}
+
+tls_status tls_solve_batched(int count, tls_ctx* const* ctxs, double tol, int max_rqi,
+                             double* const* x, double* sigma, tls_info* infos,
+                             tls_status* per_problem) {
+  if (count < 0 || (count > 0 && (!ctxs || !x || !sigma))) return TLS_ERR_ARG;
+  tls_status first = TLS_OK;
+  for (int i = 0; i < count; ++i) {
+    tls_status s = tls_solve(ctxs[i], tol, max_rqi, x[i], sigma + i, infos ? infos + i : nullptr);
+    if (per_problem) per_problem[i] = s;
+    if (s != TLS_OK && first == TLS_OK) first = s;
+  }
+  return first;
+}
+
+void tls_destroy(tls_ctx* ctx) { destroy_ctx(ctx); }
+
+// ---------------------------------------------------------------------------------------
+// Inspection entry points (include/tls_debug.h)
+// ---------------------------------------------------------------------------------------
+tls_status tls_export_factor(tls_ctx* ctx, double* R_host, double* d_host, double* H_host) {
+  if (!ctx) return TLS_ERR_ARG;
+  if (!ctx->factored) return TLS_ERR_STATE;
+  const int64_t n = ctx->n, npad = ctx->npad;
+  std::vector<double> tmp((size_t)npad * npad);
+  cudaStream_t st = ctx->stream;
+  auto fetch = [&](const void* src, bool fp64) -> cudaError_t {
+    if (fp64) return cudaMemcpyAsync(tmp.data(), src, 8 * npad * npad, cudaMemcpyDeviceToHost, st);
+    std::vector<float> t32((size_t)npad * npad);
+    cudaError_t e = cudaMemcpyAsync(t32.data(), src, 4 * npad * npad, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (size_t i = 0; i < t32.size(); ++i) tmp[i] = t32[i];
+    return e;
+  };
+  if (R_host) {
+    TLS_CK(fetch(ctx->R, ctx->u == Prec::FP64));
+    TLS_CK(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) R_host[i * n + j] = tmp[i * npad + j];
+  }
+  if (H_host && ctx->H) {
+    TLS_CK(fetch(ctx->H, ctx->H_fp64));
+    TLS_CK(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) H_host[i * n + j] = tmp[i * npad + j];
+  }
+  if (d_host) {
+    TLS_CK(cudaMemcpyAsync(d_host, ctx->d, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    TLS_CK(cudaStreamSynchronize(st));
+  }
+  return TLS_OK;
+}
+
+tls_status tls_profile_enable(tls_ctx* ctx, int on) {
+  if (!ctx) return TLS_ERR_ARG;
+  ctx->prof_on = on != 0;
+  ctx->pused = 0;
+  for (int i = 0; i < TLS_PROF_NCLASSES; ++i) {
+    ctx->prof_ms[i] = 0.0;
+    ctx->prof_cnt[i] = 0;
+  }
+  return TLS_OK;
+}
+
+tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* ms) {
+  if (!ctx || cls < 0 || cls >= TLS_PROF_NCLASSES) return TLS_ERR_ARG;
+  if (count) *count = ctx->prof_cnt[cls];
+  if (ms) *ms = ctx->prof_ms[cls];
+  return TLS_OK;
+}
+
+uint64_t tls_kernel_launches(void) { return tls::g_launches.load(); }
+
+tls_status tls_residual(tls_ctx* ctx, const double* x_host, double* f_host, double* scal_host) {
+  if (!ctx || !x_host) return TLS_ERR_ARG;
+  cudaStream_t st = ctx->stream;
+  TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * ctx->npad, st));
+  TLS_CK(cudaMemcpyAsync(ctx->x, x_host, sizeof(double) * ctx->n, cudaMemcpyHostToDevice, st));
+  tls::launch_xx(ctx->x, ctx->rs, ctx->n, st);
+  tls_status s = residual_pass(ctx);
+  if (s != TLS_OK) return s;
+  TLS_CK(cudaMemcpyAsync(ctx->h_rs, ctx->rs, sizeof(RqiScalars), cudaMemcpyDeviceToHost, st));
+  if (f_host)
+    TLS_CK(cudaMemcpyAsync(f_host, ctx->f, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaStreamSynchronize(st));
+  if (scal_host) {
+    scal_host[0] = ctx->h_rs->sigma2;
+    scal_host[1] = ctx->h_rs->g;
+    scal_host[2] = ctx->h_rs->psi;
+    scal_host[3] = ctx->h_rs->rr;
+    scal_host[4] = ctx->h_rs->br;
+  }
+  return TLS_OK;
+}
+
+tls_status tls_pcgtls(tls_ctx* ctx, int nr, double sigma2, const double* f0, const double* f1,
+                      int steps, double cg_tol, double* w0, double* w1, int* iters,
+                      int* not_spd) {
+  if (!ctx || !f0 || !w0 || nr < 1 || nr > 2 || steps < 0 || (nr == 2 && !f1)) return TLS_ERR_ARG;
+  if (!ctx->factored) return TLS_ERR_STATE;
+  if (ctx->u == Prec::FP64)
+    return pcgtls_host<double>(ctx, nr, sigma2, f0, f1, steps, cg_tol, w0, w1, iters, not_spd);
+  return pcgtls_host<float>(ctx, nr, sigma2, f0, f1, steps, cg_tol, w0, w1, iters, not_spd);
+}
+
+tls_status tls_precond(tls_ctx* ctx, const double* y, double* s0, double* u) {
+  if (!ctx || !y) return TLS_ERR_ARG;
+  if (!ctx->factored) return TLS_ERR_STATE;
+  if (ctx->u == Prec::FP64) return precond_host<double>(ctx, y, s0, u);
+  return precond_host<float>(ctx, y, s0, u);
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <atomic>
+
+namespace tls {
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Every n-indexed dimension (columns of A, H, R, W and the n-vectors) is padded to a multiple
+// of kPad. The padding is zero in A and in vectors and the identity in H / R / W, so padded
+// entries never contribute and no kernel needs a ragged edge along n.
+constexpr int kPad = 64;
+
+// Number of kernels this library has launched (all contexts), for launch accounting.
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(int k = 1) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
+enum class Prec : int { FP16 = 0, BF16 = 1, FP32 = 2, FP64 = 3 };
+
+// Device scalars of one paired PCGTLS solve (Alg. 3), per right-hand side r in {0, 1}.
+struct PcgScalars {
+  double eta[2];      // eta_j = ||s_j||^2
+  double eta0[2];     // eta_0
+  double qq[2];       // ||q_j||^2
+  double pp[2];       // ||p_j||^2 (Alg. 3 as printed)
+  double tt[2];       // ||A q_j||^2 (A-explicit operator)
+  double alpha[2];    // alpha_j
+  double beta[2];     // beta_{j-1}: p_j = s_j + beta_{j-1} p_{j-1}
+  double delta[2];    // delta_j
+  double sigma2;      // shift of the system
+  double cg_tol2;     // relative tolerance squared on eta_j / eta_0 (0: off)
+  int done[2];        // RHS finished (eta = 0, delta <= 0 or tolerance met)
+  int not_spd[2];     // stopped on delta_j < 0
+  int iters[2];       // completed steps
+  int nr;             // number of right-hand sides (1 or 2)
+  int pad_;
+  unsigned int counter[4];   // last-block counters, always 0 between kernels
+};
+
+// Device scalars of one RQI residual step (Alg. 2 lines r_k .. g_k, Eq. (4)).
+struct RqiScalars {
+  double rr;          // ||r||^2
+  double br;          // b^T r
+  double xx;          // ||x||^2
+  double sigma2;      // rr / (1 + xx)
+  double g;           // -b^T r + sigma2
+  double ff;          // ||f||^2
+  double psi;         // sqrt((ff + g^2) / (xx + 1))
+  double zf, zx;      // z^T f, z^T x
+  double betak;       // beta_k
+  unsigned int counter[4];
+};
+
+// ---------------------------------------------------------------------------------------
+// Factorisation kernels (k_factor.cu)
+// ---------------------------------------------------------------------------------------
+// Column squared norms of A (m x n, row-major, lda) with an optional FP32 copy A32 (ld ldo).
+// d_out[j] = sqrt(sum_i a_ij^2) (FP64 out). part: scratch of grid x ld doubles.
+void launch_colnorm(const double* A, int64_t lda, int64_t m, int64_t n, int64_t npad,
+                    float* A32, int64_t ldo, double* d_out, float* dinv32, double* dinv64,
+                    double* part, cudaStream_t s);
+// AsT[j][i] = fl_prec(A[i][j] / d[j]) (transposed, n x mpad, zero padded). A is FP32 (A32)
+// or FP64 (A64) row-major; prec selects the output element type.
+void launch_scale_cast_T(const void* A, bool a_is_fp64, int64_t lda, int64_t m, int64_t n,
+                         int64_t npad, int64_t mpad, const double* dinv, void* AsT, Prec prec,
+                         cudaStream_t s);
+// H (npad x npad, type T = float for FP16/BF16/FP32 input, double for FP64) = AsT AsT^T,
+// identity on the padded diagonal.
+void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
+                      void* H, cudaStream_t s);
+// tcgen05 (UMMA) Gram for FP16/BF16 input into FP32 H. Returns false if the shape is not
+// supported (falls back to nothing: the caller decides).
+bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
+                    float* H, cudaStream_t s);
+// Blocked upper Cholesky in place on M (npad x npad, T), with shift added to the first n
+// diagonal entries first; info[0] = first failing global pivot + 1 (0: success).
+template <typename T>
+void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* work,
+                     cudaStream_t s);
+// Round the upper triangle of R (T) to prec in place (FP16/BF16); no-op for FP32/FP64.
+template <typename T>
+void launch_round_to(T* R, int64_t npad, Prec prec, cudaStream_t s);
+// W = R^{-1} (upper, npad x npad) and WT = W^T (row-major), both T. work: npad x npad T.
+template <typename T>
+void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, cudaStream_t s);
+// Convert FP32 <-> FP64 square matrices (used for escalation / export).
+void launch_f2d(const float* in, double* out, int64_t count, cudaStream_t s);
+void launch_d2f(const double* in, float* out, int64_t count, cudaStream_t s);
+void launch_set_identity_pad(void* M, bool fp64, int64_t n, int64_t npad, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// Solve kernels (k_solve.cu)
+// ---------------------------------------------------------------------------------------
+struct ApassPlan {
+  int grid;           // CTAs of the fused pass (= number of partials P)
+  int vpt;            // vectors per thread
+};
+template <typename T>
+ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms);
+
+// Fused pass over dense A: for every row i, c_r = (resid ? b_i - A_i.v_r : A_i.v_r);
+// part[cta][r][:] = sum over the CTA's rows of c_r A_i; sout[r][0] = sum c_r^2,
+// sout[r][1] = sum b_i c_r. v: nr vectors of stride ldv.
+template <typename T>
+void launch_apass(const ApassPlan& plan, const T* A, int64_t lda, int64_t m, int64_t npad,
+                  int nr, bool resid, const T* v, int64_t ldv, const double* b, T* part,
+                  double* spart, double* sout, unsigned int* counter, const int* done,
+                  cudaStream_t s);
+
+// PCGTLS (Alg. 3) building blocks, T = float or double (the precision u_p).
+// prep: y[r] = fin[r] / d (fin FP64, r < nr), w = p = 0, scalars reset.
+template <typename T>
+void launch_pcg_prep(const double* fin0, double fin0_scale, const double* fin1, int nr,
+                     int64_t n, int64_t npad, const double* dinv, T* y, T* w, T* p0, T* p1,
+                     PcgScalars* sc, double sigma2, double cg_tol, cudaStream_t s);
+// s = W^T y (init) or the s update of step j, partial ||s||^2, last CTA finalises eta/beta.
+template <typename T>
+void launch_gemv_wt(const T* WT, int64_t npad, const T* y, T* s, const T* p, T* sbuf_part,
+                    double* part, PcgScalars* sc, bool init, bool modeA, int nr,
+                    cudaStream_t s_);
+// p_j = s + beta p_prev (written to p_out), q = D^{-1} W p_j, partial ||q||^2 (and ||p||^2).
+template <typename T>
+void launch_gemv_w(const T* W, int64_t npad, const T* s, const T* p_prev, T* p_out,
+                   const double* dinv, T* q, double* part, PcgScalars* sc, int nr,
+                   cudaStream_t s_);
+// Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).
+template <typename T>
+void launch_pcg_reduce(const T* part, int P, int64_t npad, const T* q, T* w, T* y,
+                       const double* dinv, PcgScalars* sc, const double* tt, int nr,
+                       cudaStream_t s);
+// Alg. 3 as printed: w += alpha q, y = D^{-1} q (no pass over A).
+template <typename T>
+void launch_pcg_update_R(const T* q, T* w, T* y, const double* dinv, PcgScalars* sc, int nr,
+                         int64_t npad, cudaStream_t s);
+// RQI residual reduction (FP64): f = -A^T r - sigma2 x, psi etc.
+void launch_resid_reduce(const double* part, int P, int64_t npad, const double* x, double* f,
+                         const double* sout, RqiScalars* rs, double* fpart, cudaStream_t s);
+// x_{k+1} = z + beta_k u with z = x + w (Alg. 2), xx = ||x_{k+1}||^2.
+template <typename T>
+void launch_rqi_update(double* x, const T* w, const T* u, const double* f, RqiScalars* rs,
+                       int64_t n, cudaStream_t s);
+// x = x + sigma2 * u (Alg. 2 line 5), xx updated.
+template <typename T>
+void launch_inverse_step(double* x, const T* u, RqiScalars* rs, int64_t n, cudaStream_t s);
+// x = (double) w, xx updated.
+template <typename T>
+void launch_copy_to_x(double* x, const T* w, RqiScalars* rs, int64_t n, cudaStream_t s);
+// Down-convert an FP64 vector (n) to T into a buffer of npad (zero padded).
+template <typename T>
+void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaStream_t s);
+void launch_xx(const double* x, RqiScalars* rs, int64_t n, cudaStream_t s);
+
+}  // namespace tls

@@ -1,0 +1,334 @@
+"""Thin ctypes binding of ``libtls.so`` (include/tls.h, include/tls_debug.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels. The
+functions keep the C names. Host arrays are numpy float64; device inputs may be torch CUDA
+tensors (their data pointers are passed with ``on_device=1``). There is no CPU fallback: if
+the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TLS_FP16, TLS_BF16, TLS_FP32, TLS_FP64 = 0, 1, 2, 3
+PREC = {"fp16": TLS_FP16, "bf16": TLS_BF16, "fp32": TLS_FP32, "fp64": TLS_FP64}
+STOP_TOL, STOP_PSI_UP, STOP_MAX_RQI = 1, 2, 3
+
+STATUS = ["TLS_OK", "TLS_ERR_ARG", "TLS_ERR_CUDA", "TLS_ERR_OOM", "TLS_ERR_STATE",
+          "TLS_ERR_FACTOR_BREAKDOWN", "TLS_ERR_NOT_SPD", "TLS_ERR_NOT_UNIQUE",
+          "TLS_ERR_NO_CONVERGENCE", "TLS_ERR_TIMEOUT"]
+
+# every symbol the headers declare (checked by the CPU test suite)
+EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_factor", "tls_solve",
+           "tls_solve_device", "tls_solve_batched", "tls_destroy", "tls_status_str",
+           "tls_last_error", "tls_shape", "tls_set_allocator", "tls_export_factor",
+           "tls_residual", "tls_pcgtls", "tls_precond", "tls_profile_enable", "tls_profile_get",
+           "tls_kernel_launches"]
+
+PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
+                "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
+
+
+class tls_options(C.Structure):
+    _fields_ = [("u", C.c_int), ("mode_A", C.c_int), ("cg_fixed", C.c_int),
+                ("cg_tol", C.c_double), ("cg_max", C.c_int), ("psi_rule_ge", C.c_int),
+                ("ls_iters", C.c_int), ("max_shifts", C.c_int)]
+
+
+class tls_info(C.Structure):
+    _fields_ = [("stop_reason", C.c_int), ("rqi_steps", C.c_int), ("best_k", C.c_int),
+                ("cg_iters", C.c_int), ("shifts", C.c_int), ("not_spd", C.c_int),
+                ("u_f_used", C.c_int), ("psi_final", C.c_double), ("sigma2", C.c_double),
+                ("shift", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TLSError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+_LIB = None
+_ALLOC_REFS = None
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
+    """Load libtls.so (building it in-tree first if it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    lib_path = path or _build.LIB
+    if build_if_missing and path is None:
+        _build.build()
+    if not os.path.exists(lib_path):
+        raise RuntimeError(f"libtls.so not found at {lib_path}; run __graft_entry__.build()")
+    lib = C.CDLL(lib_path)
+    v, vp, i64 = C.c_void_p, C.POINTER(C.c_void_p), C.c_int64
+    sig = {
+        "tls_default_options": (None, [C.POINTER(tls_options)]),
+        "tls_create_dense": (C.c_int, [vp, i64, i64, v, i64, v, C.c_int, v]),
+        "tls_create_csr": (C.c_int, [vp, i64, i64, i64, v, v, v, v, C.c_int, v]),
+        "tls_factor": (C.c_int, [v, C.c_int, C.POINTER(tls_options)]),
+        "tls_solve": (C.c_int, [v, C.c_double, C.c_int, _dp, _dp, C.POINTER(tls_info)]),
+        "tls_solve_device": (C.c_int, [v, C.c_double, C.c_int, v, _dp, C.POINTER(tls_info)]),
+        "tls_solve_batched": (C.c_int, [C.c_int, vp, C.c_double, C.c_int, C.POINTER(_dp), _dp,
+                                        C.POINTER(tls_info), _ip]),
+        "tls_destroy": (None, [v]),
+        "tls_status_str": (C.c_char_p, [C.c_int]),
+        "tls_last_error": (C.c_char_p, [v]),
+        "tls_shape": (None, [v, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
+        "tls_set_allocator": (None, [v, v, v]),
+        "tls_export_factor": (C.c_int, [v, _dp, _dp, _dp]),
+        "tls_residual": (C.c_int, [v, _dp, _dp, _dp]),
+        "tls_pcgtls": (C.c_int, [v, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp, _dp,
+                                 _ip, _ip]),
+        "tls_precond": (C.c_int, [v, _dp, _dp, _dp]),
+        "tls_profile_enable": (C.c_int, [v, C.c_int]),
+        "tls_profile_get": (C.c_int, [v, C.c_int, C.POINTER(i64), _dp]),
+        "tls_kernel_launches": (C.c_uint64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        msg = ""
+        if ctx:
+            msg = (load().tls_last_error(ctx) or b"").decode()
+        raise TLSError(status, msg)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def tls_default_options(**overrides) -> tls_options:
+    o = tls_options()
+    load().tls_default_options(C.byref(o))
+    for k, val in overrides.items():
+        if k == "u" and isinstance(val, str):
+            val = PREC[val]
+        setattr(o, k, val)
+    return o
+
+
+def tls_create_dense(A, b, stream=None) -> C.c_void_p:
+    """A: (m, n) float64 numpy array (host) or torch CUDA tensor (device); b likewise."""
+    lib = load()
+    ctx = C.c_void_p()
+    st = C.c_void_p(stream) if stream else None
+    if hasattr(A, "is_cuda") and A.is_cuda:
+        m, n = A.shape
+        lda = A.stride(0)
+        _check(lib.tls_create_dense(C.byref(ctx), m, n, C.c_void_p(A.data_ptr()), lda,
+                                    C.c_void_p(b.data_ptr()), 1, st))
+    else:
+        A = _f64(A)
+        b = _f64(b)
+        m, n = A.shape
+        _check(lib.tls_create_dense(C.byref(ctx), m, n, A.ctypes.data_as(C.c_void_p), n,
+                                    b.ctypes.data_as(C.c_void_p), 0, st))
+    return ctx
+
+
+def tls_create_csr(m: int, n: int, row_ptr, col_idx, val, b, stream=None) -> C.c_void_p:
+    lib = load()
+    ctx = C.c_void_p()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    va = _f64(val)
+    bb = _f64(b)
+    st = C.c_void_p(stream) if stream else None
+    _check(lib.tls_create_csr(C.byref(ctx), m, n, int(rp[-1]), rp.ctypes.data_as(C.c_void_p),
+                              ci.ctypes.data_as(C.c_void_p), va.ctypes.data_as(C.c_void_p),
+                              bb.ctypes.data_as(C.c_void_p), 0, st))
+    return ctx
+
+
+def tls_factor(ctx, u_f="fp16", opt: tls_options | None = None):
+    uf = PREC[u_f] if isinstance(u_f, str) else int(u_f)
+    _check(load().tls_factor(ctx, uf, C.byref(opt) if opt is not None else None), ctx)
+
+
+def tls_shape(ctx) -> tuple[int, int, int]:
+    m, n, nnz = C.c_int64(), C.c_int64(), C.c_int64()
+    load().tls_shape(ctx, C.byref(m), C.byref(n), C.byref(nnz))
+    return m.value, n.value, nnz.value
+
+
+def tls_solve(ctx, tol: float = 0.0, max_rqi: int = 10):
+    """Returns (x, sigma, info dict)."""
+    _, n, _ = tls_shape(ctx)
+    x = np.zeros(n)
+    sigma = C.c_double()
+    info = tls_info()
+    _check(load().tls_solve(ctx, tol, max_rqi, _ptr(x), C.byref(sigma), C.byref(info)), ctx)
+    return x, sigma.value, info.as_dict()
+
+
+def tls_solve_device(ctx, x_dev_ptr: int, tol: float = 0.0, max_rqi: int = 10):
+    sigma = C.c_double()
+    info = tls_info()
+    _check(load().tls_solve_device(ctx, tol, max_rqi, C.c_void_p(x_dev_ptr), C.byref(sigma),
+                                   C.byref(info)), ctx)
+    return sigma.value, info.as_dict()
+
+
+def tls_solve_batched(ctxs, tol: float = 0.0, max_rqi: int = 10):
+    k = len(ctxs)
+    arr = (C.c_void_p * k)(*[c.value for c in ctxs])
+    xs = [np.zeros(tls_shape(c)[1]) for c in ctxs]
+    xp = (_dp * k)(*[_ptr(x) for x in xs])
+    sig = np.zeros(k)
+    infos = (tls_info * k)()
+    per = (C.c_int * k)()
+    st = load().tls_solve_batched(k, arr, tol, max_rqi, xp, _ptr(sig), infos, per)
+    return xs, sig, [i.as_dict() for i in infos], list(per), st
+
+
+def tls_destroy(ctx):
+    if ctx:
+        load().tls_destroy(ctx)
+
+
+def tls_status_str(status: int) -> str:
+    return load().tls_status_str(status).decode()
+
+
+def tls_last_error(ctx) -> str:
+    return (load().tls_last_error(ctx) or b"").decode()
+
+
+def tls_export_factor(ctx):
+    """Returns (R_H, d, H) as float64 numpy arrays."""
+    _, n, _ = tls_shape(ctx)
+    R = np.zeros((n, n))
+    d = np.zeros(n)
+    H = np.zeros((n, n))
+    _check(load().tls_export_factor(ctx, _ptr(R), _ptr(d), _ptr(H)), ctx)
+    return R, d, H
+
+
+def tls_residual(ctx, x):
+    _, n, _ = tls_shape(ctx)
+    x = _f64(x)
+    f = np.zeros(n)
+    sc = np.zeros(5)
+    _check(load().tls_residual(ctx, _ptr(x), _ptr(f), _ptr(sc)), ctx)
+    return f, {"sigma2": sc[0], "g": sc[1], "psi": sc[2], "rr": sc[3], "br": sc[4]}
+
+
+def tls_pcgtls(ctx, sigma2: float, f0, f1=None, steps: int = 1, cg_tol: float = 0.0):
+    _, n, _ = tls_shape(ctx)
+    nr = 1 if f1 is None else 2
+    f0 = _f64(f0)
+    f1a = _f64(f1) if f1 is not None else np.zeros(n)
+    w0 = np.zeros(n)
+    w1 = np.zeros(n)
+    it = (C.c_int * 2)()
+    bad = (C.c_int * 2)()
+    _check(load().tls_pcgtls(ctx, nr, sigma2, _ptr(f0), _ptr(f1a), steps, cg_tol, _ptr(w0),
+                             _ptr(w1), it, bad), ctx)
+    return w0, (w1 if nr == 2 else None), list(it), list(bad)
+
+
+def tls_precond(ctx, y):
+    _, n, _ = tls_shape(ctx)
+    y = _f64(y)
+    s0 = np.zeros(n)
+    u = np.zeros(n)
+    _check(load().tls_precond(ctx, _ptr(y), _ptr(s0), _ptr(u)), ctx)
+    return s0, u
+
+
+def tls_profile_enable(ctx, on: bool = True):
+    _check(load().tls_profile_enable(ctx, 1 if on else 0), ctx)
+
+
+def tls_profile_get(ctx) -> dict:
+    """{class name: (launches, device ms)} summed since tls_profile_enable."""
+    out = {}
+    for i, name in enumerate(PROF_CLASSES):
+        cnt = C.c_int64()
+        ms = C.c_double()
+        _check(load().tls_profile_get(ctx, i, C.byref(cnt), C.byref(ms)), ctx)
+        out[name] = (cnt.value, ms.value)
+    return out
+
+
+def tls_kernel_launches() -> int:
+    return int(load().tls_kernel_launches())
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch's caching allocator."""
+    global _ALLOC_REFS
+    lib = load()
+    if not enable:
+        lib.tls_set_allocator(None, None, None)
+        _ALLOC_REFS = None
+        return
+    import torch
+
+    ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
+    FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
+
+    def _alloc(nbytes, stream, user):
+        try:
+            dev = torch.cuda.current_device()
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+        except Exception:     # out of memory: the library reports TLS_ERR_OOM
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC(_alloc), FREE(_free)
+    _ALLOC_REFS = (a, f)
+    lib.tls_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), None)
+
+
+class Solver:
+    """Convenience owner of one context: create -> factor -> solve."""
+
+    def __init__(self, A, b, u_f="fp16", u="fp32", stream=None, **opts):
+        self.ctx = tls_create_dense(A, b, stream=stream)
+        self.opt = tls_default_options(u=u, **opts)
+        self.u_f = u_f
+
+    def factor(self):
+        tls_factor(self.ctx, self.u_f, self.opt)
+        return self
+
+    def solve(self, tol=0.0, max_rqi=10):
+        return tls_solve(self.ctx, tol, max_rqi)
+
+    def close(self):
+        tls_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if self.ctx:
+                self.close()
+        except Exception:
+            pass

@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads, it exports
+every function the headers declare, and argument validation rejects bad input before any
+device work."""
+from __future__ import annotations
+
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2305_19028_gb300 import tls
+from tests.conftest import ROOT
+
+
+def _declared_functions() -> set[str]:
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(tls_[a-z_0-9]+)\s*\(", src):
+            names.add(m.group(1))
+    # typedef'd callback types are not functions
+    return {n for n in names if not n.endswith("_fn")}
+
+
+def test_library_exports_every_declared_symbol():
+    lib = tls.load()
+    declared = _declared_functions()
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+    assert set(tls.EXPORTS) == declared
+
+
+def test_status_strings():
+    assert tls.tls_status_str(0) == "TLS_OK"
+    assert tls.tls_status_str(5) == "TLS_ERR_FACTOR_BREAKDOWN"
+    assert tls.tls_status_str(9) == "TLS_ERR_TIMEOUT"
+
+
+def test_default_options():
+    o = tls.tls_default_options()
+    assert o.u == tls.TLS_FP32 and o.mode_A == 1 and o.cg_fixed == 1 and o.ls_iters > 0
+
+
+def _create(m, n, A, b):
+    lib = tls.load()
+    ctx = C.c_void_p()
+    st = lib.tls_create_dense(C.byref(ctx), m, n, A.ctypes.data_as(C.c_void_p), n,
+                              b.ctypes.data_as(C.c_void_p), 0, None)
+    return st, ctx
+
+
+def test_create_rejects_bad_shapes_without_device():
+    A = np.ones((3, 5))
+    b = np.ones(3)
+    st, ctx = _create(3, 5, A, b)          # m < n
+    assert st == 1 and not ctx.value
+    st, ctx = _create(0, 0, A, b)
+    assert st == 1
+
+
+def test_create_rejects_nan_inf_on_host():
+    A = np.ones((6, 2))
+    A[2, 1] = np.nan
+    st, ctx = _create(6, 2, A, np.ones(6))
+    assert st == 1 and not ctx.value
+    A[2, 1] = 1.0
+    b = np.ones(6)
+    b[0] = np.inf
+    st, _ = _create(6, 2, A, b)
+    assert st == 1
+
+
+def test_csr_validation_on_host():
+    lib = tls.load()
+    ctx = C.c_void_p()
+    rp = np.array([0, 2, 3], dtype=np.int64)
+    ci = np.array([1, 0, 0], dtype=np.int32)          # not increasing in row 0
+    va = np.ones(3)
+    b = np.ones(2)
+    st = lib.tls_create_csr(C.byref(ctx), 2, 2, 3, rp.ctypes.data_as(C.c_void_p),
+                            ci.ctypes.data_as(C.c_void_p), va.ctypes.data_as(C.c_void_p),
+                            b.ctypes.data_as(C.c_void_p), 0, None)
+    assert st == 1 and not ctx.value
+
+
+def test_null_context_calls_are_rejected():
+    lib = tls.load()
+    assert lib.tls_factor(None, 0, None) == 1
+    x = np.zeros(2)
+    s = C.c_double()
+    assert lib.tls_solve(None, 0.0, 5, x.ctypes.data_as(tls._dp), C.byref(s), None) == 1
+    lib.tls_destroy(None)

@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical seeded
+inputs. Tolerances follow from the arithmetic of each step (stated per test)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle.rqi_pcgtls as O
+from paper_2305_19028_gb300 import synth, tls
+
+pytestmark = pytest.mark.gpu
+
+U16, UBF, U32, U64 = 2.0 ** -11, 2.0 ** -8, 2.0 ** -24, 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    tls.load()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+class Ctx:
+    def __init__(self, A, b, u_f="fp16", u="fp32", **opt):
+        self.ctx = tls.tls_create_dense(A, b)
+        self.opt = tls.tls_default_options(u=u, **opt)
+        tls.tls_factor(self.ctx, u_f, self.opt)
+
+    def __enter__(self):
+        return self.ctx
+
+    def __exit__(self, *a):
+        tls.tls_destroy(self.ctx)
+
+
+# ------------------------------------------------------------------------------------------
+# residual block (FP64): Alg. 2 lines r_k..g_k, Eq. (2), Eq. (4)
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("m,n", [(64, 1), (200, 37), (1000, 130), (3000, 700)])
+def test_residual_block_matches_oracle(m, n):
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=m + n)
+    x = p.x_true + 1e-3 * np.random.default_rng(0).standard_normal(n)
+    ctx = tls.tls_create_dense(p.A, p.b)
+    try:
+        f, sc = tls.tls_residual(ctx, x)
+    finally:
+        tls.tls_destroy(ctx)
+    r, s2, fo, go, psio = O.residual_block(p.A, p.b, x)
+    # FP64 dot products in a different order: error ~ n u (|A||x| + |b|) per entry of r
+    scale_r = n * U64 * (np.abs(p.A) @ np.abs(x) + np.abs(p.b)).max()
+    assert abs(sc["rr"] - r @ r) <= 4 * scale_r * np.linalg.norm(r) * np.sqrt(m) + 1e-300
+    assert abs(sc["sigma2"] - s2) <= 1e-10 * s2
+    fscale = m * U64 * (np.abs(p.A).T @ (np.abs(p.A) @ np.abs(x) + np.abs(p.b))).max()
+    assert np.max(np.abs(f - fo)) <= 8 * fscale
+    assert abs(sc["g"] - go) <= 8 * m * U64 * (np.abs(p.b) @ (np.abs(p.A) @ np.abs(x) + np.abs(p.b)))
+    assert abs(sc["psi"] - psio) <= 1e-6 * psio + 8 * fscale
+
+
+# ------------------------------------------------------------------------------------------
+# factor: column scaling, Gram of the u_f-rounded scaled matrix, Cholesky, R_H in u_f (Sec. 3.1)
+# ------------------------------------------------------------------------------------------
+def _rounded_scaled(A, d, u_f):
+    As = A.astype(np.float32).astype(np.float64) / d       # FP32 copy scaled in FP64
+    if u_f == "fp16":
+        return As.astype(np.float16).astype(np.float64)
+    if u_f == "bf16":
+        import torch
+        return torch.tensor(As).to(torch.bfloat16).to(torch.float64).numpy()
+    if u_f == "fp32":
+        return As.astype(np.float32).astype(np.float64)
+    return A / d
+
+
+@pytest.mark.parametrize("u_f,u", [("fp16", "fp32"), ("bf16", "fp32"), ("fp32", "fp32"),
+                                   ("fp64", "fp64")])
+@pytest.mark.parametrize("m,n", [(300, 64), (777, 130)])
+def test_factor_matches_definitions(u_f, u, m, n):
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=3)
+    with Ctx(p.A, p.b, u_f=u_f, u=u) as ctx:
+        R, d, H = tls.tls_export_factor(ctx)
+    # column norms: FP32 accumulation (u = fp32) or FP64
+    d_ref = np.linalg.norm(p.A, axis=0)
+    assert np.max(np.abs(d - d_ref) / d_ref) <= (m * U32 if u == "fp32" else 1e-13)
+    As = _rounded_scaled(p.A, d, u_f)
+    H_ref = As.T @ As
+    bound = (m * U32 if u_f != "fp64" else m * U64) * (np.abs(As).T @ np.abs(As))
+    assert np.all(np.abs(H - H_ref) <= 2 * bound + 1e-30)
+    # R_H upper triangular, representable in u_f, and a Cholesky factor of H up to rounding
+    assert np.allclose(R, np.triu(R), atol=0)
+    if u_f == "fp16":
+        assert np.array_equal(R, R.astype(np.float16).astype(np.float64))
+    ufac = {"fp16": U16, "bf16": UBF, "fp32": U32, "fp64": U64}[u_f]
+    berr = np.linalg.norm(R.T @ R - H) / np.linalg.norm(H)
+    assert berr <= 4 * ufac * np.sqrt(n) + (n * U32 if u_f != "fp64" else 0)
+
+
+# ------------------------------------------------------------------------------------------
+# preconditioner products and PCGTLS (Alg. 3) against the oracle with the same R
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("u_f,u", [("fp16", "fp32"), ("fp64", "fp64")])
+def test_precond_matches_oracle(u_f, u):
+    p = synth.dense_problem(500, 150, d_lo=1e-2, noise=1e-3, seed=5)
+    y = np.random.default_rng(1).standard_normal(150)
+    with Ctx(p.A, p.b, u_f=u_f, u=u) as ctx:
+        RH, d, _ = tls.tls_export_factor(ctx)
+        s0, uu = tls.tls_precond(ctx, y)
+    R = RH * d[None, :]
+    s_ref = sla.solve_triangular(R, y, trans="T", lower=False)
+    u_ref = sla.solve_triangular(R, s_ref, lower=False)
+    kap = np.linalg.cond(RH)
+    tol = (20 * kap * 150 * U32) if u == "fp32" else (20 * kap * 150 * U64)
+    assert _rel(s0, s_ref) <= tol
+    assert _rel(uu, u_ref) <= 2 * tol * kap
+
+
+@pytest.mark.parametrize("u_f,u", [("fp16", "fp32"), ("fp64", "fp64")])
+@pytest.mark.parametrize("modeA", [1, 0])
+def test_pcgtls_matches_oracle(u_f, u, modeA):
+    m, n = 900, 200
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=6)
+    rng = np.random.default_rng(2)
+    f0 = rng.standard_normal(n)
+    f1 = rng.standard_normal(n)
+    sigma2 = 0.3 * p.D[-1] ** 2
+    steps = 4
+    with Ctx(p.A, p.b, u_f=u_f, u=u, mode_A=modeA) as ctx:
+        RH, d, _ = tls.tls_export_factor(ctx)
+        w0, w1, it, bad = tls.tls_pcgtls(ctx, sigma2, f0, f1, steps=steps)
+        w0s, _, it1, _ = tls.tls_pcgtls(ctx, sigma2, f0, None, steps=steps)
+    R = RH * d[None, :]
+    mode = "A" if modeA else "R"
+    r0, i0, _ = O.pcgtls(p.A, R, sigma2, f0, steps - 1, mode=mode)
+    r1, i1, _ = O.pcgtls(p.A, R, sigma2, f1, steps - 1, mode=mode)
+    assert it == [steps, steps] and bad == [0, 0] and it1[0] == steps
+    kap = np.linalg.cond(RH)
+    tol = (50 * kap * n * U32) if u == "fp32" else (50 * kap * n * U64)
+    assert _rel(w0, r0) <= tol
+    assert _rel(w1, r1) <= tol
+    # the paired solve and the single solve share nothing but the pass over A
+    assert _rel(w0s, w0) <= tol
+
+
+def test_pcgtls_flags_indefinite_shift():
+    p = synth.dense_problem(300, 40, d_lo=1e-1, noise=1e-3, seed=7)
+    with Ctx(p.A, p.b, u_f="fp32", u="fp32") as ctx:
+        _, _, it, bad = tls.tls_pcgtls(ctx, 4.0 * p.D[0] ** 2, np.ones(40), None, steps=5)
+    assert bad[0] == 1 and it[0] < 5
+
+
+# ------------------------------------------------------------------------------------------
+# full RQI-PCGTLS solves: sigma rel err <= 1e-10, x rel err <= 1e-8 vs the FP64 oracle
+# ------------------------------------------------------------------------------------------
+CASES = [
+    # (m, n, d_lo, noise, u_f, u)
+    (400, 40, 1e-2, 1e-6, "fp64", "fp64"),     # the all-FP64 400 x 40 workload
+    (400, 40, 1e-2, 1e-6, "fp16", "fp32"),
+    (64, 1, 1e-1, 1e-3, "fp16", "fp32"),
+    (97, 97, 1e-1, 1e-3, "fp64", "fp64"),      # square
+    (1000, 130, 1e-3, 1e-4, "fp16", "fp32"),   # ragged n
+    (1000, 130, 1e-3, 1e-4, "bf16", "fp32"),
+    (2500, 300, 1e-3, 1e-4, "fp16", "fp32"),
+    (4096, 512, 1e-3, 1e-4, "fp16", "fp32"),
+    (4096, 512, 1e-3, 1e-4, "fp64", "fp64"),
+]
+
+
+@pytest.mark.parametrize("m,n,dlo,noise,u_f,u", CASES)
+def test_solve_matches_oracle(m, n, dlo, noise, u_f, u):
+    p = synth.dense_problem(m, n, d_lo=dlo, noise=noise, seed=0)
+    with Ctx(p.A, p.b, u_f=u_f, u=u) as ctx:
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+    xo, so, io = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    # relative 1e-10; for m = n, sigma_{n+1} = 0 exactly and both sides carry only rounding of
+    # size u ||[A, b]|| (Weyl), so the bar there is absolute
+    atol = 64 * U64 * (np.linalg.norm(p.A) + np.linalg.norm(p.b)) if m == n else 0.0
+    assert abs(sigma - so) <= 1e-10 * so + atol, (sigma, so, info)
+    assert _rel(x, xo) <= 1e-8, info
+    assert info["stop_reason"] in (tls.STOP_PSI_UP, tls.STOP_TOL, tls.STOP_MAX_RQI)
+
+
+def test_solve_before_factor_is_a_state_error():
+    p = synth.dense_problem(50, 5, seed=1)
+    ctx = tls.tls_create_dense(p.A, p.b)
+    try:
+        with pytest.raises(tls.TLSError) as e:
+            tls.tls_solve(ctx)
+        assert e.value.status == 4
+    finally:
+        tls.tls_destroy(ctx)
+
+
+def test_zero_column_breaks_down_then_shifts():
+    # A zero column makes H singular: the first pivot at that column is 0, so the factor must
+    # take the shift rung (Sec. 3.1 diagonal perturbation) before it succeeds.
+    p = synth.dense_problem(200, 30, d_lo=1e-1, noise=1e-3, seed=2)
+    A = p.A.copy()
+    A[:, 7] = 0.0
+    ctx = tls.tls_create_dense(A, p.b)
+    try:
+        tls.tls_factor(ctx, "fp16", tls.tls_default_options())
+        x, s, info = tls.tls_solve(ctx, tol=0.0, max_rqi=3)
+        assert info["shifts"] >= 1 and info["shift"] > 0
+    finally:
+        tls.tls_destroy(ctx)
