@@ -1,0 +1,374 @@
+"""Benchmark: TLS solves/s of RQI-PCGTLS on one GB300 (or N, weak scaling).
+
+One step = one complete solve of a resident 16384 x 2048 dense problem A = Y [diag(D); 0] Z^T
+(D log-spaced in [1e-3, 1], noise std 1e-4, seed 0 + rank): the preconditioner (column scaling,
+FP16 Gram on the GPU, Cholesky, inverse) and the RQI-PCGTLS iteration (FP32 PCGTLS, FP64
+residuals). A solve counts only if sigma rel err <= 1e-10 and x rel err <= 1e-8 against the
+FP64 CPU oracle run on the same problem.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TLS solves/s on GB300 at sigma rel err<=1e-10 vs FP64 oracle; mixed vs plain FP64"
+M_ROWS, N_COLS, D_LO, NOISE = 16384, 2048, 1e-3, 1e-4
+SIGMA_TOL, X_TOL = 1e-10, 1e-8
+SOLVE_TOL, MAX_RQI = 1e-16, 12
+WORKLOAD = f"dense_{M_ROWS}x{N_COLS}_uf16_u32_ur64"
+
+
+def _peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def _problem(rank: int):
+    from paper_2305_19028_gb300 import synth
+    return synth.dense_problem(M_ROWS, N_COLS, d_lo=D_LO, noise=NOISE, seed=rank)
+
+
+def _oracle_solve(p):
+    import oracle.rqi_pcgtls as O
+    return O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=MAX_RQI)
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict | None:
+        if self.proc is None or not self.path:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(value: float, ws: int) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, ws, rank):
+    """The FP64 CPU oracle, timed on the host cores as the reference arm."""
+    if rank != 0:
+        return
+    p = _problem(0)
+    for _ in range(args.warmup):
+        _oracle_solve(p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_solve(p)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS, "d_lo": D_LO, "noise": NOISE,
+                   "seed": 0, "solver": "FP64 CPU oracle (numpy/OpenBLAS), Householder QR R"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full solves of the {M_ROWS}x{N_COLS} problem"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int) -> dict:
+    cnt, ms = prof.get(cls, (0, 0.0))
+    if cnt == 0:
+        return {}
+    avg_s = ms / cnt * 1e-3
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    src = "measured" if peaks else "fallback"
+    if cls == "pcg_pass2":
+        unit_bytes = m * n * 4 + 2 * n * 4 * 2          # A_u once + q in / partial out
+        ach = unit_bytes / avg_s / 1e9
+        return {"kernel": "pcg_pass2 (fused t=Aq, A^T t, 2 RHS, FP32)", "bound": "hbm",
+                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": src, "avg_launch_us": avg_s * 1e6,
+                "algorithmic_bytes": unit_bytes}
+    if cls == "resid_pass":
+        unit_bytes = m * n * 8 + m * 8
+        ach = unit_bytes / avg_s / 1e9
+        return {"kernel": "resid_pass (FP64 r=b-Ax, A^T r)", "bound": "hbm",
+                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": src, "avg_launch_us": avg_s * 1e6,
+                "algorithmic_bytes": unit_bytes}
+    if cls == "gram":
+        flops = m * n * (n + 1)                          # SYRK: n(n+1)/2 entries x 2m flops
+        ach = flops / avg_s / 1e12
+        return {"kernel": "gram (H = A_s^T A_s, FP16 in, FP32 acc)", "bound": "tensor",
+                "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                "traffic": None, "peak_source": src + " (bf16 sustained; fp16 nominal rate equal)",
+                "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops}
+    if cls == "chol":
+        flops = n ** 3 / 3.0
+        ach = flops / avg_s / 1e12
+        return {"kernel": "chol (blocked Cholesky of H, FP32)", "bound": "tensor",
+                "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                "traffic": None, "peak_source": src, "avg_launch_us": avg_s * 1e6,
+                "algorithmic_flops": flops}
+    return {}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2305_19028_gb300 import tls
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    tls.load()
+    p = _problem(rank)
+    stream = torch.cuda.current_stream()
+    ctx = tls.tls_create_dense(p.A, p.b, stream=stream.cuda_stream)
+    opt = tls.tls_default_options(u="fp32")
+
+    # CPU oracle on rank 0 (accuracy reference and CPU baseline)
+    cpu = None
+    ref = None
+    if not args.no_cpu:
+        t0 = time.perf_counter()
+        xo, so, io = _oracle_solve(p)
+        t_or = time.perf_counter() - t0
+        ref = (xo, so)
+        if rank == 0:
+            cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": f"1 full FP64 solve of the {M_ROWS}x{N_COLS} problem "
+                             f"({t_or:.2f} s, numpy/OpenBLAS threads)"}
+
+    def accurate(x, s):
+        if ref is None:
+            return True
+        xo, so = ref
+        return (abs(s - so) / so <= SIGMA_TOL and
+                np.linalg.norm(x - xo) / np.linalg.norm(xo) <= X_TOL)
+
+    def step():
+        tls.tls_factor(ctx, "fp16", opt)
+        return tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
+
+    for _ in range(args.warmup):
+        step()
+    tls.tls_profile_enable(ctx, True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    l0 = tls.tls_kernel_launches()
+    ok = 0
+    infos = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            x, s, info = step()
+            ok += int(accurate(x, s))
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = tls.tls_kernel_launches() - l0
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms = _barrier_max(ms, ws)
+    prof = tls.tls_profile_get(ctx)
+    tls.tls_profile_enable(ctx, False)
+    clocks = clk.summary()
+    last_x, last_s = x, s
+    err = None
+    if ref is not None:
+        err = {"sigma_rel": abs(last_s - ref[1]) / ref[1],
+               "x_rel": float(np.linalg.norm(last_x - ref[0]) / np.linalg.norm(ref[0]))}
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        A_pin = torch.from_numpy(p.A).pin_memory().numpy()
+        b_pin = torch.from_numpy(p.b).pin_memory().numpy()
+        ne = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        okc = 0
+        e0.record(stream)
+        for _ in range(ne):
+            c2 = tls.tls_create_dense(A_pin, b_pin, stream=stream.cuda_stream)
+            tls.tls_factor(c2, "fp16", opt)
+            x2, s2, _ = tls.tls_solve(c2, tol=SOLVE_TOL, max_rqi=MAX_RQI)
+            tls.tls_destroy(c2)
+            okc += int(accurate(x2, s2))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = _barrier_max(e0.elapsed_time(e1), ws)
+        e2e = {"value": ws * okc / (ems * 1e-3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(p.A.nbytes + p.b.nbytes),
+               "d2h_bytes_per_step": int(8 * N_COLS + 8), "steps": ne,
+               "ms_per_step": ems / ne}
+
+    # plain all-FP64 GPU RQI-PCGTLS on the same problem, for the mixed-vs-plain comparison
+    plain = None
+    if not args.no_plain:
+        opt64 = tls.tls_default_options(u="fp64")
+        tls.tls_factor(ctx, "fp64", opt64)
+        tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
+        np_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        okp = 0
+        q0.record(stream)
+        for _ in range(np_steps):
+            tls.tls_factor(ctx, "fp64", opt64)
+            xp, sp, ip = tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
+            okp += int(accurate(xp, sp))
+        q1.record(stream)
+        torch.cuda.synchronize()
+        pms = _barrier_max(q0.elapsed_time(q1), ws)
+        plain = {"value": ws * okp / (pms * 1e-3), "unit": "solves/s",
+                 "ms_per_step": pms / np_steps, "steps": np_steps,
+                 "rqi_steps": ip["rqi_steps"], "cg_iters": ip["cg_iters"]}
+        if ref is not None:
+            plain["sigma_rel"] = abs(sp - ref[1]) / ref[1]
+            plain["x_rel"] = float(np.linalg.norm(xp - ref[0]) / np.linalg.norm(ref[0]))
+    tls.tls_destroy(ctx)
+
+    if rank != 0:
+        return
+    peaks = _peaks()
+    total = {k: v[1] for k, v in prof.items()}
+    dom = max(total, key=total.get)
+    share = {k: round(v / max(1e-9, sum(total.values())), 4) for k, v in total.items()}
+    roof = _roofline(prof, peaks, dom, M_ROWS, N_COLS) or _roofline(prof, peaks, "pcg_pass2",
+                                                                   M_ROWS, N_COLS)
+    inner = _roofline(prof, peaks, "pcg_pass2", M_ROWS, N_COLS)
+    value = ws * ok / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS, "d_lo": D_LO, "noise": NOISE,
+                   "seed": "rank", "u_f": "fp16", "u": "fp32", "u_r": "fp64",
+                   "solve_tol": SOLVE_TOL, "max_rqi": MAX_RQI,
+                   "l2": "inputs larger than L2 (A: 268 MB FP64 + 134 MB FP32 per step)",
+                   "step": "tls_factor + tls_solve on resident A"},
+        "accurate_steps": ok, "error_vs_oracle": err,
+        "rqi_steps": infos[-1]["rqi_steps"], "cg_iters": infos[-1]["cg_iters"],
+        "shifts": infos[-1]["shifts"], "u_f_used": infos[-1]["u_f_used"],
+        "fail_pivot": infos[-1]["fail_pivot"],
+        "t_factor_ms": infos[-1]["t_factor_ms"], "t_solve_ms": infos[-1]["t_solve_ms"],
+        "roofline": roof, "inner_loop_roofline": inner,
+        "kernel_share": share, "kernel_ms": {k: round(v, 4) for k, v in total.items()},
+        "kernel_launches": {k: v[0] for k, v in prof.items()},
+        "gpu_launches": int(launches),
+        "cpu_baseline": cpu, "e2e": e2e, "plain_fp64": plain, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

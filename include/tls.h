@@ -70,6 +70,15 @@ typedef struct {
   int psi_rule_ge;     /* 1: stop on psi_k >= psi_{k-1} (the rule of Sec. 4.2)                 */
   int ls_iters;        /* PCG steps (sigma^2 = 0) that produce the LS start x_0 (default 12)   */
   int max_shifts;      /* Cholesky retries with H + s I, s = 2^-10 * 4^i before escalating u_f */
+  int gram_simt;       /* 1: form H with the CUDA-core kernel even for FP16/BF16 (default 0:   */
+                       /* tensor cores, tcgen05)                                             */
+  double psi_accept;   /* an increase psi_k > psi_{k-1} stops only once psi_{k-1} <=           */
+                       /* psi_accept * (||A||_F^2 + ||b||^2); above it the increase is taken   */
+                       /* as a transient of the inexact inner solves (default 1e-12; a very   */
+                       /* large value gives the paper's rule exactly)                          */
+  int shift_first;     /* 1 (default): FP16/BF16 factors start from H + 2 u_f I, the diagonal  */
+                       /* perturbation of low-precision Cholesky; 0: start unshifted and shift */
+                       /* only after a breakdown                                              */
 } tls_options;
 
 typedef struct {
@@ -85,12 +94,15 @@ typedef struct {
   double shift;          /* the shift s of H + s I that was used (0 if none)                 */
   double t_factor_ms;    /* device time of the last tls_factor (CUDA events)                 */
   double t_solve_ms;     /* device time of this tls_solve                                    */
+  int fail_pivot;        /* pivot index of the last Cholesky breakdown before success (-1)   */
+  int n_psi;             /* entries of psi_hist filled                                       */
+  double psi_hist[24];   /* psi_k of the RQI loop, k = 1, 2, ... (first 24)                  */
 } tls_info;
 
 typedef struct tls_ctx tls_ctx;
 
 /* Default options: u = FP32, mode A, k+1 PCGTLS steps, strict psi rule, 12 LS steps,
- * 3 shifts. */
+ * 3 shifts, tensor-core Gram. */
 void tls_default_options(tls_options* opt);
 
 /*
@@ -122,8 +134,9 @@ tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz,
  * tls_factor -- build the preconditioner R in precision u_f (Alg. 4, the factorisation step;
  * Sec. 3.1): column scaling D, the Gram matrix H = (A D^{-1})^T (A D^{-1}) from A D^{-1}
  * rounded to u_f (tensor cores, FP32 accumulation, for FP16/BF16), Cholesky H + s I = R_H^T R_H
- * with R_H rounded to u_f, and R = R_H D. On a non-positive pivot it retries with shifts
- * s = 2^-10 * 4^i (i < max_shifts), then escalates u_f (FP16/BF16 -> FP32 -> FP64);
+ * with R_H rounded to u_f, and R = R_H D. The shift ladder is s = 0 or (shift_first, FP16/BF16)
+ * s = 2 u_f, then s = 2 u_f 4^i (i <= max_shifts) after each non-positive pivot; past the
+ * ladder it escalates u_f (FP16/BF16 -> FP32 -> FP64);
  * TLS_ERR_FACTOR_BREAKDOWN if FP64 fails too. opt may be NULL (defaults).
  */
 tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt);

@@ -116,8 +116,9 @@ template <typename Tin, typename Tc, bool AK, bool BKM>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(
     int M, int N, int K, const Tin* __restrict__ A, int64_t lda, int64_t sA,
     const Tin* __restrict__ B, int64_t ldb, int64_t sB, Tc* __restrict__ C, int64_t ldc,
-    int64_t sC, Tc alpha, Tc beta, int upper, int mirror) {
+    int64_t sC, Tc alpha, Tc beta, int upper, int mirror, const int* skip) {
   constexpr int BM = 64, BN = 64, BKT = 16;
+  if (skip != nullptr && *(volatile const int*)skip != 0) return;
   __shared__ Tc As[BKT][BM + 4];
   __shared__ Tc Bs[BKT][BN + 4];
   const int tile_i = blockIdx.y, tile_j = blockIdx.x;
@@ -181,11 +182,12 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(
 template <typename Tin, typename Tc, bool AK, bool BKM>
 void gemm_simt(int M, int N, int K, const Tin* A, int64_t lda, int64_t sA, const Tin* B,
                int64_t ldb, int64_t sB, Tc* C, int64_t ldc, int64_t sC, Tc alpha, Tc beta,
-               int upper, int mirror, int batch, cudaStream_t s) {
+               int upper, int mirror, int batch, cudaStream_t s, const int* skip = nullptr) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   gemm_simt_kernel<Tin, Tc, AK, BKM><<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C,
-                                                         ldc, sC, alpha, beta, upper, mirror); count_launch();
+                                                         ldc, sC, alpha, beta, upper, mirror,
+                                                         skip); count_launch();
 }
 
 __global__ void set_identity_pad_kernel(void* M, int fp64, int64_t n, int64_t npad) {
@@ -206,35 +208,57 @@ __global__ void add_shift_kernel(T* M, int64_t n, int64_t npad, double shift) {
   if (j < n) M[j * npad + j] += (T)shift;
 }
 
-// Factor the 64 x 64 diagonal block at kb (256 threads, one barrier per pivot). Pivot k's row
-// of R is written straight to global memory, so the smem copy of row k stays unscaled and the
-// trailing update of step k reads it as S[k][i] S[k][j] / S[k][k].
+// Round to the factor precision (round to nearest even), straight from the working type.
+__device__ __forceinline__ float round_prec(float v, int prec) {
+  if (prec == (int)Prec::FP16) return __half2float(__float2half_rn(v));
+  if (prec == (int)Prec::BF16) return __bfloat162float(__float2bfloat16_rn(v));
+  return v;
+}
+__device__ __forceinline__ double round_prec(double v, int prec) {
+  if (prec == (int)Prec::FP16) return (double)__half2float(__double2half(v));
+  if (prec == (int)Prec::BF16) return (double)__bfloat162float(__double2bfloat16(v));
+  if (prec == (int)Prec::FP32) return (double)(float)v;
+  return v;
+}
+
+// Diagonal block K = [kb, kb+64) of the blocked Cholesky H = R^T R (upper):
+//  1. factor the block (256 threads, one barrier per pivot; each finished row of R_KK, rounded
+//     to the factor precision, goes straight to global memory, so the shared copy keeps the
+//     unscaled row and the update of step k reads it as S[k][i] S[k][j] / S[k][k]);
+//  2. invert the rounded R_KK by a 2 x 2 recursion on 32-blocks,
+//     W_KK = [[X11, -X11 R12 X22], [0, X22]], X11 = R11^{-1}, X22 = R22^{-1}, into W.
+// W_KK turns the panel solve R_KJ = R_KK^{-T} H_KJ into a product, and it is also the diagonal
+// block of W = R^{-1}. Nothing runs if an earlier block broke down (*info != 0).
 template <typename T>
-__global__ void __launch_bounds__(256) potrf_diag_kernel(T* M, int64_t npad, int64_t kb, int* info) {
-  __shared__ T S[NB][NB + 1];
+__global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t npad, int64_t kb,
+                                                             int* info, int prec) {
+  if (*(volatile int*)info != 0) return;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T (*S)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm);
+  T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int e = tid; e < NB * NB; e += 256) {
     const int r = e / NB, c = e % NB;
     S[r][c] = M[(kb + r) * npad + kb + c];
   }
   __syncthreads();
+  bool broke = false;
   for (int k = 0; k < NB; ++k) {
     T piv = S[k][k];
     if (!(piv > T(0))) {                    // non-positive or NaN pivot: breakdown
       if (tid == 0) atomicCAS(info, 0, (int)(kb + k + 1));
       piv = T(1);
+      broke = true;
     }
     const T rkk = sqrt(piv);
     const T inv = T(1) / rkk;
     const T inv2 = inv * inv;
-    // row k of R (final): R[k][j] = S[k][j] / r_kk, zeros left of the diagonal
     if (tid < NB) {
       T v = T(0);
       if (tid == k) v = rkk;
       else if (tid > k) v = S[k][tid] * inv;
-      M[(kb + k) * npad + kb + tid] = v;
+      M[(kb + k) * npad + kb + tid] = round_prec(v, prec);
     }
-    // trailing update of the upper part: S[i][j] -= S[k][i] S[k][j] / S[k][k], k < i <= j
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int i = k + 1 + ty + 16 * a;
@@ -248,31 +272,43 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* M, int64_t npad, int
     }
     __syncthreads();
   }
-}
-
-// Panel: M[kb:kb+64, c] <- R11^{-T} M[kb:kb+64, c] for columns c >= kb + 64 (one per thread).
-template <typename T>
-__global__ void __launch_bounds__(128) trsm_panel_kernel(T* M, int64_t npad, int64_t kb) {
-  __shared__ T R[NB][NB + 1];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e % NB;
-    R[r][c] = M[(kb + r) * npad + kb + c];
+  if (broke) return;   // uniform: every thread saw the same pivots
+  // reload the rounded R_KK (this block's own global writes are visible after the barrier)
+  for (int e = tid; e < NB * NB; e += 256) {
+    const int r = e / NB, c = e % NB;
+    S[r][c] = (c >= r) ? M[(kb + r) * npad + kb + c] : T(0);
+    X[r][c] = T(0);
   }
   __syncthreads();
-  const int64_t col = kb + NB + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= npad) return;
-  T x[NB];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) x[i] = M[(kb + i) * npad + col];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    T v = x[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) v = fma(-R[k][i], x[k], v);
-    x[i] = v / R[i][i];
+  // X11 = R11^{-1} (threads 0..31) and X22 = R22^{-1} (threads 32..63), one column each
+  if (tid < 64) {
+    const int o = (tid < 32) ? 0 : 32, j = tid & 31;
+    for (int i = j; i >= 0; --i) {
+      T v = (i == j) ? T(1) : T(0);
+      for (int k = i + 1; k <= j; ++k) v = fma(-S[o + i][o + k], X[o + k][o + j], v);
+      X[o + i][o + j] = v / S[o + i][o + i];
+    }
   }
-#pragma unroll
-  for (int i = 0; i < NB; ++i) M[(kb + i) * npad + col] = x[i];
+  __syncthreads();
+  // Tm = R12 X22 into the (zero) lower-left quarter of S, then X12 = -X11 Tm
+  for (int e = tid; e < 32 * 32; e += 256) {
+    const int i = e / 32, j = e % 32;
+    T v = T(0);
+    for (int k = 0; k <= j; ++k) v = fma(S[i][32 + k], X[32 + k][32 + j], v);
+    S[32 + i][j] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < 32 * 32; e += 256) {
+    const int i = e / 32, j = e % 32;
+    T v = T(0);
+    for (int k = i; k < 32; ++k) v = fma(X[i][k], S[32 + k][j], v);
+    X[i][32 + j] = -v;
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += 256) {
+    const int r = e / NB, c = e % NB;
+    W[(kb + r) * npad + kb + c] = X[r][c];
+  }
 }
 
 template <typename T>
@@ -322,10 +358,7 @@ template <typename T>
 __global__ void round_kernel(T* R, int64_t count, int prec) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= count) return;
-  double v = (double)R[e];
-  if (prec == (int)Prec::FP16) v = (double)__half2float(__double2half(v));
-  else if (prec == (int)Prec::BF16) v = (double)__bfloat162float(__double2bfloat16(v));
-  R[e] = (T)v;
+  R[e] = round_prec(R[e], prec);
 }
 
 __global__ void f2d_kernel(const float* in, double* out, int64_t count) {
@@ -411,20 +444,29 @@ void launch_set_identity_pad(void* M, bool fp64, int64_t n, int64_t npad, cudaSt
 }
 
 template <typename T>
-void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* work,
+void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* Wd, Prec prec,
                      cudaStream_t s) {
-  (void)work;
-  if (shift != 0.0) add_shift_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(M, n, npad, shift); count_launch();
+  if (shift != 0.0) { add_shift_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(M, n, npad, shift); count_launch(); }
+  const size_t dsmem = 2 * sizeof(T) * NB * (NB + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(potrf_inv_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)dsmem);
+    attr = true;
+  }
   for (int64_t kb = 0; kb < npad; kb += NB) {
-    potrf_diag_kernel<T><<<1, 256, 0, s>>>(M, npad, kb, info); count_launch();
+    potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb, info, (int)prec); count_launch();
     const int64_t n2 = npad - kb - NB;
     if (n2 <= 0) break;
-    trsm_panel_kernel<T><<<blocks_for(n2, 128), 128, 0, s>>>(M, npad, kb); count_launch();
-    // trailing update M22 -= P^T P (upper part), P = M[kb:kb+64, kb+64:]
+    // panel R_KJ = W_KK^T H_KJ, in place over H_KJ
+    gemm_simt<T, T, false, false>(NB, (int)n2, NB, Wd + kb * npad + kb, npad, 0,
+                                  M + kb * npad + kb + NB, npad, 0, M + kb * npad + kb + NB, npad,
+                                  0, T(1), T(0), 0, 0, 1, s, info);
+    // trailing update H22 -= R_K2^T R_K2 (upper part)
     T* P = M + kb * npad + kb + NB;
     T* C = M + (kb + NB) * npad + kb + NB;
     gemm_simt<T, T, false, false>((int)n2, (int)n2, NB, P, npad, 0, P, npad, 0, C, npad, 0,
-                                  T(-1), T(1), 1, 0, 1, s);
+                                  T(-1), T(1), 1, 0, 1, s, info);
   }
   zero_lower_kernel<T><<<blocks_for(npad * npad, 256), 256, 0, s>>>(M, npad); count_launch();
 }
@@ -436,9 +478,12 @@ void launch_round_to(T* R, int64_t npad, Prec prec, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, cudaStream_t s) {
-  cudaMemsetAsync(W, 0, sizeof(T) * npad * npad, s);
-  trtri_diag_kernel<T><<<(unsigned)(npad / NB), NB, 0, s>>>(R, W, npad); count_launch();
+void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, bool have_diag,
+                  cudaStream_t s) {
+  if (!have_diag) {
+    cudaMemsetAsync(W, 0, sizeof(T) * npad * npad, s);
+    trtri_diag_kernel<T><<<(unsigned)(npad / NB), NB, 0, s>>>(R, W, npad); count_launch();
+  }
   // recursive doubling: for blocks A = [o, o+sz), B = [o+sz, o+sz+sB):
   //   W_AB = -W_AA R_AB W_BB
   for (int64_t sz = NB; sz < npad; sz *= 2) {
@@ -475,11 +520,11 @@ void launch_d2f(const double* in, float* out, int64_t count, cudaStream_t s) {
   d2f_kernel<<<blocks_for(count, 256), 256, 0, s>>>(in, out, count); count_launch();
 }
 
-template void launch_cholesky<float>(float*, int64_t, int64_t, double, int*, float*, cudaStream_t);
-template void launch_cholesky<double>(double*, int64_t, int64_t, double, int*, double*, cudaStream_t);
+template void launch_cholesky<float>(float*, int64_t, int64_t, double, int*, float*, Prec, cudaStream_t);
+template void launch_cholesky<double>(double*, int64_t, int64_t, double, int*, double*, Prec, cudaStream_t);
 template void launch_round_to<float>(float*, int64_t, Prec, cudaStream_t);
 template void launch_round_to<double>(double*, int64_t, Prec, cudaStream_t);
-template void launch_trtri<float>(const float*, float*, float*, float*, int64_t, cudaStream_t);
-template void launch_trtri<double>(const double*, double*, double*, double*, int64_t, cudaStream_t);
+template void launch_trtri<float>(const float*, float*, float*, float*, int64_t, bool, cudaStream_t);
+template void launch_trtri<double>(const double*, double*, double*, double*, int64_t, bool, cudaStream_t);
 
 }  // namespace tls

@@ -1,12 +1,345 @@
-// tcgen05 Gram kernel placeholder: returns false so the SIMT Gram runs.
+// Gram matrix H = A_s^T A_s of the u_f-rounded, column-scaled A on the 5th-generation tensor
+// cores (Sec. 3.1 of Oktay & Carson, arXiv 2305.19028: the preconditioner is built from
+// fl(A^T A) of the scaled matrix in the low precision u_q; here FP16/BF16 inputs with FP32
+// accumulation).
+//
+// A_s^T is stored n x mpad (K-major: the contraction index m is contiguous). One CTA computes
+// one 128 x 128 tile (I, J), I <= J, of the upper triangle and also writes its mirror:
+//   warp 0   one thread issues TMA loads (128B-swizzled boxes of 128 rows x 64 K) into a
+//            6-stage shared-memory ring, completion tracked by mbarriers;
+//   warp 1   allocates 128 TMEM columns and one thread issues tcgen05.mma (M = N = 128,
+//            K = 16, FP32 accumulator in TMEM), releasing ring stages with tcgen05.commit;
+//   warps 2-5 read the accumulator with tcgen05.ld (32 lanes x 32 columns per load) and
+//            store the tile and its transpose to H.
+// Every mbarrier wait is bounded by a global-timer deadline: on expiry the kernel records an
+// error code, stops issuing work, frees its TMEM and returns (the host then falls back).
 #include "tls_internal.h"
+
+#include <cuda.h>
+
+#include <cstdio>
 
 namespace tls {
 
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 64;     // tile, K block (64 x 2 B = one 128B atom)
+constexpr int STAGES = 6;
+constexpr int STAGE_BYTES = TBM * TBK * 2;        // 16 KB per operand per stage
+constexpr int THREADS = 192;
+constexpr uint64_t WAIT_NS = 500ull * 1000 * 1000; // 0.5 s per wait, far above any real wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false (after recording `code` in *err) if the phase did not complete
+// before the deadline.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > WAIT_NS) {
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+  d |= (uint64_t)(16u >> 4) << 16;                    // leading byte offset (unused here)
+  d |= (uint64_t)(1024u >> 4) << 32;                  // stride byte offset
+  d |= (uint64_t)1 << 46;                             // descriptor version
+  d |= (uint64_t)2 << 61;                             // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor for kind::f16: D = FP32, A/B = FP16 (fmt 0) or BF16 (fmt 1), both
+// K-major, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt) {
+  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(TBN >> 3) << 17) |
+         ((uint32_t)(TBM >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int nt, int kblocks, int npad,
+                   float* __restrict__ H, uint32_t idesc, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled stages
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = smem;                                  // STAGES x 16 KB
+  unsigned char* sB = smem + STAGES * STAGE_BYTES;           // STAGES x 16 KB
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  // tile (I, J), I <= J, from the linear block index over the upper triangle
+  int t = blockIdx.x, I = 0;
+  while (t >= nt - I) { t -= nt - I; ++I; }
+  const int J = I + t;
+  const bool diag = (I == J);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    const uint32_t bytes = diag ? STAGE_BYTES : 2 * STAGE_BYTES;
+    int issued = 0;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % STAGES, it = kb / STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty_bar[s], (it - 1) & 1, err, 1)) {
+        abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      mbar_expect_tx(&full_bar[s], bytes);
+      tma_load_2d(sA + s * STAGE_BYTES, &tmap, &full_bar[s], kb * TBK, I * TBM);
+      if (!diag) tma_load_2d(sB + s * STAGE_BYTES, &tmap, &full_bar[s], kb * TBK, J * TBN);
+      issued = kb + 1;
+    }
+    // make sure no issued copy is still landing in shared memory when the CTA retires
+    const int first = issued > STAGES ? issued - STAGES : 0;
+    for (int kb = first; kb < issued; ++kb)
+      mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, err, 2);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    bool ok = true;
+    for (int kb = 0; kb < kblocks && ok; ++kb) {
+      const int s = kb % STAGES, it = kb / STAGES;
+      if (!mbar_wait(&full_bar[s], it & 1, err, 3) || *(volatile int*)&abort_flag) {
+        abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + s * STAGE_BYTES);
+      const uint32_t b0 = diag ? a0 : smem_u32(sB + s * STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < TBK / 16; ++kk) {
+        umma_f16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                 (kb | kk) != 0 ? 1u : 0u);
+      }
+      umma_commit(&empty_bar[s]);
+    }
+    umma_commit(&acc_bar);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: TMEM -> H (tile and mirror) ----------------
+    const int q = warp & 3;                         // TMEM lane quadrant of this warp
+    const bool mine = mbar_wait(&acc_bar, 0, err, 4) && !*(volatile int*)&abort_flag;
+    const bool ready = __all_sync(0xffffffffu, mine);   // warp-uniform for tcgen05.ld
+    tc_fence_after();
+    if (ready) {
+      const int row = I * TBM + q * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < TBN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        const int col0 = J * TBN + c0;
+        if (row < npad && col0 < npad) {
+          float4* dst = reinterpret_cast<float4*>(H + (int64_t)row * npad + col0);
+#pragma unroll
+          for (int v = 0; v < 8; ++v)
+            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                 __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+          if (!diag) {
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc) H[(int64_t)(col0 + cc) * npad + row] = __uint_as_float(r[cc]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+int* g_err = nullptr;   // device error word of the tensor-core kernels (one per process)
+
+}  // namespace
+
+bool gram_tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && get_encoder() != nullptr;
+}
+
+int gram_tc_error(cudaStream_t s) {
+  if (!g_err) return 0;
+  int h = 0;
+  cudaMemcpyAsync(&h, g_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (h) cudaMemsetAsync(g_err, 0, sizeof(int), s);
+  return h;
+}
+
 bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad, float* H,
                     cudaStream_t s) {
-  (void)AsT; (void)prec; (void)n; (void)npad; (void)mpad; (void)H; (void)s;
-  return false;
+  if (prec != Prec::FP16 && prec != Prec::BF16) return false;
+  if (!gram_tc_available()) return false;
+  if ((reinterpret_cast<uintptr_t>(AsT) & 15) != 0 || (mpad % TBK) != 0) return false;
+  if (!g_err) {
+    if (cudaMalloc(&g_err, sizeof(int)) != cudaSuccess) { (void)cudaGetLastError(); g_err = nullptr; return false; }
+    cudaMemset(g_err, 0, sizeof(int));
+  }
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {(cuuint64_t)mpad, (cuuint64_t)npad};
+  const cuuint64_t gstride[1] = {(cuuint64_t)mpad * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)TBM};
+  const cuuint32_t estride[2] = {1, 1};
+  CUresult r = get_encoder()(&map,
+                             prec == Prec::FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                             2, const_cast<void*>(AsT), gdim, gstride, box, estride,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  const int nt = (int)((npad + TBM - 1) / TBM);
+  const int tiles = nt * (nt + 1) / 2;
+  const size_t smem = 2 * STAGES * STAGE_BYTES + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const uint32_t idesc = idesc_f16(prec == Prec::FP16 ? 0u : 1u);
+  gram_tc_kernel<<<tiles, THREADS, smem, s>>>(map, nt, (int)(mpad / TBK), (int)npad, H, idesc,
+                                              g_err);
+  count_launch();
+  launch_set_identity_pad(H, false, n, npad, s);
+  return cudaGetLastError() == cudaSuccess;
 }
 
 }  // namespace tls

@@ -10,6 +10,7 @@
 //    W = R_H^{-1} (R = R_H D), fused with the p and s recurrences of Alg. 3.
 //  * FP64 RQI vector kernels: the x_{k+1} update of Alg. 2 and the inverse-iteration start.
 #include "tls_internal.h"
+#include "tls_ptx.cuh"
 
 #include <algorithm>
 
@@ -197,6 +198,168 @@ __global__ void __launch_bounds__(kThreads) apass_kernel(
     buf ^= 1;
   }
   // publish this CTA's partial of A^T c
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+    if (col < npad)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        V x;
+        if constexpr (VW == 4) {
+          x = make_float4(acc[r][k * 4], acc[r][k * 4 + 1], acc[r][k * 4 + 2], acc[r][k * 4 + 3]);
+        } else {
+          x = make_double2(acc[r][k * 2], acc[r][k * 2 + 1]);
+        }
+        *reinterpret_cast<V*>(part + ((int64_t)blockIdx.x * NR + r) * npad + col) = x;
+      }
+  }
+  if (tid == 0)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      spart[((int64_t)blockIdx.x * NR + r) * 2 + 0] = s_cc[r];
+      spart[((int64_t)blockIdx.x * NR + r) * 2 + 1] = s_bc[r];
+    }
+  if (arrive_last(counter)) {
+    reduce_partials<2 * NR>(spart, (int)gridDim.x, sout);
+    if (tid == 0) *counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// The same fused pass with the rows staged through shared memory by 1-D bulk async copies
+// (cp.async.bulk, completion on mbarriers). A CTA owns a contiguous block of rows, i.e. one
+// contiguous span of A, and streams it in tiles of RT rows through a kApStages-deep ring, so
+// up to kApStages-1 tiles are in flight while the block reduces the current one. A stage is
+// refilled right after the barrier of the following tile, when every thread has finished with
+// it. Requires lda == npad (rows back to back).
+// ---------------------------------------------------------------------------------------
+constexpr int kApStages = 4;
+
+template <typename T, int NR, bool RESID, int VPT>
+__global__ void __launch_bounds__(kThreads, 1) apass_tma_kernel(
+    const T* __restrict__ A, int64_t m, int64_t npad, const T* __restrict__ v, int64_t ldv,
+    const double* __restrict__ b, T* __restrict__ part, double* __restrict__ spart,
+    double* __restrict__ sout, unsigned int* counter, const int* __restrict__ done, int* err) {
+  using V = typename VecOf<T>::type;
+  constexpr int VW = VecOf<T>::W;
+  constexpr int RT = (VPT >= 8) ? 1 : (8 / VPT);   // rows per tile
+  constexpr int E = VPT * VW;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  T* ring = reinterpret_cast<T*>(dsm);
+  __shared__ uint64_t full[kApStages];
+  __shared__ T red[2][kWarps][NR * RT];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (done != nullptr) {
+    bool all = true;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) all = all && (done[r] != 0);
+    if (all) return;
+  }
+  T vv[NR][E], acc[NR][E];
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      V x = zero_vec(T(0));
+      if (col < npad) x = *reinterpret_cast<const V*>(v + r * ldv + col);
+#pragma unroll
+      for (int c = 0; c < VW; ++c) { vv[r][k * VW + c] = get(x, c); acc[r][k * VW + c] = T(0); }
+    }
+  }
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = min(m, r0 + per);
+  const int ntiles = (r1 > r0) ? (int)((r1 - r0 + RT - 1) / RT) : 0;
+  const int64_t stage_elems = (int64_t)RT * npad;
+  auto issue = [&](int t) {
+    const int64_t row = r0 + (int64_t)t * RT;
+    const int rows = (int)min((int64_t)RT, r1 - row);
+    const uint32_t bytes = (uint32_t)(rows * npad * (int64_t)sizeof(T));
+    uint64_t* bar = &full[t % kApStages];
+    ptx::mbar_expect_tx(bar, bytes);
+    ptx::bulk_g2s(ring + (t % kApStages) * stage_elems, A + row * npad, bytes, bar);
+  };
+  if (tid == 0) {
+    for (int s2 = 0; s2 < kApStages; ++s2) ptx::mbar_init(&full[s2], 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int t = 0; t < kApStages && t < ntiles; ++t) issue(t);
+  double s_cc[NR], s_bc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) { s_cc[r] = 0.0; s_bc[r] = 0.0; }
+  int buf = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    const int64_t i0 = r0 + (int64_t)t * RT;
+    ptx::mbar_wait(&full[t % kApStages], (uint32_t)((t / kApStages) & 1), err, 11);
+    const T* tile = ring + (t % kApStages) * stage_elems;
+    T pd[NR][RT];
+#pragma unroll
+    for (int rt = 0; rt < RT; ++rt) {
+      const bool rv = (i0 + rt) < r1;
+      V a[VPT];
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+        a[k] = (rv && col < npad) ? *reinterpret_cast<const V*>(tile + rt * npad + col)
+                                  : zero_vec(T(0));
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        T tt = T(0);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k)
+#pragma unroll
+          for (int c = 0; c < VW; ++c) tt = fma(get(a[k], c), vv[r][k * VW + c], tt);
+        pd[r][rt] = warp_sum(tt);
+      }
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int rt = 0; rt < RT; ++rt) red[buf][warp][r * RT + rt] = pd[r][rt];
+    __syncthreads();
+    // every thread is done with tile t-1: refill its stage with tile t-1+kApStages
+    if (tid == 0 && t >= 1 && t - 1 + kApStages < ntiles) {
+      ptx::fence_proxy_async();
+      issue(t - 1 + kApStages);
+    }
+#pragma unroll
+    for (int rt = 0; rt < RT; ++rt) {
+      const int64_t row = i0 + rt;
+      const bool valid = row < r1;
+      double brow = 0.0;
+      if (RESID && valid) brow = b[row];
+      V a[VPT];
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+        a[k] = (valid && col < npad) ? *reinterpret_cast<const V*>(tile + rt * npad + col)
+                                     : zero_vec(T(0));
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        T dot = T(0);
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) dot += red[buf][w][r * RT + rt];
+        T c = T(0);
+        if (valid) c = RESID ? (T)(brow - (double)dot) : dot;
+        if (tid == 0) {
+          s_cc[r] = fma((double)c, (double)c, s_cc[r]);
+          s_bc[r] = fma(brow, (double)c, s_bc[r]);
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k)
+#pragma unroll
+          for (int cc = 0; cc < VW; ++cc)
+            acc[r][k * VW + cc] = fma(c, get(a[k], cc), acc[r][k * VW + cc]);
+      }
+    }
+    buf ^= 1;
+  }
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
     const int64_t col = ((int64_t)k * kThreads + tid) * VW;
@@ -614,6 +777,32 @@ __global__ void vec_convert_kernel(const double* __restrict__ in, T* __restrict_
 inline int blocks_for(int64_t count, int threads) { return (int)((count + threads - 1) / threads); }
 
 template <typename T, int NR, bool RESID>
+void apass_tma_dispatch(int vpt, dim3 grid, size_t smem, const T* A, int64_t m, int64_t npad,
+                        const T* v, int64_t ldv, const double* b, T* part, double* spart,
+                        double* sout, unsigned int* counter, const int* done, int* err,
+                        cudaStream_t s) {
+  switch (vpt) {
+#define TLS_AT(V)                                                                               \
+  case V: {                                                                                     \
+    static bool attr = false;                                                                   \
+    if (!attr) {                                                                                \
+      cudaFuncSetAttribute(apass_tma_kernel<T, NR, RESID, V>,                                  \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);            \
+      attr = true;                                                                              \
+    }                                                                                           \
+    apass_tma_kernel<T, NR, RESID, V><<<grid, kThreads, smem, s>>>(A, m, npad, v, ldv, b, part, \
+                                                                   spart, sout, counter, done,  \
+                                                                   err);                        \
+    count_launch();                                                                             \
+    break;                                                                                      \
+  }
+    TLS_AT(1) TLS_AT(2) TLS_AT(4) TLS_AT(8)
+#undef TLS_AT
+    default: break;
+  }
+}
+
+template <typename T, int NR, bool RESID>
 void apass_dispatch(int vpt, dim3 grid, const T* A, int64_t lda, int64_t m, int64_t npad,
                     const T* v, int64_t ldv, const double* b, T* part, double* spart,
                     double* sout, unsigned int* counter, const int* done, cudaStream_t s) {
@@ -638,8 +827,17 @@ ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms) {
   p.vpt = 1;
   while (p.vpt < need) p.vpt *= 2;
   const int rt = (p.vpt >= 8) ? 1 : (8 / p.vpt);
-  const int64_t by_rows = std::max<int64_t>(1, m / (4 * rt));
-  p.grid = (int)std::min<int64_t>(2 * (int64_t)num_sms, by_rows);
+  const size_t stage = (size_t)rt * (size_t)npad * sizeof(T);
+  p.smem = kApStages * stage;
+  p.tma = p.smem <= 200 * 1024;
+  if (p.tma) {
+    // one CTA per SM (the ring takes most of shared memory), at least a few tiles per CTA
+    const int64_t by_rows = std::max<int64_t>(1, m / (2 * rt));
+    p.grid = (int)std::min<int64_t>((int64_t)num_sms, by_rows);
+  } else {
+    const int64_t by_rows = std::max<int64_t>(1, m / (4 * rt));
+    p.grid = (int)std::min<int64_t>(2 * (int64_t)num_sms, by_rows);
+  }
   return p;
 }
 
@@ -647,8 +845,17 @@ template <typename T>
 void launch_apass(const ApassPlan& plan, const T* A, int64_t lda, int64_t m, int64_t npad,
                   int nr, bool resid, const T* v, int64_t ldv, const double* b, T* part,
                   double* spart, double* sout, unsigned int* counter, const int* done,
-                  cudaStream_t s) {
+                  int* err, cudaStream_t s) {
   dim3 grid(plan.grid);
+  if (plan.tma && lda == npad) {
+    if (nr == 1) {
+      if (resid) apass_tma_dispatch<T, 1, true>(plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
+      else apass_tma_dispatch<T, 1, false>(plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
+    } else {
+      apass_tma_dispatch<T, 2, false>(plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
+    }
+    return;
+  }
   if (nr == 1) {
     if (resid) apass_dispatch<T, 1, true>(plan.vpt, grid, A, lda, m, npad, v, ldv, b, part, spart, sout, counter, done, s);
     else apass_dispatch<T, 1, false>(plan.vpt, grid, A, lda, m, npad, v, ldv, b, part, spart, sout, counter, done, s);
@@ -747,7 +954,7 @@ void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaS
   template ApassPlan plan_apass<T>(int64_t, int64_t, int, int);                                \
   template void launch_apass<T>(const ApassPlan&, const T*, int64_t, int64_t, int64_t, int,    \
                                 bool, const T*, int64_t, const double*, T*, double*, double*,  \
-                                unsigned int*, const int*, cudaStream_t);                      \
+                                unsigned int*, const int*, int*, cudaStream_t);                \
   template void launch_pcg_prep<T>(const double*, double, const double*, int, int64_t,         \
                                    int64_t, const double*, T*, T*, T*, T*, PcgScalars*,        \
                                    double, double, cudaStream_t);                              \

@@ -55,11 +55,13 @@ struct tls_ctx {
   double* dinv = nullptr;    // 1 / d
   void* H = nullptr;         // scaled Gram (npad^2, float or double, see H_fp64)
   bool H_fp64 = false;
+  bool gram_tc_used = false;
   void* R = nullptr;         // R_H rounded to u_f, stored in the u type (npad^2)
   void* W = nullptr;         // R_H^{-1} (u type)
   void* WT = nullptr;        // W^T (u type)
   int shifts = 0;
   double shift = 0.0;
+  int64_t fail_pivot = -1;   // pivot index of the last breakdown (-1: none)
   double t_factor_ms = 0.0;
 
   // solve workspace
@@ -73,6 +75,7 @@ struct tls_ctx {
   double* sout = nullptr;    // 4 (residual) + 4 (PCGTLS)
   double* gpart = nullptr;   // gemv / reduction partials (1024 x 4)
   unsigned int* counter = nullptr;  // 4
+  int* derr = nullptr;       // error word of bounded device waits (0: none)
   PcgScalars* sc = nullptr;
   RqiScalars* rs = nullptr;
   int P64 = 0, PU = 0;
@@ -177,14 +180,16 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->sout = alloc_t<double>(ctx, 8);
   ctx->gpart = alloc_t<double>(ctx, 4096);
   ctx->counter = alloc_t<unsigned int>(ctx, 4);
+  ctx->derr = alloc_t<int>(ctx, 1);
   ctx->sc = alloc_t<PcgScalars>(ctx, 1);
   ctx->rs = alloc_t<RqiScalars>(ctx, 1);
   if (!ctx->b || !ctx->x || !ctx->x_best || !ctx->f || !ctx->d || !ctx->dinv || !ctx->sout ||
-      !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs) {
+      !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs || !ctx->derr) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
   TLS_CK(cudaMemsetAsync(ctx->counter, 0, 4 * sizeof(unsigned int), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->sc, 0, sizeof(PcgScalars), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->rs, 0, sizeof(RqiScalars), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * npad, ctx->stream));
@@ -259,7 +264,7 @@ tls_status residual_pass(tls_ctx* ctx) {
     Prof pr(ctx, TLS_PROF_RESID_PASS);
     tls::launch_apass<double>(ctx->plan64, ctx->A64, ctx->npad, ctx->m, ctx->npad, 1, true,
                               ctx->x, ctx->npad, ctx->b, ctx->part64, ctx->spart, ctx->sout,
-                              ctx->counter, nullptr, ctx->stream);
+                              ctx->counter, nullptr, ctx->derr, ctx->stream);
   }
   {
     Prof pr(ctx, TLS_PROF_RESID_REDUCE);
@@ -321,7 +326,7 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
         Prof pr(ctx, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
         tls::launch_apass<T>(ctx->planU, Au, npad, ctx->m, npad, nr, false, v.q, npad, nullptr,
                              static_cast<T*>(ctx->part), ctx->spart, ctx->sout + 4,
-                             ctx->counter + 1, done_ptr(ctx), ctx->stream);
+                             ctx->counter + 1, done_ptr(ctx), ctx->derr, ctx->stream);
       }
       Prof pr(ctx, TLS_PROF_PCG_REDUCE);
       tls::launch_pcg_reduce<T>(static_cast<const T*>(ctx->part), ctx->PU, npad, v.q, v.w, v.y,
@@ -388,6 +393,8 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   int stop = TLS_STOP_MAX_RQI;
   int best_k = 0, k = 0, cg_total = 0, not_spd = 0;
   double best_psi = INFINITY, best_s2 = 0.0;
+  double psi_hist[24];
+  int n_psi = 0;
   for (;;) {
     ++k;
     stt = residual_pass(ctx);
@@ -401,21 +408,26 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
       not_spd |= ctx->h_sc->not_spd[0] | ctx->h_sc->not_spd[1];
     }
     const double psi = ctx->h_rs->psi, s2 = ctx->h_rs->sigma2;
+    if (n_psi < 24) psi_hist[n_psi++] = psi;
     if (!std::isfinite(psi) || !std::isfinite(s2)) {
       stop = TLS_STOP_PSI_UP;
       break;
     }
+    // Sec. 3 after Eq. (4): stop when psi increases -- unless psi is still far above the
+    // attainable level (psi_accept), where an increase is a transient of the inexact solves
     const bool up = o.psi_rule_ge ? (psi >= prev_psi) : (psi > prev_psi);
-    if (up) {
+    if (up && best_psi <= o.psi_accept * scale) {
       stop = TLS_STOP_PSI_UP;
       break;
     }
-    best_k = k;
-    best_psi = psi;
-    best_s2 = s2;
-    TLS_CK(cudaMemcpyAsync(ctx->x_best, ctx->x, sizeof(double) * ctx->npad,
-                           cudaMemcpyDeviceToDevice, st));
-    if (psi <= tol * scale) {
+    if (psi < best_psi) {
+      best_k = k;
+      best_psi = psi;
+      best_s2 = s2;
+      TLS_CK(cudaMemcpyAsync(ctx->x_best, ctx->x, sizeof(double) * ctx->npad,
+                             cudaMemcpyDeviceToDevice, st));
+    }
+    if (!up && psi <= tol * scale) {
       stop = TLS_STOP_TOL;
       break;
     }
@@ -424,6 +436,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
       break;
     }
     prev_psi = psi;
+    // two shifted solves (Alg. 4, PCGTLS with k+1 steps) and the x update
     const int steps = o.cg_fixed ? (k + 1) : std::max(1, o.cg_max);
     stt = run_pcg<T>(ctx, 2, ctx->f, -1.0, ctx->x, s2, steps, o.cg_fixed ? 0.0 : o.cg_tol, modeA);
     if (stt != TLS_OK) return stt;
@@ -434,10 +447,18 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     TLS_CK_LAUNCH("rqi update");
   }
   TLS_CK(cudaEventRecord(ctx->ev1, st));
+  int herr = 0;
+  TLS_CK(cudaMemcpyAsync(&herr, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLS_CK(cudaEventSynchronize(ctx->ev1));
+  TLS_CK(cudaStreamSynchronize(st));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   prof_collect(ctx);
+  if (herr != 0) {
+    TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), st));
+    set_err(ctx, "a bounded device wait expired (code " + std::to_string(herr) + ")");
+    return TLS_ERR_TIMEOUT;
+  }
   *sigma_out = std::sqrt(std::max(best_s2, 0.0));
   if (info) {
     info->stop_reason = stop;
@@ -452,6 +473,9 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     info->shift = ctx->shift;
     info->t_factor_ms = ctx->t_factor_ms;
     info->t_solve_ms = ms;
+    info->fail_pivot = (int)ctx->fail_pivot;
+    info->n_psi = n_psi;
+    for (int i = 0; i < n_psi; ++i) info->psi_hist[i] = psi_hist[i];
   }
   return TLS_OK;
 }
@@ -531,6 +555,7 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   if (!dinfo) return TLS_ERR_OOM;
   ctx->shifts = 0;
   ctx->shift = 0.0;
+  ctx->fail_pivot = -1;
   bool ok = false;
   for (tls_prec uf : ladder) {
     const Prec pf = to_prec(uf);
@@ -553,24 +578,48 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     {
       Prof pr(ctx, TLS_PROF_GRAM);
       bool tc = false;
-      if (pf == Prec::FP16 || pf == Prec::BF16)
+      if ((pf == Prec::FP16 || pf == Prec::BF16) && !ctx->opt.gram_simt)
         tc = tls::launch_gram_tc(AsT, pf, n, npad, mpad, static_cast<float*>(ctx->H), st);
+      if (tc) {
+        const int terr = tls::gram_tc_error(st);   // synchronises the stream
+        if (terr != 0) {
+          // a bounded wait in the tensor-core kernel gave up: recompute on CUDA cores
+          set_err(ctx, "tensor-core Gram wait expired (code " + std::to_string(terr) +
+                           "); recomputed on CUDA cores");
+          tc = false;
+        }
+      }
       if (!tc) tls::launch_gram_simt(AsT, pf, n, npad, mpad, ctx->H, st);
+      ctx->gram_tc_used = tc;
     }
     TLS_CK_LAUNCH("gram");
     dev_free(ctx, AsT);
+    void* Wc = dev_alloc(ctx, ce * (size_t)npad * (size_t)npad);   // diagonal-block inverses
+    if (!Wc) {
+      set_err(ctx, "device allocation failed (factor workspace)");
+      return TLS_ERR_OOM;
+    }
     const int max_shift = std::max(0, ctx->opt.max_shifts);
-    for (int sh = 0; sh <= max_shift; ++sh) {
-      const double shift = (sh == 0) ? 0.0 : std::ldexp(1.0, -10) * std::pow(4.0, sh - 1);
+    // unit roundoff of the factor precision (Table 2; bf16: 2^-8)
+    const double uf_round = (pf == Prec::FP16) ? std::ldexp(1.0, -11)
+                            : (pf == Prec::BF16) ? std::ldexp(1.0, -8)
+                            : (pf == Prec::FP32) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    const bool low = (pf == Prec::FP16 || pf == Prec::BF16);
+    const int first = (low && ctx->opt.shift_first) ? 1 : 0;
+    for (int sh = first; sh <= max_shift + first; ++sh) {
+      const double shift = (sh == 0) ? 0.0 : 2.0 * uf_round * std::pow(4.0, sh - 1);
       TLS_CK(cudaMemcpyAsync(M, ctx->H, ce * (size_t)npad * (size_t)npad,
                              cudaMemcpyDeviceToDevice, st));
+      TLS_CK(cudaMemsetAsync(Wc, 0, ce * (size_t)npad * (size_t)npad, st));
       TLS_CK(cudaMemsetAsync(dinfo, 0, sizeof(int), st));
       {
         Prof pr(ctx, TLS_PROF_CHOL);
         if (chol64)
-          tls::launch_cholesky<double>(static_cast<double*>(M), n, npad, shift, dinfo, nullptr, st);
+          tls::launch_cholesky<double>(static_cast<double*>(M), n, npad, shift, dinfo,
+                                       static_cast<double*>(Wc), pf, st);
         else
-          tls::launch_cholesky<float>(static_cast<float*>(M), n, npad, shift, dinfo, nullptr, st);
+          tls::launch_cholesky<float>(static_cast<float*>(M), n, npad, shift, dinfo,
+                                      static_cast<float*>(Wc), pf, st);
       }
       TLS_CK_LAUNCH("cholesky");
       int hinfo = 0;
@@ -582,8 +631,10 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
         break;
       }
       ctx->shifts += 1;
+      ctx->fail_pivot = hinfo - 1;
     }
     if (!ok) {
+      dev_free(ctx, Wc);
       dev_free(ctx, M);
       dev_free(ctx, ctx->H);
       ctx->H = nullptr;
@@ -604,18 +655,31 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     const int64_t cnt = npad * npad;
     Prof pr(ctx, TLS_PROF_TRTRI);
     if (ctx->u == Prec::FP64) {
-      if (chol64) TLS_CK(cudaMemcpyAsync(ctx->R, M, 8 * cnt, cudaMemcpyDeviceToDevice, st));
-      else tls::launch_f2d(static_cast<float*>(M), static_cast<double*>(ctx->R), cnt, st);
+      if (chol64) {
+        TLS_CK(cudaMemcpyAsync(ctx->R, M, 8 * cnt, cudaMemcpyDeviceToDevice, st));
+        TLS_CK(cudaMemcpyAsync(ctx->W, Wc, 8 * cnt, cudaMemcpyDeviceToDevice, st));
+      } else {
+        tls::launch_f2d(static_cast<float*>(M), static_cast<double*>(ctx->R), cnt, st);
+        tls::launch_f2d(static_cast<float*>(Wc), static_cast<double*>(ctx->W), cnt, st);
+      }
       tls::launch_trtri<double>(static_cast<double*>(ctx->R), static_cast<double*>(ctx->W),
-                                static_cast<double*>(ctx->WT), static_cast<double*>(work), npad, st);
+                                static_cast<double*>(ctx->WT), static_cast<double*>(work), npad,
+                                true, st);
     } else {
-      if (chol64) tls::launch_d2f(static_cast<double*>(M), static_cast<float*>(ctx->R), cnt, st);
-      else TLS_CK(cudaMemcpyAsync(ctx->R, M, 4 * cnt, cudaMemcpyDeviceToDevice, st));
+      if (chol64) {
+        tls::launch_d2f(static_cast<double*>(M), static_cast<float*>(ctx->R), cnt, st);
+        tls::launch_d2f(static_cast<double*>(Wc), static_cast<float*>(ctx->W), cnt, st);
+      } else {
+        TLS_CK(cudaMemcpyAsync(ctx->R, M, 4 * cnt, cudaMemcpyDeviceToDevice, st));
+        TLS_CK(cudaMemcpyAsync(ctx->W, Wc, 4 * cnt, cudaMemcpyDeviceToDevice, st));
+      }
       tls::launch_trtri<float>(static_cast<float*>(ctx->R), static_cast<float*>(ctx->W),
-                               static_cast<float*>(ctx->WT), static_cast<float*>(work), npad, st);
+                               static_cast<float*>(ctx->WT), static_cast<float*>(work), npad,
+                               true, st);
     }
     TLS_CK_LAUNCH("triangular inverse");
     dev_free(ctx, work);
+    dev_free(ctx, Wc);
     dev_free(ctx, M);
     ctx->uf_used = uf;
     ctx->H_fp64 = chol64;
@@ -703,6 +767,9 @@ void tls_default_options(tls_options* opt) {
   opt->psi_rule_ge = 0;
   opt->ls_iters = 12;
   opt->max_shifts = 3;
+  opt->gram_simt = 0;
+  opt->shift_first = 1;
+  opt->psi_accept = 1e-12;
 }
 
 const char* tls_status_str(tls_status s) {

@@ -77,17 +77,25 @@ void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64
 // supported (falls back to nothing: the caller decides).
 bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
                     float* H, cudaStream_t s);
+// 1 if the tensor-core path can run on the current device (sm_103 and a tensor-map encoder).
+bool gram_tc_available();
+// Error code recorded by a bounded wait of the tensor-core kernels (0: none); resets it.
+int gram_tc_error(cudaStream_t s);
 // Blocked upper Cholesky in place on M (npad x npad, T), with shift added to the first n
-// diagonal entries first; info[0] = first failing global pivot + 1 (0: success).
+// diagonal entries first; the rows of R are rounded to prec block by block and the inverses
+// of the 64 x 64 diagonal blocks are written to Wd (npad x npad, other entries untouched);
+// info[0] = first failing global pivot + 1 (0: success).
 template <typename T>
-void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* work,
+void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* Wd, Prec prec,
                      cudaStream_t s);
 // Round the upper triangle of R (T) to prec in place (FP16/BF16); no-op for FP32/FP64.
 template <typename T>
 void launch_round_to(T* R, int64_t npad, Prec prec, cudaStream_t s);
 // W = R^{-1} (upper, npad x npad) and WT = W^T (row-major), both T. work: npad x npad T.
+// have_diag: W already holds the inverses of the 64 x 64 diagonal blocks and zeros elsewhere.
 template <typename T>
-void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, cudaStream_t s);
+void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, bool have_diag,
+                  cudaStream_t s);
 // Convert FP32 <-> FP64 square matrices (used for escalation / export).
 void launch_f2d(const float* in, double* out, int64_t count, cudaStream_t s);
 void launch_d2f(const double* in, float* out, int64_t count, cudaStream_t s);
@@ -99,6 +107,8 @@ void launch_set_identity_pad(void* M, bool fp64, int64_t n, int64_t npad, cudaSt
 struct ApassPlan {
   int grid;           // CTAs of the fused pass (= number of partials P)
   int vpt;            // vectors per thread
+  bool tma;           // rows staged through shared memory by bulk async copies
+  size_t smem;        // dynamic shared memory of the staged kernel
 };
 template <typename T>
 ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms);
@@ -109,7 +119,7 @@ ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms);
 template <typename T>
 void launch_apass(const ApassPlan& plan, const T* A, int64_t lda, int64_t m, int64_t npad,
                   int nr, bool resid, const T* v, int64_t ldv, const double* b, T* part,
-                  double* spart, double* sout, unsigned int* counter, const int* done,
+                  double* spart, double* sout, unsigned int* counter, const int* done, int* err,
                   cudaStream_t s);
 
 // PCGTLS (Alg. 3) building blocks, T = float or double (the precision u_p).

@@ -36,17 +36,21 @@ PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", 
 class tls_options(C.Structure):
     _fields_ = [("u", C.c_int), ("mode_A", C.c_int), ("cg_fixed", C.c_int),
                 ("cg_tol", C.c_double), ("cg_max", C.c_int), ("psi_rule_ge", C.c_int),
-                ("ls_iters", C.c_int), ("max_shifts", C.c_int)]
+                ("ls_iters", C.c_int), ("max_shifts", C.c_int), ("gram_simt", C.c_int),
+                ("psi_accept", C.c_double), ("shift_first", C.c_int)]
 
 
 class tls_info(C.Structure):
     _fields_ = [("stop_reason", C.c_int), ("rqi_steps", C.c_int), ("best_k", C.c_int),
                 ("cg_iters", C.c_int), ("shifts", C.c_int), ("not_spd", C.c_int),
                 ("u_f_used", C.c_int), ("psi_final", C.c_double), ("sigma2", C.c_double),
-                ("shift", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double)]
+                ("shift", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("fail_pivot", C.c_int), ("n_psi", C.c_int), ("psi_hist", C.c_double * 24)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "psi_hist"}
+        d["psi_hist"] = [self.psi_hist[i] for i in range(min(self.n_psi, 24))]
+        return d
 
 
 class TLSError(RuntimeError):

@@ -71,8 +71,9 @@ def _rounded_scaled(A, d, u_f):
     if u_f == "fp16":
         return As.astype(np.float16).astype(np.float64)
     if u_f == "bf16":
-        import torch
-        return torch.tensor(As).to(torch.bfloat16).to(torch.float64).numpy()
+        # round-to-nearest-even to 8 significant bits, straight from FP64 (as the device does)
+        mant, ex = np.frexp(As)
+        return np.ldexp(np.rint(mant * 256.0) / 256.0, ex)
     if u_f == "fp32":
         return As.astype(np.float32).astype(np.float64)
     return A / d
@@ -196,16 +197,41 @@ def test_solve_before_factor_is_a_state_error():
         tls.tls_destroy(ctx)
 
 
-def test_zero_column_breaks_down_then_shifts():
-    # A zero column makes H singular: the first pivot at that column is 0, so the factor must
-    # take the shift rung (Sec. 3.1 diagonal perturbation) before it succeeds.
+@pytest.mark.parametrize("shift_first", [0, 1])
+def test_zero_column_breaks_down_then_shifts(shift_first):
+    # A zero column makes H singular: the pivot at that column is 0. Started unshifted, the
+    # factor breaks down there (reported pivot 7) and takes the shift rung before it succeeds;
+    # started from the diagonal perturbation 2 u_f it succeeds at once.
     p = synth.dense_problem(200, 30, d_lo=1e-1, noise=1e-3, seed=2)
     A = p.A.copy()
     A[:, 7] = 0.0
     ctx = tls.tls_create_dense(A, p.b)
     try:
-        tls.tls_factor(ctx, "fp16", tls.tls_default_options())
+        tls.tls_factor(ctx, "fp16", tls.tls_default_options(shift_first=shift_first))
         x, s, info = tls.tls_solve(ctx, tol=0.0, max_rqi=3)
-        assert info["shifts"] >= 1 and info["shift"] > 0
+        assert info["shift"] > 0
+        if shift_first:
+            assert info["shifts"] == 0 and info["shift"] == pytest.approx(2 * U16)
+        else:
+            assert info["shifts"] >= 1 and info["fail_pivot"] == 7
     finally:
         tls.tls_destroy(ctx)
+
+
+@pytest.mark.parametrize("u_f", ["fp16", "bf16"])
+@pytest.mark.parametrize("m,n", [(512, 128), (1000, 130), (2100, 300), (1536, 576)])
+def test_tensor_core_gram_matches_cuda_core_gram(u_f, m, n):
+    # tcgen05 Gram (FP32 accumulation in TMEM) vs the CUDA-core kernel on the same rounded
+    # inputs: both are FP32 sums of exact FP16/BF16 products, so they agree to m u_32 |A|^T|A|.
+    # Shapes cover ragged n (n not a multiple of the 128-row tile) and m not a multiple of 64.
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=9)
+    with Ctx(p.A, p.b, u_f=u_f, u="fp32") as ctx:
+        _, d, H_tc = tls.tls_export_factor(ctx)
+    with Ctx(p.A, p.b, u_f=u_f, u="fp32", gram_simt=1) as ctx:
+        _, d2, H_simt = tls.tls_export_factor(ctx)
+    assert np.array_equal(d, d2)
+    As = _rounded_scaled(p.A, d, u_f)
+    bound = m * U32 * (np.abs(As).T @ np.abs(As))
+    assert np.all(np.abs(H_tc - H_simt) <= 2 * bound)
+    assert np.all(np.abs(H_tc - As.T @ As) <= bound)
+    assert np.allclose(H_tc, H_tc.T, rtol=0, atol=0)
