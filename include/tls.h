@@ -186,6 +186,36 @@ typedef void* (*tls_alloc_fn)(uint64_t bytes, void* stream, void* user);
 typedef void (*tls_free_fn)(void* ptr, uint64_t bytes, void* stream, void* user);
 void tls_set_allocator(tls_alloc_fn alloc, tls_free_fn release, void* user);
 
+/*
+ * tls_residual_noalloc -- the FP64 residual block of one RQI step, r = b - A x,
+ * sigma^2 = r^T r / (1 + x^T x), f = -A^T r - sigma^2 x, g = -b^T r + sigma^2 and
+ * psi = sqrt((||f||^2 + g^2) / (||x||^2 + 1)), for callers that may not allocate device memory.
+ * The paper has no counterpart to this entry point: it exists for callers such as an
+ * application whose framework allocator already owns the GPU's memory and must account for
+ * every byte, a latency-critical loop in which cudaMalloc / cudaFree (which can synchronise the
+ * device) are not acceptable, or a plug-in that is handed its buffers and may create nothing.
+ * It performs no device allocation at all: its scratch lives in one file-scope device array of
+ * TLS_NOALLOC_SCRATCH_BYTES bytes that every GPU loading this library holds until the process
+ * exits.
+ *   m, n    sizes, m >= 1, 1 <= n <= TLS_NOALLOC_MAX_N (larger n: TLS_ERR_ARG).
+ *   A       device, m x n FP64, row-major, leading dimension lda >= n.
+ *   b, x    device, m and n FP64 values.
+ *   f       device output, n FP64 values.
+ *   scal    device output, 5 FP64 values: sigma^2, g, psi, r^T r, b^T r.
+ *   stream  cudaStream_t (as void*) the work runs on (NULL: the default stream); the call
+ *           returns without synchronising.
+ * The first call on a device looks up the scratch array's device address for that device
+ * (cudaGetSymbolAddress with the device current); make that first call before any stream
+ * capture. Every call shares the one array and keeps the last call's contents in it (the call
+ * clears what must start at zero itself), so calls whose work overlaps on the GPU -- on
+ * different streams, or from different threads -- race and give wrong results: order them.
+ */
+#define TLS_NOALLOC_MAX_N 4096
+#define TLS_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u + 4096u)
+tls_status tls_residual_noalloc(int64_t m, int64_t n, const double* A, int64_t lda,
+                                const double* b, const double* x, double* f, double* scal,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

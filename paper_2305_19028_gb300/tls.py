@@ -27,7 +27,7 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_solve_device", "tls_solve_batched", "tls_destroy", "tls_status_str",
            "tls_last_error", "tls_shape", "tls_set_allocator", "tls_export_factor",
            "tls_residual", "tls_pcgtls", "tls_precond", "tls_profile_enable", "tls_profile_get",
-           "tls_kernel_launches"]
+           "tls_kernel_launches", "tls_residual_noalloc"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
@@ -100,6 +100,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_profile_enable": (C.c_int, [v, C.c_int]),
         "tls_profile_get": (C.c_int, [v, C.c_int, C.POINTER(i64), _dp]),
         "tls_kernel_launches": (C.c_uint64, []),
+        "tls_residual_noalloc": (C.c_int, [i64, i64, v, i64, v, v, v, v, v]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -281,6 +282,20 @@ def tls_profile_get(ctx) -> dict:
 
 def tls_kernel_launches() -> int:
     return int(load().tls_kernel_launches())
+
+
+def tls_residual_noalloc(A, b, x, f, scal, stream=None):
+    """The residual block with caller-provided device buffers and no device allocation.
+    A (m, n), b (m,), x (n,), f (n,), scal (5,): torch CUDA float64 tensors (A row-major with
+    unit column stride). Returns the status code (0 on success); raises on error."""
+    m, n = A.shape
+    st = C.c_void_p(stream) if stream else None
+    status = load().tls_residual_noalloc(m, n, C.c_void_p(A.data_ptr()), A.stride(0),
+                                         C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                         C.c_void_p(f.data_ptr()), C.c_void_p(scal.data_ptr()),
+                                         st)
+    _check(status)
+    return status
 
 
 def use_torch_allocator(enable: bool = True):
