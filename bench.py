@@ -48,6 +48,16 @@ def _problem(rank: int):
     return synth.dense_problem(M_ROWS, N_COLS, d_lo=D_LO, noise=NOISE, seed=rank)
 
 
+def _set_size(m: int | None, n: int | None):
+    """Override the problem size (for profiling captures on a smaller case)."""
+    global M_ROWS, N_COLS, WORKLOAD
+    if m:
+        M_ROWS = m
+    if n:
+        N_COLS = n
+    WORKLOAD = f"dense_{M_ROWS}x{N_COLS}_uf16_u32_ur64"
+
+
 def _oracle_solve(p):
     import oracle.rqi_pcgtls as O
     return O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=MAX_RQI)
@@ -342,7 +352,7 @@ def run_ours(args, ws, rank, local):
         "accurate_steps": ok, "error_vs_oracle": err,
         "rqi_steps": infos[-1]["rqi_steps"], "cg_iters": infos[-1]["cg_iters"],
         "shifts": infos[-1]["shifts"], "u_f_used": infos[-1]["u_f_used"],
-        "fail_pivot": infos[-1]["fail_pivot"],
+        "fail_pivot": infos[-1]["fail_pivot"], "pass_variant": infos[-1]["pass_variant"],
         "t_factor_ms": infos[-1]["t_factor_ms"], "t_solve_ms": infos[-1]["t_solve_ms"],
         "roofline": roof, "inner_loop_roofline": inner,
         "kernel_share": share, "kernel_ms": {k: round(v, 4) for k, v in total.items()},
@@ -362,7 +372,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--m", type=int, default=None, help="rows (profiling a smaller case)")
+    ap.add_argument("--n", type=int, default=None, help="columns (profiling a smaller case)")
     args = ap.parse_args()
+    _set_size(args.m, args.n)
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -95,6 +95,8 @@ typedef struct {
   double t_factor_ms;    /* device time of the last tls_factor (CUDA events)                 */
   double t_solve_ms;     /* device time of this tls_solve                                    */
   int fail_pivot;        /* pivot index of the last Cholesky breakdown before success (-1)   */
+  int pass_variant[2];   /* autotuned kernel of the pass over A: [FP64 residual, PCGTLS];    */
+                         /* 0 register kernel, 1 staged 256 threads, 2 staged 512 threads    */
   int n_psi;             /* entries of psi_hist filled                                       */
   double psi_hist[24];   /* psi_k of the RQI loop, k = 1, 2, ... (first 24)                  */
 } tls_info;

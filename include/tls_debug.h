@@ -23,6 +23,13 @@ extern "C" {
 tls_status tls_export_factor(tls_ctx* ctx, double* R_host, double* d_host, double* H_host);
 
 /*
+ * tls_export_working_copy -- the FP32 working copy of A (m x n, row-major) that the PCGTLS
+ * passes read when u = FP32: each entry is A rounded to nearest (even) FP32. A32_host: m*n
+ * floats (host). TLS_ERR_STATE before a successful tls_factor with u = FP32.
+ */
+tls_status tls_export_working_copy(tls_ctx* ctx, float* A32_host);
+
+/*
  * tls_residual -- one RQI residual block in FP64 at x (Alg. 2 lines r_k..g_k, Eq. (2), Eq. (4)):
  * f_host (n) = -A^T r - sigma^2 x with r = b - A x; scal_host[0..4] = sigma^2 = r^T r/(1+x^T x),
  * g = -b^T r + sigma^2, psi = sqrt((||f||^2 + g^2)/(||x||^2 + 1)), r^T r, b^T r.

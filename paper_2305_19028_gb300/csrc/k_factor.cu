@@ -3,8 +3,10 @@
 // matrix, blocked Cholesky H + sI = R_H^T R_H, rounding of R_H to u_f, and the explicit inverse
 // W = R_H^{-1} that the PCGTLS iteration applies as two triangular products per step.
 #include "tls_internal.h"
+#include "tls_device.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace tls {
 
@@ -38,7 +40,7 @@ __global__ void __launch_bounds__(256) colnorm_kernel(const double* __restrict__
       for (int u = 0; u < U; ++u) v[u] = (c < n && i0 + u < r1) ? __ldcs(A + (i0 + u) * lda + c) : 0.0;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const float f = (float)v[u];
+        const float f = f64_to_f32_rn(v[u]);
         if (i0 + u < r1) A32[(i0 + u) * ldo + c] = f;
         acc = fmaf(f, f, acc);
       }
@@ -62,9 +64,16 @@ __global__ void colnorm_finish_kernel(const double* __restrict__ part, int P, in
                                       float* __restrict__ dinv32, double* __restrict__ dinv64) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= npad) return;
-  double s = 0.0;
-  for (int p = 0; p < P; ++p) s += part[(int64_t)p * npad + c];
-  double dd = sqrt(s);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int p = 0;
+  for (; p + 3 < P; p += 4) {
+    s0 += part[(int64_t)p * npad + c];
+    s1 += part[(int64_t)(p + 1) * npad + c];
+    s2 += part[(int64_t)(p + 2) * npad + c];
+    s3 += part[(int64_t)(p + 3) * npad + c];
+  }
+  for (; p < P; ++p) s0 += part[(int64_t)p * npad + c];
+  double dd = sqrt((s0 + s1) + (s2 + s3));
   // padded (and all-zero) columns get d = 1 so that D stays invertible; a zero column makes
   // A^T A singular and shows up as a Cholesky breakdown.
   if (c >= n || !(dd > 0.0)) dd = 1.0;
@@ -83,6 +92,35 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(doub
 }
 template <> __device__ __forceinline__ float cvt_out<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ double cvt_out<double>(double v) { return v; }
+
+template <typename Tout> __device__ __forceinline__ Tout cvt_out_f(float v);
+template <> __device__ __forceinline__ __half cvt_out_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt_out_f<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ float cvt_out_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ double cvt_out_f<double>(float v) { return (double)v; }
+
+// FP32 input (the working copy of A): A_s = fl(fl32(A32 * dinv32)), all in FP32 arithmetic
+template <typename Tout>
+__global__ void scale_cast_T32_kernel(const float* __restrict__ A, int64_t lda, int64_t m,
+                                      int64_t n, int64_t npad, int64_t mpad,
+                                      const float* __restrict__ dinv, Tout* __restrict__ AsT) {
+  __shared__ float tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int64_t j0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + threadIdx.x;
+    float v = 0.f;
+    if (i < m && j < n) v = A[i * lda + j] * dinv[j];
+    tile[r][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t j = j0 + r, i = i0 + threadIdx.x;
+    if (j < npad && i < mpad) AsT[j * mpad + i] = cvt_out_f<Tout>(tile[threadIdx.x][r]);
+  }
+}
 
 template <typename Tin, typename Tout>
 __global__ void scale_cast_T_kernel(const Tin* __restrict__ A, int64_t lda, int64_t m, int64_t n,
@@ -386,10 +424,26 @@ void launch_colnorm(const double* A, int64_t lda, int64_t m, int64_t n, int64_t 
 }
 
 void launch_scale_cast_T(const void* A, bool a_is_fp64, int64_t lda, int64_t m, int64_t n,
-                         int64_t npad, int64_t mpad, const double* dinv, void* AsT, Prec prec,
-                         cudaStream_t s) {
+                         int64_t npad, int64_t mpad, const double* dinv, const float* dinv32,
+                         void* AsT, Prec prec, cudaStream_t s) {
   dim3 grid((unsigned)(mpad / 32), (unsigned)(npad / 32));
   dim3 block(32, 8);
+  if (!a_is_fp64 && dinv32 != nullptr && prec != Prec::FP64) {
+    const float* Af = static_cast<const float*>(A);
+    switch (prec) {
+      case Prec::FP16:
+        scale_cast_T32_kernel<__half><<<grid, block, 0, s>>>(Af, lda, m, n, npad, mpad, dinv32, static_cast<__half*>(AsT));
+        break;
+      case Prec::BF16:
+        scale_cast_T32_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(Af, lda, m, n, npad, mpad, dinv32, static_cast<__nv_bfloat16*>(AsT));
+        break;
+      default:
+        scale_cast_T32_kernel<float><<<grid, block, 0, s>>>(Af, lda, m, n, npad, mpad, dinv32, static_cast<float*>(AsT));
+        break;
+    }
+    count_launch();
+    return;
+  }
 #define TLS_SC(TIN, TOUT)                                                                     \
   scale_cast_T_kernel<TIN, TOUT><<<grid, block, 0, s>>>(static_cast<const TIN*>(A), lda, m, n, \
                                                         npad, mpad, dinv, static_cast<TOUT*>(AsT))
@@ -455,7 +509,8 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
     attr = true;
   }
   for (int64_t kb = 0; kb < npad; kb += NB) {
-    potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb, info, (int)prec); count_launch();
+    potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb, info, (int)prec);
+    count_launch();
     const int64_t n2 = npad - kb - NB;
     if (n2 <= 0) break;
     // panel R_KJ = W_KK^T H_KJ, in place over H_KJ

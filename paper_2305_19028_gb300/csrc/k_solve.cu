@@ -50,11 +50,12 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* kWarps*K
 #pragma unroll
     for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
   __syncthreads();
+  // second level as a shuffle tree (FP64 latency is long: keep dependency chains short)
+  const int nw = (int)(blockDim.x >> 5);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w * K + k];
-    v[k] = t;
+    double t = (lane < nw) ? sh[lane * K + k] : 0.0;
+    v[k] = warp_sum(t);
   }
 }
 
@@ -136,9 +137,11 @@ __global__ void __launch_bounds__(kThreads) apass_kernel(
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = min(m, r0 + per);
-  double s_cc[NR], s_bc[NR];
+  // per-row scalar sums in the working type: FP64 instructions are very slow on this GPU, so
+  // an FP32 kernel must not issue them per row
+  T s_cc[NR], s_bc[NR];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) { s_cc[r] = 0.0; s_bc[r] = 0.0; }
+  for (int r = 0; r < NR; ++r) { s_cc[r] = T(0); s_bc[r] = T(0); }
   int buf = 0;
   for (int64_t i0 = r0; i0 < r1; i0 += RT) {
     V a[RT][VPT];
@@ -175,18 +178,18 @@ __global__ void __launch_bounds__(kThreads) apass_kernel(
     for (int rt = 0; rt < RT; ++rt) {
       const int64_t row = i0 + rt;
       const bool valid = row < r1;
-      double brow = 0.0;
-      if (RESID && valid) brow = b[row];
+      T brow = T(0);
+      if (RESID && valid) brow = (T)b[row];
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         T dot = T(0);
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) dot += red[buf][w][r * RT + rt];
         T c = T(0);
-        if (valid) c = RESID ? (T)(brow - (double)dot) : dot;
+        if (valid) c = RESID ? (brow - dot) : dot;
         if (tid == 0) {
-          s_cc[r] = fma((double)c, (double)c, s_cc[r]);
-          s_bc[r] = fma(brow, (double)c, s_bc[r]);
+          s_cc[r] = fma(c, c, s_cc[r]);
+          s_bc[r] = fma(brow, c, s_bc[r]);
         }
 #pragma unroll
         for (int k = 0; k < VPT; ++k)
@@ -216,8 +219,8 @@ __global__ void __launch_bounds__(kThreads) apass_kernel(
   if (tid == 0)
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      spart[((int64_t)blockIdx.x * NR + r) * 2 + 0] = s_cc[r];
-      spart[((int64_t)blockIdx.x * NR + r) * 2 + 1] = s_bc[r];
+      spart[((int64_t)blockIdx.x * NR + r) * 2 + 0] = (double)s_cc[r];
+      spart[((int64_t)blockIdx.x * NR + r) * 2 + 1] = (double)s_bc[r];
     }
   if (arrive_last(counter)) {
     reduce_partials<2 * NR>(spart, (int)gridDim.x, sout);
@@ -235,19 +238,30 @@ __global__ void __launch_bounds__(kThreads) apass_kernel(
 // ---------------------------------------------------------------------------------------
 constexpr int kApStages = 4;
 
-template <typename T, int NR, bool RESID, int VPT>
-__global__ void __launch_bounds__(kThreads, 1) apass_tma_kernel(
+// Layout of the work inside a CTA (kApThreads = 256 or 512 threads), RT = 4 / VPT rows per tile
+// (a stage of RT * n_pad elements, about 32 KB at the sizes that matter; VPT is the number of
+// axpy-phase vectors per thread, so RT depends on the thread count too):
+//  * dot phase: WPR = warps / RT warps share a row; warp w takes segment (w % WPR) of row (w / WPR),
+//    so each lane keeps the q values of a fixed column segment (at most 4 vectors) in registers
+//    and reduces them with one shuffle tree per row;
+//  * axpy phase (after the tile's barrier): thread t owns columns (k * threads + t) * VW, k < VPT,
+//    and accumulates c_i A_i over the tile's rows, c_i being the WPR segment sums of row i.
+template <typename T, int NR, bool RESID, int VPT, int kApThreads>
+__global__ void __launch_bounds__(kApThreads, 1) apass_tma_kernel(
     const T* __restrict__ A, int64_t m, int64_t npad, const T* __restrict__ v, int64_t ldv,
     const double* __restrict__ b, T* __restrict__ part, double* __restrict__ spart,
     double* __restrict__ sout, unsigned int* counter, const int* __restrict__ done, int* err) {
   using V = typename VecOf<T>::type;
   constexpr int VW = VecOf<T>::W;
-  constexpr int RT = (VPT >= 8) ? 1 : (8 / VPT);   // rows per tile
+  constexpr int kApWarps = kApThreads / 32;
+  constexpr int RT = 4 / VPT;                      // rows per tile
+  constexpr int WPR = kApWarps / RT;               // warps per row in the dot phase
+  constexpr int VPS = 4;                           // max vectors per lane in a segment
   constexpr int E = VPT * VW;
   extern __shared__ __align__(128) unsigned char dsm[];
   T* ring = reinterpret_cast<T*>(dsm);
   __shared__ uint64_t full[kApStages];
-  __shared__ T red[2][kWarps][NR * RT];
+  __shared__ __align__(16) T segsum[2][RT][NR][WPR];   // double-buffered by tile parity
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (done != nullptr) {
     bool all = true;
@@ -255,30 +269,40 @@ __global__ void __launch_bounds__(kThreads, 1) apass_tma_kernel(
     for (int r = 0; r < NR; ++r) all = all && (done[r] != 0);
     if (all) return;
   }
-  T vv[NR][E], acc[NR][E];
+  const int my_row = warp / WPR, my_seg = warp % WPR;
+  const int64_t seg_len = npad / WPR;
+  const int64_t seg0 = (int64_t)my_seg * seg_len;
+  T vq[NR][VPS * VW];
 #pragma unroll
-  for (int k = 0; k < VPT; ++k) {
-    const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+  for (int u = 0; u < VPS; ++u) {
+    const bool ok = ((int64_t)u * 32 + lane) * VW < seg_len;
+    const int64_t c = seg0 + ((int64_t)u * 32 + lane) * VW;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       V x = zero_vec(T(0));
-      if (col < npad) x = *reinterpret_cast<const V*>(v + r * ldv + col);
+      if (ok) x = *reinterpret_cast<const V*>(v + r * ldv + c);
 #pragma unroll
-      for (int c = 0; c < VW; ++c) { vv[r][k * VW + c] = get(x, c); acc[r][k * VW + c] = T(0); }
+      for (int cc = 0; cc < VW; ++cc) vq[r][u * VW + cc] = get(x, cc);
     }
   }
+  T acc[NR][E];
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[r][e] = T(0);
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = min(m, r0 + per);
   const int ntiles = (r1 > r0) ? (int)((r1 - r0 + RT - 1) / RT) : 0;
   const int64_t stage_elems = (int64_t)RT * npad;
+  const uint64_t pol = ptx::policy_evict_first();   // A is streamed once per pass
   auto issue = [&](int t) {
     const int64_t row = r0 + (int64_t)t * RT;
     const int rows = (int)min((int64_t)RT, r1 - row);
     const uint32_t bytes = (uint32_t)(rows * npad * (int64_t)sizeof(T));
     uint64_t* bar = &full[t % kApStages];
     ptx::mbar_expect_tx(bar, bytes);
-    ptx::bulk_g2s(ring + (t % kApStages) * stage_elems, A + row * npad, bytes, bar);
+    ptx::bulk_g2s_hint(ring + (t % kApStages) * stage_elems, A + row * npad, bytes, bar, pol);
   };
   if (tid == 0) {
     for (int s2 = 0; s2 < kApStages; ++s2) ptx::mbar_init(&full[s2], 1);
@@ -287,82 +311,95 @@ __global__ void __launch_bounds__(kThreads, 1) apass_tma_kernel(
   __syncthreads();
   if (tid == 0)
     for (int t = 0; t < kApStages && t < ntiles; ++t) issue(t);
-  double s_cc[NR], s_bc[NR];
+  T s_cc[NR], s_bc[NR];      // per-row scalar sums in the working type (see apass_kernel)
 #pragma unroll
-  for (int r = 0; r < NR; ++r) { s_cc[r] = 0.0; s_bc[r] = 0.0; }
-  int buf = 0;
+  for (int r = 0; r < NR; ++r) { s_cc[r] = T(0); s_bc[r] = T(0); }
   for (int t = 0; t < ntiles; ++t) {
     const int64_t i0 = r0 + (int64_t)t * RT;
     ptx::mbar_wait(&full[t % kApStages], (uint32_t)((t / kApStages) & 1), err, 11);
     const T* tile = ring + (t % kApStages) * stage_elems;
-    T pd[NR][RT];
+    // ---- dot phase: this warp's segment of row my_row
+    {
+      T d0[NR];
 #pragma unroll
-    for (int rt = 0; rt < RT; ++rt) {
-      const bool rv = (i0 + rt) < r1;
-      V a[VPT];
+      for (int r = 0; r < NR; ++r) d0[r] = T(0);
+      if (i0 + my_row < r1) {
+        const T* rowp = tile + (int64_t)my_row * npad + seg0;
+        V a[VPS];
 #pragma unroll
-      for (int k = 0; k < VPT; ++k) {
-        const int64_t col = ((int64_t)k * kThreads + tid) * VW;
-        a[k] = (rv && col < npad) ? *reinterpret_cast<const V*>(tile + rt * npad + col)
-                                  : zero_vec(T(0));
+        for (int u = 0; u < VPS; ++u)
+          a[u] = (((int64_t)u * 32 + lane) * VW < seg_len)
+                     ? *reinterpret_cast<const V*>(rowp + ((int64_t)u * 32 + lane) * VW)
+                     : zero_vec(T(0));
+#pragma unroll
+        for (int u = 0; u < VPS; ++u)
+#pragma unroll
+          for (int r = 0; r < NR; ++r)
+#pragma unroll
+            for (int cc = 0; cc < VW; ++cc) d0[r] = fma(get(a[u], cc), vq[r][u * VW + cc], d0[r]);
       }
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        T tt = T(0);
+      for (int r = 0; r < NR; ++r) d0[r] = warp_sum(d0[r]);
+      if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < VPT; ++k)
-#pragma unroll
-          for (int c = 0; c < VW; ++c) tt = fma(get(a[k], c), vv[r][k * VW + c], tt);
-        pd[r][rt] = warp_sum(tt);
-      }
+        for (int r = 0; r < NR; ++r) segsum[t & 1][my_row][r][my_seg] = d0[r];
     }
-    if (lane == 0)
-#pragma unroll
-      for (int r = 0; r < NR; ++r)
-#pragma unroll
-        for (int rt = 0; rt < RT; ++rt) red[buf][warp][r * RT + rt] = pd[r][rt];
     __syncthreads();
     // every thread is done with tile t-1: refill its stage with tile t-1+kApStages
     if (tid == 0 && t >= 1 && t - 1 + kApStages < ntiles) {
       ptx::fence_proxy_async();
       issue(t - 1 + kApStages);
     }
+    // ---- axpy phase
+    V a[RT][VPT];
+#pragma unroll
+    for (int rt = 0; rt < RT; ++rt)
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int64_t col = ((int64_t)k * kApThreads + tid) * VW;
+        a[rt][k] = (col < npad && i0 + rt < r1)
+                       ? *reinterpret_cast<const V*>(tile + rt * npad + col)
+                       : zero_vec(T(0));
+      }
 #pragma unroll
     for (int rt = 0; rt < RT; ++rt) {
       const int64_t row = i0 + rt;
-      const bool valid = row < r1;
-      double brow = 0.0;
-      if (RESID && valid) brow = b[row];
-      V a[VPT];
-#pragma unroll
-      for (int k = 0; k < VPT; ++k) {
-        const int64_t col = ((int64_t)k * kThreads + tid) * VW;
-        a[k] = (valid && col < npad) ? *reinterpret_cast<const V*>(tile + rt * npad + col)
-                                     : zero_vec(T(0));
-      }
+      if (row >= r1) break;
+      T brow = T(0);
+      if (RESID) brow = (T)b[row];
+      T c[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         T dot = T(0);
+        if constexpr (WPR % VW == 0) {
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) dot += red[buf][w][r * RT + rt];
-        T c = T(0);
-        if (valid) c = RESID ? (T)(brow - (double)dot) : dot;
-        if (tid == 0) {
-          s_cc[r] = fma((double)c, (double)c, s_cc[r]);
-          s_bc[r] = fma(brow, (double)c, s_bc[r]);
+          for (int sg = 0; sg < WPR; sg += VW) {
+            const V sv = *reinterpret_cast<const V*>(&segsum[t & 1][rt][r][sg]);
+#pragma unroll
+            for (int cc = 0; cc < VW; ++cc) dot += get(sv, cc);
+          }
+        } else {
+#pragma unroll
+          for (int sg = 0; sg < WPR; ++sg) dot += segsum[t & 1][rt][r][sg];
         }
+        c[r] = RESID ? (brow - dot) : dot;
+        if (tid == 0) {
+          s_cc[r] = fma(c[r], c[r], s_cc[r]);
+          s_bc[r] = fma(brow, c[r], s_bc[r]);
+        }
+      }
 #pragma unroll
-        for (int k = 0; k < VPT; ++k)
+      for (int k = 0; k < VPT; ++k)
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
 #pragma unroll
           for (int cc = 0; cc < VW; ++cc)
-            acc[r][k * VW + cc] = fma(c, get(a[k], cc), acc[r][k * VW + cc]);
-      }
+            acc[r][k * VW + cc] = fma(c[r], get(a[rt][k], cc), acc[r][k * VW + cc]);
     }
-    buf ^= 1;
   }
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+    const int64_t col = ((int64_t)k * kApThreads + tid) * VW;
     if (col < npad)
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
@@ -378,8 +415,8 @@ __global__ void __launch_bounds__(kThreads, 1) apass_tma_kernel(
   if (tid == 0)
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      spart[((int64_t)blockIdx.x * NR + r) * 2 + 0] = s_cc[r];
-      spart[((int64_t)blockIdx.x * NR + r) * 2 + 1] = s_bc[r];
+      spart[((int64_t)blockIdx.x * NR + r) * 2 + 0] = (double)s_cc[r];
+      spart[((int64_t)blockIdx.x * NR + r) * 2 + 1] = (double)s_bc[r];
     }
   if (arrive_last(counter)) {
     reduce_partials<2 * NR>(spart, (int)gridDim.x, sout);
@@ -396,52 +433,77 @@ __global__ void __launch_bounds__(kThreads, 1) apass_tma_kernel(
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pcg_reduce_kernel(
     const T* __restrict__ part, int P, int nr, int64_t npad, const T* __restrict__ q,
-    T* __restrict__ w, T* __restrict__ y, const double* __restrict__ dinv, PcgScalars* sc,
+    T* __restrict__ w, T* __restrict__ y, const T* __restrict__ dinv, PcgScalars* sc,
     const double* __restrict__ tt) {
   __shared__ T sh[kWarps][33];
+  __shared__ T s_alpha, s_sigma2;
+  __shared__ int s_ok;
   const int r = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (sc->done[r]) return;
+  if (threadIdx.x == 0) {
+    // delta_j and alpha_j once per CTA (FP64 instructions are slow; keep them off the threads)
+    const double sigma2 = sc->sigma2;
+    const double delta = tt[r * 2] - sigma2 * sc->qq[r];
+    if (blockIdx.x == 0) sc->delta[r] = delta;
+    s_ok = (delta > 0.0) ? 1 : 0;
+    const double alpha = s_ok ? sc->eta[r] / delta : 0.0;
+    if (blockIdx.x == 0 && s_ok) sc->alpha[r] = alpha;
+    s_alpha = (T)alpha;
+    s_sigma2 = (T)sigma2;
+  }
   const int64_t j = (int64_t)blockIdx.x * 32 + lane;
   T t = T(0);
-  if (j < npad)
-    for (int p = warp; p < P; p += kWarps) t += part[((int64_t)p * nr + r) * npad + j];
+  if (j < npad) {
+    T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
+    int p = warp;
+    for (; p + 3 * kWarps < P; p += 4 * kWarps) {
+      t0 += part[((int64_t)p * nr + r) * npad + j];
+      t1 += part[((int64_t)(p + kWarps) * nr + r) * npad + j];
+      t2 += part[((int64_t)(p + 2 * kWarps) * nr + r) * npad + j];
+      t3 += part[((int64_t)(p + 3 * kWarps) * nr + r) * npad + j];
+    }
+    for (; p < P; p += kWarps) t0 += part[((int64_t)p * nr + r) * npad + j];
+    t = (t0 + t1) + (t2 + t3);
+  }
   sh[warp][lane] = t;
   __syncthreads();
   if (warp != 0) return;
   T at = T(0);
 #pragma unroll
   for (int k = 0; k < kWarps; ++k) at += sh[k][lane];
-  const double sigma2 = sc->sigma2;
-  const double delta = tt[r * 2] - sigma2 * sc->qq[r];
-  if (blockIdx.x == 0 && lane == 0) sc->delta[r] = delta;
-  if (!(delta > 0.0)) return;                     // loss of positive definiteness (Sec. 3)
-  const double alpha = sc->eta[r] / delta;
-  if (blockIdx.x == 0 && lane == 0) sc->alpha[r] = alpha;
+  if (!s_ok) return;                              // loss of positive definiteness (Sec. 3)
   if (j < npad) {
     const T qj = q[r * npad + j];
-    w[r * npad + j] = fma((T)alpha, qj, w[r * npad + j]);
-    y[r * npad + j] = (at - (T)sigma2 * qj) * (T)dinv[j];
+    w[r * npad + j] = fma(s_alpha, qj, w[r * npad + j]);
+    y[r * npad + j] = (at - s_sigma2 * qj) * dinv[j];
   }
 }
 
 // Alg. 3 as printed: delta = ||p||^2 - sigma^2 ||q||^2, w += alpha q, y = D^{-1} q.
 template <typename T>
 __global__ void pcg_update_R_kernel(const T* __restrict__ q, T* __restrict__ w, T* __restrict__ y,
-                                    const double* __restrict__ dinv, PcgScalars* sc, int nr,
+                                    const T* __restrict__ dinv, PcgScalars* sc, int nr,
                                     int64_t npad) {
+  __shared__ T s_alpha;
+  __shared__ int s_ok;
   const int r = blockIdx.y;
   if (sc->done[r]) return;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double delta = sc->pp[r] - sc->sigma2 * sc->qq[r];
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->delta[r] = delta;
-  if (!(delta > 0.0)) return;
-  const double alpha = sc->eta[r] / delta;
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->alpha[r] = alpha;
+  if (threadIdx.x == 0) {
+    const double delta = sc->pp[r] - sc->sigma2 * sc->qq[r];
+    if (blockIdx.x == 0) sc->delta[r] = delta;
+    s_ok = (delta > 0.0) ? 1 : 0;
+    const double alpha = s_ok ? sc->eta[r] / delta : 0.0;
+    if (blockIdx.x == 0 && s_ok) sc->alpha[r] = alpha;
+    s_alpha = (T)alpha;
+  }
+  __syncthreads();
+  if (!s_ok) return;
   if (j < npad) {
     const T qj = q[r * npad + j];
-    w[r * npad + j] = fma((T)alpha, qj, w[r * npad + j]);
-    y[r * npad + j] = qj * (T)dinv[j];
+    w[r * npad + j] = fma(s_alpha, qj, w[r * npad + j]);
+    y[r * npad + j] = qj * dinv[j];
   }
 }
 
@@ -463,26 +525,57 @@ __global__ void __launch_bounds__(kThreads) gemv_wt_kernel(
   __shared__ double red[kWarps * 2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   bool active[2];
-  double alpha[2];
+  T alpha[2];
   for (int r = 0; r < 2; ++r) {
     active[r] = r < nr && (init || (!sc->done[r] && sc->delta[r] > 0.0));
-    alpha[r] = init ? 0.0 : sc->alpha[r];
+    alpha[r] = init ? T(0) : (T)sc->alpha[r];
   }
-  const double sigma2 = sc->sigma2;
-  for (int64_t e = tid; e < nr * npad; e += kThreads) ys[e] = y[e];
+  const T sigma2 = (T)sc->sigma2;
+  {
+    // stage y (nr x npad) with vector loads, several in flight per thread
+    const int64_t nv = nr * npad / VW;
+    for (int64_t e0 = tid; e0 < nv; e0 += 4 * kThreads) {
+      V t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + (int64_t)u * kThreads;
+        t[u] = (e < nv) ? reinterpret_cast<const V*>(y)[e] : zero_vec(T(0));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + (int64_t)u * kThreads;
+        if (e < nv) reinterpret_cast<V*>(ys)[e] = t[u];
+      }
+    }
+  }
   __syncthreads();
-  double ss[2] = {0.0, 0.0};
+  T ss[2] = {T(0), T(0)};
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, GW = (int64_t)gridDim.x * kWarps;
   for (int64_t j = gw; j < npad; j += GW) {
     const T* row = WT + j * npad;
     const int64_t lim = ((j + VW) / VW) * VW;    // entries 0..j, rounded up (zeros beyond j)
     T a0 = T(0), a1 = T(0);
-    for (int64_t c = (int64_t)lane * VW; c < lim; c += 32 * VW) {
-      V wv = *reinterpret_cast<const V*>(row + c);
+    constexpr int U = 8;                          // vector loads in flight per lane
+    for (int64_t cb = (int64_t)lane * VW; cb < lim; cb += 32 * VW * U) {
+      V wv[U];
 #pragma unroll
-      for (int k = 0; k < VW; ++k) {
-        a0 = fma(get(wv, k), ys[c + k], a0);
-        if (nr > 1) a1 = fma(get(wv, k), ys[npad + c + k], a1);
+      for (int u = 0; u < U; ++u) {
+        const int64_t c = cb + (int64_t)u * 32 * VW;
+        wv[u] = (c < lim) ? *reinterpret_cast<const V*>(row + c) : zero_vec(T(0));
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t c = cb + (int64_t)u * 32 * VW;
+        if (c < lim) {
+          const V y0 = *reinterpret_cast<const V*>(ys + c);
+#pragma unroll
+          for (int k = 0; k < VW; ++k) a0 = fma(get(wv[u], k), get(y0, k), a0);
+          if (nr > 1) {
+            const V y1 = *reinterpret_cast<const V*>(ys + npad + c);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) a1 = fma(get(wv[u], k), get(y1, k), a1);
+          }
+        }
       }
     }
     a0 = warp_sum(a0);
@@ -494,18 +587,18 @@ __global__ void __launch_bounds__(kThreads) gemv_wt_kernel(
         T sv = *sp;
         if (init) sv = vr[r];
         else if (active[r]) {
-          if (modeA) sv = sv - (T)alpha[r] * vr[r];
-          else sv = sv - (T)alpha[r] * (p[r * npad + j] - (T)sigma2 * vr[r]);
+          if (modeA) sv = sv - alpha[r] * vr[r];
+          else sv = sv - alpha[r] * (p[r * npad + j] - sigma2 * vr[r]);
         }
         if (init || active[r]) *sp = sv;
-        ss[r] += (double)sv * (double)sv;
+        ss[r] = fma(sv, sv, ss[r]);
       }
     }
   }
   // CTA partials of ||s||^2
   ss[0] = warp_sum(ss[0]);
   ss[1] = warp_sum(ss[1]);
-  if (lane == 0) { red[warp * 2] = ss[0]; red[warp * 2 + 1] = ss[1]; }
+  if (lane == 0) { red[warp * 2] = (double)ss[0]; red[warp * 2 + 1] = (double)ss[1]; }
   __syncthreads();
   if (tid < 2) {
     double t = 0.0;
@@ -547,7 +640,7 @@ __global__ void __launch_bounds__(kThreads) gemv_wt_kernel(
 template <typename T>
 __global__ void __launch_bounds__(kThreads) gemv_w_kernel(
     const T* __restrict__ W, int64_t npad, const T* __restrict__ s, const T* __restrict__ p_prev,
-    T* __restrict__ p_out, const double* __restrict__ dinv, T* __restrict__ q,
+    T* __restrict__ p_out, const T* __restrict__ dinv, T* __restrict__ q,
     double* __restrict__ part, PcgScalars* sc, int nr) {
   using V = typename VecOf<T>::type;
   constexpr int VW = VecOf<T>::W;
@@ -556,9 +649,33 @@ __global__ void __launch_bounds__(kThreads) gemv_w_kernel(
   __shared__ double red[kWarps * 4];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T beta0 = (T)sc->beta[0], beta1 = (T)(nr > 1 ? sc->beta[1] : 0.0);
-  for (int64_t e = tid; e < nr * npad; e += kThreads) {
-    const T bt = (e < npad) ? beta0 : beta1;
-    ps[e] = s[e] + bt * p_prev[e];
+  {
+    // stage p_j = s + beta p_prev (nr x npad) with vector loads, several in flight per thread
+    const int64_t nv = nr * npad / VW;
+    for (int64_t e0 = tid; e0 < nv; e0 += 4 * kThreads) {
+      V sv[4], pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + (int64_t)u * kThreads;
+        sv[u] = (e < nv) ? reinterpret_cast<const V*>(s)[e] : zero_vec(T(0));
+        pv[u] = (e < nv) ? reinterpret_cast<const V*>(p_prev)[e] : zero_vec(T(0));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + (int64_t)u * kThreads;
+        if (e < nv) {
+          const T bt = (e * VW < npad) ? beta0 : beta1;
+          V o;
+          if constexpr (VW == 4) {
+            o = make_float4(sv[u].x + bt * pv[u].x, sv[u].y + bt * pv[u].y,
+                            sv[u].z + bt * pv[u].z, sv[u].w + bt * pv[u].w);
+          } else {
+            o = make_double2(sv[u].x + bt * pv[u].x, sv[u].y + bt * pv[u].y);
+          }
+          reinterpret_cast<V*>(ps)[e] = o;
+        }
+      }
+    }
   }
   __syncthreads();
   {
@@ -566,32 +683,47 @@ __global__ void __launch_bounds__(kThreads) gemv_w_kernel(
     const int64_t e0 = (int64_t)blockIdx.x * chunk, e1 = min((int64_t)nr * npad, e0 + chunk);
     for (int64_t e = e0 + tid; e < e1; e += kThreads) p_out[e] = ps[e];
   }
-  double acc4[4] = {0.0, 0.0, 0.0, 0.0};   // qq0, qq1, pp0, pp1
+  T acc4[4] = {T(0), T(0), T(0), T(0)};   // qq0, qq1, pp0, pp1 (working type: no FP64 per row)
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, GW = (int64_t)gridDim.x * kWarps;
   for (int64_t i = gw; i < npad; i += GW) {
     const T* row = W + i * npad;
     T a0 = T(0), a1 = T(0);
-    for (int64_t c = (i / VW) * VW + (int64_t)lane * VW; c < npad; c += 32 * VW) {
-      V wv = *reinterpret_cast<const V*>(row + c);
+    constexpr int U = 8;                          // vector loads in flight per lane
+    for (int64_t cb = (i / VW) * VW + (int64_t)lane * VW; cb < npad; cb += 32 * VW * U) {
+      V wv[U];
 #pragma unroll
-      for (int k = 0; k < VW; ++k) {
-        a0 = fma(get(wv, k), ps[c + k], a0);
-        if (nr > 1) a1 = fma(get(wv, k), ps[npad + c + k], a1);
+      for (int u = 0; u < U; ++u) {
+        const int64_t c = cb + (int64_t)u * 32 * VW;
+        wv[u] = (c < npad) ? *reinterpret_cast<const V*>(row + c) : zero_vec(T(0));
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t c = cb + (int64_t)u * 32 * VW;
+        if (c < npad) {
+          const V p0 = *reinterpret_cast<const V*>(ps + c);
+#pragma unroll
+          for (int k = 0; k < VW; ++k) a0 = fma(get(wv[u], k), get(p0, k), a0);
+          if (nr > 1) {
+            const V p1 = *reinterpret_cast<const V*>(ps + npad + c);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) a1 = fma(get(wv[u], k), get(p1, k), a1);
+          }
+        }
       }
     }
     a0 = warp_sum(a0);
     if (nr > 1) a1 = warp_sum(a1);
     if (lane == 0) {
-      const T di = (T)dinv[i];
+      const T di = dinv[i];
       const T q0 = a0 * di;
       q[i] = q0;
-      acc4[0] += (double)q0 * (double)q0;
-      acc4[2] += (double)ps[i] * (double)ps[i];
+      acc4[0] = fma(q0, q0, acc4[0]);
+      acc4[2] = fma(ps[i], ps[i], acc4[2]);
       if (nr > 1) {
         const T q1 = a1 * di;
         q[npad + i] = q1;
-        acc4[1] += (double)q1 * (double)q1;
-        acc4[3] += (double)ps[npad + i] * (double)ps[npad + i];
+        acc4[1] = fma(q1, q1, acc4[1]);
+        acc4[3] = fma(ps[npad + i], ps[npad + i], acc4[3]);
       }
     }
   }
@@ -599,7 +731,7 @@ __global__ void __launch_bounds__(kThreads) gemv_w_kernel(
   for (int k = 0; k < 4; ++k) acc4[k] = warp_sum(acc4[k]);
   if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[warp * 4 + k] = acc4[k];
+    for (int k = 0; k < 4; ++k) red[warp * 4 + k] = (double)acc4[k];
   __syncthreads();
   if (tid < 4) {
     double t = 0.0;
@@ -657,8 +789,18 @@ __global__ void __launch_bounds__(kThreads) resid_reduce_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t j = (int64_t)blockIdx.x * 32 + lane;
   double t = 0.0;
-  if (j < npad)
-    for (int p = warp; p < P; p += kWarps) t += part[(int64_t)p * npad + j];
+  if (j < npad) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    int p = warp;
+    for (; p + 3 * kWarps < P; p += 4 * kWarps) {
+      t0 += part[(int64_t)p * npad + j];
+      t1 += part[(int64_t)(p + kWarps) * npad + j];
+      t2 += part[(int64_t)(p + 2 * kWarps) * npad + j];
+      t3 += part[(int64_t)(p + 3 * kWarps) * npad + j];
+    }
+    for (; p < P; p += kWarps) t0 += part[(int64_t)p * npad + j];
+    t = (t0 + t1) + (t2 + t3);
+  }
   sh[warp][lane] = t;
   __syncthreads();
   const double xx = rs->xx;
@@ -776,30 +918,43 @@ __global__ void vec_convert_kernel(const double* __restrict__ in, T* __restrict_
 
 inline int blocks_for(int64_t count, int threads) { return (int)((count + threads - 1) / threads); }
 
-template <typename T, int NR, bool RESID>
-void apass_tma_dispatch(int vpt, dim3 grid, size_t smem, const T* A, int64_t m, int64_t npad,
-                        const T* v, int64_t ldv, const double* b, T* part, double* spart,
-                        double* sout, unsigned int* counter, const int* done, int* err,
-                        cudaStream_t s) {
+template <typename T, int NR, bool RESID, int TH>
+void apass_tma_dispatch_th(int vpt, dim3 grid, size_t smem, const T* A, int64_t m, int64_t npad,
+                           const T* v, int64_t ldv, const double* b, T* part, double* spart,
+                           double* sout, unsigned int* counter, const int* done, int* err,
+                           cudaStream_t s) {
   switch (vpt) {
 #define TLS_AT(V)                                                                               \
   case V: {                                                                                     \
     static bool attr = false;                                                                   \
     if (!attr) {                                                                                \
-      cudaFuncSetAttribute(apass_tma_kernel<T, NR, RESID, V>,                                  \
+      cudaFuncSetAttribute(apass_tma_kernel<T, NR, RESID, V, TH>,                              \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);            \
       attr = true;                                                                              \
     }                                                                                           \
-    apass_tma_kernel<T, NR, RESID, V><<<grid, kThreads, smem, s>>>(A, m, npad, v, ldv, b, part, \
-                                                                   spart, sout, counter, done,  \
-                                                                   err);                        \
+    apass_tma_kernel<T, NR, RESID, V, TH><<<grid, TH, smem, s>>>(A, m, npad, v, ldv, b, part,   \
+                                                               spart, sout, counter, done,    \
+                                                               err);                          \
     count_launch();                                                                             \
     break;                                                                                      \
   }
-    TLS_AT(1) TLS_AT(2) TLS_AT(4) TLS_AT(8)
+    TLS_AT(1) TLS_AT(2) TLS_AT(4)
 #undef TLS_AT
     default: break;
   }
+}
+
+template <typename T, int NR, bool RESID>
+void apass_tma_dispatch(int threads, int vpt, dim3 grid, size_t smem, const T* A, int64_t m,
+                        int64_t npad, const T* v, int64_t ldv, const double* b, T* part,
+                        double* spart, double* sout, unsigned int* counter, const int* done,
+                        int* err, cudaStream_t s) {
+  if (threads == 512)
+    apass_tma_dispatch_th<T, NR, RESID, 512>(vpt, grid, smem, A, m, npad, v, ldv, b, part, spart,
+                                              sout, counter, done, err, s);
+  else
+    apass_tma_dispatch_th<T, NR, RESID, 256>(vpt, grid, smem, A, m, npad, v, ldv, b, part, spart,
+                                              sout, counter, done, err, s);
 }
 
 template <typename T, int NR, bool RESID>
@@ -819,23 +974,31 @@ void apass_dispatch(int vpt, dim3 grid, const T* A, int64_t lda, int64_t m, int6
 
 // =========================================================================================
 template <typename T>
-ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms) {
+ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms, int variant) {
   (void)nr;
   constexpr int VW = VecOf<T>::W;
   ApassPlan p;
+  p.variant = variant;
   int64_t need = (npad + (int64_t)kThreads * VW - 1) / ((int64_t)kThreads * VW);
   p.vpt = 1;
   while (p.vpt < need) p.vpt *= 2;
-  const int rt = (p.vpt >= 8) ? 1 : (8 / p.vpt);
+  // variant 0: registers only (apass_kernel); 1: staged, 256 threads; 2: staged, 512 threads
+  p.threads = (variant == 2) ? 512 : 256;
+  int64_t need2 = (npad + (int64_t)p.threads * VW - 1) / ((int64_t)p.threads * VW);
+  int vpt2 = 1;
+  while (vpt2 < need2) vpt2 *= 2;
+  const int rt = (vpt2 <= 4) ? (4 / vpt2) : 1;
   const size_t stage = (size_t)rt * (size_t)npad * sizeof(T);
   p.smem = kApStages * stage;
-  p.tma = p.smem <= 200 * 1024;
+  p.tma = variant != 0 && vpt2 <= 4 && p.smem <= 200 * 1024;
   if (p.tma) {
+    p.vpt = vpt2;
     // one CTA per SM (the ring takes most of shared memory), at least a few tiles per CTA
     const int64_t by_rows = std::max<int64_t>(1, m / (2 * rt));
     p.grid = (int)std::min<int64_t>((int64_t)num_sms, by_rows);
   } else {
-    const int64_t by_rows = std::max<int64_t>(1, m / (4 * rt));
+    const int rt_reg = (p.vpt >= 8) ? 1 : (8 / p.vpt);   // rows per tile of apass_kernel
+    const int64_t by_rows = std::max<int64_t>(1, m / (4 * rt_reg));
     p.grid = (int)std::min<int64_t>(2 * (int64_t)num_sms, by_rows);
   }
   return p;
@@ -849,10 +1012,10 @@ void launch_apass(const ApassPlan& plan, const T* A, int64_t lda, int64_t m, int
   dim3 grid(plan.grid);
   if (plan.tma && lda == npad) {
     if (nr == 1) {
-      if (resid) apass_tma_dispatch<T, 1, true>(plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
-      else apass_tma_dispatch<T, 1, false>(plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
+      if (resid) apass_tma_dispatch<T, 1, true>(plan.threads, plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
+      else apass_tma_dispatch<T, 1, false>(plan.threads, plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
     } else {
-      apass_tma_dispatch<T, 2, false>(plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
+      apass_tma_dispatch<T, 2, false>(plan.threads, plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
     }
     return;
   }
@@ -896,7 +1059,7 @@ void launch_gemv_wt(const T* WT, int64_t npad, const T* y, T* s, const T* p, T* 
 
 template <typename T>
 void launch_gemv_w(const T* W, int64_t npad, const T* s, const T* p_prev, T* p_out,
-                   const double* dinv, T* q, double* part, PcgScalars* sc, int nr,
+                   const T* dinv, T* q, double* part, PcgScalars* sc, int nr,
                    cudaStream_t st) {
   const size_t smem = sizeof(T) * nr * npad;
   allow_smem(gemv_w_kernel<T>, smem);
@@ -906,14 +1069,14 @@ void launch_gemv_w(const T* W, int64_t npad, const T* s, const T* p_prev, T* p_o
 
 template <typename T>
 void launch_pcg_reduce(const T* part, int P, int64_t npad, const T* q, T* w, T* y,
-                       const double* dinv, PcgScalars* sc, const double* tt, int nr,
+                       const T* dinv, PcgScalars* sc, const double* tt, int nr,
                        cudaStream_t s) {
   dim3 grid((unsigned)((npad + 31) / 32), nr);
   pcg_reduce_kernel<T><<<grid, kThreads, 0, s>>>(part, P, nr, npad, q, w, y, dinv, sc, tt); count_launch();
 }
 
 template <typename T>
-void launch_pcg_update_R(const T* q, T* w, T* y, const double* dinv, PcgScalars* sc, int nr,
+void launch_pcg_update_R(const T* q, T* w, T* y, const T* dinv, PcgScalars* sc, int nr,
                          int64_t npad, cudaStream_t s) {
   dim3 grid((unsigned)blocks_for(npad, 256), nr);
   pcg_update_R_kernel<T><<<grid, 256, 0, s>>>(q, w, y, dinv, sc, nr, npad); count_launch();
@@ -951,7 +1114,7 @@ void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaS
 }
 
 #define TLS_INST(T)                                                                            \
-  template ApassPlan plan_apass<T>(int64_t, int64_t, int, int);                                \
+  template ApassPlan plan_apass<T>(int64_t, int64_t, int, int, int);                           \
   template void launch_apass<T>(const ApassPlan&, const T*, int64_t, int64_t, int64_t, int,    \
                                 bool, const T*, int64_t, const double*, T*, double*, double*,  \
                                 unsigned int*, const int*, int*, cudaStream_t);                \
@@ -960,11 +1123,11 @@ void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaS
                                    double, double, cudaStream_t);                              \
   template void launch_gemv_wt<T>(const T*, int64_t, const T*, T*, const T*, T*, double*,      \
                                   PcgScalars*, bool, bool, int, cudaStream_t);                 \
-  template void launch_gemv_w<T>(const T*, int64_t, const T*, const T*, T*, const double*, T*, \
+  template void launch_gemv_w<T>(const T*, int64_t, const T*, const T*, T*, const T*, T*,      \
                                  double*, PcgScalars*, int, cudaStream_t);                     \
-  template void launch_pcg_reduce<T>(const T*, int, int64_t, const T*, T*, T*, const double*,  \
+  template void launch_pcg_reduce<T>(const T*, int, int64_t, const T*, T*, T*, const T*,       \
                                      PcgScalars*, const double*, int, cudaStream_t);           \
-  template void launch_pcg_update_R<T>(const T*, T*, T*, const double*, PcgScalars*, int,      \
+  template void launch_pcg_update_R<T>(const T*, T*, T*, const T*, PcgScalars*, int,           \
                                        int64_t, cudaStream_t);                                 \
   template void launch_rqi_update<T>(double*, const T*, const T*, const double*, RqiScalars*,  \
                                      int64_t, cudaStream_t);                                   \

@@ -5,6 +5,9 @@
 #include "tls_internal.h"
 
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
@@ -41,6 +44,17 @@ struct tls_ctx {
   std::vector<DevBuf> bufs;
 
   // problem data (device)
+  bool sparse = false;     // A held as CSR + CSC instead of dense
+  int* rp = nullptr;       // CSR row offsets (m + 1)
+  int* ci = nullptr;       // CSR column indices (nnz)
+  double* v64 = nullptr;   // CSR values (nnz)
+  float* v32 = nullptr;    // CSR values rounded to FP32
+  int* cp = nullptr;       // CSC column offsets (npad + 1)
+  int* ri = nullptr;       // CSC row indices (nnz)
+  double* cv64 = nullptr;  // CSC values (nnz)
+  float* cv32 = nullptr;   // CSC values rounded to FP32
+  double* rbuf = nullptr;  // residual r (m, sparse path)
+  void* tbuf = nullptr;    // t = A q, two right-hand sides (2 m, u type, sparse path)
   double* A64 = nullptr;   // m x npad, zero padded columns
   double* b = nullptr;     // m
   float* A32 = nullptr;    // m x npad, made by tls_factor when u = FP32
@@ -53,6 +67,7 @@ struct tls_ctx {
   tls_options opt{};
   double* d = nullptr;       // column norms (npad)
   double* dinv = nullptr;    // 1 / d
+  float* dinv32 = nullptr;   // 1 / d in FP32 (for the FP32 PCGTLS kernels)
   void* H = nullptr;         // scaled Gram (npad^2, float or double, see H_fp64)
   bool H_fp64 = false;
   bool gram_tc_used = false;
@@ -177,6 +192,7 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->f = alloc_t<double>(ctx, npad);
   ctx->d = alloc_t<double>(ctx, npad);
   ctx->dinv = alloc_t<double>(ctx, npad);
+  ctx->dinv32 = alloc_t<float>(ctx, npad);
   ctx->sout = alloc_t<double>(ctx, 8);
   ctx->gpart = alloc_t<double>(ctx, 4096);
   ctx->counter = alloc_t<unsigned int>(ctx, 4);
@@ -184,7 +200,7 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->sc = alloc_t<PcgScalars>(ctx, 1);
   ctx->rs = alloc_t<RqiScalars>(ctx, 1);
   if (!ctx->b || !ctx->x || !ctx->x_best || !ctx->f || !ctx->d || !ctx->dinv || !ctx->sout ||
-      !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs || !ctx->derr) {
+      !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs || !ctx->derr || !ctx->dinv32) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
@@ -196,10 +212,14 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   TLS_CK(cudaMemsetAsync(ctx->x_best, 0, sizeof(double) * npad, ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->f, 0, sizeof(double) * npad, ctx->stream));
   // FP64 residual pass plan and partials
-  ctx->plan64 = tls::plan_apass<double>(m, npad, 1, ctx->num_sms);
+  ctx->plan64 = tls::plan_apass<double>(m, npad, 1, ctx->num_sms, 1);
   ctx->P64 = ctx->plan64.grid;
-  ctx->part64 = alloc_t<double>(ctx, (int64_t)ctx->P64 * npad);
-  ctx->spart = alloc_t<double>(ctx, (int64_t)2 * ctx->num_sms * 2 * 2 + 16);
+  // partials sized for the largest grid of any pass variant (2 CTAs per SM)
+  ctx->part64 = alloc_t<double>(ctx, (int64_t)2 * ctx->num_sms * npad);
+  // pass partials: dense passes use <= 2 CTAs per SM; the sparse row kernels one CTA per 256 rows
+  const int64_t nsp = std::max<int64_t>((int64_t)2 * ctx->num_sms * 2 * 2,
+                                        4 * (int64_t)tls::sparse_grid_rows(m)) + 16;
+  ctx->spart = alloc_t<double>(ctx, nsp);
   if (!ctx->part64 || !ctx->spart) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
@@ -260,6 +280,14 @@ void prof_collect(tls_ctx* c) {
 // RQI residual block (FP64 pass over A): r, sigma^2, f, g, psi at ctx->x.
 // ---------------------------------------------------------------------------------------
 tls_status residual_pass(tls_ctx* ctx) {
+  if (ctx->sparse) {
+    Prof pr(ctx, TLS_PROF_RESID_PASS);
+    tls::sparse_resid(ctx->rp, ctx->ci, ctx->v64, ctx->cp, ctx->ri, ctx->cv64, ctx->b, ctx->x,
+                      ctx->m, ctx->n, ctx->npad, ctx->rbuf, ctx->f, ctx->spart, ctx->sout,
+                      ctx->counter, ctx->rs, ctx->gpart, ctx->stream);
+    TLS_CK_LAUNCH("sparse residual pass");
+    return TLS_OK;
+  }
   {
     Prof pr(ctx, TLS_PROF_RESID_PASS);
     tls::launch_apass<double>(ctx->plan64, ctx->A64, ctx->npad, ctx->m, ctx->npad, 1, true,
@@ -283,6 +311,13 @@ const int* done_ptr(tls_ctx* ctx) {
   return reinterpret_cast<const int*>(reinterpret_cast<const char*>(ctx->sc) +
                                       offsetof(PcgScalars, done));
 }
+
+template <typename T>
+const T* dinv_t(tls_ctx* ctx);
+template <>
+const float* dinv_t<float>(tls_ctx* ctx) { return ctx->dinv32; }
+template <>
+const double* dinv_t<double>(tls_ctx* ctx) { return ctx->dinv; }
 
 template <typename T>
 struct UVecs {
@@ -318,10 +353,19 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
     T* pprev = pb[(j + 1) & 1];
     {
       Prof pr(ctx, TLS_PROF_PCG_GEMV);
-      tls::launch_gemv_w<T>(W, npad, v.s, pprev, pcur, ctx->dinv, v.q, ctx->gpart, ctx->sc, nr,
-                            ctx->stream);
+      tls::launch_gemv_w<T>(W, npad, v.s, pprev, pcur, dinv_t<T>(ctx), v.q, ctx->gpart, ctx->sc,
+                            nr, ctx->stream);
     }
-    if (modeA) {
+    if (modeA && ctx->sparse) {
+      Prof pr(ctx, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
+      const bool f32 = sizeof(T) == 4;
+      const T* val = f32 ? reinterpret_cast<const T*>(ctx->v32) : reinterpret_cast<const T*>(ctx->v64);
+      const T* cval = f32 ? reinterpret_cast<const T*>(ctx->cv32) : reinterpret_cast<const T*>(ctx->cv64);
+      tls::sparse_pcg_pass<T>(ctx->rp, ctx->ci, val, ctx->cp, ctx->ri, cval, ctx->m, ctx->n, npad, nr,
+                              v.q, static_cast<T*>(ctx->tbuf), v.w, v.y, dinv_t<T>(ctx), ctx->sc,
+                              ctx->spart, ctx->sout + 4, ctx->counter + 1, done_ptr(ctx),
+                              ctx->stream);
+    } else if (modeA) {
       {
         Prof pr(ctx, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
         tls::launch_apass<T>(ctx->planU, Au, npad, ctx->m, npad, nr, false, v.q, npad, nullptr,
@@ -330,10 +374,10 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
       }
       Prof pr(ctx, TLS_PROF_PCG_REDUCE);
       tls::launch_pcg_reduce<T>(static_cast<const T*>(ctx->part), ctx->PU, npad, v.q, v.w, v.y,
-                                ctx->dinv, ctx->sc, ctx->sout + 4, nr, ctx->stream);
+                                dinv_t<T>(ctx), ctx->sc, ctx->sout + 4, nr, ctx->stream);
     } else {
       Prof pr(ctx, TLS_PROF_PCG_REDUCE);
-      tls::launch_pcg_update_R<T>(v.q, v.w, v.y, ctx->dinv, ctx->sc, nr, npad, ctx->stream);
+      tls::launch_pcg_update_R<T>(v.q, v.w, v.y, dinv_t<T>(ctx), ctx->sc, nr, npad, ctx->stream);
     }
     {
       Prof pr(ctx, TLS_PROF_PCG_GEMV);
@@ -353,8 +397,8 @@ tls_status precond_apply(tls_ctx* ctx, const double* y) {
                           ctx->sc, 0.0, 0.0, ctx->stream);
   tls::launch_gemv_wt<T>(static_cast<const T*>(ctx->WT), ctx->npad, v.y, v.s, nullptr, nullptr,
                          ctx->gpart, ctx->sc, true, true, 1, ctx->stream);
-  tls::launch_gemv_w<T>(static_cast<const T*>(ctx->W), ctx->npad, v.s, v.p1, v.p0, ctx->dinv,
-                        v.q, ctx->gpart, ctx->sc, 1, ctx->stream);
+  tls::launch_gemv_w<T>(static_cast<const T*>(ctx->W), ctx->npad, v.s, v.p1, v.p0,
+                        dinv_t<T>(ctx), v.q, ctx->gpart, ctx->sc, 1, ctx->stream);
   TLS_CK_LAUNCH("precond");
   return TLS_OK;
 }
@@ -474,6 +518,8 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     info->t_factor_ms = ctx->t_factor_ms;
     info->t_solve_ms = ms;
     info->fail_pivot = (int)ctx->fail_pivot;
+    info->pass_variant[0] = ctx->plan64.variant;
+    info->pass_variant[1] = ctx->planU.variant;
     info->n_psi = n_psi;
     for (int i = 0; i < n_psi; ++i) info->psi_hist[i] = psi_hist[i];
   }
@@ -485,21 +531,99 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
 // ---------------------------------------------------------------------------------------
 Prec to_prec(tls_prec p) { return static_cast<Prec>((int)p); }
 
+// ---------------------------------------------------------------------------------------
+// Autotuner for the fused pass over A: each variant (register kernel; bulk-copy-staged with 256
+// or 512 threads) is timed on the context's own matrix (one warm-up and three launches, CUDA
+// events) and the fastest is cached per (type, right-hand sides, m, n_pad) for the process.
+// ---------------------------------------------------------------------------------------
+std::map<std::tuple<int, int, int, int64_t, int64_t, int>, int> g_tune;
+std::mutex g_tune_mu;
+
+template <typename T>
+tls::ApassPlan tune_apass(tls_ctx* ctx, const T* A, int nr, bool resid, const T* v,
+                          const double* b, T* part, double* sout, unsigned int* counter) {
+  const auto key = std::make_tuple((int)sizeof(T), nr, resid ? 1 : 0, ctx->m, ctx->npad,
+                                   ctx->device);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end())
+      return tls::plan_apass<T>(ctx->m, ctx->npad, nr, ctx->num_sms, it->second);
+  }
+  int best_v = 1;
+  float best_ms = 1e30f;
+  for (int var = 0; var < tls::kApassVariants; ++var) {
+    tls::ApassPlan pl = tls::plan_apass<T>(ctx->m, ctx->npad, nr, ctx->num_sms, var);
+    if (var != 0 && !pl.tma) continue;
+    auto go = [&]() {
+      tls::launch_apass<T>(pl, A, ctx->npad, ctx->m, ctx->npad, nr, resid, v, ctx->npad, b, part,
+                           ctx->spart, sout, counter, nullptr, ctx->derr, ctx->stream);
+    };
+    go();
+    cudaEventRecord(ctx->ev0, ctx->stream);
+    for (int r = 0; r < 3; ++r) go();
+    cudaEventRecord(ctx->ev1, ctx->stream);
+    if (cudaEventSynchronize(ctx->ev1) != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_v = var;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best_v;
+  }
+  return tls::plan_apass<T>(ctx->m, ctx->npad, nr, ctx->num_sms, best_v);
+}
+
+void tune_passes(tls_ctx* ctx) {
+  // the FP64 residual pass (1 RHS) and the PCGTLS pass (2 RHS) in the u type
+  ctx->plan64 = tune_apass<double>(ctx, ctx->A64, 1, true, ctx->x, ctx->b, ctx->part64, ctx->sout,
+                                   ctx->counter);
+  ctx->P64 = ctx->plan64.grid;
+  if (ctx->u == Prec::FP64) {
+    ctx->planU = tune_apass<double>(ctx, ctx->A64, 2, false, static_cast<double*>(ctx->vbuf),
+                                    nullptr, static_cast<double*>(ctx->part), ctx->sout + 4,
+                                    ctx->counter + 1);
+  } else {
+    ctx->planU = tune_apass<float>(ctx, ctx->A32, 2, false, static_cast<float*>(ctx->vbuf),
+                                   nullptr, static_cast<float*>(ctx->part), ctx->sout + 4,
+                                   ctx->counter + 1);
+  }
+  ctx->PU = ctx->planU.grid;
+}
+
 tls_status ensure_solve_buffers(tls_ctx* ctx) {
   const int64_t npad = ctx->npad;
   const size_t us = u_size(ctx->u);
   if (ctx->vbuf) dev_free(ctx, ctx->vbuf);
   if (ctx->part) dev_free(ctx, ctx->part);
   ctx->vbuf = dev_alloc(ctx, us * 12 * (size_t)npad);
-  if (ctx->u == Prec::FP64) ctx->planU = tls::plan_apass<double>(ctx->m, npad, 2, ctx->num_sms);
-  else ctx->planU = tls::plan_apass<float>(ctx->m, npad, 2, ctx->num_sms);
+  if (ctx->u == Prec::FP64) ctx->planU = tls::plan_apass<double>(ctx->m, npad, 2, ctx->num_sms, 1);
+  else ctx->planU = tls::plan_apass<float>(ctx->m, npad, 2, ctx->num_sms, 1);
   ctx->PU = ctx->planU.grid;
-  ctx->part = dev_alloc(ctx, us * (size_t)ctx->PU * 2 * (size_t)npad);
+  ctx->part = dev_alloc(ctx, us * (size_t)2 * ctx->num_sms * 2 * (size_t)npad);
   if (!ctx->vbuf || !ctx->part) {
     set_err(ctx, "device allocation failed (solve buffers)");
     return TLS_ERR_OOM;
   }
   TLS_CK(cudaMemsetAsync(ctx->vbuf, 0, us * 12 * (size_t)npad, ctx->stream));
+  if (ctx->sparse) {
+    if (ctx->tbuf) dev_free(ctx, ctx->tbuf);
+    ctx->tbuf = dev_alloc(ctx, us * 2 * (size_t)ctx->m);
+    if (!ctx->tbuf) {
+      set_err(ctx, "device allocation failed (sparse solve buffers)");
+      return TLS_ERR_OOM;
+    }
+  } else {
+    tune_passes(ctx);
+  }
+  TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   return TLS_OK;
 }
 
@@ -513,7 +637,7 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     *p = nullptr;
   }
   ctx->factored = false;
-  if (ctx->u == Prec::FP32 && ctx->A32 == nullptr) {
+  if (!ctx->sparse && ctx->u == Prec::FP32 && ctx->A32 == nullptr) {
     ctx->A32 = alloc_t<float>(ctx, m * npad);
     if (!ctx->A32) {
       set_err(ctx, "device allocation failed (FP32 copy of A)");
@@ -528,8 +652,12 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   }
   {
     Prof pr(ctx, TLS_PROF_SCALE);
-    tls::launch_colnorm(ctx->A64, npad, m, n, npad, ctx->u == Prec::FP32 ? ctx->A32 : nullptr,
-                        npad, ctx->d, nullptr, ctx->dinv, cpart, st);
+    if (ctx->sparse)
+      tls::sparse_colnorm(ctx->cp, ctx->cv64, ctx->u == Prec::FP32 ? ctx->cv32 : nullptr, n, npad,
+                          ctx->d, ctx->dinv, ctx->dinv32, st);
+    else
+      tls::launch_colnorm(ctx->A64, npad, m, n, npad, ctx->u == Prec::FP32 ? ctx->A32 : nullptr,
+                          npad, ctx->d, ctx->dinv32, ctx->dinv, cpart, st);
   }
   TLS_CK_LAUNCH("column norms");
   {
@@ -562,7 +690,9 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     const bool chol64 = (pf == Prec::FP64);
     const size_t ce = chol64 ? 8 : 4;
     const size_t ae = (pf == Prec::FP64) ? 8 : (pf == Prec::FP32 ? 4 : 2);
-    void* AsT = dev_alloc(ctx, ae * (size_t)npad * (size_t)mpad);
+    // dense: the scaled, rounded, transposed A_s; sparse: its values in CSR and CSC order
+    void* AsT = ctx->sparse ? dev_alloc(ctx, 2 * ce * (size_t)std::max<int64_t>(ctx->nnz, 1))
+                            : dev_alloc(ctx, ae * (size_t)npad * (size_t)mpad);
     ctx->H = dev_alloc(ctx, ce * (size_t)npad * (size_t)npad);
     void* M = dev_alloc(ctx, ce * (size_t)npad * (size_t)npad);
     if (!AsT || !ctx->H || !M) {
@@ -570,10 +700,25 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
       return TLS_ERR_OOM;
     }
     const bool from64 = (ctx->u != Prec::FP32) || (pf == Prec::FP64);
+    if (ctx->sparse) {
+      Prof pr(ctx, TLS_PROF_GRAM);
+      const int64_t nz = std::max<int64_t>(ctx->nnz, 1);
+      if (chol64)
+        tls::sparse_gram<double>(ctx->rp, ctx->ci, ctx->v32, ctx->v64, ctx->cp, ctx->ri, ctx->cv32,
+                                 ctx->cv64, ctx->dinv32, ctx->dinv, n, npad, ctx->nnz, pf,
+                                 static_cast<double*>(AsT), static_cast<double*>(AsT) + nz,
+                                 static_cast<double*>(ctx->H), st);
+      else
+        tls::sparse_gram<float>(ctx->rp, ctx->ci, ctx->v32, ctx->v64, ctx->cp, ctx->ri, ctx->cv32,
+                                ctx->cv64, ctx->dinv32, ctx->dinv, n, npad, ctx->nnz, pf,
+                                static_cast<float*>(AsT), static_cast<float*>(AsT) + nz,
+                                static_cast<float*>(ctx->H), st);
+      ctx->gram_tc_used = false;
+    } else {
     {
       Prof pr(ctx, TLS_PROF_SCALE);
       tls::launch_scale_cast_T(from64 ? (const void*)ctx->A64 : (const void*)ctx->A32, from64,
-                               npad, m, n, npad, mpad, ctx->dinv, AsT, pf, st);
+                               npad, m, n, npad, mpad, ctx->dinv, ctx->dinv32, AsT, pf, st);
     }
     {
       Prof pr(ctx, TLS_PROF_GRAM);
@@ -591,6 +736,7 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
       }
       if (!tc) tls::launch_gram_simt(AsT, pf, n, npad, mpad, ctx->H, st);
       ctx->gram_tc_used = tc;
+    }
     }
     TLS_CK_LAUNCH("gram");
     dev_free(ctx, AsT);
@@ -841,26 +987,82 @@ tls_status tls_create_dense(tls_ctx** out, int64_t m, int64_t n, const double* A
 tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
                           const int32_t* col_idx, const double* val, const double* b,
                           int on_device, void* stream) {
-  // The CSR path expands A into the dense device layout until the sparse kernels land.
   if (!out) return TLS_ERR_ARG;
   *out = nullptr;
   if (on_device || m < 1 || n < 1 || m < n || nnz < 0 || !row_ptr || !b) return TLS_ERR_ARG;
   if (nnz > 0 && (!col_idx || !val)) return TLS_ERR_ARG;
+  if (nnz >= (int64_t)1 << 31 || m >= (int64_t)1 << 31) return TLS_ERR_ARG;
   if (row_ptr[0] != 0 || row_ptr[m] != nnz) return TLS_ERR_ARG;
-  std::vector<double> dense((size_t)m * (size_t)n, 0.0);
+  if (!finite_all(b, m)) return TLS_ERR_ARG;
+  const int64_t npad = tls::round_up(n, tls::kPad);
+  // validate, and build the column (CSC) index: a transpose of the sparsity structure, entries
+  // of each column in increasing row order
+  std::vector<int> rp32((size_t)m + 1), cp32((size_t)npad + 1, 0);
   for (int64_t i = 0; i < m; ++i) {
     if (row_ptr[i + 1] < row_ptr[i]) return TLS_ERR_ARG;
+    rp32[(size_t)i] = (int)row_ptr[i];
     int64_t prev = -1;
     for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
       const int64_t c = col_idx[e];
       if (c < 0 || c >= n || c <= prev || !std::isfinite(val[e])) return TLS_ERR_ARG;
       prev = c;
-      dense[(size_t)i * (size_t)n + (size_t)c] = val[e];
+      cp32[(size_t)c + 1] += 1;
     }
   }
-  tls_status s = tls_create_dense(out, m, n, dense.data(), n, b, 0, stream);
-  if (s == TLS_OK) (*out)->nnz = nnz;
-  return s;
+  rp32[(size_t)m] = (int)nnz;
+  for (int64_t j = 0; j < npad; ++j) cp32[(size_t)j + 1] += cp32[(size_t)j];
+  std::vector<int> ri32((size_t)nnz), fill(cp32.begin(), cp32.end() - 1);
+  std::vector<double> cv((size_t)nnz);
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int pos = fill[(size_t)col_idx[e]]++;
+      ri32[(size_t)pos] = (int)i;
+      cv[(size_t)pos] = val[e];
+    }
+  tls_ctx* ctx = new tls_ctx();
+  tls_options o;
+  tls_default_options(&o);
+  ctx->opt = o;
+  tls_status st = ctx_common_init(ctx, m, n, stream);
+  if (st != TLS_OK) { destroy_ctx(ctx); return st; }
+  ctx->sparse = true;
+  ctx->nnz = nnz;
+  const int64_t nz = std::max<int64_t>(nnz, 1);
+  ctx->rp = alloc_t<int>(ctx, m + 1);
+  ctx->ci = alloc_t<int>(ctx, nz);
+  ctx->v64 = alloc_t<double>(ctx, nz);
+  ctx->v32 = alloc_t<float>(ctx, nz);
+  ctx->cp = alloc_t<int>(ctx, npad + 1);
+  ctx->ri = alloc_t<int>(ctx, nz);
+  ctx->cv64 = alloc_t<double>(ctx, nz);
+  ctx->cv32 = alloc_t<float>(ctx, nz);
+  ctx->rbuf = alloc_t<double>(ctx, m);
+  if (!ctx->rp || !ctx->ci || !ctx->v64 || !ctx->v32 || !ctx->cp || !ctx->ri || !ctx->cv64 ||
+      !ctx->cv32 || !ctx->rbuf) {
+    destroy_ctx(ctx);
+    return TLS_ERR_OOM;
+  }
+  cudaStream_t sm = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(ctx->rp, rp32.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, sm);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(ctx->ci, col_idx, sizeof(int) * nnz, cudaMemcpyHostToDevice, sm);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(ctx->v64, val, sizeof(double) * nnz, cudaMemcpyHostToDevice, sm);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->cp, cp32.data(), sizeof(int) * (npad + 1), cudaMemcpyHostToDevice, sm);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(ctx->ri, ri32.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, sm);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(ctx->cv64, cv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, sm);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->b, b, sizeof(double) * m, cudaMemcpyHostToDevice, sm);
+  if (e == cudaSuccess) {
+    tls::sparse_to_f32(ctx->v64, ctx->v32, nnz, sm);
+    tls::sparse_to_f32(ctx->cv64, ctx->cv32, nnz, sm);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+  if (e != cudaSuccess) {
+    tls_status s2 = cuda_status(ctx, e, "upload");
+    destroy_ctx(ctx);
+    return s2;
+  }
+  *out = ctx;
+  return TLS_OK;
 }
 
 tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
@@ -989,6 +1191,15 @@ tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* 
 }
 
 uint64_t tls_kernel_launches(void) { return tls::g_launches.load(); }
+
+tls_status tls_export_working_copy(tls_ctx* ctx, float* A32_host) {
+  if (!ctx || !A32_host) return TLS_ERR_ARG;
+  if (!ctx->factored || !ctx->A32 || ctx->sparse) return TLS_ERR_STATE;
+  TLS_CK(cudaMemcpy2DAsync(A32_host, sizeof(float) * ctx->n, ctx->A32, sizeof(float) * ctx->npad,
+                           sizeof(float) * ctx->n, ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+  TLS_CK(cudaStreamSynchronize(ctx->stream));
+  return TLS_OK;
+}
 
 tls_status tls_residual(tls_ctx* ctx, const double* x_host, double* f_host, double* scal_host) {
   if (!ctx || !x_host) return TLS_ERR_ARG;

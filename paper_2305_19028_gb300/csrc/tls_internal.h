@@ -67,8 +67,8 @@ void launch_colnorm(const double* A, int64_t lda, int64_t m, int64_t n, int64_t 
 // AsT[j][i] = fl_prec(A[i][j] / d[j]) (transposed, n x mpad, zero padded). A is FP32 (A32)
 // or FP64 (A64) row-major; prec selects the output element type.
 void launch_scale_cast_T(const void* A, bool a_is_fp64, int64_t lda, int64_t m, int64_t n,
-                         int64_t npad, int64_t mpad, const double* dinv, void* AsT, Prec prec,
-                         cudaStream_t s);
+                         int64_t npad, int64_t mpad, const double* dinv, const float* dinv32,
+                         void* AsT, Prec prec, cudaStream_t s);
 // H (npad x npad, type T = float for FP16/BF16/FP32 input, double for FP64) = AsT AsT^T,
 // identity on the padded diagonal.
 void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
@@ -109,9 +109,12 @@ struct ApassPlan {
   int vpt;            // vectors per thread
   bool tma;           // rows staged through shared memory by bulk async copies
   size_t smem;        // dynamic shared memory of the staged kernel
+  int threads;        // CTA size of the staged kernel
+  int variant;        // 0: register kernel, 1: staged 256 threads, 2: staged 512 threads
 };
+constexpr int kApassVariants = 3;
 template <typename T>
-ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms);
+ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms, int variant);
 
 // Fused pass over dense A: for every row i, c_r = (resid ? b_i - A_i.v_r : A_i.v_r);
 // part[cta][r][:] = sum over the CTA's rows of c_r A_i; sout[r][0] = sum c_r^2,
@@ -136,16 +139,16 @@ void launch_gemv_wt(const T* WT, int64_t npad, const T* y, T* s, const T* p, T* 
 // p_j = s + beta p_prev (written to p_out), q = D^{-1} W p_j, partial ||q||^2 (and ||p||^2).
 template <typename T>
 void launch_gemv_w(const T* W, int64_t npad, const T* s, const T* p_prev, T* p_out,
-                   const double* dinv, T* q, double* part, PcgScalars* sc, int nr,
+                   const T* dinv, T* q, double* part, PcgScalars* sc, int nr,
                    cudaStream_t s_);
 // Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).
 template <typename T>
 void launch_pcg_reduce(const T* part, int P, int64_t npad, const T* q, T* w, T* y,
-                       const double* dinv, PcgScalars* sc, const double* tt, int nr,
+                       const T* dinv, PcgScalars* sc, const double* tt, int nr,
                        cudaStream_t s);
 // Alg. 3 as printed: w += alpha q, y = D^{-1} q (no pass over A).
 template <typename T>
-void launch_pcg_update_R(const T* q, T* w, T* y, const double* dinv, PcgScalars* sc, int nr,
+void launch_pcg_update_R(const T* q, T* w, T* y, const T* dinv, PcgScalars* sc, int nr,
                          int64_t npad, cudaStream_t s);
 // RQI residual reduction (FP64): f = -A^T r - sigma2 x, psi etc.
 void launch_resid_reduce(const double* part, int P, int64_t npad, const double* x, double* f,
@@ -164,5 +167,27 @@ void launch_copy_to_x(double* x, const T* w, RqiScalars* rs, int64_t n, cudaStre
 template <typename T>
 void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaStream_t s);
 void launch_xx(const double* x, RqiScalars* rs, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// Sparse (CSR + CSC) kernels (k_sparse.cu)
+// ---------------------------------------------------------------------------------------
+void sparse_to_f32(const double* v64, float* v32, int64_t nnz, cudaStream_t s);
+void sparse_colnorm(const int* cp, const double* cv64, const float* cv32, int64_t n, int64_t npad,
+                    double* d, double* dinv, float* dinv32, cudaStream_t s);
+template <typename T>
+void sparse_gram(const int* rp, const int* ci, const float* v32, const double* v64,
+                 const int* cp, const int* ri, const float* cv32, const double* cv64,
+                 const float* dinv32, const double* dinv, int64_t n, int64_t npad, int64_t nnz,
+                 Prec prec, T* as, T* cas, T* H, cudaStream_t s);
+void sparse_resid(const int* rp, const int* ci, const double* v64, const int* cp, const int* ri,
+                  const double* cv64, const double* b, const double* x, int64_t m, int64_t n,
+                  int64_t npad, double* r, double* f, double* spart, double* sout,
+                  unsigned int* counter, RqiScalars* rs, double* fpart, cudaStream_t s);
+template <typename T>
+void sparse_pcg_pass(const int* rp, const int* ci, const T* val, const int* cp, const int* ri,
+                     const T* cval, int64_t m, int64_t n, int64_t npad, int nr, const T* q, T* t,
+                     T* w, T* y, const T* dinv, PcgScalars* sc, double* spart, double* sout,
+                     unsigned int* counter, const int* done, cudaStream_t s);
+int sparse_grid_rows(int64_t m);
 
 }  // namespace tls

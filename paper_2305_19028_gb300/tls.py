@@ -27,7 +27,7 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_solve_device", "tls_solve_batched", "tls_destroy", "tls_status_str",
            "tls_last_error", "tls_shape", "tls_set_allocator", "tls_export_factor",
            "tls_residual", "tls_pcgtls", "tls_precond", "tls_profile_enable", "tls_profile_get",
-           "tls_kernel_launches", "tls_residual_noalloc"]
+           "tls_kernel_launches", "tls_residual_noalloc", "tls_export_working_copy"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
@@ -45,10 +45,12 @@ class tls_info(C.Structure):
                 ("cg_iters", C.c_int), ("shifts", C.c_int), ("not_spd", C.c_int),
                 ("u_f_used", C.c_int), ("psi_final", C.c_double), ("sigma2", C.c_double),
                 ("shift", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
-                ("fail_pivot", C.c_int), ("n_psi", C.c_int), ("psi_hist", C.c_double * 24)]
+                ("fail_pivot", C.c_int), ("pass_variant", C.c_int * 2), ("n_psi", C.c_int),
+                ("psi_hist", C.c_double * 24)]
 
     def as_dict(self) -> dict:
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "psi_hist"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("psi_hist", "pass_variant")}
+        d["pass_variant"] = [self.pass_variant[0], self.pass_variant[1]]
         d["psi_hist"] = [self.psi_hist[i] for i in range(min(self.n_psi, 24))]
         return d
 
@@ -101,6 +103,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_profile_get": (C.c_int, [v, C.c_int, C.POINTER(i64), _dp]),
         "tls_kernel_launches": (C.c_uint64, []),
         "tls_residual_noalloc": (C.c_int, [i64, i64, v, i64, v, v, v, v, v]),
+        "tls_export_working_copy": (C.c_int, [v, C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -231,6 +234,14 @@ def tls_export_factor(ctx):
     H = np.zeros((n, n))
     _check(load().tls_export_factor(ctx, _ptr(R), _ptr(d), _ptr(H)), ctx)
     return R, d, H
+
+
+def tls_export_working_copy(ctx):
+    """The FP32 working copy of A (m x n float32)."""
+    m, n, _ = tls_shape(ctx)
+    out = np.zeros((m, n), dtype=np.float32)
+    _check(load().tls_export_working_copy(ctx, out.ctypes.data_as(C.POINTER(C.c_float))), ctx)
+    return out
 
 
 def tls_residual(ctx, x):

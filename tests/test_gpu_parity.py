@@ -67,16 +67,18 @@ def test_residual_block_matches_oracle(m, n):
 # factor: column scaling, Gram of the u_f-rounded scaled matrix, Cholesky, R_H in u_f (Sec. 3.1)
 # ------------------------------------------------------------------------------------------
 def _rounded_scaled(A, d, u_f):
-    As = A.astype(np.float32).astype(np.float64) / d       # FP32 copy scaled in FP64
+    """A_s as the device forms it: FP64 path A / d; FP32 path fl32(fl32(A) * fl32(1/d)) rounded
+    (to nearest even) to u_f."""
+    if u_f == "fp64":
+        return A / d
+    As = A.astype(np.float32) * (1.0 / d).astype(np.float32)     # FP32 product, RN
     if u_f == "fp16":
         return As.astype(np.float16).astype(np.float64)
     if u_f == "bf16":
-        # round-to-nearest-even to 8 significant bits, straight from FP64 (as the device does)
-        mant, ex = np.frexp(As)
+        # round-to-nearest-even to 8 significant bits
+        mant, ex = np.frexp(As.astype(np.float64))
         return np.ldexp(np.rint(mant * 256.0) / 256.0, ex)
-    if u_f == "fp32":
-        return As.astype(np.float32).astype(np.float64)
-    return A / d
+    return As.astype(np.float64)
 
 
 @pytest.mark.parametrize("u_f,u", [("fp16", "fp32"), ("bf16", "fp32"), ("fp32", "fp32"),
@@ -100,6 +102,19 @@ def test_factor_matches_definitions(u_f, u, m, n):
     ufac = {"fp16": U16, "bf16": UBF, "fp32": U32, "fp64": U64}[u_f]
     berr = np.linalg.norm(R.T @ R - H) / np.linalg.norm(H)
     assert berr <= 4 * ufac * np.sqrt(n) + (n * U32 if u_f != "fp64" else 0)
+
+
+def test_working_copy_is_fp32_round_to_nearest():
+    # the FP32 copy of A is formed with integer instructions; it must equal IEEE RN exactly,
+    # including signed zeros, subnormal FP32 results and ties
+    p = synth.dense_problem(300, 70, d_lo=1e-2, noise=1e-3, seed=4)
+    A = p.A.copy()
+    A[0, :8] = [0.0, -0.0, 1e-40, -3e-39, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 2.0 ** -149,
+                -(1.0 + 2.0 ** -23 + 2.0 ** -24)]
+    with Ctx(A, p.b, u_f="fp16", u="fp32") as ctx:
+        A32 = tls.tls_export_working_copy(ctx)
+    ref = A.astype(np.float32)
+    assert np.array_equal(A32.view(np.uint32), ref.view(np.uint32))
 
 
 # ------------------------------------------------------------------------------------------
