@@ -79,6 +79,10 @@ typedef struct {
   int shift_first;     /* 1 (default): FP16/BF16 factors start from H + 2 u_f I, the diagonal  */
                        /* perturbation of low-precision Cholesky; 0: start unshifted and shift */
                        /* only after a breakdown                                              */
+  int fallback;        /* 1 (default): when the RQI loop ends on max_rqi (not converged), refactor */
+                       /* one precision up (FP16/BF16 -> FP32 -> FP64) and solve again, at most  */
+                       /* twice -- the precision fallback for a factor that violates the         */
+                       /* stability constraints of Sec. 3.1; 0: return the max_rqi result       */
 } tls_options;
 
 typedef struct {
@@ -99,6 +103,8 @@ typedef struct {
                          /* 0 register kernel, 1 staged 256 threads, 2 staged 512 threads    */
   int n_psi;             /* entries of psi_hist filled                                       */
   double psi_hist[24];   /* psi_k of the RQI loop, k = 1, 2, ... (first 24)                  */
+  int fallbacks;         /* precision fallbacks taken (tls_options.fallback); the other       */
+                         /* fields describe the final factor and solve                        */
 } tls_info;
 
 typedef struct tls_ctx tls_ctx;
@@ -163,13 +169,31 @@ tls_status tls_solve_device(tls_ctx* ctx, double tol, int max_rqi, double* x_dev
                             double* sigma, tls_info* info);
 
 /*
- * tls_solve_batched -- solve `count` independent, already factored contexts; per_problem[i]
- * receives each status, x[i] (host, n_i FP64) and sigma[i] the results, infos may be NULL.
- * Returns the first non-OK status in index order, or TLS_OK.
+ * tls_factor_batched / tls_solve_batched -- `count` independent problems (contexts of any sizes,
+ * each created with its own stream, i.e. stream NULL at creation, for the work to overlap).
+ * Up to 16 host worker threads drive the contexts; the kernels of different problems run
+ * concurrently on the GPU. per_problem[i] receives each status (may be NULL); x[i] (host, n_i
+ * FP64), sigma[i] and infos[i] (may be NULL) the results. Returns the first non-OK status in
+ * index order, or TLS_OK. Contexts must be distinct.
  */
+tls_status tls_factor_batched(int count, tls_ctx* const* ctxs, tls_prec u_f,
+                              const tls_options* opt, tls_status* per_problem);
 tls_status tls_solve_batched(int count, tls_ctx* const* ctxs, double tol, int max_rqi,
                              double* const* x, double* sigma, tls_info* infos,
                              tls_status* per_problem);
+
+/*
+ * tls_condition -- estimates behind the two constraints on the factor precision (Sec. 3.1):
+ * constraint 1, u_q <~ kappa(A)^{-1} (Eq. (5)), and constraint 2,
+ * u_q <~ kappa_F(A)^{-1} (1 - sigma_{n+1}^2 / sigma'_n^2) (Eq. (9)).
+ * Power iterations (iters steps each) give sigma'_1 (on A^T A through the Gram matrix) and
+ * sigma'_n (on (R^T R)^{-1} through the factor's triangular products, so the estimate is that
+ * of the computed factor, shift included); ||A^+||_F is taken as ||R^{-1}||_F.
+ * out (host, 9 values): sigma'_1, sigma'_n, kappa(A), ||A||_F, ||A^+||_F, kappa_F(A),
+ * sigma_{n+1} (of the last tls_solve; NaN before one), constraint 1, constraint 2.
+ * Requires a successful tls_factor (TLS_ERR_STATE otherwise).
+ */
+tls_status tls_condition(tls_ctx* ctx, int iters, double* out);
 
 void tls_destroy(tls_ctx* ctx);
 const char* tls_status_str(tls_status s);

@@ -502,12 +502,12 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
                      cudaStream_t s) {
   if (shift != 0.0) { add_shift_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(M, n, npad, shift); count_launch(); }
   const size_t dsmem = 2 * sizeof(T) * NB * (NB + 1);
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [dsmem] {   // thread-safe one-time initialisation
     cudaFuncSetAttribute(potrf_inv_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)dsmem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   for (int64_t kb = 0; kb < npad; kb += NB) {
     potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb, info, (int)prec);
     count_launch();

@@ -18,6 +18,7 @@
 #include <cuda.h>
 
 #include <cstdio>
+#include <mutex>
 
 namespace tls {
 
@@ -268,9 +269,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 EncodeTiledFn get_encoder() {
   static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
@@ -279,11 +279,9 @@ EncodeTiledFn get_encoder() {
       fn = reinterpret_cast<EncodeTiledFn>(p);
     else
       (void)cudaGetLastError();
-  }
+  });
   return fn;
 }
-
-int* g_err = nullptr;   // device error word of the tensor-core kernels (one per process)
 
 }  // namespace
 
@@ -295,24 +293,20 @@ bool gram_tc_available() {
   return major == 10 && minor == 3 && get_encoder() != nullptr;
 }
 
-int gram_tc_error(cudaStream_t s) {
-  if (!g_err) return 0;
+int gram_tc_error(int* err, cudaStream_t s) {
   int h = 0;
-  cudaMemcpyAsync(&h, g_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
-  if (h) cudaMemsetAsync(g_err, 0, sizeof(int), s);
+  if (h) cudaMemsetAsync(err, 0, sizeof(int), s);
   return h;
 }
 
 bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad, float* H,
-                    cudaStream_t s) {
+                    int* err, cudaStream_t s) {
   if (prec != Prec::FP16 && prec != Prec::BF16) return false;
   if (!gram_tc_available()) return false;
-  if ((reinterpret_cast<uintptr_t>(AsT) & 15) != 0 || (mpad % TBK) != 0) return false;
-  if (!g_err) {
-    if (cudaMalloc(&g_err, sizeof(int)) != cudaSuccess) { (void)cudaGetLastError(); g_err = nullptr; return false; }
-    cudaMemset(g_err, 0, sizeof(int));
-  }
+  if ((reinterpret_cast<uintptr_t>(AsT) & 15) != 0 || (mpad % TBK) != 0 || err == nullptr)
+    return false;
   CUtensorMap map;
   const cuuint64_t gdim[2] = {(cuuint64_t)mpad, (cuuint64_t)npad};
   const cuuint64_t gstride[1] = {(cuuint64_t)mpad * 2};
@@ -329,14 +323,14 @@ bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t
   const int nt = (int)((npad + TBM - 1) / TBM);
   const int tiles = nt * (nt + 1) / 2;
   const size_t smem = 2 * STAGES * STAGE_BYTES + 1024;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [smem] {   // thread-safe one-time initialisation
     cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const uint32_t idesc = idesc_f16(prec == Prec::FP16 ? 0u : 1u);
   gram_tc_kernel<<<tiles, THREADS, smem, s>>>(map, nt, (int)(mpad / TBK), (int)npad, H, idesc,
-                                              g_err);
+                                              err);
   count_launch();
   launch_set_identity_pad(H, false, n, npad, s);
   return cudaGetLastError() == cudaSuccess;

@@ -926,12 +926,12 @@ void apass_tma_dispatch_th(int vpt, dim3 grid, size_t smem, const T* A, int64_t 
   switch (vpt) {
 #define TLS_AT(V)                                                                               \
   case V: {                                                                                     \
-    static bool attr = false;                                                                   \
-    if (!attr) {                                                                                \
+    static const bool attr = [] {                                                               \
       cudaFuncSetAttribute(apass_tma_kernel<T, NR, RESID, V, TH>,                              \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);            \
-      attr = true;                                                                              \
-    }                                                                                           \
+      return true;                                                                              \
+    }();                                                                                        \
+    (void)attr;                                                                                 \
     apass_tma_kernel<T, NR, RESID, V, TH><<<grid, TH, smem, s>>>(A, m, npad, v, ldv, b, part,   \
                                                                spart, sout, counter, done,    \
                                                                err);                          \

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <thread>
+#include <atomic>
 #include <tuple>
 #include <cstddef>
 #include <cstdio>
@@ -77,6 +79,7 @@ struct tls_ctx {
   int shifts = 0;
   double shift = 0.0;
   int64_t fail_pivot = -1;   // pivot index of the last breakdown (-1: none)
+  double last_sigma2 = -1.0; // sigma^2 of the last successful tls_solve (-1: none yet)
   double t_factor_ms = 0.0;
 
   // solve workspace
@@ -504,6 +507,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     return TLS_ERR_TIMEOUT;
   }
   *sigma_out = std::sqrt(std::max(best_s2, 0.0));
+  ctx->last_sigma2 = best_s2;
   if (info) {
     info->stop_reason = stop;
     info->rqi_steps = k;
@@ -724,9 +728,10 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
       Prof pr(ctx, TLS_PROF_GRAM);
       bool tc = false;
       if ((pf == Prec::FP16 || pf == Prec::BF16) && !ctx->opt.gram_simt)
-        tc = tls::launch_gram_tc(AsT, pf, n, npad, mpad, static_cast<float*>(ctx->H), st);
+        tc = tls::launch_gram_tc(AsT, pf, n, npad, mpad, static_cast<float*>(ctx->H), ctx->derr,
+                                 st);
       if (tc) {
-        const int terr = tls::gram_tc_error(st);   // synchronises the stream
+        const int terr = tls::gram_tc_error(ctx->derr, st);   // synchronises the stream
         if (terr != 0) {
           // a bounded wait in the tensor-core kernel gave up: recompute on CUDA cores
           set_err(ctx, "tensor-core Gram wait expired (code " + std::to_string(terr) +
@@ -898,9 +903,92 @@ static tls_status precond_host(tls_ctx* ctx, const double* y, double* s0, double
   return TLS_OK;
 }
 
+template <typename TH, typename TU>
+static tls_status condition_impl(tls_ctx* ctx, int iters, double* out) {
+  cudaStream_t st = ctx->stream;
+  const int64_t n = ctx->n, npad = ctx->npad;
+  void* scratch = dev_alloc(ctx, sizeof(double) * (size_t)(4 * npad + 2 + 4096));
+  if (!scratch) return TLS_ERR_OOM;
+  TH* xh = static_cast<TH*>(scratch);
+  TH* yh = xh + npad;
+  TU* xu = reinterpret_cast<TU*>(static_cast<double*>(scratch) + 2 * npad);
+  double* lam = static_cast<double*>(scratch) + 4 * npad;
+  double* part = lam + 2;
+  const TH* dinvH = reinterpret_cast<const TH*>(sizeof(TH) == 4 ? (const void*)ctx->dinv32
+                                                                : (const void*)ctx->dinv);
+  // sigma'_1^2 = lambda_max(D H D)
+  tls::launch_power_init<TH>(xh, n, npad, st);
+  for (int it = 0; it < iters; ++it) {
+    tls::launch_dhd<TH>(static_cast<const TH*>(ctx->H), npad, dinvH, xh, yh, st);
+    tls::launch_power_finish<TH>(xh, yh, n, lam, st);
+  }
+  // 1 / sigma'_n^2 = lambda_max((R^T R)^{-1}) with the preconditioner products
+  UVecs<TU> v = uvecs<TU>(ctx);
+  tls::launch_power_init<TU>(xu, n, npad, st);
+  for (int it = 0; it < iters; ++it) {
+    tls::launch_vec_to_double<TU>(xu, ctx->f, n, npad, st);
+    tls_status s2 = precond_apply<TU>(ctx, ctx->f);
+    if (s2 != TLS_OK) return s2;
+    tls::launch_power_finish<TU>(xu, v.q, n, lam + 1, st);
+  }
+  const int g = tls::launch_frob_dw<TU>(static_cast<const TU*>(ctx->W), n, npad, dinv_t<TU>(ctx),
+                                        part, st);
+  TLS_CK_LAUNCH("condition estimate");
+  std::vector<double> h(2 + (size_t)g);
+  TLS_CK(cudaMemcpyAsync(h.data(), lam, sizeof(double) * (2 + g), cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaStreamSynchronize(st));
+  dev_free(ctx, scratch);
+  double frob = 0.0;
+  for (int i = 0; i < g; ++i) frob += h[2 + i];
+  const double s1 = std::sqrt(std::max(h[0], 0.0));
+  const double sn = (h[1] > 0.0) ? 1.0 / std::sqrt(h[1]) : 0.0;
+  const double fa = std::sqrt(ctx->norm2_A), fi = std::sqrt(frob);
+  const double kappa = (sn > 0.0) ? s1 / sn : INFINITY;
+  const double kf = fa * fi;
+  const double sig = ctx->last_sigma2 >= 0.0 ? std::sqrt(ctx->last_sigma2) : NAN;
+  out[0] = s1;
+  out[1] = sn;
+  out[2] = kappa;
+  out[3] = fa;
+  out[4] = fi;
+  out[5] = kf;
+  out[6] = sig;
+  out[7] = 1.0 / kappa;
+  out[8] = (1.0 - (sig * sig) / (sn * sn)) / kf;
+  return TLS_OK;
+}
+
 }  // namespace
 
 // =========================================================================================
+namespace {
+
+// Runs fn(i) for i < count on up to `workers` host threads (each context has its own CUDA
+// stream, so the kernels of different problems overlap on the GPU).
+template <typename F>
+void run_workers(int count, int workers, F fn) {
+  workers = std::max(1, std::min(workers, count));
+  std::atomic<int> next{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto body = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) fn(i);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(body);
+  body();
+  for (auto& t : pool) t.join();
+}
+
+int batch_workers(int count) {
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int cap = (int)std::min<unsigned>(16u, std::max<unsigned>(1u, hc ? hc : 4u));
+  return std::min(cap, std::max(count, 1));
+}
+
+}  // namespace
+
 extern "C" {
 
 void tls_default_options(tls_options* opt) {
@@ -916,6 +1004,7 @@ void tls_default_options(tls_options* opt) {
   opt->gram_simt = 0;
   opt->shift_first = 1;
   opt->psi_accept = 1e-12;
+  opt->fallback = 1;
 }
 
 const char* tls_status_str(tls_status s) {
@@ -1088,6 +1177,15 @@ tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
   return factor_impl(ctx, u_f);
 }
 
+static tls_status solve_once(tls_ctx* ctx, double tol, int max_rqi, double* sigma,
+                             tls_info* info) {
+  if (ctx->u == Prec::FP64) return solve_impl<double>(ctx, tol, max_rqi, info, sigma);
+  return solve_impl<float>(ctx, tol, max_rqi, info, sigma);
+}
+
+// Solve; when the RQI loop ends on max_rqi without converging and the factor precision is
+// below FP64, refactor one precision up and solve again (the precision fallback for a factor
+// that violates the stability constraints of Sec. 3.1).
 static tls_status solve_common(tls_ctx* ctx, double tol, int max_rqi, double* sigma,
                                tls_info* info) {
   if (!ctx || !sigma || max_rqi < 0 || !(tol >= 0.0)) return TLS_ERR_ARG;
@@ -1095,8 +1193,21 @@ static tls_status solve_common(tls_ctx* ctx, double tol, int max_rqi, double* si
     set_err(ctx, "tls_solve called before a successful tls_factor");
     return TLS_ERR_STATE;
   }
-  if (ctx->u == Prec::FP64) return solve_impl<double>(ctx, tol, max_rqi, info, sigma);
-  return solve_impl<float>(ctx, tol, max_rqi, info, sigma);
+  tls_info loc{};
+  tls_status s = solve_once(ctx, tol, max_rqi, sigma, &loc);
+  int fb = 0;
+  while (s == TLS_OK && ctx->opt.fallback && loc.stop_reason == TLS_STOP_MAX_RQI &&
+         ctx->uf_used != TLS_FP64 && fb < 2) {
+    const tls_prec next = (ctx->uf_used == TLS_FP32) ? TLS_FP64 : TLS_FP32;
+    const tls_options o = ctx->opt;
+    s = tls_factor(ctx, next, &o);
+    if (s != TLS_OK) break;
+    ++fb;
+    s = solve_once(ctx, tol, max_rqi, sigma, &loc);
+  }
+  loc.fallbacks = fb;
+  if (info) *info = loc;
+  return s;
 }
 
 tls_status tls_solve(tls_ctx* ctx, double tol, int max_rqi, double* x, double* sigma,
@@ -1121,15 +1232,31 @@ tls_status tls_solve_device(tls_ctx* ctx, double tol, int max_rqi, double* x_dev
   return cuda_status(ctx, e, "copy x");
 }
 
+tls_status tls_factor_batched(int count, tls_ctx* const* ctxs, tls_prec u_f,
+                              const tls_options* opt, tls_status* per_problem) {
+  if (count < 0 || (count > 0 && !ctxs)) return TLS_ERR_ARG;
+  std::vector<tls_status> st((size_t)std::max(count, 1), TLS_OK);
+  run_workers(count, batch_workers(count), [&](int i) { st[(size_t)i] = tls_factor(ctxs[i], u_f, opt); });
+  tls_status first = TLS_OK;
+  for (int i = 0; i < count; ++i) {
+    if (per_problem) per_problem[i] = st[(size_t)i];
+    if (st[(size_t)i] != TLS_OK && first == TLS_OK) first = st[(size_t)i];
+  }
+  return first;
+}
+
 tls_status tls_solve_batched(int count, tls_ctx* const* ctxs, double tol, int max_rqi,
                              double* const* x, double* sigma, tls_info* infos,
                              tls_status* per_problem) {
   if (count < 0 || (count > 0 && (!ctxs || !x || !sigma))) return TLS_ERR_ARG;
+  std::vector<tls_status> st((size_t)std::max(count, 1), TLS_OK);
+  run_workers(count, batch_workers(count), [&](int i) {
+    st[(size_t)i] = tls_solve(ctxs[i], tol, max_rqi, x[i], sigma + i, infos ? infos + i : nullptr);
+  });
   tls_status first = TLS_OK;
   for (int i = 0; i < count; ++i) {
-    tls_status s = tls_solve(ctxs[i], tol, max_rqi, x[i], sigma + i, infos ? infos + i : nullptr);
-    if (per_problem) per_problem[i] = s;
-    if (s != TLS_OK && first == TLS_OK) first = s;
+    if (per_problem) per_problem[i] = st[(size_t)i];
+    if (st[(size_t)i] != TLS_OK && first == TLS_OK) first = st[(size_t)i];
   }
   return first;
 }
@@ -1191,6 +1318,17 @@ tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* 
 }
 
 uint64_t tls_kernel_launches(void) { return tls::g_launches.load(); }
+
+tls_status tls_condition(tls_ctx* ctx, int iters, double* out) {
+  if (!ctx || !out || iters < 1) return TLS_ERR_ARG;
+  if (!ctx->factored) return TLS_ERR_STATE;
+  if (ctx->H_fp64) {
+    if (ctx->u == Prec::FP64) return condition_impl<double, double>(ctx, iters, out);
+    return condition_impl<double, float>(ctx, iters, out);
+  }
+  if (ctx->u == Prec::FP64) return condition_impl<float, double>(ctx, iters, out);
+  return condition_impl<float, float>(ctx, iters, out);
+}
 
 tls_status tls_export_working_copy(tls_ctx* ctx, float* A32_host) {
   if (!ctx || !A32_host) return TLS_ERR_ARG;

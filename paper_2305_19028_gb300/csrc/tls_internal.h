@@ -76,11 +76,11 @@ void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64
 // tcgen05 (UMMA) Gram for FP16/BF16 input into FP32 H. Returns false if the shape is not
 // supported (falls back to nothing: the caller decides).
 bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
-                    float* H, cudaStream_t s);
+                    float* H, int* err, cudaStream_t s);
 // 1 if the tensor-core path can run on the current device (sm_103 and a tensor-map encoder).
 bool gram_tc_available();
-// Error code recorded by a bounded wait of the tensor-core kernels (0: none); resets it.
-int gram_tc_error(cudaStream_t s);
+// Error code recorded in *err by a bounded wait of the tensor-core kernel (0: none); resets it.
+int gram_tc_error(int* err, cudaStream_t s);
 // Blocked upper Cholesky in place on M (npad x npad, T), with shift added to the first n
 // diagonal entries first; the rows of R are rounded to prec block by block and the inverses
 // of the 64 x 64 diagonal blocks are written to Wd (npad x npad, other entries untouched);
@@ -167,6 +167,21 @@ void launch_copy_to_x(double* x, const T* w, RqiScalars* rs, int64_t n, cudaStre
 template <typename T>
 void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaStream_t s);
 void launch_xx(const double* x, RqiScalars* rs, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// Condition estimates (k_cond.cu)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+void launch_dhd(const T* H, int64_t npad, const T* dinv, const T* x, T* y, cudaStream_t s);
+template <typename T>
+void launch_power_finish(T* x, const T* y, int64_t n, double* lam, cudaStream_t s);
+template <typename T>
+void launch_power_init(T* x, int64_t n, int64_t npad, cudaStream_t s);
+template <typename T>
+int launch_frob_dw(const T* W, int64_t n, int64_t npad, const T* dinv, double* part,
+                   cudaStream_t s);
+template <typename T>
+void launch_vec_to_double(const T* x, double* y, int64_t n, int64_t npad, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------
 // Sparse (CSR + CSC) kernels (k_sparse.cu)

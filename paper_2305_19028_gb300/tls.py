@@ -27,7 +27,8 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_solve_device", "tls_solve_batched", "tls_destroy", "tls_status_str",
            "tls_last_error", "tls_shape", "tls_set_allocator", "tls_export_factor",
            "tls_residual", "tls_pcgtls", "tls_precond", "tls_profile_enable", "tls_profile_get",
-           "tls_kernel_launches", "tls_residual_noalloc", "tls_export_working_copy"]
+           "tls_kernel_launches", "tls_residual_noalloc", "tls_export_working_copy",
+           "tls_condition", "tls_factor_batched"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
@@ -37,7 +38,7 @@ class tls_options(C.Structure):
     _fields_ = [("u", C.c_int), ("mode_A", C.c_int), ("cg_fixed", C.c_int),
                 ("cg_tol", C.c_double), ("cg_max", C.c_int), ("psi_rule_ge", C.c_int),
                 ("ls_iters", C.c_int), ("max_shifts", C.c_int), ("gram_simt", C.c_int),
-                ("psi_accept", C.c_double), ("shift_first", C.c_int)]
+                ("psi_accept", C.c_double), ("shift_first", C.c_int), ("fallback", C.c_int)]
 
 
 class tls_info(C.Structure):
@@ -46,7 +47,7 @@ class tls_info(C.Structure):
                 ("u_f_used", C.c_int), ("psi_final", C.c_double), ("sigma2", C.c_double),
                 ("shift", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("fail_pivot", C.c_int), ("pass_variant", C.c_int * 2), ("n_psi", C.c_int),
-                ("psi_hist", C.c_double * 24)]
+                ("psi_hist", C.c_double * 24), ("fallbacks", C.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("psi_hist", "pass_variant")}
@@ -104,6 +105,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_kernel_launches": (C.c_uint64, []),
         "tls_residual_noalloc": (C.c_int, [i64, i64, v, i64, v, v, v, v, v]),
         "tls_export_working_copy": (C.c_int, [v, C.POINTER(C.c_float)]),
+        "tls_condition": (C.c_int, [v, C.c_int, _dp]),
+        "tls_factor_batched": (C.c_int, [C.c_int, vp, C.c_int, C.POINTER(tls_options), _ip]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -213,6 +216,16 @@ def tls_solve_batched(ctxs, tol: float = 0.0, max_rqi: int = 10):
     return xs, sig, [i.as_dict() for i in infos], list(per), st
 
 
+def tls_factor_batched(ctxs, u_f="fp16", opt: tls_options | None = None):
+    """Factor several contexts concurrently; returns the per-problem status list."""
+    k = len(ctxs)
+    arr = (C.c_void_p * k)(*[c.value for c in ctxs])
+    per = (C.c_int * k)()
+    uf = PREC[u_f] if isinstance(u_f, str) else int(u_f)
+    load().tls_factor_batched(k, arr, uf, C.byref(opt) if opt is not None else None, per)
+    return list(per)
+
+
 def tls_destroy(ctx):
     if ctx:
         load().tls_destroy(ctx)
@@ -234,6 +247,17 @@ def tls_export_factor(ctx):
     H = np.zeros((n, n))
     _check(load().tls_export_factor(ctx, _ptr(R), _ptr(d), _ptr(H)), ctx)
     return R, d, H
+
+
+COND_KEYS = ["sigma1", "sigma_n", "kappa", "norm_F", "pinv_norm_F", "kappa_F", "sigma_n1",
+             "constr1", "constr2"]
+
+
+def tls_condition(ctx, iters: int = 30) -> dict:
+    """Estimates of Sec. 3.1: see include/tls.h."""
+    out = np.zeros(9)
+    _check(load().tls_condition(ctx, iters, _ptr(out)), ctx)
+    return dict(zip(COND_KEYS, out.tolist()))
 
 
 def tls_export_working_copy(ctx):

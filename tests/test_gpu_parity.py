@@ -222,7 +222,7 @@ def test_zero_column_breaks_down_then_shifts(shift_first):
     A[:, 7] = 0.0
     ctx = tls.tls_create_dense(A, p.b)
     try:
-        tls.tls_factor(ctx, "fp16", tls.tls_default_options(shift_first=shift_first))
+        tls.tls_factor(ctx, "fp16", tls.tls_default_options(shift_first=shift_first, fallback=0))
         x, s, info = tls.tls_solve(ctx, tol=0.0, max_rqi=3)
         assert info["shift"] > 0
         if shift_first:
@@ -250,3 +250,46 @@ def test_tensor_core_gram_matches_cuda_core_gram(u_f, m, n):
     assert np.all(np.abs(H_tc - H_simt) <= 2 * bound)
     assert np.all(np.abs(H_tc - As.T @ As) <= bound)
     assert np.allclose(H_tc, H_tc.T, rtol=0, atol=0)
+
+
+# ------------------------------------------------------------------------------------------
+# Sec. 3.1 constraint estimates on the GPU vs the oracle's exact SVD values and the paper's
+# printed bounds (Examples 1, 2, 3, 5)
+# ------------------------------------------------------------------------------------------
+from tests.conftest import read_golden  # noqa: E402
+
+_EXAMPLES_GPU = {
+    "random_100x60": lambda: synth.random_matrix_problem(seed=0),
+    "delta_9x4": lambda: synth.delta_matrix_problem(seed=1),
+    "bjorck_30x15": lambda: synth.bjorck_problem(seed=1),
+    "van_huffel_100": lambda: synth.van_huffel_problem(seed=1),
+}
+
+
+@pytest.mark.parametrize("row", read_golden("paper_constraint_bounds.txt"), ids=lambda r: r[0])
+def test_condition_estimates(row):
+    name, c1_paper, c2_paper = row[0], float(row[1]), float(row[2])
+    p = _EXAMPLES_GPU[name]()
+    with Ctx(p.A, p.b, u_f="fp64", u="fp64") as ctx:
+        tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+        est = tls.tls_condition(ctx, iters=60)
+    c = O.constraints(p.A, p.b)
+    # power iterations approach the extreme singular values from inside: kappa from below
+    assert 0.5 <= est["kappa"] / c["kappa"] <= 1.0 + 1e-6
+    # with an FP64 factor, ||R^{-1}||_F = ||A^+||_F up to rounding
+    assert est["kappa_F"] == pytest.approx(c["kappa_F"], rel=1e-8)
+    assert est["sigma_n1"] == pytest.approx(c["sigma_n1"], rel=1e-8)
+    assert c["constr1"] * (1 - 1e-9) <= est["constr1"] <= 2.0 * c["constr1"]
+    f2 = 25.0 if name == "bjorck_30x15" else 2.5
+    assert c1_paper / 2.5 <= est["constr1"] <= c1_paper * 2.5
+    assert c2_paper / f2 <= est["constr2"] <= c2_paper * f2
+
+
+def test_condition_estimate_generator_problem():
+    # A = Y [diag(D); 0] Z^T: sigma'_1 = 1 and sigma'_n = d_lo exactly
+    p = synth.dense_problem(3000, 200, d_lo=1e-3, noise=1e-4, seed=3)
+    with Ctx(p.A, p.b, u_f="fp64", u="fp64") as ctx:
+        est = tls.tls_condition(ctx, iters=200)
+    assert est["sigma1"] == pytest.approx(1.0, rel=5e-3)
+    assert est["sigma_n"] == pytest.approx(1e-3, rel=5e-3)
+    assert est["norm_F"] == pytest.approx(np.linalg.norm(p.D), rel=1e-12)
