@@ -7,8 +7,13 @@ residuals). A solve counts only if sigma rel err <= 1e-10 and x rel err <= 1e-8 
 FP64 CPU oracle run on the same problem.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload batch [--batch 512]
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+`--workload batch`: one step = factor + solve of a resident packed batch of 512 uneven dense
+problems (n ~ U{32..512}, m = n U{4..20}, D log-spaced in [10^-U(1,4), 1], seeds 1000 + i); a
+solve counts if it matches the FP64 oracle (run on every problem, in a process pool) to the same
+tolerances.
 """
 from __future__ import annotations
 
@@ -363,6 +368,207 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------
+# packed batch workload
+# ------------------------------------------------------------------------------------------
+BATCH_K = 512
+
+
+def _batch_workload(k: int) -> str:
+    return f"batch_{k}_dense_n32-512_m4-20n_uf16_u32_ur64"
+
+
+def _oracle_batch_member(i: int):
+    """Pool worker: rebuild batch member i from its seed and solve it with the FP64 oracle."""
+    from paper_2305_19028_gb300 import synth
+    import oracle.rqi_pcgtls as O
+    p = synth.batch_problem(i)
+    x, s, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=MAX_RQI)
+    return i, x, s
+
+
+def _oracle_pool(ids, procs):
+    """FP64 oracle on every listed batch member, one single-threaded process per core."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                             "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(processes=procs) as pool:
+            res = pool.map(_oracle_batch_member, ids, chunksize=1)
+        dt = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {i: (x, s) for i, x, s in res}, dt
+
+
+def _batch_roofline(prof: dict, peaks: dict, cls: str) -> dict:
+    cnt, ms, elems = prof.get(cls, (0, 0.0, 0))
+    if cnt == 0 or ms <= 0:
+        return {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "measured" if peaks else "fallback"
+    if cls in ("pcg_pass2", "pcg_pass1"):
+        # algorithmic bytes: the FP32 entries of A of the active problems, once per launch
+        byts = 4.0 * elems
+        ach = byts / (ms * 1e-3) / 1e9
+        return {"kernel": f"{cls} (batched fused t = A q, A^T t over all active problems, FP32)",
+                "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "avg_launch_us": ms / cnt * 1e3, "algorithmic_bytes_per_launch": byts / cnt}
+    if cls == "resid_pass":
+        # FP64 FMA-bound: 2 FMA (4 flops) per entry of A; peak 1.25 TFLOP/s FP64 (nominal)
+        flops = 4.0 * elems
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"kernel": "resid_pass (batched FP64 r = b - A x, A^T r)", "bound": "alu",
+                "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                "traffic": None, "peak_source": "nominal FP64 rate (no measured FP64 peak)",
+                "avg_launch_us": ms / cnt * 1e3, "algorithmic_flops_per_launch": flops / cnt,
+                "hbm_gbs": 8.0 * elems / (ms * 1e-3) / 1e9}
+    return {}
+
+
+def run_batch(args, ws, rank, local):
+    import torch
+    from paper_2305_19028_gb300 import synth, tls
+
+    K = args.batch
+    ids = [rank * K + i for i in range(K)]
+    ref, t_or = {}, None
+    procs = max(1, (os.cpu_count() or 1) // ws)
+    if not args.no_cpu:
+        ref, t_or = _oracle_pool(ids, procs)       # before the first CUDA call
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    tls.load()
+    probs = [synth.batch_problem(i) for i in ids]
+    stream = torch.cuda.current_stream()
+    bt = tls.Batch([(p.A, p.b) for p in probs], stream=stream.cuda_stream)
+
+    def count_ok(xs, sig):
+        if not ref:
+            return len(xs)
+        ok = 0
+        for i, x, s in zip(ids, xs, sig):
+            xo, so = ref[i]
+            ok += int(abs(s - so) <= SIGMA_TOL * so and
+                      np.linalg.norm(x - xo) <= X_TOL * np.linalg.norm(xo))
+        return ok
+
+    def step():
+        bt.factor("fp16", u="fp32")
+        return bt.solve(tol=SOLVE_TOL, max_rqi=MAX_RQI)
+
+    for _ in range(args.warmup):
+        step()
+    bt.profile(True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    l0 = tls.tls_kernel_launches()
+    ok = 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            xs, sig, infos, per = step()
+            ok += count_ok(xs, sig)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = tls.tls_kernel_launches() - l0
+    ms = _barrier_max(ev0.elapsed_time(ev1), ws)
+    prof = bt.profile_get()
+    bt.profile(False)
+    clocks = clk.summary()
+    n_fb = sum(i["fallbacks"] for i in infos)
+    uf_hist = np.bincount([i["u_f_used"] for i in infos], minlength=4).tolist()
+
+    e2e = None
+    if not args.no_e2e:
+        pins = [(torch.from_numpy(p.A).pin_memory().numpy(), torch.from_numpy(p.b).pin_memory().numpy())
+                for p in probs]
+        ne = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        okc = 0
+        e0.record(stream)
+        for _ in range(ne):
+            with tls.Batch(pins, stream=stream.cuda_stream) as b2:
+                b2.factor("fp16", u="fp32")
+                x2, s2, _, _ = b2.solve(tol=SOLVE_TOL, max_rqi=MAX_RQI)
+            okc += count_ok(x2, s2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = _barrier_max(e0.elapsed_time(e1), ws)
+        e2e = {"value": ws * okc / (ems * 1e-3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(sum(p.A.nbytes + p.b.nbytes for p in probs)),
+               "d2h_bytes_per_step": int(sum(8 * p.A.shape[1] + 8 for p in probs)),
+               "steps": ne, "ms_per_step": ems / ne}
+
+    plain = None
+    if not args.no_plain:
+        def step64():
+            bt.factor("fp64", u="fp64")
+            return bt.solve(tol=SOLVE_TOL, max_rqi=MAX_RQI)
+        step64()
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        np_steps = max(1, min(args.steps, 2))
+        okp = 0
+        q0.record(stream)
+        for _ in range(np_steps):
+            xp, sp_, ip, _ = step64()
+            okp += count_ok(xp, sp_)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        pms = _barrier_max(q0.elapsed_time(q1), ws)
+        plain = {"value": ws * okp / (pms * 1e-3), "unit": "solves/s", "ms_per_step": pms / np_steps,
+                 "steps": np_steps, "accurate": okp, "of": np_steps * K}
+    bt.close()
+    if rank != 0:
+        return
+    peaks = _peaks()
+    total = {k: v[1] for k, v in prof.items()}
+    dom = max(total, key=total.get)
+    share = {k: round(v / max(1e-9, sum(total.values())), 4) for k, v in total.items()}
+    roof = _batch_roofline(prof, peaks, dom) or _batch_roofline(prof, peaks, "pcg_pass2")
+    cpu = None
+    if t_or is not None:
+        cpu = {"value": K / t_or, "unit": "solves/s", "cores": procs, "kind": "oracle",
+               "sample": f"all {K} problems of the batch, one FP64 oracle solve each "
+                         f"({t_or:.1f} s on {procs} single-threaded processes)"}
+    line = {
+        "metric": METRIC, "value": ws * ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16+f32+f64", "data": "synthetic",
+        "config": {"workload": _batch_workload(K), "problems": K, "u_f": "fp16", "u": "fp32",
+                   "u_r": "fp64", "solve_tol": SOLVE_TOL, "max_rqi": MAX_RQI,
+                   "seeds": f"1000 + rank*{K} + i",
+                   "l2": "inputs larger than L2 (A: %.1f GB FP64 + %.1f GB FP32)" % (
+                       sum(p.A.nbytes for p in probs) / 1e9, sum(p.A.nbytes for p in probs) / 2e9),
+                   "step": "tls_batch_factor + tls_batch_solve on the resident batch"},
+        "accurate_solves": ok, "of": args.steps * K, "fallbacks": n_fb, "u_f_used_hist": uf_hist,
+        "roofline": roof, "inner_loop_roofline": _batch_roofline(prof, peaks, "pcg_pass2"),
+        "resid_roofline": _batch_roofline(prof, peaks, "resid_pass"),
+        "kernel_share": share, "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()},
+        "kernel_launches": {k: v[0] for k, v in prof.items()}, "gpu_launches": int(launches),
+        "cpu_baseline": cpu, "e2e": e2e, "plain_fp64": plain, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,11 +580,15 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--m", type=int, default=None, help="rows (profiling a smaller case)")
     ap.add_argument("--n", type=int, default=None, help="columns (profiling a smaller case)")
+    ap.add_argument("--workload", choices=["dense", "batch"], default="dense")
+    ap.add_argument("--batch", type=int, default=BATCH_K, help="problems in the packed batch")
     args = ap.parse_args()
     _set_size(args.m, args.n)
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batch":
+        run_batch(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

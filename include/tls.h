@@ -183,6 +183,41 @@ tls_status tls_solve_batched(int count, tls_ctx* const* ctxs, double tol, int ma
                              tls_status* per_problem);
 
 /*
+ * Packed batch -- many small dense problems (n <= TLS_BATCH_MAX_N, any m >= n) packed into
+ * shared device arrays and solved together: every phase of RQI-PCGTLS (Alg. 2, with the
+ * PCGTLS solves of Alg. 3 in the precisions of Alg. 4) is one kernel launch for the whole
+ * batch -- passes over A tiled across all problems, one CTA per problem for the n-sized work.
+ * The problems advance in lock step (same RQI step, same PCGTLS step); a problem that stops
+ * is skipped by later launches.
+ *
+ * tls_batch_create_dense -- count >= 1 problems; problem i has A[i] (m[i] x n[i], row-major,
+ *   leading dimension lda[i] >= n[i], FP64) and b[i] (m[i] FP64), host pointers (on_device 0,
+ *   checked for NaN/Inf) or device pointers (on_device 1). The batch copies the data; stream
+ *   as in tls_create_dense. Computes the column norms and the FP32 working copy. Errors:
+ *   TLS_ERR_ARG (sizes, n > TLS_BATCH_MAX_N, m >= 2^31, non-finite data), TLS_ERR_OOM.
+ * tls_batch_factor -- Gram, Cholesky and W = R_H^{-1} of every problem at factor precision
+ *   u_f, with the shift ladder of tls_factor per problem and, for a problem whose every shift
+ *   breaks down, the next precision (FP16/BF16 -> FP32 -> FP64). opt as in tls_factor (NULL:
+ *   defaults); the packed batch requires mode_A = 1 and u = TLS_FP32 or TLS_FP64.
+ *   TLS_ERR_FACTOR_BREAKDOWN if some problem broke down at FP64 as well.
+ * tls_batch_solve -- RQI-PCGTLS for every problem, same stopping rules as tls_solve and the
+ *   same precision fallback (tls_options.fallback) applied per problem. x[i] (host, n[i]
+ *   doubles; a NULL entry skips the copy), sigma[i], infos[i] (NULL: none), per_problem[i]
+ *   (NULL: none). t_factor_ms / t_solve_ms of every info are the batch's times.
+ *   Returns TLS_ERR_STATE before a successful factor, else the first non-OK per-problem status.
+ */
+#define TLS_BATCH_MAX_N 512
+typedef struct tls_batch tls_batch;
+tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, const int64_t* n,
+                                  const double* const* A, const int64_t* lda,
+                                  const double* const* b, int on_device, void* stream);
+tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt);
+tls_status tls_batch_solve(tls_batch* bt, double tol, int max_rqi, double* const* x,
+                           double* sigma, tls_info* infos, tls_status* per_problem);
+void tls_batch_destroy(tls_batch* bt);
+const char* tls_batch_last_error(const tls_batch* bt);
+
+/*
  * tls_condition -- estimates behind the two constraints on the factor precision (Sec. 3.1):
  * constraint 1, u_q <~ kappa(A)^{-1} (Eq. (5)), and constraint 2,
  * u_q <~ kappa_F(A)^{-1} (1 - sigma_{n+1}^2 / sigma'_n^2) (Eq. (9)).

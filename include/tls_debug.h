@@ -23,6 +23,14 @@ extern "C" {
 tls_status tls_export_factor(tls_ctx* ctx, double* R_host, double* d_host, double* H_host);
 
 /*
+ * tls_batch_export_factor -- as tls_export_factor for problem i of a packed batch: R_host and
+ * H_host (n_i x n_i), d_host (n_i); any may be NULL. TLS_ERR_ARG for i out of range,
+ * TLS_ERR_STATE before a successful tls_batch_factor.
+ */
+tls_status tls_batch_export_factor(tls_batch* bt, int i, double* R_host, double* d_host,
+                                   double* H_host);
+
+/*
  * tls_export_working_copy -- the FP32 working copy of A (m x n, row-major) that the PCGTLS
  * passes read when u = FP32: each entry is A rounded to nearest (even) FP32. A32_host: m*n
  * floats (host). TLS_ERR_STATE before a successful tls_factor with u = FP32.
@@ -78,6 +86,13 @@ enum {
 tls_status tls_profile_enable(tls_ctx* ctx, int on);
 /* Launch count and summed device milliseconds of one class (TLS_PROF_*). */
 tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* ms);
+/* The same per-class timing for a packed batch (classes as above; PCG_REDUCE covers the
+ * per-problem PCGTLS step including its W / W^T products; VEC the small per-problem kernels). */
+tls_status tls_batch_profile_enable(tls_batch* bt, int on);
+tls_status tls_batch_profile_get(const tls_batch* bt, int cls, int64_t* count, double* ms);
+/* Entries of A (sum of m n over the problems still active) that the pass launches of class
+ * cls read while profiling was on: the algorithmic work behind the timed launches. */
+tls_status tls_batch_profile_elems(const tls_batch* bt, int cls, int64_t* elems);
 /* Kernels launched by the library since it was loaded (all contexts). */
 uint64_t tls_kernel_launches(void);
 

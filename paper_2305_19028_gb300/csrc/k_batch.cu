@@ -1,0 +1,1316 @@
+// Kernels of the packed batched path: many dense TLS problems of uneven sizes, every phase of
+// RQI-PCGTLS (Alg. 2; PCGTLS of Alg. 3 with the precisions of Alg. 4) launched once for the
+// whole batch.
+//
+//  * pass kernels: one CTA per row tile of any problem (one tile table for the batch). A group
+//    of `lr` lanes owns a row; each lane holds `ch` chunks of 4 columns and keeps the vector
+//    entries of its columns (q or x) in registers. Per row: the dot products with the vectors
+//    (group shuffle), then the row's contribution to A^T t (or A^T r) into per-lane column
+//    accumulators; at the end the CTA writes its partial column sums (deterministic two-stage
+//    reduction, no atomics).
+//  * per-problem kernels: one CTA (512 threads) per problem for the n-sized work -- summing the
+//    tile partials, the Rayleigh quotient and psi (Eq. (2), Eq. (4)), the PCGTLS scalars, and
+//    the products with the explicit inverse factor W = R_H^{-1} (row-per-warp GEMVs from L2).
+//  * factor kernels: Gram tiles of every problem in one grid (FP32 FMA on the u_f-rounded,
+//    column-scaled entries, i.e. exactly the products a tensor core forms), then one CTA per
+//    problem for the blocked Cholesky (64-blocks) and for the blocked triangular inverse.
+#include "../../include/tls.h"
+#include "tls_batch_internal.h"
+#include "tls_device.cuh"
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+namespace tls {
+namespace bat {
+
+namespace {
+
+constexpr int kPW = kPT / 32;   // warps of a pass CTA
+constexpr int kCW = kCT / 32;   // warps of a per-problem CTA
+constexpr int kLd = kNB + 4;    // shared-memory row stride of 64-wide tiles (16-byte rows)
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of K values over the CTA; every thread receives the totals. sh: 32 * K entries.
+template <typename T, int K>
+__device__ __forceinline__ void bsum(T (&v)[K], T* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = wsum(v[k]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = wsum(lane < nw ? sh[lane * K + k] : T(0));
+}
+
+__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
+  const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
+  const double2 t0 = __ldcs(reinterpret_cast<const double2*>(p));
+  const double2 t1 = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+}
+// 4 consecutive entries of a row that stays in cache (W, W^T)
+__device__ __forceinline__ void ldrow4(const float* p, float (&o)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ldrow4(const double* p, double (&o)[4]) {
+  const double2 t0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+}
+
+// rounding to the factor precision u_f (Table 2): FP16 / BF16 round to nearest even
+__device__ __forceinline__ float round_uf(float v, int prec) {
+  if (prec == (int)Prec::FP16) return __half2float(__float2half_rn(v));
+  if (prec == (int)Prec::BF16) return __bfloat162float(__float2bfloat16_rn(v));
+  return v;
+}
+__device__ __forceinline__ double round_uf(double v, int prec) {
+  if (prec == (int)Prec::FP16) return (double)__half2float(__double2half(v));
+  if (prec == (int)Prec::BF16) return (double)__bfloat162float(__double2bfloat16(v));
+  if (prec == (int)Prec::FP32) return (double)__double2float_rn(v);
+  return v;
+}
+
+template <typename T> __device__ __forceinline__ const T* dinv_of(const BArrays& a);
+template <> __device__ __forceinline__ const float* dinv_of<float>(const BArrays& a) { return a.dinv32; }
+template <> __device__ __forceinline__ const double* dinv_of<double>(const BArrays& a) { return a.dinv; }
+
+// =========================================================================================
+// Pass over the rows of one tile
+// =========================================================================================
+template <typename TA, int NR, int MODE, int LR, int CH>
+__device__ __forceinline__ void pass_body(const BArrays& a, const BProb& P, const BTile& t,
+                                          int tile, unsigned char* smem) {
+  constexpr int G = 32 / LR;      // row groups per warp
+  constexpr int NG = kPW * G;     // row groups per CTA
+  constexpr int NC = 4 * LR * CH; // columns covered by a group
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane & (LR - 1);
+  const int lda = (int)P.lda;
+  const int npb = (int)P.npb;
+  const TA* A;
+  if constexpr (sizeof(TA) == 4) A = reinterpret_cast<const TA*>(a.A32);
+  else A = reinterpret_cast<const TA*>(a.A64);
+  const TA* Ab = A + P.offA + (int64_t)t.row0 * lda;
+  const TA* vec = nullptr;
+  if constexpr (MODE == kPcg) vec = static_cast<const TA*>(a.vq) + 2 * P.offV;
+  if constexpr (MODE == kResid) vec = reinterpret_cast<const TA*>(a.x) + P.offV;
+
+  TA vq[NR][CH][4];
+  TA acc[NR][CH][4];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = 4 * (gl + LR * c);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        acc[r][c][e] = TA(0);
+        vq[r][c][e] = (MODE != kColnorm && col < lda) ? vec[r * npb + col + e] : TA(0);
+      }
+  }
+  TA sc0 = TA(0), sc1 = TA(0);
+  for (int base = warp * G; base < t.rows; base += 2 * NG) {   // warp-uniform trip count
+    const int ra = base + lane / LR, rb = ra + NG;
+    const bool ha = ra < t.rows, hb = rb < t.rows;
+    TA x0[CH][4], x1[CH][4];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int col = 4 * (gl + LR * c);
+      const bool ok = col < lda;
+      if (ok && ha) load4(Ab + (int64_t)ra * lda + col, x0[c]);
+      else x0[c][0] = x0[c][1] = x0[c][2] = x0[c][3] = TA(0);
+      if (ok && hb) load4(Ab + (int64_t)rb * lda + col, x1[c]);
+      else x1[c][0] = x1[c][1] = x1[c][2] = x1[c][3] = TA(0);
+    }
+    if constexpr (MODE == kColnorm) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int col = 4 * (gl + LR * c);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          acc[0][c][e] = fma(x0[c][e], x0[c][e], acc[0][c][e]);
+          acc[0][c][e] = fma(x1[c][e], x1[c][e], acc[0][c][e]);
+        }
+        // the FP32 working copy fl32(A) (round to nearest)
+        if (col < lda) {
+          if (ha)
+            *reinterpret_cast<float4*>(a.A32 + P.offA + (int64_t)(t.row0 + ra) * lda + col) =
+                make_float4(f64_to_f32_rn(x0[c][0]), f64_to_f32_rn(x0[c][1]),
+                            f64_to_f32_rn(x0[c][2]), f64_to_f32_rn(x0[c][3]));
+          if (hb)
+            *reinterpret_cast<float4*>(a.A32 + P.offA + (int64_t)(t.row0 + rb) * lda + col) =
+                make_float4(f64_to_f32_rn(x1[c][0]), f64_to_f32_rn(x1[c][1]),
+                            f64_to_f32_rn(x1[c][2]), f64_to_f32_rn(x1[c][3]));
+        }
+      }
+    } else {
+      TA d0[NR], d1[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        d0[r] = TA(0);
+        d1[r] = TA(0);
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            d0[r] = fma(x0[c][e], vq[r][c][e], d0[r]);
+            d1[r] = fma(x1[c][e], vq[r][c][e], d1[r]);
+          }
+      }
+#pragma unroll
+      for (int o = LR / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          d0[r] += __shfl_xor_sync(0xffffffffu, d0[r], o);
+          d1[r] += __shfl_xor_sync(0xffffffffu, d1[r], o);
+        }
+      if constexpr (MODE == kResid) {
+        // r_i = b_i - a_i^T x (FP64), Alg. 2
+        const double bv0 = ha ? a.b[P.offB + t.row0 + ra] : 0.0;
+        const double bv1 = hb ? a.b[P.offB + t.row0 + rb] : 0.0;
+        const TA r0 = (TA)bv0 - d0[0], r1 = (TA)bv1 - d1[0];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            acc[0][c][e] = fma(r0, x0[c][e], acc[0][c][e]);
+            acc[0][c][e] = fma(r1, x1[c][e], acc[0][c][e]);
+          }
+        if (gl == 0) {
+          sc0 = fma(r0, r0, sc0);
+          sc0 = fma(r1, r1, sc0);
+          sc1 = fma((TA)bv0, r0, sc1);
+          sc1 = fma((TA)bv1, r1, sc1);
+        }
+      } else {
+        // t = A q; the row's share of A^T t; ||t||^2
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+          for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              acc[r][c][e] = fma(d0[r], x0[c][e], acc[r][c][e]);
+              acc[r][c][e] = fma(d1[r], x1[c][e], acc[r][c][e]);
+            }
+        if (gl == 0) {
+          sc0 = fma(d0[0], d0[0], sc0);
+          sc0 = fma(d1[0], d1[0], sc0);
+          if constexpr (NR > 1) {
+            sc1 = fma(d0[1], d0[1], sc1);
+            sc1 = fma(d1[1], d1[1], sc1);
+          }
+        }
+      }
+    }
+  }
+  // the G groups of a warp cover the same columns
+#pragma unroll
+  for (int o = LR; o < 32; o <<= 1)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          acc[r][c][e] += __shfl_xor_sync(0xffffffffu, acc[r][c][e], o);
+  TA* red = reinterpret_cast<TA*>(smem);   // [kPW][NR][NC]
+  if (lane < LR)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          red[(warp * NR + r) * NC + 4 * (gl + LR * c) + e] = acc[r][c][e];
+  __shared__ double sred[kPW][2];
+  sc0 = wsum(sc0);
+  sc1 = wsum(sc1);
+  if (lane == 0) {
+    sred[warp][0] = (double)sc0;
+    sred[warp][1] = (double)sc1;
+  }
+  __syncthreads();
+  TA* out;
+  if constexpr (MODE == kPcg) out = static_cast<TA*>(a.partU);
+  else out = reinterpret_cast<TA*>(a.part64);
+  const int64_t slab = (P.poff + (int64_t)(tile - P.tile0) * lda) * NR;
+  for (int e = threadIdx.x; e < NR * lda; e += kPT) {
+    const int r = e / lda, col = e - r * lda;
+    TA s = TA(0);
+#pragma unroll
+    for (int w = 0; w < kPW; ++w) s += red[(w * NR + r) * NC + col];
+    out[slab + e] = s;
+  }
+  if (threadIdx.x < 2) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kPW; ++w) s += sred[w][threadIdx.x];
+    a.spart[(int64_t)tile * 4 + threadIdx.x] = s;
+  }
+}
+
+template <typename TA, int NR, int MODE>
+__global__ void __launch_bounds__(kPT) pass_kernel(BArrays a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tile = blockIdx.x;
+  const BTile t = a.tiles[tile];
+  if (MODE != kColnorm && !a.st[t.prob].active) return;
+  const BProb P = a.probs[t.prob];
+  switch (P.cfg) {
+    case 0: pass_body<TA, NR, MODE, 8, 1>(a, P, t, tile, smem); break;
+    case 1: pass_body<TA, NR, MODE, 16, 1>(a, P, t, tile, smem); break;
+    case 2: pass_body<TA, NR, MODE, 32, 1>(a, P, t, tile, smem); break;
+    case 3: pass_body<TA, NR, MODE, 32, 2>(a, P, t, tile, smem); break;
+    default: pass_body<TA, NR, MODE, 32, 4>(a, P, t, tile, smem); break;
+  }
+}
+
+template <typename TA, int NR>
+constexpr size_t pass_smem() { return sizeof(TA) * kPW * NR * 4 * 32 * 4; }
+
+// =========================================================================================
+// Column norms: d_j = ||a_j||_2 (zero columns and padding: d = 1), ||A||_F^2, ||b||^2
+// =========================================================================================
+__global__ void __launch_bounds__(kCT) colnorm_post_kernel(BArrays a, const int* list) {
+  const int pi = list[blockIdx.x];
+  const BProb P = a.probs[pi];
+  const int lda = (int)P.lda, npb = (int)P.npb, n = (int)P.n;
+  __shared__ double sh[32 * 2];
+  double s2[2] = {0.0, 0.0};
+  for (int c = threadIdx.x; c < npb; c += kCT) {
+    double dd = 1.0;
+    if (c < n) {
+      const double* base = a.part64 + P.poff + c;
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      int i = 0;
+      for (; i + 3 < P.ntiles; i += 4) {
+        t0 += base[(int64_t)i * lda];
+        t1 += base[(int64_t)(i + 1) * lda];
+        t2 += base[(int64_t)(i + 2) * lda];
+        t3 += base[(int64_t)(i + 3) * lda];
+      }
+      for (; i < P.ntiles; ++i) t0 += base[(int64_t)i * lda];
+      dd = sqrt((t0 + t1) + (t2 + t3));
+      if (!(dd > 0.0)) dd = 1.0;
+      s2[0] = fma(dd, dd, s2[0]);
+    }
+    a.d[P.offV + c] = dd;
+    a.dinv[P.offV + c] = 1.0 / dd;
+    a.dinv32[P.offV + c] = (float)(1.0 / dd);
+  }
+  for (int64_t i = threadIdx.x; i < P.m; i += kCT) {
+    const double bv = a.b[P.offB + i];
+    s2[1] = fma(bv, bv, s2[1]);
+  }
+  bsum<double, 2>(s2, sh);
+  if (threadIdx.x == 0) {
+    BState& st = a.st[pi];
+    st.norm2_A = s2[0];
+    st.norm2_b = s2[1];
+    st.scale = s2[0] + s2[1];
+  }
+}
+
+// =========================================================================================
+// Gram H = A_s^T A_s, A_s = fl_uf(A D^{-1}) (upper 64 x 64 tiles of every problem)
+// =========================================================================================
+template <typename C>
+__device__ __forceinline__ C scaled_entry(const BArrays& a, const BProb& P, int64_t row, int col);
+template <>
+__device__ __forceinline__ float scaled_entry<float>(const BArrays& a, const BProb& P, int64_t row,
+                                                     int col) {
+  // FP32 product fl32(fl32(a_ij) * fl32(1/d_j)), then rounded to u_f
+  return round_uf(a.A32[P.offA + row * P.lda + col] * a.dinv32[P.offV + col], P.prec);
+}
+template <>
+__device__ __forceinline__ double scaled_entry<double>(const BArrays& a, const BProb& P,
+                                                       int64_t row, int col) {
+  return round_uf(a.A64[P.offA + row * P.lda + col] * a.dinv[P.offV + col], P.prec);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) gram_kernel(BArrays a, const int4* gt) {
+  const int4 g = gt[blockIdx.x];   // (problem, row block, column block), row block <= column block
+  const BProb P = a.probs[g.x];
+  const int n = (int)P.n, npb = (int)P.npb;
+  const int c0 = g.y * kNB, c1 = g.z * kNB;
+  __shared__ __align__(16) C SA[32][kLd];
+  __shared__ __align__(16) C SB[32][kLd];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = C(0);
+  for (int64_t r0 = 0; r0 < P.m; r0 += 32) {
+    for (int e = tid; e < 32 * kNB; e += 256) {
+      const int rr = e / kNB, cc = e % kNB;
+      const int64_t row = r0 + rr;
+      C va = C(0), vb = C(0);
+      if (row < P.m) {
+        if (c0 + cc < n) va = scaled_entry<C>(a, P, row, c0 + cc);
+        if (c1 + cc < n) vb = scaled_entry<C>(a, P, row, c1 + cc);
+      }
+      SA[rr][cc] = va;
+      SB[rr][cc] = vb;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      C av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        av[i] = SA[k][ty * 4 + i];
+        bv[i] = SB[k][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  C* H = static_cast<C*>(a.H) + P.offM;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = c0 + ty * 4 + i, c = c1 + tx * 4 + j;
+      // identity on the padding (rows / columns >= n): padded entries never couple
+      H[(int64_t)r * npb + c] = (r == c && r >= n) ? C(1) : acc[i][j];
+    }
+}
+
+// =========================================================================================
+// Inverse of an upper-triangular 64 x 64 block S (shared, row stride kLd) into X (shared):
+// X11 = R11^{-1}, X22 = R22^{-1} by columns (threads 0..63), X12 = -X11 R12 X22.
+// Tm is a 32 x 32 scratch area (row stride kLd). Call with all threads of the CTA.
+// =========================================================================================
+template <typename C>
+__device__ void inv_upper64(const C* S, C* X, C* Tm) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kNB * kLd; e += blockDim.x) X[e] = C(0);
+  __syncthreads();
+  if (tid < 64) {
+    const int o = (tid < 32) ? 0 : 32, j = tid & 31;
+    for (int i = j; i >= 0; --i) {
+      C v = (i == j) ? C(1) : C(0);
+      for (int k = i + 1; k <= j; ++k) v = fma(-S[(o + i) * kLd + o + k], X[(o + k) * kLd + o + j], v);
+      X[(o + i) * kLd + o + j] = v / S[(o + i) * kLd + o + i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 32 * 32; e += blockDim.x) {   // Tm = R12 X22
+    const int i = e / 32, j = e % 32;
+    C v = C(0);
+    for (int k = 0; k <= j; ++k) v = fma(S[i * kLd + 32 + k], X[(32 + k) * kLd + 32 + j], v);
+    Tm[i * kLd + j] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < 32 * 32; e += blockDim.x) {   // X12 = -X11 Tm
+    const int i = e / 32, j = e % 32;
+    C v = C(0);
+    for (int k = i; k < 32; ++k) v = fma(X[i * kLd + k], Tm[k * kLd + j], v);
+    X[i * kLd + 32 + j] = -v;
+  }
+  __syncthreads();
+}
+
+// =========================================================================================
+// Blocked Cholesky H + s I = R_H^T R_H (upper, 64-blocks), one CTA per problem:
+//  diagonal block: one barrier per pivot, each finished row of R_KK rounded to u_f as it is
+//  written (the shared copy keeps the unrounded row for the block's own update); panel
+//  R_KJ = R_KK^{-T} H_KJ through the inverse of the rounded R_KK; trailing update
+//  H_22 -= R_K2^T R_K2. Finally every entry of R_H is rounded to u_f and the lower part zeroed.
+// A non-positive (or NaN) pivot stops the problem: info = pivot + 1.
+// =========================================================================================
+template <typename C>
+__global__ void __launch_bounds__(kCT) chol_kernel(BArrays a, const int* list, const double* shift,
+                                                   int* info) {
+  const int pi = list[blockIdx.x];
+  const BProb P = a.probs[pi];
+  const int npb = (int)P.npb, n = (int)P.n, prec = P.prec;
+  const C* H = static_cast<const C*>(a.H) + P.offM;
+  C* M = static_cast<C*>(a.R) + P.offM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* S = reinterpret_cast<C*>(smem);   // 64 x kLd each
+  C* X = S + kNB * kLd;
+  C* TA = X + kNB * kLd;
+  C* TB = TA + kNB * kLd;
+  __shared__ int s_broke;
+  const int tid = threadIdx.x;
+  const C sh = (C)shift[pi];
+  for (int64_t e = tid; e < (int64_t)npb * npb; e += kCT) {
+    const int r = (int)(e / npb), c = (int)(e % npb);
+    C v = H[e];
+    if (r == c && r < n) v += sh;
+    M[e] = v;
+  }
+  if (tid == 0) s_broke = 0;
+  __syncthreads();
+  for (int kb = 0; kb < npb; kb += kNB) {
+    for (int e = tid; e < kNB * kNB; e += kCT) {
+      const int r = e / kNB, c = e % kNB;
+      S[r * kLd + c] = M[(int64_t)(kb + r) * npb + kb + c];
+    }
+    __syncthreads();
+    for (int k = 0; k < kNB; ++k) {
+      C piv = S[k * kLd + k];
+      const bool bad = !(piv > C(0));
+      if (bad) piv = C(1);
+      const C rkk = sqrt(piv);
+      const C inv = C(1) / rkk;
+      const C inv2 = inv * inv;
+      if (tid < kNB) {
+        C v = C(0);
+        if (tid == k) v = rkk;
+        else if (tid > k) v = S[k * kLd + tid] * inv;
+        M[(int64_t)(kb + k) * npb + kb + tid] = round_uf(v, prec);
+      }
+      if (bad && tid == 0 && s_broke == 0) s_broke = kb + k + 1;
+      // rows i = k+1+ty+16u, columns j = k+1+tx+32v, j >= i
+      const int ty = tid >> 5, tx = tid & 31;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = k + 1 + ty + 16 * u;
+        if (i < kNB) {
+          const C ski = S[k * kLd + i] * inv2;
+#pragma unroll
+          for (int v2 = 0; v2 < 2; ++v2) {
+            const int j = k + 1 + tx + 32 * v2;
+            if (j < kNB && j >= i) S[i * kLd + j] = fma(-ski, S[k * kLd + j], S[i * kLd + j]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (s_broke) {
+      if (tid == 0) info[pi] = s_broke;
+      return;
+    }
+    // inverse of the rounded diagonal block R_KK
+    for (int e = tid; e < kNB * kNB; e += kCT) {
+      const int r = e / kNB, c = e % kNB;
+      S[r * kLd + c] = (c >= r) ? M[(int64_t)(kb + r) * npb + kb + c] : C(0);
+    }
+    __syncthreads();
+    inv_upper64<C>(S, X, TA);
+    // panel: R_KJ = W_KK^T H_KJ, 64 columns at a time (thread: column j, rows i0 .. i0+7)
+    for (int jb = kb + kNB; jb < npb; jb += kNB) {
+      for (int e = tid; e < kNB * kNB; e += kCT) {
+        const int r = e / kNB, c = e % kNB;
+        TA[r * kLd + c] = M[(int64_t)(kb + r) * npb + jb + c];
+      }
+      __syncthreads();
+      const int j = tid & 63, i0 = (tid >> 6) * 8;
+      C o[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) o[u] = C(0);
+      for (int k = 0; k < i0 + 8; ++k) {
+        const C t = TA[k * kLd + j];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (k <= i0 + u) o[u] = fma(X[k * kLd + i0 + u], t, o[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) M[(int64_t)(kb + i0 + u) * npb + jb + j] = o[u];
+      __syncthreads();
+    }
+    // trailing update of the upper blocks (bi <= bj) right of and below the panel
+    for (int bi = kb + kNB; bi < npb; bi += kNB) {
+      for (int bj = bi; bj < npb; bj += kNB) {
+        for (int e = tid; e < kNB * kNB; e += kCT) {
+          const int r = e / kNB, c = e % kNB;
+          TA[r * kLd + c] = M[(int64_t)(kb + r) * npb + bi + c];
+          TB[r * kLd + c] = M[(int64_t)(kb + r) * npb + bj + c];
+        }
+        __syncthreads();
+        const int i = tid >> 3, j0 = (tid & 7) * 8;
+        C o[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) o[u] = C(0);
+#pragma unroll 4
+        for (int k = 0; k < kNB; ++k) {
+          const C ak = TA[k * kLd + i];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) o[u] = fma(ak, TB[k * kLd + j0 + u], o[u]);
+        }
+        C* row = M + (int64_t)(bi + i) * npb + bj + j0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) row[u] -= o[u];
+        __syncthreads();
+      }
+    }
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < (int64_t)npb * npb; e += kCT) {
+    const int r = (int)(e / npb), c = (int)(e % npb);
+    M[e] = (c < r) ? C(0) : round_uf(M[e], prec);
+  }
+  if (tid == 0) info[pi] = 0;
+}
+
+// =========================================================================================
+// W = R_H^{-1} (u type T) by block rows from the bottom: W_II = R_II^{-1},
+// W_IJ = -W_II sum_{I<K<=J} R_IK W_KJ; then W^T. One CTA per problem.
+// =========================================================================================
+template <typename C, typename T>
+__global__ void __launch_bounds__(kCT) trtri_kernel(BArrays a, const int* list) {
+  const int pi = list[blockIdx.x];
+  const BProb P = a.probs[pi];
+  const int npb = (int)P.npb, nb = npb / kNB;
+  const C* R = static_cast<const C*>(a.R) + P.offM;
+  T* W = static_cast<T*>(a.W) + P.offM;
+  T* WT = static_cast<T*>(a.WT) + P.offM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* S = reinterpret_cast<T*>(smem);
+  T* X = S + kNB * kLd;
+  T* TA = X + kNB * kLd;
+  T* TB = TA + kNB * kLd;
+  const int tid = threadIdx.x;
+  for (int64_t e = tid; e < (int64_t)npb * npb; e += kCT) W[e] = T(0);
+  __syncthreads();
+  for (int ib = nb - 1; ib >= 0; --ib) {
+    const int r0 = ib * kNB;
+    for (int e = tid; e < kNB * kNB; e += kCT) {
+      const int r = e / kNB, c = e % kNB;
+      S[r * kLd + c] = (c >= r) ? (T)R[(int64_t)(r0 + r) * npb + r0 + c] : T(0);
+    }
+    __syncthreads();
+    inv_upper64<T>(S, X, TA);   // X = W_II
+    for (int e = tid; e < kNB * kNB; e += kCT) {
+      const int r = e / kNB, c = e % kNB;
+      W[(int64_t)(r0 + r) * npb + r0 + c] = X[r * kLd + c];
+    }
+    for (int jb = ib + 1; jb < nb; ++jb) {
+      // Tacc = sum_{K = ib+1 .. jb} R_IK W_KJ   (thread: row i, columns j0 .. j0+7)
+      const int i = tid >> 3, j0 = (tid & 7) * 8;
+      T o[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) o[u] = T(0);
+      for (int kb2 = ib + 1; kb2 <= jb; ++kb2) {
+        __syncthreads();
+        for (int e = tid; e < kNB * kNB; e += kCT) {
+          const int r = e / kNB, c = e % kNB;
+          TA[r * kLd + c] = (T)R[(int64_t)(r0 + r) * npb + kb2 * kNB + c];
+          TB[r * kLd + c] = W[(int64_t)(kb2 * kNB + r) * npb + jb * kNB + c];
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kNB; ++k) {
+          const T ak = TA[i * kLd + k];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) o[u] = fma(ak, TB[k * kLd + j0 + u], o[u]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) TB[i * kLd + j0 + u] = o[u];
+      __syncthreads();
+      // W_IJ = -X Tacc (X upper triangular)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) o[u] = T(0);
+      for (int k = i; k < kNB; ++k) {
+        const T xk = X[i * kLd + k];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) o[u] = fma(xk, TB[k * kLd + j0 + u], o[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) W[(int64_t)(r0 + i) * npb + jb * kNB + j0 + u] = -o[u];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < (int64_t)npb * npb; e += kCT) {
+    const int r = (int)(e / npb), c = (int)(e % npb);
+    WT[(int64_t)c * npb + r] = W[e];
+  }
+}
+
+// =========================================================================================
+// Per-problem GEMVs with the inverse factor (one warp per row, rows from L2)
+// =========================================================================================
+// v_r[i] = sum_{j <= i} WT[i][j] y_r[j]   (WT = W^T lower triangular), r < nr
+template <typename T>
+__device__ void gemv_lower(const T* __restrict__ WT, int npb, const T* ys, T* vs, int nr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < npb; i += kCW) {
+    const T* row = WT + (int64_t)i * npb;
+    T a0 = T(0), a1 = T(0);
+    for (int c = lane * 4; c <= i; c += 128) {
+      T w[4];
+      ldrow4(row + c, w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        a0 = fma(w[e], ys[c + e], a0);
+        if (nr > 1) a1 = fma(w[e], ys[npb + c + e], a1);
+      }
+    }
+    a0 = wsum(a0);
+    a1 = wsum(a1);
+    if (lane == 0) {
+      vs[i] = a0;
+      if (nr > 1) vs[npb + i] = a1;
+    }
+  }
+}
+// v_r[i] = sum_{j >= i} W[i][j] p_r[j]   (W upper triangular)
+template <typename T>
+__device__ void gemv_upper(const T* __restrict__ W, int npb, const T* ps, T* vs, int nr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < npb; i += kCW) {
+    const T* row = W + (int64_t)i * npb;
+    T a0 = T(0), a1 = T(0);
+    for (int c = (i & ~3) + lane * 4; c < npb; c += 128) {
+      T w[4];
+      ldrow4(row + c, w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        a0 = fma(w[e], ps[c + e], a0);
+        if (nr > 1) a1 = fma(w[e], ps[npb + c + e], a1);
+      }
+    }
+    a0 = wsum(a0);
+    a1 = wsum(a1);
+    if (lane == 0) {
+      vs[i] = a0;
+      if (nr > 1) vs[npb + i] = a1;
+    }
+  }
+}
+
+// Shared memory of the per-problem solve kernels: 4 vectors of 2 x kMaxN in T plus FP64 scratch
+template <typename T>
+constexpr size_t post_smem() { return sizeof(T) * 4 * 2 * kMaxN; }
+
+struct PVec {   // u-type vector pairs of one problem
+  template <typename T> __device__ static T* at(void* base, const BProb& P) {
+    return static_cast<T*>(base) + 2 * P.offV;
+  }
+};
+
+// PCGTLS start (Alg. 3): s_0 = R^{-T} rhs (y = D^{-1} rhs staged in ys by the caller),
+// eta_0 = ||s_0||^2, p_0 = s_0, q_0 = R^{-1} p_0 = D^{-1} W p_0, w = 0.
+template <typename T>
+__device__ void pcg_start(const BArrays& a, const BProb& P, BState& st, int nr, T* ys, T* vs,
+                          double* dsh) {
+  const int npb = (int)P.npb;
+  const T* W = static_cast<const T*>(a.W) + P.offM;
+  const T* WT = static_cast<const T*>(a.WT) + P.offM;
+  const T* dv = dinv_of<T>(a) + P.offV;
+  T* s = PVec::at<T>(a.vs, P);
+  T* p = PVec::at<T>(a.vp, P);
+  T* q = PVec::at<T>(a.vq, P);
+  T* w = PVec::at<T>(a.vw, P);
+  __syncthreads();
+  gemv_lower<T>(WT, npb, ys, vs, nr);
+  __syncthreads();
+  double e[2] = {0.0, 0.0};
+  {
+    T el[2] = {T(0), T(0)};
+    for (int c = threadIdx.x; c < npb; c += kCT)
+      for (int r = 0; r < 2; ++r) {
+        const T sv = (r < nr) ? vs[r * npb + c] : T(0);
+        s[r * npb + c] = sv;
+        p[r * npb + c] = sv;
+        w[r * npb + c] = T(0);
+        ys[r * npb + c] = sv;
+        el[r] = fma(sv, sv, el[r]);
+      }
+    e[0] = (double)el[0];
+    e[1] = (double)el[1];
+  }
+  bsum<double, 2>(e, dsh);
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < 2; ++r) {
+      st.eta[r] = e[r];
+      st.eta0[r] = e[r];
+      st.beta[r] = 0.0;
+      st.alpha[r] = 0.0;
+      st.delta[r] = 1.0;
+      st.done[r] = (r < nr) ? (e[r] == 0.0 ? 1 : 0) : 1;
+      st.not_spd[r] = 0;
+      st.iters[r] = 0;
+    }
+    st.nr = nr;
+  }
+  __syncthreads();
+  gemv_upper<T>(W, npb, ys, vs, nr);
+  __syncthreads();
+  T qp[4] = {T(0), T(0), T(0), T(0)};
+  for (int c = threadIdx.x; c < npb; c += kCT)
+    for (int r = 0; r < nr; ++r) {
+      const T qv = vs[r * npb + c] * dv[c];
+      q[r * npb + c] = qv;
+      qp[r] = fma(qv, qv, qp[r]);
+      qp[2 + r] = fma(ys[r * npb + c], ys[r * npb + c], qp[2 + r]);
+    }
+  double qd[4] = {(double)qp[0], (double)qp[1], (double)qp[2], (double)qp[3]};
+  bsum<double, 4>(qd, dsh);
+  if (threadIdx.x == 0) {
+    st.qq[0] = qd[0];
+    st.qq[1] = qd[1];
+    st.pp[0] = qd[2];
+    st.pp[1] = qd[3];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCT) solve_init_kernel(BArrays a, const int* list) {
+  const int pi = list[blockIdx.x];
+  const BProb P = a.probs[pi];
+  for (int c = threadIdx.x; c < P.npb; c += kCT) {
+    a.x[P.offV + c] = 0.0;
+    a.xbest[P.offV + c] = 0.0;
+    a.f[P.offV + c] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    BState& st = a.st[pi];
+    st.xx = 0.0;
+    st.k = 0;
+    st.best_k = 0;
+    st.best_psi = INFINITY;
+    st.prev_psi = INFINITY;
+    st.best_s2 = 0.0;
+    st.stop = TLS_STOP_MAX_RQI;
+    st.active = 1;
+    st.n_psi = 0;
+    st.cg_total = 0;
+    st.not_spd_any = 0;
+    st.nr = 1;
+  }
+}
+
+// Residual block of Alg. 2 in FP64 (r = b - A x, sigma^2 = ||r||^2 / (1 + ||x||^2),
+// f = -A^T r - sigma^2 x, g = -b^T r + sigma^2, psi of Eq. (4)), then by `mode`:
+//  kResidLs    start PCGTLS with sigma^2 = 0 on -f (the LS start x_0, Alg. 2 line 1)
+//  kResidStart the inverse-iteration step x_1 = x_0 + sigma_0^2 (R^T R)^{-1} x_0
+//  kResidRqi   the stopping rules (Sec. 3 after Eq. (4)) and, if the problem goes on, the
+//              two shifted solves' start on -f and x
+template <typename T>
+__global__ void __launch_bounds__(kCT) resid_post_kernel(BArrays a, const int* list, int mode,
+                                                         SolveParams sp) {
+  const int pi = list[blockIdx.x];
+  BState& st = a.st[pi];
+  if (!st.active) return;
+  const BProb P = a.probs[pi];
+  const int npb = (int)P.npb, n = (int)P.n, lda = (int)P.lda;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* ys = reinterpret_cast<T*>(smem);
+  T* vs = ys + 2 * kMaxN;
+  double* at = reinterpret_cast<double*>(vs + 2 * kMaxN);   // kMaxN doubles
+  __shared__ double dsh[32 * 4];
+  __shared__ int s_dec[2];
+  double* x = a.x + P.offV;
+  double* f = a.f + P.offV;
+  const double* dinv = a.dinv + P.offV;
+  // sum of the tile partials of A^T r, ||r||^2, b^T r
+  double rs[2] = {0.0, 0.0};
+  for (int c = threadIdx.x; c < npb; c += kCT) {
+    double t0 = 0.0, t1 = 0.0;
+    if (c < lda) {
+      const double* base = a.part64 + P.poff + c;
+      int i = 0;
+      for (; i + 1 < P.ntiles; i += 2) {
+        t0 += base[(int64_t)i * lda];
+        t1 += base[(int64_t)(i + 1) * lda];
+      }
+      if (i < P.ntiles) t0 += base[(int64_t)i * lda];
+    }
+    at[c] = t0 + t1;
+  }
+  for (int i = threadIdx.x; i < P.ntiles; i += kCT) {
+    rs[0] += a.spart[(int64_t)(P.tile0 + i) * 4 + 0];
+    rs[1] += a.spart[(int64_t)(P.tile0 + i) * 4 + 1];
+  }
+  bsum<double, 2>(rs, dsh);
+  const double xx = st.xx;
+  const double sigma2 = rs[0] / (1.0 + xx);
+  double ff[1] = {0.0};
+  for (int c = threadIdx.x; c < npb; c += kCT) {
+    const double fj = (c < n) ? (-at[c] - sigma2 * x[c]) : 0.0;
+    f[c] = fj;
+    ff[0] = fma(fj, fj, ff[0]);
+  }
+  bsum<double, 1>(ff, dsh);
+  const double g = -rs[1] + sigma2;
+  const double psi = sqrt((ff[0] + g * g) / (xx + 1.0));
+  if (threadIdx.x == 0) {
+    st.rr = rs[0];
+    st.br = rs[1];
+    st.sigma2 = sigma2;
+    st.g = g;
+    st.ff = ff[0];
+    st.psi = psi;
+  }
+  if (mode == kResidLs) {
+    for (int c = threadIdx.x; c < npb; c += kCT) {
+      ys[c] = (T)(-f[c] * dinv[c]);
+      ys[npb + c] = T(0);
+    }
+    if (threadIdx.x == 0) {
+      st.cg_sigma2 = 0.0;
+      st.cg_tol2 = 0.0;
+    }
+    pcg_start<T>(a, P, st, 1, ys, vs, dsh);
+    return;
+  }
+  if (mode == kResidStart) {
+    // u_0 = R^{-1} R^{-T} x_0 = D^{-1} W W^T D^{-1} x_0; x_1 = x_0 + sigma_0^2 u_0
+    const T* W = static_cast<const T*>(a.W) + P.offM;
+    const T* WT = static_cast<const T*>(a.WT) + P.offM;
+    const T* dv = dinv_of<T>(a) + P.offV;
+    for (int c = threadIdx.x; c < npb; c += kCT) ys[c] = (T)(x[c] * dinv[c]);
+    __syncthreads();
+    gemv_lower<T>(WT, npb, ys, vs, 1);
+    __syncthreads();
+    gemv_upper<T>(W, npb, vs, ys, 1);
+    __syncthreads();
+    double xs[1] = {0.0};
+    for (int c = threadIdx.x; c < npb; c += kCT) {
+      double xn = 0.0;
+      if (c < n) xn = fma(sigma2, (double)(ys[c] * dv[c]), x[c]);
+      x[c] = xn;
+      xs[0] = fma(xn, xn, xs[0]);
+    }
+    bsum<double, 1>(xs, dsh);
+    if (threadIdx.x == 0) st.xx = xs[0];
+    return;
+  }
+  // RQI step k: stopping rules, best iterate
+  if (threadIdx.x == 0) {
+    const int k = st.k + 1;
+    st.k = k;
+    if (st.n_psi < 24) st.psi_hist[st.n_psi++] = psi;
+    int stop = 0, improve = 0;
+    if (!isfinite(psi) || !isfinite(sigma2)) {
+      stop = TLS_STOP_PSI_UP;
+    } else {
+      const bool up = sp.psi_rule_ge ? (psi >= st.prev_psi) : (psi > st.prev_psi);
+      if (up && st.best_psi <= sp.psi_accept * st.scale) {
+        stop = TLS_STOP_PSI_UP;
+      } else {
+        if (psi < st.best_psi) {
+          improve = 1;
+          st.best_k = k;
+          st.best_psi = psi;
+          st.best_s2 = sigma2;
+        }
+        if (!up && psi <= sp.tol * st.scale) stop = TLS_STOP_TOL;
+        else if (k > sp.max_rqi) stop = TLS_STOP_MAX_RQI;
+      }
+    }
+    st.prev_psi = psi;
+    s_dec[0] = stop;
+    s_dec[1] = improve;
+  }
+  __syncthreads();
+  if (s_dec[1])
+    for (int c = threadIdx.x; c < npb; c += kCT) a.xbest[P.offV + c] = x[c];
+  if (s_dec[0]) {
+    if (threadIdx.x == 0) {
+      st.stop = s_dec[0];
+      st.active = 0;
+    }
+    return;
+  }
+  for (int c = threadIdx.x; c < npb; c += kCT) {
+    ys[c] = (T)(-f[c] * dinv[c]);
+    ys[npb + c] = (T)(x[c] * dinv[c]);
+  }
+  if (threadIdx.x == 0) {
+    st.cg_sigma2 = sigma2;
+    st.cg_tol2 = sp.cg_fixed ? 0.0 : sp.cg_tol * sp.cg_tol;
+  }
+  pcg_start<T>(a, P, st, 2, ys, vs, dsh);
+}
+
+// One PCGTLS step after the pass t = A q (Alg. 3, operator with A):
+// delta = ||t||^2 - sigma^2 ||q||^2, alpha = eta / delta, w += alpha q,
+// s -= alpha R^{-T}(A^T t - sigma^2 q), eta' = ||s||^2, beta = eta'/eta, p = s + beta p,
+// q = R^{-1} p.
+template <typename T>
+__global__ void __launch_bounds__(kCT) pcg_post_kernel(BArrays a, const int* list) {
+  const int pi = list[blockIdx.x];
+  BState& st = a.st[pi];
+  if (!st.active) return;
+  const int nr = st.nr;
+  if (st.done[0] && (nr < 2 || st.done[1])) return;
+  const BProb P = a.probs[pi];
+  const int npb = (int)P.npb, lda = (int)P.lda;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* ys = reinterpret_cast<T*>(smem);
+  T* vs = ys + 2 * kMaxN;
+  T* at = vs + 2 * kMaxN;
+  __shared__ double dsh[32 * 4];
+  __shared__ T s_alpha[2];
+  __shared__ int s_ok[2];
+  const T* W = static_cast<const T*>(a.W) + P.offM;
+  const T* WT = static_cast<const T*>(a.WT) + P.offM;
+  const T* dv = dinv_of<T>(a) + P.offV;
+  T* s = PVec::at<T>(a.vs, P);
+  T* p = PVec::at<T>(a.vp, P);
+  T* q = PVec::at<T>(a.vq, P);
+  T* w = PVec::at<T>(a.vw, P);
+  const T* part = static_cast<const T*>(a.partU);
+  // sum of the tile partials of A^T t (per right-hand side) and ||t||^2
+  for (int e = threadIdx.x; e < nr * npb; e += kCT) {
+    const int r = e / npb, c = e - r * npb;
+    T t0 = T(0), t1 = T(0);
+    if (c < lda) {
+      const T* base = part + P.poff * nr + (int64_t)r * lda + c;
+      const int64_t step = (int64_t)lda * nr;
+      int i = 0;
+      for (; i + 1 < P.ntiles; i += 2) {
+        t0 += base[(int64_t)i * step];
+        t1 += base[(int64_t)(i + 1) * step];
+      }
+      if (i < P.ntiles) t0 += base[(int64_t)i * step];
+    }
+    at[e] = t0 + t1;
+  }
+  double tt[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < P.ntiles; i += kCT) {
+    tt[0] += a.spart[(int64_t)(P.tile0 + i) * 4 + 0];
+    tt[1] += a.spart[(int64_t)(P.tile0 + i) * 4 + 1];
+  }
+  bsum<double, 2>(tt, dsh);
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < 2; ++r) {
+      s_ok[r] = 0;
+      s_alpha[r] = T(0);
+      if (r < nr && !st.done[r]) {
+        const double delta = tt[r] - st.cg_sigma2 * st.qq[r];
+        st.delta[r] = delta;
+        if (delta > 0.0) {
+          const double alpha = st.eta[r] / delta;
+          st.alpha[r] = alpha;
+          s_alpha[r] = (T)alpha;
+          s_ok[r] = 1;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const T sig2 = (T)st.cg_sigma2;
+  for (int e = threadIdx.x; e < nr * npb; e += kCT) {
+    const int r = e / npb, c = e - r * npb;
+    T yv = T(0);
+    if (s_ok[r]) {
+      const T qv = q[e];
+      w[e] = fma(s_alpha[r], qv, w[e]);
+      yv = (at[e] - sig2 * qv) * dv[c];
+    }
+    ys[e] = yv;
+  }
+  __syncthreads();
+  gemv_lower<T>(WT, npb, ys, vs, nr);
+  __syncthreads();
+  T el[2] = {T(0), T(0)};
+  for (int e = threadIdx.x; e < nr * npb; e += kCT) {
+    const int r = e / npb;
+    T sv = s[e];
+    if (s_ok[r]) {
+      sv = sv - s_alpha[r] * vs[e];
+      s[e] = sv;
+    }
+    el[r] = fma(sv, sv, el[r]);
+  }
+  double eta2[2] = {(double)el[0], (double)el[1]};
+  bsum<double, 2>(eta2, dsh);
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < nr; ++r) {
+      if (st.done[r]) continue;
+      if (!(st.delta[r] > 0.0)) {
+        st.done[r] = 1;
+        st.not_spd[r] = (st.delta[r] < 0.0) ? 1 : 0;
+      } else {
+        const double en = eta2[r];
+        st.beta[r] = en / st.eta[r];
+        st.eta[r] = en;
+        st.iters[r] += 1;
+        if (en == 0.0 || (st.cg_tol2 > 0.0 && en <= st.cg_tol2 * st.eta0[r])) st.done[r] = 1;
+      }
+    }
+  }
+  __syncthreads();
+  const T b0 = (T)st.beta[0], b1 = (T)st.beta[1];
+  for (int e = threadIdx.x; e < nr * npb; e += kCT) {
+    const T pv = s[e] + (e < npb ? b0 : b1) * p[e];
+    p[e] = pv;
+    ys[e] = pv;
+  }
+  __syncthreads();
+  gemv_upper<T>(W, npb, ys, vs, nr);
+  __syncthreads();
+  T qp[4] = {T(0), T(0), T(0), T(0)};
+  for (int e = threadIdx.x; e < nr * npb; e += kCT) {
+    const int r = e / npb, c = e - r * npb;
+    const T qv = vs[e] * dv[c];
+    q[e] = qv;
+    qp[r] = fma(qv, qv, qp[r]);
+    qp[2 + r] = fma(ys[e], ys[e], qp[2 + r]);
+  }
+  double qd[4] = {(double)qp[0], (double)qp[1], (double)qp[2], (double)qp[3]};
+  bsum<double, 4>(qd, dsh);
+  if (threadIdx.x == 0) {
+    st.qq[0] = qd[0];
+    st.qq[1] = qd[1];
+    st.pp[0] = qd[2];
+    st.pp[1] = qd[3];
+  }
+}
+
+// x_0 = w (the LS solution of the sigma^2 = 0 solve), ||x_0||^2
+template <typename T>
+__global__ void __launch_bounds__(kCT) ls_finish_kernel(BArrays a, const int* list) {
+  const int pi = list[blockIdx.x];
+  BState& st = a.st[pi];
+  if (!st.active) return;
+  const BProb P = a.probs[pi];
+  const T* w = PVec::at<T>(a.vw, P);
+  __shared__ double dsh[32];
+  double xs[1] = {0.0};
+  for (int c = threadIdx.x; c < P.npb; c += kCT) {
+    const double xn = (c < P.n) ? (double)w[c] : 0.0;
+    a.x[P.offV + c] = xn;
+    xs[0] = fma(xn, xn, xs[0]);
+  }
+  bsum<double, 1>(xs, dsh);
+  if (threadIdx.x == 0) st.xx = xs[0];
+}
+
+// z = x + w_f, beta_k = (z^T f - g) / (z^T x + 1), x = z + beta_k u (Alg. 2), u = w_x
+template <typename T>
+__global__ void __launch_bounds__(kCT) rqi_update_kernel(BArrays a, const int* list) {
+  const int pi = list[blockIdx.x];
+  BState& st = a.st[pi];
+  if (!st.active) return;
+  const BProb P = a.probs[pi];
+  const int npb = (int)P.npb, n = (int)P.n;
+  const T* w = PVec::at<T>(a.vw, P);
+  double* x = a.x + P.offV;
+  const double* f = a.f + P.offV;
+  __shared__ double dsh[32 * 2];
+  double v[2] = {0.0, 0.0};
+  for (int c = threadIdx.x; c < n; c += kCT) {
+    const double z = x[c] + (double)w[c];
+    v[0] = fma(z, f[c], v[0]);
+    v[1] = fma(z, x[c], v[1]);
+  }
+  bsum<double, 2>(v, dsh);
+  const double betak = (v[0] - st.g) / (v[1] + 1.0);
+  __syncthreads();
+  double xs[1] = {0.0};
+  for (int c = threadIdx.x; c < npb; c += kCT) {
+    double xn = 0.0;
+    if (c < n) xn = fma(betak, (double)w[npb + c], x[c] + (double)w[c]);
+    x[c] = xn;
+    xs[0] = fma(xn, xn, xs[0]);
+  }
+  bsum<double, 1>(xs, dsh);
+  if (threadIdx.x == 0) {
+    st.betak = betak;
+    st.xx = xs[0];
+    st.cg_total += st.iters[0] + st.iters[1];
+    st.not_spd_any |= st.not_spd[0] | st.not_spd[1];
+  }
+}
+
+// number of active problems in out[0]; the sum of m n over them (entries of A a pass over the
+// active problems reads) in out[2..3] as one 64-bit count
+__global__ void count_active_kernel(BArrays a, const int* list, int cnt, int* out) {
+  int c = 0;
+  unsigned long long el = 0ull;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int pi = list[i];
+    if (a.st[pi].active) {
+      c += 1;
+      el += (unsigned long long)(a.probs[pi].m * a.probs[pi].n);
+    }
+  }
+  c = wsum(c);
+  el = wsum(el);
+  __shared__ int sh[32];
+  __shared__ unsigned long long she[32];
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = c;
+    she[threadIdx.x >> 5] = el;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    unsigned long long te = 0ull;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t += sh[w];
+      te += she[w];
+    }
+    out[0] = t;
+    *reinterpret_cast<unsigned long long*>(out + 2) = te;
+  }
+}
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+void launch_pass_colnorm(const BArrays& a, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  constexpr size_t sm = pass_smem<double, 1>();
+  static const bool once = [] { set_smem(pass_kernel<double, 1, kColnorm>, sm); return true; }();
+  (void)once;
+  pass_kernel<double, 1, kColnorm><<<ntiles, kPT, sm, s>>>(a);
+  count_launch();
+}
+
+void launch_colnorm_post(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
+  if (cnt <= 0) return;
+  colnorm_post_kernel<<<cnt, kCT, 0, s>>>(a, list);
+  count_launch();
+}
+
+void launch_pass_resid(const BArrays& a, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  constexpr size_t sm = pass_smem<double, 1>();
+  static const bool once = [] { set_smem(pass_kernel<double, 1, kResid>, sm); return true; }();
+  (void)once;
+  pass_kernel<double, 1, kResid><<<ntiles, kPT, sm, s>>>(a);
+  count_launch();
+}
+
+template <typename T>
+void launch_pass_pcg(const BArrays& a, int ntiles, int nr, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  if (nr == 2) {
+    constexpr size_t sm = pass_smem<T, 2>();
+    static const bool once = [] { set_smem(pass_kernel<T, 2, kPcg>, sm); return true; }();
+    (void)once;
+    pass_kernel<T, 2, kPcg><<<ntiles, kPT, sm, s>>>(a);
+  } else {
+    constexpr size_t sm = pass_smem<T, 1>();
+    static const bool once = [] { set_smem(pass_kernel<T, 1, kPcg>, sm); return true; }();
+    (void)once;
+    pass_kernel<T, 1, kPcg><<<ntiles, kPT, sm, s>>>(a);
+  }
+  count_launch();
+}
+
+template <typename C>
+void launch_gram(const BArrays& a, const int4* gtiles, int ngt, cudaStream_t s) {
+  if (ngt <= 0) return;
+  gram_kernel<C><<<ngt, 256, 0, s>>>(a, gtiles);
+  count_launch();
+}
+
+template <typename C>
+void launch_chol(const BArrays& a, const int* list, int cnt, const double* shift, int* info,
+                 cudaStream_t s) {
+  if (cnt <= 0) return;
+  constexpr size_t sm = sizeof(C) * 4 * kNB * kLd;
+  static const bool once = [] { set_smem(chol_kernel<C>, sm); return true; }();
+  (void)once;
+  chol_kernel<C><<<cnt, kCT, sm, s>>>(a, list, shift, info);
+  count_launch();
+}
+
+template <typename C, typename T>
+void launch_trtri(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
+  if (cnt <= 0) return;
+  constexpr size_t sm = sizeof(T) * 4 * kNB * kLd;
+  static const bool once = [] { set_smem(trtri_kernel<C, T>, sm); return true; }();
+  (void)once;
+  trtri_kernel<C, T><<<cnt, kCT, sm, s>>>(a, list);
+  count_launch();
+}
+
+template <typename T>
+void launch_solve_init(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
+  if (cnt <= 0) return;
+  solve_init_kernel<T><<<cnt, kCT, 0, s>>>(a, list);
+  count_launch();
+}
+
+template <typename T>
+void launch_resid_post(const BArrays& a, const int* list, int cnt, int mode,
+                       const SolveParams& sp, cudaStream_t s) {
+  if (cnt <= 0) return;
+  constexpr size_t sm = post_smem<T>() + sizeof(double) * kMaxN;
+  static const bool once = [] { set_smem(resid_post_kernel<T>, sm); return true; }();
+  (void)once;
+  resid_post_kernel<T><<<cnt, kCT, sm, s>>>(a, list, mode, sp);
+  count_launch();
+}
+
+template <typename T>
+void launch_pcg_post(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
+  if (cnt <= 0) return;
+  constexpr size_t sm = post_smem<T>();
+  static const bool once = [] { set_smem(pcg_post_kernel<T>, sm); return true; }();
+  (void)once;
+  pcg_post_kernel<T><<<cnt, kCT, sm, s>>>(a, list);
+  count_launch();
+}
+
+template <typename T>
+void launch_ls_finish(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
+  if (cnt <= 0) return;
+  ls_finish_kernel<T><<<cnt, kCT, 0, s>>>(a, list);
+  count_launch();
+}
+
+template <typename T>
+void launch_rqi_update(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
+  if (cnt <= 0) return;
+  rqi_update_kernel<T><<<cnt, kCT, 0, s>>>(a, list);
+  count_launch();
+}
+
+void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, cudaStream_t s) {
+  count_active_kernel<<<1, 1024, 0, s>>>(a, list, cnt, out);
+  count_launch();
+}
+
+template void launch_pass_pcg<float>(const BArrays&, int, int, cudaStream_t);
+template void launch_pass_pcg<double>(const BArrays&, int, int, cudaStream_t);
+template void launch_gram<float>(const BArrays&, const int4*, int, cudaStream_t);
+template void launch_gram<double>(const BArrays&, const int4*, int, cudaStream_t);
+template void launch_chol<float>(const BArrays&, const int*, int, const double*, int*, cudaStream_t);
+template void launch_chol<double>(const BArrays&, const int*, int, const double*, int*, cudaStream_t);
+template void launch_trtri<float, float>(const BArrays&, const int*, int, cudaStream_t);
+template void launch_trtri<double, float>(const BArrays&, const int*, int, cudaStream_t);
+template void launch_trtri<double, double>(const BArrays&, const int*, int, cudaStream_t);
+template void launch_trtri<float, double>(const BArrays&, const int*, int, cudaStream_t);
+#define TLS_BI(T)                                                                                 \
+  template void launch_solve_init<T>(const BArrays&, const int*, int, cudaStream_t);              \
+  template void launch_resid_post<T>(const BArrays&, const int*, int, int, const SolveParams&,    \
+                                     cudaStream_t);                                               \
+  template void launch_pcg_post<T>(const BArrays&, const int*, int, cudaStream_t);                \
+  template void launch_ls_finish<T>(const BArrays&, const int*, int, cudaStream_t);               \
+  template void launch_rqi_update<T>(const BArrays&, const int*, int, cudaStream_t);
+TLS_BI(float)
+TLS_BI(double)
+#undef TLS_BI
+
+}  // namespace bat
+}  // namespace tls

@@ -135,15 +135,32 @@ tls_status cuda_status(tls_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_status(ctx, e_, what);        \
   } while (0)
 
-void* dev_alloc(tls_ctx* c, size_t bytes) {
+}  // namespace
+
+namespace tls {
+void* hook_alloc(size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
   void* p = nullptr;
   if (g_alloc) {
-    p = g_alloc((uint64_t)bytes, (void*)c->stream, g_alloc_user);
+    p = g_alloc((uint64_t)bytes, (void*)s, g_alloc_user);
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     p = nullptr;
   }
+  return p;
+}
+void hook_free(void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (g_free) g_free(p, (uint64_t)bytes, (void*)s, g_alloc_user);
+  else cudaFree(p);
+}
+}  // namespace tls
+
+namespace {
+
+void* dev_alloc(tls_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = tls::hook_alloc(bytes, c->stream);
   if (p) c->bufs.push_back({p, bytes});
   return p;
 }
@@ -152,8 +169,7 @@ void dev_free(tls_ctx* c, void* p) {
   if (!p) return;
   for (size_t i = 0; i < c->bufs.size(); ++i) {
     if (c->bufs[i].ptr == p) {
-      if (g_free) g_free(p, (uint64_t)c->bufs[i].bytes, (void*)c->stream, g_alloc_user);
-      else cudaFree(p);
+      tls::hook_free(p, c->bufs[i].bytes, c->stream);
       c->bufs.erase(c->bufs.begin() + (long)i);
       return;
     }

@@ -1,0 +1,696 @@
+// C ABI of the packed batched path (include/tls.h, tls_batch_*): many dense TLS problems of
+// uneven sizes solved together by RQI-PCGTLS (Alg. 2 / Alg. 4), each phase one launch for the
+// whole batch (kernels in k_batch.cu). The host only sequences the phases, runs the shift ladder
+// of the factorisation and the precision fallback, and reads one counter per RQI step.
+#include "../../include/tls.h"
+#include "../../include/tls_debug.h"
+#include "tls_batch_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using tls::Prec;
+using namespace tls::bat;
+
+struct tls_batch {
+  int count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<std::pair<void*, size_t>> bufs;
+  std::vector<BProb> hp;
+  std::vector<BTile> ht;
+  std::vector<int4> hgram;          // Gram tiles of every problem
+  std::vector<int> gram0;           // first Gram tile of each problem
+  std::vector<double> hshift;
+  std::vector<int> hinfo, shifts, fail_pivot, fallbacks, broke;
+  std::vector<tls_prec> uf_used;
+  BArrays a{};
+  BProb* dprobs = nullptr;
+  BTile* dtiles = nullptr;
+  BState* dst = nullptr;
+  int4* dgram = nullptr;
+  int* dlist = nullptr;             // problem list of the current launch sequence
+  double* dshift = nullptr;
+  int* dinfo = nullptr;
+  int* dcount = nullptr;
+  int* hcount = nullptr;            // pinned
+  int ntiles = 0;
+  Prec u = Prec::FP32;
+  bool factored = false;
+  tls_options opt{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double t_factor_ms = 0.0;
+  // per-class kernel timing (tls_batch_profile_enable): event pairs around every launch
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  std::vector<std::pair<int, size_t>> marks;
+  int64_t prof_cnt[TLS_PROF_NCLASSES] = {};
+  double prof_ms[TLS_PROF_NCLASSES] = {};
+  int64_t prof_elems[TLS_PROF_NCLASSES] = {};   // entries of A read by the pass launches
+};
+
+namespace {
+
+void set_err(tls_batch* bt, const std::string& s) { bt->err = s; }
+
+void* balloc(tls_batch* bt, size_t bytes) {
+  void* p = tls::hook_alloc(bytes, bt->stream);
+  if (p) bt->bufs.push_back({p, bytes});
+  return p;
+}
+
+tls_status cuda_st(tls_batch* bt, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TLS_OK;
+  set_err(bt, std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? TLS_ERR_OOM : TLS_ERR_CUDA;
+}
+
+#define BT_CK(call)                                           \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_st(bt, e_, #call);     \
+  } while (0)
+#define BT_CK_LAUNCH(what)                                    \
+  do {                                                        \
+    cudaError_t e_ = cudaGetLastError();                      \
+    if (e_ != cudaSuccess) return cuda_st(bt, e_, what);      \
+  } while (0)
+
+int64_t rup(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// Row tiles of roughly `target` bytes of FP32 data (at least one row)
+int64_t rows_per_tile(int64_t lda) {
+  const int64_t target = 64 * 1024;
+  return std::max<int64_t>(1, target / (lda * 4));
+}
+
+double unit_roundoff(Prec p) {
+  switch (p) {
+    case Prec::FP16: return std::ldexp(1.0, -11);
+    case Prec::BF16: return std::ldexp(1.0, -8);
+    case Prec::FP32: return std::ldexp(1.0, -24);
+    default: return std::ldexp(1.0, -53);
+  }
+}
+
+cudaEvent_t pool_event(tls_batch* bt) {
+  if (bt->evused == bt->evpool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    bt->evpool.push_back(e);
+  }
+  return bt->evpool[bt->evused++];
+}
+
+// Brackets the launches of one scope with an event pair when profiling is on.
+struct BProfScope {
+  tls_batch* bt;
+  int cls;
+  size_t i0 = 0;
+  bool on = false;
+  BProfScope(tls_batch* b, int c) : bt(b), cls(c) {
+    if (!bt->prof) return;
+    cudaEvent_t e = pool_event(bt);
+    if (!e) return;
+    i0 = bt->evused - 1;
+    on = cudaEventRecord(e, bt->stream) == cudaSuccess;
+  }
+  ~BProfScope() {
+    if (!on) return;
+    cudaEvent_t e = pool_event(bt);
+    if (!e || cudaEventRecord(e, bt->stream) != cudaSuccess) return;
+    bt->marks.push_back({cls, i0});
+  }
+};
+
+void prof_collect(tls_batch* bt) {
+  if (!bt->prof || bt->marks.empty()) {
+    bt->evused = 0;
+    bt->marks.clear();
+    return;
+  }
+  cudaStreamSynchronize(bt->stream);
+  for (auto& mk : bt->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, bt->evpool[mk.second], bt->evpool[mk.second + 1]) ==
+        cudaSuccess) {
+      bt->prof_cnt[mk.first] += 1;
+      bt->prof_ms[mk.first] += ms;
+    }
+  }
+  bt->marks.clear();
+  bt->evused = 0;
+}
+
+void destroy(tls_batch* bt) {
+  if (!bt) return;
+  if (bt->stream) cudaStreamSynchronize(bt->stream);
+  for (cudaEvent_t e : bt->evpool) cudaEventDestroy(e);
+  for (auto& b : bt->bufs) tls::hook_free(b.first, b.second, bt->stream);
+  if (bt->hcount) cudaFreeHost(bt->hcount);
+  if (bt->ev0) cudaEventDestroy(bt->ev0);
+  if (bt->ev1) cudaEventDestroy(bt->ev1);
+  if (bt->own_stream && bt->stream) cudaStreamDestroy(bt->stream);
+  delete bt;
+}
+
+tls_status upload_list(tls_batch* bt, const std::vector<int>& L) {
+  BT_CK(cudaMemcpyAsync(bt->dlist, L.data(), sizeof(int) * L.size(), cudaMemcpyHostToDevice,
+                        bt->stream));
+  return TLS_OK;
+}
+
+// Gram + shift ladder + triangular inverse for the problems in L at factor precision p;
+// problems whose every shift breaks down move on to the next precision.
+template <typename T>
+tls_status factor_list(tls_batch* bt, std::vector<int> L, Prec p) {
+  cudaStream_t st = bt->stream;
+  while (!L.empty()) {
+    for (int i : L) bt->hp[(size_t)i].prec = (int)p;
+    BT_CK(cudaMemcpyAsync(bt->dprobs, bt->hp.data(), sizeof(BProb) * bt->hp.size(),
+                          cudaMemcpyHostToDevice, st));
+    // Gram tiles of the listed problems (a contiguous range per problem in hgram)
+    std::vector<int4> gl;
+    for (int i : L) {
+      const int64_t nbk = bt->hp[(size_t)i].npb / kNB;
+      const int64_t g0 = bt->gram0[(size_t)i];
+      for (int64_t k = 0; k < nbk * (nbk + 1) / 2; ++k) gl.push_back(bt->hgram[(size_t)(g0 + k)]);
+    }
+    BT_CK(cudaMemcpyAsync(bt->dgram, gl.data(), sizeof(int4) * gl.size(), cudaMemcpyHostToDevice,
+                          st));
+    const bool c64 = (p == Prec::FP64);
+    {
+      BProfScope pr(bt, TLS_PROF_GRAM);
+      if (c64) launch_gram<double>(bt->a, bt->dgram, (int)gl.size(), st);
+      else launch_gram<float>(bt->a, bt->dgram, (int)gl.size(), st);
+    }
+    BT_CK_LAUNCH("batched Gram");
+    // shift ladder (the diagonal perturbation of low-precision Cholesky)
+    const bool low = (p == Prec::FP16 || p == Prec::BF16);
+    const int first = (low && bt->opt.shift_first) ? 1 : 0;
+    const int max_shift = std::max(0, bt->opt.max_shifts);
+    const double u = unit_roundoff(p);
+    std::vector<int> pending = L, ok;
+    for (int sh = first; sh <= max_shift + first && !pending.empty(); ++sh) {
+      const double shift = (sh == 0) ? 0.0 : 2.0 * u * std::pow(4.0, sh - 1);
+      for (int i : pending) bt->hshift[(size_t)i] = shift;
+      BT_CK(cudaMemcpyAsync(bt->dshift, bt->hshift.data(), sizeof(double) * bt->count,
+                            cudaMemcpyHostToDevice, st));
+      tls_status s = upload_list(bt, pending);
+      if (s != TLS_OK) return s;
+      {
+        BProfScope pr(bt, TLS_PROF_CHOL);
+        if (c64)
+          launch_chol<double>(bt->a, bt->dlist, (int)pending.size(), bt->dshift, bt->dinfo, st);
+        else
+          launch_chol<float>(bt->a, bt->dlist, (int)pending.size(), bt->dshift, bt->dinfo, st);
+      }
+      BT_CK_LAUNCH("batched Cholesky");
+      BT_CK(cudaMemcpyAsync(bt->hinfo.data(), bt->dinfo, sizeof(int) * bt->count,
+                            cudaMemcpyDeviceToHost, st));
+      BT_CK(cudaStreamSynchronize(st));
+      std::vector<int> failed;
+      for (int i : pending) {
+        const int inf = bt->hinfo[(size_t)i];
+        if (inf == 0) {
+          ok.push_back(i);
+        } else {
+          failed.push_back(i);
+          bt->shifts[(size_t)i] += 1;
+          bt->fail_pivot[(size_t)i] = inf - 1;
+        }
+      }
+      pending.swap(failed);
+    }
+    if (!ok.empty()) {
+      tls_status s = upload_list(bt, ok);
+      if (s != TLS_OK) return s;
+      BProfScope pr(bt, TLS_PROF_TRTRI);
+      if (c64) launch_trtri<double, T>(bt->a, bt->dlist, (int)ok.size(), st);
+      else launch_trtri<float, T>(bt->a, bt->dlist, (int)ok.size(), st);
+      BT_CK_LAUNCH("batched triangular inverse");
+      for (int i : ok) bt->uf_used[(size_t)i] = (tls_prec)(int)p;
+    }
+    if (pending.empty()) break;
+    if (p == Prec::FP64) {
+      for (int i : pending) bt->broke[(size_t)i] = 1;
+      break;
+    }
+    p = (p == Prec::FP32) ? Prec::FP64 : Prec::FP32;
+    L = pending;
+  }
+  return TLS_OK;
+}
+
+// Lock-step RQI-PCGTLS over the problems in L (Alg. 2 with the PCGTLS of Alg. 3 / 4).
+template <typename T>
+tls_status solve_list(tls_batch* bt, const std::vector<int>& L, const SolveParams& sp) {
+  cudaStream_t st = bt->stream;
+  const int cnt = (int)L.size();
+  if (cnt == 0) return TLS_OK;
+  tls_status s = upload_list(bt, L);
+  if (s != TLS_OK) return s;
+  const int* dl = bt->dlist;
+  const BArrays& a = bt->a;
+  const int nt = bt->ntiles;
+  int64_t elems = 0;   // entries of A of the active problems
+  for (int i : L) elems += bt->hp[(size_t)i].m * bt->hp[(size_t)i].n;
+  auto resid = [&](int mode) {
+    {
+      BProfScope pr(bt, TLS_PROF_RESID_PASS);
+      launch_pass_resid(a, nt, st);
+      if (bt->prof) bt->prof_elems[TLS_PROF_RESID_PASS] += elems;
+    }
+    BProfScope pr(bt, TLS_PROF_RESID_REDUCE);
+    launch_resid_post<T>(a, dl, cnt, mode, sp, st);
+  };
+  auto pcg_step = [&](int nr) {
+    {
+      BProfScope pr(bt, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
+      launch_pass_pcg<T>(a, nt, nr, st);
+      if (bt->prof) bt->prof_elems[nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1] += elems;
+    }
+    BProfScope pr(bt, TLS_PROF_PCG_REDUCE);
+    launch_pcg_post<T>(a, dl, cnt, st);
+  };
+  {
+    BProfScope pr(bt, TLS_PROF_VEC);
+    launch_solve_init<T>(a, dl, cnt, st);
+  }
+  // line 1: LS start, x = 0 residual (f = -A^T b), PCGTLS with sigma^2 = 0
+  resid(kResidLs);
+  for (int j = 0; j < std::max(1, bt->opt.ls_iters); ++j) pcg_step(1);
+  {
+    BProfScope pr(bt, TLS_PROF_VEC);
+    launch_ls_finish<T>(a, dl, cnt, st);
+  }
+  // lines 2-5: sigma_0^2 and the inverse-iteration step
+  resid(kResidStart);
+  BT_CK_LAUNCH("batched solve start");
+  for (int k = 1; k <= sp.max_rqi + 2; ++k) {
+    resid(kResidRqi);
+    {
+      BProfScope pr(bt, TLS_PROF_VEC);
+      launch_count_active(a, dl, cnt, bt->dcount, st);
+    }
+    BT_CK_LAUNCH("batched residual");
+    BT_CK(cudaMemcpyAsync(bt->hcount, bt->dcount, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    BT_CK(cudaStreamSynchronize(st));
+    if (bt->hcount[0] == 0) break;
+    unsigned long long el = 0ull;
+    std::memcpy(&el, bt->hcount + 2, sizeof(el));
+    elems = (int64_t)el;
+    const int steps = sp.cg_fixed ? (k + 1) : std::max(1, sp.cg_max);
+    for (int j = 0; j < steps; ++j) pcg_step(2);
+    {
+      BProfScope pr(bt, TLS_PROF_VEC);
+      launch_rqi_update<T>(a, dl, cnt, st);
+    }
+    BT_CK_LAUNCH("batched PCGTLS");
+  }
+  return TLS_OK;
+}
+
+template <typename T>
+tls_status batch_solve_impl(tls_batch* bt, double tol, int max_rqi, std::vector<BState>& hst) {
+  const tls_options& o = bt->opt;
+  SolveParams sp{};
+  sp.tol = tol;
+  sp.psi_accept = o.psi_accept;
+  sp.max_rqi = max_rqi;
+  sp.psi_rule_ge = o.psi_rule_ge;
+  sp.cg_fixed = o.cg_fixed;
+  sp.cg_max = o.cg_max;
+  sp.cg_tol = o.cg_tol;
+  std::vector<int> L;
+  for (int i = 0; i < bt->count; ++i)
+    if (!bt->broke[(size_t)i]) L.push_back(i);
+  for (int round = 0; round < 3 && !L.empty(); ++round) {
+    tls_status s = solve_list<T>(bt, L, sp);
+    if (s != TLS_OK) return s;
+    BT_CK(cudaMemcpyAsync(hst.data(), bt->dst, sizeof(BState) * hst.size(),
+                          cudaMemcpyDeviceToHost, bt->stream));
+    BT_CK(cudaStreamSynchronize(bt->stream));
+    if (!o.fallback || round == 2) break;
+    // precision fallback: a problem that ended on max_rqi gets a factor one precision up
+    std::vector<int> to32, to64;
+    for (int i : L) {
+      if (hst[(size_t)i].stop != TLS_STOP_MAX_RQI) continue;
+      const tls_prec uf = bt->uf_used[(size_t)i];
+      if (uf == TLS_FP64) continue;
+      (uf == TLS_FP32 ? to64 : to32).push_back(i);
+      bt->fallbacks[(size_t)i] += 1;
+    }
+    if (!to32.empty()) {
+      tls_status s2 = factor_list<T>(bt, to32, Prec::FP32);
+      if (s2 != TLS_OK) return s2;
+    }
+    if (!to64.empty()) {
+      tls_status s2 = factor_list<T>(bt, to64, Prec::FP64);
+      if (s2 != TLS_OK) return s2;
+    }
+    L.clear();
+    for (int i : to32) if (!bt->broke[(size_t)i]) L.push_back(i);
+    for (int i : to64) if (!bt->broke[(size_t)i]) L.push_back(i);
+  }
+  return TLS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, const int64_t* n,
+                                  const double* const* A, const int64_t* lda,
+                                  const double* const* b, int on_device, void* stream) {
+  if (!out) return TLS_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || !m || !n || !A || !lda || !b) return TLS_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (m[i] < n[i] || n[i] < 1 || n[i] > TLS_BATCH_MAX_N || lda[i] < n[i] || !A[i] || !b[i] ||
+        m[i] > (int64_t)INT32_MAX)
+      return TLS_ERR_ARG;
+    if (!on_device) {
+      for (int64_t r = 0; r < m[i]; ++r)
+        for (int64_t c = 0; c < n[i]; ++c)
+          if (!std::isfinite(A[i][r * lda[i] + c])) return TLS_ERR_ARG;
+      for (int64_t r = 0; r < m[i]; ++r)
+        if (!std::isfinite(b[i][r])) return TLS_ERR_ARG;
+    }
+  }
+  tls_batch* bt = new tls_batch();
+  bt->count = count;
+  if (stream) {
+    bt->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete bt;
+      return TLS_ERR_CUDA;
+    }
+    bt->own_stream = true;
+  }
+  // layout
+  int64_t offA = 0, offB = 0, offV = 0, offM = 0, poff = 0, ngram = 0;
+  bt->hp.resize((size_t)count);
+  bt->gram0.resize((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    BProb& P = bt->hp[(size_t)i];
+    P.m = m[i];
+    P.n = n[i];
+    P.lda = rup(n[i], 4);
+    P.npb = rup(n[i], kNB);
+    P.offA = offA;
+    P.offB = offB;
+    P.offV = offV;
+    P.offM = offM;
+    P.poff = poff;
+    P.cfg = cfg_for(P.lda);
+    P.prec = (int)Prec::FP16;
+    const int64_t rpt = std::min<int64_t>(rows_per_tile(P.lda), P.m);
+    P.tile0 = (int)bt->ht.size();
+    for (int64_t r = 0; r < P.m; r += rpt) {
+      BTile t{};
+      t.prob = i;
+      t.row0 = (int)r;
+      t.rows = (int)std::min<int64_t>(rpt, P.m - r);
+      bt->ht.push_back(t);
+    }
+    P.ntiles = (int)bt->ht.size() - P.tile0;
+    poff += (int64_t)P.ntiles * P.lda;
+    offA += rup(P.m * P.lda, 64);
+    offB += rup(P.m, 32);
+    offV += P.npb;
+    offM += P.npb * P.npb;
+    const int nbk = (int)(P.npb / kNB);
+    bt->gram0[(size_t)i] = (int)ngram;
+    for (int bi = 0; bi < nbk; ++bi)
+      for (int bj = bi; bj < nbk; ++bj) bt->hgram.push_back(make_int4(i, bi, bj, 0));
+    ngram += (int64_t)nbk * (nbk + 1) / 2;
+  }
+  bt->ntiles = (int)bt->ht.size();
+  const size_t vbytes = sizeof(double) * (size_t)offV;
+  BArrays& a = bt->a;
+  bt->dprobs = static_cast<BProb*>(balloc(bt, sizeof(BProb) * count));
+  bt->dtiles = static_cast<BTile*>(balloc(bt, sizeof(BTile) * bt->ht.size()));
+  bt->dst = static_cast<BState*>(balloc(bt, sizeof(BState) * count));
+  bt->dgram = static_cast<int4*>(balloc(bt, sizeof(int4) * (size_t)std::max<int64_t>(ngram, 1)));
+  bt->dlist = static_cast<int*>(balloc(bt, sizeof(int) * count));
+  bt->dshift = static_cast<double*>(balloc(bt, sizeof(double) * count));
+  bt->dinfo = static_cast<int*>(balloc(bt, sizeof(int) * count));
+  bt->dcount = static_cast<int*>(balloc(bt, 4 * sizeof(int)));
+  double* A64 = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)offA));
+  a.A32 = static_cast<float*>(balloc(bt, sizeof(float) * (size_t)offA));
+  double* bb = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)offB));
+  a.d = static_cast<double*>(balloc(bt, vbytes));
+  a.dinv = static_cast<double*>(balloc(bt, vbytes));
+  a.dinv32 = static_cast<float*>(balloc(bt, sizeof(float) * (size_t)offV));
+  a.x = static_cast<double*>(balloc(bt, vbytes));
+  a.xbest = static_cast<double*>(balloc(bt, vbytes));
+  a.f = static_cast<double*>(balloc(bt, vbytes));
+  a.vw = balloc(bt, 2 * vbytes);
+  a.vs = balloc(bt, 2 * vbytes);
+  a.vp = balloc(bt, 2 * vbytes);
+  a.vq = balloc(bt, 2 * vbytes);
+  a.H = balloc(bt, sizeof(double) * (size_t)offM);
+  a.R = balloc(bt, sizeof(double) * (size_t)offM);
+  a.W = balloc(bt, sizeof(double) * (size_t)offM);
+  a.WT = balloc(bt, sizeof(double) * (size_t)offM);
+  a.partU = balloc(bt, sizeof(double) * 2 * (size_t)std::max<int64_t>(poff, 1));
+  a.part64 = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)std::max<int64_t>(poff, 1)));
+  a.spart = static_cast<double*>(balloc(bt, sizeof(double) * 4 * bt->ht.size()));
+  if (!bt->dprobs || !bt->dtiles || !bt->dst || !bt->dgram || !bt->dlist || !bt->dshift ||
+      !bt->dinfo || !bt->dcount || !A64 || !a.A32 || !bb || !a.d || !a.dinv || !a.dinv32 ||
+      !a.x || !a.xbest || !a.f || !a.vw || !a.vs || !a.vp || !a.vq || !a.H || !a.R || !a.W ||
+      !a.WT || !a.partU || !a.part64 || !a.spart) {
+    destroy(bt);
+    return TLS_ERR_OOM;
+  }
+  a.A64 = A64;
+  a.b = bb;
+  a.probs = bt->dprobs;
+  a.tiles = bt->dtiles;
+  a.st = bt->dst;
+  cudaStream_t st = bt->stream;
+  cudaError_t e = cudaMallocHost(&bt->hcount, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&bt->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&bt->ev1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A64, 0, sizeof(double) * (size_t)offA, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->dst, 0, sizeof(BState) * count, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.H, 0, sizeof(double) * (size_t)offM, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.vw, 0, 2 * vbytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.vs, 0, 2 * vbytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.vp, 0, 2 * vbytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.vq, 0, 2 * vbytes, st);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    const BProb& P = bt->hp[(size_t)i];
+    e = cudaMemcpy2DAsync(A64 + P.offA, sizeof(double) * P.lda, A[i], sizeof(double) * lda[i],
+                          sizeof(double) * P.n, P.m, kind, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bb + P.offB, b[i], sizeof(double) * P.m, kind, st);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->dprobs, bt->hp.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->dtiles, bt->ht.data(), sizeof(BTile) * bt->ht.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    destroy(bt);
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? TLS_ERR_OOM : TLS_ERR_CUDA;
+  }
+  bt->hshift.assign((size_t)count, 0.0);
+  bt->hinfo.assign((size_t)count, 0);
+  bt->shifts.assign((size_t)count, 0);
+  bt->fail_pivot.assign((size_t)count, -1);
+  bt->fallbacks.assign((size_t)count, 0);
+  bt->broke.assign((size_t)count, 0);
+  bt->uf_used.assign((size_t)count, TLS_FP16);
+  // column norms d_j, ||A||_F^2, ||b||^2 and the FP32 working copy, for the whole batch
+  std::vector<int> all((size_t)count);
+  for (int i = 0; i < count; ++i) all[(size_t)i] = i;
+  if (upload_list(bt, all) != TLS_OK) {
+    destroy(bt);
+    return TLS_ERR_CUDA;
+  }
+  launch_pass_colnorm(a, bt->ntiles, st);
+  launch_colnorm_post(a, bt->dlist, count, st);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    destroy(bt);
+    return TLS_ERR_CUDA;
+  }
+  *out = bt;
+  return TLS_OK;
+}
+
+tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt) {
+  if (!bt || (int)u_f < 0 || (int)u_f > 3) return TLS_ERR_ARG;
+  tls_options o;
+  if (opt) o = *opt;
+  else tls_default_options(&o);
+  if (o.u != TLS_FP32 && o.u != TLS_FP64) return TLS_ERR_ARG;
+  if (!o.mode_A) {
+    set_err(bt, "the packed batch implements the A-explicit PCGTLS operator (mode_A = 1)");
+    return TLS_ERR_ARG;
+  }
+  bt->opt = o;
+  bt->u = (o.u == TLS_FP64) ? Prec::FP64 : Prec::FP32;
+  bt->factored = false;
+  std::fill(bt->shifts.begin(), bt->shifts.end(), 0);
+  std::fill(bt->fail_pivot.begin(), bt->fail_pivot.end(), -1);
+  std::fill(bt->fallbacks.begin(), bt->fallbacks.end(), 0);
+  std::fill(bt->broke.begin(), bt->broke.end(), 0);
+  std::vector<int> all((size_t)bt->count);
+  for (int i = 0; i < bt->count; ++i) all[(size_t)i] = i;
+  BT_CK(cudaEventRecord(bt->ev0, bt->stream));
+  tls_status s = (bt->u == Prec::FP64) ? factor_list<double>(bt, all, (Prec)(int)u_f)
+                                       : factor_list<float>(bt, all, (Prec)(int)u_f);
+  if (s != TLS_OK) return s;
+  BT_CK(cudaEventRecord(bt->ev1, bt->stream));
+  BT_CK(cudaEventSynchronize(bt->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, bt->ev0, bt->ev1);
+  bt->t_factor_ms = ms;
+  prof_collect(bt);
+  bt->factored = true;
+  for (int i = 0; i < bt->count; ++i)
+    if (bt->broke[(size_t)i]) {
+      set_err(bt, "Cholesky breakdown at every shift and precision for problem " +
+                      std::to_string(i));
+      return TLS_ERR_FACTOR_BREAKDOWN;
+    }
+  return TLS_OK;
+}
+
+tls_status tls_batch_solve(tls_batch* bt, double tol, int max_rqi, double* const* x,
+                           double* sigma, tls_info* infos, tls_status* per_problem) {
+  if (!bt || !x || !sigma || max_rqi < 0 || !(tol >= 0.0)) return TLS_ERR_ARG;
+  if (!bt->factored) {
+    set_err(bt, "tls_batch_solve called before tls_batch_factor");
+    return TLS_ERR_STATE;
+  }
+  std::vector<BState> hst((size_t)bt->count);
+  BT_CK(cudaEventRecord(bt->ev0, bt->stream));
+  tls_status s = (bt->u == Prec::FP64) ? batch_solve_impl<double>(bt, tol, max_rqi, hst)
+                                       : batch_solve_impl<float>(bt, tol, max_rqi, hst);
+  if (s != TLS_OK) return s;
+  BT_CK(cudaEventRecord(bt->ev1, bt->stream));
+  int64_t nv = 0;
+  for (const BProb& P : bt->hp) nv += P.npb;
+  std::vector<double> xb((size_t)nv);
+  BT_CK(cudaMemcpyAsync(xb.data(), bt->a.xbest, sizeof(double) * (size_t)nv,
+                        cudaMemcpyDeviceToHost, bt->stream));
+  BT_CK(cudaStreamSynchronize(bt->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, bt->ev0, bt->ev1);
+  prof_collect(bt);
+  tls_status first = TLS_OK;
+  for (int i = 0; i < bt->count; ++i) {
+    const BProb& P = bt->hp[(size_t)i];
+    const BState& S = hst[(size_t)i];
+    const tls_status si = bt->broke[(size_t)i] ? TLS_ERR_FACTOR_BREAKDOWN : TLS_OK;
+    if (per_problem) per_problem[i] = si;
+    if (si != TLS_OK && first == TLS_OK) first = si;
+    if (x[i]) std::memcpy(x[i], xb.data() + P.offV, sizeof(double) * (size_t)P.n);
+    sigma[i] = std::sqrt(std::max(S.best_s2, 0.0));
+    if (infos) {
+      tls_info& in = infos[i];
+      std::memset(&in, 0, sizeof(in));
+      in.stop_reason = S.stop;
+      in.rqi_steps = S.k;
+      in.best_k = S.best_k;
+      in.cg_iters = S.cg_total;
+      in.shifts = bt->shifts[(size_t)i];
+      in.not_spd = S.not_spd_any;
+      in.u_f_used = bt->uf_used[(size_t)i];
+      in.psi_final = S.best_psi;
+      in.sigma2 = S.best_s2;
+      in.shift = bt->hshift[(size_t)i];
+      in.t_factor_ms = bt->t_factor_ms;
+      in.t_solve_ms = ms;
+      in.fail_pivot = bt->fail_pivot[(size_t)i];
+      in.pass_variant[0] = in.pass_variant[1] = P.cfg;
+      in.n_psi = std::min(S.n_psi, 24);
+      for (int k = 0; k < in.n_psi; ++k) in.psi_hist[k] = S.psi_hist[k];
+      in.fallbacks = bt->fallbacks[(size_t)i];
+    }
+  }
+  return first;
+}
+
+void tls_batch_destroy(tls_batch* bt) { destroy(bt); }
+
+tls_status tls_batch_profile_enable(tls_batch* bt, int on) {
+  if (!bt) return TLS_ERR_ARG;
+  bt->prof = on != 0;
+  for (int k = 0; k < TLS_PROF_NCLASSES; ++k) {
+    bt->prof_cnt[k] = 0;
+    bt->prof_ms[k] = 0.0;
+    bt->prof_elems[k] = 0;
+  }
+  bt->marks.clear();
+  bt->evused = 0;
+  return TLS_OK;
+}
+
+tls_status tls_batch_profile_get(const tls_batch* bt, int cls, int64_t* count, double* ms) {
+  if (!bt || cls < 0 || cls >= TLS_PROF_NCLASSES) return TLS_ERR_ARG;
+  if (count) *count = bt->prof_cnt[cls];
+  if (ms) *ms = bt->prof_ms[cls];
+  return TLS_OK;
+}
+
+tls_status tls_batch_profile_elems(const tls_batch* bt, int cls, int64_t* elems) {
+  if (!bt || cls < 0 || cls >= TLS_PROF_NCLASSES || !elems) return TLS_ERR_ARG;
+  *elems = bt->prof_elems[cls];
+  return TLS_OK;
+}
+
+tls_status tls_batch_export_factor(tls_batch* bt, int i, double* R_host, double* d_host,
+                                   double* H_host) {
+  if (!bt || i < 0 || i >= bt->count) return TLS_ERR_ARG;
+  if (!bt->factored || bt->broke[(size_t)i]) return TLS_ERR_STATE;
+  const BProb& P = bt->hp[(size_t)i];
+  const int64_t n = P.n, npb = P.npb;
+  const bool c64 = bt->uf_used[(size_t)i] == TLS_FP64;
+  const size_t es = c64 ? 8 : 4;
+  std::vector<unsigned char> buf(es * (size_t)(npb * npb));
+  auto fetch = [&](const void* base, double* out, bool mirror) -> tls_status {
+    const unsigned char* src = static_cast<const unsigned char*>(base) + es * (size_t)P.offM;
+    BT_CK(cudaMemcpyAsync(buf.data(), src, buf.size(), cudaMemcpyDeviceToHost, bt->stream));
+    BT_CK(cudaStreamSynchronize(bt->stream));
+    for (int64_t r = 0; r < n; ++r)
+      for (int64_t c = 0; c < n; ++c) {
+        const int64_t rr = (mirror && c < r) ? c : r, cc = (mirror && c < r) ? r : c;
+        const size_t e = (size_t)(rr * npb + cc);
+        out[r * n + c] = c64 ? reinterpret_cast<const double*>(buf.data())[e]
+                             : (double)reinterpret_cast<const float*>(buf.data())[e];
+      }
+    return TLS_OK;
+  };
+  if (R_host) {
+    tls_status s = fetch(bt->a.R, R_host, false);
+    if (s != TLS_OK) return s;
+  }
+  if (H_host) {
+    tls_status s = fetch(bt->a.H, H_host, true);
+    if (s != TLS_OK) return s;
+  }
+  if (d_host) {
+    BT_CK(cudaMemcpyAsync(d_host, bt->a.d + P.offV, sizeof(double) * (size_t)n,
+                          cudaMemcpyDeviceToHost, bt->stream));
+    BT_CK(cudaStreamSynchronize(bt->stream));
+  }
+  return TLS_OK;
+}
+
+const char* tls_batch_last_error(const tls_batch* bt) { return bt ? bt->err.c_str() : ""; }
+
+}  // extern "C"

@@ -22,6 +22,10 @@ inline void count_launch(int k = 1) { g_launches.fetch_add((unsigned long long)k
 
 enum class Prec : int { FP16 = 0, BF16 = 1, FP32 = 2, FP64 = 3 };
 
+// Device allocation through the caller's allocator (tls_set_allocator) or cudaMalloc.
+void* hook_alloc(size_t bytes, cudaStream_t s);
+void hook_free(void* p, size_t bytes, cudaStream_t s);
+
 // Device scalars of one paired PCGTLS solve (Alg. 3), per right-hand side r in {0, 1}.
 struct PcgScalars {
   double eta[2];      // eta_j = ||s_j||^2

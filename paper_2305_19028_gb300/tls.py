@@ -28,7 +28,10 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_last_error", "tls_shape", "tls_set_allocator", "tls_export_factor",
            "tls_residual", "tls_pcgtls", "tls_precond", "tls_profile_enable", "tls_profile_get",
            "tls_kernel_launches", "tls_residual_noalloc", "tls_export_working_copy",
-           "tls_condition", "tls_factor_batched"]
+           "tls_condition", "tls_factor_batched", "tls_batch_create_dense", "tls_batch_factor",
+           "tls_batch_solve", "tls_batch_destroy", "tls_batch_last_error",
+           "tls_batch_export_factor", "tls_batch_profile_enable", "tls_batch_profile_get",
+           "tls_batch_profile_elems"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
@@ -107,6 +110,17 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_export_working_copy": (C.c_int, [v, C.POINTER(C.c_float)]),
         "tls_condition": (C.c_int, [v, C.c_int, _dp]),
         "tls_factor_batched": (C.c_int, [C.c_int, vp, C.c_int, C.POINTER(tls_options), _ip]),
+        "tls_batch_create_dense": (C.c_int, [vp, C.c_int, C.POINTER(i64), C.POINTER(i64), vp,
+                                             C.POINTER(i64), vp, C.c_int, v]),
+        "tls_batch_factor": (C.c_int, [v, C.c_int, C.POINTER(tls_options)]),
+        "tls_batch_solve": (C.c_int, [v, C.c_double, C.c_int, C.POINTER(_dp), _dp,
+                                      C.POINTER(tls_info), _ip]),
+        "tls_batch_destroy": (None, [v]),
+        "tls_batch_last_error": (C.c_char_p, [v]),
+        "tls_batch_export_factor": (C.c_int, [v, C.c_int, _dp, _dp, _dp]),
+        "tls_batch_profile_enable": (C.c_int, [v, C.c_int]),
+        "tls_batch_profile_get": (C.c_int, [v, C.c_int, C.POINTER(i64), _dp]),
+        "tls_batch_profile_elems": (C.c_int, [v, C.c_int, C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -359,6 +373,109 @@ def use_torch_allocator(enable: bool = True):
     a, f = ALLOC(_alloc), FREE(_free)
     _ALLOC_REFS = (a, f)
     lib.tls_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), None)
+
+
+class Batch:
+    """A packed batch of dense problems (n <= 512) solved together (tls_batch_* entry points).
+
+    problems: sequence of (A, b) host arrays, or pass device=True with torch CUDA tensors."""
+
+    def __init__(self, problems, stream=None):
+        lib = load()
+        k = len(problems)
+        self.k = k
+        self.shapes = []
+        self._keep = []
+        ms = (C.c_int64 * k)()
+        ns = (C.c_int64 * k)()
+        ld = (C.c_int64 * k)()
+        ap = (C.c_void_p * k)()
+        bp = (C.c_void_p * k)()
+        on_dev = 0
+        for i, (A, b) in enumerate(problems):
+            if hasattr(A, "is_cuda") and A.is_cuda:
+                on_dev = 1
+                m, n = A.shape
+                ms[i], ns[i], ld[i] = m, n, A.stride(0)
+                ap[i], bp[i] = A.data_ptr(), b.data_ptr()
+            else:
+                A, b = _f64(A), _f64(b)
+                m, n = A.shape
+                ms[i], ns[i], ld[i] = m, n, n
+                ap[i], bp[i] = A.ctypes.data, b.ctypes.data
+            self._keep.append((A, b))
+            self.shapes.append((m, n))
+        h = C.c_void_p()
+        st = lib.tls_batch_create_dense(C.byref(h), k, ms, ns, ap, ld, bp, on_dev,
+                                        C.c_void_p(stream) if stream else None)
+        self._keep = None
+        if st != 0:
+            raise TLSError(st, "tls_batch_create_dense")
+        self.h = h
+
+    def _err(self, st):
+        if st != 0:
+            raise TLSError(st, (load().tls_batch_last_error(self.h) or b"").decode())
+
+    def factor(self, u_f="fp16", **opt):
+        o = tls_default_options(**opt)
+        uf = PREC[u_f] if isinstance(u_f, str) else int(u_f)
+        self._err(load().tls_batch_factor(self.h, uf, C.byref(o)))
+
+    def solve(self, tol: float = 0.0, max_rqi: int = 10, check: bool = True):
+        """Returns (list of x, sigma array, list of info dicts, per-problem statuses)."""
+        k = self.k
+        xs = [np.zeros(n) for _, n in self.shapes]
+        xp = (_dp * k)(*[_ptr(x) for x in xs])
+        sig = np.zeros(k)
+        infos = (tls_info * k)()
+        per = (C.c_int * k)()
+        st = load().tls_batch_solve(self.h, tol, max_rqi, xp, _ptr(sig), infos, per)
+        if check:
+            self._err(st)
+        return xs, sig, [i.as_dict() for i in infos], list(per)
+
+    def profile(self, on: bool = True):
+        load().tls_batch_profile_enable(self.h, int(on))
+
+    def profile_get(self) -> dict:
+        """{class name: (launches, device ms, entries of A read)} for classes with launches."""
+        out = {}
+        for k, name in enumerate(PROF_CLASSES):
+            c = C.c_int64()
+            ms = C.c_double()
+            el = C.c_int64()
+            load().tls_batch_profile_get(self.h, k, C.byref(c), C.byref(ms))
+            load().tls_batch_profile_elems(self.h, k, C.byref(el))
+            if c.value:
+                out[name] = (c.value, ms.value, el.value)
+        return out
+
+    def export_factor(self, i: int):
+        """(R_H, d, H) of problem i, as tls_export_factor."""
+        n = self.shapes[i][1]
+        R = np.zeros((n, n))
+        H = np.zeros((n, n))
+        d = np.zeros(n)
+        self._err(load().tls_batch_export_factor(self.h, i, _ptr(R), _ptr(d), _ptr(H)))
+        return R, d, H
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().tls_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:
