@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TLS solves/s on GB300 at sigma rel err<=1e-10 vs FP64 oracle; mixed vs plain FP64"
 M_ROWS, N_COLS, D_LO, NOISE = 16384, 2048, 1e-3, 1e-4
 SIGMA_TOL, X_TOL = 1e-10, 1e-8
-SOLVE_TOL, MAX_RQI = 1e-16, 12
+SOLVE_TOL, MAX_RQI = 0.0, 12      # tol 0: the stopping rule of Sec. 3 (first increase of psi)
 WORKLOAD = f"dense_{M_ROWS}x{N_COLS}_uf16_u32_ur64"
 
 

@@ -74,8 +74,9 @@ typedef struct {
                        /* tensor cores, tcgen05)                                             */
   double psi_accept;   /* an increase psi_k > psi_{k-1} stops only once psi_{k-1} <=           */
                        /* psi_accept * (||A||_F^2 + ||b||^2); above it the increase is taken   */
-                       /* as a transient of the inexact inner solves (default 1e-12; a very   */
-                       /* large value gives the paper's rule exactly)                          */
+                       /* as a transient of the inexact inner solves (default 1e-15, near the */
+                       /* FP64 rounding level of psi; a very large value gives the paper's    */
+                       /* rule exactly)                                                        */
   int shift_first;     /* 1 (default): FP16/BF16 factors start from H + 2 u_f I, the diagonal  */
                        /* perturbation of low-precision Cholesky; 0: start unshifted and shift */
                        /* only after a breakdown                                              */

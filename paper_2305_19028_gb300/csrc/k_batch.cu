@@ -123,96 +123,84 @@ __device__ __forceinline__ void pass_body(const BArrays& a, const BProb& P, cons
       }
   }
   TA sc0 = TA(0), sc1 = TA(0);
-  for (int base = warp * G; base < t.rows; base += 2 * NG) {   // warp-uniform trip count
-    const int ra = base + lane / LR, rb = ra + NG;
-    const bool ha = ra < t.rows, hb = rb < t.rows;
-    TA x0[CH][4], x1[CH][4];
+  constexpr int RU = 8 / CH;   // rows per group in flight: ~8 vector loads per lane
+  for (int base = warp * G; base < t.rows; base += RU * NG) {   // warp-uniform trip count
+    int rr[RU];
+    bool hv[RU];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int col = 4 * (gl + LR * c);
-      const bool ok = col < lda;
-      if (ok && ha) load4(Ab + (int64_t)ra * lda + col, x0[c]);
-      else x0[c][0] = x0[c][1] = x0[c][2] = x0[c][3] = TA(0);
-      if (ok && hb) load4(Ab + (int64_t)rb * lda + col, x1[c]);
-      else x1[c][0] = x1[c][1] = x1[c][2] = x1[c][3] = TA(0);
+    for (int u = 0; u < RU; ++u) {
+      rr[u] = base + lane / LR + u * NG;
+      hv[u] = rr[u] < t.rows;
     }
-    if constexpr (MODE == kColnorm) {
+    TA x[RU][CH][4];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const int col = 4 * (gl + LR * c);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          acc[0][c][e] = fma(x0[c][e], x0[c][e], acc[0][c][e]);
-          acc[0][c][e] = fma(x1[c][e], x1[c][e], acc[0][c][e]);
-        }
-        // the FP32 working copy fl32(A) (round to nearest)
-        if (col < lda) {
-          if (ha)
-            *reinterpret_cast<float4*>(a.A32 + P.offA + (int64_t)(t.row0 + ra) * lda + col) =
-                make_float4(f64_to_f32_rn(x0[c][0]), f64_to_f32_rn(x0[c][1]),
-                            f64_to_f32_rn(x0[c][2]), f64_to_f32_rn(x0[c][3]));
-          if (hb)
-            *reinterpret_cast<float4*>(a.A32 + P.offA + (int64_t)(t.row0 + rb) * lda + col) =
-                make_float4(f64_to_f32_rn(x1[c][0]), f64_to_f32_rn(x1[c][1]),
-                            f64_to_f32_rn(x1[c][2]), f64_to_f32_rn(x1[c][3]));
-        }
+        if (hv[u] && col < lda) load4(Ab + (int64_t)rr[u] * lda + col, x[u][c]);
+        else x[u][c][0] = x[u][c][1] = x[u][c][2] = x[u][c][3] = TA(0);
       }
+    if constexpr (MODE == kColnorm) {
+#pragma unroll
+      for (int u = 0; u < RU; ++u)
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int col = 4 * (gl + LR * c);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[0][c][e] = fma(x[u][c][e], x[u][c][e], acc[0][c][e]);
+          // the FP32 working copy fl32(A) (round to nearest)
+          if (hv[u] && col < lda)
+            *reinterpret_cast<float4*>(a.A32 + P.offA + (int64_t)(t.row0 + rr[u]) * lda + col) =
+                make_float4(f64_to_f32_rn(x[u][c][0]), f64_to_f32_rn(x[u][c][1]),
+                            f64_to_f32_rn(x[u][c][2]), f64_to_f32_rn(x[u][c][3]));
+        }
     } else {
-      TA d0[NR], d1[NR];
+      TA d[RU][NR];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        d0[r] = TA(0);
-        d1[r] = TA(0);
+      for (int u = 0; u < RU; ++u)
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+        for (int r = 0; r < NR; ++r) {
+          d[u][r] = TA(0);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            d0[r] = fma(x0[c][e], vq[r][c][e], d0[r]);
-            d1[r] = fma(x1[c][e], vq[r][c][e], d1[r]);
-          }
-      }
+          for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) d[u][r] = fma(x[u][c][e], vq[r][c][e], d[u][r]);
+        }
 #pragma unroll
       for (int o = LR / 2; o > 0; o >>= 1)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          d0[r] += __shfl_xor_sync(0xffffffffu, d0[r], o);
-          d1[r] += __shfl_xor_sync(0xffffffffu, d1[r], o);
-        }
+        for (int u = 0; u < RU; ++u)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) d[u][r] += __shfl_xor_sync(0xffffffffu, d[u][r], o);
       if constexpr (MODE == kResid) {
         // r_i = b_i - a_i^T x (FP64), Alg. 2
-        const double bv0 = ha ? a.b[P.offB + t.row0 + ra] : 0.0;
-        const double bv1 = hb ? a.b[P.offB + t.row0 + rb] : 0.0;
-        const TA r0 = (TA)bv0 - d0[0], r1 = (TA)bv1 - d1[0];
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+        for (int u = 0; u < RU; ++u) {
+          const double bv = hv[u] ? a.b[P.offB + t.row0 + rr[u]] : 0.0;
+          const TA rv = (TA)bv - d[u][0];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            acc[0][c][e] = fma(r0, x0[c][e], acc[0][c][e]);
-            acc[0][c][e] = fma(r1, x1[c][e], acc[0][c][e]);
+          for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[0][c][e] = fma(rv, x[u][c][e], acc[0][c][e]);
+          if (gl == 0) {
+            sc0 = fma(rv, rv, sc0);
+            sc1 = fma((TA)bv, rv, sc1);
           }
-        if (gl == 0) {
-          sc0 = fma(r0, r0, sc0);
-          sc0 = fma(r1, r1, sc0);
-          sc1 = fma((TA)bv0, r0, sc1);
-          sc1 = fma((TA)bv1, r1, sc1);
         }
       } else {
         // t = A q; the row's share of A^T t; ||t||^2
 #pragma unroll
-        for (int r = 0; r < NR; ++r)
+        for (int u = 0; u < RU; ++u) {
 #pragma unroll
-          for (int c = 0; c < CH; ++c)
+          for (int r = 0; r < NR; ++r)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              acc[r][c][e] = fma(d0[r], x0[c][e], acc[r][c][e]);
-              acc[r][c][e] = fma(d1[r], x1[c][e], acc[r][c][e]);
-            }
-        if (gl == 0) {
-          sc0 = fma(d0[0], d0[0], sc0);
-          sc0 = fma(d1[0], d1[0], sc0);
-          if constexpr (NR > 1) {
-            sc1 = fma(d0[1], d0[1], sc1);
-            sc1 = fma(d1[1], d1[1], sc1);
+            for (int c = 0; c < CH; ++c)
+#pragma unroll
+              for (int e = 0; e < 4; ++e) acc[r][c][e] = fma(d[u][r], x[u][c][e], acc[r][c][e]);
+          if (gl == 0) {
+            sc0 = fma(d[u][0], d[u][0], sc0);
+            if constexpr (NR > 1) sc1 = fma(d[u][1], d[u][1], sc1);
           }
         }
       }
@@ -265,11 +253,10 @@ __device__ __forceinline__ void pass_body(const BArrays& a, const BProb& P, cons
 }
 
 template <typename TA, int NR, int MODE>
-__global__ void __launch_bounds__(kPT) pass_kernel(BArrays a) {
+__global__ void __launch_bounds__(kPT) pass_kernel(BArrays a, const int* __restrict__ tlist) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int tile = blockIdx.x;
-  const BTile t = a.tiles[tile];
-  if (MODE != kColnorm && !a.st[t.prob].active) return;
+  const int tile = tlist ? tlist[blockIdx.x] : (int)blockIdx.x;
+  const BTile t = a.tiles[tile];   // tile lists hold only active problems' tiles
   const BProb P = a.probs[t.prob];
   switch (P.cfg) {
     case 0: pass_body<TA, NR, MODE, 8, 1>(a, P, t, tile, smem); break;
@@ -645,53 +632,84 @@ __global__ void __launch_bounds__(kCT) trtri_kernel(BArrays a, const int* list) 
 // =========================================================================================
 // Per-problem GEMVs with the inverse factor (one warp per row, rows from L2)
 // =========================================================================================
-// v_r[i] = sum_{j <= i} WT[i][j] y_r[j]   (WT = W^T lower triangular), r < nr
-template <typename T>
-__device__ void gemv_lower(const T* __restrict__ WT, int npb, const T* ys, T* vs, int nr) {
+// v_r[i] = sum_{j <= i} WT[i][j] y_r[j]   (WT = W^T lower triangular), r < nr.
+// A warp takes two rows at a time and issues every load of both rows before its FMAs (the
+// rows come from L2 / HBM; a loop of dependent load-FMA rounds would be latency bound).
+template <typename T, bool LOWER>
+__device__ __forceinline__ void gemv_tri(const T* __restrict__ M, int npb, const T* xs, T* vs,
+                                         int nr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < npb; i += kCW) {
-    const T* row = WT + (int64_t)i * npb;
-    T a0 = T(0), a1 = T(0);
-    for (int c = lane * 4; c <= i; c += 128) {
-      T w[4];
-      ldrow4(row + c, w);
+  constexpr int U = kMaxN / 128;   // 4-column chunks per lane of a full row
+  for (int i0 = warp; i0 < npb; i0 += 2 * kCW) {
+    const int i1 = i0 + kCW;
+    T w0[U][4], w1[U][4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        a0 = fma(w[e], ys[c + e], a0);
-        if (nr > 1) a1 = fma(w[e], ys[npb + c + e], a1);
+    for (int u = 0; u < U; ++u) {
+      const int c = lane * 4 + 128 * u;
+      // lower: columns c <= i; upper: columns from the chunk holding i to the end
+      const bool ok0 = LOWER ? (c <= i0) : (c + 3 >= i0 && c < npb);
+      const bool ok1 = (i1 < npb) && (LOWER ? (c <= i1) : (c + 3 >= i1 && c < npb));
+      if (ok0) ldrow4(M + (int64_t)i0 * npb + c, w0[u]);
+      else w0[u][0] = w0[u][1] = w0[u][2] = w0[u][3] = T(0);
+      if (ok1) ldrow4(M + (int64_t)i1 * npb + c, w1[u]);
+      else w1[u][0] = w1[u][1] = w1[u][2] = w1[u][3] = T(0);
+    }
+    T a00 = T(0), a01 = T(0), a10 = T(0), a11 = T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = lane * 4 + 128 * u;
+      if (c < npb) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const T x0 = xs[c + e];
+          a00 = fma(w0[u][e], x0, a00);
+          a10 = fma(w1[u][e], x0, a10);
+          if (nr > 1) {
+            const T x1 = xs[npb + c + e];
+            a01 = fma(w0[u][e], x1, a01);
+            a11 = fma(w1[u][e], x1, a11);
+          }
+        }
       }
     }
-    a0 = wsum(a0);
-    a1 = wsum(a1);
+    a00 = wsum(a00);
+    a10 = wsum(a10);
+    if (nr > 1) {
+      a01 = wsum(a01);
+      a11 = wsum(a11);
+    }
     if (lane == 0) {
-      vs[i] = a0;
-      if (nr > 1) vs[npb + i] = a1;
+      vs[i0] = a00;
+      if (nr > 1) vs[npb + i0] = a01;
+      if (i1 < npb) {
+        vs[i1] = a10;
+        if (nr > 1) vs[npb + i1] = a11;
+      }
     }
   }
+}
+template <typename T>
+__device__ void gemv_lower(const T* __restrict__ WT, int npb, const T* ys, T* vs, int nr) {
+  gemv_tri<T, true>(WT, npb, ys, vs, nr);
 }
 // v_r[i] = sum_{j >= i} W[i][j] p_r[j]   (W upper triangular)
 template <typename T>
 __device__ void gemv_upper(const T* __restrict__ W, int npb, const T* ps, T* vs, int nr) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < npb; i += kCW) {
-    const T* row = W + (int64_t)i * npb;
-    T a0 = T(0), a1 = T(0);
-    for (int c = (i & ~3) + lane * 4; c < npb; c += 128) {
-      T w[4];
-      ldrow4(row + c, w);
+  gemv_tri<T, false>(W, npb, ps, vs, nr);
+}
+
+// sum over the tiles of a problem of part[i * step] (8 loads in flight)
+template <typename T>
+__device__ __forceinline__ T sum_tiles(const T* __restrict__ base, int ntiles, int64_t step) {
+  T t[8];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        a0 = fma(w[e], ps[c + e], a0);
-        if (nr > 1) a1 = fma(w[e], ps[npb + c + e], a1);
-      }
-    }
-    a0 = wsum(a0);
-    a1 = wsum(a1);
-    if (lane == 0) {
-      vs[i] = a0;
-      if (nr > 1) vs[npb + i] = a1;
-    }
-  }
+  for (int k = 0; k < 8; ++k) t[k] = T(0);
+  int i = 0;
+  for (; i + 7 < ntiles; i += 8)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] += base[(int64_t)(i + k) * step];
+  for (; i < ntiles; ++i) t[0] += base[(int64_t)i * step];
+  return ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
 }
 
 // Shared memory of the per-problem solve kernels: 4 vectors of 2 x kMaxN in T plus FP64 scratch
@@ -821,19 +839,8 @@ __global__ void __launch_bounds__(kCT) resid_post_kernel(BArrays a, const int* l
   const double* dinv = a.dinv + P.offV;
   // sum of the tile partials of A^T r, ||r||^2, b^T r
   double rs[2] = {0.0, 0.0};
-  for (int c = threadIdx.x; c < npb; c += kCT) {
-    double t0 = 0.0, t1 = 0.0;
-    if (c < lda) {
-      const double* base = a.part64 + P.poff + c;
-      int i = 0;
-      for (; i + 1 < P.ntiles; i += 2) {
-        t0 += base[(int64_t)i * lda];
-        t1 += base[(int64_t)(i + 1) * lda];
-      }
-      if (i < P.ntiles) t0 += base[(int64_t)i * lda];
-    }
-    at[c] = t0 + t1;
-  }
+  for (int c = threadIdx.x; c < npb; c += kCT)
+    at[c] = (c < lda) ? sum_tiles<double>(a.part64 + P.poff + c, P.ntiles, lda) : 0.0;
   for (int i = threadIdx.x; i < P.ntiles; i += kCT) {
     rs[0] += a.spart[(int64_t)(P.tile0 + i) * 4 + 0];
     rs[1] += a.spart[(int64_t)(P.tile0 + i) * 4 + 1];
@@ -971,18 +978,9 @@ __global__ void __launch_bounds__(kCT) pcg_post_kernel(BArrays a, const int* lis
   // sum of the tile partials of A^T t (per right-hand side) and ||t||^2
   for (int e = threadIdx.x; e < nr * npb; e += kCT) {
     const int r = e / npb, c = e - r * npb;
-    T t0 = T(0), t1 = T(0);
-    if (c < lda) {
-      const T* base = part + P.poff * nr + (int64_t)r * lda + c;
-      const int64_t step = (int64_t)lda * nr;
-      int i = 0;
-      for (; i + 1 < P.ntiles; i += 2) {
-        t0 += base[(int64_t)i * step];
-        t1 += base[(int64_t)(i + 1) * step];
-      }
-      if (i < P.ntiles) t0 += base[(int64_t)i * step];
-    }
-    at[e] = t0 + t1;
+    at[e] = (c < lda) ? sum_tiles<T>(part + P.poff * nr + (int64_t)r * lda + c, P.ntiles,
+                                     (int64_t)lda * nr)
+                      : T(0);
   }
   double tt[2] = {0.0, 0.0};
   for (int i = threadIdx.x; i < P.ntiles; i += kCT) {
@@ -1132,35 +1130,77 @@ __global__ void __launch_bounds__(kCT) rqi_update_kernel(BArrays a, const int* l
   }
 }
 
-// number of active problems in out[0]; the sum of m n over them (entries of A a pass over the
-// active problems reads) in out[2..3] as one 64-bit count
-__global__ void count_active_kernel(BArrays a, const int* list, int cnt, int* out) {
-  int c = 0;
-  unsigned long long el = 0ull;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    const int pi = list[i];
-    if (a.st[pi].active) {
-      c += 1;
-      el += (unsigned long long)(a.probs[pi].m * a.probs[pi].n);
-    }
-  }
-  c = wsum(c);
-  el = wsum(el);
-  __shared__ int sh[32];
-  __shared__ unsigned long long she[32];
-  if ((threadIdx.x & 31) == 0) {
-    sh[threadIdx.x >> 5] = c;
-    she[threadIdx.x >> 5] = el;
+// Exclusive prefix sum of one int per thread over the CTA (blockDim.x <= 1024); returns the
+// thread's offset and writes the CTA total to *total.
+__device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    unsigned long long te = 0ull;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      t += sh[w];
-      te += she[w];
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < nw) ? sh[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
     }
-    out[0] = t;
+    if (lane < nw) sh[lane] = wi - w;       // exclusive offset of each warp
+    if (lane == 31) sh[32] = wi;            // total
+  }
+  __syncthreads();
+  const int off = sh[warp] + incl - v;
+  *total = sh[32];
+  return off;
+}
+
+// Active set of the problems in `list`: out[0] = active problems, out[1] = their row tiles,
+// out[2..3] = sum of m n over them (one 64-bit count); act_probs / act_tiles receive the
+// compacted problem and tile lists the next launches run over. One CTA.
+__global__ void __launch_bounds__(1024) count_active_kernel(BArrays a, const int* list, int cnt,
+                                                            int* out, int* act_probs,
+                                                            int* act_tiles) {
+  __shared__ int sh[33];
+  __shared__ unsigned long long she[32];
+  int base_p = 0, base_t = 0;
+  unsigned long long el = 0ull;
+  for (int c0 = 0; c0 < cnt; c0 += (int)blockDim.x) {
+    const int i = c0 + (int)threadIdx.x;
+    int pi = -1, act = 0, nt = 0;
+    if (i < cnt) {
+      pi = list[i];
+      act = a.st[pi].active ? 1 : 0;
+      if (act) {
+        nt = a.probs[pi].ntiles;
+        el += (unsigned long long)(a.probs[pi].m * a.probs[pi].n);
+      }
+    }
+    int tot_p = 0, tot_t = 0;
+    const int op = block_excl_scan(act, sh, &tot_p);
+    const int ot = block_excl_scan(nt, sh, &tot_t);
+    if (act) {
+      act_probs[base_p + op] = pi;
+      const int t0 = a.probs[pi].tile0;
+      for (int t = 0; t < nt; ++t) act_tiles[base_t + ot + t] = t0 + t;
+    }
+    base_p += tot_p;
+    base_t += tot_t;
+  }
+  el = wsum(el);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) she[threadIdx.x >> 5] = el;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long te = 0ull;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) te += she[w];
+    out[0] = base_p;
+    out[1] = base_t;
     *reinterpret_cast<unsigned long long*>(out + 2) = te;
   }
 }
@@ -1180,7 +1220,7 @@ void launch_pass_colnorm(const BArrays& a, int ntiles, cudaStream_t s) {
   constexpr size_t sm = pass_smem<double, 1>();
   static const bool once = [] { set_smem(pass_kernel<double, 1, kColnorm>, sm); return true; }();
   (void)once;
-  pass_kernel<double, 1, kColnorm><<<ntiles, kPT, sm, s>>>(a);
+  pass_kernel<double, 1, kColnorm><<<ntiles, kPT, sm, s>>>(a, nullptr);
   count_launch();
 }
 
@@ -1190,28 +1230,28 @@ void launch_colnorm_post(const BArrays& a, const int* list, int cnt, cudaStream_
   count_launch();
 }
 
-void launch_pass_resid(const BArrays& a, int ntiles, cudaStream_t s) {
+void launch_pass_resid(const BArrays& a, const int* tlist, int ntiles, cudaStream_t s) {
   if (ntiles <= 0) return;
   constexpr size_t sm = pass_smem<double, 1>();
   static const bool once = [] { set_smem(pass_kernel<double, 1, kResid>, sm); return true; }();
   (void)once;
-  pass_kernel<double, 1, kResid><<<ntiles, kPT, sm, s>>>(a);
+  pass_kernel<double, 1, kResid><<<ntiles, kPT, sm, s>>>(a, tlist);
   count_launch();
 }
 
 template <typename T>
-void launch_pass_pcg(const BArrays& a, int ntiles, int nr, cudaStream_t s) {
+void launch_pass_pcg(const BArrays& a, const int* tlist, int ntiles, int nr, cudaStream_t s) {
   if (ntiles <= 0) return;
   if (nr == 2) {
     constexpr size_t sm = pass_smem<T, 2>();
     static const bool once = [] { set_smem(pass_kernel<T, 2, kPcg>, sm); return true; }();
     (void)once;
-    pass_kernel<T, 2, kPcg><<<ntiles, kPT, sm, s>>>(a);
+    pass_kernel<T, 2, kPcg><<<ntiles, kPT, sm, s>>>(a, tlist);
   } else {
     constexpr size_t sm = pass_smem<T, 1>();
     static const bool once = [] { set_smem(pass_kernel<T, 1, kPcg>, sm); return true; }();
     (void)once;
-    pass_kernel<T, 1, kPcg><<<ntiles, kPT, sm, s>>>(a);
+    pass_kernel<T, 1, kPcg><<<ntiles, kPT, sm, s>>>(a, tlist);
   }
   count_launch();
 }
@@ -1286,13 +1326,14 @@ void launch_rqi_update(const BArrays& a, const int* list, int cnt, cudaStream_t 
   count_launch();
 }
 
-void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, cudaStream_t s) {
-  count_active_kernel<<<1, 1024, 0, s>>>(a, list, cnt, out);
+void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, int* act_probs,
+                         int* act_tiles, cudaStream_t s) {
+  count_active_kernel<<<1, 1024, 0, s>>>(a, list, cnt, out, act_probs, act_tiles);
   count_launch();
 }
 
-template void launch_pass_pcg<float>(const BArrays&, int, int, cudaStream_t);
-template void launch_pass_pcg<double>(const BArrays&, int, int, cudaStream_t);
+template void launch_pass_pcg<float>(const BArrays&, const int*, int, int, cudaStream_t);
+template void launch_pass_pcg<double>(const BArrays&, const int*, int, int, cudaStream_t);
 template void launch_gram<float>(const BArrays&, const int4*, int, cudaStream_t);
 template void launch_gram<double>(const BArrays&, const int4*, int, cudaStream_t);
 template void launch_chol<float>(const BArrays&, const int*, int, const double*, int*, cudaStream_t);

@@ -1019,7 +1019,7 @@ void tls_default_options(tls_options* opt) {
   opt->max_shifts = 3;
   opt->gram_simt = 0;
   opt->shift_first = 1;
-  opt->psi_accept = 1e-12;
+  opt->psi_accept = 1e-15;
   opt->fallback = 1;
 }
 

@@ -7,6 +7,9 @@
 #include "tls_batch_internal.h"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -34,11 +37,17 @@ struct tls_batch {
   BState* dst = nullptr;
   int4* dgram = nullptr;
   int* dlist = nullptr;             // problem list of the current launch sequence
+  int* dact_probs = nullptr;        // its active problems (compacted)
+  int* dact_tiles = nullptr;        // their row tiles (compacted)
   double* dshift = nullptr;
   int* dinfo = nullptr;
   int* dcount = nullptr;
   int* hcount = nullptr;            // pinned
   int ntiles = 0;
+  int cap_tiles = 0;                // capacity of the tile arrays and partial buffers
+  int64_t cap_poff = 0;
+  int64_t tile_bytes[kNumCfg] = {};  // row-tile size (FP32 bytes) per pass lane layout
+  int tuned_u = 0;                  // sizeof the u type the tile sizes were tuned for
   Prec u = Prec::FP32;
   bool factored = false;
   tls_options opt{};
@@ -84,9 +93,34 @@ tls_status cuda_st(tls_batch* bt, cudaError_t e, const char* what) {
 int64_t rup(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 // Row tiles of roughly `target` bytes of FP32 data (at least one row)
-int64_t rows_per_tile(int64_t lda) {
-  const int64_t target = 64 * 1024;
+int64_t rows_per_tile(int64_t lda, int64_t target) {
   return std::max<int64_t>(1, target / (lda * 4));
+}
+
+constexpr int64_t kTileMin = 64 * 1024;   // smallest tile the partial buffers are sized for
+constexpr int64_t kTileCand[] = {64 * 1024, 128 * 1024, 256 * 1024, 512 * 1024, 1024 * 1024};
+
+// (Re)build the row-tile table from tile_bytes: tiles of every problem, their partial-sum
+// offsets (poff) and counts. Host side only.
+void build_tiles(tls_batch* bt) {
+  bt->ht.clear();
+  int64_t poff = 0;
+  for (size_t i = 0; i < bt->hp.size(); ++i) {
+    BProb& P = bt->hp[i];
+    const int64_t rpt = std::min<int64_t>(rows_per_tile(P.lda, bt->tile_bytes[P.cfg]), P.m);
+    P.tile0 = (int)bt->ht.size();
+    P.poff = poff;
+    for (int64_t r = 0; r < P.m; r += rpt) {
+      BTile t{};
+      t.prob = (int)i;
+      t.row0 = (int)r;
+      t.rows = (int)std::min<int64_t>(rpt, P.m - r);
+      bt->ht.push_back(t);
+    }
+    P.ntiles = (int)bt->ht.size() - P.tile0;
+    poff += (int64_t)P.ntiles * P.lda;
+  }
+  bt->ntiles = (int)bt->ht.size();
 }
 
 double unit_roundoff(Prec p) {
@@ -255,65 +289,150 @@ tls_status solve_list(tls_batch* bt, const std::vector<int>& L, const SolveParam
   if (cnt == 0) return TLS_OK;
   tls_status s = upload_list(bt, L);
   if (s != TLS_OK) return s;
-  const int* dl = bt->dlist;
   const BArrays& a = bt->a;
-  const int nt = bt->ntiles;
+  // compacted lists of the active problems and their row tiles (rebuilt at every check)
+  const int* dl = bt->dact_probs;
+  const int* tl = bt->dact_tiles;
+  int cnt_act = 0, nt = 0;
   int64_t elems = 0;   // entries of A of the active problems
-  for (int i : L) elems += bt->hp[(size_t)i].m * bt->hp[(size_t)i].n;
+  auto refresh = [&]() -> tls_status {
+    {
+      BProfScope pr(bt, TLS_PROF_VEC);
+      launch_count_active(a, bt->dlist, cnt, bt->dcount, bt->dact_probs, bt->dact_tiles, st);
+    }
+    BT_CK_LAUNCH("batched active set");
+    BT_CK(cudaMemcpyAsync(bt->hcount, bt->dcount, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    BT_CK(cudaStreamSynchronize(st));
+    cnt_act = bt->hcount[0];
+    nt = bt->hcount[1];
+    unsigned long long el = 0ull;
+    std::memcpy(&el, bt->hcount + 2, sizeof(el));
+    elems = (int64_t)el;
+    return TLS_OK;
+  };
   auto resid = [&](int mode) {
     {
       BProfScope pr(bt, TLS_PROF_RESID_PASS);
-      launch_pass_resid(a, nt, st);
+      launch_pass_resid(a, tl, nt, st);
       if (bt->prof) bt->prof_elems[TLS_PROF_RESID_PASS] += elems;
     }
     BProfScope pr(bt, TLS_PROF_RESID_REDUCE);
-    launch_resid_post<T>(a, dl, cnt, mode, sp, st);
+    launch_resid_post<T>(a, dl, cnt_act, mode, sp, st);
   };
   auto pcg_step = [&](int nr) {
     {
       BProfScope pr(bt, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
-      launch_pass_pcg<T>(a, nt, nr, st);
+      launch_pass_pcg<T>(a, tl, nt, nr, st);
       if (bt->prof) bt->prof_elems[nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1] += elems;
     }
     BProfScope pr(bt, TLS_PROF_PCG_REDUCE);
-    launch_pcg_post<T>(a, dl, cnt, st);
+    launch_pcg_post<T>(a, dl, cnt_act, st);
   };
   {
     BProfScope pr(bt, TLS_PROF_VEC);
-    launch_solve_init<T>(a, dl, cnt, st);
+    launch_solve_init<T>(a, bt->dlist, cnt, st);
   }
+  s = refresh();
+  if (s != TLS_OK) return s;
   // line 1: LS start, x = 0 residual (f = -A^T b), PCGTLS with sigma^2 = 0
   resid(kResidLs);
   for (int j = 0; j < std::max(1, bt->opt.ls_iters); ++j) pcg_step(1);
   {
     BProfScope pr(bt, TLS_PROF_VEC);
-    launch_ls_finish<T>(a, dl, cnt, st);
+    launch_ls_finish<T>(a, dl, cnt_act, st);
   }
   // lines 2-5: sigma_0^2 and the inverse-iteration step
   resid(kResidStart);
   BT_CK_LAUNCH("batched solve start");
   for (int k = 1; k <= sp.max_rqi + 2; ++k) {
     resid(kResidRqi);
-    {
-      BProfScope pr(bt, TLS_PROF_VEC);
-      launch_count_active(a, dl, cnt, bt->dcount, st);
-    }
-    BT_CK_LAUNCH("batched residual");
-    BT_CK(cudaMemcpyAsync(bt->hcount, bt->dcount, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    BT_CK(cudaStreamSynchronize(st));
-    if (bt->hcount[0] == 0) break;
-    unsigned long long el = 0ull;
-    std::memcpy(&el, bt->hcount + 2, sizeof(el));
-    elems = (int64_t)el;
+    s = refresh();
+    if (s != TLS_OK) return s;
+    if (cnt_act == 0) break;
     const int steps = sp.cg_fixed ? (k + 1) : std::max(1, sp.cg_max);
     for (int j = 0; j < steps; ++j) pcg_step(2);
     {
       BProfScope pr(bt, TLS_PROF_VEC);
-      launch_rqi_update<T>(a, dl, cnt, st);
+      launch_rqi_update<T>(a, dl, cnt_act, st);
     }
     BT_CK_LAUNCH("batched PCGTLS");
   }
   return TLS_OK;
+}
+
+// Autotuner of the row-tile size per pass lane layout (size bucket): for each layout present,
+// every candidate size is timed on this batch's own problems of that bucket (the paired FP32
+// PCGTLS pass and the FP64 residual pass, weighted as in a solve: ~5 PCGTLS passes per
+// residual pass); the fastest is kept and cached per device, u type and bucket.
+std::map<std::tuple<int, int, int>, int64_t> g_tile_tune;
+std::mutex g_tile_mu;
+
+tls_status upload_tiles(tls_batch* bt) {
+  BT_CK(cudaMemcpyAsync(bt->dprobs, bt->hp.data(), sizeof(BProb) * bt->hp.size(),
+                        cudaMemcpyHostToDevice, bt->stream));
+  BT_CK(cudaMemcpyAsync(bt->dtiles, bt->ht.data(), sizeof(BTile) * bt->ht.size(),
+                        cudaMemcpyHostToDevice, bt->stream));
+  return TLS_OK;
+}
+
+template <typename T>
+tls_status tune_tiles(tls_batch* bt) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaStream_t st = bt->stream;
+  bool present[kNumCfg] = {};
+  for (const BProb& P : bt->hp) present[P.cfg] = true;
+  for (int c = 0; c < kNumCfg; ++c) {
+    if (!present[c]) continue;
+    const auto key = std::make_tuple(dev, c, (int)sizeof(T));
+    {
+      std::lock_guard<std::mutex> lk(g_tile_mu);
+      auto it = g_tile_tune.find(key);
+      if (it != g_tile_tune.end()) {
+        bt->tile_bytes[c] = it->second;
+        continue;
+      }
+    }
+    double best = 1e30;
+    int64_t best_b = bt->tile_bytes[c];
+    for (int64_t cand : kTileCand) {
+      bt->tile_bytes[c] = cand;
+      build_tiles(bt);
+      std::vector<int> tl;
+      for (const BProb& P : bt->hp)
+        if (P.cfg == c)
+          for (int t = 0; t < P.ntiles; ++t) tl.push_back(P.tile0 + t);
+      tls_status s = upload_tiles(bt);
+      if (s != TLS_OK) return s;
+      BT_CK(cudaMemcpyAsync(bt->dact_tiles, tl.data(), sizeof(int) * tl.size(),
+                            cudaMemcpyHostToDevice, st));
+      const int nt = (int)tl.size();
+      launch_pass_pcg<T>(bt->a, bt->dact_tiles, nt, 2, st);   // warm-up
+      launch_pass_resid(bt->a, bt->dact_tiles, nt, st);
+      BT_CK(cudaEventRecord(bt->ev0, st));
+      for (int r = 0; r < 3; ++r) launch_pass_pcg<T>(bt->a, bt->dact_tiles, nt, 2, st);
+      BT_CK(cudaEventRecord(bt->ev1, st));
+      BT_CK(cudaEventSynchronize(bt->ev1));
+      float ms_p = 0.f, ms_r = 0.f;
+      cudaEventElapsedTime(&ms_p, bt->ev0, bt->ev1);
+      BT_CK(cudaEventRecord(bt->ev0, st));
+      launch_pass_resid(bt->a, bt->dact_tiles, nt, st);
+      BT_CK(cudaEventRecord(bt->ev1, st));
+      BT_CK(cudaEventSynchronize(bt->ev1));
+      cudaEventElapsedTime(&ms_r, bt->ev0, bt->ev1);
+      BT_CK_LAUNCH("tile autotuner");
+      const double cost = ms_p / 3.0 + 0.2 * ms_r;
+      if (cost < best) {
+        best = cost;
+        best_b = cand;
+      }
+    }
+    bt->tile_bytes[c] = best_b;
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    g_tile_tune[key] = best_b;
+  }
+  build_tiles(bt);
+  return upload_tiles(bt);
 }
 
 template <typename T>
@@ -395,7 +514,7 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
     bt->own_stream = true;
   }
   // layout
-  int64_t offA = 0, offB = 0, offV = 0, offM = 0, poff = 0, ngram = 0;
+  int64_t offA = 0, offB = 0, offV = 0, offM = 0, ngram = 0;
   bt->hp.resize((size_t)count);
   bt->gram0.resize((size_t)count);
   for (int i = 0; i < count; ++i) {
@@ -408,20 +527,8 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
     P.offB = offB;
     P.offV = offV;
     P.offM = offM;
-    P.poff = poff;
     P.cfg = cfg_for(P.lda);
     P.prec = (int)Prec::FP16;
-    const int64_t rpt = std::min<int64_t>(rows_per_tile(P.lda), P.m);
-    P.tile0 = (int)bt->ht.size();
-    for (int64_t r = 0; r < P.m; r += rpt) {
-      BTile t{};
-      t.prob = i;
-      t.row0 = (int)r;
-      t.rows = (int)std::min<int64_t>(rpt, P.m - r);
-      bt->ht.push_back(t);
-    }
-    P.ntiles = (int)bt->ht.size() - P.tile0;
-    poff += (int64_t)P.ntiles * P.lda;
     offA += rup(P.m * P.lda, 64);
     offB += rup(P.m, 32);
     offV += P.npb;
@@ -432,7 +539,12 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
       for (int bj = bi; bj < nbk; ++bj) bt->hgram.push_back(make_int4(i, bi, bj, 0));
     ngram += (int64_t)nbk * (nbk + 1) / 2;
   }
-  bt->ntiles = (int)bt->ht.size();
+  // the smallest tiles give the most tiles and partials: size the buffers for them
+  for (int c = 0; c < kNumCfg; ++c) bt->tile_bytes[c] = kTileMin;
+  build_tiles(bt);
+  const int64_t poff = bt->hp.back().poff + (int64_t)bt->hp.back().ntiles * bt->hp.back().lda;
+  bt->cap_tiles = bt->ntiles;
+  bt->cap_poff = poff;
   const size_t vbytes = sizeof(double) * (size_t)offV;
   BArrays& a = bt->a;
   bt->dprobs = static_cast<BProb*>(balloc(bt, sizeof(BProb) * count));
@@ -440,6 +552,8 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   bt->dst = static_cast<BState*>(balloc(bt, sizeof(BState) * count));
   bt->dgram = static_cast<int4*>(balloc(bt, sizeof(int4) * (size_t)std::max<int64_t>(ngram, 1)));
   bt->dlist = static_cast<int*>(balloc(bt, sizeof(int) * count));
+  bt->dact_probs = static_cast<int*>(balloc(bt, sizeof(int) * count));
+  bt->dact_tiles = static_cast<int*>(balloc(bt, sizeof(int) * bt->ht.size()));
   bt->dshift = static_cast<double*>(balloc(bt, sizeof(double) * count));
   bt->dinfo = static_cast<int*>(balloc(bt, sizeof(int) * count));
   bt->dcount = static_cast<int*>(balloc(bt, 4 * sizeof(int)));
@@ -464,6 +578,7 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   a.part64 = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)std::max<int64_t>(poff, 1)));
   a.spart = static_cast<double*>(balloc(bt, sizeof(double) * 4 * bt->ht.size()));
   if (!bt->dprobs || !bt->dtiles || !bt->dst || !bt->dgram || !bt->dlist || !bt->dshift ||
+      !bt->dact_probs || !bt->dact_tiles ||
       !bt->dinfo || !bt->dcount || !A64 || !a.A32 || !bb || !a.d || !a.dinv || !a.dinv32 ||
       !a.x || !a.xbest || !a.f || !a.vw || !a.vs || !a.vp || !a.vq || !a.H || !a.R || !a.W ||
       !a.WT || !a.partU || !a.part64 || !a.spart) {
@@ -486,6 +601,7 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   if (e == cudaSuccess) e = cudaMemsetAsync(a.vs, 0, 2 * vbytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.vp, 0, 2 * vbytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.vq, 0, 2 * vbytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.x, 0, vbytes, st);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   for (int i = 0; i < count && e == cudaSuccess; ++i) {
     const BProb& P = bt->hp[(size_t)i];
@@ -549,6 +665,12 @@ tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt)
   std::fill(bt->broke.begin(), bt->broke.end(), 0);
   std::vector<int> all((size_t)bt->count);
   for (int i = 0; i < bt->count; ++i) all[(size_t)i] = i;
+  const int usz = (bt->u == Prec::FP64) ? 8 : 4;
+  if (bt->tuned_u != usz) {
+    tls_status s0 = (usz == 8) ? tune_tiles<double>(bt) : tune_tiles<float>(bt);
+    if (s0 != TLS_OK) return s0;
+    bt->tuned_u = usz;
+  }
   BT_CK(cudaEventRecord(bt->ev0, bt->stream));
   tls_status s = (bt->u == Prec::FP64) ? factor_list<double>(bt, all, (Prec)(int)u_f)
                                        : factor_list<float>(bt, all, (Prec)(int)u_f);

@@ -99,9 +99,9 @@ struct SolveParams {
 // ---- launchers (k_batch.cu) --------------------------------------------------------------
 void launch_pass_colnorm(const BArrays& a, int ntiles, cudaStream_t s);
 void launch_colnorm_post(const BArrays& a, const int* list, int cnt, cudaStream_t s);
-void launch_pass_resid(const BArrays& a, int ntiles, cudaStream_t s);
+void launch_pass_resid(const BArrays& a, const int* tlist, int ntiles, cudaStream_t s);
 template <typename T>
-void launch_pass_pcg(const BArrays& a, int ntiles, int nr, cudaStream_t s);
+void launch_pass_pcg(const BArrays& a, const int* tlist, int ntiles, int nr, cudaStream_t s);
 template <typename C>
 void launch_gram(const BArrays& a, const int4* gtiles, int ngt, cudaStream_t s);
 template <typename C>
@@ -120,7 +120,8 @@ template <typename T>
 void launch_ls_finish(const BArrays& a, const int* list, int cnt, cudaStream_t s);
 template <typename T>
 void launch_rqi_update(const BArrays& a, const int* list, int cnt, cudaStream_t s);
-void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, cudaStream_t s);
+void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, int* act_probs,
+                         int* act_tiles, cudaStream_t s);
 
 }  // namespace bat
 }  // namespace tls
