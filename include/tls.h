@@ -49,7 +49,8 @@ typedef enum {
   TLS_FP16 = 0,
   TLS_BF16 = 1,
   TLS_FP32 = 2,
-  TLS_FP64 = 3
+  TLS_FP64 = 3,
+  TLS_AUTO = 4   /* packed batch only: the selector network picks u_f per problem */
 } tls_prec;
 
 /* Stop reasons reported in tls_info.stop_reason. */
@@ -213,10 +214,45 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
                                   const double* const* A, const int64_t* lda,
                                   const double* const* b, int on_device, void* stream);
 tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt);
+tls_status tls_batch_set_selector(tls_batch* bt, const float* params, const float* mean,
+                                  const float* scale);
+tls_status tls_batch_features(tls_batch* bt, float* F_host);
 tls_status tls_batch_solve(tls_batch* bt, double tol, int max_rqi, double* const* x,
                            double* sigma, tls_info* infos, tls_status* per_problem);
 void tls_batch_destroy(tls_batch* bt);
 const char* tls_batch_last_error(const tls_batch* bt);
+
+/*
+ * Selector network for the packed batch (a learned choice of the factor precision, Sec. 3.1's
+ * constraints as its hand-rule baseline): a 16 -> 64 -> 64 -> 4 MLP (ReLU) on 16 features of
+ * each problem. tls_batch_factor(bt, TLS_AUTO, opt) factors every problem at FP16, computes the
+ * features from A, b and that factor, runs the network, and refactors each problem at the
+ * precision it picks (logits for FP16 / BF16 / FP32); with opt->cg_fixed = 0 the fourth output
+ * (log10 of the inner tolerance) sets each problem's PCGTLS tolerance. The fallback of
+ * tls_batch_solve still guards every problem.
+ *
+ * tls_batch_set_selector -- params: TLS_MLP_PARAMS FP32 values (W1[64][16], b1[64], W2[64][64],
+ *   b2[64], W3[4][64], b3[4]; used rounded to FP16), mean / scale: the feature normalisation
+ *   (16 each). Host pointers, copied. Without a selector, TLS_AUTO means FP16.
+ * tls_batch_features -- the 16 raw features of every problem from its current factor, into
+ *   F_host (count x 16, row-major). TLS_ERR_STATE before a successful tls_batch_factor.
+ *
+ * Training entry points (device pointers, the caller's stream; FP32 master parameters):
+ * tls_mlp_forward -- out (nsamp x 4) for X (nsamp x 16, normalised features).
+ * tls_mlp_grad    -- mean loss and gradient over the samples idx[0..nsamp) of X (idx NULL: the
+ *   first nsamp rows): cross-entropy of the logits against ycls plus
+ *   lambda * ymask * (out[3] - ytol)^2; scratch holds nsamp * (TLS_MLP_PARAMS + 1) floats.
+ * tls_mlp_adam    -- one Adam step (step >= 1) of params with gradient grad and moments m, v.
+ */
+#define TLS_MLP_PARAMS 5508
+#define TLS_SELECTOR_FEATURES 16
+tls_status tls_mlp_forward(const float* params, int nsamp, const float* X, float* out,
+                           void* stream);
+tls_status tls_mlp_grad(const float* params, int nsamp, const float* X, const int* idx,
+                        const int* ycls, const float* ytol, const float* ymask, float lambda,
+                        float* scratch, float* grad, float* loss_mean, void* stream);
+tls_status tls_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr,
+                        float beta1, float beta2, float eps, void* stream);
 
 /*
  * tls_condition -- estimates behind the two constraints on the factor precision (Sec. 3.1):

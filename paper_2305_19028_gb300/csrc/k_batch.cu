@@ -257,6 +257,11 @@ __global__ void __launch_bounds__(kPT) pass_kernel(BArrays a, const int* __restr
   extern __shared__ __align__(16) unsigned char smem[];
   const int tile = tlist ? tlist[blockIdx.x] : (int)blockIdx.x;
   const BTile t = a.tiles[tile];   // tile lists hold only active problems' tiles
+  if constexpr (MODE == kPcg) {
+    // both shifted solves of this problem already met their tolerance: nothing to add
+    const BState& st = a.st[t.prob];
+    if (st.done[0] && (NR < 2 || st.done[1])) return;
+  }
   const BProb P = a.probs[t.prob];
   switch (P.cfg) {
     case 0: pass_body<TA, NR, MODE, 8, 1>(a, P, t, tile, smem); break;
@@ -942,7 +947,8 @@ __global__ void __launch_bounds__(kCT) resid_post_kernel(BArrays a, const int* l
   }
   if (threadIdx.x == 0) {
     st.cg_sigma2 = sigma2;
-    st.cg_tol2 = sp.cg_fixed ? 0.0 : sp.cg_tol * sp.cg_tol;
+    const double ct = a.cg_tol ? a.cg_tol[pi] : sp.cg_tol;
+    st.cg_tol2 = sp.cg_fixed ? 0.0 : ct * ct;
   }
   pcg_start<T>(a, P, st, 2, ys, vs, dsh);
 }
@@ -1205,6 +1211,130 @@ __global__ void __launch_bounds__(1024) count_active_kernel(BArrays a, const int
   }
 }
 
+// -----------------------------------------------------------------------------------------
+// Features of the selector network (16 per problem) from the problem data and the factor just
+// computed: sizes, the column-norm spread of A, ||b|| / ||A||_F, the spread of diag(R_H), the
+// shifts the factorisation needed, ||W||_F and ||W||_2 (power iteration; W = R_H^{-1}, so
+// ||W||_2 estimates kappa of the scaled A), and the two constraint values of Sec. 3.1 written
+// with these estimates (u_f ||W||_2^2 for the Cholesky route, u_f ||W||_2 for Eq. (5)).
+// Normalised in place as (f - mean) / scale when mean / scale are given.
+// -----------------------------------------------------------------------------------------
+__device__ __forceinline__ double lg(double v) { return log10(fmax(v, 1e-300)); }
+
+template <typename C, typename T>
+__global__ void __launch_bounds__(kCT) features_kernel(BArrays a, const int* list,
+                                                       const int* nshift, const int* fpiv,
+                                                       const int* prec, const double* shift,
+                                                       const float* mean, const float* scale,
+                                                       float* F) {
+  const int pi = list[blockIdx.x];
+  // log10 of the unit roundoff of the problem's factor precision (Table 2)
+  const int pr = prec[pi];
+  const double log10_uf = (pr == 0) ? -11.0 * 0.30102999566398120
+                          : (pr == 1) ? -8.0 * 0.30102999566398120
+                          : (pr == 2) ? -24.0 * 0.30102999566398120 : -53.0 * 0.30102999566398120;
+  const BProb P = a.probs[pi];
+  const int n = (int)P.n, npb = (int)P.npb;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* ys = reinterpret_cast<T*>(smem);
+  T* vs = ys + 2 * kMaxN;
+  __shared__ double dsh[32 * 4];
+  __shared__ double mx[32 * 2];
+  const double* d = a.d + P.offV;
+  const C* R = static_cast<const C*>(a.R) + P.offM;
+  const T* W = static_cast<const T*>(a.W) + P.offM;
+  const T* WT = static_cast<const T*>(a.WT) + P.offM;
+  // spreads of d and diag(R_H): max via sums of -min / max through shuffles
+  double dmax = 0.0, dmin = 1e300, rmax = 0.0, rmin = 1e300, sums[2] = {0.0, 0.0};
+  for (int j = threadIdx.x; j < n; j += kCT) {
+    const double dj = d[j], rj = (double)R[(int64_t)j * npb + j];
+    dmax = fmax(dmax, dj);
+    dmin = fmin(dmin, dj);
+    rmax = fmax(rmax, rj);
+    rmin = fmin(rmin, rj);
+    sums[0] += lg(dj);
+  }
+  // ||W||_F^2 over the n x n block
+  for (int64_t e = threadIdx.x; e < (int64_t)n * npb; e += kCT) {
+    const int c = (int)(e % npb);
+    if (c < n) {
+      const double w = (double)W[e];
+      sums[1] = fma(w, w, sums[1]);
+    }
+  }
+  bsum<double, 2>(sums, dsh);
+  double ext[4] = {dmax, -dmin, rmax, -rmin};
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ext[k] = fmax(ext[k], __shfl_xor_sync(0xffffffffu, ext[k], o));
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dsh[warp * 4 + k] = ext[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double v = (lane < kCW) ? dsh[lane * 4 + k] : -1e300;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      ext[k] = v;
+    }
+  }
+  // ||W||_2 by power iteration on W^T W (8 steps from the vector of ones)
+  for (int j = threadIdx.x; j < npb; j += kCT) ys[j] = (j < n) ? T(1) : T(0);
+  double wn = 0.0;
+  for (int it = 0; it < 9; ++it) {
+    __syncthreads();
+    gemv_upper<T>(W, npb, ys, vs, 1);            // y = W v
+    __syncthreads();
+    double yy[1] = {0.0};
+    for (int j = threadIdx.x; j < npb; j += kCT) yy[0] = fma((double)vs[j], (double)vs[j], yy[0]);
+    bsum<double, 1>(yy, mx);
+    double vv[1] = {0.0};
+    for (int j = threadIdx.x; j < npb; j += kCT) vv[0] = fma((double)ys[j], (double)ys[j], vv[0]);
+    bsum<double, 1>(vv, mx + 32);
+    wn = sqrt(yy[0] / fmax(vv[0], 1e-300));      // ||W v|| / ||v||
+    if (it == 8) break;
+    __syncthreads();
+    gemv_lower<T>(WT, npb, vs, vs + npb, 1);     // z = W^T y
+    __syncthreads();
+    double zz[1] = {0.0};
+    for (int j = threadIdx.x; j < npb; j += kCT) zz[0] = fma((double)vs[npb + j], (double)vs[npb + j], zz[0]);
+    bsum<double, 1>(zz, mx);
+    const double inv = 1.0 / sqrt(fmax(zz[0], 1e-300));
+    for (int j = threadIdx.x; j < npb; j += kCT) ys[j] = (T)((double)vs[npb + j] * inv);
+  }
+  if (threadIdx.x == 0) {
+    const BState& st = a.st[pi];
+    float f[16];
+    const double lw2 = lg(wn), lwf = 0.5 * lg(sums[1]);
+    f[0] = (float)lg((double)P.m);
+    f[1] = (float)lg((double)n);
+    f[2] = (float)lg((double)P.m / (double)n);
+    f[3] = (float)(lg(ext[0]) - lg(-ext[1]));
+    f[4] = (float)(sums[0] / n - lg(ext[0]));
+    f[5] = (float)(0.5 * (lg(st.norm2_b) - lg(st.norm2_A)));
+    f[6] = (float)(lg(ext[2]) - lg(-ext[3]));
+    f[7] = (float)lg(-ext[3]);
+    f[8] = (float)nshift[pi];
+    f[9] = (float)lg(1.0 + shift[pi] / pow(10.0, log10_uf));
+    f[10] = (float)lwf;
+    f[11] = (float)lw2;
+    f[12] = (float)(lwf - lw2);
+    f[13] = (float)(log10_uf + 2.0 * lw2);
+    f[14] = (float)(log10_uf + lw2);
+    f[15] = (fpiv[pi] >= 0) ? (float)fpiv[pi] / (float)n : 0.f;
+    for (int k = 0; k < 16; ++k) {
+      float v = f[k];
+      if (mean && scale) v = (v - mean[k]) / scale[k];
+      F[(int64_t)pi * 16 + k] = v;
+    }
+  }
+}
+
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1325,6 +1455,26 @@ void launch_rqi_update(const BArrays& a, const int* list, int cnt, cudaStream_t 
   rqi_update_kernel<T><<<cnt, kCT, 0, s>>>(a, list);
   count_launch();
 }
+
+template <typename C, typename T>
+void launch_features(const BArrays& a, const int* list, int cnt, const int* nshift,
+                     const int* fpiv, const int* prec, const double* shift, const float* mean,
+                     const float* scale, float* F, cudaStream_t s) {
+  if (cnt <= 0) return;
+  constexpr size_t sm = post_smem<T>();
+  static const bool once = [] { set_smem(features_kernel<C, T>, sm); return true; }();
+  (void)once;
+  features_kernel<C, T><<<cnt, kCT, sm, s>>>(a, list, nshift, fpiv, prec, shift, mean, scale, F);
+  count_launch();
+}
+template void launch_features<float, float>(const BArrays&, const int*, int, const int*, const int*,
+    const int*, const double*, const float*, const float*, float*, cudaStream_t);
+template void launch_features<double, float>(const BArrays&, const int*, int, const int*, const int*,
+    const int*, const double*, const float*, const float*, float*, cudaStream_t);
+template void launch_features<float, double>(const BArrays&, const int*, int, const int*, const int*,
+    const int*, const double*, const float*, const float*, float*, cudaStream_t);
+template void launch_features<double, double>(const BArrays&, const int*, int, const int*, const int*,
+    const int*, const double*, const float*, const float*, float*, cudaStream_t);
 
 void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, int* act_probs,
                          int* act_tiles, cudaStream_t s) {

@@ -48,6 +48,16 @@ struct tls_batch {
   int64_t cap_poff = 0;
   int64_t tile_bytes[kNumCfg] = {};  // row-tile size (FP32 bytes) per pass lane layout
   int tuned_u = 0;                  // sizeof the u type the tile sizes were tuned for
+  // selector network
+  float* dsel = nullptr;            // parameters (TLS_MLP_PARAMS) + mean (16) + scale (16)
+  bool has_sel = false;
+  float* dF = nullptr;              // features (count x 16)
+  float* dnet = nullptr;            // network outputs (count x 4)
+  int* dfint = nullptr;             // shifts and failed pivot per problem (2 x count)
+  double* dcgtol = nullptr;         // per-problem PCGTLS tolerance
+  std::vector<double> hcgtol;
+  bool use_cgtol = false;
+  std::vector<int> sel_class;       // the network's choice per problem (-1: none)
   Prec u = Prec::FP32;
   bool factored = false;
   tls_options opt{};
@@ -435,6 +445,81 @@ tls_status tune_tiles(tls_batch* bt) {
   return upload_tiles(bt);
 }
 
+// Features of every problem from its current factor (normalised by the selector's mean /
+// scale when `norm`) into bt->dF.
+template <typename T>
+tls_status compute_features(tls_batch* bt, bool norm) {
+  cudaStream_t st = bt->stream;
+  std::vector<int> fi((size_t)3 * bt->count);
+  std::vector<int> l32, l64;
+  for (int i = 0; i < bt->count; ++i) {
+    fi[(size_t)i] = bt->shifts[(size_t)i];
+    fi[(size_t)bt->count + i] = bt->fail_pivot[(size_t)i];
+    fi[(size_t)2 * bt->count + i] = (int)bt->uf_used[(size_t)i];
+    if (bt->broke[(size_t)i]) continue;
+    (bt->uf_used[(size_t)i] == TLS_FP64 ? l64 : l32).push_back(i);
+  }
+  BT_CK(cudaMemcpyAsync(bt->dfint, fi.data(), sizeof(int) * fi.size(), cudaMemcpyHostToDevice, st));
+  const float* mean = norm ? bt->dsel + TLS_MLP_PARAMS : nullptr;
+  const float* scale = norm ? bt->dsel + TLS_MLP_PARAMS + 16 : nullptr;
+  for (int pass = 0; pass < 2; ++pass) {
+    const std::vector<int>& L = pass ? l64 : l32;
+    if (L.empty()) continue;
+    tls_status s = upload_list(bt, L);
+    if (s != TLS_OK) return s;
+    const int* fi_d = bt->dfint;
+    if (pass)
+      launch_features<double, T>(bt->a, bt->dlist, (int)L.size(), fi_d, fi_d + bt->count,
+                                 fi_d + 2 * bt->count, bt->dshift, mean, scale, bt->dF, st);
+    else
+      launch_features<float, T>(bt->a, bt->dlist, (int)L.size(), fi_d, fi_d + bt->count,
+                                fi_d + 2 * bt->count, bt->dshift, mean, scale, bt->dF, st);
+    BT_CK_LAUNCH("selector features");
+  }
+  return TLS_OK;
+}
+
+// TLS_AUTO: FP16 factor, features, network, then each problem refactored at its chosen u_f.
+template <typename T>
+tls_status factor_auto(tls_batch* bt) {
+  std::vector<int> all((size_t)bt->count);
+  for (int i = 0; i < bt->count; ++i) all[(size_t)i] = i;
+  tls_status s = factor_list<T>(bt, all, Prec::FP16);
+  if (s != TLS_OK || !bt->has_sel) return s;
+  s = compute_features<T>(bt, true);
+  if (s != TLS_OK) return s;
+  tls::mlp::launch_mlp_forward(bt->dsel, bt->count, bt->dF, bt->dnet, bt->stream);
+  BT_CK_LAUNCH("selector network");
+  std::vector<float> out((size_t)4 * bt->count);
+  BT_CK(cudaMemcpyAsync(out.data(), bt->dnet, sizeof(float) * out.size(), cudaMemcpyDeviceToHost,
+                        bt->stream));
+  BT_CK(cudaStreamSynchronize(bt->stream));
+  std::vector<int> to_bf16, to_fp32;
+  for (int i = 0; i < bt->count; ++i) {
+    const float* o = out.data() + (size_t)4 * i;
+    int c = 0;
+    if (o[1] > o[c]) c = 1;
+    if (o[2] > o[c]) c = 2;
+    bt->sel_class[(size_t)i] = c;
+    bt->hcgtol[(size_t)i] = std::pow(10.0, std::min(-1.0, std::max(-12.0, (double)o[3])));
+    if (bt->broke[(size_t)i] || bt->uf_used[(size_t)i] != TLS_FP16) continue;
+    if (c == 1) to_bf16.push_back(i);
+    if (c == 2) to_fp32.push_back(i);
+  }
+  if (!to_bf16.empty()) {
+    s = factor_list<T>(bt, to_bf16, Prec::BF16);
+    if (s != TLS_OK) return s;
+  }
+  if (!to_fp32.empty()) {
+    s = factor_list<T>(bt, to_fp32, Prec::FP32);
+    if (s != TLS_OK) return s;
+  }
+  BT_CK(cudaMemcpyAsync(bt->dcgtol, bt->hcgtol.data(), sizeof(double) * bt->count,
+                        cudaMemcpyHostToDevice, bt->stream));
+  bt->use_cgtol = true;
+  return TLS_OK;
+}
+
 template <typename T>
 tls_status batch_solve_impl(tls_batch* bt, double tol, int max_rqi, std::vector<BState>& hst) {
   const tls_options& o = bt->opt;
@@ -446,6 +531,7 @@ tls_status batch_solve_impl(tls_batch* bt, double tol, int max_rqi, std::vector<
   sp.cg_fixed = o.cg_fixed;
   sp.cg_max = o.cg_max;
   sp.cg_tol = o.cg_tol;
+  bt->a.cg_tol = bt->use_cgtol ? bt->dcgtol : nullptr;
   std::vector<int> L;
   for (int i = 0; i < bt->count; ++i)
     if (!bt->broke[(size_t)i]) L.push_back(i);
@@ -557,6 +643,11 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   bt->dshift = static_cast<double*>(balloc(bt, sizeof(double) * count));
   bt->dinfo = static_cast<int*>(balloc(bt, sizeof(int) * count));
   bt->dcount = static_cast<int*>(balloc(bt, 4 * sizeof(int)));
+  bt->dsel = static_cast<float*>(balloc(bt, sizeof(float) * (TLS_MLP_PARAMS + 32)));
+  bt->dF = static_cast<float*>(balloc(bt, sizeof(float) * 16 * count));
+  bt->dnet = static_cast<float*>(balloc(bt, sizeof(float) * 4 * count));
+  bt->dfint = static_cast<int*>(balloc(bt, sizeof(int) * 3 * count));
+  bt->dcgtol = static_cast<double*>(balloc(bt, sizeof(double) * count));
   double* A64 = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)offA));
   a.A32 = static_cast<float*>(balloc(bt, sizeof(float) * (size_t)offA));
   double* bb = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)offB));
@@ -578,7 +669,8 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   a.part64 = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)std::max<int64_t>(poff, 1)));
   a.spart = static_cast<double*>(balloc(bt, sizeof(double) * 4 * bt->ht.size()));
   if (!bt->dprobs || !bt->dtiles || !bt->dst || !bt->dgram || !bt->dlist || !bt->dshift ||
-      !bt->dact_probs || !bt->dact_tiles ||
+      !bt->dact_probs || !bt->dact_tiles || !bt->dsel || !bt->dF || !bt->dnet || !bt->dfint ||
+      !bt->dcgtol ||
       !bt->dinfo || !bt->dcount || !A64 || !a.A32 || !bb || !a.d || !a.dinv || !a.dinv32 ||
       !a.x || !a.xbest || !a.f || !a.vw || !a.vs || !a.vp || !a.vq || !a.H || !a.R || !a.W ||
       !a.WT || !a.partU || !a.part64 || !a.spart) {
@@ -627,6 +719,8 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   bt->fallbacks.assign((size_t)count, 0);
   bt->broke.assign((size_t)count, 0);
   bt->uf_used.assign((size_t)count, TLS_FP16);
+  bt->hcgtol.assign((size_t)count, 0.0);
+  bt->sel_class.assign((size_t)count, -1);
   // column norms d_j, ||A||_F^2, ||b||^2 and the FP32 working copy, for the whole batch
   std::vector<int> all((size_t)count);
   for (int i = 0; i < count; ++i) all[(size_t)i] = i;
@@ -647,7 +741,7 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
 }
 
 tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt) {
-  if (!bt || (int)u_f < 0 || (int)u_f > 3) return TLS_ERR_ARG;
+  if (!bt || (int)u_f < 0 || (int)u_f > (int)TLS_AUTO) return TLS_ERR_ARG;
   tls_options o;
   if (opt) o = *opt;
   else tls_default_options(&o);
@@ -663,6 +757,8 @@ tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt)
   std::fill(bt->fail_pivot.begin(), bt->fail_pivot.end(), -1);
   std::fill(bt->fallbacks.begin(), bt->fallbacks.end(), 0);
   std::fill(bt->broke.begin(), bt->broke.end(), 0);
+  std::fill(bt->sel_class.begin(), bt->sel_class.end(), -1);
+  bt->use_cgtol = false;
   std::vector<int> all((size_t)bt->count);
   for (int i = 0; i < bt->count; ++i) all[(size_t)i] = i;
   const int usz = (bt->u == Prec::FP64) ? 8 : 4;
@@ -672,8 +768,12 @@ tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt)
     bt->tuned_u = usz;
   }
   BT_CK(cudaEventRecord(bt->ev0, bt->stream));
-  tls_status s = (bt->u == Prec::FP64) ? factor_list<double>(bt, all, (Prec)(int)u_f)
-                                       : factor_list<float>(bt, all, (Prec)(int)u_f);
+  tls_status s;
+  if (u_f == TLS_AUTO)
+    s = (bt->u == Prec::FP64) ? factor_auto<double>(bt) : factor_auto<float>(bt);
+  else
+    s = (bt->u == Prec::FP64) ? factor_list<double>(bt, all, (Prec)(int)u_f)
+                              : factor_list<float>(bt, all, (Prec)(int)u_f);
   if (s != TLS_OK) return s;
   BT_CK(cudaEventRecord(bt->ev1, bt->stream));
   BT_CK(cudaEventSynchronize(bt->ev1));
@@ -748,6 +848,38 @@ tls_status tls_batch_solve(tls_batch* bt, double tol, int max_rqi, double* const
 }
 
 void tls_batch_destroy(tls_batch* bt) { destroy(bt); }
+
+tls_status tls_batch_set_selector(tls_batch* bt, const float* params, const float* mean,
+                                  const float* scale) {
+  if (!bt) return TLS_ERR_ARG;
+  if (!params || !mean || !scale) {
+    bt->has_sel = false;
+    return TLS_OK;
+  }
+  for (int k = 0; k < 16; ++k)
+    if (!(scale[k] != 0.f) || !std::isfinite(scale[k]) || !std::isfinite(mean[k])) return TLS_ERR_ARG;
+  std::vector<float> h((size_t)TLS_MLP_PARAMS + 32);
+  std::memcpy(h.data(), params, sizeof(float) * TLS_MLP_PARAMS);
+  std::memcpy(h.data() + TLS_MLP_PARAMS, mean, sizeof(float) * 16);
+  std::memcpy(h.data() + TLS_MLP_PARAMS + 16, scale, sizeof(float) * 16);
+  BT_CK(cudaMemcpyAsync(bt->dsel, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice,
+                        bt->stream));
+  BT_CK(cudaStreamSynchronize(bt->stream));
+  bt->has_sel = true;
+  return TLS_OK;
+}
+
+tls_status tls_batch_features(tls_batch* bt, float* F_host) {
+  if (!bt || !F_host) return TLS_ERR_ARG;
+  if (!bt->factored) return TLS_ERR_STATE;
+  tls_status s = (bt->u == Prec::FP64) ? compute_features<double>(bt, false)
+                                       : compute_features<float>(bt, false);
+  if (s != TLS_OK) return s;
+  BT_CK(cudaMemcpyAsync(F_host, bt->dF, sizeof(float) * 16 * bt->count, cudaMemcpyDeviceToHost,
+                        bt->stream));
+  BT_CK(cudaStreamSynchronize(bt->stream));
+  return TLS_OK;
+}
 
 tls_status tls_batch_profile_enable(tls_batch* bt, int on) {
   if (!bt) return TLS_ERR_ARG;

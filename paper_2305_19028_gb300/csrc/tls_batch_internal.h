@@ -85,6 +85,7 @@ struct BArrays {
   void* partU;          // pass partials in the u type (two right-hand sides)
   double* part64;       // pass partials in FP64 (one right-hand side)
   double* spart;        // per-tile scalar partials (4 per tile)
+  const double* cg_tol; // per-problem PCGTLS tolerance (selector), or NULL: the solve's own
 };
 
 enum PassMode : int { kColnorm = 0, kResid = 1, kPcg = 2 };
@@ -120,6 +121,10 @@ template <typename T>
 void launch_ls_finish(const BArrays& a, const int* list, int cnt, cudaStream_t s);
 template <typename T>
 void launch_rqi_update(const BArrays& a, const int* list, int cnt, cudaStream_t s);
+template <typename C, typename T>
+void launch_features(const BArrays& a, const int* list, int cnt, const int* nshift,
+                     const int* fpiv, const int* prec, const double* shift, const float* mean,
+                     const float* scale, float* F, cudaStream_t s);
 void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, int* act_probs,
                          int* act_tiles, cudaStream_t s);
 

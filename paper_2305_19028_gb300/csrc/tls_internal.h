@@ -22,6 +22,11 @@ inline void count_launch(int k = 1) { g_launches.fetch_add((unsigned long long)k
 
 enum class Prec : int { FP16 = 0, BF16 = 1, FP32 = 2, FP64 = 3 };
 
+namespace mlp {
+// selector network forward pass: out (nsamp x 4) for normalised features X (nsamp x 16)
+void launch_mlp_forward(const float* P, int nsamp, const float* X, float* out, cudaStream_t s);
+}
+
 // Device allocation through the caller's allocator (tls_set_allocator) or cudaMalloc.
 void* hook_alloc(size_t bytes, cudaStream_t s);
 void hook_free(void* p, size_t bytes, cudaStream_t s);

@@ -125,6 +125,19 @@ def batch_problem(i: int, noise: float = 1e-6) -> DenseProblem:
     return dense_problem(n * ratio, n, d_lo=d_lo, noise=noise, seed=seed)
 
 
+def selector_problem(seed: int) -> DenseProblem:
+    """A problem of the selector network's training / evaluation distribution (seeds 10000.. for
+    training, 100000.. held out): n ~ U{32..512}, m = n*U{4..12}, D log-spaced in
+    [10^-U(1,6), 1], noise std 10^-U(3,7) (so that sigma_{n+1} / sigma'_n, which the second
+    constraint of Sec. 3.1 depends on, varies over several orders of magnitude)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(rng.integers(32, 513))
+    ratio = int(rng.integers(4, 13))
+    d_lo = 10.0 ** (-rng.uniform(1.0, 6.0))
+    noise = 10.0 ** (-rng.uniform(3.0, 7.0))
+    return dense_problem(n * ratio, n, d_lo=d_lo, noise=noise, seed=seed)
+
+
 def csr_problem(m: int, n: int, nnz_per_row: int = 12, noise: float = 1e-3, seed: int = 0,
                 col_scale_lo: float = -2.0) -> CsrProblem:
     """Sparse A: nnz_per_row distinct uniform columns per row, N(0,1) values, A[i,i] += 1 for

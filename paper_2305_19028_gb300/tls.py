@@ -15,7 +15,10 @@ import numpy as np
 from . import build as _build
 
 TLS_FP16, TLS_BF16, TLS_FP32, TLS_FP64 = 0, 1, 2, 3
-PREC = {"fp16": TLS_FP16, "bf16": TLS_BF16, "fp32": TLS_FP32, "fp64": TLS_FP64}
+TLS_AUTO = 4
+PREC = {"fp16": TLS_FP16, "bf16": TLS_BF16, "fp32": TLS_FP32, "fp64": TLS_FP64, "auto": TLS_AUTO}
+MLP_PARAMS = 5508
+N_FEATURES = 16
 STOP_TOL, STOP_PSI_UP, STOP_MAX_RQI = 1, 2, 3
 
 STATUS = ["TLS_OK", "TLS_ERR_ARG", "TLS_ERR_CUDA", "TLS_ERR_OOM", "TLS_ERR_STATE",
@@ -31,7 +34,8 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_condition", "tls_factor_batched", "tls_batch_create_dense", "tls_batch_factor",
            "tls_batch_solve", "tls_batch_destroy", "tls_batch_last_error",
            "tls_batch_export_factor", "tls_batch_profile_enable", "tls_batch_profile_get",
-           "tls_batch_profile_elems"]
+           "tls_batch_profile_elems", "tls_mlp_forward", "tls_mlp_grad", "tls_mlp_adam",
+           "tls_batch_set_selector", "tls_batch_features"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
@@ -121,6 +125,13 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_batch_profile_enable": (C.c_int, [v, C.c_int]),
         "tls_batch_profile_get": (C.c_int, [v, C.c_int, C.POINTER(i64), _dp]),
         "tls_batch_profile_elems": (C.c_int, [v, C.c_int, C.POINTER(i64)]),
+        "tls_mlp_forward": (C.c_int, [v, C.c_int, v, v, v]),
+        "tls_mlp_grad": (C.c_int, [v, C.c_int, v, v, v, v, v, C.c_float, v, v, v, v]),
+        "tls_mlp_adam": (C.c_int, [v, v, v, v, C.c_int, C.c_float, C.c_float, C.c_float,
+                                   C.c_float, v]),
+        "tls_batch_set_selector": (C.c_int, [v, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                             C.POINTER(C.c_float)]),
+        "tls_batch_features": (C.c_int, [v, C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -434,6 +445,23 @@ class Batch:
         if check:
             self._err(st)
         return xs, sig, [i.as_dict() for i in infos], list(per)
+
+    def set_selector(self, params, mean, scale):
+        """Install the selector network (FP32 params, feature mean and scale) for factor("auto")."""
+        fp = C.POINTER(C.c_float)
+        P = np.ascontiguousarray(params, dtype=np.float32)
+        mu = np.ascontiguousarray(mean, dtype=np.float32)
+        sd = np.ascontiguousarray(scale, dtype=np.float32)
+        if P.size != MLP_PARAMS or mu.size != N_FEATURES or sd.size != N_FEATURES:
+            raise ValueError("selector: wrong parameter or feature sizes")
+        self._err(load().tls_batch_set_selector(self.h, P.ctypes.data_as(fp), mu.ctypes.data_as(fp),
+                                                sd.ctypes.data_as(fp)))
+
+    def features(self) -> np.ndarray:
+        """Raw selector features (count x 16) from the current factor."""
+        F = np.zeros((self.k, N_FEATURES), dtype=np.float32)
+        self._err(load().tls_batch_features(self.h, F.ctypes.data_as(C.POINTER(C.c_float))))
+        return F
 
     def profile(self, on: bool = True):
         load().tls_batch_profile_enable(self.h, int(on))

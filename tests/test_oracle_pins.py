@@ -312,3 +312,46 @@ def test_planted_mistakes_are_caught(monkeypatch, target, mutant):
     assert _pins_pass()
     monkeypatch.setattr(O, target, mutant)
     assert not _pins_pass(), f"planted mistake in {target} went unnoticed"
+
+
+# ------------------------------------------------------------------------------------------
+# selector network oracle: backpropagation pinned by central finite differences
+# ------------------------------------------------------------------------------------------
+def test_mlp_oracle_gradient_matches_finite_differences():
+    import oracle.mlp as M
+    rng = np.random.Generator(np.random.PCG64(7))
+    P = rng.normal(0.0, 0.3, size=M.N_PARAMS)
+    X = rng.normal(size=(6, M.N_IN))
+    y = rng.integers(0, 3, size=6)
+    t = rng.normal(size=6)
+    mask = np.array([1.0, 0.0, 1.0, 1.0, 0.0, 1.0])
+    lam = 0.7
+    _, g = M.loss_and_grad(P, X, y, t, mask, lam)
+    assert g.shape == (M.N_PARAMS,)
+    h = 1e-6
+    for k in rng.choice(M.N_PARAMS, size=300, replace=False):
+        e = np.zeros(M.N_PARAMS)
+        e[k] = h
+        fd = (M.loss_and_grad(P + e, X, y, t, mask, lam)[0] -
+              M.loss_and_grad(P - e, X, y, t, mask, lam)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-7 + 1e-5 * abs(fd), (k, fd, g[k])
+
+
+def test_mlp_oracle_special_cases():
+    import oracle.mlp as M
+    # zero weights: uniform softmax, loss log 3 plus the regression term on out[3] = 0
+    P = np.zeros(M.N_PARAMS)
+    X = np.ones((4, M.N_IN))
+    y = np.array([0, 1, 2, 0])
+    t = np.array([1.0, -2.0, 0.5, 0.0])
+    L, g = M.loss_and_grad(P, X, y, t, np.ones(4), 0.5)
+    assert L == pytest.approx(np.log(3.0) + 0.5 * np.mean(t ** 2), rel=1e-14)
+    # the bias gradient of the logits is the mean of (softmax - one-hot): (1/3 - freq)
+    b3 = g[-4:]
+    assert b3[:3] == pytest.approx([1 / 3 - 2 / 4, 1 / 3 - 1 / 4, 1 / 3 - 1 / 4], abs=1e-15)
+    assert b3[3] == pytest.approx(2 * 0.5 * np.mean(0.0 - t), abs=1e-15)
+    # FP16 storage: the forward pass equals the FP64 pass on the rounded weights
+    rng = np.random.Generator(np.random.PCG64(3))
+    P = rng.normal(0.0, 0.5, size=M.N_PARAMS)
+    Ph = P.astype(np.float32).astype(np.float16).astype(np.float64)
+    assert np.array_equal(M.forward(P, X, fp16=True)[0], M.forward(Ph, X)[0])
