@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TLS solves/s on GB300 at sigma rel err<=1e-10 vs FP64 oracle; mixed vs plain FP64"
 M_ROWS, N_COLS, D_LO, NOISE = 16384, 2048, 1e-3, 1e-4
 SIGMA_TOL, X_TOL = 1e-10, 1e-8
-SOLVE_TOL, MAX_RQI = 0.0, 12      # tol 0: the stopping rule of Sec. 3 (first increase of psi)
+SOLVE_TOL, MAX_RQI = 1e-16, 12
 WORKLOAD = f"dense_{M_ROWS}x{N_COLS}_uf16_u32_ur64"
 
 
@@ -452,6 +452,15 @@ def run_batch(args, ws, rank, local):
     probs = [synth.batch_problem(i) for i in ids]
     stream = torch.cuda.current_stream()
     bt = tls.Batch([(p.A, p.b) for p in probs], stream=stream.cuda_stream)
+    uf = "fp16"
+    model = None
+    if args.selector:
+        from paper_2305_19028_gb300 import selector
+        model = selector.load_model()
+        if model is None:
+            raise RuntimeError("--selector: no trained selector model in the package")
+        bt.set_selector(*model)
+        uf = "auto"
 
     def count_ok(xs, sig):
         if not ref:
@@ -464,7 +473,7 @@ def run_batch(args, ws, rank, local):
         return ok
 
     def step():
-        bt.factor("fp16", u="fp32")
+        bt.factor(uf, u="fp32")
         return bt.solve(tol=SOLVE_TOL, max_rqi=MAX_RQI)
 
     for _ in range(args.warmup):
@@ -504,7 +513,9 @@ def run_batch(args, ws, rank, local):
         e0.record(stream)
         for _ in range(ne):
             with tls.Batch(pins, stream=stream.cuda_stream) as b2:
-                b2.factor("fp16", u="fp32")
+                if model is not None:
+                    b2.set_selector(*model)
+                b2.factor(uf, u="fp32")
                 x2, s2, _, _ = b2.solve(tol=SOLVE_TOL, max_rqi=MAX_RQI)
             okc += count_ok(x2, s2)
         e1.record(stream)
@@ -553,7 +564,8 @@ def run_batch(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16+f32+f64", "data": "synthetic",
-        "config": {"workload": _batch_workload(K), "problems": K, "u_f": "fp16", "u": "fp32",
+        "config": {"workload": _batch_workload(K), "problems": K,
+                   "u_f": "selector (TLS_AUTO)" if model is not None else "fp16", "u": "fp32",
                    "u_r": "fp64", "solve_tol": SOLVE_TOL, "max_rqi": MAX_RQI,
                    "seeds": f"1000 + rank*{K} + i",
                    "l2": "inputs larger than L2 (A: %.1f GB FP64 + %.1f GB FP32)" % (
@@ -582,6 +594,8 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="columns (profiling a smaller case)")
     ap.add_argument("--workload", choices=["dense", "batch"], default="dense")
     ap.add_argument("--batch", type=int, default=BATCH_K, help="problems in the packed batch")
+    ap.add_argument("--selector", action="store_true",
+                    help="batch: let the trained selector network pick u_f per problem")
     args = ap.parse_args()
     _set_size(args.m, args.n)
     ws, rank, local = _dist()

@@ -55,7 +55,7 @@ typedef enum {
 
 /* Stop reasons reported in tls_info.stop_reason. */
 enum {
-  TLS_STOP_TOL = 1,       /* psi_k <= tol * (||A||_F^2 + ||b||^2)                          */
+  TLS_STOP_TOL = 1,       /* psi_k <= tol * (||A||_F^2 + ||b||^2), tested from k = 2 on       */
   TLS_STOP_PSI_UP = 2,    /* psi_k > psi_{k-1} (or >= with psi_rule_ge), Sec. 3 after Eq. (4) */
   TLS_STOP_MAX_RQI = 3    /* k reached max_rqi                                              */
 };

@@ -27,9 +27,11 @@ Readings of the paper taken here (each also recorded in the design notes):
   optional relative tolerance on ||s_j|| / ||s_0|| stops earlier. delta_j <= 0 stops the loop
   and flags loss of positive definiteness.
 * Alg. 2 line "f_k = -A^T r_k - sigma_k^2 x" uses x = x_k.
-* Stop at the first of: psi_k <= tol * (||A||_F^2 + ||b||^2); psi_k > psi_{k-1} (or >= when
-  ``psi_rule_ge``); k > max_rqi. The iterate with the smallest psi is returned with
-  sigma = sqrt(sigma_k^2) of that iterate.
+* Stop at the first of: psi_k <= tol * (||A||_F^2 + ||b||^2) for k >= 2; psi_k > psi_{k-1}
+  (or >= when ``psi_rule_ge``); k > max_rqi. The iterate with the smallest psi is returned with
+  sigma = sqrt(sigma_k^2) of that iterate. The tolerance test starts at k = 2: psi_1 is taken at
+  the inverse-iteration start x_1 (Alg. 2, before the loop), whose error is only first order in
+  psi_1, so a small psi_1 (a small sigma_{n+1}) does not make x_1 accurate.
 """
 from __future__ import annotations
 
@@ -205,7 +207,7 @@ def rqi_pcgtls(A: np.ndarray, b: np.ndarray, R: np.ndarray | None = None,
             stop = STOP_PSI_UP
             break
         best = (k, x.copy(), sigma2)
-        if psi <= tol * scale:
+        if k >= 2 and psi <= tol * scale:
             stop = STOP_TOL
             break
         if k > max_rqi:

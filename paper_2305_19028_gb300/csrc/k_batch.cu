@@ -252,23 +252,30 @@ __device__ __forceinline__ void pass_body(const BArrays& a, const BProb& P, cons
   }
 }
 
+// ntile: device count of the tile list (a persistent grid loops over it), or NULL: one tile
+// per CTA (tlist NULL: tile = CTA index)
 template <typename TA, int NR, int MODE>
-__global__ void __launch_bounds__(kPT) pass_kernel(BArrays a, const int* __restrict__ tlist) {
+__global__ void __launch_bounds__(kPT) pass_kernel(BArrays a, const int* __restrict__ tlist,
+                                                   const int* __restrict__ ntile) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int tile = tlist ? tlist[blockIdx.x] : (int)blockIdx.x;
-  const BTile t = a.tiles[tile];   // tile lists hold only active problems' tiles
-  if constexpr (MODE == kPcg) {
-    // both shifted solves of this problem already met their tolerance: nothing to add
-    const BState& st = a.st[t.prob];
-    if (st.done[0] && (NR < 2 || st.done[1])) return;
-  }
-  const BProb P = a.probs[t.prob];
-  switch (P.cfg) {
-    case 0: pass_body<TA, NR, MODE, 8, 1>(a, P, t, tile, smem); break;
-    case 1: pass_body<TA, NR, MODE, 16, 1>(a, P, t, tile, smem); break;
-    case 2: pass_body<TA, NR, MODE, 32, 1>(a, P, t, tile, smem); break;
-    case 3: pass_body<TA, NR, MODE, 32, 2>(a, P, t, tile, smem); break;
-    default: pass_body<TA, NR, MODE, 32, 4>(a, P, t, tile, smem); break;
+  const int nt = ntile ? *ntile : (int)gridDim.x;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const int tile = tlist ? tlist[ti] : ti;
+    const BTile t = a.tiles[tile];   // tile lists hold only active problems' tiles
+    if constexpr (MODE == kPcg) {
+      // both shifted solves of this problem already met their tolerance: nothing to add
+      const BState& st = a.st[t.prob];
+      if (st.done[0] && (NR < 2 || st.done[1])) continue;
+    }
+    const BProb P = a.probs[t.prob];
+    switch (P.cfg) {
+      case 0: pass_body<TA, NR, MODE, 8, 1>(a, P, t, tile, smem); break;
+      case 1: pass_body<TA, NR, MODE, 16, 1>(a, P, t, tile, smem); break;
+      case 2: pass_body<TA, NR, MODE, 32, 1>(a, P, t, tile, smem); break;
+      case 3: pass_body<TA, NR, MODE, 32, 2>(a, P, t, tile, smem); break;
+      default: pass_body<TA, NR, MODE, 32, 4>(a, P, t, tile, smem); break;
+    }
+    __syncthreads();   // shared memory is reused by the next tile
   }
 }
 
@@ -335,57 +342,92 @@ __device__ __forceinline__ double scaled_entry<double>(const BArrays& a, const B
   return round_uf(a.A64[P.offA + row * P.lda + col] * a.dinv[P.offV + col], P.prec);
 }
 
+// One CTA (64 threads, 8 x 8 outputs each) forms the 64 x 64 tile H[I][J] over the rows
+// [r0, r1) of its problem: staged 32-row chunks of the scaled, u_f-rounded columns of I and J
+// (a diagonal tile stages one block for both), FMA into registers. Tiles whose rows are split
+// write their partial tile to a workspace slot; the others write H directly.
 template <typename C>
-__global__ void __launch_bounds__(256) gram_kernel(BArrays a, const int4* gt) {
-  const int4 g = gt[blockIdx.x];   // (problem, row block, column block), row block <= column block
-  const BProb P = a.probs[g.x];
+__global__ void __launch_bounds__(64) gram_kernel(BArrays a, const GTile* __restrict__ gt,
+                                                  C* __restrict__ work) {
+  const GTile g = gt[blockIdx.x];
+  const BProb P = a.probs[g.prob];
   const int n = (int)P.n, npb = (int)P.npb;
-  const int c0 = g.y * kNB, c1 = g.z * kNB;
+  const int c0 = g.bi * kNB, c1 = g.bj * kNB;
+  const bool diag = (g.bi == g.bj);
   __shared__ __align__(16) C SA[32][kLd];
   __shared__ __align__(16) C SB[32][kLd];
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  C acc[4][4];
+  const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+  C acc[8][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = C(0);
-  for (int64_t r0 = 0; r0 < P.m; r0 += 32) {
-    for (int e = tid; e < 32 * kNB; e += 256) {
-      const int rr = e / kNB, cc = e % kNB;
+    for (int j = 0; j < 8; ++j) acc[i][j] = C(0);
+  // this thread stages column tid of each block; its scale factor stays in a register
+  const bool okA = c0 + tid < n, okB = c1 + tid < n;
+  for (int64_t r0 = g.r0; r0 < g.r1; r0 += 32) {
+    const int rows = (int)min((int64_t)32, (int64_t)g.r1 - r0);
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
       const int64_t row = r0 + rr;
       C va = C(0), vb = C(0);
-      if (row < P.m) {
-        if (c0 + cc < n) va = scaled_entry<C>(a, P, row, c0 + cc);
-        if (c1 + cc < n) vb = scaled_entry<C>(a, P, row, c1 + cc);
+      if (rr < rows) {
+        if (okA) va = scaled_entry<C>(a, P, row, c0 + tid);
+        if (!diag && okB) vb = scaled_entry<C>(a, P, row, c1 + tid);
       }
-      SA[rr][cc] = va;
-      SB[rr][cc] = vb;
+      SA[rr][tid] = va;
+      if (!diag) SB[rr][tid] = vb;
     }
     __syncthreads();
-#pragma unroll 8
+    const C (*B)[kLd] = diag ? SA : SB;
+#pragma unroll 4
     for (int k = 0; k < 32; ++k) {
-      C av[4], bv[4];
+      C av[8], bv[8];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        av[i] = SA[k][ty * 4 + i];
-        bv[i] = SB[k][tx * 4 + i];
+      for (int i = 0; i < 8; ++i) {
+        av[i] = SA[k][ty * 8 + i];
+        bv[i] = B[k][tx * 8 + i];
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
+  if (g.slot >= 0) {
+    C* w = work + (int64_t)g.slot * kNB * kNB;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[(ty * 8 + i) * kNB + tx * 8 + j] = acc[i][j];
+    return;
+  }
   C* H = static_cast<C*>(a.H) + P.offM;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = c0 + ty * 4 + i, c = c1 + tx * 4 + j;
+    for (int j = 0; j < 8; ++j) {
+      const int r = c0 + ty * 8 + i, c = c1 + tx * 8 + j;
       // identity on the padding (rows / columns >= n): padded entries never couple
       H[(int64_t)r * npb + c] = (r == c && r >= n) ? C(1) : acc[i][j];
     }
+}
+
+// Sum of the row-split partial tiles of one H tile, in slot order (deterministic).
+template <typename C>
+__global__ void __launch_bounds__(256) gram_reduce_kernel(BArrays a, const GTile* __restrict__ gr,
+                                                          const C* __restrict__ work) {
+  const GTile g = gr[blockIdx.x];     // slot = first slot, r1 - r0 = number of slots
+  const BProb P = a.probs[g.prob];
+  const int n = (int)P.n, npb = (int)P.npb;
+  const int ns = g.r1 - g.r0;
+  C* H = static_cast<C*>(a.H) + P.offM;
+  for (int e = threadIdx.x; e < kNB * kNB; e += 256) {
+    C v = C(0);
+    for (int sidx = 0; sidx < ns; ++sidx) v += work[(int64_t)(g.slot + sidx) * kNB * kNB + e];
+    const int r = g.bi * kNB + e / kNB, c = g.bj * kNB + e % kNB;
+    H[(int64_t)r * npb + c] = (r == c && r >= n) ? C(1) : v;
+  }
 }
 
 // =========================================================================================
@@ -826,9 +868,7 @@ __global__ void __launch_bounds__(kCT) solve_init_kernel(BArrays a, const int* l
 //  kResidRqi   the stopping rules (Sec. 3 after Eq. (4)) and, if the problem goes on, the
 //              two shifted solves' start on -f and x
 template <typename T>
-__global__ void __launch_bounds__(kCT) resid_post_kernel(BArrays a, const int* list, int mode,
-                                                         SolveParams sp) {
-  const int pi = list[blockIdx.x];
+__device__ void resid_post_body(const BArrays& a, const int pi, int mode, const SolveParams& sp) {
   BState& st = a.st[pi];
   if (!st.active) return;
   const BProb P = a.probs[pi];
@@ -923,7 +963,8 @@ __global__ void __launch_bounds__(kCT) resid_post_kernel(BArrays a, const int* l
           st.best_psi = psi;
           st.best_s2 = sigma2;
         }
-        if (!up && psi <= sp.tol * st.scale) stop = TLS_STOP_TOL;
+        // tolerance test from the second RQI step on (psi_1 is taken at the start x_1)
+        if (!up && k >= 2 && psi <= sp.tol * st.scale) stop = TLS_STOP_TOL;
         else if (k > sp.max_rqi) stop = TLS_STOP_MAX_RQI;
       }
     }
@@ -953,13 +994,23 @@ __global__ void __launch_bounds__(kCT) resid_post_kernel(BArrays a, const int* l
   pcg_start<T>(a, P, st, 2, ys, vs, dsh);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kCT) resid_post_kernel(BArrays a, const int* list,
+                                                         const int* cnt, int mode,
+                                                         SolveParams sp) {
+  const int n = cnt ? *cnt : (int)gridDim.x;
+  for (int li = blockIdx.x; li < n; li += gridDim.x) {
+    resid_post_body<T>(a, list[li], mode, sp);
+    __syncthreads();
+  }
+}
+
 // One PCGTLS step after the pass t = A q (Alg. 3, operator with A):
 // delta = ||t||^2 - sigma^2 ||q||^2, alpha = eta / delta, w += alpha q,
 // s -= alpha R^{-T}(A^T t - sigma^2 q), eta' = ||s||^2, beta = eta'/eta, p = s + beta p,
 // q = R^{-1} p.
 template <typename T>
-__global__ void __launch_bounds__(kCT) pcg_post_kernel(BArrays a, const int* list) {
-  const int pi = list[blockIdx.x];
+__device__ void pcg_post_body(const BArrays& a, const int pi) {
   BState& st = a.st[pi];
   if (!st.active) return;
   const int nr = st.nr;
@@ -1080,10 +1131,18 @@ __global__ void __launch_bounds__(kCT) pcg_post_kernel(BArrays a, const int* lis
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kCT) pcg_post_kernel(BArrays a, const int* list, const int* cnt) {
+  const int n = cnt ? *cnt : (int)gridDim.x;
+  for (int li = blockIdx.x; li < n; li += gridDim.x) {
+    pcg_post_body<T>(a, list[li]);
+    __syncthreads();
+  }
+}
+
 // x_0 = w (the LS solution of the sigma^2 = 0 solve), ||x_0||^2
 template <typename T>
-__global__ void __launch_bounds__(kCT) ls_finish_kernel(BArrays a, const int* list) {
-  const int pi = list[blockIdx.x];
+__device__ void ls_finish_body(const BArrays& a, const int pi) {
   BState& st = a.st[pi];
   if (!st.active) return;
   const BProb P = a.probs[pi];
@@ -1099,10 +1158,18 @@ __global__ void __launch_bounds__(kCT) ls_finish_kernel(BArrays a, const int* li
   if (threadIdx.x == 0) st.xx = xs[0];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kCT) ls_finish_kernel(BArrays a, const int* list, const int* cnt) {
+  const int n = cnt ? *cnt : (int)gridDim.x;
+  for (int li = blockIdx.x; li < n; li += gridDim.x) {
+    ls_finish_body<T>(a, list[li]);
+    __syncthreads();
+  }
+}
+
 // z = x + w_f, beta_k = (z^T f - g) / (z^T x + 1), x = z + beta_k u (Alg. 2), u = w_x
 template <typename T>
-__global__ void __launch_bounds__(kCT) rqi_update_kernel(BArrays a, const int* list) {
-  const int pi = list[blockIdx.x];
+__device__ void rqi_update_body(const BArrays& a, const int pi) {
   BState& st = a.st[pi];
   if (!st.active) return;
   const BProb P = a.probs[pi];
@@ -1133,6 +1200,15 @@ __global__ void __launch_bounds__(kCT) rqi_update_kernel(BArrays a, const int* l
     st.xx = xs[0];
     st.cg_total += st.iters[0] + st.iters[1];
     st.not_spd_any |= st.not_spd[0] | st.not_spd[1];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCT) rqi_update_kernel(BArrays a, const int* list, const int* cnt) {
+  const int n = cnt ? *cnt : (int)gridDim.x;
+  for (int li = blockIdx.x; li < n; li += gridDim.x) {
+    rqi_update_body<T>(a, list[li]);
+    __syncthreads();
   }
 }
 
@@ -1350,7 +1426,7 @@ void launch_pass_colnorm(const BArrays& a, int ntiles, cudaStream_t s) {
   constexpr size_t sm = pass_smem<double, 1>();
   static const bool once = [] { set_smem(pass_kernel<double, 1, kColnorm>, sm); return true; }();
   (void)once;
-  pass_kernel<double, 1, kColnorm><<<ntiles, kPT, sm, s>>>(a, nullptr);
+  pass_kernel<double, 1, kColnorm><<<ntiles, kPT, sm, s>>>(a, nullptr, nullptr);
   count_launch();
 }
 
@@ -1360,37 +1436,45 @@ void launch_colnorm_post(const BArrays& a, const int* list, int cnt, cudaStream_
   count_launch();
 }
 
-void launch_pass_resid(const BArrays& a, const int* tlist, int ntiles, cudaStream_t s) {
-  if (ntiles <= 0) return;
+void launch_pass_resid(const BArrays& a, const int* tlist, const int* ntile, int grid,
+                       cudaStream_t s) {
+  if (grid <= 0) return;
   constexpr size_t sm = pass_smem<double, 1>();
   static const bool once = [] { set_smem(pass_kernel<double, 1, kResid>, sm); return true; }();
   (void)once;
-  pass_kernel<double, 1, kResid><<<ntiles, kPT, sm, s>>>(a, tlist);
+  pass_kernel<double, 1, kResid><<<grid, kPT, sm, s>>>(a, tlist, ntile);
   count_launch();
 }
 
 template <typename T>
-void launch_pass_pcg(const BArrays& a, const int* tlist, int ntiles, int nr, cudaStream_t s) {
-  if (ntiles <= 0) return;
+void launch_pass_pcg(const BArrays& a, const int* tlist, const int* ntile, int grid, int nr,
+                     cudaStream_t s) {
+  if (grid <= 0) return;
   if (nr == 2) {
     constexpr size_t sm = pass_smem<T, 2>();
     static const bool once = [] { set_smem(pass_kernel<T, 2, kPcg>, sm); return true; }();
     (void)once;
-    pass_kernel<T, 2, kPcg><<<ntiles, kPT, sm, s>>>(a, tlist);
+    pass_kernel<T, 2, kPcg><<<grid, kPT, sm, s>>>(a, tlist, ntile);
   } else {
     constexpr size_t sm = pass_smem<T, 1>();
     static const bool once = [] { set_smem(pass_kernel<T, 1, kPcg>, sm); return true; }();
     (void)once;
-    pass_kernel<T, 1, kPcg><<<ntiles, kPT, sm, s>>>(a, tlist);
+    pass_kernel<T, 1, kPcg><<<grid, kPT, sm, s>>>(a, tlist, ntile);
   }
   count_launch();
 }
 
 template <typename C>
-void launch_gram(const BArrays& a, const int4* gtiles, int ngt, cudaStream_t s) {
-  if (ngt <= 0) return;
-  gram_kernel<C><<<ngt, 256, 0, s>>>(a, gtiles);
-  count_launch();
+void launch_gram(const BArrays& a, const GTile* gtiles, int ngt, const GTile* groups, int ngr,
+                 void* work, cudaStream_t s) {
+  if (ngt > 0) {
+    gram_kernel<C><<<ngt, 64, 0, s>>>(a, gtiles, static_cast<C*>(work));
+    count_launch();
+  }
+  if (ngr > 0) {
+    gram_reduce_kernel<C><<<ngr, 256, 0, s>>>(a, groups, static_cast<const C*>(work));
+    count_launch();
+  }
 }
 
 template <typename C>
@@ -1422,37 +1506,39 @@ void launch_solve_init(const BArrays& a, const int* list, int cnt, cudaStream_t 
 }
 
 template <typename T>
-void launch_resid_post(const BArrays& a, const int* list, int cnt, int mode,
+void launch_resid_post(const BArrays& a, const int* list, const int* cnt, int grid, int mode,
                        const SolveParams& sp, cudaStream_t s) {
-  if (cnt <= 0) return;
+  if (grid <= 0) return;
   constexpr size_t sm = post_smem<T>() + sizeof(double) * kMaxN;
   static const bool once = [] { set_smem(resid_post_kernel<T>, sm); return true; }();
   (void)once;
-  resid_post_kernel<T><<<cnt, kCT, sm, s>>>(a, list, mode, sp);
+  resid_post_kernel<T><<<grid, kCT, sm, s>>>(a, list, cnt, mode, sp);
   count_launch();
 }
 
 template <typename T>
-void launch_pcg_post(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
-  if (cnt <= 0) return;
+void launch_pcg_post(const BArrays& a, const int* list, const int* cnt, int grid, cudaStream_t s) {
+  if (grid <= 0) return;
   constexpr size_t sm = post_smem<T>();
   static const bool once = [] { set_smem(pcg_post_kernel<T>, sm); return true; }();
   (void)once;
-  pcg_post_kernel<T><<<cnt, kCT, sm, s>>>(a, list);
+  pcg_post_kernel<T><<<grid, kCT, sm, s>>>(a, list, cnt);
   count_launch();
 }
 
 template <typename T>
-void launch_ls_finish(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
-  if (cnt <= 0) return;
-  ls_finish_kernel<T><<<cnt, kCT, 0, s>>>(a, list);
+void launch_ls_finish(const BArrays& a, const int* list, const int* cnt, int grid,
+                      cudaStream_t s) {
+  if (grid <= 0) return;
+  ls_finish_kernel<T><<<grid, kCT, 0, s>>>(a, list, cnt);
   count_launch();
 }
 
 template <typename T>
-void launch_rqi_update(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
-  if (cnt <= 0) return;
-  rqi_update_kernel<T><<<cnt, kCT, 0, s>>>(a, list);
+void launch_rqi_update(const BArrays& a, const int* list, const int* cnt, int grid,
+                       cudaStream_t s) {
+  if (grid <= 0) return;
+  rqi_update_kernel<T><<<grid, kCT, 0, s>>>(a, list, cnt);
   count_launch();
 }
 
@@ -1482,10 +1568,12 @@ void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, i
   count_launch();
 }
 
-template void launch_pass_pcg<float>(const BArrays&, const int*, int, int, cudaStream_t);
-template void launch_pass_pcg<double>(const BArrays&, const int*, int, int, cudaStream_t);
-template void launch_gram<float>(const BArrays&, const int4*, int, cudaStream_t);
-template void launch_gram<double>(const BArrays&, const int4*, int, cudaStream_t);
+template void launch_pass_pcg<float>(const BArrays&, const int*, const int*, int, int, cudaStream_t);
+template void launch_pass_pcg<double>(const BArrays&, const int*, const int*, int, int, cudaStream_t);
+template void launch_gram<float>(const BArrays&, const GTile*, int, const GTile*, int, void*,
+                                 cudaStream_t);
+template void launch_gram<double>(const BArrays&, const GTile*, int, const GTile*, int, void*,
+                                  cudaStream_t);
 template void launch_chol<float>(const BArrays&, const int*, int, const double*, int*, cudaStream_t);
 template void launch_chol<double>(const BArrays&, const int*, int, const double*, int*, cudaStream_t);
 template void launch_trtri<float, float>(const BArrays&, const int*, int, cudaStream_t);
@@ -1494,11 +1582,11 @@ template void launch_trtri<double, double>(const BArrays&, const int*, int, cuda
 template void launch_trtri<float, double>(const BArrays&, const int*, int, cudaStream_t);
 #define TLS_BI(T)                                                                                 \
   template void launch_solve_init<T>(const BArrays&, const int*, int, cudaStream_t);              \
-  template void launch_resid_post<T>(const BArrays&, const int*, int, int, const SolveParams&,    \
-                                     cudaStream_t);                                               \
-  template void launch_pcg_post<T>(const BArrays&, const int*, int, cudaStream_t);                \
-  template void launch_ls_finish<T>(const BArrays&, const int*, int, cudaStream_t);               \
-  template void launch_rqi_update<T>(const BArrays&, const int*, int, cudaStream_t);
+  template void launch_resid_post<T>(const BArrays&, const int*, const int*, int, int,             \
+                                     const SolveParams&, cudaStream_t);                           \
+  template void launch_pcg_post<T>(const BArrays&, const int*, const int*, int, cudaStream_t);    \
+  template void launch_ls_finish<T>(const BArrays&, const int*, const int*, int, cudaStream_t);   \
+  template void launch_rqi_update<T>(const BArrays&, const int*, const int*, int, cudaStream_t);
 TLS_BI(float)
 TLS_BI(double)
 #undef TLS_BI

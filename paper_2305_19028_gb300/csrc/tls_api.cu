@@ -490,7 +490,9 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
       TLS_CK(cudaMemcpyAsync(ctx->x_best, ctx->x, sizeof(double) * ctx->npad,
                              cudaMemcpyDeviceToDevice, st));
     }
-    if (!up && psi <= tol * scale) {
+    // the tolerance test from the second RQI step on: psi_1 is taken at the inverse-iteration
+    // start x_1, whose error is only first order in psi_1
+    if (!up && k >= 2 && psi <= tol * scale) {
       stop = TLS_STOP_TOL;
       break;
     }

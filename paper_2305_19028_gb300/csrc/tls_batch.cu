@@ -26,8 +26,7 @@ struct tls_batch {
   std::vector<std::pair<void*, size_t>> bufs;
   std::vector<BProb> hp;
   std::vector<BTile> ht;
-  std::vector<int4> hgram;          // Gram tiles of every problem
-  std::vector<int> gram0;           // first Gram tile of each problem
+
   std::vector<double> hshift;
   std::vector<int> hinfo, shifts, fail_pivot, fallbacks, broke;
   std::vector<tls_prec> uf_used;
@@ -35,7 +34,10 @@ struct tls_batch {
   BProb* dprobs = nullptr;
   BTile* dtiles = nullptr;
   BState* dst = nullptr;
-  int4* dgram = nullptr;
+  GTile* dgram = nullptr;           // Gram CTA list and split-tile reduction list
+  size_t cap_gram = 0;
+  void* gwork = nullptr;            // Gram partial tiles of row-split tiles
+  size_t cap_gwork = 0;
   int* dlist = nullptr;             // problem list of the current launch sequence
   int* dact_probs = nullptr;        // its active problems (compacted)
   int* dact_tiles = nullptr;        // their row tiles (compacted)
@@ -48,6 +50,13 @@ struct tls_batch {
   int64_t cap_poff = 0;
   int64_t tile_bytes[kNumCfg] = {};  // row-tile size (FP32 bytes) per pass lane layout
   int tuned_u = 0;                  // sizeof the u type the tile sizes were tuned for
+  bool use_graph = true;            // replay the solve as one CUDA graph
+  struct Graph {
+    std::vector<double> key;
+    cudaGraphExec_t exec;
+    unsigned long long kernels;     // kernel nodes (for the launch count)
+  };
+  std::vector<Graph> graphs;        // a few captured solves (full list, fallback subsets)
   // selector network
   float* dsel = nullptr;            // parameters (TLS_MLP_PARAMS) + mean (16) + scale (16)
   bool has_sel = false;
@@ -81,6 +90,26 @@ void* balloc(tls_batch* bt, size_t bytes) {
   void* p = tls::hook_alloc(bytes, bt->stream);
   if (p) bt->bufs.push_back({p, bytes});
   return p;
+}
+
+// Grow a device buffer owned by the batch to at least `bytes` (contents are not kept).
+bool ensure_cap(tls_batch* bt, void** p, size_t* cap, size_t bytes) {
+  if (*p && *cap >= bytes) return true;
+  if (*p) {
+    cudaStreamSynchronize(bt->stream);
+    for (size_t i = 0; i < bt->bufs.size(); ++i)
+      if (bt->bufs[i].first == *p) {
+        tls::hook_free(*p, bt->bufs[i].second, bt->stream);
+        bt->bufs.erase(bt->bufs.begin() + (long)i);
+        break;
+      }
+    *p = nullptr;
+    *cap = 0;
+  }
+  *p = balloc(bt, bytes);
+  if (!*p) return false;
+  *cap = bytes;
+  return true;
 }
 
 tls_status cuda_st(tls_batch* bt, cudaError_t e, const char* what) {
@@ -195,6 +224,7 @@ void destroy(tls_batch* bt) {
   if (!bt) return;
   if (bt->stream) cudaStreamSynchronize(bt->stream);
   for (cudaEvent_t e : bt->evpool) cudaEventDestroy(e);
+  for (auto& g : bt->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& b : bt->bufs) tls::hook_free(b.first, b.second, bt->stream);
   if (bt->hcount) cudaFreeHost(bt->hcount);
   if (bt->ev0) cudaEventDestroy(bt->ev0);
@@ -218,20 +248,50 @@ tls_status factor_list(tls_batch* bt, std::vector<int> L, Prec p) {
     for (int i : L) bt->hp[(size_t)i].prec = (int)p;
     BT_CK(cudaMemcpyAsync(bt->dprobs, bt->hp.data(), sizeof(BProb) * bt->hp.size(),
                           cudaMemcpyHostToDevice, st));
-    // Gram tiles of the listed problems (a contiguous range per problem in hgram)
-    std::vector<int4> gl;
-    for (int i : L) {
-      const int64_t nbk = bt->hp[(size_t)i].npb / kNB;
-      const int64_t g0 = bt->gram0[(size_t)i];
-      for (int64_t k = 0; k < nbk * (nbk + 1) / 2; ++k) gl.push_back(bt->hgram[(size_t)(g0 + k)]);
-    }
-    BT_CK(cudaMemcpyAsync(bt->dgram, gl.data(), sizeof(int4) * gl.size(), cudaMemcpyHostToDevice,
-                          st));
+    // Gram CTAs of the listed problems: every upper 64 x 64 tile, its rows split into chunks
+    // of kc rows (FP64 rows cost far more on this GPU, so they are split finer), longest
+    // chunks first; split tiles are summed in slot order afterwards.
     const bool c64 = (p == Prec::FP64);
+    const int64_t kc = c64 ? 512 : 2048;
+    std::vector<GTile> gl, gred;
+    int slots = 0;
+    for (int i : L) {
+      const BProb& P = bt->hp[(size_t)i];
+      const int nbk = (int)(P.npb / kNB);
+      const int ns = (int)((P.m + kc - 1) / kc);
+      for (int bi = 0; bi < nbk; ++bi)
+        for (int bj = bi; bj < nbk; ++bj) {
+          if (ns == 1) {
+            gl.push_back(GTile{i, bi, bj, 0, (int)P.m, -1, 0, 0});
+            continue;
+          }
+          gred.push_back(GTile{i, bi, bj, 0, ns, slots, 0, 0});
+          for (int k = 0; k < ns; ++k)
+            gl.push_back(GTile{i, bi, bj, (int)(k * kc), (int)std::min<int64_t>(P.m, (k + 1) * kc),
+                               slots + k, 0, 0});
+          slots += ns;
+        }
+    }
+    std::stable_sort(gl.begin(), gl.end(), [](const GTile& x, const GTile& y) {
+      return (x.r1 - x.r0) > (y.r1 - y.r0);
+    });
+    const size_t ngl = gl.size(), ngr = gred.size();
+    gl.insert(gl.end(), gred.begin(), gred.end());
+    if (!ensure_cap(bt, reinterpret_cast<void**>(&bt->dgram), &bt->cap_gram,
+                    sizeof(GTile) * std::max<size_t>(gl.size(), 1)) ||
+        !ensure_cap(bt, &bt->gwork, &bt->cap_gwork,
+                    (c64 ? 8 : 4) * (size_t)kNB * kNB * std::max(slots, 1))) {
+      set_err(bt, "device allocation failed (Gram workspace)");
+      return TLS_ERR_OOM;
+    }
+    BT_CK(cudaMemcpyAsync(bt->dgram, gl.data(), sizeof(GTile) * gl.size(), cudaMemcpyHostToDevice,
+                          st));
     {
       BProfScope pr(bt, TLS_PROF_GRAM);
-      if (c64) launch_gram<double>(bt->a, bt->dgram, (int)gl.size(), st);
-      else launch_gram<float>(bt->a, bt->dgram, (int)gl.size(), st);
+      if (c64)
+        launch_gram<double>(bt->a, bt->dgram, (int)ngl, bt->dgram + ngl, (int)ngr, bt->gwork, st);
+      else
+        launch_gram<float>(bt->a, bt->dgram, (int)ngl, bt->dgram + ngl, (int)ngr, bt->gwork, st);
     }
     BT_CK_LAUNCH("batched Gram");
     // shift ladder (the diagonal perturbation of low-precision Cholesky)
@@ -292,6 +352,88 @@ tls_status factor_list(tls_batch* bt, std::vector<int> L, Prec p) {
 }
 
 // Lock-step RQI-PCGTLS over the problems in L (Alg. 2 with the PCGTLS of Alg. 3 / 4).
+//
+// The launch sequence of a whole solve needs no host knowledge of which problems are still
+// active: after every stop test the count_active kernel compacts the active problems and their
+// row tiles into device lists, and the pass / per-problem kernels run persistent grids over
+// those lists. The sequence is issued for k = 1 .. max_rqi + 1 (a stopped problem drops out of
+// the lists; once none is left the remaining kernels find empty lists and return at once), so
+// it is captured once as a CUDA graph and replayed: one graph launch and one synchronisation
+// per solve. With profiling on, the same sequence runs eagerly with one synchronisation per RQI
+// step (event pairs per launch class and per-step work accounting).
+struct SolveGrid {
+  int pass, post;
+};
+
+template <typename T>
+void issue_solve(tls_batch* bt, int cnt, const SolveParams& sp, const SolveGrid& g, bool eager,
+                 tls_status* err) {
+  cudaStream_t st = bt->stream;
+  const BArrays& a = bt->a;
+  const int* dl = bt->dact_probs;
+  const int* tl = bt->dact_tiles;
+  const int* n_prob = bt->dcount;       // device counts written by count_active
+  const int* n_tile = bt->dcount + 1;
+  int64_t elems = 0;
+  auto refresh = [&]() -> bool {        // returns false when no problem is left (eager only)
+    {
+      BProfScope pr(bt, TLS_PROF_VEC);
+      launch_count_active(a, bt->dlist, cnt, bt->dcount, bt->dact_probs, bt->dact_tiles, st);
+    }
+    if (!eager) return true;
+    if (cudaMemcpyAsync(bt->hcount, bt->dcount, 4 * sizeof(int), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      *err = TLS_ERR_CUDA;
+      return false;
+    }
+    unsigned long long el = 0ull;
+    std::memcpy(&el, bt->hcount + 2, sizeof(el));
+    elems = (int64_t)el;
+    return bt->hcount[0] > 0;
+  };
+  auto resid = [&](int mode) {
+    {
+      BProfScope pr(bt, TLS_PROF_RESID_PASS);
+      launch_pass_resid(a, tl, n_tile, g.pass, st);
+      if (bt->prof) bt->prof_elems[TLS_PROF_RESID_PASS] += elems;
+    }
+    BProfScope pr(bt, TLS_PROF_RESID_REDUCE);
+    launch_resid_post<T>(a, dl, n_prob, g.post, mode, sp, st);
+  };
+  auto pcg_step = [&](int nr) {
+    {
+      BProfScope pr(bt, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
+      launch_pass_pcg<T>(a, tl, n_tile, g.pass, nr, st);
+      if (bt->prof) bt->prof_elems[nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1] += elems;
+    }
+    BProfScope pr(bt, TLS_PROF_PCG_REDUCE);
+    launch_pcg_post<T>(a, dl, n_prob, g.post, st);
+  };
+  {
+    BProfScope pr(bt, TLS_PROF_VEC);
+    launch_solve_init<T>(a, bt->dlist, cnt, st);
+  }
+  if (!refresh()) return;
+  // line 1: LS start, x = 0 residual (f = -A^T b), PCGTLS with sigma^2 = 0
+  resid(kResidLs);
+  for (int j = 0; j < std::max(1, bt->opt.ls_iters); ++j) pcg_step(1);
+  {
+    BProfScope pr(bt, TLS_PROF_VEC);
+    launch_ls_finish<T>(a, dl, n_prob, g.post, st);
+  }
+  // lines 2-5: sigma_0^2 and the inverse-iteration step
+  resid(kResidStart);
+  for (int k = 1; k <= sp.max_rqi + 1; ++k) {
+    resid(kResidRqi);
+    if (!refresh()) return;
+    const int steps = sp.cg_fixed ? (k + 1) : std::max(1, sp.cg_max);
+    for (int j = 0; j < steps; ++j) pcg_step(2);
+    BProfScope pr(bt, TLS_PROF_VEC);
+    launch_rqi_update<T>(a, dl, n_prob, g.post, st);
+  }
+}
+
 template <typename T>
 tls_status solve_list(tls_batch* bt, const std::vector<int>& L, const SolveParams& sp) {
   cudaStream_t st = bt->stream;
@@ -299,74 +441,52 @@ tls_status solve_list(tls_batch* bt, const std::vector<int>& L, const SolveParam
   if (cnt == 0) return TLS_OK;
   tls_status s = upload_list(bt, L);
   if (s != TLS_OK) return s;
-  const BArrays& a = bt->a;
-  // compacted lists of the active problems and their row tiles (rebuilt at every check)
-  const int* dl = bt->dact_probs;
-  const int* tl = bt->dact_tiles;
-  int cnt_act = 0, nt = 0;
-  int64_t elems = 0;   // entries of A of the active problems
-  auto refresh = [&]() -> tls_status {
-    {
-      BProfScope pr(bt, TLS_PROF_VEC);
-      launch_count_active(a, bt->dlist, cnt, bt->dcount, bt->dact_probs, bt->dact_tiles, st);
-    }
-    BT_CK_LAUNCH("batched active set");
-    BT_CK(cudaMemcpyAsync(bt->hcount, bt->dcount, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    BT_CK(cudaStreamSynchronize(st));
-    cnt_act = bt->hcount[0];
-    nt = bt->hcount[1];
-    unsigned long long el = 0ull;
-    std::memcpy(&el, bt->hcount + 2, sizeof(el));
-    elems = (int64_t)el;
+  int tiles = 0;
+  for (int i : L) tiles += bt->hp[(size_t)i].ntiles;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  SolveGrid g{std::max(1, std::min(tiles, 4 * sms)), std::max(1, std::min(cnt, 4 * sms))};
+  tls_status err = TLS_OK;
+  if (bt->prof || !bt->use_graph) {
+    issue_solve<T>(bt, cnt, sp, g, true, &err);
+    if (err != TLS_OK) return err;
+    BT_CK_LAUNCH("batched solve");
     return TLS_OK;
-  };
-  auto resid = [&](int mode) {
-    {
-      BProfScope pr(bt, TLS_PROF_RESID_PASS);
-      launch_pass_resid(a, tl, nt, st);
-      if (bt->prof) bt->prof_elems[TLS_PROF_RESID_PASS] += elems;
-    }
-    BProfScope pr(bt, TLS_PROF_RESID_REDUCE);
-    launch_resid_post<T>(a, dl, cnt_act, mode, sp, st);
-  };
-  auto pcg_step = [&](int nr) {
-    {
-      BProfScope pr(bt, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
-      launch_pass_pcg<T>(a, tl, nt, nr, st);
-      if (bt->prof) bt->prof_elems[nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1] += elems;
-    }
-    BProfScope pr(bt, TLS_PROF_PCG_REDUCE);
-    launch_pcg_post<T>(a, dl, cnt_act, st);
-  };
-  {
-    BProfScope pr(bt, TLS_PROF_VEC);
-    launch_solve_init<T>(a, bt->dlist, cnt, st);
   }
-  s = refresh();
-  if (s != TLS_OK) return s;
-  // line 1: LS start, x = 0 residual (f = -A^T b), PCGTLS with sigma^2 = 0
-  resid(kResidLs);
-  for (int j = 0; j < std::max(1, bt->opt.ls_iters); ++j) pcg_step(1);
-  {
-    BProfScope pr(bt, TLS_PROF_VEC);
-    launch_ls_finish<T>(a, dl, cnt_act, st);
-  }
-  // lines 2-5: sigma_0^2 and the inverse-iteration step
-  resid(kResidStart);
-  BT_CK_LAUNCH("batched solve start");
-  for (int k = 1; k <= sp.max_rqi + 2; ++k) {
-    resid(kResidRqi);
-    s = refresh();
-    if (s != TLS_OK) return s;
-    if (cnt_act == 0) break;
-    const int steps = sp.cg_fixed ? (k + 1) : std::max(1, sp.cg_max);
-    for (int j = 0; j < steps; ++j) pcg_step(2);
-    {
-      BProfScope pr(bt, TLS_PROF_VEC);
-      launch_rqi_update<T>(a, dl, cnt_act, st);
+  // graph: captured once per (problem list, solve parameters, grids), replayed afterwards
+  std::vector<double> key = {(double)sizeof(T), (double)cnt, (double)tiles, (double)g.pass,
+                             (double)g.post, sp.tol, sp.psi_accept, (double)sp.max_rqi,
+                             (double)sp.psi_rule_ge, (double)sp.cg_fixed, (double)sp.cg_max,
+                             sp.cg_tol, (double)bt->opt.ls_iters, bt->a.cg_tol ? 1.0 : 0.0};
+  for (int i : L) key.push_back((double)i);
+  tls_batch::Graph* gr = nullptr;
+  for (auto& c : bt->graphs)
+    if (c.key == key) gr = &c;
+  if (!gr) {
+    if (bt->graphs.size() >= 4) {
+      cudaGraphExecDestroy(bt->graphs.front().exec);
+      bt->graphs.erase(bt->graphs.begin());
     }
-    BT_CK_LAUNCH("batched PCGTLS");
+    cudaGraph_t graph = nullptr;
+    const unsigned long long l0 = tls::g_launches.load();
+    BT_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    issue_solve<T>(bt, cnt, sp, g, false, &err);
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    // capturing launches nothing: the nodes are counted when the graph is launched
+    const unsigned long long nodes = tls::g_launches.load() - l0;
+    tls::g_launches.fetch_sub(nodes);
+    if (err != TLS_OK) return err;
+    BT_CK(ce);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    BT_CK(ie);
+    bt->graphs.push_back({key, exec, nodes});
+    gr = &bt->graphs.back();
   }
+  BT_CK(cudaGraphLaunch(gr->exec, st));
+  tls::count_launch((int)gr->kernels);
   return TLS_OK;
 }
 
@@ -417,16 +537,16 @@ tls_status tune_tiles(tls_batch* bt) {
       BT_CK(cudaMemcpyAsync(bt->dact_tiles, tl.data(), sizeof(int) * tl.size(),
                             cudaMemcpyHostToDevice, st));
       const int nt = (int)tl.size();
-      launch_pass_pcg<T>(bt->a, bt->dact_tiles, nt, 2, st);   // warm-up
-      launch_pass_resid(bt->a, bt->dact_tiles, nt, st);
+      launch_pass_pcg<T>(bt->a, bt->dact_tiles, nullptr, nt, 2, st);   // warm-up
+      launch_pass_resid(bt->a, bt->dact_tiles, nullptr, nt, st);
       BT_CK(cudaEventRecord(bt->ev0, st));
-      for (int r = 0; r < 3; ++r) launch_pass_pcg<T>(bt->a, bt->dact_tiles, nt, 2, st);
+      for (int r = 0; r < 3; ++r) launch_pass_pcg<T>(bt->a, bt->dact_tiles, nullptr, nt, 2, st);
       BT_CK(cudaEventRecord(bt->ev1, st));
       BT_CK(cudaEventSynchronize(bt->ev1));
       float ms_p = 0.f, ms_r = 0.f;
       cudaEventElapsedTime(&ms_p, bt->ev0, bt->ev1);
       BT_CK(cudaEventRecord(bt->ev0, st));
-      launch_pass_resid(bt->a, bt->dact_tiles, nt, st);
+      launch_pass_resid(bt->a, bt->dact_tiles, nullptr, nt, st);
       BT_CK(cudaEventRecord(bt->ev1, st));
       BT_CK(cudaEventSynchronize(bt->ev1));
       cudaEventElapsedTime(&ms_r, bt->ev0, bt->ev1);
@@ -600,9 +720,8 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
     bt->own_stream = true;
   }
   // layout
-  int64_t offA = 0, offB = 0, offV = 0, offM = 0, ngram = 0;
+  int64_t offA = 0, offB = 0, offV = 0, offM = 0;
   bt->hp.resize((size_t)count);
-  bt->gram0.resize((size_t)count);
   for (int i = 0; i < count; ++i) {
     BProb& P = bt->hp[(size_t)i];
     P.m = m[i];
@@ -619,11 +738,6 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
     offB += rup(P.m, 32);
     offV += P.npb;
     offM += P.npb * P.npb;
-    const int nbk = (int)(P.npb / kNB);
-    bt->gram0[(size_t)i] = (int)ngram;
-    for (int bi = 0; bi < nbk; ++bi)
-      for (int bj = bi; bj < nbk; ++bj) bt->hgram.push_back(make_int4(i, bi, bj, 0));
-    ngram += (int64_t)nbk * (nbk + 1) / 2;
   }
   // the smallest tiles give the most tiles and partials: size the buffers for them
   for (int c = 0; c < kNumCfg; ++c) bt->tile_bytes[c] = kTileMin;
@@ -636,7 +750,6 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   bt->dprobs = static_cast<BProb*>(balloc(bt, sizeof(BProb) * count));
   bt->dtiles = static_cast<BTile*>(balloc(bt, sizeof(BTile) * bt->ht.size()));
   bt->dst = static_cast<BState*>(balloc(bt, sizeof(BState) * count));
-  bt->dgram = static_cast<int4*>(balloc(bt, sizeof(int4) * (size_t)std::max<int64_t>(ngram, 1)));
   bt->dlist = static_cast<int*>(balloc(bt, sizeof(int) * count));
   bt->dact_probs = static_cast<int*>(balloc(bt, sizeof(int) * count));
   bt->dact_tiles = static_cast<int*>(balloc(bt, sizeof(int) * bt->ht.size()));
@@ -668,7 +781,7 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   a.partU = balloc(bt, sizeof(double) * 2 * (size_t)std::max<int64_t>(poff, 1));
   a.part64 = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)std::max<int64_t>(poff, 1)));
   a.spart = static_cast<double*>(balloc(bt, sizeof(double) * 4 * bt->ht.size()));
-  if (!bt->dprobs || !bt->dtiles || !bt->dst || !bt->dgram || !bt->dlist || !bt->dshift ||
+  if (!bt->dprobs || !bt->dtiles || !bt->dst || !bt->dlist || !bt->dshift ||
       !bt->dact_probs || !bt->dact_tiles || !bt->dsel || !bt->dF || !bt->dnet || !bt->dfint ||
       !bt->dcgtol ||
       !bt->dinfo || !bt->dcount || !A64 || !a.A32 || !bb || !a.d || !a.dinv || !a.dinv32 ||

@@ -46,6 +46,12 @@ struct BProb {
 
 struct BTile { int prob, row0, rows, pad_; };
 
+// One CTA of the batched Gram: the 64 x 64 tile (bi, bj) of problem `prob` over rows [r0, r1);
+// slot >= 0: a partial tile written to workspace slot `slot` (rows split over several CTAs).
+// For the reduction list the same struct names a split tile: its slots are slot .. slot +
+// (r1 - r0) - 1.
+struct GTile { int prob, bi, bj, r0, r1, slot, pad0_, pad1_; };
+
 // Device state of one problem (host reads it back at the end of a solve).
 struct BState {
   // factor
@@ -100,11 +106,17 @@ struct SolveParams {
 // ---- launchers (k_batch.cu) --------------------------------------------------------------
 void launch_pass_colnorm(const BArrays& a, int ntiles, cudaStream_t s);
 void launch_colnorm_post(const BArrays& a, const int* list, int cnt, cudaStream_t s);
-void launch_pass_resid(const BArrays& a, const int* tlist, int ntiles, cudaStream_t s);
+// Pass and per-problem kernels take a work list and its length: a device count with a
+// persistent grid that loops over the list (graph-capturable: no host knowledge of the count),
+// or NULL with one list entry per CTA (grid = the list length).
+void launch_pass_resid(const BArrays& a, const int* tlist, const int* ntile, int grid,
+                       cudaStream_t s);
 template <typename T>
-void launch_pass_pcg(const BArrays& a, const int* tlist, int ntiles, int nr, cudaStream_t s);
+void launch_pass_pcg(const BArrays& a, const int* tlist, const int* ntile, int grid, int nr,
+                     cudaStream_t s);
 template <typename C>
-void launch_gram(const BArrays& a, const int4* gtiles, int ngt, cudaStream_t s);
+void launch_gram(const BArrays& a, const GTile* gtiles, int ngt, const GTile* groups, int ngr,
+                 void* work, cudaStream_t s);
 template <typename C>
 void launch_chol(const BArrays& a, const int* list, int cnt, const double* shift, int* info,
                  cudaStream_t s);
@@ -113,14 +125,16 @@ void launch_trtri(const BArrays& a, const int* list, int cnt, cudaStream_t s);
 template <typename T>
 void launch_solve_init(const BArrays& a, const int* list, int cnt, cudaStream_t s);
 template <typename T>
-void launch_resid_post(const BArrays& a, const int* list, int cnt, int mode,
+void launch_resid_post(const BArrays& a, const int* list, const int* cnt, int grid, int mode,
                        const SolveParams& sp, cudaStream_t s);
 template <typename T>
-void launch_pcg_post(const BArrays& a, const int* list, int cnt, cudaStream_t s);
+void launch_pcg_post(const BArrays& a, const int* list, const int* cnt, int grid, cudaStream_t s);
 template <typename T>
-void launch_ls_finish(const BArrays& a, const int* list, int cnt, cudaStream_t s);
+void launch_ls_finish(const BArrays& a, const int* list, const int* cnt, int grid,
+                      cudaStream_t s);
 template <typename T>
-void launch_rqi_update(const BArrays& a, const int* list, int cnt, cudaStream_t s);
+void launch_rqi_update(const BArrays& a, const int* list, const int* cnt, int grid,
+                       cudaStream_t s);
 template <typename C, typename T>
 void launch_features(const BArrays& a, const int* list, int cnt, const int* nshift,
                      const int* fpiv, const int* prec, const double* shift, const float* mean,

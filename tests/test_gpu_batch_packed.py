@@ -126,3 +126,22 @@ def test_packed_batch_validation():
     with tls.Batch([(q.A, q.b)]) as bt:
         with pytest.raises(tls.TLSError):
             bt.solve()                          # before factor: state error
+
+
+def test_graph_replay_equals_eager_launches():
+    # the solve is captured once as a CUDA graph and replayed; with profiling on the same
+    # launches run eagerly with a synchronisation per RQI step. Every kernel is deterministic,
+    # so all three runs give bit-identical results.
+    probs = _mixed_problems()[:6]
+    with tls.Batch([(p.A, p.b) for p in probs]) as bt:
+        bt.factor("fp16", u="fp32", fallback=0)
+        x1, s1, i1, _ = bt.solve(tol=0.0, max_rqi=12)
+        x2, s2, i2, _ = bt.solve(tol=0.0, max_rqi=12)
+        bt.profile(True)
+        x3, s3, i3, _ = bt.solve(tol=0.0, max_rqi=12)
+        prof = bt.profile_get()
+    assert np.array_equal(s1, s2) and np.array_equal(s1, s3)
+    for a, b, c in zip(x1, x2, x3):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert [i["rqi_steps"] for i in i1] == [i["rqi_steps"] for i in i3]
+    assert prof["pcg_pass2"][0] > 0 and prof["resid_pass"][0] > 0
