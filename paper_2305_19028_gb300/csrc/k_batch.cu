@@ -123,7 +123,9 @@ __device__ __forceinline__ void pass_body(const BArrays& a, const BProb& P, cons
       }
   }
   TA sc0 = TA(0), sc1 = TA(0);
-  constexpr int RU = 8 / CH;   // rows per group in flight: ~8 vector loads per lane
+  // rows per group in flight: ~8 vector loads per lane (FP32), ~4 (FP64: twice the bytes per
+  // load and twice the registers per value; two CTAs per SM hide the FP64 pipe's latency)
+  constexpr int RU = (sizeof(TA) == 8) ? (CH >= 4 ? 1 : 4 / CH) : 8 / CH;
   for (int base = warp * G; base < t.rows; base += RU * NG) {   // warp-uniform trip count
     int rr[RU];
     bool hv[RU];
@@ -255,7 +257,7 @@ __device__ __forceinline__ void pass_body(const BArrays& a, const BProb& P, cons
 // ntile: device count of the tile list (a persistent grid loops over it), or NULL: one tile
 // per CTA (tlist NULL: tile = CTA index)
 template <typename TA, int NR, int MODE>
-__global__ void __launch_bounds__(kPT) pass_kernel(BArrays a, const int* __restrict__ tlist,
+__global__ void __launch_bounds__(kPT, (sizeof(TA) == 8 && NR == 2) ? 1 : 2) pass_kernel(BArrays a, const int* __restrict__ tlist,
                                                    const int* __restrict__ ntile) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nt = ntile ? *ntile : (int)gridDim.x;
@@ -328,19 +330,17 @@ __global__ void __launch_bounds__(kCT) colnorm_post_kernel(BArrays a, const int*
 // =========================================================================================
 // Gram H = A_s^T A_s, A_s = fl_uf(A D^{-1}) (upper 64 x 64 tiles of every problem)
 // =========================================================================================
-template <typename C>
-__device__ __forceinline__ C scaled_entry(const BArrays& a, const BProb& P, int64_t row, int col);
-template <>
-__device__ __forceinline__ float scaled_entry<float>(const BArrays& a, const BProb& P, int64_t row,
-                                                     int col) {
-  // FP32 product fl32(fl32(a_ij) * fl32(1/d_j)), then rounded to u_f
-  return round_uf(a.A32[P.offA + row * P.lda + col] * a.dinv32[P.offV + col], P.prec);
-}
-template <>
-__device__ __forceinline__ double scaled_entry<double>(const BArrays& a, const BProb& P,
-                                                       int64_t row, int col) {
-  return round_uf(a.A64[P.offA + row * P.lda + col] * a.dinv[P.offV + col], P.prec);
-}
+// fl_uf(a_ij / d_j): FP32 path fl32(fl32(a_ij) * fl32(1/d_j)) rounded to u_f (the product a
+// tensor core would form from the stored operand); FP64 path a_ij * (1/d_j) in FP64
+template <typename C> struct GramSrc;
+template <> struct GramSrc<float> {
+  static __device__ __forceinline__ const float* A(const BArrays& a) { return a.A32; }
+  static __device__ __forceinline__ float dinv(const BArrays& a, int64_t k) { return a.dinv32[k]; }
+};
+template <> struct GramSrc<double> {
+  static __device__ __forceinline__ const double* A(const BArrays& a) { return a.A64; }
+  static __device__ __forceinline__ double dinv(const BArrays& a, int64_t k) { return a.dinv[k]; }
+};
 
 // One CTA (64 threads, 8 x 8 outputs each) forms the 64 x 64 tile H[I][J] over the rows
 // [r0, r1) of its problem: staged 32-row chunks of the scaled, u_f-rounded columns of I and J
@@ -364,18 +364,28 @@ __global__ void __launch_bounds__(64) gram_kernel(BArrays a, const GTile* __rest
     for (int j = 0; j < 8; ++j) acc[i][j] = C(0);
   // this thread stages column tid of each block; its scale factor stays in a register
   const bool okA = c0 + tid < n, okB = c1 + tid < n;
+  const C* Ab = GramSrc<C>::A(a) + P.offA;
+  const C dA = okA ? GramSrc<C>::dinv(a, P.offV + c0 + tid) : C(0);
+  const C dB = okB ? GramSrc<C>::dinv(a, P.offV + c1 + tid) : C(0);
+  const int lda = (int)P.lda, prec = P.prec;
   for (int64_t r0 = g.r0; r0 < g.r1; r0 += 32) {
     const int rows = (int)min((int64_t)32, (int64_t)g.r1 - r0);
-#pragma unroll 4
-    for (int rr = 0; rr < 32; ++rr) {
-      const int64_t row = r0 + rr;
-      C va = C(0), vb = C(0);
-      if (rr < rows) {
-        if (okA) va = scaled_entry<C>(a, P, row, c0 + tid);
-        if (!diag && okB) vb = scaled_entry<C>(a, P, row, c1 + tid);
+    // the loads of 16 rows first, then their scaling and the stores to shared memory
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+      C ra[16], rb[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int rr = h + u;
+        const int64_t row = r0 + rr;
+        ra[u] = (rr < rows && okA) ? Ab[row * lda + c0 + tid] : C(0);
+        rb[u] = (!diag && rr < rows && okB) ? Ab[row * lda + c1 + tid] : C(0);
       }
-      SA[rr][tid] = va;
-      if (!diag) SB[rr][tid] = vb;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        SA[h + u][tid] = round_uf(ra[u] * dA, prec);
+        if (!diag) SB[h + u][tid] = round_uf(rb[u] * dB, prec);
+      }
     }
     __syncthreads();
     const C (*B)[kLd] = diag ? SA : SB;
