@@ -84,6 +84,14 @@ enum {
  * Enabling (or disabling) resets the sums.
  */
 tls_status tls_profile_enable(tls_ctx* ctx, int on);
+
+/*
+ * tls_set_pass_variant -- replace the autotuned kernel of the dense passes over A (until the
+ * next tls_factor): 0 register kernel, 1 / 2 bulk-copy-staged with 256 / 512 threads (only
+ * where the staging fits: TLS_ERR_ARG otherwise), 3 pipelined register kernel. For the FP64
+ * residual pass and the PCGTLS pass respectively. TLS_ERR_STATE before tls_factor or for CSR.
+ */
+tls_status tls_set_pass_variant(tls_ctx* ctx, int variant_fp64, int variant_u);
 /* Launch count and summed device milliseconds of one class (TLS_PROF_*). */
 tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* ms);
 /* The same per-class timing for a packed batch (classes as above; PCG_REDUCE covers the

@@ -263,8 +263,8 @@ __device__ __forceinline__ double round_prec(double v, int prec) {
 //  1. factor the block (256 threads, one barrier per pivot; each finished row of R_KK, rounded
 //     to the factor precision, goes straight to global memory, so the shared copy keeps the
 //     unscaled row and the update of step k reads it as S[k][i] S[k][j] / S[k][k]);
-//  2. invert the rounded R_KK by a 2 x 2 recursion on 32-blocks,
-//     W_KK = [[X11, -X11 R12 X22], [0, X22]], X11 = R11^{-1}, X22 = R22^{-1}, into W.
+//  2. invert the rounded R_KK by doubling from 8 x 8 blocks,
+//     [[X11, -X11 R12 X22], [0, X22]] at block sizes 8, 16, 32, into W.
 // W_KK turns the panel solve R_KJ = R_KK^{-T} H_KJ into a product, and it is also the diagonal
 // block of W = R^{-1}. Nothing runs if an earlier block broke down (*info != 0).
 template <typename T>
@@ -318,9 +318,12 @@ __global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t
     X[r][c] = T(0);
   }
   __syncthreads();
-  // X11 = R11^{-1} (threads 0..31) and X22 = R22^{-1} (threads 32..63), one column each
+  // inverse by doubling: the eight 8 x 8 diagonal blocks by substitution (thread: one column,
+  // chains of at most 8), then for s = 8, 16, 32 every pair of s-blocks A, B gets
+  // X_AB = -X_AA (R_AB X_BB) as two small products; Tm = R_AB X_BB lives in the (zero, unused)
+  // lower part of S
   if (tid < 64) {
-    const int o = (tid < 32) ? 0 : 32, j = tid & 31;
+    const int o = (tid >> 3) * 8, j = tid & 7;
     for (int i = j; i >= 0; --i) {
       T v = (i == j) ? T(1) : T(0);
       for (int k = i + 1; k <= j; ++k) v = fma(-S[o + i][o + k], X[o + k][o + j], v);
@@ -328,21 +331,25 @@ __global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t
     }
   }
   __syncthreads();
-  // Tm = R12 X22 into the (zero) lower-left quarter of S, then X12 = -X11 Tm
-  for (int e = tid; e < 32 * 32; e += 256) {
-    const int i = e / 32, j = e % 32;
-    T v = T(0);
-    for (int k = 0; k <= j; ++k) v = fma(S[i][32 + k], X[32 + k][32 + j], v);
-    S[32 + i][j] = v;
+  for (int sb = 8; sb < NB; sb *= 2) {
+    const int pairs = NB / (2 * sb), cnt = pairs * sb * sb;
+    for (int e = tid; e < cnt; e += 256) {
+      const int pr = e / (sb * sb), rem = e % (sb * sb), i = rem / sb, j = rem % sb;
+      const int a = 2 * pr * sb;
+      T v = T(0);
+      for (int k = 0; k <= j; ++k) v = fma(S[a + i][a + sb + k], X[a + sb + k][a + sb + j], v);
+      S[a + sb + i][a + j] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt; e += 256) {
+      const int pr = e / (sb * sb), rem = e % (sb * sb), i = rem / sb, j = rem % sb;
+      const int a = 2 * pr * sb;
+      T v = T(0);
+      for (int k = i; k < sb; ++k) v = fma(X[a + i][a + k], S[a + sb + k][a + j], v);
+      X[a + i][a + sb + j] = -v;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = tid; e < 32 * 32; e += 256) {
-    const int i = e / 32, j = e % 32;
-    T v = T(0);
-    for (int k = i; k < 32; ++k) v = fma(X[i][k], S[32 + k][j], v);
-    X[i][32 + j] = -v;
-  }
-  __syncthreads();
   for (int e = tid; e < NB * NB; e += 256) {
     const int r = e / NB, c = e % NB;
     W[(kb + r) * npad + kb + c] = X[r][c];

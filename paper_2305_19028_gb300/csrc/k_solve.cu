@@ -229,6 +229,151 @@ __global__ void __launch_bounds__(kThreads) apass_kernel(
 }
 
 // ---------------------------------------------------------------------------------------
+// The same fused pass with direct vector loads, software pipelined: a tile of RW rows is
+// loaded into registers while the previous tile is reduced, so every thread keeps RW * VPT
+// vector loads in flight across the two barriers of a tile. Dots: one shuffle tree per (row,
+// RHS) value and warp, then warp 0 sums the kWarps warp partials and broadcasts the NR * RW
+// results through shared memory (one read per value per thread instead of kWarps).
+// ---------------------------------------------------------------------------------------
+template <typename T, int NR, bool RESID, int VPT>
+__global__ void __launch_bounds__(kThreads, 1) apass_pipe_kernel(
+    const T* __restrict__ A, int64_t lda, int64_t m, int64_t npad, const T* __restrict__ v,
+    int64_t ldv, const double* __restrict__ b, T* __restrict__ part,
+    double* __restrict__ spart, double* __restrict__ sout, unsigned int* counter,
+    const int* __restrict__ done) {
+  using V = typename VecOf<T>::type;
+  constexpr int VW = VecOf<T>::W;
+  constexpr int RW = (VPT >= 16) ? 1 : (16 / VPT);  // rows per tile
+  constexpr int E = VPT * VW;
+  constexpr int NV = NR * RW;                        // dot values per tile
+  __shared__ T red[kWarps][NV];
+  __shared__ T full[NV];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (done != nullptr) {
+    bool all = true;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) all = all && (done[r] != 0);
+    if (all) return;   // uniform over the grid: no CTA touches the counter
+  }
+  T vv[NR][E], acc[NR][E];
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      V x = zero_vec(T(0));
+      if (col < npad) x = *reinterpret_cast<const V*>(v + r * ldv + col);
+#pragma unroll
+      for (int c = 0; c < VW; ++c) { vv[r][k * VW + c] = get(x, c); acc[r][k * VW + c] = T(0); }
+    }
+  }
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = min(m, r0 + per);
+  // lane l < NV of warp 0 always reduces value l (RHS l / RW): its sums stay in two scalars
+  T s_cc = T(0), s_bc = T(0);
+  auto load = [&](V (&a)[RW][VPT], int64_t i0) {
+#pragma unroll
+    for (int rt = 0; rt < RW; ++rt) {
+      const int64_t row = i0 + rt;
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+        a[rt][k] = (row < r1 && col < npad)
+                       ? __ldcs(reinterpret_cast<const V*>(A + row * lda + col))
+                       : zero_vec(T(0));
+      }
+    }
+  };
+  auto process = [&](const V (&a)[RW][VPT], int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int rt = 0; rt < RW; ++rt) {
+        T t = T(0);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k)
+#pragma unroll
+          for (int c = 0; c < VW; ++c) t = fma(get(a[rt][k], c), vv[r][k * VW + c], t);
+        t = warp_sum(t);
+        if (lane == 0) red[warp][r * RW + rt] = t;
+      }
+    __syncthreads();
+    if (warp == 0 && lane < NV) {
+      const int rt = lane % RW;
+      const int64_t row = i0 + rt;
+      T dot = T(0);
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) dot += red[w][lane];
+      T brow = T(0);
+      if (RESID && row < r1) brow = (T)b[row];
+      T c = T(0);
+      if (row < r1) c = RESID ? (brow - dot) : dot;
+      full[lane] = c;
+      s_cc = fma(c, c, s_cc);
+      s_bc = fma(brow, c, s_bc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rt = 0; rt < RW; ++rt)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T c = full[r * RW + rt];
+#pragma unroll
+        for (int k = 0; k < VPT; ++k)
+#pragma unroll
+          for (int cc = 0; cc < VW; ++cc)
+            acc[r][k * VW + cc] = fma(c, get(a[rt][k], cc), acc[r][k * VW + cc]);
+      }
+  };
+  V a0[RW][VPT], a1[RW][VPT];
+  int64_t i0 = r0;
+  if (i0 < r1) load(a0, i0);
+  while (i0 < r1) {
+    if (i0 + RW < r1) load(a1, i0 + RW);   // next tile in flight during this tile's barriers
+    process(a0, i0);
+    i0 += RW;
+    if (i0 >= r1) break;
+    if (i0 + RW < r1) load(a0, i0 + RW);
+    process(a1, i0);
+    i0 += RW;
+  }
+  // publish this CTA's partial of A^T c
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const int64_t col = ((int64_t)k * kThreads + tid) * VW;
+    if (col < npad)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        V x;
+        if constexpr (VW == 4) {
+          x = make_float4(acc[r][k * 4], acc[r][k * 4 + 1], acc[r][k * 4 + 2], acc[r][k * 4 + 3]);
+        } else {
+          x = make_double2(acc[r][k * 2], acc[r][k * 2 + 1]);
+        }
+        *reinterpret_cast<V*>(part + ((int64_t)blockIdx.x * NR + r) * npad + col) = x;
+      }
+  }
+  // scalar sums: lanes < NV of warp 0 hold partials of the rows they reduced
+  if (warp == 0) {
+    const int rl = lane / RW;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const T cc = warp_sum((lane < NV && rl == r) ? s_cc : T(0));
+      const T bc = warp_sum((lane < NV && rl == r) ? s_bc : T(0));
+      if (lane == 0) {
+        spart[((int64_t)blockIdx.x * NR + r) * 2 + 0] = (double)cc;
+        spart[((int64_t)blockIdx.x * NR + r) * 2 + 1] = (double)bc;
+      }
+    }
+  }
+  if (arrive_last(counter)) {
+    reduce_partials<2 * NR>(spart, (int)gridDim.x, sout);
+    if (tid == 0) *counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // The same fused pass with the rows staged through shared memory by 1-D bulk async copies
 // (cp.async.bulk, completion on mbarriers). A CTA owns a contiguous block of rows, i.e. one
 // contiguous span of A, and streams it in tiles of RT rows through a kApStages-deep ring, so
@@ -958,6 +1103,18 @@ void apass_tma_dispatch(int threads, int vpt, dim3 grid, size_t smem, const T* A
 }
 
 template <typename T, int NR, bool RESID>
+void apass_pipe_dispatch(int vpt, dim3 grid, const T* A, int64_t lda, int64_t m, int64_t npad,
+                         const T* v, int64_t ldv, const double* b, T* part, double* spart,
+                         double* sout, unsigned int* counter, const int* done, cudaStream_t s) {
+  switch (vpt) {
+#define TLS_AP(V) \
+  case V: apass_pipe_kernel<T, NR, RESID, V><<<grid, kThreads, 0, s>>>(A, lda, m, npad, v, ldv, b, part, spart, sout, counter, done); count_launch(); break;
+    TLS_AP(1) TLS_AP(2) TLS_AP(4) TLS_AP(8)
+#undef TLS_AP
+    default: break;
+  }
+}
+template <typename T, int NR, bool RESID>
 void apass_dispatch(int vpt, dim3 grid, const T* A, int64_t lda, int64_t m, int64_t npad,
                     const T* v, int64_t ldv, const double* b, T* part, double* spart,
                     double* sout, unsigned int* counter, const int* done, cudaStream_t s) {
@@ -982,7 +1139,8 @@ ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms, int variant) 
   int64_t need = (npad + (int64_t)kThreads * VW - 1) / ((int64_t)kThreads * VW);
   p.vpt = 1;
   while (p.vpt < need) p.vpt *= 2;
-  // variant 0: registers only (apass_kernel); 1: staged, 256 threads; 2: staged, 512 threads
+  // variant 0: registers only (apass_kernel); 1: staged, 256 threads; 2: staged, 512 threads;
+  // 3: registers, software pipelined (apass_pipe_kernel)
   p.threads = (variant == 2) ? 512 : 256;
   int64_t need2 = (npad + (int64_t)p.threads * VW - 1) / ((int64_t)p.threads * VW);
   int vpt2 = 1;
@@ -990,7 +1148,15 @@ ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms, int variant) 
   const int rt = (vpt2 <= 4) ? (4 / vpt2) : 1;
   const size_t stage = (size_t)rt * (size_t)npad * sizeof(T);
   p.smem = kApStages * stage;
-  p.tma = variant != 0 && vpt2 <= 4 && p.smem <= 200 * 1024;
+  p.tma = (variant == 1 || variant == 2) && vpt2 <= 4 && p.smem <= 200 * 1024;
+  if (variant == 3) {
+    // pipelined register kernel: one CTA per SM, at least two tiles per CTA
+    p.threads = kThreads;
+    const int rw = (p.vpt >= 16) ? 1 : (16 / p.vpt);
+    const int64_t by_rows = std::max<int64_t>(1, m / (2 * rw));
+    p.grid = (int)std::min<int64_t>((int64_t)num_sms, by_rows);
+    return p;
+  }
   if (p.tma) {
     p.vpt = vpt2;
     // one CTA per SM (the ring takes most of shared memory), at least a few tiles per CTA
@@ -1016,6 +1182,15 @@ void launch_apass(const ApassPlan& plan, const T* A, int64_t lda, int64_t m, int
       else apass_tma_dispatch<T, 1, false>(plan.threads, plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
     } else {
       apass_tma_dispatch<T, 2, false>(plan.threads, plan.vpt, grid, plan.smem, A, m, npad, v, ldv, b, part, spart, sout, counter, done, err, s);
+    }
+    return;
+  }
+  if (plan.variant == 3) {
+    if (nr == 1) {
+      if (resid) apass_pipe_dispatch<T, 1, true>(plan.vpt, grid, A, lda, m, npad, v, ldv, b, part, spart, sout, counter, done, s);
+      else apass_pipe_dispatch<T, 1, false>(plan.vpt, grid, A, lda, m, npad, v, ldv, b, part, spart, sout, counter, done, s);
+    } else {
+      apass_pipe_dispatch<T, 2, false>(plan.vpt, grid, A, lda, m, npad, v, ldv, b, part, spart, sout, counter, done, s);
     }
     return;
   }

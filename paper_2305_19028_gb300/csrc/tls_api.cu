@@ -555,7 +555,7 @@ Prec to_prec(tls_prec p) { return static_cast<Prec>((int)p); }
 
 // ---------------------------------------------------------------------------------------
 // Autotuner for the fused pass over A: each variant (register kernel; bulk-copy-staged with 256
-// or 512 threads) is timed on the context's own matrix (one warm-up and three launches, CUDA
+// or 512 threads; pipelined register kernel) is timed on the context's own matrix (one warm-up and three launches, CUDA
 // events) and the fastest is cached per (type, right-hand sides, m, n_pad) for the process.
 // ---------------------------------------------------------------------------------------
 std::map<std::tuple<int, int, int, int64_t, int64_t, int>, int> g_tune;
@@ -576,7 +576,7 @@ tls::ApassPlan tune_apass(tls_ctx* ctx, const T* A, int nr, bool resid, const T*
   float best_ms = 1e30f;
   for (int var = 0; var < tls::kApassVariants; ++var) {
     tls::ApassPlan pl = tls::plan_apass<T>(ctx->m, ctx->npad, nr, ctx->num_sms, var);
-    if (var != 0 && !pl.tma) continue;
+    if ((var == 1 || var == 2) && !pl.tma) continue;   // staging does not fit: not a candidate
     auto go = [&]() {
       tls::launch_apass<T>(pl, A, ctx->npad, ctx->m, ctx->npad, nr, resid, v, ctx->npad, b, part,
                            ctx->spart, sout, counter, nullptr, ctx->derr, ctx->stream);
@@ -1314,6 +1314,25 @@ tls_status tls_export_factor(tls_ctx* ctx, double* R_host, double* d_host, doubl
     TLS_CK(cudaMemcpyAsync(d_host, ctx->d, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     TLS_CK(cudaStreamSynchronize(st));
   }
+  return TLS_OK;
+}
+
+tls_status tls_set_pass_variant(tls_ctx* ctx, int variant_fp64, int variant_u) {
+  if (!ctx || !ctx->factored || ctx->sparse) return TLS_ERR_STATE;
+  if (variant_fp64 < 0 || variant_fp64 >= tls::kApassVariants || variant_u < 0 ||
+      variant_u >= tls::kApassVariants)
+    return TLS_ERR_ARG;
+  const tls::ApassPlan p64 = tls::plan_apass<double>(ctx->m, ctx->npad, 1, ctx->num_sms, variant_fp64);
+  const tls::ApassPlan pu = (ctx->u == Prec::FP64)
+                                ? tls::plan_apass<double>(ctx->m, ctx->npad, 2, ctx->num_sms, variant_u)
+                                : tls::plan_apass<float>(ctx->m, ctx->npad, 2, ctx->num_sms, variant_u);
+  if (((variant_fp64 == 1 || variant_fp64 == 2) && !p64.tma) ||
+      ((variant_u == 1 || variant_u == 2) && !pu.tma))
+    return TLS_ERR_ARG;   // the staged kernel does not fit this n
+  ctx->plan64 = p64;
+  ctx->P64 = p64.grid;
+  ctx->planU = pu;
+  ctx->PU = pu.grid;
   return TLS_OK;
 }
 

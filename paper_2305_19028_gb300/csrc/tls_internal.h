@@ -119,9 +119,10 @@ struct ApassPlan {
   bool tma;           // rows staged through shared memory by bulk async copies
   size_t smem;        // dynamic shared memory of the staged kernel
   int threads;        // CTA size of the staged kernel
-  int variant;        // 0: register kernel, 1: staged 256 threads, 2: staged 512 threads
+  int variant;        // 0: register kernel, 1: staged 256 threads, 2: staged 512 threads,
+                      // 3: pipelined register kernel
 };
-constexpr int kApassVariants = 3;
+constexpr int kApassVariants = 4;
 template <typename T>
 ApassPlan plan_apass(int64_t m, int64_t npad, int nr, int num_sms, int variant);
 

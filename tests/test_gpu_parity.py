@@ -293,3 +293,32 @@ def test_condition_estimate_generator_problem():
     assert est["sigma1"] == pytest.approx(1.0, rel=5e-3)
     assert est["sigma_n"] == pytest.approx(1e-3, rel=5e-3)
     assert est["norm_F"] == pytest.approx(np.linalg.norm(p.D), rel=1e-12)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("m,n", [(3001, 700), (4099, 2048)])
+def test_pass_variants_match_oracle(variant, m, n):
+    # every kernel the autotuner can pick for the passes over A (register, bulk-copy staged with
+    # 256 / 512 threads, pipelined register) against the oracle: the FP64 residual block and a
+    # paired PCGTLS solve; ragged row counts
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=9)
+    rng = np.random.default_rng(4)
+    x = p.x_true + 1e-3 * rng.standard_normal(n)
+    f0, f1 = rng.standard_normal(n), rng.standard_normal(n)
+    sigma2 = 0.3 * p.D[-1] ** 2
+    with Ctx(p.A, p.b, u_f="fp16", u="fp32") as ctx:
+        if tls.load().tls_set_pass_variant(ctx, variant, variant) != 0:
+            pytest.skip("the staged kernel does not fit this n")
+        f, sc = tls.tls_residual(ctx, x)
+        RH, d, _ = tls.tls_export_factor(ctx)
+        w0, w1, it, bad = tls.tls_pcgtls(ctx, sigma2, f0, f1, steps=4)
+    r, s2, fo, go, psio = O.residual_block(p.A, p.b, x)
+    assert abs(sc["sigma2"] - s2) <= 1e-10 * s2
+    fscale = m * U64 * (np.abs(p.A).T @ (np.abs(p.A) @ np.abs(x) + np.abs(p.b))).max()
+    assert np.max(np.abs(f - fo)) <= 8 * fscale
+    R = RH * d[None, :]
+    r0, _, _ = O.pcgtls(p.A, R, sigma2, f0, 3)
+    r1, _, _ = O.pcgtls(p.A, R, sigma2, f1, 3)
+    tol = 50 * np.linalg.cond(RH) * n * U32
+    assert it == [4, 4] and bad == [0, 0]
+    assert _rel(w0, r0) <= tol and _rel(w1, r1) <= tol
