@@ -260,9 +260,10 @@ __device__ __forceinline__ double round_prec(double v, int prec) {
 }
 
 // Diagonal block K = [kb, kb+64) of the blocked Cholesky H = R^T R (upper):
-//  1. factor the block (256 threads, one barrier per pivot; each finished row of R_KK, rounded
-//     to the factor precision, goes straight to global memory, so the shared copy keeps the
-//     unscaled row and the update of step k reads it as S[k][i] S[k][j] / S[k][k]);
+//  1. factor the block (256 threads, the upper triangle held in registers, one barrier per
+//     pivot; each finished row of R_KK, rounded to the factor precision, goes straight to
+//     global memory, while the update of step k uses the unrounded row as
+//     S[k][i] S[k][j] / S[k][k]);
 //  2. invert the rounded R_KK by doubling from 8 x 8 blocks,
 //     [[X11, -X11 R12 X22], [0, X22]] at block sizes 8, 16, 32, into W.
 // W_KK turns the panel solve R_KJ = R_KK^{-T} H_KJ into a product, and it is also the diagonal
@@ -274,47 +275,68 @@ __global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t
   extern __shared__ __align__(16) unsigned char dsm[];
   T (*S)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm);
   T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int r = e / NB, c = e % NB;
-    S[r][c] = M[(kb + r) * npad + kb + c];
+  const int tid = threadIdx.x;
+  // the 2080 entries of the block's upper triangle are dealt round-robin to the 256 threads
+  // and stay in registers through the factorisation (entry e = tid + 256 p, row-major order)
+  constexpr int NE = NB * (NB + 1) / 2;
+  constexpr int PE = (NE + 255) / 256;
+  T v[PE];
+  int ei[PE], ej[PE];
+#pragma unroll
+  for (int p = 0; p < PE; ++p) {
+    const int e = tid + 256 * p;
+    ei[p] = NB;   // never updated or published
+    ej[p] = 0;
+    v[p] = T(0);
+    if (e < NE) {
+      int i = 0, off = 0;
+      while (off + (NB - i) <= e) { off += NB - i; ++i; }
+      ei[p] = i;
+      ej[p] = i + (e - off);
+      v[p] = M[(kb + i) * npad + kb + ej[p]];
+    }
   }
-  __syncthreads();
+  // one barrier per pivot: row k (updated, unscaled) is published into rowk[k & 1] by its owners;
+  // the next row goes to the other buffer, whose readers all passed this barrier
+  __shared__ T rowk[2][NB];
   bool broke = false;
   for (int k = 0; k < NB; ++k) {
-    T piv = S[k][k];
+    T* rk = rowk[k & 1];
+#pragma unroll
+    for (int p = 0; p < PE; ++p)
+      if (ei[p] == k) rk[ej[p]] = v[p];
+    __syncthreads();
+    T piv = rk[k];
     if (!(piv > T(0))) {                    // non-positive or NaN pivot: breakdown
       if (tid == 0) atomicCAS(info, 0, (int)(kb + k + 1));
       piv = T(1);
       broke = true;
     }
-    const T rkk = sqrt(piv);
-    const T inv = T(1) / rkk;
+    T rkk, inv;
+    if constexpr (sizeof(T) == 4) {
+      inv = rsqrtf(piv);                    // 1/sqrt(pivot) in one instruction; R_KK is
+      rkk = piv * inv;                      // rounded to u_f or carries an FP32 error anyway
+    } else {
+      rkk = sqrt(piv);
+      inv = T(1) / rkk;
+    }
     const T inv2 = inv * inv;
-    if (tid < NB) {
-      T v = T(0);
-      if (tid == k) v = rkk;
-      else if (tid > k) v = S[k][tid] * inv;
-      M[(kb + k) * npad + kb + tid] = round_prec(v, prec);
+    if (tid < NB && tid >= k) {
+      // row k of R_KK, rounded to the factor precision: to global memory and to S for the
+      // inverse below
+      const T val = round_prec((tid == k) ? rkk : rk[tid] * inv, prec);
+      M[(kb + k) * npad + kb + tid] = val;
+      S[k][tid] = val;
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = k + 1 + ty + 16 * a;
-      if (i >= NB) break;
-      const T ski = S[k][i] * inv2;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int j = k + 1 + tx + 16 * b;
-        if (j < NB && j >= i) S[i][j] = fma(-ski, S[k][j], S[i][j]);
-      }
-    }
-    __syncthreads();
+    for (int p = 0; p < PE; ++p)
+      if (ei[p] > k) v[p] = fma(-(rk[ei[p]] * inv2), rk[ej[p]], v[p]);
   }
+  __syncthreads();
   if (broke) return;   // uniform: every thread saw the same pivots
-  // reload the rounded R_KK (this block's own global writes are visible after the barrier)
   for (int e = tid; e < NB * NB; e += 256) {
     const int r = e / NB, c = e % NB;
-    S[r][c] = (c >= r) ? M[(kb + r) * npad + kb + c] : T(0);
+    if (c < r) S[r][c] = T(0);
     X[r][c] = T(0);
   }
   __syncthreads();
