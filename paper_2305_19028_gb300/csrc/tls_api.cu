@@ -44,6 +44,10 @@ struct tls_ctx {
   bool own_stream = false;
   std::string err;
   std::vector<DevBuf> bufs;
+  // persistent work buffers, reused by every factor / solve while they are large enough (no
+  // cudaMalloc / cudaFree, which synchronise the device, between repeated calls)
+  DevBuf slots[16];
+  RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
 
   // problem data (device)
   bool sparse = false;     // A held as CSR + CSC instead of dense
@@ -102,6 +106,8 @@ struct tls_ctx {
   RqiScalars* h_rs = nullptr;
   PcgScalars* h_sc = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t evf0 = nullptr, evf1 = nullptr;   // the last factor's start and end
+  bool factor_time_pending = false;
   // per-kernel-class CUDA-event timing (tls_profile_enable)
   bool prof_on = false;
   std::vector<cudaEvent_t> pev;
@@ -176,6 +182,23 @@ void dev_free(tls_ctx* c, void* p) {
   }
 }
 
+enum Slot : int {
+  kSlotCpart, kSlotInfo, kSlotAsT, kSlotH, kSlotM, kSlotWc, kSlotR, kSlotW, kSlotWT, kSlotWork,
+  kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotCount
+};
+static_assert(kSlotCount <= 16, "slots");
+
+// A persistent buffer of at least `bytes` for slot `id` (contents not kept when it grows).
+void* slot(tls_ctx* c, int id, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  DevBuf& sl = c->slots[id];
+  if (sl.ptr && sl.bytes >= bytes) return sl.ptr;
+  if (sl.ptr) dev_free(c, sl.ptr);
+  sl.ptr = dev_alloc(c, bytes);
+  sl.bytes = sl.ptr ? bytes : 0;
+  return sl.ptr;
+}
+
 template <typename T>
 T* alloc_t(tls_ctx* c, int64_t count) {
   return static_cast<T*>(dev_alloc(c, sizeof(T) * (size_t)count));
@@ -202,8 +225,11 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   }
   TLS_CK(cudaEventCreate(&ctx->ev0));
   TLS_CK(cudaEventCreate(&ctx->ev1));
+  TLS_CK(cudaEventCreate(&ctx->evf0));
+  TLS_CK(cudaEventCreate(&ctx->evf1));
   TLS_CK(cudaMallocHost(&ctx->h_rs, sizeof(RqiScalars)));
   TLS_CK(cudaMallocHost(&ctx->h_sc, sizeof(PcgScalars)));
+  TLS_CK(cudaMallocHost(&ctx->h_norm, 2 * sizeof(RqiScalars)));
   const int64_t npad = ctx->npad;
   ctx->b = alloc_t<double>(ctx, m);
   ctx->x = alloc_t<double>(ctx, npad);
@@ -251,9 +277,12 @@ void destroy_ctx(tls_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   while (!ctx->bufs.empty()) dev_free(ctx, ctx->bufs.back().ptr);
   if (ctx->h_rs) cudaFreeHost(ctx->h_rs);
+  if (ctx->h_norm) cudaFreeHost(ctx->h_norm);
   if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->evf0) cudaEventDestroy(ctx->evf0);
+  if (ctx->evf1) cudaEventDestroy(ctx->evf1);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -519,6 +548,11 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   prof_collect(ctx);
+  if (ctx->factor_time_pending) {
+    float fms = 0.f;
+    if (cudaEventElapsedTime(&fms, ctx->evf0, ctx->evf1) == cudaSuccess) ctx->t_factor_ms = fms;
+    ctx->factor_time_pending = false;
+  }
   if (herr != 0) {
     TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), st));
     set_err(ctx, "a bounded device wait expired (code " + std::to_string(herr) + ")");
@@ -623,21 +657,18 @@ void tune_passes(tls_ctx* ctx) {
 tls_status ensure_solve_buffers(tls_ctx* ctx) {
   const int64_t npad = ctx->npad;
   const size_t us = u_size(ctx->u);
-  if (ctx->vbuf) dev_free(ctx, ctx->vbuf);
-  if (ctx->part) dev_free(ctx, ctx->part);
-  ctx->vbuf = dev_alloc(ctx, us * 12 * (size_t)npad);
+  ctx->vbuf = slot(ctx, kSlotVbuf, us * 12 * (size_t)npad);
   if (ctx->u == Prec::FP64) ctx->planU = tls::plan_apass<double>(ctx->m, npad, 2, ctx->num_sms, 1);
   else ctx->planU = tls::plan_apass<float>(ctx->m, npad, 2, ctx->num_sms, 1);
   ctx->PU = ctx->planU.grid;
-  ctx->part = dev_alloc(ctx, us * (size_t)2 * ctx->num_sms * 2 * (size_t)npad);
+  ctx->part = slot(ctx, kSlotPart, us * (size_t)2 * ctx->num_sms * 2 * (size_t)npad);
   if (!ctx->vbuf || !ctx->part) {
     set_err(ctx, "device allocation failed (solve buffers)");
     return TLS_ERR_OOM;
   }
   TLS_CK(cudaMemsetAsync(ctx->vbuf, 0, us * 12 * (size_t)npad, ctx->stream));
   if (ctx->sparse) {
-    if (ctx->tbuf) dev_free(ctx, ctx->tbuf);
-    ctx->tbuf = dev_alloc(ctx, us * 2 * (size_t)ctx->m);
+    ctx->tbuf = slot(ctx, kSlotTbuf, us * 2 * (size_t)ctx->m);
     if (!ctx->tbuf) {
       set_err(ctx, "device allocation failed (sparse solve buffers)");
       return TLS_ERR_OOM;
@@ -652,12 +683,7 @@ tls_status ensure_solve_buffers(tls_ctx* ctx) {
 tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   cudaStream_t st = ctx->stream;
   const int64_t m = ctx->m, n = ctx->n, npad = ctx->npad, mpad = ctx->mpad;
-  TLS_CK(cudaEventRecord(ctx->ev0, st));
-  // free previous factor buffers
-  for (void** p : {&ctx->H, &ctx->R, &ctx->W, &ctx->WT}) {
-    dev_free(ctx, *p);
-    *p = nullptr;
-  }
+  TLS_CK(cudaEventRecord(ctx->evf0, st));
   ctx->factored = false;
   if (!ctx->sparse && ctx->u == Prec::FP32 && ctx->A32 == nullptr) {
     ctx->A32 = alloc_t<float>(ctx, m * npad);
@@ -667,8 +693,9 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     }
   }
   // column scaling D (Sec. 3.1); the FP32 copy of A for u = FP32 is written in the same pass
-  double* cpart = alloc_t<double>(ctx, 64 * npad);
-  if (!cpart) {
+  double* cpart = static_cast<double*>(slot(ctx, kSlotCpart, sizeof(double) * 64 * npad));
+  RqiScalars* dnorm = static_cast<RqiScalars*>(slot(ctx, kSlotNorm, 2 * sizeof(RqiScalars)));
+  if (!cpart || !dnorm) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
@@ -682,26 +709,26 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
                           npad, ctx->d, ctx->dinv32, ctx->dinv, cpart, st);
   }
   TLS_CK_LAUNCH("column norms");
-  {
-    std::vector<double> hd(npad);
-    TLS_CK(cudaMemcpyAsync(hd.data(), ctx->d, sizeof(double) * npad, cudaMemcpyDeviceToHost, st));
-    TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * npad, st));
-    tls::launch_xx(ctx->b, ctx->rs, m, st);   // ||b||^2 into rs->xx (scratch use)
-    TLS_CK(cudaMemcpyAsync(ctx->h_rs, ctx->rs, sizeof(RqiScalars), cudaMemcpyDeviceToHost, st));
-    TLS_CK(cudaStreamSynchronize(st));
-    double s = 0.0;
-    for (int64_t j = 0; j < n; ++j) s += hd[j] * hd[j];
-    ctx->norm2_A = s;
-    ctx->norm2_b = ctx->h_rs->xx;
-  }
-  dev_free(ctx, cpart);
+  // ||A||_F^2 = sum of d_j^2 and ||b||^2 on the device; read back with the factor's first
+  // synchronisation (no extra host round trip)
+  TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * npad, st));
+  tls::launch_xx(ctx->d, dnorm, n, st);
+  tls::launch_xx(ctx->b, dnorm + 1, m, st);
+  TLS_CK(cudaMemcpyAsync(ctx->h_norm, dnorm, 2 * sizeof(RqiScalars), cudaMemcpyDeviceToHost, st));
+  bool norms_read = false;
+  auto read_norms = [&]() {
+    if (norms_read) return;
+    norms_read = true;
+    ctx->norm2_A = ctx->h_norm[0].xx;
+    ctx->norm2_b = ctx->h_norm[1].xx;
+  };
 
   // the ladder of factor precisions (Sec. 3.1 constraints, escalation on breakdown)
   std::vector<tls_prec> ladder;
   ladder.push_back(uf_req);
   if (uf_req == TLS_FP16 || uf_req == TLS_BF16) ladder.push_back(TLS_FP32);
   if (uf_req != TLS_FP64) ladder.push_back(TLS_FP64);
-  int* dinfo = alloc_t<int>(ctx, 1);
+  int* dinfo = static_cast<int*>(slot(ctx, kSlotInfo, sizeof(int)));
   if (!dinfo) return TLS_ERR_OOM;
   ctx->shifts = 0;
   ctx->shift = 0.0;
@@ -713,10 +740,11 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     const size_t ce = chol64 ? 8 : 4;
     const size_t ae = (pf == Prec::FP64) ? 8 : (pf == Prec::FP32 ? 4 : 2);
     // dense: the scaled, rounded, transposed A_s; sparse: its values in CSR and CSC order
-    void* AsT = ctx->sparse ? dev_alloc(ctx, 2 * ce * (size_t)std::max<int64_t>(ctx->nnz, 1))
-                            : dev_alloc(ctx, ae * (size_t)npad * (size_t)mpad);
-    ctx->H = dev_alloc(ctx, ce * (size_t)npad * (size_t)npad);
-    void* M = dev_alloc(ctx, ce * (size_t)npad * (size_t)npad);
+    void* AsT = ctx->sparse
+                    ? slot(ctx, kSlotAsT, 2 * ce * (size_t)std::max<int64_t>(ctx->nnz, 1))
+                    : slot(ctx, kSlotAsT, ae * (size_t)npad * (size_t)mpad);
+    ctx->H = slot(ctx, kSlotH, ce * (size_t)npad * (size_t)npad);
+    void* M = slot(ctx, kSlotM, ce * (size_t)npad * (size_t)npad);
     if (!AsT || !ctx->H || !M) {
       set_err(ctx, "device allocation failed (factor workspace)");
       return TLS_ERR_OOM;
@@ -762,8 +790,7 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     }
     }
     TLS_CK_LAUNCH("gram");
-    dev_free(ctx, AsT);
-    void* Wc = dev_alloc(ctx, ce * (size_t)npad * (size_t)npad);   // diagonal-block inverses
+    void* Wc = slot(ctx, kSlotWc, ce * (size_t)npad * (size_t)npad);   // diagonal-block inverses
     if (!Wc) {
       set_err(ctx, "device allocation failed (factor workspace)");
       return TLS_ERR_OOM;
@@ -794,6 +821,7 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
       int hinfo = 0;
       TLS_CK(cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
       TLS_CK(cudaStreamSynchronize(st));
+      read_norms();
       if (hinfo == 0) {
         ok = true;
         ctx->shift = shift;
@@ -802,21 +830,15 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
       ctx->shifts += 1;
       ctx->fail_pivot = hinfo - 1;
     }
-    if (!ok) {
-      dev_free(ctx, Wc);
-      dev_free(ctx, M);
-      dev_free(ctx, ctx->H);
-      ctx->H = nullptr;
-      continue;
-    }
+    if (!ok) continue;
     // R_H rounded to u_f (the computed factor R-hat), then carried in the u type
     if (chol64) tls::launch_round_to<double>(static_cast<double*>(M), npad, pf, st);
     else tls::launch_round_to<float>(static_cast<float*>(M), npad, pf, st);
     const size_t us = u_size(ctx->u);
-    ctx->R = dev_alloc(ctx, us * (size_t)npad * (size_t)npad);
-    ctx->W = dev_alloc(ctx, us * (size_t)npad * (size_t)npad);
-    ctx->WT = dev_alloc(ctx, us * (size_t)npad * (size_t)npad);
-    void* work = dev_alloc(ctx, us * (size_t)npad * (size_t)npad);
+    ctx->R = slot(ctx, kSlotR, us * (size_t)npad * (size_t)npad);
+    ctx->W = slot(ctx, kSlotW, us * (size_t)npad * (size_t)npad);
+    ctx->WT = slot(ctx, kSlotWT, us * (size_t)npad * (size_t)npad);
+    void* work = slot(ctx, kSlotWork, us * (size_t)npad * (size_t)npad);
     if (!ctx->R || !ctx->W || !ctx->WT || !work) {
       set_err(ctx, "device allocation failed (inverse factor)");
       return TLS_ERR_OOM;
@@ -847,26 +869,24 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
                                true, st);
     }
     TLS_CK_LAUNCH("triangular inverse");
-    dev_free(ctx, work);
-    dev_free(ctx, Wc);
-    dev_free(ctx, M);
     ctx->uf_used = uf;
     ctx->H_fp64 = chol64;
     break;
   }
-  dev_free(ctx, dinfo);
   if (!ok) {
     set_err(ctx, "Cholesky breakdown at every shift and precision");
     return TLS_ERR_FACTOR_BREAKDOWN;
   }
   tls_status s2 = ensure_solve_buffers(ctx);
   if (s2 != TLS_OK) return s2;
-  TLS_CK(cudaEventRecord(ctx->ev1, st));
-  TLS_CK(cudaEventSynchronize(ctx->ev1));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-  prof_collect(ctx);
-  ctx->t_factor_ms = ms;
+  // the triangular inverse may still run: the next call on the stream orders after it, and
+  // the factor's device time is read once it is known to be complete
+  TLS_CK(cudaEventRecord(ctx->evf1, st));
+  ctx->factor_time_pending = true;
+  if (ctx->prof_on) {
+    TLS_CK(cudaEventSynchronize(ctx->evf1));
+    prof_collect(ctx);
+  }
   ctx->factored = true;
   return TLS_OK;
 }
@@ -925,7 +945,7 @@ template <typename TH, typename TU>
 static tls_status condition_impl(tls_ctx* ctx, int iters, double* out) {
   cudaStream_t st = ctx->stream;
   const int64_t n = ctx->n, npad = ctx->npad;
-  void* scratch = dev_alloc(ctx, sizeof(double) * (size_t)(4 * npad + 2 + 4096));
+  void* scratch = slot(ctx, kSlotCond, sizeof(double) * (size_t)(4 * npad + 2 + 4096));
   if (!scratch) return TLS_ERR_OOM;
   TH* xh = static_cast<TH*>(scratch);
   TH* yh = xh + npad;
@@ -955,7 +975,7 @@ static tls_status condition_impl(tls_ctx* ctx, int iters, double* out) {
   std::vector<double> h(2 + (size_t)g);
   TLS_CK(cudaMemcpyAsync(h.data(), lam, sizeof(double) * (2 + g), cudaMemcpyDeviceToHost, st));
   TLS_CK(cudaStreamSynchronize(st));
-  dev_free(ctx, scratch);
+
   double frob = 0.0;
   for (int i = 0; i < g; ++i) frob += h[2 + i];
   const double s1 = std::sqrt(std::max(h[0], 0.0));
