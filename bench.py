@@ -37,6 +37,9 @@ METRIC = "TLS solves/s on GB300 at sigma rel err<=1e-10 vs FP64 oracle; mixed vs
 M_ROWS, N_COLS, D_LO, NOISE = 16384, 2048, 1e-3, 1e-4
 SIGMA_TOL, X_TOL = 1e-10, 1e-8
 SOLVE_TOL, MAX_RQI = 1e-16, 12
+# derived ALU peaks (no measured FP32 / FP64 peak in the measured-peaks file)
+FP64_PEAK = 2 * 2 * 152 * 2.07e9 / 1e12       # TFLOP/s: 2 FMA/clk/SM
+FP32_PEAK = 2 * 128 * 152 * 2.07e9 / 1e12     # TFLOP/s: 128 FMA/clk/SM
 WORKLOAD = f"dense_{M_ROWS}x{N_COLS}_uf16_u32_ur64"
 
 
@@ -188,12 +191,14 @@ def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int) -> dict:
                 "traffic": None, "peak_source": src, "avg_launch_us": avg_s * 1e6,
                 "algorithmic_bytes": unit_bytes}
     if cls == "resid_pass":
-        unit_bytes = m * n * 8 + m * 8
-        ach = unit_bytes / avg_s / 1e9
-        return {"kernel": "resid_pass (FP64 r=b-Ax, A^T r)", "bound": "hbm",
-                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_source": src, "avg_launch_us": avg_s * 1e6,
-                "algorithmic_bytes": unit_bytes}
+        # FP64 FMA-bound on this GPU: r = b - A x and A^T r are 2 FMA (4 flops) per entry of A
+        flops = 4.0 * m * n
+        ach = flops / avg_s / 1e12
+        return {"kernel": "resid_pass (FP64 r=b-Ax, A^T r)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK, "unit": "TFLOP/s", "frac": ach / FP64_PEAK, "traffic": None,
+                "peak_source": "nominal FP64 rate (2 FMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops,
+                "hbm_gbs": (m * n * 8 + m * 8) / avg_s / 1e9}
     if cls == "gram":
         flops = m * n * (n + 1)                          # SYRK: n(n+1)/2 entries x 2m flops
         ach = flops / avg_s / 1e12
@@ -202,12 +207,15 @@ def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int) -> dict:
                 "traffic": None, "peak_source": src + " (bf16 sustained; fp16 nominal rate equal)",
                 "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops}
     if cls == "chol":
+        # one launch-class entry per factor: the diagonal blocks (a chain of n pivots, one CTA
+        # per 64-block) and the panel / trailing updates, FP32 on CUDA cores
         flops = n ** 3 / 3.0
         ach = flops / avg_s / 1e12
-        return {"kernel": "chol (blocked Cholesky of H, FP32)", "bound": "tensor",
-                "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                "traffic": None, "peak_source": src, "avg_launch_us": avg_s * 1e6,
-                "algorithmic_flops": flops}
+        return {"kernel": "chol (blocked Cholesky of H, FP32 CUDA cores; latency of the "
+                          "diagonal-block chain)", "bound": "alu", "achieved": ach,
+                "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": ach / FP32_PEAK, "traffic": None,
+                "peak_source": "nominal FP32 rate (128 FMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops}
     return {}
 
 
@@ -376,6 +384,174 @@ def run_ours(args, ws, rank, local):
 
 
 # ------------------------------------------------------------------------------------------
+# sparse workload (CSR 200000 x 4000, u_f BF16)
+# ------------------------------------------------------------------------------------------
+CSR_M, CSR_N, CSR_NNZ, CSR_NOISE = 200000, 4000, 12, 1e-3
+
+
+def _csr_oracle(p):
+    """FP64 oracle on the CSR problem: R from the Cholesky factor of A^T A (the oracle's
+    alternative factor; a dense QR of a 200000 x 4000 matrix is far too slow for a bench) and
+    the normal-equation LS start."""
+    import scipy.linalg as sla
+    import scipy.sparse as sps
+    import oracle.rqi_pcgtls as O
+    A = sps.csr_matrix((p.val, p.col_idx, p.row_ptr), shape=(p.m, p.n))
+    R = O.r_factor_cholesky(A)
+    x0 = sla.solve_triangular(R, sla.solve_triangular(R, A.T @ p.b, trans="T"))
+    return O.rqi_pcgtls(A, p.b, R=R, x0=x0, tol=0.0, max_rqi=MAX_RQI)
+
+
+def run_sparse(args, ws, rank, local):
+    import torch
+    from paper_2305_19028_gb300 import synth, tls
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    tls.load()
+    p = synth.csr_problem(CSR_M, CSR_N, nnz_per_row=CSR_NNZ, noise=CSR_NOISE, seed=rank)
+    nnz = int(p.row_ptr[-1])
+    stream = torch.cuda.current_stream()
+    ctx = tls.tls_create_csr(p.m, p.n, p.row_ptr, p.col_idx, p.val, p.b, stream=stream.cuda_stream)
+    opt = tls.tls_default_options(u="fp32")
+    ref, cpu = None, None
+    if not args.no_cpu:
+        t0 = time.perf_counter()
+        xo, so, _ = _csr_oracle(p)
+        t_or = time.perf_counter() - t0
+        ref = (xo, so)
+        if rank == 0:
+            cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": f"1 full FP64 solve of the {CSR_M}x{CSR_N} CSR problem "
+                             f"({t_or:.2f} s: sparse A^T A, dense Cholesky R, scipy products)"}
+
+    def accurate(x, s):
+        if ref is None:
+            return True
+        xo, so = ref
+        return abs(s - so) / so <= SIGMA_TOL and np.linalg.norm(x - xo) <= X_TOL * np.linalg.norm(xo)
+
+    def step():
+        tls.tls_factor(ctx, "bf16", opt)
+        return tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    l0 = tls.tls_kernel_launches()
+    ok = 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            x, s, info = step()
+            ok += int(accurate(x, s))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = tls.tls_kernel_launches() - l0
+    ms = _barrier_max(ev0.elapsed_time(ev1), ws)
+    clocks = clk.summary()
+    tls.tls_profile_enable(ctx, True)
+    for _ in range(max(1, min(args.steps, 3))):
+        step()
+    torch.cuda.synchronize()
+    prof = tls.tls_profile_get(ctx)
+    tls.tls_profile_enable(ctx, False)
+    plain = None
+    if not args.no_plain:
+        opt64 = tls.tls_default_options(u="fp64")
+        tls.tls_factor(ctx, "fp64", opt64)
+        tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        okp, nps = 0, 2
+        q0.record(stream)
+        for _ in range(nps):
+            tls.tls_factor(ctx, "fp64", opt64)
+            xp, sp_, _ = tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
+            okp += int(accurate(xp, sp_))
+        q1.record(stream)
+        torch.cuda.synchronize()
+        pms = _barrier_max(q0.elapsed_time(q1), ws)
+        plain = {"value": ws * okp / (pms * 1e-3), "unit": "solves/s", "ms_per_step": pms / nps,
+                 "steps": nps, "accurate": okp}
+    e2e = None
+    if not args.no_e2e:
+        pins = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+                for a in (p.row_ptr.astype(np.int64), p.col_idx.astype(np.int32), p.val, p.b)]
+        ne = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        okc = 0
+        e0.record(stream)
+        for _ in range(ne):
+            c2 = tls.tls_create_csr(p.m, p.n, *pins, stream=stream.cuda_stream)
+            tls.tls_factor(c2, "bf16", opt)
+            x2, s2, _ = tls.tls_solve(c2, tol=SOLVE_TOL, max_rqi=MAX_RQI)
+            tls.tls_destroy(c2)
+            okc += int(accurate(x2, s2))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = _barrier_max(e0.elapsed_time(e1), ws)
+        e2e = {"value": ws * okc / (ems * 1e-3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(sum(a.nbytes for a in pins)),
+               "d2h_bytes_per_step": int(8 * CSR_N + 8), "steps": ne, "ms_per_step": ems / ne}
+    tls.tls_destroy(ctx)
+    if rank != 0:
+        return
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    total = {k: v[1] for k, v in prof.items()}
+    share = {k: round(v / max(1e-9, sum(total.values())), 4) for k, v in total.items()}
+
+    def sparse_roof(cls):
+        cnt, tms = prof.get(cls, (0, 0.0))
+        if not cnt:
+            return {}
+        avg = tms / cnt * 1e-3
+        # the paired PCGTLS pass reads the FP32 values and int32 indices once in CSR order
+        # (t = A q) and once in CSC order (A^T t), plus row / column offsets and t (2 RHS)
+        byts = 2 * nnz * 8 + (CSR_M + CSR_N) * 4 + 2 * 2 * CSR_M * 4
+        if cls == "resid_pass":
+            byts = 2 * nnz * 12 + (CSR_M + CSR_N) * 4 + 2 * CSR_M * 8
+        ach = byts / avg / 1e9
+        return {"kernel": f"{cls} (CSR/CSC passes)", "bound": "hbm", "achieved": ach,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "peak_source": "measured" if peaks else "fallback",
+                "avg_launch_us": avg * 1e6, "algorithmic_bytes": byts}
+
+    dom = max(total, key=total.get)
+    line = {
+        "metric": METRIC, "value": ws * ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32+f64", "data": "synthetic",
+        "config": {"workload": f"csr_{CSR_M}x{CSR_N}_nnz{nnz}_ufbf16_u32_ur64", "m": CSR_M,
+                   "n": CSR_N, "nnz": nnz, "noise": CSR_NOISE, "u_f": "bf16", "u": "fp32",
+                   "u_r": "fp64", "solve_tol": SOLVE_TOL, "max_rqi": MAX_RQI,
+                   "l2": "values, indices and the dense factor (2 x 64 MB) exceed L2",
+                   "step": "tls_factor + tls_solve on resident CSR A"},
+        "accurate_steps": ok, "rqi_steps": info["rqi_steps"], "cg_iters": info["cg_iters"],
+        "roofline": sparse_roof("pcg_pass2") if dom in ("pcg_pass2", "pcg_pass1") else
+                    {"kernel": dom, "note": "dominant class is not a pass over A",
+                     **{k: v for k, v in sparse_roof("pcg_pass2").items() if k != "kernel"}},
+        "inner_loop_roofline": sparse_roof("pcg_pass2"), "resid_roofline": sparse_roof("resid_pass"),
+        "kernel_share": share, "kernel_ms": {k: round(v, 4) for k, v in total.items()},
+        "kernel_launches": {k: v[0] for k, v in prof.items()},
+        "kernel_profile": "profiled steps after the timed region", "gpu_launches": int(launches),
+        "cpu_baseline": cpu, "e2e": e2e, "plain_fp64": plain, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
 # packed batch workload
 # ------------------------------------------------------------------------------------------
 BATCH_K = 512
@@ -434,8 +610,9 @@ def _batch_roofline(prof: dict, peaks: dict, cls: str) -> dict:
         flops = 4.0 * elems
         ach = flops / (ms * 1e-3) / 1e12
         return {"kernel": "resid_pass (batched FP64 r = b - A x, A^T r)", "bound": "alu",
-                "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
-                "traffic": None, "peak_source": "nominal FP64 rate (no measured FP64 peak)",
+                "achieved": ach, "peak": FP64_PEAK, "unit": "TFLOP/s", "frac": ach / FP64_PEAK,
+                "traffic": None,
+                "peak_source": "nominal FP64 rate (2 FMA/clk/SM x 152 SMs x 2.07 GHz)",
                 "avg_launch_us": ms / cnt * 1e3, "algorithmic_flops_per_launch": flops / cnt,
                 "hbm_gbs": 8.0 * elems / (ms * 1e-3) / 1e9}
     return {}
@@ -604,7 +781,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--m", type=int, default=None, help="rows (profiling a smaller case)")
     ap.add_argument("--n", type=int, default=None, help="columns (profiling a smaller case)")
-    ap.add_argument("--workload", choices=["dense", "batch"], default="dense")
+    ap.add_argument("--workload", choices=["dense", "batch", "sparse"], default="dense")
     ap.add_argument("--batch", type=int, default=BATCH_K, help="problems in the packed batch")
     ap.add_argument("--selector", action="store_true",
                     help="batch: let the trained selector network pick u_f per problem")
@@ -615,6 +792,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batch":
         run_batch(args, ws, rank, local)
+    elif args.workload == "sparse":
+        run_sparse(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

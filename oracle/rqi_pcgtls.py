@@ -64,9 +64,17 @@ def r_factor_qr(A: np.ndarray) -> np.ndarray:
     return np.triu(R * s[:, None])
 
 
-def r_factor_cholesky(A: np.ndarray) -> np.ndarray:
-    """Upper-triangular Cholesky factor of A^T A (the alternative preconditioner, Sec. 3)."""
-    return np.linalg.cholesky(A.T @ A).T
+def _is_sparse(A) -> bool:
+    return hasattr(A, "tocsr")
+
+
+def r_factor_cholesky(A) -> np.ndarray:
+    """Upper-triangular Cholesky factor of A^T A (the alternative preconditioner, Sec. 3).
+    A may be dense or a scipy sparse matrix (A^T A is then formed sparse and factored dense)."""
+    G = A.T @ A
+    if _is_sparse(G):
+        G = G.toarray()
+    return np.linalg.cholesky(G).T
 
 
 def scaled_gram(A: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
@@ -177,8 +185,15 @@ def rqi_pcgtls(A: np.ndarray, b: np.ndarray, R: np.ndarray | None = None,
                mode: str = "A", cg_tol: float | None = None, cg_max: int | None = None,
                psi_rule_ge: bool = False):
     """RQI-PCGTLS in FP64 (Alg. 2 with the solves of Alg. 3, i.e. Alg. 4 at u = u_p = u_q =
-    double). Returns (x, sigma, info)."""
-    A = np.asarray(A, dtype=np.float64)
+    double). Returns (x, sigma, info). A may be a scipy sparse matrix: the method only applies
+    A and A^T to vectors (then R and x0 must be given)."""
+    sparse = _is_sparse(A)
+    if sparse:
+        A = A.tocsr().astype(np.float64)
+        if R is None or x0 is None:
+            raise ValueError("a sparse A needs R and x0")
+    else:
+        A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     if R is None:
         R = r_factor_qr(A)
@@ -189,7 +204,7 @@ def rqi_pcgtls(A: np.ndarray, b: np.ndarray, R: np.ndarray | None = None,
     u0 = sla.solve_triangular(R, sla.solve_triangular(R, x, trans="T", lower=False),
                               lower=False)                       # A^T A u_0 = x_0 via R^T R
     x = x + sigma2_0 * u0
-    scale = float(np.sum(A * A) + b @ b)
+    scale = float((A.multiply(A).sum() if sparse else np.sum(A * A)) + b @ b)
     best = None
     psis, sig2s = [], []
     prev_psi = math.inf

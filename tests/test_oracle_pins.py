@@ -355,3 +355,17 @@ def test_mlp_oracle_special_cases():
     P = rng.normal(0.0, 0.5, size=M.N_PARAMS)
     Ph = P.astype(np.float32).astype(np.float16).astype(np.float64)
     assert np.array_equal(M.forward(P, X, fp16=True)[0], M.forward(Ph, X)[0])
+
+
+def test_oracle_on_sparse_input_matches_dense_input():
+    # the oracle only applies A and A^T: a scipy CSR matrix with the Cholesky R and the
+    # normal-equation start gives the dense QR run's result (same exact-arithmetic method)
+    sp = pytest.importorskip("scipy.sparse")
+    p = synth.csr_problem(3000, 200, nnz_per_row=12, noise=1e-3, seed=0)
+    A = sp.csr_matrix((p.val, p.col_idx, p.row_ptr), shape=(p.m, p.n))
+    R = O.r_factor_cholesky(A)
+    x0 = sla.solve_triangular(R, sla.solve_triangular(R, A.T @ p.b, trans="T"))
+    x1, s1, _ = O.rqi_pcgtls(A, p.b, R=R, x0=x0, tol=0.0, max_rqi=12)
+    x2, s2, _ = O.rqi_pcgtls(A.toarray(), p.b, tol=0.0, max_rqi=12)
+    assert abs(s1 - s2) <= 1e-12 * s2
+    assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x2)
