@@ -484,7 +484,7 @@ __device__ void inv_upper64(const C* S, C* X, C* Tm) {
 // A non-positive (or NaN) pivot stops the problem: info = pivot + 1.
 // =========================================================================================
 template <typename C>
-__global__ void __launch_bounds__(kCT) chol_kernel(BArrays a, const int* list, const double* shift,
+__global__ void __launch_bounds__(kCT, 2) chol_kernel(BArrays a, const int* list, const double* shift,
                                                    int* info) {
   const int pi = list[blockIdx.x];
   const BProb P = a.probs[pi];
@@ -507,50 +507,112 @@ __global__ void __launch_bounds__(kCT) chol_kernel(BArrays a, const int* list, c
   }
   if (tid == 0) s_broke = 0;
   __syncthreads();
-  for (int kb = 0; kb < npb; kb += kNB) {
-    for (int e = tid; e < kNB * kNB; e += kCT) {
-      const int r = e / kNB, c = e % kNB;
-      S[r * kLd + c] = M[(int64_t)(kb + r) * npb + kb + c];
+  // diagonal block: its 2080 upper entries dealt round-robin to the threads and kept in
+  // registers; four pivots per step (publish rows k .. k+3, 64 threads form R11 and
+  // Y = R11^{-T} S[k:k+4][:], rank-4 update of the rest), two barriers per step
+  constexpr int NE = kNB * (kNB + 1) / 2;
+  constexpr int PE = (NE + kCT - 1) / kCT;
+  constexpr int PB = 4;
+  __shared__ C rowk[PB][kNB];
+  __shared__ C Yk[PB][kNB];
+  int ei[PE], ej[PE];
+#pragma unroll
+  for (int p = 0; p < PE; ++p) {
+    const int e = tid + kCT * p;
+    ei[p] = kNB;
+    ej[p] = 0;
+    if (e < NE) {
+      int i = 0, off = 0;
+      while (off + (kNB - i) <= e) { off += kNB - i; ++i; }
+      ei[p] = i;
+      ej[p] = i + (e - off);
     }
-    __syncthreads();
-    for (int k = 0; k < kNB; ++k) {
-      C piv = S[k * kLd + k];
-      const bool bad = !(piv > C(0));
-      if (bad) piv = C(1);
-      const C rkk = sqrt(piv);
-      const C inv = C(1) / rkk;
-      const C inv2 = inv * inv;
-      if (tid < kNB) {
-        C v = C(0);
-        if (tid == k) v = rkk;
-        else if (tid > k) v = S[k * kLd + tid] * inv;
-        M[(int64_t)(kb + k) * npb + kb + tid] = round_uf(v, prec);
-      }
-      if (bad && tid == 0 && s_broke == 0) s_broke = kb + k + 1;
-      // rows i = k+1+ty+16u, columns j = k+1+tx+32v, j >= i
-      const int ty = tid >> 5, tx = tid & 31;
+  }
+  for (int kb = 0; kb < npb; kb += kNB) {
+    C v[PE];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = k + 1 + ty + 16 * u;
-        if (i < kNB) {
-          const C ski = S[k * kLd + i] * inv2;
+    for (int p = 0; p < PE; ++p)
+      v[p] = (ei[p] < kNB) ? M[(int64_t)(kb + ei[p]) * npb + kb + ej[p]] : C(0);
+    for (int k = 0; k < kNB; k += PB) {
 #pragma unroll
-          for (int v2 = 0; v2 < 2; ++v2) {
-            const int j = k + 1 + tx + 32 * v2;
-            if (j < kNB && j >= i) S[i * kLd + j] = fma(-ski, S[k * kLd + j], S[i * kLd + j]);
+      for (int p = 0; p < PE; ++p)
+        if (ei[p] >= k && ei[p] < k + PB) rowk[ei[p] - k][ej[p]] = v[p];
+      __syncthreads();
+      if (tid < kNB && tid >= k) {
+        C r[PB][PB], rinv[PB];
+        int bad = 0;
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+          C dsum = rowk[t][k + t];
+#pragma unroll
+          for (int q = 0; q < t; ++q) dsum = fma(-r[q][t], r[q][t], dsum);
+          if (!(dsum > C(0))) {                // non-positive or NaN pivot: breakdown
+            bad = bad ? bad : (k + t + 1);
+            dsum = C(1);
+          }
+          C rtt, inv;
+          if constexpr (sizeof(C) == 4) {
+            inv = rsqrtf(dsum);
+            rtt = dsum * inv;
+          } else {
+            rtt = sqrt(dsum);
+            inv = C(1) / rtt;
+          }
+          r[t][t] = rtt;
+          rinv[t] = inv;
+#pragma unroll
+          for (int u = t + 1; u < PB; ++u) {
+            C e = rowk[t][k + u];
+#pragma unroll
+            for (int q = 0; q < t; ++q) e = fma(-r[q][t], r[q][u], e);
+            r[t][u] = e * inv;
           }
         }
+        const int c = tid;
+        C y[PB];
+        if (c < k + PB) {
+#pragma unroll
+          for (int t = 0; t < PB; ++t) y[t] = (c - k >= t) ? r[t][c - k] : C(0);
+        } else {
+#pragma unroll
+          for (int t = 0; t < PB; ++t) {
+            C e = rowk[t][c];
+#pragma unroll
+            for (int q = 0; q < t; ++q) e = fma(-r[q][t], y[q], e);
+            y[t] = e * rinv[t];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+          Yk[t][c] = y[t];
+          if (c >= k + t) {
+            // rows of R_KK rounded to u_f: to global memory and to S for the inverse
+            const C val = round_uf(y[t], prec);
+            M[(int64_t)(kb + k + t) * npb + kb + c] = val;
+            S[(k + t) * kLd + c] = val;
+          }
+        }
+        if (bad && tid == k) atomicCAS(&s_broke, 0, kb + bad);
       }
       __syncthreads();
+#pragma unroll
+      for (int p = 0; p < PE; ++p)
+        if (ei[p] >= k + PB && ei[p] < kNB) {
+          C acc = v[p];
+#pragma unroll
+          for (int t = 0; t < PB; ++t) acc = fma(-Yk[t][ei[p]], Yk[t][ej[p]], acc);
+          v[p] = acc;
+        }
     }
+    __syncthreads();
     if (s_broke) {
       if (tid == 0) info[pi] = s_broke;
       return;
     }
-    // inverse of the rounded diagonal block R_KK
+    // inverse of the rounded diagonal block R_KK (its rows are in S; zero the lower part)
     for (int e = tid; e < kNB * kNB; e += kCT) {
       const int r = e / kNB, c = e % kNB;
-      S[r * kLd + c] = (c >= r) ? M[(int64_t)(kb + r) * npb + kb + c] : C(0);
+      if (c < r) S[r * kLd + c] = C(0);
     }
     __syncthreads();
     inv_upper64<C>(S, X, TA);

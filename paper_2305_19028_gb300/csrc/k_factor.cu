@@ -296,41 +296,94 @@ __global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t
       v[p] = M[(kb + i) * npad + kb + ej[p]];
     }
   }
-  // one barrier per pivot: row k (updated, unscaled) is published into rowk[k & 1] by its owners;
-  // the next row goes to the other buffer, whose readers all passed this barrier
-  __shared__ T rowk[2][NB];
+  // four pivots per step: the owners publish rows k .. k+3 of the updated (unscaled) block;
+  // 64 threads form the 4 x 4 factor R11 and Y = R11^{-T} S[k:k+4][:] (rows k .. k+3 of R,
+  // unrounded) into shared memory; every entry below takes the rank-4 update
+  // S[i][j] -= sum_t Y[t][i] Y[t][j]. Two barriers per step.
+  constexpr int PB = 4;
+  __shared__ T rowk[PB][NB];
+  __shared__ T Yk[PB][NB];
+  __shared__ int s_bad;
+  if (tid == 0) s_bad = 0;
   bool broke = false;
-  for (int k = 0; k < NB; ++k) {
-    T* rk = rowk[k & 1];
+  for (int k = 0; k < NB; k += PB) {
 #pragma unroll
     for (int p = 0; p < PE; ++p)
-      if (ei[p] == k) rk[ej[p]] = v[p];
+      if (ei[p] >= k && ei[p] < k + PB) rowk[ei[p] - k][ej[p]] = v[p];
     __syncthreads();
-    T piv = rk[k];
-    if (!(piv > T(0))) {                    // non-positive or NaN pivot: breakdown
-      if (tid == 0) atomicCAS(info, 0, (int)(kb + k + 1));
-      piv = T(1);
-      broke = true;
-    }
-    T rkk, inv;
-    if constexpr (sizeof(T) == 4) {
-      inv = rsqrtf(piv);                    // 1/sqrt(pivot) in one instruction; R_KK is
-      rkk = piv * inv;                      // rounded to u_f or carries an FP32 error anyway
-    } else {
-      rkk = sqrt(piv);
-      inv = T(1) / rkk;
-    }
-    const T inv2 = inv * inv;
     if (tid < NB && tid >= k) {
-      // row k of R_KK, rounded to the factor precision: to global memory and to S for the
-      // inverse below
-      const T val = round_prec((tid == k) ? rkk : rk[tid] * inv, prec);
-      M[(kb + k) * npad + kb + tid] = val;
-      S[k][tid] = val;
+      // R11 = chol(S11) (S11 symmetric: its lower entries from the published upper ones)
+      T r[PB][PB], rinv[PB];
+      int bad = 0;
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        T dsum = rowk[t][k + t];
+#pragma unroll
+        for (int q = 0; q < t; ++q) dsum = fma(-r[q][t], r[q][t], dsum);
+        if (!(dsum > T(0))) {                // non-positive or NaN pivot: breakdown
+          bad = bad ? bad : (k + t + 1);
+          dsum = T(1);
+        }
+        T rtt, inv;
+        if constexpr (sizeof(T) == 4) {
+          inv = rsqrtf(dsum);                // R_KK is rounded to u_f or carries an FP32 error
+          rtt = dsum * inv;
+        } else {
+          rtt = sqrt(dsum);
+          inv = T(1) / rtt;
+        }
+        r[t][t] = rtt;
+        rinv[t] = inv;
+#pragma unroll
+        for (int u = t + 1; u < PB; ++u) {
+          T e = rowk[t][k + u];
+#pragma unroll
+          for (int q = 0; q < t; ++q) e = fma(-r[q][t], r[q][u], e);
+          r[t][u] = e * inv;
+        }
+      }
+      // column c = tid of rows k .. k+3 of R: the pivot block from R11, the rest by forward
+      // substitution with R11^T
+      const int c = tid;
+      T y[PB];
+      if (c < k + PB) {
+#pragma unroll
+        for (int t = 0; t < PB; ++t) y[t] = (c - k >= t) ? r[t][c - k] : T(0);
+      } else {
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+          T e = rowk[t][c];
+#pragma unroll
+          for (int q = 0; q < t; ++q) e = fma(-r[q][t], y[q], e);
+          y[t] = e * rinv[t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        Yk[t][c] = y[t];
+        if (c >= k + t) {
+          // rows of R_KK rounded to the factor precision: global memory and S (for the inverse)
+          const T val = round_prec(y[t], prec);
+          M[(kb + k + t) * npad + kb + c] = val;
+          S[k + t][c] = val;
+        }
+      }
+      if (bad && tid == k) atomicCAS(&s_bad, 0, bad);
     }
+    __syncthreads();
 #pragma unroll
     for (int p = 0; p < PE; ++p)
-      if (ei[p] > k) v[p] = fma(-(rk[ei[p]] * inv2), rk[ej[p]], v[p]);
+      if (ei[p] >= k + PB) {
+        T acc = v[p];
+#pragma unroll
+        for (int t = 0; t < PB; ++t) acc = fma(-Yk[t][ei[p]], Yk[t][ej[p]], acc);
+        v[p] = acc;
+      }
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) atomicCAS(info, 0, (int)kb + s_bad);
+    broke = true;
   }
   __syncthreads();
   if (broke) return;   // uniform: every thread saw the same pivots
