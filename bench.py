@@ -384,6 +384,122 @@ def run_ours(args, ws, rank, local):
 
 
 # ------------------------------------------------------------------------------------------
+# C1: the small all-FP64 problem (400 x 40, tol 1e-12, max 10 RQI steps): latency bound
+# ------------------------------------------------------------------------------------------
+def run_c1(args, ws, rank, local):
+    import torch
+    import oracle.rqi_pcgtls as O
+    from paper_2305_19028_gb300 import synth, tls
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    tls.load()
+    p = synth.dense_problem(400, 40, d_lo=1e-2, noise=1e-6, seed=rank)
+    cpu = None
+    t0 = time.perf_counter()
+    reps = 20
+    for _ in range(reps):
+        xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=1e-12, max_rqi=10)
+    t_or = (time.perf_counter() - t0) / reps
+    if rank == 0:
+        cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} FP64 solves of the 400x40 problem, one thread of numpy"}
+    stream = torch.cuda.current_stream()
+    ctx = tls.tls_create_dense(p.A, p.b, stream=stream.cuda_stream)
+    opt = tls.tls_default_options(u="fp64")
+
+    def accurate(x, s):
+        return bool(abs(s - so) <= SIGMA_TOL * so and
+                    np.linalg.norm(x - xo) <= X_TOL * np.linalg.norm(xo))
+
+    def step():
+        tls.tls_factor(ctx, "fp64", opt)
+        return tls.tls_solve(ctx, tol=1e-12, max_rqi=10)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ok = 0
+    l0 = tls.tls_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            x, s, info = step()
+            ok += int(accurate(x, s))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = tls.tls_kernel_launches() - l0
+    ms = _barrier_max(ev0.elapsed_time(ev1), ws)
+    tls.tls_destroy(ctx)
+    # end to end from pinned host memory: create + factor + solve + destroy per step
+    A_pin = torch.from_numpy(p.A).pin_memory().numpy()
+    b_pin = torch.from_numpy(p.b).pin_memory().numpy()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    oke = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        c2 = tls.tls_create_dense(A_pin, b_pin, stream=stream.cuda_stream)
+        tls.tls_factor(c2, "fp64", opt)
+        x2, s2, _ = tls.tls_solve(c2, tol=1e-12, max_rqi=10)
+        tls.tls_destroy(c2)
+        oke += int(accurate(x2, s2))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ems = _barrier_max(e0.elapsed_time(e1), ws)
+    # the same problem as a packed batch of one (the whole solve is one CUDA graph launch)
+    with tls.Batch([(p.A, p.b)], stream=stream.cuda_stream) as bt:
+        for _ in range(args.warmup):
+            bt.factor("fp64", u="fp64")
+            bt.solve(tol=1e-12, max_rqi=10)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        okb = 0
+        b0.record(stream)
+        for _ in range(args.steps):
+            bt.factor("fp64", u="fp64")
+            xb, sb, _, _ = bt.solve(tol=1e-12, max_rqi=10)
+            okb += int(accurate(xb[0], sb[0]))
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = _barrier_max(b0.elapsed_time(b1), ws)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": ws * ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "dense_400x40_f64", "m": 400, "n": 40, "d_lo": 1e-2,
+                   "noise": 1e-6, "seed": "rank", "u_f": "fp64", "u": "fp64", "u_r": "fp64",
+                   "solve_tol": 1e-12, "max_rqi": 10,
+                   "l2": "A is 128 KB and stays in L2 (a latency-bound configuration)",
+                   "step": "tls_factor + tls_solve"},
+        "accurate_steps": ok, "rqi_steps": info["rqi_steps"],
+        "roofline": {"kernel": "none (latency bound: every kernel is a few microseconds)",
+                     "bound": "latency", "achieved": None, "peak": None, "unit": None,
+                     "frac": None, "traffic": None},
+        "packed_batch_of_one": {"value": ws * okb / (bms * 1e-3), "unit": "solves/s",
+                                "ms_per_step": bms / args.steps, "accurate": okb},
+        "gpu_launches": int(launches), "cpu_baseline": cpu,
+        "e2e": {"value": ws * oke / (ems * 1e-3), "unit": "solves/s",
+                "h2d_bytes_per_step": int(p.A.nbytes + p.b.nbytes),
+                "d2h_bytes_per_step": int(8 * 40 + 8), "ms_per_step": ems / args.steps},
+        "plain_fp64": "this configuration is the plain all-FP64 method",
+        "error_vs_oracle": {"sigma_rel": abs(s - so) / so,
+                            "x_rel": float(np.linalg.norm(x - xo) / np.linalg.norm(xo))},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
 # sparse workload (CSR 200000 x 4000, u_f BF16)
 # ------------------------------------------------------------------------------------------
 CSR_M, CSR_N, CSR_NNZ, CSR_NOISE = 200000, 4000, 12, 1e-3
@@ -781,7 +897,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--m", type=int, default=None, help="rows (profiling a smaller case)")
     ap.add_argument("--n", type=int, default=None, help="columns (profiling a smaller case)")
-    ap.add_argument("--workload", choices=["dense", "batch", "sparse"], default="dense")
+    ap.add_argument("--workload", choices=["dense", "batch", "sparse", "c1"], default="dense")
     ap.add_argument("--batch", type=int, default=BATCH_K, help="problems in the packed batch")
     ap.add_argument("--selector", action="store_true",
                     help="batch: let the trained selector network pick u_f per problem")
@@ -794,6 +910,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "sparse":
         run_sparse(args, ws, rank, local)
+    elif args.workload == "c1":
+        run_c1(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 
