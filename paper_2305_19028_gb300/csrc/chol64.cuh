@@ -1,0 +1,143 @@
+// Cholesky of one 64 x 64 diagonal block of a blocked factorisation H = R^T R (upper), shared by
+// the single-problem factor and the packed batch.
+//
+// The block's upper triangle is held in registers as the 136 4 x 4 tiles (I, J), I <= J, of its
+// 16 x 16 tile grid, one tile per thread. Four pivots per step: the threads of tile row k/4
+// publish rows k .. k+3 of the updated (unscaled) block; 64 threads form the 4 x 4 factor R11 of
+// the pivot block and the rows k .. k+3 of R, Y = R11^{-T} S[k:k+4][:] (unrounded); every tile
+// below takes the rank-4 update S[i][j] -= sum_t Y[t][i] Y[t][j] from registers. Two barriers
+// per step. Each finished row of R goes out rounded to the factor precision (global memory and
+// the shared copy S used for the inverse), while the block's own update uses the unrounded row.
+#pragma once
+#include <cstdint>
+
+namespace tls {
+namespace chol64 {
+
+constexpr int kB = 64;   // block order
+constexpr int kPB = 4;   // pivots per step
+constexpr int kTT = kB / 4;
+
+template <typename T>
+struct Scratch {
+  T rowk[kPB][kB];
+  T Yk[kPB][kB];
+  int bad;
+};
+
+// Factor the block at G (global, row stride ld; only its upper triangle is read). On return,
+// when no pivot broke down: the upper triangle of G holds R_KK rounded by `rnd`, and S (shared,
+// row stride lds) holds the same rows with zeros below the diagonal. Returns the first
+// non-positive (or NaN) pivot + 1, or 0; the value is the same in every thread. Call with all
+// threads of a CTA of at least 136 threads (blockDim.x <= 1024).
+template <typename T, typename Round>
+__device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Round rnd) {
+  const int tid = threadIdx.x;
+  int tI = kTT, tJ = 0;
+  if (tid < kTT * (kTT + 1) / 2) {
+    int off = 0, I = 0;
+    while (off + (kTT - I) <= tid) { off += kTT - I; ++I; }
+    tI = I;
+    tJ = I + (tid - off);
+  }
+  // (entries below the diagonal inside the diagonal tiles ride along and are never published)
+  T v[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      v[a][c] = (tI < kTT) ? G[(int64_t)(4 * tI + a) * ld + 4 * tJ + c] : T(0);
+  if (tid == 0) sc.bad = 0;
+  for (int k = 0; k < kB; k += kPB) {
+    if (tI == k / 4)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sc.rowk[a][4 * tJ + c] = v[a][c];
+    __syncthreads();
+    if (tid < kB && tid >= k) {
+      // R11 = chol(S11) from the published upper entries
+      T r[kPB][kPB], rinv[kPB];
+      int bad = 0;
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        T dsum = sc.rowk[t][k + t];
+#pragma unroll
+        for (int q = 0; q < t; ++q) dsum = fma(-r[q][t], r[q][t], dsum);
+        if (!(dsum > T(0))) {                // non-positive or NaN pivot: breakdown
+          bad = bad ? bad : (k + t + 1);
+          dsum = T(1);
+        }
+        T rtt, inv;
+        if constexpr (sizeof(T) == 4) {
+          inv = rsqrtf(dsum);                // R_KK is rounded to u_f or carries an FP32 error
+          rtt = dsum * inv;
+        } else {
+          rtt = sqrt(dsum);
+          inv = T(1) / rtt;
+        }
+        r[t][t] = rtt;
+        rinv[t] = inv;
+#pragma unroll
+        for (int u = t + 1; u < kPB; ++u) {
+          T e = sc.rowk[t][k + u];
+#pragma unroll
+          for (int q = 0; q < t; ++q) e = fma(-r[q][t], r[q][u], e);
+          r[t][u] = e * inv;
+        }
+      }
+      // column c = tid of rows k .. k+3 of R by forward substitution with R11^T (inside the
+      // pivot block it reproduces R11's entries operation for operation; zeros below them)
+      const int c = tid;
+      T y[kPB];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        T e = sc.rowk[t][c];
+#pragma unroll
+        for (int q = 0; q < t; ++q) e = fma(-r[q][t], y[q], e);
+        y[t] = (c - k < t) ? T(0) : e * rinv[t];
+      }
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        sc.Yk[t][c] = y[t];
+        if (c >= k + t) {
+          const T val = rnd(y[t]);
+          G[(int64_t)(k + t) * ld + c] = val;
+          S[(k + t) * lds + c] = val;
+        }
+      }
+      if (bad && tid == k) atomicCAS(&sc.bad, 0, bad);
+    }
+    __syncthreads();
+    if (tI < kTT && tI > k / 4) {
+      T yi[kPB][4], yj[kPB][4];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          yi[t][c] = sc.Yk[t][4 * tI + c];
+          yj[t][c] = sc.Yk[t][4 * tJ + c];
+        }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          T acc = v[a][c];
+#pragma unroll
+          for (int t = 0; t < kPB; ++t) acc = fma(-yi[t][a], yj[t][c], acc);
+          v[a][c] = acc;
+        }
+    }
+  }
+  __syncthreads();
+  const int bad = sc.bad;
+  for (int e = tid; e < kB * kB; e += blockDim.x) {
+    const int rr = e / kB, cc = e % kB;
+    if (cc < rr) S[rr * lds + cc] = T(0);
+  }
+  __syncthreads();
+  return bad;
+}
+
+}  // namespace chol64
+}  // namespace tls

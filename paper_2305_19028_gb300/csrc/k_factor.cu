@@ -4,6 +4,7 @@
 // W = R_H^{-1} that the PCGTLS iteration applies as two triangular products per step.
 #include "tls_internal.h"
 #include "tls_device.cuh"
+#include "chol64.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -217,11 +218,279 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// FP32 SIMT GEMM for the larger products of the factor (trailing updates, the inverse by
+// doubling, the FP32 Gram): 128 x 128 tiles, BK = 8, 256 threads with an 8 x 8 register tile
+// each (two 4-row and two 4-column strips, read from shared memory as float4), the next k-slab
+// prefetched into registers while the current one is used (one barrier per slab).
+// Same layouts and flags as gemm_simt_kernel; in addition
+//   kfrom_i: the k range of a tile row block starts at i0 (A upper triangular: A(i,k) = 0, k < i)
+//   kto_j:   the k range of a tile column block ends at j0 + 128 (B upper triangular).
+// Requires M, N multiples of 4, K a multiple of 8, lda, ldb multiples of 4 and 16-byte aligned
+// A, B (the dispatcher checks).
+// ---------------------------------------------------------------------------------------
+template <bool AK, bool BKM>
+__global__ void __launch_bounds__(256, 2) gemm_big_kernel(
+    int M, int N, int K, const float* __restrict__ A, int64_t lda, int64_t sA,
+    const float* __restrict__ B, int64_t ldb, int64_t sB, float* __restrict__ C, int64_t ldc,
+    int64_t sC, float alpha, float beta, int upper, int mirror, int kfrom_i, int kto_j,
+    const int* skip) {
+  constexpr int BM = 128, BN = 128, BK = 8;
+  if (skip != nullptr && *(volatile const int*)skip != 0) return;
+  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
+  if (upper && tile_i > tile_j) return;
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  A += (int64_t)blockIdx.z * sA;
+  B += (int64_t)blockIdx.z * sB;
+  C += (int64_t)blockIdx.z * sC;
+  const int i0 = tile_i * BM, j0 = tile_j * BN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  int k_lo = kfrom_i ? (i0 / BK) * BK : 0;
+  int k_hi = kto_j ? min(K, j0 + BN) : K;
+  if (k_lo > K) k_lo = K;
+  // global -> register slab loader: one float4 of A and one of B per thread
+  // A: AK: row i = tid / 2, k = (tid & 1) * 4 (contiguous in k); else k = tid / 32, i = (tid & 31) * 4
+  // B: BKM: col j = tid / 2, k = (tid & 1) * 4; else k = tid / 32, j = (tid & 31) * 4
+  const int a_r = AK ? (tid >> 1) : ((tid & 31) * 4);
+  const int a_k = AK ? ((tid & 1) * 4) : (tid >> 5);
+  const int b_c = BKM ? (tid >> 1) : ((tid & 31) * 4);
+  const int b_k = BKM ? ((tid & 1) * 4) : (tid >> 5);
+  auto load_a = [&](int k0) -> float4 {
+    const int gi = i0 + a_r, gk = k0 + a_k;
+    if (AK) {
+      if (gi < M && gk < K) return *reinterpret_cast<const float4*>(A + (int64_t)gi * lda + gk);
+    } else {
+      if (gi < M && gk < K) return *reinterpret_cast<const float4*>(A + (int64_t)gk * lda + gi);
+    }
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto load_b = [&](int k0) -> float4 {
+    const int gj = j0 + b_c, gk = k0 + b_k;
+    if (BKM) {
+      if (gj < N && gk < K) return *reinterpret_cast<const float4*>(B + (int64_t)gj * ldb + gk);
+    } else {
+      if (gj < N && gk < K) return *reinterpret_cast<const float4*>(B + (int64_t)gk * ldb + gj);
+    }
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto store = [&](int buf, const float4& va, const float4& vb) {
+    if (AK) {
+      As[buf][a_k + 0][a_r] = va.x;
+      As[buf][a_k + 1][a_r] = va.y;
+      As[buf][a_k + 2][a_r] = va.z;
+      As[buf][a_k + 3][a_r] = va.w;
+    } else {
+      *reinterpret_cast<float4*>(&As[buf][a_k][a_r]) = va;
+    }
+    if (BKM) {
+      Bs[buf][b_k + 0][b_c] = vb.x;
+      Bs[buf][b_k + 1][b_c] = vb.y;
+      Bs[buf][b_k + 2][b_c] = vb.z;
+      Bs[buf][b_k + 3][b_c] = vb.w;
+    } else {
+      *reinterpret_cast<float4*>(&Bs[buf][b_k][b_c]) = vb;
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  if (k_lo < k_hi) {
+    float4 va = load_a(k_lo), vb = load_b(k_lo);
+    store(0, va, vb);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
+      const bool more = k0 + BK < k_hi;
+      if (more) {
+        va = load_a(k0 + BK);
+        vb = load_b(k0 + BK);
+      }
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+      }
+      if (more) {
+        store(buf ^ 1, va, vb);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int gi = i0 + (p < 4 ? ty * 4 + p : 64 + ty * 4 + p - 4);
+    if (gi >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int gj = j0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
+      if (gj >= N || (upper && gi > gj)) continue;
+      float* cp = C + (int64_t)gi * ldc + gj;
+      float v = alpha * acc[p][q];
+      if (beta != 0.f) v += beta * (*cp);
+      *cp = v;
+      if (mirror && gi != gj) C[(int64_t)gj * ldc + gi] = v;
+    }
+  }
+}
+
+// FP32 64 x 64-tile variant of the same product for grids too small for 128 x 128 tiles (or K
+// too short to amortise them): BK = 16, 256 threads with a 4 x 4 register tile each, operands
+// read from shared memory as float4, the next k-slab prefetched into registers (one barrier per
+// slab). Same requirements as gemm_big_kernel, K a multiple of 16.
+template <bool AK, bool BKM>
+__global__ void __launch_bounds__(256) gemm_mid_kernel(
+    int M, int N, int K, const float* __restrict__ A, int64_t lda, int64_t sA,
+    const float* __restrict__ B, int64_t ldb, int64_t sB, float* __restrict__ C, int64_t ldc,
+    int64_t sC, float alpha, float beta, int upper, int mirror, int kfrom_i, int kto_j,
+    const int* skip) {
+  constexpr int BM = 64, BN = 64, BK = 16, LD = 68;
+  if (skip != nullptr && *(volatile const int*)skip != 0) return;
+  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
+  if (upper && tile_i > tile_j) return;
+  __shared__ __align__(16) float As[2][BK][LD];
+  __shared__ __align__(16) float Bs[2][BK][LD];
+  A += (int64_t)blockIdx.z * sA;
+  B += (int64_t)blockIdx.z * sB;
+  C += (int64_t)blockIdx.z * sC;
+  const int i0 = tile_i * BM, j0 = tile_j * BN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  int k_lo = kfrom_i ? (i0 / BK) * BK : 0;
+  const int k_hi = kto_j ? min(K, j0 + BN) : K;
+  if (k_lo > K) k_lo = K;
+  // A: AK: row i = tid / 4, k = (tid & 3) * 4; else k = tid / 16, i = (tid & 15) * 4
+  const int a_r = AK ? (tid >> 2) : ((tid & 15) * 4);
+  const int a_k = AK ? ((tid & 3) * 4) : (tid >> 4);
+  const int b_c = BKM ? (tid >> 2) : ((tid & 15) * 4);
+  const int b_k = BKM ? ((tid & 3) * 4) : (tid >> 4);
+  auto load_a = [&](int k0) -> float4 {
+    const int gi = i0 + a_r, gk = k0 + a_k;
+    if (gi < M && gk < K)
+      return *reinterpret_cast<const float4*>(AK ? (A + (int64_t)gi * lda + gk)
+                                                 : (A + (int64_t)gk * lda + gi));
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto load_b = [&](int k0) -> float4 {
+    const int gj = j0 + b_c, gk = k0 + b_k;
+    if (gj < N && gk < K)
+      return *reinterpret_cast<const float4*>(BKM ? (B + (int64_t)gj * ldb + gk)
+                                                  : (B + (int64_t)gk * ldb + gj));
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto store = [&](int buf, const float4& va, const float4& vb) {
+    if (AK) {
+      As[buf][a_k + 0][a_r] = va.x;
+      As[buf][a_k + 1][a_r] = va.y;
+      As[buf][a_k + 2][a_r] = va.z;
+      As[buf][a_k + 3][a_r] = va.w;
+    } else {
+      *reinterpret_cast<float4*>(&As[buf][a_k][a_r]) = va;
+    }
+    if (BKM) {
+      Bs[buf][b_k + 0][b_c] = vb.x;
+      Bs[buf][b_k + 1][b_c] = vb.y;
+      Bs[buf][b_k + 2][b_c] = vb.z;
+      Bs[buf][b_k + 3][b_c] = vb.w;
+    } else {
+      *reinterpret_cast<float4*>(&Bs[buf][b_k][b_c]) = vb;
+    }
+  };
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  if (k_lo < k_hi) {
+    float4 va = load_a(k_lo), vb = load_b(k_lo);
+    store(0, va, vb);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
+      const bool more = k0 + BK < k_hi;
+      if (more) {
+        va = load_a(k0 + BK);
+        vb = load_b(k0 + BK);
+      }
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+      }
+      if (more) {
+        store(buf ^ 1, va, vb);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int gi = i0 + ty * 4 + p;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gj = j0 + tx * 4 + q;
+      if (gj >= N || (upper && gi > gj)) continue;
+      float* cp = C + (int64_t)gi * ldc + gj;
+      float v = alpha * acc[p][q];
+      if (beta != 0.f) v += beta * (*cp);
+      *cp = v;
+      if (mirror && gi != gj) C[(int64_t)gj * ldc + gi] = v;
+    }
+  }
+}
+
 template <typename Tin, typename Tc, bool AK, bool BKM>
 void gemm_simt(int M, int N, int K, const Tin* A, int64_t lda, int64_t sA, const Tin* B,
                int64_t ldb, int64_t sB, Tc* C, int64_t ldc, int64_t sC, Tc alpha, Tc beta,
-               int upper, int mirror, int batch, cudaStream_t s, const int* skip = nullptr) {
+               int upper, int mirror, int batch, cudaStream_t s, const int* skip = nullptr,
+               int kfrom_i = 0, int kto_j = 0) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
+  if constexpr (std::is_same<Tin, float>::value && std::is_same<Tc, float>::value) {
+    const bool aligned = (M % 4 == 0) && (N % 4 == 0) && (K % 8 == 0) && (lda % 4 == 0) &&
+                         (ldb % 4 == 0) && (sA % 4 == 0) && (sB % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(B) % 16 == 0);
+    if (aligned) {
+      // 128 x 128 tiles when they still fill the GPU twice over and K is long enough to
+      // amortise them; 64 x 64 otherwise
+      const int64_t t128 = (int64_t)((N + 127) / 128) * ((M + 127) / 128) * batch;
+      const int64_t busy = upper ? (t128 + (int64_t)((N + 127) / 128) * batch) / 2 : t128;
+      if (M >= 128 && N >= 128 && K >= 256 && busy >= 2 * 152) {
+        dim3 g((N + 127) / 128, (M + 127) / 128, batch);
+        gemm_big_kernel<AK, BKM><<<g, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC,
+                                                   alpha, beta, upper, mirror, kfrom_i, kto_j,
+                                                   skip);
+        count_launch();
+        return;
+      }
+      if (K % 16 == 0) {
+        dim3 g((N + 63) / 64, (M + 63) / 64, batch);
+        gemm_mid_kernel<AK, BKM><<<g, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC,
+                                                   alpha, beta, upper, mirror, kfrom_i, kto_j,
+                                                   skip);
+        count_launch();
+        return;
+      }
+    }
+  }
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   gemm_simt_kernel<Tin, Tc, AK, BKM><<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C,
                                                          ldc, sC, alpha, beta, upper, mirror,
@@ -260,10 +529,9 @@ __device__ __forceinline__ double round_prec(double v, int prec) {
 }
 
 // Diagonal block K = [kb, kb+64) of the blocked Cholesky H = R^T R (upper):
-//  1. factor the block (256 threads, the upper triangle held in registers, one barrier per
-//     pivot; each finished row of R_KK, rounded to the factor precision, goes straight to
-//     global memory, while the update of step k uses the unrounded row as
-//     S[k][i] S[k][j] / S[k][k]);
+//  1. factor the block (chol64::factor_block: four pivots per step, the block's upper triangle
+//     in registers as 4 x 4 tiles; each finished row of R_KK, rounded to the factor precision,
+//     goes to global memory and to S, while the block's own update uses the unrounded rows);
 //  2. invert the rounded R_KK by doubling from 8 x 8 blocks,
 //     [[X11, -X11 R12 X22], [0, X22]] at block sizes 8, 16, 32, into W.
 // W_KK turns the panel solve R_KJ = R_KK^{-T} H_KJ into a product, and it is also the diagonal
@@ -276,122 +544,14 @@ __global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t
   T (*S)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm);
   T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
   const int tid = threadIdx.x;
-  // the 2080 entries of the block's upper triangle are dealt round-robin to the 256 threads
-  // and stay in registers through the factorisation (entry e = tid + 256 p, row-major order)
-  constexpr int NE = NB * (NB + 1) / 2;
-  constexpr int PE = (NE + 255) / 256;
-  T v[PE];
-  int ei[PE], ej[PE];
-#pragma unroll
-  for (int p = 0; p < PE; ++p) {
-    const int e = tid + 256 * p;
-    ei[p] = NB;   // never updated or published
-    ej[p] = 0;
-    v[p] = T(0);
-    if (e < NE) {
-      int i = 0, off = 0;
-      while (off + (NB - i) <= e) { off += NB - i; ++i; }
-      ei[p] = i;
-      ej[p] = i + (e - off);
-      v[p] = M[(kb + i) * npad + kb + ej[p]];
-    }
+  __shared__ chol64::Scratch<T> sc;
+  const int bad = chol64::factor_block<T>(M + kb * npad + kb, npad, &S[0][0], NB + 1, sc,
+                                          [prec](T v) { return round_prec(v, prec); });
+  if (bad) {
+    if (tid == 0) atomicCAS(info, 0, (int)kb + bad);
+    return;   // uniform: every thread saw the same pivots
   }
-  // four pivots per step: the owners publish rows k .. k+3 of the updated (unscaled) block;
-  // 64 threads form the 4 x 4 factor R11 and Y = R11^{-T} S[k:k+4][:] (rows k .. k+3 of R,
-  // unrounded) into shared memory; every entry below takes the rank-4 update
-  // S[i][j] -= sum_t Y[t][i] Y[t][j]. Two barriers per step.
-  constexpr int PB = 4;
-  __shared__ T rowk[PB][NB];
-  __shared__ T Yk[PB][NB];
-  __shared__ int s_bad;
-  if (tid == 0) s_bad = 0;
-  bool broke = false;
-  for (int k = 0; k < NB; k += PB) {
-#pragma unroll
-    for (int p = 0; p < PE; ++p)
-      if (ei[p] >= k && ei[p] < k + PB) rowk[ei[p] - k][ej[p]] = v[p];
-    __syncthreads();
-    if (tid < NB && tid >= k) {
-      // R11 = chol(S11) (S11 symmetric: its lower entries from the published upper ones)
-      T r[PB][PB], rinv[PB];
-      int bad = 0;
-#pragma unroll
-      for (int t = 0; t < PB; ++t) {
-        T dsum = rowk[t][k + t];
-#pragma unroll
-        for (int q = 0; q < t; ++q) dsum = fma(-r[q][t], r[q][t], dsum);
-        if (!(dsum > T(0))) {                // non-positive or NaN pivot: breakdown
-          bad = bad ? bad : (k + t + 1);
-          dsum = T(1);
-        }
-        T rtt, inv;
-        if constexpr (sizeof(T) == 4) {
-          inv = rsqrtf(dsum);                // R_KK is rounded to u_f or carries an FP32 error
-          rtt = dsum * inv;
-        } else {
-          rtt = sqrt(dsum);
-          inv = T(1) / rtt;
-        }
-        r[t][t] = rtt;
-        rinv[t] = inv;
-#pragma unroll
-        for (int u = t + 1; u < PB; ++u) {
-          T e = rowk[t][k + u];
-#pragma unroll
-          for (int q = 0; q < t; ++q) e = fma(-r[q][t], r[q][u], e);
-          r[t][u] = e * inv;
-        }
-      }
-      // column c = tid of rows k .. k+3 of R: the pivot block from R11, the rest by forward
-      // substitution with R11^T
-      const int c = tid;
-      T y[PB];
-      if (c < k + PB) {
-#pragma unroll
-        for (int t = 0; t < PB; ++t) y[t] = (c - k >= t) ? r[t][c - k] : T(0);
-      } else {
-#pragma unroll
-        for (int t = 0; t < PB; ++t) {
-          T e = rowk[t][c];
-#pragma unroll
-          for (int q = 0; q < t; ++q) e = fma(-r[q][t], y[q], e);
-          y[t] = e * rinv[t];
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < PB; ++t) {
-        Yk[t][c] = y[t];
-        if (c >= k + t) {
-          // rows of R_KK rounded to the factor precision: global memory and S (for the inverse)
-          const T val = round_prec(y[t], prec);
-          M[(kb + k + t) * npad + kb + c] = val;
-          S[k + t][c] = val;
-        }
-      }
-      if (bad && tid == k) atomicCAS(&s_bad, 0, bad);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PE; ++p)
-      if (ei[p] >= k + PB) {
-        T acc = v[p];
-#pragma unroll
-        for (int t = 0; t < PB; ++t) acc = fma(-Yk[t][ei[p]], Yk[t][ej[p]], acc);
-        v[p] = acc;
-      }
-  }
-  __syncthreads();
-  if (s_bad) {
-    if (tid == 0) atomicCAS(info, 0, (int)kb + s_bad);
-    broke = true;
-  }
-  __syncthreads();
-  if (broke) return;   // uniform: every thread saw the same pivots
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int r = e / NB, c = e % NB;
-    if (c < r) S[r][c] = T(0);
-    X[r][c] = T(0);
-  }
+  for (int e = tid; e < NB * NB; e += 256) X[e / NB][e % NB] = T(0);
   __syncthreads();
   // inverse by doubling: the eight 8 x 8 diagonal blocks by substitution (thread: one column,
   // chains of at most 8), then for s = 8, 16, 32 every pair of s-blocks A, B gets
@@ -628,11 +788,13 @@ void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, bool have_diag
     if (full_pairs > 0) {
       // work_AB = R_AB W_BB ; W_AB = -W_AA work_AB   (batched over the full pairs)
       const int64_t st = 2 * sz * npad + 2 * sz;   // stride between pairs along the diagonal
+      // (W_BB and W_AA are upper triangular: the products skip their zero k-slabs)
       gemm_simt<T, T, true, false>((int)sz, (int)sz, (int)sz, R + sz, npad, st, W + sz * npad + sz,
                                    npad, st, work + sz, npad, st, T(1), T(0), 0, 0,
-                                   (int)full_pairs, s);
+                                   (int)full_pairs, s, nullptr, 0, 1);
       gemm_simt<T, T, true, false>((int)sz, (int)sz, (int)sz, W, npad, st, work + sz, npad, st,
-                                   W + sz, npad, st, T(-1), T(0), 0, 0, (int)full_pairs, s);
+                                   W + sz, npad, st, T(-1), T(0), 0, 0, (int)full_pairs, s,
+                                   nullptr, 1, 0);
     }
     const int64_t o = full_pairs * 2 * sz;
     const int64_t sB = npad - o - sz;
@@ -641,9 +803,10 @@ void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, bool have_diag
       const T* Wbb = W + (o + sz) * npad + o + sz;
       T* Wk = work + o * npad + o + sz;
       gemm_simt<T, T, true, false>((int)sz, (int)sB, (int)sB, Rab, npad, 0, Wbb, npad, 0, Wk, npad,
-                                   0, T(1), T(0), 0, 0, 1, s);
+                                   0, T(1), T(0), 0, 0, 1, s, nullptr, 0, 1);
       gemm_simt<T, T, true, false>((int)sz, (int)sB, (int)sz, W + o * npad + o, npad, 0, Wk, npad,
-                                   0, W + o * npad + o + sz, npad, 0, T(-1), T(0), 0, 0, 1, s);
+                                   0, W + o * npad + o + sz, npad, 0, T(-1), T(0), 0, 0, 1, s,
+                                   nullptr, 1, 0);
     }
   }
   dim3 grid((unsigned)(npad / 32), (unsigned)(npad / 32));
