@@ -20,6 +20,8 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
+#include "chol64.cuh"
+
 namespace tls {
 namespace bat {
 
@@ -476,276 +478,228 @@ __device__ void inv_upper64(const C* S, C* X, C* Tm) {
 }
 
 // =========================================================================================
-// Blocked Cholesky H + s I = R_H^T R_H (upper, 64-blocks), one CTA per problem:
-//  diagonal block: one barrier per pivot, each finished row of R_KK rounded to u_f as it is
-//  written (the shared copy keeps the unrounded row for the block's own update); panel
-//  R_KJ = R_KK^{-T} H_KJ through the inverse of the rounded R_KK; trailing update
-//  H_22 -= R_K2^T R_K2. Finally every entry of R_H is rounded to u_f and the lower part zeroed.
-// A non-positive (or NaN) pivot stops the problem: info = pivot + 1.
+// Blocked Cholesky H + s I = R_H^T R_H (upper, 64-blocks) and W = R_H^{-1}, as task lists over
+// all listed problems: step s of every problem runs in the same three launches (diagonal
+// blocks, panels, trailing tiles), so the work of the large problems spreads over the GPU
+// instead of one CTA each. A CTask names a problem and a block step; the host builds the lists.
 // =========================================================================================
-template <typename C>
-__global__ void __launch_bounds__(kCT, 2) chol_kernel(BArrays a, const int* list, const double* shift,
-                                                   int* info) {
-  const int pi = list[blockIdx.x];
-  const BProb P = a.probs[pi];
-  const int npb = (int)P.npb, n = (int)P.n, prec = P.prec;
-  const C* H = static_cast<const C*>(a.H) + P.offM;
-  C* M = static_cast<C*>(a.R) + P.offM;
-  extern __shared__ __align__(16) unsigned char smem[];
-  C* S = reinterpret_cast<C*>(smem);   // 64 x kLd each
-  C* X = S + kNB * kLd;
-  C* TA = X + kNB * kLd;
-  C* TB = TA + kNB * kLd;
-  __shared__ int s_broke;
-  const int tid = threadIdx.x;
-  const C sh = (C)shift[pi];
-  for (int64_t e = tid; e < (int64_t)npb * npb; e += kCT) {
-    const int r = (int)(e / npb), c = (int)(e % npb);
-    C v = H[e];
-    if (r == c && r < n) v += sh;
-    M[e] = v;
+
+// 64 x 64 global tile G (row stride ld) into shared memory D (row stride kLd), transposed
+// (D[c][r] = G[r][c]) or not; 256 threads.
+template <typename Tin, typename T>
+__device__ __forceinline__ void stage64(const Tin* __restrict__ G, int64_t ld, T* D, bool trans) {
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const int r = e >> 6, c = e & 63;
+    const T v = (T)G[(int64_t)r * ld + c];
+    if (trans) D[c * kLd + r] = v;
+    else D[r * kLd + c] = v;
   }
-  if (tid == 0) s_broke = 0;
-  __syncthreads();
-  // diagonal block: its 2080 upper entries dealt round-robin to the threads and kept in
-  // registers; four pivots per step (publish rows k .. k+3, 64 threads form R11 and
-  // Y = R11^{-T} S[k:k+4][:], rank-4 update of the rest), two barriers per step
-  constexpr int NE = kNB * (kNB + 1) / 2;
-  constexpr int PE = (NE + kCT - 1) / kCT;
-  constexpr int PB = 4;
-  __shared__ C rowk[PB][kNB];
-  __shared__ C Yk[PB][kNB];
-  int ei[PE], ej[PE];
-#pragma unroll
-  for (int p = 0; p < PE; ++p) {
-    const int e = tid + kCT * p;
-    ei[p] = kNB;
-    ej[p] = 0;
-    if (e < NE) {
-      int i = 0, off = 0;
-      while (off + (kNB - i) <= e) { off += kNB - i; ++i; }
-      ei[p] = i;
-      ej[p] = i + (e - off);
-    }
-  }
-  for (int kb = 0; kb < npb; kb += kNB) {
-    C v[PE];
-#pragma unroll
-    for (int p = 0; p < PE; ++p)
-      v[p] = (ei[p] < kNB) ? M[(int64_t)(kb + ei[p]) * npb + kb + ej[p]] : C(0);
-    for (int k = 0; k < kNB; k += PB) {
-#pragma unroll
-      for (int p = 0; p < PE; ++p)
-        if (ei[p] >= k && ei[p] < k + PB) rowk[ei[p] - k][ej[p]] = v[p];
-      __syncthreads();
-      if (tid < kNB && tid >= k) {
-        C r[PB][PB], rinv[PB];
-        int bad = 0;
-#pragma unroll
-        for (int t = 0; t < PB; ++t) {
-          C dsum = rowk[t][k + t];
-#pragma unroll
-          for (int q = 0; q < t; ++q) dsum = fma(-r[q][t], r[q][t], dsum);
-          if (!(dsum > C(0))) {                // non-positive or NaN pivot: breakdown
-            bad = bad ? bad : (k + t + 1);
-            dsum = C(1);
-          }
-          C rtt, inv;
-          if constexpr (sizeof(C) == 4) {
-            inv = rsqrtf(dsum);
-            rtt = dsum * inv;
-          } else {
-            rtt = sqrt(dsum);
-            inv = C(1) / rtt;
-          }
-          r[t][t] = rtt;
-          rinv[t] = inv;
-#pragma unroll
-          for (int u = t + 1; u < PB; ++u) {
-            C e = rowk[t][k + u];
-#pragma unroll
-            for (int q = 0; q < t; ++q) e = fma(-r[q][t], r[q][u], e);
-            r[t][u] = e * inv;
-          }
-        }
-        const int c = tid;
-        C y[PB];
-        if (c < k + PB) {
-#pragma unroll
-          for (int t = 0; t < PB; ++t) y[t] = (c - k >= t) ? r[t][c - k] : C(0);
-        } else {
-#pragma unroll
-          for (int t = 0; t < PB; ++t) {
-            C e = rowk[t][c];
-#pragma unroll
-            for (int q = 0; q < t; ++q) e = fma(-r[q][t], y[q], e);
-            y[t] = e * rinv[t];
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < PB; ++t) {
-          Yk[t][c] = y[t];
-          if (c >= k + t) {
-            // rows of R_KK rounded to u_f: to global memory and to S for the inverse
-            const C val = round_uf(y[t], prec);
-            M[(int64_t)(kb + k + t) * npb + kb + c] = val;
-            S[(k + t) * kLd + c] = val;
-          }
-        }
-        if (bad && tid == k) atomicCAS(&s_broke, 0, kb + bad);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int p = 0; p < PE; ++p)
-        if (ei[p] >= k + PB && ei[p] < kNB) {
-          C acc = v[p];
-#pragma unroll
-          for (int t = 0; t < PB; ++t) acc = fma(-Yk[t][ei[p]], Yk[t][ej[p]], acc);
-          v[p] = acc;
-        }
-    }
-    __syncthreads();
-    if (s_broke) {
-      if (tid == 0) info[pi] = s_broke;
-      return;
-    }
-    // inverse of the rounded diagonal block R_KK (its rows are in S; zero the lower part)
-    for (int e = tid; e < kNB * kNB; e += kCT) {
-      const int r = e / kNB, c = e % kNB;
-      if (c < r) S[r * kLd + c] = C(0);
-    }
-    __syncthreads();
-    inv_upper64<C>(S, X, TA);
-    // panel: R_KJ = W_KK^T H_KJ, 64 columns at a time (thread: column j, rows i0 .. i0+7)
-    for (int jb = kb + kNB; jb < npb; jb += kNB) {
-      for (int e = tid; e < kNB * kNB; e += kCT) {
-        const int r = e / kNB, c = e % kNB;
-        TA[r * kLd + c] = M[(int64_t)(kb + r) * npb + jb + c];
-      }
-      __syncthreads();
-      const int j = tid & 63, i0 = (tid >> 6) * 8;
-      C o[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) o[u] = C(0);
-      for (int k = 0; k < i0 + 8; ++k) {
-        const C t = TA[k * kLd + j];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (k <= i0 + u) o[u] = fma(X[k * kLd + i0 + u], t, o[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) M[(int64_t)(kb + i0 + u) * npb + jb + j] = o[u];
-      __syncthreads();
-    }
-    // trailing update of the upper blocks (bi <= bj) right of and below the panel
-    for (int bi = kb + kNB; bi < npb; bi += kNB) {
-      for (int bj = bi; bj < npb; bj += kNB) {
-        for (int e = tid; e < kNB * kNB; e += kCT) {
-          const int r = e / kNB, c = e % kNB;
-          TA[r * kLd + c] = M[(int64_t)(kb + r) * npb + bi + c];
-          TB[r * kLd + c] = M[(int64_t)(kb + r) * npb + bj + c];
-        }
-        __syncthreads();
-        const int i = tid >> 3, j0 = (tid & 7) * 8;
-        C o[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) o[u] = C(0);
-#pragma unroll 4
-        for (int k = 0; k < kNB; ++k) {
-          const C ak = TA[k * kLd + i];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) o[u] = fma(ak, TB[k * kLd + j0 + u], o[u]);
-        }
-        C* row = M + (int64_t)(bi + i) * npb + bj + j0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) row[u] -= o[u];
-        __syncthreads();
-      }
-    }
-  }
-  __syncthreads();
-  for (int64_t e = tid; e < (int64_t)npb * npb; e += kCT) {
-    const int r = (int)(e / npb), c = (int)(e % npb);
-    M[e] = (c < r) ? C(0) : round_uf(M[e], prec);
-  }
-  if (tid == 0) info[pi] = 0;
 }
 
-// =========================================================================================
-// W = R_H^{-1} (u type T) by block rows from the bottom: W_II = R_II^{-1},
-// W_IJ = -W_II sum_{I<K<=J} R_IK W_KJ; then W^T. One CTA per problem.
-// =========================================================================================
-template <typename C, typename T>
-__global__ void __launch_bounds__(kCT) trtri_kernel(BArrays a, const int* list) {
+__device__ __forceinline__ void lds4(const float* p, float (&o)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&o)[4]) {
+  const double2 t0 = *reinterpret_cast<const double2*>(p);
+  const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+}
+
+// acc += As^T Bs over k = 0..63 for the 4 x 4 outputs of this thread: rows 4 ty .. +3, columns
+// 4 tx .. +3 (tx = tid % 16, ty = tid / 16; 256 threads); As[k][i], Bs[k][j] in shared memory.
+template <typename T>
+__device__ __forceinline__ void tile_atb(const T* As, const T* Bs, T (&acc)[4][4]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 8
+  for (int k = 0; k < kNB; ++k) {
+    T av[4], bv[4];
+    lds4(As + k * kLd + 4 * ty, av);
+    lds4(Bs + k * kLd + 4 * tx, bv);
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = fma(av[p], bv[q], acc[p][q]);
+  }
+}
+
+// M = H + shift I for the listed problems; info = 0. Grid (problems, 8).
+template <typename C>
+__global__ void __launch_bounds__(256) chol_init_kernel(BArrays a, const int* list,
+                                                        const double* shift, int* info) {
   const int pi = list[blockIdx.x];
   const BProb P = a.probs[pi];
-  const int npb = (int)P.npb, nb = npb / kNB;
+  const int64_t npb = P.npb;
+  const C* H = static_cast<const C*>(a.H) + P.offM;
+  C* M = static_cast<C*>(a.R) + P.offM;
+  const C sh = (C)shift[pi];
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < npb * npb;
+       e += (int64_t)blockDim.x * gridDim.y) {
+    const int64_t r = e / npb, c = e % npb;
+    C v = H[e];
+    if (r == c && r < P.n) v += sh;
+    M[e] = v;
+  }
+  if (blockIdx.y == 0 && threadIdx.x == 0) info[pi] = 0;
+}
+
+// Step s, diagonal block: R_ss (rows rounded to u_f as they are written) and, when a panel
+// follows, W_ss = R_ss^{-1} of the rounded block, parked in the unused block (s+1, s) below the
+// diagonal. A non-positive (or NaN) pivot stops the problem: info = pivot + 1.
+template <typename C>
+__global__ void __launch_bounds__(256) chol_diag_kernel(BArrays a, const CTask* tasks, int* info) {
+  const CTask t = tasks[blockIdx.x];
+  if (*(volatile int*)(info + t.prob) != 0) return;
+  const BProb P = a.probs[t.prob];
+  const int64_t npb = P.npb;
+  const int nb = (int)(npb / kNB), kb = t.s * kNB, prec = P.prec;
+  C* M = static_cast<C*>(a.R) + P.offM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* S = reinterpret_cast<C*>(smem);
+  C* X = S + kNB * kLd;
+  C* Tm = X + kNB * kLd;
+  __shared__ chol64::Scratch<C> sc;
+  const int bad = chol64::factor_block<C>(M + (int64_t)kb * npb + kb, npb, S, kLd, sc,
+                                          [prec](C v) { return round_uf(v, prec); });
+  if (bad) {
+    if (threadIdx.x == 0) info[t.prob] = kb + bad;
+    return;
+  }
+  if (t.s + 1 < nb) {
+    inv_upper64<C>(S, X, Tm);
+    C* Wp = M + (int64_t)(kb + kNB) * npb + kb;
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x)
+      Wp[(int64_t)(e >> 6) * npb + (e & 63)] = X[(e >> 6) * kLd + (e & 63)];
+  }
+}
+
+// Step s, panel block (s, bj): R_s,bj = W_ss^T H_s,bj in place.
+// Step s, trailing block (bi, bj), s < bi <= bj: H_bi,bj -= R_s,bi^T R_s,bj.
+template <typename C, bool PANEL>
+__global__ void __launch_bounds__(256) chol_tile_kernel(BArrays a, const CTask* tasks,
+                                                        const int* info) {
+  const CTask t = tasks[blockIdx.x];
+  if (*(volatile const int*)(info + t.prob) != 0) return;
+  const BProb P = a.probs[t.prob];
+  const int64_t npb = P.npb;
+  const int kb = t.s * kNB;
+  C* M = static_cast<C*>(a.R) + P.offM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* As = reinterpret_cast<C*>(smem);
+  C* Bs = As + kNB * kLd;
+  const C* Ag = PANEL ? M + (int64_t)(kb + kNB) * npb + kb : M + (int64_t)kb * npb + t.bi * kNB;
+  const C* Bg = M + (int64_t)kb * npb + t.bj * kNB;
+  C* Cg = PANEL ? M + (int64_t)kb * npb + t.bj * kNB
+                : M + (int64_t)t.bi * kNB * npb + t.bj * kNB;
+  stage64<C, C>(Ag, npb, As, false);
+  stage64<C, C>(Bg, npb, Bs, false);
+  __syncthreads();
+  C acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = C(0);
+  tile_atb<C>(As, Bs, acc);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      C* cp = Cg + (int64_t)(4 * ty + p) * npb + 4 * tx + q;
+      *cp = PANEL ? acc[p][q] : *cp - acc[p][q];
+    }
+}
+
+// Every entry of R_H rounded to u_f, the lower part zeroed (W_ss blocks included).
+// Grid (problems, 8).
+template <typename C>
+__global__ void __launch_bounds__(256) chol_final_kernel(BArrays a, const int* list,
+                                                         const int* info) {
+  const int pi = list[blockIdx.x];
+  if (info[pi] != 0) return;
+  const BProb P = a.probs[pi];
+  const int64_t npb = P.npb;
+  const int prec = P.prec;
+  C* M = static_cast<C*>(a.R) + P.offM;
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < npb * npb;
+       e += (int64_t)blockDim.x * gridDim.y) {
+    const int64_t r = e / npb, c = e % npb;
+    M[e] = (c < r) ? C(0) : round_uf(M[e], prec);
+  }
+}
+
+// W = R_H^{-1} (u type T) by block diagonals. Level 0, task (prob, I): W_II = R_II^{-1} and the
+// zero blocks left of it. Level d, task (prob, I, J = I + d): W_IJ = -W_II sum_{I<K<=J} R_IK W_KJ
+// (the W_KJ are on lower levels). Each task also writes its block of W^T.
+template <typename C, typename T>
+__global__ void __launch_bounds__(256) trtri_tile_kernel(BArrays a, const CTask* tasks) {
+  const CTask t = tasks[blockIdx.x];
+  const BProb P = a.probs[t.prob];
+  const int64_t npb = P.npb;
+  const int I = t.bi, J = t.bj;
   const C* R = static_cast<const C*>(a.R) + P.offM;
   T* W = static_cast<T*>(a.W) + P.offM;
   T* WT = static_cast<T*>(a.WT) + P.offM;
   extern __shared__ __align__(16) unsigned char smem[];
-  T* S = reinterpret_cast<T*>(smem);
-  T* X = S + kNB * kLd;
-  T* TA = X + kNB * kLd;
-  T* TB = TA + kNB * kLd;
+  T* S = reinterpret_cast<T*>(smem);      // 64 x kLd
+  T* X = S + kNB * kLd;                   // 64 x kLd
+  T* Tm = X + kNB * kLd;                  // 64 x kLd
   const int tid = threadIdx.x;
-  for (int64_t e = tid; e < (int64_t)npb * npb; e += kCT) W[e] = T(0);
-  __syncthreads();
-  for (int ib = nb - 1; ib >= 0; --ib) {
-    const int r0 = ib * kNB;
-    for (int e = tid; e < kNB * kNB; e += kCT) {
-      const int r = e / kNB, c = e % kNB;
-      S[r * kLd + c] = (c >= r) ? (T)R[(int64_t)(r0 + r) * npb + r0 + c] : T(0);
+  if (I == J) {
+    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+      const int r = e >> 6, c = e & 63;
+      S[r * kLd + c] = (c >= r) ? (T)R[(int64_t)(I * kNB + r) * npb + I * kNB + c] : T(0);
     }
     __syncthreads();
-    inv_upper64<T>(S, X, TA);   // X = W_II
-    for (int e = tid; e < kNB * kNB; e += kCT) {
-      const int r = e / kNB, c = e % kNB;
-      W[(int64_t)(r0 + r) * npb + r0 + c] = X[r * kLd + c];
+    inv_upper64<T>(S, X, Tm);
+    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+      const int r = e >> 6, c = e & 63;
+      const T v = X[r * kLd + c];
+      W[(int64_t)(I * kNB + r) * npb + I * kNB + c] = v;
+      WT[(int64_t)(I * kNB + c) * npb + I * kNB + r] = v;
     }
-    for (int jb = ib + 1; jb < nb; ++jb) {
-      // Tacc = sum_{K = ib+1 .. jb} R_IK W_KJ   (thread: row i, columns j0 .. j0+7)
-      const int i = tid >> 3, j0 = (tid & 7) * 8;
-      T o[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) o[u] = T(0);
-      for (int kb2 = ib + 1; kb2 <= jb; ++kb2) {
-        __syncthreads();
-        for (int e = tid; e < kNB * kNB; e += kCT) {
-          const int r = e / kNB, c = e % kNB;
-          TA[r * kLd + c] = (T)R[(int64_t)(r0 + r) * npb + kb2 * kNB + c];
-          TB[r * kLd + c] = W[(int64_t)(kb2 * kNB + r) * npb + jb * kNB + c];
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int k = 0; k < kNB; ++k) {
-          const T ak = TA[i * kLd + k];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) o[u] = fma(ak, TB[k * kLd + j0 + u], o[u]);
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 8; ++u) TB[i * kLd + j0 + u] = o[u];
-      __syncthreads();
-      // W_IJ = -X Tacc (X upper triangular)
-#pragma unroll
-      for (int u = 0; u < 8; ++u) o[u] = T(0);
-      for (int k = i; k < kNB; ++k) {
-        const T xk = X[i * kLd + k];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) o[u] = fma(xk, TB[k * kLd + j0 + u], o[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) W[(int64_t)(r0 + i) * npb + jb * kNB + j0 + u] = -o[u];
+    // blocks (I, K < I) of W and (K < I, I) of W^T are zero
+    for (int64_t e = tid; e < (int64_t)I * kNB * kNB; e += blockDim.x) {
+      const int64_t r = e / (I * kNB), c = e % (I * kNB);
+      W[(int64_t)(I * kNB + r) * npb + c] = T(0);
+      WT[c * npb + I * kNB + r] = T(0);
     }
+    return;
+  }
+  // Tacc = sum_K R_IK W_KJ: As[k][i] = R_IK[i][k] (transposed stage), Bs[k][j] = W_KJ[k][j]
+  T acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+  for (int K = I + 1; K <= J; ++K) {
+    stage64<C, T>(R + (int64_t)(I * kNB) * npb + K * kNB, npb, S, true);
+    stage64<T, T>(W + (int64_t)(K * kNB) * npb + J * kNB, npb, X, false);
+    __syncthreads();
+    tile_atb<T>(S, X, acc);
     __syncthreads();
   }
+  const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Tm[(4 * ty + p) * kLd + 4 * tx + q] = acc[p][q];
+  // W_IJ = -W_II Tacc: As[k][i] = W_II[i][k]
+  stage64<T, T>(W + (int64_t)(I * kNB) * npb + I * kNB, npb, S, true);
   __syncthreads();
-  for (int64_t e = tid; e < (int64_t)npb * npb; e += kCT) {
-    const int r = (int)(e / npb), c = (int)(e % npb);
-    WT[(int64_t)c * npb + r] = W[e];
-  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+  tile_atb<T>(S, Tm, acc);
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t r = I * kNB + 4 * ty + p, c = J * kNB + 4 * tx + q;
+      W[r * npb + c] = -acc[p][q];
+      WT[c * npb + r] = -acc[p][q];
+    }
 }
 
 // =========================================================================================
@@ -1551,23 +1505,41 @@ void launch_gram(const BArrays& a, const GTile* gtiles, int ngt, const GTile* gr
 
 template <typename C>
 void launch_chol(const BArrays& a, const int* list, int cnt, const double* shift, int* info,
-                 cudaStream_t s) {
+                 const CTask* tasks, const int* off, int steps, cudaStream_t s) {
   if (cnt <= 0) return;
-  constexpr size_t sm = sizeof(C) * 4 * kNB * kLd;
-  static const bool once = [] { set_smem(chol_kernel<C>, sm); return true; }();
+  constexpr size_t sm_diag = sizeof(C) * 3 * kNB * kLd;
+  constexpr size_t sm_tile = sizeof(C) * 2 * kNB * kLd;
+  static const bool once = [] {
+    set_smem(chol_diag_kernel<C>, sm_diag);
+    set_smem(chol_tile_kernel<C, true>, sm_tile);
+    set_smem(chol_tile_kernel<C, false>, sm_tile);
+    return true;
+  }();
   (void)once;
-  chol_kernel<C><<<cnt, kCT, sm, s>>>(a, list, shift, info);
+  chol_init_kernel<C><<<dim3(cnt, 8), 256, 0, s>>>(a, list, shift, info);
+  count_launch();
+  // off[3 s + 0 .. 2]: starts of the diagonal, panel and trailing lists of step s; off[3 steps]
+  // the end of the last list
+  for (int st = 0; st < steps; ++st) {
+    const int d0 = off[3 * st], p0 = off[3 * st + 1], u0 = off[3 * st + 2], e = off[3 * st + 3];
+    if (p0 > d0) { chol_diag_kernel<C><<<p0 - d0, 256, sm_diag, s>>>(a, tasks + d0, info); count_launch(); }
+    if (u0 > p0) { chol_tile_kernel<C, true><<<u0 - p0, 256, sm_tile, s>>>(a, tasks + p0, info); count_launch(); }
+    if (e > u0) { chol_tile_kernel<C, false><<<e - u0, 256, sm_tile, s>>>(a, tasks + u0, info); count_launch(); }
+  }
+  chol_final_kernel<C><<<dim3(cnt, 8), 256, 0, s>>>(a, list, info);
   count_launch();
 }
 
 template <typename C, typename T>
-void launch_trtri(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
-  if (cnt <= 0) return;
-  constexpr size_t sm = sizeof(T) * 4 * kNB * kLd;
-  static const bool once = [] { set_smem(trtri_kernel<C, T>, sm); return true; }();
+void launch_trtri(const BArrays& a, const CTask* tasks, const int* off, int levels,
+                  cudaStream_t s) {
+  constexpr size_t sm = sizeof(T) * 3 * kNB * kLd;
+  static const bool once = [] { set_smem(trtri_tile_kernel<C, T>, sm); return true; }();
   (void)once;
-  trtri_kernel<C, T><<<cnt, kCT, sm, s>>>(a, list);
-  count_launch();
+  for (int l = 0; l < levels; ++l) {
+    const int n = off[l + 1] - off[l];
+    if (n > 0) { trtri_tile_kernel<C, T><<<n, 256, sm, s>>>(a, tasks + off[l]); count_launch(); }
+  }
 }
 
 template <typename T>
@@ -1646,12 +1618,14 @@ template void launch_gram<float>(const BArrays&, const GTile*, int, const GTile*
                                  cudaStream_t);
 template void launch_gram<double>(const BArrays&, const GTile*, int, const GTile*, int, void*,
                                   cudaStream_t);
-template void launch_chol<float>(const BArrays&, const int*, int, const double*, int*, cudaStream_t);
-template void launch_chol<double>(const BArrays&, const int*, int, const double*, int*, cudaStream_t);
-template void launch_trtri<float, float>(const BArrays&, const int*, int, cudaStream_t);
-template void launch_trtri<double, float>(const BArrays&, const int*, int, cudaStream_t);
-template void launch_trtri<double, double>(const BArrays&, const int*, int, cudaStream_t);
-template void launch_trtri<float, double>(const BArrays&, const int*, int, cudaStream_t);
+template void launch_chol<float>(const BArrays&, const int*, int, const double*, int*,
+                                 const CTask*, const int*, int, cudaStream_t);
+template void launch_chol<double>(const BArrays&, const int*, int, const double*, int*,
+                                  const CTask*, const int*, int, cudaStream_t);
+template void launch_trtri<float, float>(const BArrays&, const CTask*, const int*, int, cudaStream_t);
+template void launch_trtri<double, float>(const BArrays&, const CTask*, const int*, int, cudaStream_t);
+template void launch_trtri<double, double>(const BArrays&, const CTask*, const int*, int, cudaStream_t);
+template void launch_trtri<float, double>(const BArrays&, const CTask*, const int*, int, cudaStream_t);
 #define TLS_BI(T)                                                                                 \
   template void launch_solve_init<T>(const BArrays&, const int*, int, cudaStream_t);              \
   template void launch_resid_post<T>(const BArrays&, const int*, const int*, int, int,             \

@@ -38,6 +38,8 @@ struct tls_batch {
   size_t cap_gram = 0;
   void* gwork = nullptr;            // Gram partial tiles of row-split tiles
   size_t cap_gwork = 0;
+  CTask* dtask = nullptr;           // Cholesky / inverse task lists
+  size_t cap_task = 0;
   int* dlist = nullptr;             // problem list of the current launch sequence
   int* dact_probs = nullptr;        // its active problems (compacted)
   int* dact_tiles = nullptr;        // their row tiles (compacted)
@@ -239,6 +241,64 @@ tls_status upload_list(tls_batch* bt, const std::vector<int>& L) {
   return TLS_OK;
 }
 
+tls_status upload_tasks(tls_batch* bt, const std::vector<CTask>& tk) {
+  if (!ensure_cap(bt, reinterpret_cast<void**>(&bt->dtask), &bt->cap_task,
+                  sizeof(CTask) * std::max<size_t>(tk.size(), 1))) {
+    set_err(bt, "device allocation failed (factor task lists)");
+    return TLS_ERR_OOM;
+  }
+  if (!tk.empty())
+    BT_CK(cudaMemcpyAsync(bt->dtask, tk.data(), sizeof(CTask) * tk.size(), cudaMemcpyHostToDevice,
+                          bt->stream));
+  return TLS_OK;
+}
+
+// Task lists of the blocked Cholesky of the problems in L: for every block step s the diagonal
+// blocks, then the panel blocks, then the trailing blocks. off: 3 entries per step + the end.
+int chol_tasks(const tls_batch* bt, const std::vector<int>& L, std::vector<CTask>& tk,
+               std::vector<int>& off) {
+  int steps = 0;
+  for (int i : L) steps = std::max(steps, (int)(bt->hp[(size_t)i].npb / kNB));
+  tk.clear();
+  off.clear();
+  for (int st = 0; st < steps; ++st) {
+    off.push_back((int)tk.size());
+    for (int i : L)
+      if (st < (int)(bt->hp[(size_t)i].npb / kNB)) tk.push_back(CTask{i, st, st, st});
+    off.push_back((int)tk.size());
+    for (int i : L) {
+      const int nb = (int)(bt->hp[(size_t)i].npb / kNB);
+      for (int bj = st + 1; bj < nb; ++bj) tk.push_back(CTask{i, st, st, bj});
+    }
+    off.push_back((int)tk.size());
+    for (int i : L) {
+      const int nb = (int)(bt->hp[(size_t)i].npb / kNB);
+      for (int bi = st + 1; bi < nb; ++bi)
+        for (int bj = bi; bj < nb; ++bj) tk.push_back(CTask{i, st, bi, bj});
+    }
+  }
+  off.push_back((int)tk.size());
+  return steps;
+}
+
+// Task lists of W = R^{-1} by block diagonals: level d holds the blocks (I, I + d).
+int trtri_tasks(const tls_batch* bt, const std::vector<int>& L, std::vector<CTask>& tk,
+                std::vector<int>& off) {
+  int levels = 0;
+  for (int i : L) levels = std::max(levels, (int)(bt->hp[(size_t)i].npb / kNB));
+  tk.clear();
+  off.clear();
+  for (int d = 0; d < levels; ++d) {
+    off.push_back((int)tk.size());
+    for (int i : L) {
+      const int nb = (int)(bt->hp[(size_t)i].npb / kNB);
+      for (int I = 0; I + d < nb; ++I) tk.push_back(CTask{i, d, I, I + d});
+    }
+  }
+  off.push_back((int)tk.size());
+  return levels;
+}
+
 // Gram + shift ladder + triangular inverse for the problems in L at factor precision p;
 // problems whose every shift breaks down move on to the next precision.
 template <typename T>
@@ -307,12 +367,19 @@ tls_status factor_list(tls_batch* bt, std::vector<int> L, Prec p) {
                             cudaMemcpyHostToDevice, st));
       tls_status s = upload_list(bt, pending);
       if (s != TLS_OK) return s;
+      std::vector<CTask> tk;
+      std::vector<int> off;
+      const int steps = chol_tasks(bt, pending, tk, off);
+      s = upload_tasks(bt, tk);
+      if (s != TLS_OK) return s;
       {
         BProfScope pr(bt, TLS_PROF_CHOL);
         if (c64)
-          launch_chol<double>(bt->a, bt->dlist, (int)pending.size(), bt->dshift, bt->dinfo, st);
+          launch_chol<double>(bt->a, bt->dlist, (int)pending.size(), bt->dshift, bt->dinfo,
+                              bt->dtask, off.data(), steps, st);
         else
-          launch_chol<float>(bt->a, bt->dlist, (int)pending.size(), bt->dshift, bt->dinfo, st);
+          launch_chol<float>(bt->a, bt->dlist, (int)pending.size(), bt->dshift, bt->dinfo,
+                             bt->dtask, off.data(), steps, st);
       }
       BT_CK_LAUNCH("batched Cholesky");
       BT_CK(cudaMemcpyAsync(bt->hinfo.data(), bt->dinfo, sizeof(int) * bt->count,
@@ -332,11 +399,14 @@ tls_status factor_list(tls_batch* bt, std::vector<int> L, Prec p) {
       pending.swap(failed);
     }
     if (!ok.empty()) {
-      tls_status s = upload_list(bt, ok);
+      std::vector<CTask> tk;
+      std::vector<int> off;
+      const int levels = trtri_tasks(bt, ok, tk, off);
+      tls_status s = upload_tasks(bt, tk);
       if (s != TLS_OK) return s;
       BProfScope pr(bt, TLS_PROF_TRTRI);
-      if (c64) launch_trtri<double, T>(bt->a, bt->dlist, (int)ok.size(), st);
-      else launch_trtri<float, T>(bt->a, bt->dlist, (int)ok.size(), st);
+      if (c64) launch_trtri<double, T>(bt->a, bt->dtask, off.data(), levels, st);
+      else launch_trtri<float, T>(bt->a, bt->dtask, off.data(), levels, st);
       BT_CK_LAUNCH("batched triangular inverse");
       for (int i : ok) bt->uf_used[(size_t)i] = (tls_prec)(int)p;
     }

@@ -52,6 +52,11 @@ struct BTile { int prob, row0, rows, pad_; };
 // (r1 - r0) - 1.
 struct GTile { int prob, bi, bj, r0, r1, slot, pad0_, pad1_; };
 
+// One CTA of the blocked Cholesky / inverse task lists: problem `prob`, block step `s`, block
+// (bi, bj). Cholesky step s: the diagonal block (s, s), the panel blocks (s, bj) and the
+// trailing blocks (bi, bj), s < bi <= bj, in three launches. Inverse: level bj - bi.
+struct CTask { int prob, s, bi, bj; };
+
 // Device state of one problem (host reads it back at the end of a solve).
 struct BState {
   // factor
@@ -117,11 +122,15 @@ void launch_pass_pcg(const BArrays& a, const int* tlist, const int* ntile, int g
 template <typename C>
 void launch_gram(const BArrays& a, const GTile* gtiles, int ngt, const GTile* groups, int ngr,
                  void* work, cudaStream_t s);
+// tasks: device task list; off (host): starts of the diagonal, panel and trailing lists of each
+// step (3 steps + 1 entries)
 template <typename C>
 void launch_chol(const BArrays& a, const int* list, int cnt, const double* shift, int* info,
-                 cudaStream_t s);
+                 const CTask* tasks, const int* off, int steps, cudaStream_t s);
+// tasks: device task list; off (host): starts of the levels (levels + 1 entries)
 template <typename C, typename T>
-void launch_trtri(const BArrays& a, const int* list, int cnt, cudaStream_t s);
+void launch_trtri(const BArrays& a, const CTask* tasks, const int* off, int levels,
+                  cudaStream_t s);
 template <typename T>
 void launch_solve_init(const BArrays& a, const int* list, int cnt, cudaStream_t s);
 template <typename T>
