@@ -233,19 +233,11 @@ def run_ours(args, ws, rank, local):
     ctx = tls.tls_create_dense(p.A, p.b, stream=stream.cuda_stream)
     opt = tls.tls_default_options(u="fp32")
 
-    # CPU oracle on rank 0 (accuracy reference and CPU baseline)
+    # the CPU oracle (accuracy reference and CPU baseline) runs after every GPU measurement,
+    # so that its host threads cannot slow the launches being timed; results are kept and
+    # checked against it at the end
     cpu = None
     ref = None
-    if not args.no_cpu:
-        t0 = time.perf_counter()
-        xo, so, io = _oracle_solve(p)
-        t_or = time.perf_counter() - t0
-        ref = (xo, so)
-        if rank == 0:
-            cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(),
-                   "kind": "oracle",
-                   "sample": f"1 full FP64 solve of the {M_ROWS}x{N_COLS} problem "
-                             f"({t_or:.2f} s, numpy/OpenBLAS threads)"}
 
     def accurate(x, s):
         if ref is None:
@@ -264,7 +256,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     l0 = tls.tls_kernel_launches()
-    ok = 0
+    results = []
     infos = []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -272,7 +264,7 @@ def run_ours(args, ws, rank, local):
         ev0.record(stream)
         for _ in range(args.steps):
             x, s, info = step()
-            ok += int(accurate(x, s))
+            results.append((x, s))
             infos.append(info)
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -291,10 +283,6 @@ def run_ours(args, ws, rank, local):
     prof = tls.tls_profile_get(ctx)
     tls.tls_profile_enable(ctx, False)
     last_x, last_s = x, s
-    err = None
-    if ref is not None:
-        err = {"sigma_rel": abs(last_s - ref[1]) / ref[1],
-               "x_rel": float(np.linalg.norm(last_x - ref[0]) / np.linalg.norm(ref[0]))}
 
     # end to end through the public API from pinned host memory
     e2e = None
@@ -305,18 +293,18 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        okc = 0
+        e2e_res = []
         e0.record(stream)
         for _ in range(ne):
             c2 = tls.tls_create_dense(A_pin, b_pin, stream=stream.cuda_stream)
             tls.tls_factor(c2, "fp16", opt)
             x2, s2, _ = tls.tls_solve(c2, tol=SOLVE_TOL, max_rqi=MAX_RQI)
             tls.tls_destroy(c2)
-            okc += int(accurate(x2, s2))
+            e2e_res.append((x2, s2))
         e1.record(stream)
         torch.cuda.synchronize()
         ems = _barrier_max(e0.elapsed_time(e1), ws)
-        e2e = {"value": ws * okc / (ems * 1e-3), "unit": "solves/s",
+        e2e = {"value": None, "unit": "solves/s",
                "h2d_bytes_per_step": int(p.A.nbytes + p.b.nbytes),
                "d2h_bytes_per_step": int(8 * N_COLS + 8), "steps": ne,
                "ms_per_step": ems / ne}
@@ -331,22 +319,45 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         q0 = torch.cuda.Event(enable_timing=True)
         q1 = torch.cuda.Event(enable_timing=True)
-        okp = 0
+        plain_res = []
         q0.record(stream)
         for _ in range(np_steps):
             tls.tls_factor(ctx, "fp64", opt64)
             xp, sp, ip = tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
-            okp += int(accurate(xp, sp))
+            plain_res.append((xp, sp))
         q1.record(stream)
         torch.cuda.synchronize()
         pms = _barrier_max(q0.elapsed_time(q1), ws)
-        plain = {"value": ws * okp / (pms * 1e-3), "unit": "solves/s",
+        plain = {"value": None, "unit": "solves/s",
                  "ms_per_step": pms / np_steps, "steps": np_steps,
                  "rqi_steps": ip["rqi_steps"], "cg_iters": ip["cg_iters"]}
+    tls.tls_destroy(ctx)
+
+    # CPU oracle leg, then the accuracy of every result against it
+    if not args.no_cpu:
+        t0 = time.perf_counter()
+        xo, so, io = _oracle_solve(p)
+        t_or = time.perf_counter() - t0
+        ref = (xo, so)
+        if rank == 0:
+            cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": f"1 full FP64 solve of the {M_ROWS}x{N_COLS} problem "
+                             f"({t_or:.2f} s, numpy/OpenBLAS threads)"}
+    ok = sum(int(accurate(x_, s_)) for x_, s_ in results)
+    err = None
+    if ref is not None:
+        err = {"sigma_rel": abs(last_s - ref[1]) / ref[1],
+               "x_rel": float(np.linalg.norm(last_x - ref[0]) / np.linalg.norm(ref[0]))}
+    if e2e is not None:
+        okc = sum(int(accurate(x_, s_)) for x_, s_ in e2e_res)
+        e2e["value"] = ws * okc / (e2e["ms_per_step"] * e2e["steps"] * 1e-3)
+    if plain is not None:
+        okp = sum(int(accurate(x_, s_)) for x_, s_ in plain_res)
+        plain["value"] = ws * okp / (plain["ms_per_step"] * plain["steps"] * 1e-3)
         if ref is not None:
             plain["sigma_rel"] = abs(sp - ref[1]) / ref[1]
             plain["x_rel"] = float(np.linalg.norm(xp - ref[0]) / np.linalg.norm(ref[0]))
-    tls.tls_destroy(ctx)
 
     if rank != 0:
         return
@@ -386,9 +397,19 @@ def run_ours(args, ws, rank, local):
 # ------------------------------------------------------------------------------------------
 # C1: the small all-FP64 problem (400 x 40, tol 1e-12, max 10 RQI steps): latency bound
 # ------------------------------------------------------------------------------------------
+def _c1_oracle(seed: int, reps: int):
+    """The 400 x 40 oracle solve, timed over `reps` repetitions (runs in a spawned process)."""
+    import oracle.rqi_pcgtls as O
+    from paper_2305_19028_gb300 import synth
+    p = synth.dense_problem(400, 40, d_lo=1e-2, noise=1e-6, seed=seed)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=1e-12, max_rqi=10)
+    return xo, so, (time.perf_counter() - t0) / reps
+
+
 def run_c1(args, ws, rank, local):
     import torch
-    import oracle.rqi_pcgtls as O
     from paper_2305_19028_gb300 import synth, tls
 
     torch.cuda.set_device(local)
@@ -398,14 +419,26 @@ def run_c1(args, ws, rank, local):
     tls.load()
     p = synth.dense_problem(400, 40, d_lo=1e-2, noise=1e-6, seed=rank)
     cpu = None
-    t0 = time.perf_counter()
     reps = 20
-    for _ in range(reps):
-        xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=1e-12, max_rqi=10)
-    t_or = (time.perf_counter() - t0) / reps
+    # the oracle in one spawned single-threaded process (its BLAS threads end with it)
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                             "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes=1) as pool:
+            xo, so, t_or = pool.apply(_c1_oracle, (rank, reps))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     if rank == 0:
         cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": f"{reps} FP64 solves of the 400x40 problem, one thread of numpy"}
+               "sample": f"{reps} FP64 solves of the 400x40 problem in one single-threaded "
+                         f"process"}
     stream = torch.cuda.current_stream()
     ctx = tls.tls_create_dense(p.A, p.b, stream=stream.cuda_stream)
     opt = tls.tls_default_options(u="fp64")
@@ -532,17 +565,7 @@ def run_sparse(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     ctx = tls.tls_create_csr(p.m, p.n, p.row_ptr, p.col_idx, p.val, p.b, stream=stream.cuda_stream)
     opt = tls.tls_default_options(u="fp32")
-    ref, cpu = None, None
-    if not args.no_cpu:
-        t0 = time.perf_counter()
-        xo, so, _ = _csr_oracle(p)
-        t_or = time.perf_counter() - t0
-        ref = (xo, so)
-        if rank == 0:
-            cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(),
-                   "kind": "oracle",
-                   "sample": f"1 full FP64 solve of the {CSR_M}x{CSR_N} CSR problem "
-                             f"({t_or:.2f} s: sparse A^T A, dense Cholesky R, scipy products)"}
+    ref, cpu = None, None   # the CPU oracle runs after the GPU measurements (see run_ours)
 
     def accurate(x, s):
         if ref is None:
@@ -560,14 +583,14 @@ def run_sparse(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     l0 = tls.tls_kernel_launches()
-    ok = 0
+    results = []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             x, s, info = step()
-            ok += int(accurate(x, s))
+            results.append((x, s))
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = tls.tls_kernel_launches() - l0
@@ -586,17 +609,17 @@ def run_sparse(args, ws, rank, local):
         tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
         q0 = torch.cuda.Event(enable_timing=True)
         q1 = torch.cuda.Event(enable_timing=True)
-        okp, nps = 0, 2
+        plain_res, nps = [], 2
         q0.record(stream)
         for _ in range(nps):
             tls.tls_factor(ctx, "fp64", opt64)
             xp, sp_, _ = tls.tls_solve(ctx, tol=SOLVE_TOL, max_rqi=MAX_RQI)
-            okp += int(accurate(xp, sp_))
+            plain_res.append((xp, sp_))
         q1.record(stream)
         torch.cuda.synchronize()
         pms = _barrier_max(q0.elapsed_time(q1), ws)
-        plain = {"value": ws * okp / (pms * 1e-3), "unit": "solves/s", "ms_per_step": pms / nps,
-                 "steps": nps, "accurate": okp}
+        plain = {"value": None, "unit": "solves/s", "ms_per_step": pms / nps,
+                 "steps": nps, "accurate": None}
     e2e = None
     if not args.no_e2e:
         pins = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -605,21 +628,39 @@ def run_sparse(args, ws, rank, local):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        okc = 0
+        e2e_res = []
         e0.record(stream)
         for _ in range(ne):
             c2 = tls.tls_create_csr(p.m, p.n, *pins, stream=stream.cuda_stream)
             tls.tls_factor(c2, "bf16", opt)
             x2, s2, _ = tls.tls_solve(c2, tol=SOLVE_TOL, max_rqi=MAX_RQI)
             tls.tls_destroy(c2)
-            okc += int(accurate(x2, s2))
+            e2e_res.append((x2, s2))
         e1.record(stream)
         torch.cuda.synchronize()
         ems = _barrier_max(e0.elapsed_time(e1), ws)
-        e2e = {"value": ws * okc / (ems * 1e-3), "unit": "solves/s",
+        e2e = {"value": None, "unit": "solves/s",
                "h2d_bytes_per_step": int(sum(a.nbytes for a in pins)),
                "d2h_bytes_per_step": int(8 * CSR_N + 8), "steps": ne, "ms_per_step": ems / ne}
     tls.tls_destroy(ctx)
+    if not args.no_cpu:
+        t0 = time.perf_counter()
+        xo, so, _ = _csr_oracle(p)
+        t_or = time.perf_counter() - t0
+        ref = (xo, so)
+        if rank == 0:
+            cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": f"1 full FP64 solve of the {CSR_M}x{CSR_N} CSR problem "
+                             f"({t_or:.2f} s: sparse A^T A, dense Cholesky R, scipy products)"}
+    ok = sum(int(accurate(x_, s_)) for x_, s_ in results)
+    if plain is not None:
+        okp = sum(int(accurate(x_, s_)) for x_, s_ in plain_res)
+        plain["value"] = ws * okp / (plain["ms_per_step"] * plain["steps"] * 1e-3)
+        plain["accurate"] = okp
+    if e2e is not None:
+        okc = sum(int(accurate(x_, s_)) for x_, s_ in e2e_res)
+        e2e["value"] = ws * okc / (e2e["ms_per_step"] * e2e["steps"] * 1e-3)
     if rank != 0:
         return
     peaks = _peaks()

@@ -39,6 +39,33 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Warp sums of NV values at once (NV a power of two <= 32) by recursive halving: at each of the
+// first log2(NV) butterfly stages a lane keeps half of its values and adds the partner's copy
+// of them, so the stages cost NV/2, NV/4, ... adds instead of NV each; plain butterfly stages
+// finish. Lane l returns the warp total of value l >> (5 - log2 NV).
+template <typename T, int NV>
+__device__ __forceinline__ T warp_reduce_scatter(const T (&v)[NV]) {
+  static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV: a power of two <= 32");
+  const int lane = threadIdx.x & 31;
+  T x[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) x[i] = v[i];
+  int o = 16;
+#pragma unroll
+  for (int k = NV; k > 1; k >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < k / 2; ++i) {
+      const T keep = up ? x[k / 2 + i] : x[i];
+      const T give = up ? x[i] : x[k / 2 + i];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+    }
+  }
+  T r = x[0];
+  for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
 // Block-wide sum of up to 4 doubles per thread into smem result (all threads get it).
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* kWarps*K */) {
@@ -62,6 +89,7 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* kWarps*K
 // Last-CTA detection after every CTA has published its partials (threadfence reduction).
 __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __shared__ bool last;
+  __threadfence();   // every thread's partials are visible device-wide before the arrival
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -71,6 +99,33 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __syncthreads();
   if (last) __threadfence();
   return last;
+}
+
+// Sum of K interleaved partial vectors written by other CTAs of the same launch into out
+// (shared memory, written by thread 0; the caller synchronises before reading it).
+template <int K>
+__device__ __forceinline__ void reduce_partials_cg(const double* part, int P, double* out) {
+  __shared__ double sh[kWarps * K];
+  double v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __ldcg(part + (int64_t)p * K + k);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w * K + k];
+      out[k] = t;
+    }
 }
 
 // Sum of K interleaved partial vectors part[p*K + k] (p < P) by the whole block; the result
@@ -286,6 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) apass_pipe_kernel(
     }
   };
   auto process = [&](const V (&a)[RW][VPT], int64_t i0) {
+    T tv[NV];
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
@@ -295,9 +351,14 @@ __global__ void __launch_bounds__(kThreads, 1) apass_pipe_kernel(
         for (int k = 0; k < VPT; ++k)
 #pragma unroll
           for (int c = 0; c < VW; ++c) t = fma(get(a[rt][k], c), vv[r][k * VW + c], t);
-        t = warp_sum(t);
-        if (lane == 0) red[warp][r * RW + rt] = t;
+        tv[r * RW + rt] = t;
       }
+    {
+      // one reduce-scatter for the NV row values of the tile (value index lane >> kSh)
+      constexpr int kSh = (NV >= 32) ? 0 : (NV >= 16 ? 1 : (NV >= 8 ? 2 : (NV >= 4 ? 3 : (NV >= 2 ? 4 : 5))));
+      const T t = warp_reduce_scatter<T, NV>(tv);
+      if ((lane & ((1 << kSh) - 1)) == 0) red[warp][lane >> kSh] = t;
+    }
     __syncthreads();
     if (warp == 0 && lane < NV) {
       const int rt = lane % RW;
@@ -653,49 +714,83 @@ __global__ void pcg_update_R_kernel(const T* __restrict__ q, T* __restrict__ w, 
 }
 
 // ---------------------------------------------------------------------------------------
-// v = W^T y (row products with WT = W^T, lower triangular), then the s recurrence:
-//   init: s = v, eta_0 = ||s||^2                     (s_0 = R^{-T} f)
-//   step: s -= alpha v (A-explicit) or s -= alpha (p - sigma^2 v) (as printed)
-// last CTA: eta_{j+1}, beta_j = eta_{j+1}/eta_j, termination flags.
+// Pieces of the two triangular products of a PCGTLS step, shared by the separate kernels and
+// the fused step kernel below. `cg` selects L2-only loads (ld.global.cg) for data that other
+// CTAs of the same launch wrote (the fused kernel); the separate kernels read through L1.
 // ---------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) gemv_wt_kernel(
-    const T* __restrict__ WT, int64_t npad, const T* __restrict__ y, T* __restrict__ s,
-    const T* __restrict__ p, double* __restrict__ part, PcgScalars* sc, int init, int modeA,
-    int nr) {
+template <typename T, bool CG>
+__device__ __forceinline__ typename VecOf<T>::type ldv(const T* p) {
+  using V = typename VecOf<T>::type;
+  if constexpr (CG) return __ldcg(reinterpret_cast<const V*>(p));
+  else return *reinterpret_cast<const V*>(p);
+}
+
+// stage y (nr x npad) into shared memory with vector loads, several in flight per thread
+template <typename T, bool CG>
+__device__ __forceinline__ void stage_vec(const T* __restrict__ y, T* ys, int nr, int64_t npad) {
   using V = typename VecOf<T>::type;
   constexpr int VW = VecOf<T>::W;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ys = reinterpret_cast<T*>(smem_raw);
-  __shared__ double red[kWarps * 2];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  bool active[2];
-  T alpha[2];
-  for (int r = 0; r < 2; ++r) {
-    active[r] = r < nr && (init || (!sc->done[r] && sc->delta[r] > 0.0));
-    alpha[r] = init ? T(0) : (T)sc->alpha[r];
+  const int tid = threadIdx.x;
+  const int64_t nv = nr * npad / VW;
+  for (int64_t e0 = tid; e0 < nv; e0 += 4 * kThreads) {
+    V t[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e0 + (int64_t)u * kThreads;
+      t[u] = (e < nv) ? ldv<T, CG>(y + e * VW) : zero_vec(T(0));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e0 + (int64_t)u * kThreads;
+      if (e < nv) reinterpret_cast<V*>(ys)[e] = t[u];
+    }
   }
-  const T sigma2 = (T)sc->sigma2;
-  {
-    // stage y (nr x npad) with vector loads, several in flight per thread
-    const int64_t nv = nr * npad / VW;
-    for (int64_t e0 = tid; e0 < nv; e0 += 4 * kThreads) {
-      V t[4];
+}
+
+// stage p_j = s + beta_{j-1} p_{j-1} (nr x npad) into shared memory
+template <typename T, bool CG>
+__device__ __forceinline__ void stage_p(const T* __restrict__ s, const T* __restrict__ p_prev,
+                                        T* ps, int nr, int64_t npad, T beta0, T beta1) {
+  using V = typename VecOf<T>::type;
+  constexpr int VW = VecOf<T>::W;
+  const int tid = threadIdx.x;
+  const int64_t nv = nr * npad / VW;
+  for (int64_t e0 = tid; e0 < nv; e0 += 4 * kThreads) {
+    V sv[4], pv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t e = e0 + (int64_t)u * kThreads;
-        t[u] = (e < nv) ? reinterpret_cast<const V*>(y)[e] : zero_vec(T(0));
-      }
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e0 + (int64_t)u * kThreads;
+      sv[u] = (e < nv) ? ldv<T, CG>(s + e * VW) : zero_vec(T(0));
+      pv[u] = (e < nv) ? ldv<T, CG>(p_prev + e * VW) : zero_vec(T(0));
+    }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t e = e0 + (int64_t)u * kThreads;
-        if (e < nv) reinterpret_cast<V*>(ys)[e] = t[u];
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e0 + (int64_t)u * kThreads;
+      if (e < nv) {
+        const T bt = (e * VW < npad) ? beta0 : beta1;
+        V o;
+        if constexpr (VW == 4) {
+          o = make_float4(sv[u].x + bt * pv[u].x, sv[u].y + bt * pv[u].y,
+                          sv[u].z + bt * pv[u].z, sv[u].w + bt * pv[u].w);
+        } else {
+          o = make_double2(sv[u].x + bt * pv[u].x, sv[u].y + bt * pv[u].y);
+        }
+        reinterpret_cast<V*>(ps)[e] = o;
       }
     }
   }
-  __syncthreads();
-  T ss[2] = {T(0), T(0)};
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, GW = (int64_t)gridDim.x * kWarps;
+}
+
+// Rows gw, gw + GW, ... of v = W^T y (WT = W^T lower triangular, entries 0..j of row j) and the
+// s recurrence of those rows; ss accumulates ||s||^2 over the rows of the calling lane 0.
+template <typename T>
+__device__ __forceinline__ void wt_rows(const T* __restrict__ WT, int64_t npad, const T* ys,
+                                        T* __restrict__ s, const T* __restrict__ p, bool act0,
+                                        bool act1, T alpha0, T alpha1, T sigma2, bool init,
+                                        bool modeA, int nr, int64_t gw, int64_t GW, T (&ss)[2]) {
+  using V = typename VecOf<T>::type;
+  constexpr int VW = VecOf<T>::W;
+  const int lane = threadIdx.x & 31;
   for (int64_t j = gw; j < npad; j += GW) {
     const T* row = WT + j * npad;
     const int64_t lim = ((j + VW) / VW) * VW;    // entries 0..j, rounded up (zeros beyond j)
@@ -726,110 +821,35 @@ __global__ void __launch_bounds__(kThreads) gemv_wt_kernel(
     a0 = warp_sum(a0);
     if (nr > 1) a1 = warp_sum(a1);
     if (lane == 0) {
-      T vr[2] = {a0, a1};
-      for (int r = 0; r < nr; ++r) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (r >= nr) break;
+        const T vr = r ? a1 : a0;
+        const bool act = r ? act1 : act0;
+        const T al = r ? alpha1 : alpha0;
         T* sp = s + r * npad + j;
         T sv = *sp;
-        if (init) sv = vr[r];
-        else if (active[r]) {
-          if (modeA) sv = sv - alpha[r] * vr[r];
-          else sv = sv - alpha[r] * (p[r * npad + j] - sigma2 * vr[r]);
+        if (init) sv = vr;
+        else if (act) {
+          if (modeA) sv = sv - al * vr;
+          else sv = sv - al * (p[r * npad + j] - sigma2 * vr);
         }
-        if (init || active[r]) *sp = sv;
+        if (init || act) *sp = sv;
         ss[r] = fma(sv, sv, ss[r]);
       }
     }
   }
-  // CTA partials of ||s||^2
-  ss[0] = warp_sum(ss[0]);
-  ss[1] = warp_sum(ss[1]);
-  if (lane == 0) { red[warp * 2] = (double)ss[0]; red[warp * 2 + 1] = (double)ss[1]; }
-  __syncthreads();
-  if (tid < 2) {
-    double t = 0.0;
-    for (int w2 = 0; w2 < kWarps; ++w2) t += red[w2 * 2 + tid];
-    part[(int64_t)blockIdx.x * 2 + tid] = t;
-  }
-  if (arrive_last(&sc->counter[0])) {
-    __shared__ double eta_sum[2];
-    reduce_partials<2>(part, (int)gridDim.x, eta_sum);
-    if (tid < nr) {
-      const int r = tid;
-      const double eta_new = eta_sum[r];
-      if (init) {
-        sc->eta[r] = eta_new;
-        sc->eta0[r] = eta_new;
-        sc->beta[r] = 0.0;
-        sc->done[r] = (eta_new == 0.0) ? 1 : 0;
-        sc->iters[r] = 0;
-      } else if (!sc->done[r]) {
-        if (!(sc->delta[r] > 0.0)) {
-          sc->done[r] = 1;
-          sc->not_spd[r] = (sc->delta[r] < 0.0) ? 1 : 0;
-        } else {
-          sc->beta[r] = eta_new / sc->eta[r];
-          sc->eta[r] = eta_new;
-          sc->iters[r] += 1;
-          if (eta_new == 0.0 || (sc->cg_tol2 > 0.0 && eta_new <= sc->cg_tol2 * sc->eta0[r]))
-            sc->done[r] = 1;
-        }
-      }
-    }
-    if (tid == 0) sc->counter[0] = 0u;
-  }
 }
 
-// ---------------------------------------------------------------------------------------
-// p_j = s_j + beta_{j-1} p_{j-1}; q_j = D^{-1} W p_j; partials of ||q||^2 and ||p||^2.
-// ---------------------------------------------------------------------------------------
+// Rows gw, gw + GW, ... of q = D^{-1} W p (W upper triangular) from the staged p; acc4
+// accumulates ||q||^2 (two RHS) and ||p||^2 (two RHS) over the rows of the calling lane 0.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) gemv_w_kernel(
-    const T* __restrict__ W, int64_t npad, const T* __restrict__ s, const T* __restrict__ p_prev,
-    T* __restrict__ p_out, const T* __restrict__ dinv, T* __restrict__ q,
-    double* __restrict__ part, PcgScalars* sc, int nr) {
+__device__ __forceinline__ void w_rows(const T* __restrict__ W, int64_t npad, const T* ps,
+                                       const T* __restrict__ dinv, T* __restrict__ q, int nr,
+                                       int64_t gw, int64_t GW, T (&acc4)[4]) {
   using V = typename VecOf<T>::type;
   constexpr int VW = VecOf<T>::W;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ps = reinterpret_cast<T*>(smem_raw);
-  __shared__ double red[kWarps * 4];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T beta0 = (T)sc->beta[0], beta1 = (T)(nr > 1 ? sc->beta[1] : 0.0);
-  {
-    // stage p_j = s + beta p_prev (nr x npad) with vector loads, several in flight per thread
-    const int64_t nv = nr * npad / VW;
-    for (int64_t e0 = tid; e0 < nv; e0 += 4 * kThreads) {
-      V sv[4], pv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t e = e0 + (int64_t)u * kThreads;
-        sv[u] = (e < nv) ? reinterpret_cast<const V*>(s)[e] : zero_vec(T(0));
-        pv[u] = (e < nv) ? reinterpret_cast<const V*>(p_prev)[e] : zero_vec(T(0));
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t e = e0 + (int64_t)u * kThreads;
-        if (e < nv) {
-          const T bt = (e * VW < npad) ? beta0 : beta1;
-          V o;
-          if constexpr (VW == 4) {
-            o = make_float4(sv[u].x + bt * pv[u].x, sv[u].y + bt * pv[u].y,
-                            sv[u].z + bt * pv[u].z, sv[u].w + bt * pv[u].w);
-          } else {
-            o = make_double2(sv[u].x + bt * pv[u].x, sv[u].y + bt * pv[u].y);
-          }
-          reinterpret_cast<V*>(ps)[e] = o;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  {
-    const int64_t chunk = (nr * npad + gridDim.x - 1) / gridDim.x;
-    const int64_t e0 = (int64_t)blockIdx.x * chunk, e1 = min((int64_t)nr * npad, e0 + chunk);
-    for (int64_t e = e0 + tid; e < e1; e += kThreads) p_out[e] = ps[e];
-  }
-  T acc4[4] = {T(0), T(0), T(0), T(0)};   // qq0, qq1, pp0, pp1 (working type: no FP64 per row)
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, GW = (int64_t)gridDim.x * kWarps;
+  const int lane = threadIdx.x & 31;
   for (int64_t i = gw; i < npad; i += GW) {
     const T* row = W + i * npad;
     T a0 = T(0), a1 = T(0);
@@ -872,20 +892,312 @@ __global__ void __launch_bounds__(kThreads) gemv_w_kernel(
       }
     }
   }
+}
+
+// CTA partial sums (FP64) of K per-lane values into part[slot * K + k]
+template <typename T, int K>
+__device__ __forceinline__ void cta_partials(T (&v)[K], double* red /* kWarps * K */,
+                                             double* part, int64_t slot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) acc4[k] = warp_sum(acc4[k]);
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
   if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[warp * 4 + k] = (double)acc4[k];
+    for (int k = 0; k < K; ++k) red[warp * K + k] = (double)v[k];
   __syncthreads();
-  if (tid < 4) {
+  if (tid < K) {
     double t = 0.0;
-    for (int w2 = 0; w2 < kWarps; ++w2) t += red[w2 * 4 + tid];
-    part[(int64_t)blockIdx.x * 4 + tid] = t;
+    for (int w2 = 0; w2 < kWarps; ++w2) t += red[w2 * K + tid];
+    part[slot * K + tid] = t;
   }
+}
+
+// eta_{j+1}, beta_j and the termination flags of Alg. 3 from eta_new (one RHS r).
+__device__ __forceinline__ void eta_update(double eta_new, bool init, double& eta, double& eta0,
+                                           double& beta, int& done, int& iters, int& not_spd,
+                                           double delta, double cg_tol2) {
+  if (init) {
+    eta = eta_new;
+    eta0 = eta_new;
+    beta = 0.0;
+    done = (eta_new == 0.0) ? 1 : 0;
+    iters = 0;
+  } else if (!done) {
+    if (!(delta > 0.0)) {
+      done = 1;
+      not_spd = (delta < 0.0) ? 1 : 0;
+    } else {
+      beta = eta_new / eta;
+      eta = eta_new;
+      iters += 1;
+      if (eta_new == 0.0 || (cg_tol2 > 0.0 && eta_new <= cg_tol2 * eta0)) done = 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// v = W^T y (row products with WT = W^T, lower triangular), then the s recurrence:
+//   init: s = v, eta_0 = ||s||^2                     (s_0 = R^{-T} f)
+//   step: s -= alpha v (A-explicit) or s -= alpha (p - sigma^2 v) (as printed)
+// last CTA: eta_{j+1}, beta_j = eta_{j+1}/eta_j, termination flags.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gemv_wt_kernel(
+    const T* __restrict__ WT, int64_t npad, const T* __restrict__ y, T* __restrict__ s,
+    const T* __restrict__ p, double* __restrict__ part, PcgScalars* sc, int init, int modeA,
+    int nr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ys = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[kWarps * 2];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const bool act0 = 0 < nr && (init || (!sc->done[0] && sc->delta[0] > 0.0));
+  const bool act1 = 1 < nr && (init || (!sc->done[1] && sc->delta[1] > 0.0));
+  const T alpha0 = init ? T(0) : (T)sc->alpha[0];
+  const T alpha1 = init ? T(0) : (T)sc->alpha[1];
+  const T sigma2 = (T)sc->sigma2;
+  stage_vec<T, false>(y, ys, nr, npad);
+  __syncthreads();
+  T ss[2] = {T(0), T(0)};
+  wt_rows<T>(WT, npad, ys, s, p, act0, act1, alpha0, alpha1, sigma2, init != 0, modeA != 0, nr,
+             (int64_t)blockIdx.x * kWarps + warp, (int64_t)gridDim.x * kWarps, ss);
+  cta_partials<T, 2>(ss, red, part, blockIdx.x);
+  if (arrive_last(&sc->counter[0])) {
+    __shared__ double eta_sum[2];
+    reduce_partials<2>(part, (int)gridDim.x, eta_sum);
+    if (tid < nr) {
+      const int r = tid;
+      double eta = sc->eta[r], eta0 = sc->eta0[r], beta = sc->beta[r];
+      int done = sc->done[r], iters = sc->iters[r], nspd = sc->not_spd[r];
+      eta_update(eta_sum[r], init != 0, eta, eta0, beta, done, iters, nspd, sc->delta[r],
+                 sc->cg_tol2);
+      sc->eta[r] = eta;
+      sc->eta0[r] = eta0;
+      sc->beta[r] = beta;
+      sc->done[r] = done;
+      sc->iters[r] = iters;
+      sc->not_spd[r] = nspd;
+    }
+    if (tid == 0) sc->counter[0] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// p_j = s_j + beta_{j-1} p_{j-1}; q_j = D^{-1} W p_j; partials of ||q||^2 and ||p||^2.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gemv_w_kernel(
+    const T* __restrict__ W, int64_t npad, const T* __restrict__ s, const T* __restrict__ p_prev,
+    T* __restrict__ p_out, const T* __restrict__ dinv, T* __restrict__ q,
+    double* __restrict__ part, PcgScalars* sc, int nr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ps = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[kWarps * 4];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const T beta0 = (T)sc->beta[0], beta1 = (T)(nr > 1 ? sc->beta[1] : 0.0);
+  stage_p<T, false>(s, p_prev, ps, nr, npad, beta0, beta1);
+  __syncthreads();
+  {
+    const int64_t chunk = (nr * npad + gridDim.x - 1) / gridDim.x;
+    const int64_t e0 = (int64_t)blockIdx.x * chunk, e1 = min((int64_t)nr * npad, e0 + chunk);
+    for (int64_t e = e0 + tid; e < e1; e += kThreads) p_out[e] = ps[e];
+  }
+  T acc4[4] = {T(0), T(0), T(0), T(0)};   // qq0, qq1, pp0, pp1 (working type: no FP64 per row)
+  w_rows<T>(W, npad, ps, dinv, q, nr, (int64_t)blockIdx.x * kWarps + warp,
+            (int64_t)gridDim.x * kWarps, acc4);
+  cta_partials<T, 4>(acc4, red, part, blockIdx.x);
   if (arrive_last(&sc->counter[1])) {
     __shared__ double qp[4];
     reduce_partials<4>(part, (int)gridDim.x, qp);
+    if (tid < 4) {
+      if (tid < 2) sc->qq[tid] = qp[tid];
+      else sc->pp[tid - 2] = qp[tid];
+    }
+    if (tid == 0) sc->counter[1] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Grid-wide barrier of a cooperative launch (every CTA is resident): an arrival counter and a
+// generation word in global memory. The wait is bounded: after about a second it records
+// code 3 in *err and goes on (the host then reports the solve as timed out).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void grid_sync(unsigned int* bar, int* err) {
+  __threadfence();   // this thread's writes are visible device-wide before the arrival
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned int it = 0;
+      while (*gen == g) {
+        if (++it > (1u << 24)) {
+          atomicExch(err, 3);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// The tail of PCGTLS step j and the head of step j + 1 in one cooperative launch, A-explicit
+// operator (Alg. 3 / 4), every CTA resident:
+//   R: column sums of the pass partials, delta_j, alpha_j, w += alpha q, y = D^{-1}(A^T t - s2 q)
+//   -- grid barrier --
+//   T: v = W^T y, s -= alpha v; partials of ||s||^2
+//   -- grid barrier --
+//   every CTA sums those partials itself (same order everywhere): eta_{j+1}, beta_j, flags;
+//   CTA 0 stores them. If a step j + 1 follows:
+//   S: p_{j+1} = s + beta_j p_j, q_{j+1} = D^{-1} W p_{j+1}; the last CTA stores ||q||^2, ||p||^2.
+// Data written by other CTAs of this launch is read with ld.global.cg (L1 is not coherent).
+// The three phases replace the pcg_reduce, gemv_wt and gemv_w launches with the same
+// arithmetic; virtual block b of a phase stands for CTA b of the separate launch.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) pcg_step_kernel(
+    const T* __restrict__ part, int P, int nr, int64_t npad, T* __restrict__ q,
+    T* __restrict__ w, T* __restrict__ y, const T* __restrict__ dinv, PcgScalars* sc,
+    const double* __restrict__ tt, const T* __restrict__ WT, const T* __restrict__ W,
+    T* __restrict__ s, const T* __restrict__ p_cur, T* __restrict__ p_next, double* gpart,
+    int gemv_blocks, int next, unsigned int* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* vs = reinterpret_cast<T*>(smem_raw);
+  __shared__ T sh[kWarps][33];
+  __shared__ T s_alpha[2], s_sigma2;
+  __shared__ int s_ok[2];
+  __shared__ double red[kWarps * 4];
+  __shared__ double s_eta_new[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // nothing to do once every right-hand side has stopped (the flags are only written after the
+  // second barrier, so every CTA takes the same branch)
+  if (sc->done[0] && (nr < 2 || sc->done[1])) return;
+  // scalars of step j as the previous launches left them (thread 0; shared with the CTA)
+  __shared__ double s_eta[2], s_eta0[2], s_beta[2], s_delta[2];
+  __shared__ int s_done[2], s_iters[2], s_nspd[2];
+  if (tid == 0) {
+    const double sigma2 = sc->sigma2;
+    for (int r = 0; r < 2; ++r) {
+      s_done[r] = sc->done[r];
+      s_eta[r] = sc->eta[r];
+      s_eta0[r] = sc->eta0[r];
+      s_beta[r] = sc->beta[r];
+      s_iters[r] = sc->iters[r];
+      s_nspd[r] = sc->not_spd[r];
+      s_delta[r] = sc->delta[r];
+      s_ok[r] = 0;
+      s_alpha[r] = T(0);
+      if (r < nr && !s_done[r]) {
+        const double delta = tt[r * 2] - sigma2 * sc->qq[r];
+        s_delta[r] = delta;
+        s_ok[r] = (delta > 0.0) ? 1 : 0;
+        const double alpha = s_ok[r] ? s_eta[r] / delta : 0.0;
+        if (blockIdx.x == 0) {
+          sc->delta[r] = delta;
+          if (s_ok[r]) sc->alpha[r] = alpha;
+        }
+        s_alpha[r] = (T)alpha;
+      }
+    }
+    s_sigma2 = (T)sigma2;
+  }
+  __syncthreads();
+  // ---- R: reduction of the pass partials (virtual grid npad/32 x nr)
+  const int nbx = (int)((npad + 31) / 32);
+  for (int vb = blockIdx.x; vb < nbx * nr; vb += gridDim.x) {
+    const int r = vb / nbx, bx = vb % nbx;
+    if (!s_done[r]) {
+      const int64_t j = (int64_t)bx * 32 + lane;
+      T t = T(0);
+      if (j < npad) {
+        T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
+        int pp = warp;
+        for (; pp + 3 * kWarps < P; pp += 4 * kWarps) {
+          t0 += part[((int64_t)pp * nr + r) * npad + j];
+          t1 += part[((int64_t)(pp + kWarps) * nr + r) * npad + j];
+          t2 += part[((int64_t)(pp + 2 * kWarps) * nr + r) * npad + j];
+          t3 += part[((int64_t)(pp + 3 * kWarps) * nr + r) * npad + j];
+        }
+        for (; pp < P; pp += kWarps) t0 += part[((int64_t)pp * nr + r) * npad + j];
+        t = (t0 + t1) + (t2 + t3);
+      }
+      sh[warp][lane] = t;
+      __syncthreads();
+      if (warp == 0 && s_ok[r]) {
+        T at = T(0);
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) at += sh[k][lane];
+        if (j < npad) {
+          const T qj = q[r * npad + j];
+          w[r * npad + j] = fma(s_alpha[r], qj, w[r * npad + j]);
+          y[r * npad + j] = (at - s_sigma2 * qj) * dinv[j];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  grid_sync(bar, err);
+  // ---- T: v = W^T y and the s recurrence (virtual grid gemv_blocks)
+  const bool act0 = 0 < nr && !s_done[0] && s_delta[0] > 0.0;
+  const bool act1 = 1 < nr && !s_done[1] && s_delta[1] > 0.0;
+  for (int vb = blockIdx.x; vb < gemv_blocks; vb += gridDim.x) {
+    stage_vec<T, true>(y, vs, nr, npad);
+    __syncthreads();
+    T ss[2] = {T(0), T(0)};
+    wt_rows<T>(WT, npad, vs, s, p_cur, act0, act1, s_alpha[0], s_alpha[1], s_sigma2, false,
+               true, nr, (int64_t)vb * kWarps + warp, (int64_t)gemv_blocks * kWarps, ss);
+    cta_partials<T, 2>(ss, red, gpart, vb);
+    __syncthreads();
+  }
+  grid_sync(bar, err);
+  // ---- scalars of step j + 1 (every CTA, the same summation order)
+  reduce_partials_cg<2>(gpart, gemv_blocks, s_eta_new);
+  __syncthreads();
+  if (tid == 0) {
+    const double cg_tol2 = sc->cg_tol2;
+    for (int r = 0; r < nr; ++r) {
+      double eta = s_eta[r], eta0 = s_eta0[r], beta = s_beta[r];
+      int done = s_done[r], iters = s_iters[r], nspd = s_nspd[r];
+      eta_update(s_eta_new[r], false, eta, eta0, beta, done, iters, nspd, s_delta[r], cg_tol2);
+      s_beta[r] = beta;
+      if (blockIdx.x == 0) {
+        sc->eta[r] = eta;
+        sc->eta0[r] = eta0;
+        sc->beta[r] = beta;
+        sc->done[r] = done;
+        sc->iters[r] = iters;
+        sc->not_spd[r] = nspd;
+      }
+    }
+  }
+  __syncthreads();
+  if (!next) return;
+  // ---- S: p_{j+1}, q_{j+1} (virtual grid gemv_blocks)
+  const T beta0 = (T)s_beta[0], beta1 = (T)(nr > 1 ? s_beta[1] : 0.0);
+  for (int vb = blockIdx.x; vb < gemv_blocks; vb += gridDim.x) {
+    stage_p<T, true>(s, p_cur, vs, nr, npad, beta0, beta1);
+    __syncthreads();
+    {
+      const int64_t chunk = (nr * npad + gemv_blocks - 1) / gemv_blocks;
+      const int64_t e0 = (int64_t)vb * chunk, e1 = min((int64_t)nr * npad, e0 + chunk);
+      for (int64_t e = e0 + tid; e < e1; e += kThreads) p_next[e] = vs[e];
+    }
+    T acc4[4] = {T(0), T(0), T(0), T(0)};
+    w_rows<T>(W, npad, vs, dinv, q, nr, (int64_t)vb * kWarps + warp,
+              (int64_t)gemv_blocks * kWarps, acc4);
+    cta_partials<T, 4>(acc4, red, gpart + 2048, vb);
+    __syncthreads();
+  }
+  if (arrive_last(&sc->counter[1])) {
+    __shared__ double qp[4];
+    reduce_partials<4>(gpart + 2048, gemv_blocks, qp);
     if (tid < 4) {
       if (tid < 2) sc->qq[tid] = qp[tid];
       else sc->pp[tid - 2] = qp[tid];
@@ -1243,6 +1555,30 @@ void launch_gemv_w(const T* W, int64_t npad, const T* s, const T* p_prev, T* p_o
 }
 
 template <typename T>
+bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* y,
+                     const T* dinv, PcgScalars* sc, const double* tt, const T* WT, const T* W,
+                     T* s, const T* p_cur, T* p_next, double* gpart, bool next,
+                     unsigned int* bar, int* err, int num_sms, cudaStream_t st) {
+  const size_t smem = sizeof(T) * nr * npad;
+  allow_smem(pcg_step_kernel<T>, smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_step_kernel<T>, kThreads,
+                                                    smem) != cudaSuccess || per_sm < 1)
+    return false;
+  int gb = gemv_grid(npad);
+  const int grid = std::max(1, std::min(gb, per_sm * num_sms));
+  int nx = next ? 1 : 0;
+  void* args[] = {(void*)&part, (void*)&P,  (void*)&nr,    (void*)&npad,  (void*)&q,
+                  (void*)&w,    (void*)&y,  (void*)&dinv,  (void*)&sc,    (void*)&tt,
+                  (void*)&WT,   (void*)&W,  (void*)&s,     (void*)&p_cur, (void*)&p_next,
+                  (void*)&gpart, (void*)&gb, (void*)&nx,   (void*)&bar,   (void*)&err};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_step_kernel<T>, grid,
+                                                    kThreads, args, smem, st);
+  count_launch();
+  return e == cudaSuccess;
+}
+
+template <typename T>
 void launch_pcg_reduce(const T* part, int P, int64_t npad, const T* q, T* w, T* y,
                        const T* dinv, PcgScalars* sc, const double* tt, int nr,
                        cudaStream_t s) {
@@ -1302,6 +1638,10 @@ void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaS
                                  double*, PcgScalars*, int, cudaStream_t);                     \
   template void launch_pcg_reduce<T>(const T*, int, int64_t, const T*, T*, T*, const T*,       \
                                      PcgScalars*, const double*, int, cudaStream_t);           \
+  template bool launch_pcg_step<T>(const T*, int, int, int64_t, T*, T*, T*, const T*,          \
+                                   PcgScalars*, const double*, const T*, const T*, T*,         \
+                                   const T*, T*, double*, bool, unsigned int*, int*, int,      \
+                                   cudaStream_t);                                              \
   template void launch_pcg_update_R<T>(const T*, T*, T*, const T*, PcgScalars*, int,           \
                                        int64_t, cudaStream_t);                                 \
   template void launch_rqi_update<T>(double*, const T*, const T*, const double*, RqiScalars*,  \

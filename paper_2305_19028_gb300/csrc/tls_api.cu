@@ -240,7 +240,7 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->dinv32 = alloc_t<float>(ctx, npad);
   ctx->sout = alloc_t<double>(ctx, 8);
   ctx->gpart = alloc_t<double>(ctx, 4096);
-  ctx->counter = alloc_t<unsigned int>(ctx, 4);
+  ctx->counter = alloc_t<unsigned int>(ctx, 8);   // last-CTA counters; [4..5] grid barrier
   ctx->derr = alloc_t<int>(ctx, 1);
   ctx->sc = alloc_t<PcgScalars>(ctx, 1);
   ctx->rs = alloc_t<RqiScalars>(ctx, 1);
@@ -249,7 +249,7 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
-  TLS_CK(cudaMemsetAsync(ctx->counter, 0, 4 * sizeof(unsigned int), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->counter, 0, 8 * sizeof(unsigned int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->sc, 0, sizeof(PcgScalars), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->rs, 0, sizeof(RqiScalars), ctx->stream));
@@ -396,6 +396,35 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
                            modeA, nr, ctx->stream);
   }
   T* pb[2] = {v.p0, v.p1};
+  if (modeA && !ctx->sparse && steps > 0) {
+    // pass over A, then the rest of the step and the head of the next in one cooperative
+    // launch (pcg_step)
+    {
+      Prof pr(ctx, TLS_PROF_PCG_GEMV);
+      tls::launch_gemv_w<T>(W, npad, v.s, pb[1], pb[0], dinv_t<T>(ctx), v.q, ctx->gpart, ctx->sc,
+                            nr, ctx->stream);
+    }
+    for (int j = 0; j < steps; ++j) {
+      T* pcur = pb[j & 1];
+      T* pnext = pb[(j + 1) & 1];
+      {
+        Prof pr(ctx, nr == 2 ? TLS_PROF_PCG_PASS2 : TLS_PROF_PCG_PASS1);
+        tls::launch_apass<T>(ctx->planU, Au, npad, ctx->m, npad, nr, false, v.q, npad, nullptr,
+                             static_cast<T*>(ctx->part), ctx->spart, ctx->sout + 4,
+                             ctx->counter + 1, done_ptr(ctx), ctx->derr, ctx->stream);
+      }
+      Prof pr(ctx, TLS_PROF_PCG_REDUCE);
+      if (!tls::launch_pcg_step<T>(static_cast<const T*>(ctx->part), ctx->PU, nr, npad, v.q, v.w,
+                                   v.y, dinv_t<T>(ctx), ctx->sc, ctx->sout + 4, WT, W, v.s, pcur,
+                                   pnext, ctx->gpart, j + 1 < steps, ctx->counter + 4, ctx->derr,
+                                   ctx->num_sms, ctx->stream)) {
+        set_err(ctx, "cooperative launch of the PCGTLS step failed");
+        return TLS_ERR_CUDA;
+      }
+    }
+    TLS_CK_LAUNCH("pcgtls");
+    return TLS_OK;
+  }
   for (int j = 0; j < steps; ++j) {
     T* pcur = pb[j & 1];
     T* pprev = pb[(j + 1) & 1];

@@ -151,6 +151,15 @@ template <typename T>
 void launch_gemv_w(const T* W, int64_t npad, const T* s, const T* p_prev, T* p_out,
                    const T* dinv, T* q, double* part, PcgScalars* sc, int nr,
                    cudaStream_t s_);
+// The rest of PCGTLS step j after its pass over A (reduction of the pass partials, w and y,
+// v = W^T y and s, eta and beta) and, when `next`, the head of step j + 1 (p and q = D^{-1} W p),
+// in one cooperative launch. bar: two zero-initialised words (grid barrier); err: the bounded
+// waits record code 3 there. Returns false when the cooperative launch is not possible.
+template <typename T>
+bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* y,
+                     const T* dinv, PcgScalars* sc, const double* tt, const T* WT, const T* W,
+                     T* s, const T* p_cur, T* p_next, double* gpart, bool next,
+                     unsigned int* bar, int* err, int num_sms, cudaStream_t st);
 // Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).
 template <typename T>
 void launch_pcg_reduce(const T* part, int P, int64_t npad, const T* q, T* w, T* y,
