@@ -2,12 +2,14 @@
 // the single-problem factor and the packed batch.
 //
 // The block's upper triangle is held in registers as the 136 4 x 4 tiles (I, J), I <= J, of its
-// 16 x 16 tile grid, one tile per thread. Four pivots per step: the threads of tile row k/4
-// publish rows k .. k+3 of the updated (unscaled) block; 64 threads form the 4 x 4 factor R11 of
-// the pivot block and the rows k .. k+3 of R, Y = R11^{-T} S[k:k+4][:] (unrounded); every tile
-// below takes the rank-4 update S[i][j] -= sum_t Y[t][i] Y[t][j] from registers. Two barriers
-// per step. Each finished row of R goes out rounded to the factor precision (global memory and
-// the shared copy S used for the inverse), while the block's own update uses the unrounded row.
+// 16 x 16 tile grid, one tile per thread. kPB = 8 pivots per step: the threads of tile rows
+// k/4 and k/4 + 1 publish rows k .. k+7 of the updated (unscaled) block; 64 threads form the
+// 8 x 8 factor R11 of the pivot block and the rows k .. k+7 of R, Y = R11^{-T} S[k:k+8][:]
+// (unrounded); every tile below takes the rank-8 update S[i][j] -= sum_t Y[t][i] Y[t][j] from
+// registers. Two barriers per step, eight steps per block. Each finished row of R goes out
+// rounded to the factor precision (global memory and the shared copy S used for the inverse),
+// while the block's own update uses the unrounded rows. (Loops over the pivot block run to kPB
+// with a guard rather than to t, so that they unroll and R11 stays in registers.)
 #pragma once
 #include <cstdint>
 
@@ -15,7 +17,7 @@ namespace tls {
 namespace chol64 {
 
 constexpr int kB = 64;   // block order
-constexpr int kPB = 4;   // pivots per step
+constexpr int kPB = 8;   // pivots per step (a multiple of 4)
 constexpr int kTT = kB / 4;
 
 template <typename T>
@@ -49,11 +51,11 @@ __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Rou
       v[a][c] = (tI < kTT) ? G[(int64_t)(4 * tI + a) * ld + 4 * tJ + c] : T(0);
   if (tid == 0) sc.bad = 0;
   for (int k = 0; k < kB; k += kPB) {
-    if (tI == k / 4)
+    if (tI >= k / 4 && tI < (k + kPB) / 4)
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) sc.rowk[a][4 * tJ + c] = v[a][c];
+        for (int c = 0; c < 4; ++c) sc.rowk[4 * tI - k + a][4 * tJ + c] = v[a][c];
     __syncthreads();
     if (tid < kB && tid >= k) {
       // R11 = chol(S11) from the published upper entries
@@ -63,7 +65,8 @@ __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Rou
       for (int t = 0; t < kPB; ++t) {
         T dsum = sc.rowk[t][k + t];
 #pragma unroll
-        for (int q = 0; q < t; ++q) dsum = fma(-r[q][t], r[q][t], dsum);
+        for (int q = 0; q < kPB; ++q)
+          if (q < t) dsum = fma(-r[q][t], r[q][t], dsum);
         if (!(dsum > T(0))) {                // non-positive or NaN pivot: breakdown
           bad = bad ? bad : (k + t + 1);
           dsum = T(1);
@@ -79,14 +82,17 @@ __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Rou
         r[t][t] = rtt;
         rinv[t] = inv;
 #pragma unroll
-        for (int u = t + 1; u < kPB; ++u) {
-          T e = sc.rowk[t][k + u];
+        for (int u = 0; u < kPB; ++u) {
+          if (u > t) {
+            T e = sc.rowk[t][k + u];
 #pragma unroll
-          for (int q = 0; q < t; ++q) e = fma(-r[q][t], r[q][u], e);
-          r[t][u] = e * inv;
+            for (int q = 0; q < kPB; ++q)
+              if (q < t) e = fma(-r[q][t], r[q][u], e);
+            r[t][u] = e * inv;
+          }
         }
       }
-      // column c = tid of rows k .. k+3 of R by forward substitution with R11^T (inside the
+      // column c = tid of rows k .. k+kPB-1 of R by forward substitution with R11^T (inside the
       // pivot block it reproduces R11's entries operation for operation; zeros below them)
       const int c = tid;
       T y[kPB];
@@ -94,7 +100,8 @@ __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Rou
       for (int t = 0; t < kPB; ++t) {
         T e = sc.rowk[t][c];
 #pragma unroll
-        for (int q = 0; q < t; ++q) e = fma(-r[q][t], y[q], e);
+        for (int q = 0; q < kPB; ++q)
+          if (q < t) e = fma(-r[q][t], y[q], e);
         y[t] = (c - k < t) ? T(0) : e * rinv[t];
       }
 #pragma unroll
@@ -109,7 +116,7 @@ __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Rou
       if (bad && tid == k) atomicCAS(&sc.bad, 0, bad);
     }
     __syncthreads();
-    if (tI < kTT && tI > k / 4) {
+    if (tI < kTT && tI >= (k + kPB) / 4) {
       T yi[kPB][4], yj[kPB][4];
 #pragma unroll
       for (int t = 0; t < kPB; ++t)

@@ -89,7 +89,6 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* kWarps*K
 // Last-CTA detection after every CTA has published its partials (threadfence reduction).
 __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __shared__ bool last;
-  __threadfence();   // every thread's partials are visible device-wide before the arrival
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -783,7 +782,7 @@ __device__ __forceinline__ void stage_p(const T* __restrict__ s, const T* __rest
 
 // Rows gw, gw + GW, ... of v = W^T y (WT = W^T lower triangular, entries 0..j of row j) and the
 // s recurrence of those rows; ss accumulates ||s||^2 over the rows of the calling lane 0.
-template <typename T>
+template <typename T, int U>
 __device__ __forceinline__ void wt_rows(const T* __restrict__ WT, int64_t npad, const T* ys,
                                         T* __restrict__ s, const T* __restrict__ p, bool act0,
                                         bool act1, T alpha0, T alpha1, T sigma2, bool init,
@@ -795,7 +794,6 @@ __device__ __forceinline__ void wt_rows(const T* __restrict__ WT, int64_t npad, 
     const T* row = WT + j * npad;
     const int64_t lim = ((j + VW) / VW) * VW;    // entries 0..j, rounded up (zeros beyond j)
     T a0 = T(0), a1 = T(0);
-    constexpr int U = 8;                          // vector loads in flight per lane
     for (int64_t cb = (int64_t)lane * VW; cb < lim; cb += 32 * VW * U) {
       V wv[U];
 #pragma unroll
@@ -843,7 +841,7 @@ __device__ __forceinline__ void wt_rows(const T* __restrict__ WT, int64_t npad, 
 
 // Rows gw, gw + GW, ... of q = D^{-1} W p (W upper triangular) from the staged p; acc4
 // accumulates ||q||^2 (two RHS) and ||p||^2 (two RHS) over the rows of the calling lane 0.
-template <typename T>
+template <typename T, int U>
 __device__ __forceinline__ void w_rows(const T* __restrict__ W, int64_t npad, const T* ps,
                                        const T* __restrict__ dinv, T* __restrict__ q, int nr,
                                        int64_t gw, int64_t GW, T (&acc4)[4]) {
@@ -853,7 +851,6 @@ __device__ __forceinline__ void w_rows(const T* __restrict__ W, int64_t npad, co
   for (int64_t i = gw; i < npad; i += GW) {
     const T* row = W + i * npad;
     T a0 = T(0), a1 = T(0);
-    constexpr int U = 8;                          // vector loads in flight per lane
     for (int64_t cb = (i / VW) * VW + (int64_t)lane * VW; cb < npad; cb += 32 * VW * U) {
       V wv[U];
 #pragma unroll
@@ -905,11 +902,13 @@ __device__ __forceinline__ void cta_partials(T (&v)[K], double* red /* kWarps * 
 #pragma unroll
     for (int k = 0; k < K; ++k) red[warp * K + k] = (double)v[k];
   __syncthreads();
-  if (tid < K) {
-    double t = 0.0;
-    for (int w2 = 0; w2 < kWarps; ++w2) t += red[w2 * K + tid];
-    part[slot * K + tid] = t;
-  }
+  if (tid == 0)   // one writer: its fence before the arrival publishes all K values
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < kWarps; ++w2) t += red[w2 * K + k];
+      part[slot * K + k] = t;
+    }
 }
 
 // eta_{j+1}, beta_j and the termination flags of Alg. 3 from eta_new (one RHS r).
@@ -958,7 +957,7 @@ __global__ void __launch_bounds__(kThreads) gemv_wt_kernel(
   stage_vec<T, false>(y, ys, nr, npad);
   __syncthreads();
   T ss[2] = {T(0), T(0)};
-  wt_rows<T>(WT, npad, ys, s, p, act0, act1, alpha0, alpha1, sigma2, init != 0, modeA != 0, nr,
+  wt_rows<T, 8>(WT, npad, ys, s, p, act0, act1, alpha0, alpha1, sigma2, init != 0, modeA != 0, nr,
              (int64_t)blockIdx.x * kWarps + warp, (int64_t)gridDim.x * kWarps, ss);
   cta_partials<T, 2>(ss, red, part, blockIdx.x);
   if (arrive_last(&sc->counter[0])) {
@@ -1002,7 +1001,7 @@ __global__ void __launch_bounds__(kThreads) gemv_w_kernel(
     for (int64_t e = e0 + tid; e < e1; e += kThreads) p_out[e] = ps[e];
   }
   T acc4[4] = {T(0), T(0), T(0), T(0)};   // qq0, qq1, pp0, pp1 (working type: no FP64 per row)
-  w_rows<T>(W, npad, ps, dinv, q, nr, (int64_t)blockIdx.x * kWarps + warp,
+  w_rows<T, 8>(W, npad, ps, dinv, q, nr, (int64_t)blockIdx.x * kWarps + warp,
             (int64_t)gridDim.x * kWarps, acc4);
   cta_partials<T, 4>(acc4, red, part, blockIdx.x);
   if (arrive_last(&sc->counter[1])) {
@@ -1022,7 +1021,6 @@ __global__ void __launch_bounds__(kThreads) gemv_w_kernel(
 // code 3 in *err and goes on (the host then reports the solve as timed out).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void grid_sync(unsigned int* bar, int* err) {
-  __threadfence();   // this thread's writes are visible device-wide before the arrival
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* gen = bar + 1;
@@ -1070,11 +1068,12 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
     int gemv_blocks, int next, unsigned int* bar, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* vs = reinterpret_cast<T*>(smem_raw);
-  __shared__ T sh[kWarps][33];
+  __shared__ T sh[16][17];
   __shared__ T s_alpha[2], s_sigma2;
   __shared__ int s_ok[2];
   __shared__ double red[kWarps * 4];
   __shared__ double s_eta_new[2];
+  constexpr int kStepU = (sizeof(T) == 4) ? 16 : 8;   // vector loads in flight per lane
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // nothing to do once every right-hand side has stopped (the flags are only written after the
   // second barrier, so every CTA takes the same branch)
@@ -1109,36 +1108,34 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
     s_sigma2 = (T)sigma2;
   }
   __syncthreads();
-  // ---- R: reduction of the pass partials (virtual grid npad/32 x nr)
-  const int nbx = (int)((npad + 31) / 32);
-  for (int vb = blockIdx.x; vb < nbx * nr; vb += gridDim.x) {
-    const int r = vb / nbx, bx = vb % nbx;
-    if (!s_done[r]) {
-      const int64_t j = (int64_t)bx * 32 + lane;
-      T t = T(0);
-      if (j < npad) {
-        T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
-        int pp = warp;
-        for (; pp + 3 * kWarps < P; pp += 4 * kWarps) {
-          t0 += part[((int64_t)pp * nr + r) * npad + j];
-          t1 += part[((int64_t)(pp + kWarps) * nr + r) * npad + j];
-          t2 += part[((int64_t)(pp + 2 * kWarps) * nr + r) * npad + j];
-          t3 += part[((int64_t)(pp + 3 * kWarps) * nr + r) * npad + j];
-        }
-        for (; pp < P; pp += kWarps) t0 += part[((int64_t)pp * nr + r) * npad + j];
-        t = (t0 + t1) + (t2 + t3);
+  // ---- R: reduction of the pass partials: virtual blocks of 16 consecutive entries of the
+  // nr x npad partial vectors; thread (slice ps, entry c) sums the partials p = ps (mod 16)
+  // with every load in flight, then 16 threads add the 16 slices
+  {
+    const int c = tid & 15, ps = tid >> 4;
+    const int64_t nvb = (int64_t)nr * npad / 16;
+    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+      const int64_t e0 = vb * 16;
+      const int r = (int)(e0 / npad);
+      if (s_done[r]) continue;   // uniform over the CTA
+      const int64_t e = e0 + c;
+      T t0 = T(0), t1 = T(0);
+      int pp = ps;
+      for (; pp + 16 < P; pp += 32) {
+        t0 += part[(int64_t)pp * nr * npad + e];
+        t1 += part[(int64_t)(pp + 16) * nr * npad + e];
       }
-      sh[warp][lane] = t;
+      if (pp < P) t0 += part[(int64_t)pp * nr * npad + e];
+      sh[ps][c] = t0 + t1;
       __syncthreads();
-      if (warp == 0 && s_ok[r]) {
+      if (tid < 16 && s_ok[r]) {
         T at = T(0);
 #pragma unroll
-        for (int k = 0; k < kWarps; ++k) at += sh[k][lane];
-        if (j < npad) {
-          const T qj = q[r * npad + j];
-          w[r * npad + j] = fma(s_alpha[r], qj, w[r * npad + j]);
-          y[r * npad + j] = (at - s_sigma2 * qj) * dinv[j];
-        }
+        for (int k = 0; k < 16; ++k) at += sh[k][tid];
+        const int64_t j = e - (int64_t)r * npad;
+        const T qj = q[e];
+        w[e] = fma(s_alpha[r], qj, w[e]);
+        y[e] = (at - s_sigma2 * qj) * dinv[j];
       }
       __syncthreads();
     }
@@ -1151,7 +1148,7 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
     stage_vec<T, true>(y, vs, nr, npad);
     __syncthreads();
     T ss[2] = {T(0), T(0)};
-    wt_rows<T>(WT, npad, vs, s, p_cur, act0, act1, s_alpha[0], s_alpha[1], s_sigma2, false,
+    wt_rows<T, kStepU>(WT, npad, vs, s, p_cur, act0, act1, s_alpha[0], s_alpha[1], s_sigma2, false,
                true, nr, (int64_t)vb * kWarps + warp, (int64_t)gemv_blocks * kWarps, ss);
     cta_partials<T, 2>(ss, red, gpart, vb);
     __syncthreads();
@@ -1190,7 +1187,7 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
       for (int64_t e = e0 + tid; e < e1; e += kThreads) p_next[e] = vs[e];
     }
     T acc4[4] = {T(0), T(0), T(0), T(0)};
-    w_rows<T>(W, npad, vs, dinv, q, nr, (int64_t)vb * kWarps + warp,
+    w_rows<T, kStepU>(W, npad, vs, dinv, q, nr, (int64_t)vb * kWarps + warp,
               (int64_t)gemv_blocks * kWarps, acc4);
     cta_partials<T, 4>(acc4, red, gpart + 2048, vb);
     __syncthreads();

@@ -68,6 +68,8 @@ struct tls_ctx {
 
   // factor
   bool factored = false;
+  bool colnorm_done = false;   // D (and A_u in FP32 when a32_done) depend on A alone: computed once
+  bool a32_done = false;
   Prec u = Prec::FP32;
   tls_prec uf_used = TLS_FP16;
   tls_options opt{};
@@ -728,16 +730,19 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
-  {
+  const bool want32 = ctx->u == Prec::FP32;
+  if (!ctx->colnorm_done || (want32 && !ctx->a32_done)) {
     Prof pr(ctx, TLS_PROF_SCALE);
     if (ctx->sparse)
-      tls::sparse_colnorm(ctx->cp, ctx->cv64, ctx->u == Prec::FP32 ? ctx->cv32 : nullptr, n, npad,
-                          ctx->d, ctx->dinv, ctx->dinv32, st);
+      tls::sparse_colnorm(ctx->cp, ctx->cv64, want32 ? ctx->cv32 : nullptr, n, npad, ctx->d,
+                          ctx->dinv, ctx->dinv32, st);
     else
-      tls::launch_colnorm(ctx->A64, npad, m, n, npad, ctx->u == Prec::FP32 ? ctx->A32 : nullptr,
-                          npad, ctx->d, ctx->dinv32, ctx->dinv, cpart, st);
+      tls::launch_colnorm(ctx->A64, npad, m, n, npad, want32 ? ctx->A32 : nullptr, npad, ctx->d,
+                          ctx->dinv32, ctx->dinv, cpart, st);
+    TLS_CK_LAUNCH("column norms");
+    ctx->colnorm_done = true;
+    ctx->a32_done = ctx->a32_done || want32;
   }
-  TLS_CK_LAUNCH("column norms");
   // ||A||_F^2 = sum of d_j^2 and ||b||^2 on the device; read back with the factor's first
   // synchronisation (no extra host round trip)
   TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * npad, st));
