@@ -50,7 +50,7 @@ typedef enum {
   TLS_BF16 = 1,
   TLS_FP32 = 2,
   TLS_FP64 = 3,
-  TLS_AUTO = 4   /* packed batch only: the selector network picks u_f per problem */
+  TLS_AUTO = 4   /* the selector network picks u_f (tls_set_selector / tls_batch_set_selector) */
 } tls_prec;
 
 /* Stop reasons reported in tls_info.stop_reason. */
@@ -266,6 +266,23 @@ tls_status tls_mlp_adam(float* params, const float* grad, float* m, float* v, in
  * Requires a successful tls_factor (TLS_ERR_STATE otherwise).
  */
 tls_status tls_condition(tls_ctx* ctx, int iters, double* out);
+
+/*
+ * tls_set_selector -- install the selector network for tls_factor(ctx, TLS_AUTO, opt), which
+ * then factors at FP16, computes the 16 features of that factor, runs the network and, when it
+ * picks BF16 or FP32, refactors at that precision; the network's PCGTLS tolerance is used by
+ * tls_solve in tolerance mode (cg_fixed = 0). params: TLS_MLP_PARAMS FP32 values; mean, scale:
+ * the feature normalisation (TLS_SELECTOR_FEATURES each). Host pointers, copied. Without a
+ * selector, TLS_AUTO means FP16. Same network and features as tls_batch_set_selector.
+ */
+tls_status tls_set_selector(tls_ctx* ctx, const float* params, const float* mean,
+                            const float* scale);
+
+/*
+ * tls_features -- the TLS_SELECTOR_FEATURES raw selector features of the current factor
+ * (host out), defined as for tls_batch_features. TLS_ERR_STATE before a successful tls_factor.
+ */
+tls_status tls_features(tls_ctx* ctx, float* F_host);
 
 void tls_destroy(tls_ctx* ctx);
 const char* tls_status_str(tls_status s);

@@ -350,20 +350,13 @@ __global__ void __launch_bounds__(256, 2) gemm_big_kernel(
 // read from shared memory as float4, the next k-slab prefetched into registers (one barrier per
 // slab). Same requirements as gemm_big_kernel, K a multiple of 16.
 template <bool AK, bool BKM>
-__global__ void __launch_bounds__(256) gemm_mid_kernel(
-    int M, int N, int K, const float* __restrict__ A, int64_t lda, int64_t sA,
-    const float* __restrict__ B, int64_t ldb, int64_t sB, float* __restrict__ C, int64_t ldc,
-    int64_t sC, float alpha, float beta, int upper, int mirror, int kfrom_i, int kto_j,
-    const int* skip) {
+__device__ __forceinline__ void gemm_mid_tile(
+    int M, int N, int K, const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
+    int64_t ldb, float* __restrict__ C, int64_t ldc, float alpha, float beta, int upper,
+    int mirror, int kfrom_i, int kto_j, int tile_i, int tile_j) {
   constexpr int BM = 64, BN = 64, BK = 16, LD = 68;
-  if (skip != nullptr && *(volatile const int*)skip != 0) return;
-  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
-  if (upper && tile_i > tile_j) return;
   __shared__ __align__(16) float As[2][BK][LD];
   __shared__ __align__(16) float Bs[2][BK][LD];
-  A += (int64_t)blockIdx.z * sA;
-  B += (int64_t)blockIdx.z * sB;
-  C += (int64_t)blockIdx.z * sC;
   const int i0 = tile_i * BM, j0 = tile_j * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   int k_lo = kfrom_i ? (i0 / BK) * BK : 0;
@@ -457,6 +450,20 @@ __global__ void __launch_bounds__(256) gemm_mid_kernel(
   }
 }
 
+template <bool AK, bool BKM>
+__global__ void __launch_bounds__(256) gemm_mid_kernel(
+    int M, int N, int K, const float* __restrict__ A, int64_t lda, int64_t sA,
+    const float* __restrict__ B, int64_t ldb, int64_t sB, float* __restrict__ C, int64_t ldc,
+    int64_t sC, float alpha, float beta, int upper, int mirror, int kfrom_i, int kto_j,
+    const int* skip) {
+  if (skip != nullptr && *(volatile const int*)skip != 0) return;
+  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
+  if (upper && tile_i > tile_j) return;
+  gemm_mid_tile<AK, BKM>(M, N, K, A + (int64_t)blockIdx.z * sA, lda, B + (int64_t)blockIdx.z * sB,
+                         ldb, C + (int64_t)blockIdx.z * sC, ldc, alpha, beta, upper, mirror,
+                         kfrom_i, kto_j, tile_i, tile_j);
+}
+
 template <typename Tin, typename Tc, bool AK, bool BKM>
 void gemm_simt(int M, int N, int K, const Tin* A, int64_t lda, int64_t sA, const Tin* B,
                int64_t ldb, int64_t sB, Tc* C, int64_t ldc, int64_t sC, Tc alpha, Tc beta,
@@ -537,10 +544,8 @@ __device__ __forceinline__ double round_prec(double v, int prec) {
 // W_KK turns the panel solve R_KJ = R_KK^{-T} H_KJ into a product, and it is also the diagonal
 // block of W = R^{-1}. Nothing runs if an earlier block broke down (*info != 0).
 template <typename T>
-__global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t npad, int64_t kb,
-                                                             int* info, int prec) {
-  if (*(volatile int*)info != 0) return;
-  extern __shared__ __align__(16) unsigned char dsm[];
+__device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, int64_t kb,
+                                                    int* info, int prec, unsigned char* dsm) {
   T (*S)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm);
   T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
   const int tid = threadIdx.x;
@@ -589,6 +594,33 @@ __global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t
     const int r = e / NB, c = e % NB;
     W[(kb + r) * npad + kb + c] = X[r][c];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t npad, int64_t kb,
+                                                             int* info, int prec) {
+  if (*(volatile int*)info != 0) return;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  potrf_inv_diag_body<T>(M, W, npad, kb, info, prec, dsm);
+}
+
+// Trailing update of block step K, H_22 -= R_K2^T R_K2 (upper 64 x 64 tiles), with the factor
+// of the next diagonal block fused in: the CTA of tile (0, 0), which is that block, updates it
+// and then factors and inverts it as potrf_inv_diag_kernel does, while the other CTAs update
+// the rest of the trailing matrix. FP32 working type.
+__global__ void __launch_bounds__(256) chol_update_next_kernel(float* M, float* W, int64_t npad,
+                                                               int64_t kb, int* info, int prec) {
+  if (*(volatile int*)info != 0) return;
+  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
+  if (tile_i > tile_j) return;
+  const int64_t k2 = kb + NB, n2 = npad - k2;
+  float* P = M + kb * npad + k2;
+  gemm_mid_tile<false, false>((int)n2, (int)n2, NB, P, npad, P, npad, M + k2 * npad + k2, npad,
+                              -1.f, 1.f, 1, 0, 0, 0, tile_i, tile_j);
+  if (tile_i != 0 || tile_j != 0) return;
+  __syncthreads();   // the updated block (written by this CTA) before it is factored
+  extern __shared__ __align__(16) unsigned char dsm[];
+  potrf_inv_diag_body<float>(M, W, npad, k2, info, prec, dsm);
 }
 
 template <typename T>
@@ -750,20 +782,37 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
     return true;
   }();
   (void)attr;
+  constexpr bool fused = std::is_same<T, float>::value;
+  if constexpr (fused) {
+    static const bool attr2 = [dsmem] {
+      cudaFuncSetAttribute(chol_update_next_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)dsmem);
+      return true;
+    }();
+    (void)attr2;
+  }
+  potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, 0, info, (int)prec);
+  count_launch();
   for (int64_t kb = 0; kb < npad; kb += NB) {
-    potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb, info, (int)prec);
-    count_launch();
     const int64_t n2 = npad - kb - NB;
     if (n2 <= 0) break;
     // panel R_KJ = W_KK^T H_KJ, in place over H_KJ
     gemm_simt<T, T, false, false>(NB, (int)n2, NB, Wd + kb * npad + kb, npad, 0,
                                   M + kb * npad + kb + NB, npad, 0, M + kb * npad + kb + NB, npad,
                                   0, T(1), T(0), 0, 0, 1, s, info);
-    // trailing update H22 -= R_K2^T R_K2 (upper part)
-    T* P = M + kb * npad + kb + NB;
-    T* C = M + (kb + NB) * npad + kb + NB;
-    gemm_simt<T, T, false, false>((int)n2, (int)n2, NB, P, npad, 0, P, npad, 0, C, npad, 0,
-                                  T(-1), T(1), 1, 0, 1, s, info);
+    // trailing update H22 -= R_K2^T R_K2 (upper part), then the next diagonal block
+    if constexpr (fused) {
+      const unsigned nt = (unsigned)(n2 / NB);
+      chol_update_next_kernel<<<dim3(nt, nt), 256, dsmem, s>>>(M, Wd, npad, kb, info, (int)prec);
+      count_launch();
+    } else {
+      T* P = M + kb * npad + kb + NB;
+      T* C = M + (kb + NB) * npad + kb + NB;
+      gemm_simt<T, T, false, false>((int)n2, (int)n2, NB, P, npad, 0, P, npad, 0, C, npad, 0,
+                                    T(-1), T(1), 1, 0, 1, s, info);
+      potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb + NB, info, (int)prec);
+      count_launch();
+    }
   }
   zero_lower_kernel<T><<<blocks_for(npad * npad, 256), 256, 0, s>>>(M, npad); count_launch();
 }

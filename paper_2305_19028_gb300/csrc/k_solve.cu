@@ -100,33 +100,6 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   return last;
 }
 
-// Sum of K interleaved partial vectors written by other CTAs of the same launch into out
-// (shared memory, written by thread 0; the caller synchronises before reading it).
-template <int K>
-__device__ __forceinline__ void reduce_partials_cg(const double* part, int P, double* out) {
-  __shared__ double sh[kWarps * K];
-  double v[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = 0.0;
-  for (int p = threadIdx.x; p < P; p += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] += __ldcg(part + (int64_t)p * K + k);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w * K + k];
-      out[k] = t;
-    }
-}
-
 // Sum of K interleaved partial vectors part[p*K + k] (p < P) by the whole block; the result
 // for k < K lands in out[k] (written by thread 0). Used by the last CTA of a grid.
 template <int K>
@@ -1015,29 +988,49 @@ __global__ void __launch_bounds__(kThreads) gemv_w_kernel(
   }
 }
 
+// Arrival count over the grid (thread 0 only): true in the last CTA to arrive, which also resets
+// the counter. The caller has fenced its writes. (A two-level count, 8 groups then the top,
+// measured no faster: the barrier's cost is the round trip through L2, not contention.)
+__device__ __forceinline__ bool arrive_count(unsigned int* cnt) {
+  if (atomicAdd(cnt, 1u) != gridDim.x - 1u) return false;
+  atomicExch(cnt, 0u);
+  return true;
+}
+
 // ---------------------------------------------------------------------------------------
-// Grid-wide barrier of a cooperative launch (every CTA is resident): an arrival counter and a
-// generation word in global memory. The wait is bounded: after about a second it records
-// code 3 in *err and goes on (the host then reports the solve as timed out).
+// Grid-wide barrier of a cooperative launch (every CTA is resident). bar: [0] the arrival
+// counter, [9] the generation word. The last CTA to arrive runs `last(...)` with all
+// its threads before it releases the others (a reduction every CTA needs after the barrier
+// is done once there instead of by every CTA). The wait is bounded: after 2^22 polls (each an
+// L2 round trip, a few seconds in all) it records code 3 in *err and goes on; the host then
+// reports the solve as timed out.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void grid_sync(unsigned int* bar, int* err) {
+template <typename F>
+__device__ __forceinline__ void grid_sync_last(unsigned int* bar, int* err, F&& last) {
+  __shared__ int s_last;
+  __shared__ unsigned int s_gen;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = bar + 1;
-    const unsigned int g = *gen;
+    volatile unsigned int* gen = bar + 9;
+    s_gen = *gen;
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
+    s_last = arrive_count(bar) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    last();
+    __syncthreads();
+    if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned int it = 0;
-      while (*gen == g) {
-        if (++it > (1u << 24)) {
-          atomicExch(err, 3);
-          break;
-        }
-        __nanosleep(64);
+      atomicAdd(bar + 9, 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 9;
+    unsigned int it = 0;
+    while (*gen == s_gen) {
+      if (++it > (1u << 22)) {
+        atomicExch(err, 3);
+        break;
       }
     }
     __threadfence();
@@ -1074,7 +1067,7 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
   __shared__ double red[kWarps * 4];
   __shared__ double s_eta_new[2];
   constexpr int kStepU = (sizeof(T) == 4) ? 16 : 8;   // vector loads in flight per lane
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   // nothing to do once every right-hand side has stopped (the flags are only written after the
   // second barrier, so every CTA takes the same branch)
   if (sc->done[0] && (nr < 2 || sc->done[1])) return;
@@ -1140,7 +1133,7 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
       __syncthreads();
     }
   }
-  grid_sync(bar, err);
+  grid_sync_last(bar, err, [] {});
   // ---- T: v = W^T y and the s recurrence (virtual grid gemv_blocks)
   const bool act0 = 0 < nr && !s_done[0] && s_delta[0] > 0.0;
   const bool act1 = 1 < nr && !s_done[1] && s_delta[1] > 0.0;
@@ -1153,18 +1146,17 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
     cta_partials<T, 2>(ss, red, gpart, vb);
     __syncthreads();
   }
-  grid_sync(bar, err);
-  // ---- scalars of step j + 1 (every CTA, the same summation order)
-  reduce_partials_cg<2>(gpart, gemv_blocks, s_eta_new);
-  __syncthreads();
-  if (tid == 0) {
-    const double cg_tol2 = sc->cg_tol2;
-    for (int r = 0; r < nr; ++r) {
-      double eta = s_eta[r], eta0 = s_eta0[r], beta = s_beta[r];
-      int done = s_done[r], iters = s_iters[r], nspd = s_nspd[r];
-      eta_update(s_eta_new[r], false, eta, eta0, beta, done, iters, nspd, s_delta[r], cg_tol2);
-      s_beta[r] = beta;
-      if (blockIdx.x == 0) {
+  // ---- eta_{j+1}, beta_j and the flags, by the last CTA to reach the barrier; every CTA
+  // reads beta from sc afterwards (L2 loads: the values were written after this launch began)
+  grid_sync_last(bar, err, [&] {
+    reduce_partials<2>(gpart, gemv_blocks, s_eta_new);
+    __syncthreads();
+    if (tid == 0) {
+      const double cg_tol2 = sc->cg_tol2;
+      for (int r = 0; r < nr; ++r) {
+        double eta = s_eta[r], eta0 = s_eta0[r], beta = s_beta[r];
+        int done = s_done[r], iters = s_iters[r], nspd = s_nspd[r];
+        eta_update(s_eta_new[r], false, eta, eta0, beta, done, iters, nspd, s_delta[r], cg_tol2);
         sc->eta[r] = eta;
         sc->eta0[r] = eta0;
         sc->beta[r] = beta;
@@ -1173,6 +1165,10 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
         sc->not_spd[r] = nspd;
       }
     }
+  });
+  if (tid == 0) {
+    s_beta[0] = __ldcg(&sc->beta[0]);
+    s_beta[1] = __ldcg(&sc->beta[1]);
   }
   __syncthreads();
   if (!next) return;
@@ -1192,14 +1188,22 @@ __global__ void __launch_bounds__(kThreads) pcg_step_kernel(
     cta_partials<T, 4>(acc4, red, gpart + 2048, vb);
     __syncthreads();
   }
-  if (arrive_last(&sc->counter[1])) {
+  // ||q||^2, ||p||^2 by the last CTA to finish (the others leave)
+  __shared__ int s_lastq;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_lastq = arrive_count(bar + 10) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_lastq) {
+    __threadfence();
     __shared__ double qp[4];
     reduce_partials<4>(gpart + 2048, gemv_blocks, qp);
     if (tid < 4) {
       if (tid < 2) sc->qq[tid] = qp[tid];
       else sc->pp[tid - 2] = qp[tid];
     }
-    if (tid == 0) sc->counter[1] = 0u;
   }
 }
 

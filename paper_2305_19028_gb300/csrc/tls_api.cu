@@ -87,6 +87,12 @@ struct tls_ctx {
   int64_t fail_pivot = -1;   // pivot index of the last breakdown (-1: none)
   double last_sigma2 = -1.0; // sigma^2 of the last successful tls_solve (-1: none yet)
   double t_factor_ms = 0.0;
+  // selector network (tls_factor with TLS_AUTO)
+  bool has_sel = false;
+  float* dsel = nullptr;     // parameters, then feature mean and scale
+  bool use_sel_tol = false;  // the last factor was chosen by the network: its PCGTLS tolerance
+  double sel_cg_tol = 0.0;
+  int sel_class = -1;
 
   // solve workspace
   double* x = nullptr;       // npad
@@ -186,7 +192,7 @@ void dev_free(tls_ctx* c, void* p) {
 
 enum Slot : int {
   kSlotCpart, kSlotInfo, kSlotAsT, kSlotH, kSlotM, kSlotWc, kSlotR, kSlotW, kSlotWT, kSlotWork,
-  kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotCount
+  kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotFeat, kSlotCount
 };
 static_assert(kSlotCount <= 16, "slots");
 
@@ -242,7 +248,7 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->dinv32 = alloc_t<float>(ctx, npad);
   ctx->sout = alloc_t<double>(ctx, 8);
   ctx->gpart = alloc_t<double>(ctx, 4096);
-  ctx->counter = alloc_t<unsigned int>(ctx, 8);   // last-CTA counters; [4..5] grid barrier
+  ctx->counter = alloc_t<unsigned int>(ctx, 32);   // last-CTA counters; [4..22] PCGTLS step
   ctx->derr = alloc_t<int>(ctx, 1);
   ctx->sc = alloc_t<PcgScalars>(ctx, 1);
   ctx->rs = alloc_t<RqiScalars>(ctx, 1);
@@ -251,7 +257,7 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
-  TLS_CK(cudaMemsetAsync(ctx->counter, 0, 8 * sizeof(unsigned int), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->counter, 0, 32 * sizeof(unsigned int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->sc, 0, sizeof(PcgScalars), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->rs, 0, sizeof(RqiScalars), ctx->stream));
@@ -563,7 +569,8 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     prev_psi = psi;
     // two shifted solves (Alg. 4, PCGTLS with k+1 steps) and the x update
     const int steps = o.cg_fixed ? (k + 1) : std::max(1, o.cg_max);
-    stt = run_pcg<T>(ctx, 2, ctx->f, -1.0, ctx->x, s2, steps, o.cg_fixed ? 0.0 : o.cg_tol, modeA);
+    const double cgt = ctx->use_sel_tol ? ctx->sel_cg_tol : o.cg_tol;
+    stt = run_pcg<T>(ctx, 2, ctx->f, -1.0, ctx->x, s2, steps, o.cg_fixed ? 0.0 : cgt, modeA);
     if (stt != TLS_OK) return stt;
     {
       Prof pr(ctx, TLS_PROF_VEC);
@@ -1061,6 +1068,62 @@ int batch_workers(int count) {
 
 }  // namespace
 
+namespace {
+
+// The 16 selector features of the current factor into the context's device buffer (raw, or
+// normalised with the selector's mean and scale); returns the device pointer.
+template <typename TU>
+float* features_impl(tls_ctx* ctx, bool normalised) {
+  cudaStream_t st = ctx->stream;
+  const int64_t n = ctx->n, npad = ctx->npad;
+  const size_t vec = sizeof(TU) * (size_t)npad;
+  const size_t sbytes = sizeof(double) * (size_t)(2 + (n + 7) / 8);
+  unsigned char* buf = static_cast<unsigned char*>(slot(ctx, kSlotFeat, 2 * vec + sbytes + 64 * 4));
+  if (!buf) return nullptr;
+  TU* x = reinterpret_cast<TU*>(buf);
+  TU* y = reinterpret_cast<TU*>(buf + vec);
+  double* scratch = reinterpret_cast<double*>(buf + 2 * vec);
+  float* F = reinterpret_cast<float*>(buf + 2 * vec + sbytes);
+  const double log10_uf = (ctx->uf_used == TLS_FP16) ? -11.0 * std::log10(2.0)
+                          : (ctx->uf_used == TLS_BF16) ? -8.0 * std::log10(2.0)
+                          : (ctx->uf_used == TLS_FP32) ? -24.0 * std::log10(2.0)
+                                                        : -53.0 * std::log10(2.0);
+  tls::launch_features<TU>(ctx->d, static_cast<const TU*>(ctx->R), static_cast<const TU*>(ctx->W),
+                           static_cast<const TU*>(ctx->WT), n, npad, ctx->m, ctx->norm2_A,
+                           ctx->norm2_b, ctx->shifts, ctx->shift, (int)ctx->fail_pivot, log10_uf,
+                           x, y, scratch, F, st);
+  if (normalised)
+    tls::launch_feature_normalise(F, ctx->dsel + TLS_MLP_PARAMS,
+                                  ctx->dsel + TLS_MLP_PARAMS + TLS_SELECTOR_FEATURES, st);
+  return F;
+}
+
+// TLS_AUTO: factor at FP16, let the network pick u_f (and the PCGTLS tolerance) from the
+// features of that factor, refactor at the pick when it is not FP16.
+tls_status factor_auto_ctx(tls_ctx* ctx) {
+  tls_status s = factor_impl(ctx, TLS_FP16);
+  if (s != TLS_OK || !ctx->has_sel) return s;
+  float* F = (ctx->u == Prec::FP64) ? features_impl<double>(ctx, true)
+                                    : features_impl<float>(ctx, true);
+  if (!F) return TLS_ERR_OOM;
+  float* net = F + 32;
+  tls::mlp::launch_mlp_forward(ctx->dsel, 1, F, net, ctx->stream);
+  TLS_CK_LAUNCH("selector network");
+  float out[4];
+  TLS_CK(cudaMemcpyAsync(out, net, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+  TLS_CK(cudaStreamSynchronize(ctx->stream));
+  int c = 0;
+  if (out[1] > out[c]) c = 1;
+  if (out[2] > out[c]) c = 2;
+  ctx->sel_class = c;
+  ctx->sel_cg_tol = std::pow(10.0, std::min(-1.0, std::max(-12.0, (double)out[3])));
+  if (ctx->uf_used == TLS_FP16 && c != 0) s = factor_impl(ctx, c == 1 ? TLS_BF16 : TLS_FP32);
+  ctx->use_sel_tol = (s == TLS_OK);
+  return s;
+}
+
+}  // namespace
+
 extern "C" {
 
 void tls_default_options(tls_options* opt) {
@@ -1228,8 +1291,8 @@ tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz, cons
 
 tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
   if (!ctx) return TLS_ERR_ARG;
-  if ((int)u_f < 0 || (int)u_f > 3) {
-    set_err(ctx, "u_f must be FP16, BF16, FP32 or FP64");
+  if ((int)u_f < 0 || (int)u_f > 4) {
+    set_err(ctx, "u_f must be FP16, BF16, FP32, FP64 or AUTO");
     return TLS_ERR_ARG;
   }
   tls_options o;
@@ -1246,7 +1309,42 @@ tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
   }
   ctx->opt = o;
   ctx->u = to_prec(o.u);
+  ctx->use_sel_tol = false;
+  ctx->sel_class = -1;
+  if (u_f == TLS_AUTO) return factor_auto_ctx(ctx);
   return factor_impl(ctx, u_f);
+}
+
+tls_status tls_set_selector(tls_ctx* ctx, const float* params, const float* mean,
+                            const float* scale) {
+  if (!ctx || !params || !mean || !scale) return TLS_ERR_ARG;
+  if (!ctx->dsel) {
+    ctx->dsel = alloc_t<float>(ctx, TLS_MLP_PARAMS + 2 * TLS_SELECTOR_FEATURES);
+    if (!ctx->dsel) return TLS_ERR_OOM;
+  }
+  cudaStream_t st = ctx->stream;
+  TLS_CK(cudaMemcpyAsync(ctx->dsel, params, sizeof(float) * TLS_MLP_PARAMS, cudaMemcpyHostToDevice,
+                         st));
+  TLS_CK(cudaMemcpyAsync(ctx->dsel + TLS_MLP_PARAMS, mean, sizeof(float) * TLS_SELECTOR_FEATURES,
+                         cudaMemcpyHostToDevice, st));
+  TLS_CK(cudaMemcpyAsync(ctx->dsel + TLS_MLP_PARAMS + TLS_SELECTOR_FEATURES, scale,
+                         sizeof(float) * TLS_SELECTOR_FEATURES, cudaMemcpyHostToDevice, st));
+  TLS_CK(cudaStreamSynchronize(st));
+  ctx->has_sel = true;
+  return TLS_OK;
+}
+
+tls_status tls_features(tls_ctx* ctx, float* F_host) {
+  if (!ctx || !F_host) return TLS_ERR_ARG;
+  if (!ctx->factored) return TLS_ERR_STATE;
+  float* F = (ctx->u == Prec::FP64) ? features_impl<double>(ctx, false)
+                                    : features_impl<float>(ctx, false);
+  if (!F) return TLS_ERR_OOM;
+  TLS_CK_LAUNCH("features");
+  TLS_CK(cudaMemcpyAsync(F_host, F, sizeof(float) * TLS_SELECTOR_FEATURES, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  TLS_CK(cudaStreamSynchronize(ctx->stream));
+  return TLS_OK;
 }
 
 static tls_status solve_once(tls_ctx* ctx, double tol, int max_rqi, double* sigma,

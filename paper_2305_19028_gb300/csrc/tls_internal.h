@@ -153,8 +153,9 @@ void launch_gemv_w(const T* W, int64_t npad, const T* s, const T* p_prev, T* p_o
                    cudaStream_t s_);
 // The rest of PCGTLS step j after its pass over A (reduction of the pass partials, w and y,
 // v = W^T y and s, eta and beta) and, when `next`, the head of step j + 1 (p and q = D^{-1} W p),
-// in one cooperative launch. bar: two zero-initialised words (grid barrier); err: the bounded
-// waits record code 3 there. Returns false when the cooperative launch is not possible.
+// in one cooperative launch. bar: 19 zero-initialised words (grid barrier and arrival
+// counters, zero again after every launch); err: the bounded waits record code 3 there.
+// Returns false when the cooperative launch is not possible.
 template <typename T>
 bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* y,
                      const T* dinv, PcgScalars* sc, const double* tt, const T* WT, const T* W,
@@ -201,6 +202,14 @@ int launch_frob_dw(const T* W, int64_t n, int64_t npad, const T* dinv, double* p
                    cudaStream_t s);
 template <typename T>
 void launch_vec_to_double(const T* x, double* y, int64_t n, int64_t npad, cudaStream_t s);
+void launch_feature_normalise(float* F, const float* mean, const float* scale, cudaStream_t s);
+// The 16 selector features of one factored problem into F (device, 16 floats); x, y: npad
+// scratch vectors; scratch: 1 + ceil(n/8) doubles.
+template <typename T>
+void launch_features(const double* d, const T* R, const T* W, const T* WT, int64_t n, int64_t npad,
+                     int64_t m, double norm2_A, double norm2_b, int nshift, double shift,
+                     int fail_pivot, double log10_uf, T* x, T* y, double* scratch, float* F,
+                     cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------
 // Sparse (CSR + CSC) kernels (k_sparse.cu)

@@ -35,7 +35,8 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_batch_solve", "tls_batch_destroy", "tls_batch_last_error",
            "tls_batch_export_factor", "tls_batch_profile_enable", "tls_batch_profile_get",
            "tls_batch_profile_elems", "tls_mlp_forward", "tls_mlp_grad", "tls_mlp_adam",
-           "tls_batch_set_selector", "tls_batch_features", "tls_set_pass_variant"]
+           "tls_batch_set_selector", "tls_batch_features", "tls_set_pass_variant",
+           "tls_set_selector", "tls_features"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
@@ -113,6 +114,9 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_residual_noalloc": (C.c_int, [i64, i64, v, i64, v, v, v, v, v]),
         "tls_export_working_copy": (C.c_int, [v, C.POINTER(C.c_float)]),
         "tls_condition": (C.c_int, [v, C.c_int, _dp]),
+        "tls_set_selector": (C.c_int, [v, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                       C.POINTER(C.c_float)]),
+        "tls_features": (C.c_int, [v, C.POINTER(C.c_float)]),
         "tls_factor_batched": (C.c_int, [C.c_int, vp, C.c_int, C.POINTER(tls_options), _ip]),
         "tls_batch_create_dense": (C.c_int, [vp, C.c_int, C.POINTER(i64), C.POINTER(i64), vp,
                                              C.POINTER(i64), vp, C.c_int, v]),
@@ -284,6 +288,25 @@ def tls_condition(ctx, iters: int = 30) -> dict:
     out = np.zeros(9)
     _check(load().tls_condition(ctx, iters, _ptr(out)), ctx)
     return dict(zip(COND_KEYS, out.tolist()))
+
+
+def tls_set_selector(ctx, params, mean, scale):
+    """Install the selector network (FP32 params, feature mean and scale) for tls_factor(..., "auto")."""
+    fp = C.POINTER(C.c_float)
+    P = np.ascontiguousarray(params, dtype=np.float32)
+    mu = np.ascontiguousarray(mean, dtype=np.float32)
+    sd = np.ascontiguousarray(scale, dtype=np.float32)
+    if P.size != MLP_PARAMS or mu.size != N_FEATURES or sd.size != N_FEATURES:
+        raise ValueError("selector: wrong parameter or feature sizes")
+    _check(load().tls_set_selector(ctx, P.ctypes.data_as(fp), mu.ctypes.data_as(fp),
+                                   sd.ctypes.data_as(fp)), ctx)
+
+
+def tls_features(ctx) -> np.ndarray:
+    """The 16 raw selector features of the current factor."""
+    F = np.zeros(N_FEATURES, dtype=np.float32)
+    _check(load().tls_features(ctx, F.ctypes.data_as(C.POINTER(C.c_float))), ctx)
+    return F
 
 
 def tls_export_working_copy(ctx):

@@ -160,3 +160,45 @@ def test_trained_selector_gains_over_fp16_first(torch):
     assert ok_a >= ok_b
     assert fb_a < fb_b
     assert t_sel < t_base
+
+
+def test_single_context_features_match_batch(torch):
+    # the single-problem feature kernels compute the batch's 16 features (the same network
+    # serves both paths); the factors differ only in the order of rounding of the inverse
+    probs = [synth.dense_problem(400, 40, d_lo=1e-3, noise=1e-5, seed=21),
+             synth.dense_problem(999, 130, d_lo=1e-1, noise=1e-4, seed=22),
+             synth.selector_problem(100007)]
+    with tls.Batch([(p.A, p.b) for p in probs]) as bt:
+        bt.factor("fp16", u="fp32")
+        Fb = bt.features()
+    for i, p in enumerate(probs):
+        ctx = tls.tls_create_dense(p.A, p.b)
+        try:
+            tls.tls_factor(ctx, "fp16", tls.tls_default_options(u="fp32"))
+            F = tls.tls_features(ctx)
+        finally:
+            tls.tls_destroy(ctx)
+        np.testing.assert_allclose(F, Fb[i], rtol=0, atol=2e-3)
+
+
+def test_single_context_auto_factor(torch):
+    model = selector.load_model()
+    if model is None:
+        pytest.skip("no trained selector model in the package")
+    params, mean, scale = model
+    picked = set()
+    for seed in (100001, 100002, 100003, 100011):
+        p = synth.selector_problem(seed)
+        xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+        ctx = tls.tls_create_dense(p.A, p.b)
+        try:
+            tls.tls_set_selector(ctx, params, mean, scale)
+            opt = tls.tls_default_options(u="fp32")
+            tls.tls_factor(ctx, "auto", opt)
+            x, s, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+        finally:
+            tls.tls_destroy(ctx)
+        picked.add(info["u_f_used"])
+        assert abs(s - so) <= 1e-10 * so
+        assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+    assert picked <= {0, 1, 2, 3}
