@@ -198,6 +198,95 @@ def label(problems):
     return F[keep], ycls[keep], ytol[keep], ymask[keep], cost[keep], ok[keep]
 
 
+# ---------------------------------------------------------------------------------------------
+# The wider configuration (dense and sparse problems, n up to 2048): one context per problem
+# ---------------------------------------------------------------------------------------------
+def _ctx(p):
+    if isinstance(p, synth.CsrProblem):
+        return tls.tls_create_csr(p.m, p.n, p.row_ptr, p.col_idx, p.val, p.b)
+    return tls.tls_create_dense(p.A, p.b)
+
+
+def _cost_any(p, info, u_f) -> float:
+    """The time model of _cost for a dense problem; for CSR the Gram costs nnz * (nnz/m)^2
+    FMA on CUDA cores and a pass moves the values and indices (12 bytes per entry)."""
+    if not isinstance(p, synth.CsrProblem):
+        return _cost(p, info, u_f)
+    m, n, nnz = p.m, p.n, p.nnz
+    t = 2.0 * nnz * (nnz / m) ** 2 / RATE["gram_fp32"] + n ** 3 / 3.0 / RATE["chol"]
+    t += info["rqi_steps"] * 4.0 * nnz / RATE["fp64"]
+    t += (info["cg_iters"] / 2.0 + 12) * 2.0 * 12.0 * nnz / RATE["hbm"]
+    return t
+
+
+def _close(x, s, xr, sr) -> bool:
+    return bool(abs(s - sr) <= SIGMA_TOL * sr and np.linalg.norm(x - xr) <= X_TOL * np.linalg.norm(xr))
+
+
+def label_one(p):
+    """Labels of one problem from single-context solves on one resident copy of A: features of
+    the FP16 factor, the class (cheapest precision whose own factor, not an escalated one,
+    matches the plain FP64 reference), the tolerance label, per-class costs and successes, and
+    whether the reference converged."""
+    ctx = _ctx(p)
+    try:
+        tls.tls_factor(ctx, "fp64", tls.tls_default_options(u="fp64", fallback=0))
+        xr, sr, ir = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+        ref_ok = ir["stop_reason"] != tls.STOP_MAX_RQI
+        ok = np.zeros(3, dtype=bool)
+        cost = np.full(3, np.inf)
+        F = None
+        for c, uf in enumerate(CLASSES):
+            try:
+                tls.tls_factor(ctx, uf, tls.tls_default_options(u="fp32", fallback=0))
+            except tls.TLSError:
+                continue
+            if uf == "fp16":
+                F = tls.tls_features(ctx)
+            x, s, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+            if info["u_f_used"] == tls.PREC[uf] and _close(x, s, xr, sr):
+                ok[c] = True
+                cost[c] = _cost_any(p, info, uf)
+        ycls = int(np.argmin(cost)) if ok.any() else 2
+        ytol, ymask = 0.0, 0.0
+        if ok[ycls]:
+            for tol in TOLS:    # largest tolerance first
+                tls.tls_factor(ctx, CLASSES[ycls], tls.tls_default_options(
+                    u="fp32", fallback=0, cg_fixed=0, cg_tol=tol, cg_max=60))
+                x, s, _ = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+                if _close(x, s, xr, sr):
+                    ytol, ymask = float(np.log10(tol)), 1.0
+                    break
+    finally:
+        tls.tls_destroy(ctx)
+    return F, ycls, ytol, ymask, cost, ok, ref_ok
+
+
+def dataset_wide(seed0: int, count: int, workers: int = 6, log_every: int = 500):
+    """Labels of `count` problems of synth.selector_problem_wide (seeds seed0 ..), generated and
+    solved by `workers` host threads, each on its own context and stream."""
+    import concurrent.futures as cf
+
+    def job(seed):
+        return label_one(synth.selector_problem_wide(seed))
+
+    rows = []
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        for k, r in enumerate(ex.map(job, range(seed0, seed0 + count))):
+            rows.append(r)
+            if log_every and (k + 1) % log_every == 0:
+                print(f"  labelled {k + 1}/{count} ({time.perf_counter() - t0:.0f} s)", flush=True)
+    keep = [r for r in rows if r[6] and r[0] is not None]
+    F = np.stack([r[0] for r in keep]).astype(np.float32)
+    ycls = np.array([r[1] for r in keep], dtype=np.int32)
+    ytol = np.array([r[2] for r in keep], dtype=np.float32)
+    ymask = np.array([r[3] for r in keep], dtype=np.float32)
+    cost = np.stack([r[4] for r in keep])
+    ok = np.stack([r[5] for r in keep])
+    return F, ycls, ytol, ymask, cost, ok
+
+
 def dataset(seed0: int, count: int, chunk: int = 400):
     parts = []
     for c0 in range(0, count, chunk):
@@ -217,15 +306,54 @@ def load_model(path: str = MODEL_PATH):
     return z["params"], z["mean"], z["scale"]
 
 
+def evaluate_wide(params, mean, scale, seed0: int, count: int, workers: int = 6):
+    """Held-out comparison on the wider distribution, one problem at a time (so the timings are
+    not shared with other solves): the plain FP64 reference, then FP16 first with the precision
+    fallback, then the selector (TLS_AUTO) with the fallback. Returns per-problem arrays
+    (reference converged, accurate fp16-first, accurate selector, seconds fp16-first, seconds
+    selector, u_f used by the selector). Problems are generated ahead by `workers` threads."""
+    import concurrent.futures as cf
+    rows = []
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        for p in ex.map(synth.selector_problem_wide, range(seed0, seed0 + count)):
+            ctx = _ctx(p)
+            try:
+                tls.tls_factor(ctx, "fp64", tls.tls_default_options(u="fp64", fallback=0))
+                xr, sr, ir = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+                ref_ok = ir["stop_reason"] != tls.STOP_MAX_RQI
+                o = tls.tls_default_options(u="fp32")
+                t0 = time.perf_counter()
+                tls.tls_factor(ctx, "fp16", o)
+                x1, s1, _ = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+                t1 = time.perf_counter()
+                tls.tls_set_selector(ctx, params, mean, scale)
+                t2 = time.perf_counter()
+                tls.tls_factor(ctx, "auto", o)
+                x2, s2, i2 = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+                t3 = time.perf_counter()
+            finally:
+                tls.tls_destroy(ctx)
+            rows.append((ref_ok, _close(x1, s1, xr, sr), _close(x2, s2, xr, sr), t1 - t0, t3 - t2,
+                         i2["u_f_used"]))
+    return tuple(np.array([r[k] for r in rows]) for k in range(6))
+
+
 def main():
     ap = argparse.ArgumentParser(description="label, train and evaluate the precision selector")
     ap.add_argument("--n-train", type=int, default=4000)
     ap.add_argument("--n-eval", type=int, default=1000)
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--out", default=MODEL_PATH)
+    ap.add_argument("--wide", action="store_true",
+                    help="the wider distribution (dense and sparse, n up to 2048), one context per "
+                         "problem; seeds 200000.. training, 300000.. held out")
+    ap.add_argument("--workers", type=int, default=6)
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
+    if args.wide:
+        main_wide(args)
+        return
     t0 = time.time()
     Ftr, ytr, ttr, mtr, ctr, oktr = dataset(10000, args.n_train)
     Fev, yev, tev, mev, cev, okev = dataset(100000, args.n_eval)
@@ -244,6 +372,31 @@ def main():
           f"final loss {hist[-1]:.4f}; FP16 success rate {okev[:, 0].mean():.3f}", flush=True)
     save(args.out, params, mean, scale, loss=np.array(hist), eval_accuracy=acc,
          n_train=len(ytr), n_eval=len(yev))
+
+
+def main_wide(args):
+    t0 = time.time()
+    Ftr, ytr, ttr, mtr, ctr, oktr = dataset_wide(200000, args.n_train, workers=args.workers)
+    Fev, yev, tev, mev, cev, okev = dataset_wide(300000, args.n_eval, workers=args.workers)
+    t1 = time.time()
+    params, mean, scale, hist = train(Ftr, ytr, ttr, mtr, epochs=args.epochs)
+    t2 = time.time()
+    out = predict(params, mean, scale, Fev)
+    acc = float((out[:, :3].argmax(axis=1) == yev).mean())
+    print(f"labels {t1 - t0:.1f}s train {t2 - t1:.1f}s; train {len(ytr)} eval {len(yev)}; "
+          f"class mix train {np.bincount(ytr, minlength=3).tolist()} eval "
+          f"{np.bincount(yev, minlength=3).tolist()}; eval accuracy {acc:.3f}; "
+          f"final loss {hist[-1]:.4f}", flush=True)
+    ref_ok, ok1, ok2, sec1, sec2, uf2 = evaluate_wide(params, mean, scale, 300000,
+                                                      args.n_eval, workers=args.workers)
+    sel = ref_ok.astype(bool)
+    res = {"eval_problems": int(sel.sum()), "accurate_fp16_first": int(ok1[sel].sum()),
+           "accurate_selector": int(ok2[sel].sum()), "seconds_fp16_first": float(sec1[sel].sum()),
+           "seconds_selector": float(sec2[sel].sum()),
+           "selector_u_f_hist": np.bincount(uf2[sel].astype(int), minlength=4).tolist()}
+    print("held-out:", res, flush=True)
+    save(args.out, params, mean, scale, loss=np.array(hist), eval_accuracy=acc,
+         n_train=len(ytr), n_eval=len(yev), **{k: np.array(v) for k, v in res.items()})
 
 
 if __name__ == "__main__":

@@ -138,6 +138,23 @@ def selector_problem(seed: int) -> DenseProblem:
     return dense_problem(n * ratio, n, d_lo=d_lo, noise=noise, seed=seed)
 
 
+def selector_problem_wide(seed: int):
+    """A problem of the selector configuration's wider distribution (seeds 200000.. for training,
+    300000.. held out): dense or sparse with equal probability, n ~ U{64..2048},
+    m = n*U{4..12}, noise std 10^-U(3,7). Dense: D log-spaced in [10^-U(1,6), 1]. Sparse (as
+    csr_problem): 12 entries per row plus the unit diagonal block, column scales
+    10^U(-U(1,6), 0)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sparse = bool(rng.uniform() < 0.5)
+    n = int(rng.integers(64, 2049))
+    ratio = int(rng.integers(4, 13))
+    lo = float(rng.uniform(1.0, 6.0))
+    noise = 10.0 ** (-rng.uniform(3.0, 7.0))
+    if sparse:
+        return csr_problem(n * ratio, n, nnz_per_row=12, noise=noise, seed=seed, col_scale_lo=-lo)
+    return dense_problem(n * ratio, n, d_lo=10.0 ** (-lo), noise=noise, seed=seed)
+
+
 def csr_problem(m: int, n: int, nnz_per_row: int = 12, noise: float = 1e-3, seed: int = 0,
                 col_scale_lo: float = -2.0) -> CsrProblem:
     """Sparse A: nnz_per_row distinct uniform columns per row, N(0,1) values, A[i,i] += 1 for
