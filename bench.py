@@ -137,14 +137,31 @@ def _dist():
     return ws, rank, local
 
 
-def _barrier_max(value: float, ws: int) -> float:
+def _reduce(value: float, ws: int, op: str) -> float:
+    """Max or sum of a scalar over the ranks (a CUDA tensor under NCCL, a host one under gloo)."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def _barrier_max(value: float, ws: int) -> float:
+    """The slowest rank's time (the job's time)."""
+    return _reduce(value, ws, "max")
+
+
+def _total(value: float, ws: int) -> float:
+    """Units processed by all ranks together."""
+    return _reduce(value, ws, "sum")
+
+
+def _shard_ids(rank: int, count: int) -> list[int]:
+    """The batch members of one rank: independent problems, no exchange between ranks."""
+    return [rank * count + i for i in range(count)]
 
 
 def run_reference(args, ws, rank):
@@ -344,17 +361,17 @@ def run_ours(args, ws, rank, local):
                    "kind": "oracle",
                    "sample": f"1 full FP64 solve of the {M_ROWS}x{N_COLS} problem "
                              f"({t_or:.2f} s, numpy/OpenBLAS threads)"}
-    ok = sum(int(accurate(x_, s_)) for x_, s_ in results)
+    ok = _total(sum(int(accurate(x_, s_)) for x_, s_ in results), ws)
     err = None
     if ref is not None:
         err = {"sigma_rel": abs(last_s - ref[1]) / ref[1],
                "x_rel": float(np.linalg.norm(last_x - ref[0]) / np.linalg.norm(ref[0]))}
     if e2e is not None:
-        okc = sum(int(accurate(x_, s_)) for x_, s_ in e2e_res)
-        e2e["value"] = ws * okc / (e2e["ms_per_step"] * e2e["steps"] * 1e-3)
+        okc = _total(sum(int(accurate(x_, s_)) for x_, s_ in e2e_res), ws)
+        e2e["value"] = okc / (e2e["ms_per_step"] * e2e["steps"] * 1e-3)
     if plain is not None:
-        okp = sum(int(accurate(x_, s_)) for x_, s_ in plain_res)
-        plain["value"] = ws * okp / (plain["ms_per_step"] * plain["steps"] * 1e-3)
+        okp = _total(sum(int(accurate(x_, s_)) for x_, s_ in plain_res), ws)
+        plain["value"] = okp / (plain["ms_per_step"] * plain["steps"] * 1e-3)
         if ref is not None:
             plain["sigma_rel"] = abs(sp - ref[1]) / ref[1]
             plain["x_rel"] = float(np.linalg.norm(xp - ref[0]) / np.linalg.norm(ref[0]))
@@ -368,7 +385,7 @@ def run_ours(args, ws, rank, local):
     roof = _roofline(prof, peaks, dom, M_ROWS, N_COLS) or _roofline(prof, peaks, "pcg_pass2",
                                                                    M_ROWS, N_COLS)
     inner = _roofline(prof, peaks, "pcg_pass2", M_ROWS, N_COLS)
-    value = ws * ok / (ms * 1e-3)
+    value = ok / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -502,10 +519,11 @@ def run_c1(args, ws, rank, local):
         b1.record(stream)
         torch.cuda.synchronize()
         bms = _barrier_max(b0.elapsed_time(b1), ws)
+    ok, okb, oke = _total(ok, ws), _total(okb, ws), _total(oke, ws)
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": ws * ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
+        "metric": METRIC, "value": ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -518,10 +536,10 @@ def run_c1(args, ws, rank, local):
         "roofline": {"kernel": "none (latency bound: every kernel is a few microseconds)",
                      "bound": "latency", "achieved": None, "peak": None, "unit": None,
                      "frac": None, "traffic": None},
-        "packed_batch_of_one": {"value": ws * okb / (bms * 1e-3), "unit": "solves/s",
+        "packed_batch_of_one": {"value": okb / (bms * 1e-3), "unit": "solves/s",
                                 "ms_per_step": bms / args.steps, "accurate": okb},
         "gpu_launches": int(launches), "cpu_baseline": cpu,
-        "e2e": {"value": ws * oke / (ems * 1e-3), "unit": "solves/s",
+        "e2e": {"value": oke / (ems * 1e-3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(p.A.nbytes + p.b.nbytes),
                 "d2h_bytes_per_step": int(8 * 40 + 8), "ms_per_step": ems / args.steps},
         "plain_fp64": "this configuration is the plain all-FP64 method",
@@ -653,14 +671,14 @@ def run_sparse(args, ws, rank, local):
                    "kind": "oracle",
                    "sample": f"1 full FP64 solve of the {CSR_M}x{CSR_N} CSR problem "
                              f"({t_or:.2f} s: sparse A^T A, dense Cholesky R, scipy products)"}
-    ok = sum(int(accurate(x_, s_)) for x_, s_ in results)
+    ok = _total(sum(int(accurate(x_, s_)) for x_, s_ in results), ws)
     if plain is not None:
-        okp = sum(int(accurate(x_, s_)) for x_, s_ in plain_res)
-        plain["value"] = ws * okp / (plain["ms_per_step"] * plain["steps"] * 1e-3)
+        okp = _total(sum(int(accurate(x_, s_)) for x_, s_ in plain_res), ws)
+        plain["value"] = okp / (plain["ms_per_step"] * plain["steps"] * 1e-3)
         plain["accurate"] = okp
     if e2e is not None:
-        okc = sum(int(accurate(x_, s_)) for x_, s_ in e2e_res)
-        e2e["value"] = ws * okc / (e2e["ms_per_step"] * e2e["steps"] * 1e-3)
+        okc = _total(sum(int(accurate(x_, s_)) for x_, s_ in e2e_res), ws)
+        e2e["value"] = okc / (e2e["ms_per_step"] * e2e["steps"] * 1e-3)
     if rank != 0:
         return
     peaks = _peaks()
@@ -686,7 +704,7 @@ def run_sparse(args, ws, rank, local):
 
     dom = max(total, key=total.get)
     line = {
-        "metric": METRIC, "value": ws * ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
+        "metric": METRIC, "value": ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16+f32+f64", "data": "synthetic",
@@ -780,7 +798,7 @@ def run_batch(args, ws, rank, local):
     from paper_2305_19028_gb300 import synth, tls
 
     K = args.batch
-    ids = [rank * K + i for i in range(K)]
+    ids = _shard_ids(rank, K)
     ref, t_or = {}, None
     procs = max(1, (os.cpu_count() or 1) // ws)
     if not args.no_cpu:
@@ -865,7 +883,7 @@ def run_batch(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ems = _barrier_max(e0.elapsed_time(e1), ws)
-        e2e = {"value": ws * okc / (ems * 1e-3), "unit": "solves/s",
+        e2e = {"value": _total(okc, ws) / (ems * 1e-3), "unit": "solves/s",
                "h2d_bytes_per_step": int(sum(p.A.nbytes + p.b.nbytes for p in probs)),
                "d2h_bytes_per_step": int(sum(8 * p.A.shape[1] + 8 for p in probs)),
                "steps": ne, "ms_per_step": ems / ne}
@@ -888,9 +906,11 @@ def run_batch(args, ws, rank, local):
         q1.record(stream)
         torch.cuda.synchronize()
         pms = _barrier_max(q0.elapsed_time(q1), ws)
-        plain = {"value": ws * okp / (pms * 1e-3), "unit": "solves/s", "ms_per_step": pms / np_steps,
+        plain = {"value": _total(okp, ws) / (pms * 1e-3), "unit": "solves/s",
+                 "ms_per_step": pms / np_steps,
                  "steps": np_steps, "accurate": okp, "of": np_steps * K}
     bt.close()
+    ok = int(_total(ok, ws))
     if rank != 0:
         return
     peaks = _peaks()
@@ -904,7 +924,7 @@ def run_batch(args, ws, rank, local):
                "sample": f"all {K} problems of the batch, one FP64 oracle solve each "
                          f"({t_or:.1f} s on {procs} single-threaded processes)"}
     line = {
-        "metric": METRIC, "value": ws * ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
+        "metric": METRIC, "value": ok / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16+f32+f64", "data": "synthetic",
@@ -915,7 +935,7 @@ def run_batch(args, ws, rank, local):
                    "l2": "inputs larger than L2 (A: %.1f GB FP64 + %.1f GB FP32)" % (
                        sum(p.A.nbytes for p in probs) / 1e9, sum(p.A.nbytes for p in probs) / 2e9),
                    "step": "tls_batch_factor + tls_batch_solve on the resident batch"},
-        "accurate_solves": ok, "of": args.steps * K, "fallbacks": n_fb, "u_f_used_hist": uf_hist,
+        "accurate_solves": ok, "of": args.steps * K * ws, "fallbacks": n_fb, "u_f_used_hist": uf_hist,
         "roofline": roof, "inner_loop_roofline": _batch_roofline(prof, peaks, "pcg_pass2"),
         "resid_roofline": _batch_roofline(prof, peaks, "resid_pass"),
         "kernel_share": share, "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()},
