@@ -201,6 +201,23 @@ def test_solve_matches_oracle(m, n, dlo, noise, u_f, u):
     assert info["stop_reason"] in (tls.STOP_PSI_UP, tls.STOP_TOL, tls.STOP_MAX_RQI)
 
 
+def test_refactor_with_another_working_precision():
+    # the column norms and the FP32 copy of A are computed once per context: a context factored
+    # first for u = FP64 (no FP32 copy yet) and then for u = FP32 still solves correctly, and so
+    # does a repeat of the first
+    p = synth.dense_problem(2500, 300, d_lo=1e-3, noise=1e-4, seed=3)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    ctx = tls.tls_create_dense(p.A, p.b)
+    try:
+        for u_f, u in (("fp64", "fp64"), ("fp16", "fp32"), ("fp64", "fp64"), ("bf16", "fp32")):
+            tls.tls_factor(ctx, u_f, tls.tls_default_options(u=u))
+            x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+            assert abs(sigma - so) <= 1e-10 * so, (u_f, u, info)
+            assert _rel(x, xo) <= 1e-8, (u_f, u, info)
+    finally:
+        tls.tls_destroy(ctx)
+
+
 def test_solve_before_factor_is_a_state_error():
     p = synth.dense_problem(50, 5, seed=1)
     ctx = tls.tls_create_dense(p.A, p.b)
