@@ -443,17 +443,44 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(BArrays a, const GTile
 }
 
 // =========================================================================================
-// Inverse of an upper-triangular 64 x 64 block S (shared, row stride kLd) into X (shared):
-// X11 = R11^{-1}, X22 = R22^{-1} by columns (threads 0..63), X12 = -X11 R12 X22.
-// Tm is a 32 x 32 scratch area (row stride kLd). Call with all threads of the CTA.
+// Inverse of an upper-triangular 64 x 64 block S (shared, row stride kLd) into X (shared), by
+// doubling: the eight 8 x 8 diagonal blocks by substitution (chains of at most 8), then for
+// SB = 8, 16, 32 every pair of SB-blocks A, B gets X_AB = -X_AA (R_AB X_BB) as two products
+// through Tm (scratch, 64 x kLd). The k sums run over the whole block length (the entries of
+// X_BB below and of X_AA left of the diagonal are zero), so they unroll. Call with all
+// threads of the CTA.
 // =========================================================================================
+template <typename C, int SB>
+__device__ __forceinline__ void inv_level(const C* S, C* X, C* Tm) {
+  constexpr int pairs = kNB / (2 * SB), cnt = pairs * SB * SB;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int pr = e / (SB * SB), rem = e % (SB * SB), i = rem / SB, j = rem % SB;
+    const int a = 2 * pr * SB;
+    C v = C(0);
+#pragma unroll
+    for (int k = 0; k < SB; ++k)
+      v = fma(S[(a + i) * kLd + a + SB + k], X[(a + SB + k) * kLd + a + SB + j], v);
+    Tm[(pr * SB + i) * kLd + j] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int pr = e / (SB * SB), rem = e % (SB * SB), i = rem / SB, j = rem % SB;
+    const int a = 2 * pr * SB;
+    C v = C(0);
+#pragma unroll
+    for (int k = 0; k < SB; ++k) v = fma(X[(a + i) * kLd + a + k], Tm[(pr * SB + k) * kLd + j], v);
+    X[(a + i) * kLd + a + SB + j] = -v;
+  }
+  __syncthreads();
+}
+
 template <typename C>
 __device__ void inv_upper64(const C* S, C* X, C* Tm) {
   const int tid = threadIdx.x;
   for (int e = tid; e < kNB * kLd; e += blockDim.x) X[e] = C(0);
   __syncthreads();
   if (tid < 64) {
-    const int o = (tid < 32) ? 0 : 32, j = tid & 31;
+    const int o = (tid >> 3) * 8, j = tid & 7;
     for (int i = j; i >= 0; --i) {
       C v = (i == j) ? C(1) : C(0);
       for (int k = i + 1; k <= j; ++k) v = fma(-S[(o + i) * kLd + o + k], X[(o + k) * kLd + o + j], v);
@@ -461,20 +488,9 @@ __device__ void inv_upper64(const C* S, C* X, C* Tm) {
     }
   }
   __syncthreads();
-  for (int e = tid; e < 32 * 32; e += blockDim.x) {   // Tm = R12 X22
-    const int i = e / 32, j = e % 32;
-    C v = C(0);
-    for (int k = 0; k <= j; ++k) v = fma(S[i * kLd + 32 + k], X[(32 + k) * kLd + 32 + j], v);
-    Tm[i * kLd + j] = v;
-  }
-  __syncthreads();
-  for (int e = tid; e < 32 * 32; e += blockDim.x) {   // X12 = -X11 Tm
-    const int i = e / 32, j = e % 32;
-    C v = C(0);
-    for (int k = i; k < 32; ++k) v = fma(X[i * kLd + k], Tm[k * kLd + j], v);
-    X[i * kLd + 32 + j] = -v;
-  }
-  __syncthreads();
+  inv_level<C, 8>(S, X, Tm);
+  inv_level<C, 16>(S, X, Tm);
+  inv_level<C, 32>(S, X, Tm);
 }
 
 // =========================================================================================

@@ -230,20 +230,13 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(
 // A, B (the dispatcher checks).
 // ---------------------------------------------------------------------------------------
 template <bool AK, bool BKM>
-__global__ void __launch_bounds__(256, 2) gemm_big_kernel(
-    int M, int N, int K, const float* __restrict__ A, int64_t lda, int64_t sA,
-    const float* __restrict__ B, int64_t ldb, int64_t sB, float* __restrict__ C, int64_t ldc,
-    int64_t sC, float alpha, float beta, int upper, int mirror, int kfrom_i, int kto_j,
-    const int* skip) {
+__device__ __forceinline__ void gemm_big_tile(
+    int M, int N, int K, const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
+    int64_t ldb, float* __restrict__ C, int64_t ldc, float alpha, float beta, int upper,
+    int mirror, int kfrom_i, int kto_j, int tile_i, int tile_j) {
   constexpr int BM = 128, BN = 128, BK = 8;
-  if (skip != nullptr && *(volatile const int*)skip != 0) return;
-  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
-  if (upper && tile_i > tile_j) return;
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
-  A += (int64_t)blockIdx.z * sA;
-  B += (int64_t)blockIdx.z * sB;
-  C += (int64_t)blockIdx.z * sC;
   const int i0 = tile_i * BM, j0 = tile_j * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   int k_lo = kfrom_i ? (i0 / BK) * BK : 0;
@@ -343,6 +336,20 @@ __global__ void __launch_bounds__(256, 2) gemm_big_kernel(
       if (mirror && gi != gj) C[(int64_t)gj * ldc + gi] = v;
     }
   }
+}
+
+template <bool AK, bool BKM>
+__global__ void __launch_bounds__(256, 2) gemm_big_kernel(
+    int M, int N, int K, const float* __restrict__ A, int64_t lda, int64_t sA,
+    const float* __restrict__ B, int64_t ldb, int64_t sB, float* __restrict__ C, int64_t ldc,
+    int64_t sC, float alpha, float beta, int upper, int mirror, int kfrom_i, int kto_j,
+    const int* skip) {
+  if (skip != nullptr && *(volatile const int*)skip != 0) return;
+  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
+  if (upper && tile_i > tile_j) return;
+  gemm_big_tile<AK, BKM>(M, N, K, A + (int64_t)blockIdx.z * sA, lda, B + (int64_t)blockIdx.z * sB,
+                         ldb, C + (int64_t)blockIdx.z * sC, ldc, alpha, beta, upper, mirror,
+                         kfrom_i, kto_j, tile_i, tile_j);
 }
 
 // FP32 64 x 64-tile variant of the same product for grids too small for 128 x 128 tiles (or K
@@ -543,6 +550,33 @@ __device__ __forceinline__ double round_prec(double v, int prec) {
 //     [[X11, -X11 R12 X22], [0, X22]] at block sizes 8, 16, 32, into W.
 // W_KK turns the panel solve R_KJ = R_KK^{-T} H_KJ into a product, and it is also the diagonal
 // block of W = R^{-1}. Nothing runs if an earlier block broke down (*info != 0).
+// One doubling level of the inverse of the 64 x 64 upper-triangular block S into X: for every
+// pair of SB-blocks A, B, Tm = R_AB X_BB (kept in the zero lower part of S), then
+// X_AB = -X_AA Tm. The k sums run over the whole block length (the entries of X_BB below and of
+// X_AA left of the diagonal are zero), so they unroll and the loads pipeline.
+template <typename T, int SB>
+__device__ __forceinline__ void inv_double_level(T (*S)[NB + 1], T (*X)[NB + 1], int tid) {
+  constexpr int pairs = NB / (2 * SB), cnt = pairs * SB * SB;
+  for (int e = tid; e < cnt; e += 256) {
+    const int pr = e / (SB * SB), rem = e % (SB * SB), i = rem / SB, j = rem % SB;
+    const int a = 2 * pr * SB;
+    T v = T(0);
+#pragma unroll
+    for (int k = 0; k < SB; ++k) v = fma(S[a + i][a + SB + k], X[a + SB + k][a + SB + j], v);
+    S[a + SB + i][a + j] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < cnt; e += 256) {
+    const int pr = e / (SB * SB), rem = e % (SB * SB), i = rem / SB, j = rem % SB;
+    const int a = 2 * pr * SB;
+    T v = T(0);
+#pragma unroll
+    for (int k = 0; k < SB; ++k) v = fma(X[a + i][a + k], S[a + SB + k][a + j], v);
+    X[a + i][a + SB + j] = -v;
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, int64_t kb,
                                                     int* info, int prec, unsigned char* dsm) {
@@ -571,25 +605,9 @@ __device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, in
     }
   }
   __syncthreads();
-  for (int sb = 8; sb < NB; sb *= 2) {
-    const int pairs = NB / (2 * sb), cnt = pairs * sb * sb;
-    for (int e = tid; e < cnt; e += 256) {
-      const int pr = e / (sb * sb), rem = e % (sb * sb), i = rem / sb, j = rem % sb;
-      const int a = 2 * pr * sb;
-      T v = T(0);
-      for (int k = 0; k <= j; ++k) v = fma(S[a + i][a + sb + k], X[a + sb + k][a + sb + j], v);
-      S[a + sb + i][a + j] = v;
-    }
-    __syncthreads();
-    for (int e = tid; e < cnt; e += 256) {
-      const int pr = e / (sb * sb), rem = e % (sb * sb), i = rem / sb, j = rem % sb;
-      const int a = 2 * pr * sb;
-      T v = T(0);
-      for (int k = i; k < sb; ++k) v = fma(X[a + i][a + k], S[a + sb + k][a + j], v);
-      X[a + i][a + sb + j] = -v;
-    }
-    __syncthreads();
-  }
+  inv_double_level<T, 8>(S, X, tid);
+  inv_double_level<T, 16>(S, X, tid);
+  inv_double_level<T, 32>(S, X, tid);
   for (int e = tid; e < NB * NB; e += 256) {
     const int r = e / NB, c = e % NB;
     W[(kb + r) * npad + kb + c] = X[r][c];
@@ -608,6 +626,9 @@ __global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t
 // of the next diagonal block fused in: the CTA of tile (0, 0), which is that block, updates it
 // and then factors and inverts it as potrf_inv_diag_kernel does, while the other CTAs update
 // the rest of the trailing matrix. FP32 working type.
+// BIG: 128 x 128 update tiles (for large trailing matrices; tile (0, 0) still holds the next
+// diagonal block at its top left).
+template <bool BIG>
 __global__ void __launch_bounds__(256) chol_update_next_kernel(float* M, float* W, int64_t npad,
                                                                int64_t kb, int* info, int prec) {
   if (*(volatile int*)info != 0) return;
@@ -615,8 +636,12 @@ __global__ void __launch_bounds__(256) chol_update_next_kernel(float* M, float* 
   if (tile_i > tile_j) return;
   const int64_t k2 = kb + NB, n2 = npad - k2;
   float* P = M + kb * npad + k2;
-  gemm_mid_tile<false, false>((int)n2, (int)n2, NB, P, npad, P, npad, M + k2 * npad + k2, npad,
-                              -1.f, 1.f, 1, 0, 0, 0, tile_i, tile_j);
+  if constexpr (BIG)
+    gemm_big_tile<false, false>((int)n2, (int)n2, NB, P, npad, P, npad, M + k2 * npad + k2, npad,
+                                -1.f, 1.f, 1, 0, 0, 0, tile_i, tile_j);
+  else
+    gemm_mid_tile<false, false>((int)n2, (int)n2, NB, P, npad, P, npad, M + k2 * npad + k2, npad,
+                                -1.f, 1.f, 1, 0, 0, 0, tile_i, tile_j);
   if (tile_i != 0 || tile_j != 0) return;
   __syncthreads();   // the updated block (written by this CTA) before it is factored
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -740,9 +765,51 @@ void launch_scale_cast_T(const void* A, bool a_is_fp64, int64_t lda, int64_t m, 
   count_launch();
 }
 
+// Sum of `chunks` partial npad x npad FP64 Gram matrices (fixed order) into H, mirrored
+__global__ void gram_sum_kernel(const double* __restrict__ part, int chunks, int64_t npad,
+                                double* __restrict__ H) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npad * npad) return;
+  const int64_t r = e / npad, c = e % npad;
+  const int64_t src = (r <= c) ? e : c * npad + r;   // partials hold the upper triangle
+  double a = 0.0;
+  for (int k = 0; k < chunks; ++k) a += part[(int64_t)k * npad * npad + src];
+  H[e] = a;
+}
+
+int gram_split_chunks(int64_t npad, int64_t mpad) {
+  // an FP64 Gram of a few output tiles runs on a few SMs: split its rows into chunks of 32
+  if (npad > 128) return 1;
+  return (int)std::min<int64_t>(64, std::max<int64_t>(1, mpad / 32));
+}
+
 void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
-                      void* H, cudaStream_t s) {
+                      void* H, cudaStream_t s, void* work) {
   const int M = (int)npad, K = (int)mpad;
+  if (prec == Prec::FP64 && work != nullptr) {
+    const int chunks = gram_split_chunks(npad, mpad);
+    if (chunks > 1) {
+      // chunk z: rows [z*kc, min(K, (z+1)*kc)) of A_s^T A_s (upper tiles) into work[z]
+      const int kc = (int)(((int64_t)K + chunks - 1) / chunks);
+      const int full = K / kc, rest = K - full * kc;
+      gemm_simt<double, double, true, true>(M, M, kc, (const double*)AsT, mpad, kc,
+                                            (const double*)AsT, mpad, kc, (double*)work, npad,
+                                            npad * npad, 1.0, 0.0, 1, 0, full, s);
+      int used = full;
+      if (rest > 0) {
+        gemm_simt<double, double, true, true>(M, M, rest, (const double*)AsT + (int64_t)full * kc,
+                                              mpad, 0, (const double*)AsT + (int64_t)full * kc,
+                                              mpad, 0, (double*)work + (int64_t)full * npad * npad,
+                                              npad, 0, 1.0, 0.0, 1, 0, 1, s);
+        ++used;
+      }
+      gram_sum_kernel<<<blocks_for(npad * npad, 256), 256, 0, s>>>((const double*)work, used, npad,
+                                                                  (double*)H);
+      count_launch();
+      launch_set_identity_pad(H, true, n, npad, s);
+      return;
+    }
+  }
   switch (prec) {
     case Prec::FP16:
       gemm_simt<__half, float, true, true>(M, M, K, (const __half*)AsT, mpad, 0, (const __half*)AsT,
@@ -785,8 +852,10 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
   constexpr bool fused = std::is_same<T, float>::value;
   if constexpr (fused) {
     static const bool attr2 = [dsmem] {
-      cudaFuncSetAttribute(chol_update_next_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)dsmem);
+      cudaFuncSetAttribute(chol_update_next_kernel<false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+      cudaFuncSetAttribute(chol_update_next_kernel<true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
       return true;
     }();
     (void)attr2;
@@ -802,8 +871,16 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
                                   0, T(1), T(0), 0, 0, 1, s, info);
     // trailing update H22 -= R_K2^T R_K2 (upper part), then the next diagonal block
     if constexpr (fused) {
-      const unsigned nt = (unsigned)(n2 / NB);
-      chol_update_next_kernel<<<dim3(nt, nt), 256, dsmem, s>>>(M, Wd, npad, kb, info, (int)prec);
+      // 128 x 128 tiles once they still give about two CTAs per SM
+      if (n2 >= 2048) {
+        const unsigned nt = (unsigned)((n2 + 127) / 128);
+        chol_update_next_kernel<true><<<dim3(nt, nt), 256, dsmem, s>>>(M, Wd, npad, kb, info,
+                                                                      (int)prec);
+      } else {
+        const unsigned nt = (unsigned)(n2 / NB);
+        chol_update_next_kernel<false><<<dim3(nt, nt), 256, dsmem, s>>>(M, Wd, npad, kb, info,
+                                                                       (int)prec);
+      }
       count_launch();
     } else {
       T* P = M + kb * npad + kb + NB;

@@ -46,7 +46,7 @@ struct tls_ctx {
   std::vector<DevBuf> bufs;
   // persistent work buffers, reused by every factor / solve while they are large enough (no
   // cudaMalloc / cudaFree, which synchronise the device, between repeated calls)
-  DevBuf slots[16];
+  DevBuf slots[24];
   RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
 
   // problem data (device)
@@ -192,9 +192,9 @@ void dev_free(tls_ctx* c, void* p) {
 
 enum Slot : int {
   kSlotCpart, kSlotInfo, kSlotAsT, kSlotH, kSlotM, kSlotWc, kSlotR, kSlotW, kSlotWT, kSlotWork,
-  kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotFeat, kSlotCount
+  kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotFeat, kSlotGsplit, kSlotCount
 };
-static_assert(kSlotCount <= 16, "slots");
+static_assert(kSlotCount <= 24, "slots");
 
 // A persistent buffer of at least `bytes` for slot `id` (contents not kept when it grows).
 void* slot(tls_ctx* c, int id, size_t bytes) {
@@ -488,8 +488,75 @@ tls_status precond_apply(tls_ctx* ctx, const double* y) {
   return TLS_OK;
 }
 
+// A small dense problem in FP64 (n <= 64 and A, b, W and the vectors within one SM's shared
+// memory) with the default PCGTLS schedule: the whole solve in one CTA (k_small.cu).
+bool small_eligible(const tls_ctx* ctx) {
+  const tls_options& o = ctx->opt;
+  return !ctx->sparse && ctx->u == Prec::FP64 && ctx->n <= 64 && o.mode_A != 0 &&
+         o.cg_fixed != 0 && !ctx->use_sel_tol &&
+         tls::small_solve_smem((int)ctx->m, (int)ctx->n) > 0 &&
+         tls::small_solve_smem((int)ctx->m, (int)ctx->n) <= tls::kSmallSmemMax;
+}
+
+tls_status small_solve(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, double* sigma_out) {
+  const tls_options& o = ctx->opt;
+  cudaStream_t st = ctx->stream;
+  TLS_CK(cudaEventRecord(ctx->ev0, st));
+  tls::SmallParams prm{};
+  prm.tol = tol;
+  prm.psi_accept = o.psi_accept;
+  prm.max_rqi = max_rqi;
+  prm.ls_iters = std::max(1, o.ls_iters);
+  prm.psi_rule_ge = o.psi_rule_ge;
+  auto* dres = reinterpret_cast<tls::SmallResult*>(ctx->gpart);
+  {
+    Prof pr(ctx, TLS_PROF_VEC);
+    if (!tls::launch_small_solve(ctx->A64, ctx->npad, (int)ctx->m, (int)ctx->n, ctx->b,
+                                 ctx->dinv, static_cast<const double*>(ctx->W), ctx->npad,
+                                 ctx->norm2_A + ctx->norm2_b, prm, ctx->x_best, dres, st))
+      return TLS_ERR_ARG;
+  }
+  TLS_CK_LAUNCH("small solve");
+  tls::SmallResult r{};
+  TLS_CK(cudaMemcpyAsync(&r, dres, sizeof(r), cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaEventRecord(ctx->ev1, st));
+  TLS_CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  prof_collect(ctx);
+  if (ctx->factor_time_pending) {
+    float fms = 0.f;
+    if (cudaEventElapsedTime(&fms, ctx->evf0, ctx->evf1) == cudaSuccess) ctx->t_factor_ms = fms;
+    ctx->factor_time_pending = false;
+  }
+  *sigma_out = std::sqrt(std::max(r.sigma2, 0.0));
+  ctx->last_sigma2 = r.sigma2;
+  if (info) {
+    info->stop_reason = r.stop;
+    info->rqi_steps = r.rqi_steps;
+    info->best_k = r.best_k;
+    info->cg_iters = r.cg_iters;
+    info->shifts = ctx->shifts;
+    info->not_spd = r.not_spd;
+    info->u_f_used = ctx->uf_used;
+    info->psi_final = r.psi_final;
+    info->sigma2 = r.sigma2;
+    info->shift = ctx->shift;
+    info->t_factor_ms = ctx->t_factor_ms;
+    info->t_solve_ms = ms;
+    info->fail_pivot = (int)ctx->fail_pivot;
+    info->pass_variant[0] = -1;   // no pass kernels: the one-CTA solve
+    info->pass_variant[1] = -1;
+    info->n_psi = r.n_psi;
+    for (int i = 0; i < r.n_psi; ++i) info->psi_hist[i] = r.psi_hist[i];
+  }
+  return TLS_OK;
+}
+
 template <typename T>
 tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, double* sigma_out) {
+  if constexpr (std::is_same<T, double>::value)
+    if (small_eligible(ctx)) return small_solve(ctx, tol, max_rqi, info, sigma_out);
   const tls_options& o = ctx->opt;
   const bool modeA = o.mode_A != 0;
   UVecs<T> v = uvecs<T>(ctx);
@@ -826,7 +893,13 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
           tc = false;
         }
       }
-      if (!tc) tls::launch_gram_simt(AsT, pf, n, npad, mpad, ctx->H, st);
+      if (!tc) {
+        void* gw = nullptr;
+        const int chunks = tls::gram_split_chunks(npad, mpad);
+        if (pf == Prec::FP64 && chunks > 1)
+          gw = slot(ctx, kSlotGsplit, sizeof(double) * (size_t)chunks * npad * npad);
+        tls::launch_gram_simt(AsT, pf, n, npad, mpad, ctx->H, st, gw);
+      }
       ctx->gram_tc_used = tc;
     }
     }
@@ -1134,7 +1207,7 @@ void tls_default_options(tls_options* opt) {
   opt->cg_tol = 1e-6;
   opt->cg_max = 50;
   opt->psi_rule_ge = 0;
-  opt->ls_iters = 12;
+  opt->ls_iters = 8;
   opt->max_shifts = 3;
   opt->gram_simt = 0;
   opt->shift_first = 1;

@@ -65,6 +65,26 @@ struct RqiScalars {
   unsigned int counter[4];
 };
 
+// One-CTA solve of a small dense problem in FP64 (k_small.cu).
+struct SmallParams {
+  double tol, psi_accept;
+  int max_rqi, ls_iters, psi_rule_ge, pad_;
+};
+struct SmallResult {
+  double sigma2, psi_final;
+  int stop, rqi_steps, best_k, cg_iters, not_spd, n_psi;
+  double psi_hist[24];
+};
+constexpr size_t kSmallSmemMax = 200 * 1024;
+// Shared memory the small solve needs for m x n (0 when n is outside 1..64).
+size_t small_solve_smem(int m, int n);
+// A: m x n of an m x lda FP64 array; W: n x n of an ldw-strided upper-triangular inverse of
+// R_H; dinv: 1 / d; scale = ||A||_F^2 + ||b||^2. Returns false (nothing launched) when the
+// problem does not fit.
+bool launch_small_solve(const double* A, int64_t lda, int m, int n, const double* b,
+                        const double* dinv, const double* W, int64_t ldw, double scale,
+                        const SmallParams& prm, double* x_out, SmallResult* res, cudaStream_t s);
+
 // ---------------------------------------------------------------------------------------
 // Factorisation kernels (k_factor.cu)
 // ---------------------------------------------------------------------------------------
@@ -80,8 +100,11 @@ void launch_scale_cast_T(const void* A, bool a_is_fp64, int64_t lda, int64_t m, 
                          void* AsT, Prec prec, cudaStream_t s);
 // H (npad x npad, type T = float for FP16/BF16/FP32 input, double for FP64) = AsT AsT^T,
 // identity on the padded diagonal.
+// work (may be NULL): for an FP64 Gram of npad <= 128, gram_split_chunks(npad, mpad) partial
+// npad x npad FP64 matrices (the rows are split over that many CTA sets, summed in fixed order).
 void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
-                      void* H, cudaStream_t s);
+                      void* H, cudaStream_t s, void* work = nullptr);
+int gram_split_chunks(int64_t npad, int64_t mpad);
 // tcgen05 (UMMA) Gram for FP16/BF16 input into FP32 H. Returns false if the shape is not
 // supported (falls back to nothing: the caller decides).
 bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,

@@ -179,6 +179,9 @@ CASES = [
     (400, 40, 1e-2, 1e-6, "fp16", "fp32"),
     (64, 1, 1e-1, 1e-3, "fp16", "fp32"),
     (97, 97, 1e-1, 1e-3, "fp64", "fp64"),      # square
+    (400, 40, 1e-2, 1e-6, "fp64", "fp64"),     # the one-CTA solve (n <= 64, FP64)
+    (230, 7, 1e-3, 1e-5, "fp64", "fp64"),      # the one-CTA solve, ragged
+    (64, 64, 1e-1, 1e-3, "fp64", "fp64"),      # the one-CTA solve, square
     (1000, 130, 1e-3, 1e-4, "fp16", "fp32"),   # ragged n
     (1000, 130, 1e-3, 1e-4, "bf16", "fp32"),
     (2500, 300, 1e-3, 1e-4, "fp16", "fp32"),
