@@ -82,6 +82,7 @@ class Clocks:
         self.dev = device_index
         self.proc = None
         self.path = None
+        self.skip = 0
 
     def __enter__(self):
         try:
@@ -92,6 +93,11 @@ class Clocks:
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
+            # let the sampler finish starting (its driver initialisation otherwise overlaps the
+            # first timed steps and slows their launches); samples from before this point are
+            # not the timed region's
+            time.sleep(1.0)
+            self.skip = os.path.getsize(self.path)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -111,23 +117,30 @@ class Clocks:
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
-            for line in fh:
-                f = [x.strip() for x in line.split(",")]
-                if len(f) < 9:
-                    continue
-                try:
-                    sm.append(float(f[1]))
-                    smax.append(float(f[2]))
-                except ValueError:
-                    continue
-                for nm, v in zip(names, f[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
+            lines = fh.read().splitlines()
+        with open(self.path) as fh:
+            fh.seek(self.skip)
+            during = fh.read().splitlines()
+        # only the samples taken while the timed steps ran, unless the region was shorter than
+        # the sampling period (then the nearest ones, taken just before it)
+        in_region = bool(during)
+        for line in during if in_region else lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
         os.unlink(self.path)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "in_timed_region": in_region}
 
 
 def _dist():
@@ -950,7 +963,9 @@ def run_batch(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: enough for a timed region of about half a "
+                         "second, so that the clock sampler sees it)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
@@ -963,6 +978,9 @@ def main():
     ap.add_argument("--selector", action="store_true",
                     help="batch: let the trained selector network pick u_f per problem")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = (10 if args.impl == "reference" or args.workload == "batch"
+                      else 1000 if args.workload == "c1" else 100)
     _set_size(args.m, args.n)
     ws, rank, local = _dist()
     if args.impl == "reference":

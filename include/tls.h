@@ -124,7 +124,8 @@ void tls_default_options(tls_options* opt);
  *   on_device 0: A and b are host pointers; 1: they are device pointers of the current device.
  *   stream    a cudaStream_t (as void*) for all the context's work, or NULL to create one.
  * The context copies A and b into device memory it owns (the caller keeps its buffers).
- * On host pointers the data is checked for NaN/Inf (TLS_ERR_ARG). *out is NULL on error.
+ * The copy is checked for NaN/Inf on the device (TLS_ERR_ARG; one read of the data, host or
+ * device pointers alike). *out is NULL on error.
  */
 tls_status tls_create_dense(tls_ctx** out, int64_t m, int64_t n, const double* A, int64_t lda,
                             const double* b, int on_device, void* stream);
@@ -193,8 +194,9 @@ tls_status tls_solve_batched(int count, tls_ctx* const* ctxs, double tol, int ma
  * is skipped by later launches.
  *
  * tls_batch_create_dense -- count >= 1 problems; problem i has A[i] (m[i] x n[i], row-major,
- *   leading dimension lda[i] >= n[i], FP64) and b[i] (m[i] FP64), host pointers (on_device 0,
- *   checked for NaN/Inf) or device pointers (on_device 1). The batch copies the data; stream
+ *   leading dimension lda[i] >= n[i], FP64) and b[i] (m[i] FP64), host pointers (on_device 0)
+ *   or device pointers (on_device 1); the copies are checked for NaN/Inf on the device (one
+ *   read of the data). The batch copies the data; stream
  *   as in tls_create_dense. Computes the column norms and the FP32 working copy. Errors:
  *   TLS_ERR_ARG (sizes, n > TLS_BATCH_MAX_N, m >= 2^31, non-finite data), TLS_ERR_OOM.
  * tls_batch_factor -- Gram, Cholesky and W = R_H^{-1} of every problem at factor precision
@@ -294,12 +296,34 @@ void tls_shape(const tls_ctx* ctx, int64_t* m, int64_t* n, int64_t* nnz);
 /*
  * tls_set_allocator -- route the library's device allocations through caller functions
  * (e.g. a framework's caching allocator). alloc(bytes, stream, user) returns a device pointer
- * or NULL; release(ptr, bytes, stream, user) frees it. Pass NULLs to restore cudaMalloc /
- * cudaFree. Affects contexts created afterwards. Not thread-safe with concurrent creation.
+ * or NULL; release(ptr, bytes, stream, user) frees it. Pass NULLs to go back to the library's
+ * own block cache (tls_pool_enable). Affects allocations made afterwards; every block is
+ * returned to the allocator that made it, whatever is set when it is freed.
  */
 typedef void* (*tls_alloc_fn)(uint64_t bytes, void* stream, void* user);
 typedef void (*tls_free_fn)(void* ptr, uint64_t bytes, void* stream, void* user);
 void tls_set_allocator(tls_alloc_fn alloc, tls_free_fn release, void* user);
+
+/*
+ * Block cache. Without a caller allocator, the device buffers of contexts and batches, and
+ * their small pinned host buffers, come from a process-wide cache: a destroyed context's
+ * blocks stay allocated (per device, in size classes of 512 B up to 1 MiB and 2 MiB above)
+ * and serve the next context, so that a create / factor / solve / destroy cycle per problem
+ * makes no cudaMalloc, cudaFree (which synchronises the device), cudaMallocHost or
+ * cudaFreeHost call once the cache is warm. Cached blocks are not cleared: the library never
+ * reads a buffer before writing it. A failed cudaMalloc releases the device's cached blocks and
+ * is retried once. Thread-safe.
+ *   tls_pool_enable(on)  on = 1 (default) caches freed blocks; on = 0 releases the cache and
+ *                        frees blocks with cudaFree / cudaFreeHost from then on.
+ *   tls_pool_trim()      releases every cached (unused) block; returns the bytes released.
+ *                        Blocks held by live contexts are untouched.
+ *   tls_pool_stats(...)  bytes cached on devices, cached pinned host bytes, and bytes held by
+ *                        live contexts and batches through the cache or cudaMalloc (all
+ *                        devices); any pointer may be NULL.
+ */
+void tls_pool_enable(int on);
+uint64_t tls_pool_trim(void);
+void tls_pool_stats(uint64_t* cached_device, uint64_t* cached_host, uint64_t* live_device);
 
 /*
  * tls_residual_noalloc -- the FP64 residual block of one RQI step, r = b - A x,

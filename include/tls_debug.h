@@ -104,6 +104,15 @@ tls_status tls_batch_profile_elems(const tls_batch* bt, int cls, int64_t* elems)
 /* Kernels launched by the library since it was loaded (all contexts). */
 uint64_t tls_kernel_launches(void);
 
+/*
+ * tls_pool_poison -- fill every block the library allocates from then on (device blocks from
+ * the cache or from cudaMalloc, with cudaMemsetAsync on the allocating stream; pinned host
+ * blocks with memset) with the byte `value` (0..255; 0xFF makes every FP32 / FP64 word a NaN),
+ * so that a test can show that no result depends on a buffer's previous contents. value < 0
+ * turns it off (the default). Blocks from a caller allocator (tls_set_allocator) are not filled.
+ */
+void tls_pool_poison(int value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,17 @@ __device__ __forceinline__ void ldrow4(const double* p, double (&o)[4]) {
   o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
 }
 
+// 4 consecutive entries from shared memory (16-byte aligned)
+__device__ __forceinline__ void lds4(const float* p, float (&o)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&o)[4]) {
+  const double2 t0 = *reinterpret_cast<const double2*>(p);
+  const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+}
+
 // rounding to the factor precision u_f (Table 2): FP16 / BF16 round to nearest even
 __device__ __forceinline__ float round_uf(float v, int prec) {
   if (prec == (int)Prec::FP16) return __half2float(__float2half_rn(v));
@@ -393,12 +404,12 @@ __global__ void __launch_bounds__(64) gram_kernel(BArrays a, const GTile* __rest
     const C (*B)[kLd] = diag ? SA : SB;
 #pragma unroll 4
     for (int k = 0; k < 32; ++k) {
+      // vector reads from shared memory: 4 loads (FP32) for 64 FMA
       C av[8], bv[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        av[i] = SA[k][ty * 8 + i];
-        bv[i] = B[k][tx * 8 + i];
-      }
+      lds4(&SA[k][ty * 8], *reinterpret_cast<C(*)[4]>(av));
+      lds4(&SA[k][ty * 8 + 4], *reinterpret_cast<C(*)[4]>(av + 4));
+      lds4(&B[k][tx * 8], *reinterpret_cast<C(*)[4]>(bv));
+      lds4(&B[k][tx * 8 + 4], *reinterpret_cast<C(*)[4]>(bv + 4));
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -512,15 +523,6 @@ __device__ __forceinline__ void stage64(const Tin* __restrict__ G, int64_t ld, T
   }
 }
 
-__device__ __forceinline__ void lds4(const float* p, float (&o)[4]) {
-  const float4 t = *reinterpret_cast<const float4*>(p);
-  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-}
-__device__ __forceinline__ void lds4(const double* p, double (&o)[4]) {
-  const double2 t0 = *reinterpret_cast<const double2*>(p);
-  const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
-  o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
-}
 
 // acc += As^T Bs over k = 0..63 for the 4 x 4 outputs of this thread: rows 4 ty .. +3, columns
 // 4 tx .. +3 (tx = tid % 16, ty = tid / 16; 256 threads); As[k][i], Bs[k][j] in shared memory.

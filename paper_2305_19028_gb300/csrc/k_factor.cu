@@ -648,6 +648,113 @@ __global__ void __launch_bounds__(256) chol_update_next_kernel(float* M, float* 
   potrf_inv_diag_body<float>(M, W, npad, k2, info, prec, dsm);
 }
 
+// acc += As^T Bs over k < 64 for the 4 x 4 outputs of this thread (rows 4 ty .. +3, columns
+// 4 tx .. +3; tx = tid % 16, ty = tid / 16; 256 threads); As[k][i], Bs[k][j] in shared memory
+// with row stride LDT (float4 reads).
+constexpr int LDT = 68;
+__device__ __forceinline__ void tile_atb64(const float* As, const float* Bs, float (&acc)[4][4]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 8
+  for (int k = 0; k < NB; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(As + k * LDT + 4 * ty);
+    const float4 b = *reinterpret_cast<const float4*>(Bs + k * LDT + 4 * tx);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+  }
+}
+
+// Block step K with the panel folded in (FP32). CTA (I, J), I <= J, of the trailing tiles forms
+// the panel blocks it needs, P_I = W_KK^T H_KI and P_J = W_KK^T H_KJ (W_KK the inverse of the
+// rounded diagonal block), and updates H_IJ -= P_I^T P_J. The CTA of a diagonal tile (I, I)
+// also stores P_I, transposed, in the unused lower part of M (column block K), from where
+// mirror_panels_kernel copies it into row block K at the end; the CTA of tile (0, 0) then
+// factors and inverts the next diagonal block. One launch per block step instead of two (the
+// panel products are repeated by the CTAs of a tile row and column; the same arithmetic, in the
+// same order, as the separate panel and update products).
+__global__ void __launch_bounds__(256) chol_step_kernel(float* M, float* W, int64_t npad,
+                                                        int64_t kb, int* info, int prec) {
+  if (*(volatile int*)info != 0) return;
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (ti > tj) return;
+  const bool diag = (ti == tj);
+  const int64_t k2 = kb + NB;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float* Wk = reinterpret_cast<float*>(dsm);
+  float* Hi = Wk + NB * LDT;
+  float* Hj = Hi + NB * LDT;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float* Wsrc = W + kb * npad + kb;
+  const float* Ri = M + kb * npad + k2 + (int64_t)ti * NB;
+  const float* Rj = M + kb * npad + k2 + (int64_t)tj * NB;
+  for (int e = tid; e < NB * NB / 4; e += 256) {
+    const int r = e >> 4, c = (e & 15) * 4;
+    *reinterpret_cast<float4*>(Wk + r * LDT + c) =
+        *reinterpret_cast<const float4*>(Wsrc + (int64_t)r * npad + c);
+    *reinterpret_cast<float4*>(Hi + r * LDT + c) =
+        *reinterpret_cast<const float4*>(Ri + (int64_t)r * npad + c);
+    if (!diag)
+      *reinterpret_cast<float4*>(Hj + r * LDT + c) =
+          *reinterpret_cast<const float4*>(Rj + (int64_t)r * npad + c);
+  }
+  __syncthreads();
+  float pi[4][4], pj[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pi[p][q] = pj[p][q] = 0.f;
+  tile_atb64(Wk, Hi, pi);
+  if (!diag) tile_atb64(Wk, Hj, pj);
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    *reinterpret_cast<float4*>(Hi + (4 * ty + p) * LDT + 4 * tx) =
+        make_float4(pi[p][0], pi[p][1], pi[p][2], pi[p][3]);
+    if (!diag)
+      *reinterpret_cast<float4*>(Hj + (4 * ty + p) * LDT + 4 * tx) =
+          make_float4(pj[p][0], pj[p][1], pj[p][2], pj[p][3]);
+  }
+  if (diag) {
+    // P_I transposed into rows k2 + 64 I .. of column block K (below the diagonal)
+    float* low = M + (k2 + (int64_t)ti * NB) * npad + kb;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) low[(int64_t)(4 * tx + q) * npad + 4 * ty + p] = pi[p][q];
+  }
+  __syncthreads();
+  float acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+  tile_atb64(Hi, diag ? Hi : Hj, acc);
+  float* C = M + (k2 + (int64_t)ti * NB) * npad + k2 + (int64_t)tj * NB;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int a = 4 * ty + p, b = 4 * tx + q;
+      if (diag && a > b) continue;
+      float* cp = C + (int64_t)a * npad + b;
+      *cp = -acc[p][q] + *cp;
+    }
+  if (ti != 0 || tj != 0) return;
+  __syncthreads();   // the updated block (written by this CTA) before it is factored
+  potrf_inv_diag_body<float>(M, W, npad, k2, info, prec, dsm);
+}
+
+// Row blocks K >= kb_from kept their panels transposed below the diagonal (chol_step_kernel):
+// M[r][c] = M[c][r] for r in those row blocks and c right of their diagonal block.
+__global__ void mirror_panels_kernel(float* M, int64_t npad, int64_t kb_from) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npad * npad) return;
+  const int64_t r = e / npad, c = e % npad;
+  if (r >= kb_from && c >= (r / NB + 1) * NB) M[e] = M[c * npad + r];
+}
+
 template <typename T>
 __global__ void zero_lower_kernel(T* M, int64_t npad) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -709,7 +816,30 @@ __global__ void d2f_kernel(const double* in, float* out, int64_t count) {
 
 inline int blocks_for(int64_t count, int threads) { return (int)((count + threads - 1) / threads); }
 
+// Sets *flag = 1 when one of the `count` FP64 values at p (16-byte aligned) is NaN or infinite.
+// Grid-stride, 16-byte loads: one read of the data at copy bandwidth.
+__global__ void __launch_bounds__(256) nonfinite_kernel(const double* __restrict__ p,
+                                                        int64_t count, int* __restrict__ flag) {
+  const double2* p2 = reinterpret_cast<const double2*>(p);
+  const int64_t n2 = count / 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const double2 v = p2[i];
+    bad |= !(isfinite(v.x) && isfinite(v.y));
+  }
+  if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0) bad |= !isfinite(p[count - 1]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 }  // namespace
+
+void launch_nonfinite(const double* p, int64_t count, int* flag, int num_sms, cudaStream_t s) {
+  if (count <= 0) return;
+  const int64_t want = (count / 2 + 255) / 256;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms * 8));
+  nonfinite_kernel<<<grid, 256, 0, s>>>(p, count, flag); count_launch();
+}
 
 // =========================================================================================
 void launch_colnorm(const double* A, int64_t lda, int64_t m, int64_t n, int64_t npad,
@@ -862,9 +992,28 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
   }
   potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, 0, info, (int)prec);
   count_launch();
+  int64_t kb_from = npad;   // first block step with the panel folded into the update
   for (int64_t kb = 0; kb < npad; kb += NB) {
     const int64_t n2 = npad - kb - NB;
     if (n2 <= 0) break;
+    if constexpr (fused) {
+      // one launch per step while the trailing tiles fit in about four CTAs per SM (the panel
+      // products are then repeated at little cost and the step is the diagonal block's chain)
+      const int64_t nt = n2 / NB;
+      if (nt * (nt + 1) / 2 <= 4 * 152) {
+        static const bool attr3 = [] {
+          cudaFuncSetAttribute(chol_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(3 * NB * LDT * sizeof(float)));
+          return true;
+        }();
+        (void)attr3;
+        if (kb_from == npad) kb_from = kb;
+        chol_step_kernel<<<dim3((unsigned)nt, (unsigned)nt), 256, 3 * NB * LDT * sizeof(float),
+                           s>>>(M, Wd, npad, kb, info, (int)prec);
+        count_launch();
+        continue;
+      }
+    }
     // panel R_KJ = W_KK^T H_KJ, in place over H_KJ
     gemm_simt<T, T, false, false>(NB, (int)n2, NB, Wd + kb * npad + kb, npad, 0,
                                   M + kb * npad + kb + NB, npad, 0, M + kb * npad + kb + NB, npad,
@@ -888,6 +1037,12 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
       gemm_simt<T, T, false, false>((int)n2, (int)n2, NB, P, npad, 0, P, npad, 0, C, npad, 0,
                                     T(-1), T(1), 1, 0, 1, s, info);
       potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb + NB, info, (int)prec);
+      count_launch();
+    }
+  }
+  if constexpr (fused) {
+    if (kb_from < npad) {
+      mirror_panels_kernel<<<blocks_for(npad * npad, 256), 256, 0, s>>>(M, npad, kb_from);
       count_launch();
     }
   }

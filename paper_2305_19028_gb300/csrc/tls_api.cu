@@ -26,10 +26,6 @@ using tls::RqiScalars;
 
 namespace {
 
-tls_alloc_fn g_alloc = nullptr;
-tls_free_fn g_free = nullptr;
-void* g_alloc_user = nullptr;
-
 struct DevBuf {
   void* ptr = nullptr;
   size_t bytes = 0;
@@ -151,24 +147,6 @@ tls_status cuda_status(tls_ctx* c, cudaError_t e, const char* what) {
 
 }  // namespace
 
-namespace tls {
-void* hook_alloc(size_t bytes, cudaStream_t s) {
-  if (bytes == 0) bytes = 16;
-  void* p = nullptr;
-  if (g_alloc) {
-    p = g_alloc((uint64_t)bytes, (void*)s, g_alloc_user);
-  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    (void)cudaGetLastError();
-    p = nullptr;
-  }
-  return p;
-}
-void hook_free(void* p, size_t bytes, cudaStream_t s) {
-  if (!p) return;
-  if (g_free) g_free(p, (uint64_t)bytes, (void*)s, g_alloc_user);
-  else cudaFree(p);
-}
-}  // namespace tls
 
 namespace {
 
@@ -235,9 +213,13 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   TLS_CK(cudaEventCreate(&ctx->ev1));
   TLS_CK(cudaEventCreate(&ctx->evf0));
   TLS_CK(cudaEventCreate(&ctx->evf1));
-  TLS_CK(cudaMallocHost(&ctx->h_rs, sizeof(RqiScalars)));
-  TLS_CK(cudaMallocHost(&ctx->h_sc, sizeof(PcgScalars)));
-  TLS_CK(cudaMallocHost(&ctx->h_norm, 2 * sizeof(RqiScalars)));
+  ctx->h_rs = static_cast<RqiScalars*>(tls::host_alloc(sizeof(RqiScalars)));
+  ctx->h_sc = static_cast<PcgScalars*>(tls::host_alloc(sizeof(PcgScalars)));
+  ctx->h_norm = static_cast<RqiScalars*>(tls::host_alloc(2 * sizeof(RqiScalars)));
+  if (!ctx->h_rs || !ctx->h_sc || !ctx->h_norm) {
+    set_err(ctx, "pinned host allocation failed");
+    return TLS_ERR_OOM;
+  }
   const int64_t npad = ctx->npad;
   ctx->b = alloc_t<double>(ctx, m);
   ctx->x = alloc_t<double>(ctx, npad);
@@ -284,9 +266,9 @@ void destroy_ctx(tls_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   while (!ctx->bufs.empty()) dev_free(ctx, ctx->bufs.back().ptr);
-  if (ctx->h_rs) cudaFreeHost(ctx->h_rs);
-  if (ctx->h_norm) cudaFreeHost(ctx->h_norm);
-  if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
+  tls::host_free(ctx->h_rs);
+  tls::host_free(ctx->h_norm);
+  tls::host_free(ctx->h_sc);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->evf0) cudaEventDestroy(ctx->evf0);
@@ -1233,11 +1215,6 @@ const char* tls_status_str(tls_status s) {
 
 const char* tls_last_error(const tls_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
 
-void tls_set_allocator(tls_alloc_fn alloc, tls_free_fn release, void* user) {
-  g_alloc = alloc;
-  g_free = release;
-  g_alloc_user = user;
-}
 
 void tls_shape(const tls_ctx* ctx, int64_t* m, int64_t* n, int64_t* nnz) {
   if (!ctx) return;
@@ -1251,11 +1228,6 @@ tls_status tls_create_dense(tls_ctx** out, int64_t m, int64_t n, const double* A
   if (!out) return TLS_ERR_ARG;
   *out = nullptr;
   if (m < 1 || n < 1 || m < n || lda < n || !A || !b) return TLS_ERR_ARG;
-  if (!on_device) {
-    for (int64_t i = 0; i < m; ++i)
-      if (!finite_all(A + i * lda, n)) return TLS_ERR_ARG;
-    if (!finite_all(b, m)) return TLS_ERR_ARG;
-  }
   tls_ctx* ctx = new tls_ctx();
   tls_options o;
   tls_default_options(&o);
@@ -1266,16 +1238,34 @@ tls_status tls_create_dense(tls_ctx** out, int64_t m, int64_t n, const double* A
   ctx->A64 = alloc_t<double>(ctx, m * npad);
   if (!ctx->A64) { destroy_ctx(ctx); return TLS_ERR_OOM; }
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaError_t e = cudaMemsetAsync(ctx->A64, 0, sizeof(double) * m * npad, ctx->stream);
+  // zero padding columns n .. npad-1, the copy, then the NaN / Inf check on the device copy
+  // (one read at copy bandwidth instead of a host pass over the caller's data); the error word
+  // (zero until a solve) serves as its flag
+  cudaError_t e = cudaSuccess;
+  if (npad > n)
+    e = cudaMemset2DAsync(ctx->A64 + n, sizeof(double) * npad, 0, sizeof(double) * (npad - n),
+                          m, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(ctx->A64, sizeof(double) * npad, A, sizeof(double) * lda,
                           sizeof(double) * n, m, kind, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->b, b, sizeof(double) * m, kind, ctx->stream);
+  int bad = 0;
+  if (e == cudaSuccess) {
+    tls::launch_nonfinite(ctx->A64, m * npad, ctx->derr, ctx->num_sms, ctx->stream);
+    tls::launch_nonfinite(ctx->b, m, ctx->derr, ctx->num_sms, ctx->stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&bad, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     tls_status st = cuda_status(ctx, e, "upload");
     destroy_ctx(ctx);
     return st;
+  }
+  if (bad) {
+    destroy_ctx(ctx);
+    return TLS_ERR_ARG;   // NaN or Inf in A or b
   }
   *out = ctx;
   return TLS_OK;

@@ -228,7 +228,7 @@ void destroy(tls_batch* bt) {
   for (cudaEvent_t e : bt->evpool) cudaEventDestroy(e);
   for (auto& g : bt->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& b : bt->bufs) tls::hook_free(b.first, b.second, bt->stream);
-  if (bt->hcount) cudaFreeHost(bt->hcount);
+  tls::host_free(bt->hcount);
   if (bt->ev0) cudaEventDestroy(bt->ev0);
   if (bt->ev1) cudaEventDestroy(bt->ev1);
   if (bt->own_stream && bt->stream) cudaStreamDestroy(bt->stream);
@@ -770,13 +770,6 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
     if (m[i] < n[i] || n[i] < 1 || n[i] > TLS_BATCH_MAX_N || lda[i] < n[i] || !A[i] || !b[i] ||
         m[i] > (int64_t)INT32_MAX)
       return TLS_ERR_ARG;
-    if (!on_device) {
-      for (int64_t r = 0; r < m[i]; ++r)
-        for (int64_t c = 0; c < n[i]; ++c)
-          if (!std::isfinite(A[i][r * lda[i] + c])) return TLS_ERR_ARG;
-      for (int64_t r = 0; r < m[i]; ++r)
-        if (!std::isfinite(b[i][r])) return TLS_ERR_ARG;
-    }
   }
   tls_batch* bt = new tls_batch();
   bt->count = count;
@@ -866,10 +859,13 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   a.tiles = bt->dtiles;
   a.st = bt->dst;
   cudaStream_t st = bt->stream;
-  cudaError_t e = cudaMallocHost(&bt->hcount, 4 * sizeof(int));
+  bt->hcount = static_cast<int*>(tls::host_alloc(4 * sizeof(int)));
+  cudaError_t e = bt->hcount ? cudaSuccess : cudaErrorMemoryAllocation;
   if (e == cudaSuccess) e = cudaEventCreate(&bt->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&bt->ev1);
   if (e == cudaSuccess) e = cudaMemsetAsync(A64, 0, sizeof(double) * (size_t)offA, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bb, 0, sizeof(double) * (size_t)offB, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->dcount, 0, 4 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(bt->dst, 0, sizeof(BState) * count, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.H, 0, sizeof(double) * (size_t)offM, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.vw, 0, 2 * vbytes, st);
@@ -884,6 +880,22 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
                           sizeof(double) * P.n, P.m, kind, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(bb + P.offB, b[i], sizeof(double) * P.m, kind, st);
+  }
+  // NaN / Inf check on the device copy (padding is zero): one read at copy bandwidth
+  if (e == cudaSuccess) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    tls::launch_nonfinite(A64, offA, bt->dcount, sms, st);
+    tls::launch_nonfinite(bb, offB, bt->dcount, sms, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->hcount, bt->dcount, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && bt->hcount[0] != 0) {
+    destroy(bt);
+    return TLS_ERR_ARG;   // NaN or Inf in some A_i or b_i
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(bt->dprobs, bt->hp.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice, st);

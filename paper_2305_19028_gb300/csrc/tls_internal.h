@@ -27,9 +27,13 @@ namespace mlp {
 void launch_mlp_forward(const float* P, int nsamp, const float* X, float* out, cudaStream_t s);
 }
 
-// Device allocation through the caller's allocator (tls_set_allocator) or cudaMalloc.
+// Device allocation through the caller's allocator (tls_set_allocator), the library's block
+// cache or cudaMalloc; hook_free returns a block to where it came from (pool.cu).
 void* hook_alloc(size_t bytes, cudaStream_t s);
 void hook_free(void* p, size_t bytes, cudaStream_t s);
+// Pinned host blocks (cached like the device blocks).
+void* host_alloc(size_t bytes);
+void host_free(void* p);
 
 // Device scalars of one paired PCGTLS solve (Alg. 3), per right-hand side r in {0, 1}.
 struct PcgScalars {
@@ -88,6 +92,9 @@ bool launch_small_solve(const double* A, int64_t lda, int m, int n, const double
 // ---------------------------------------------------------------------------------------
 // Factorisation kernels (k_factor.cu)
 // ---------------------------------------------------------------------------------------
+// *flag |= 1 when one of the `count` FP64 values at p (device, 16-byte aligned) is NaN or
+// infinite (the input check of the create calls, on the device copy).
+void launch_nonfinite(const double* p, int64_t count, int* flag, int num_sms, cudaStream_t s);
 // Column squared norms of A (m x n, row-major, lda) with an optional FP32 copy A32 (ld ldo).
 // d_out[j] = sqrt(sum_i a_ij^2) (FP64 out). part: scratch of grid x ld doubles.
 void launch_colnorm(const double* A, int64_t lda, int64_t m, int64_t n, int64_t npad,

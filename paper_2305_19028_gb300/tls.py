@@ -36,7 +36,8 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_batch_export_factor", "tls_batch_profile_enable", "tls_batch_profile_get",
            "tls_batch_profile_elems", "tls_mlp_forward", "tls_mlp_grad", "tls_mlp_adam",
            "tls_batch_set_selector", "tls_batch_features", "tls_set_pass_variant",
-           "tls_set_selector", "tls_features"]
+           "tls_set_selector", "tls_features", "tls_pool_enable", "tls_pool_trim",
+           "tls_pool_stats", "tls_pool_poison"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
@@ -72,7 +73,7 @@ class TLSError(RuntimeError):
 
 
 _LIB = None
-_ALLOC_REFS = None
+_ALLOC_REFS: list = []
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
 
@@ -103,6 +104,10 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_last_error": (C.c_char_p, [v]),
         "tls_shape": (None, [v, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
         "tls_set_allocator": (None, [v, v, v]),
+        "tls_pool_enable": (None, [C.c_int]),
+        "tls_pool_trim": (C.c_uint64, []),
+        "tls_pool_stats": (None, [C.POINTER(C.c_uint64)] * 3),
+        "tls_pool_poison": (None, [C.c_int]),
         "tls_export_factor": (C.c_int, [v, _dp, _dp, _dp]),
         "tls_residual": (C.c_int, [v, _dp, _dp, _dp]),
         "tls_pcgtls": (C.c_int, [v, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp, _dp,
@@ -382,13 +387,32 @@ def tls_residual_noalloc(A, b, x, f, scal, stream=None):
     return status
 
 
+def tls_pool_enable(on: bool = True) -> None:
+    """Cache freed device / pinned host blocks for later contexts (default on)."""
+    load().tls_pool_enable(1 if on else 0)
+
+
+def tls_pool_trim() -> int:
+    """Release every cached block; returns the bytes released."""
+    return int(load().tls_pool_trim())
+
+
+def tls_pool_stats() -> dict:
+    cd, ch, ld = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    load().tls_pool_stats(C.byref(cd), C.byref(ch), C.byref(ld))
+    return {"cached_device": cd.value, "cached_host": ch.value, "live_device": ld.value}
+
+
+def tls_pool_poison(value: int | None) -> None:
+    """Fill every newly allocated block with the byte `value` (None: off)."""
+    load().tls_pool_poison(-1 if value is None else int(value))
+
+
 def use_torch_allocator(enable: bool = True):
     """Route the library's device allocations through torch's caching allocator."""
-    global _ALLOC_REFS
     lib = load()
     if not enable:
         lib.tls_set_allocator(None, None, None)
-        _ALLOC_REFS = None
         return
     import torch
 
@@ -406,7 +430,9 @@ def use_torch_allocator(enable: bool = True):
         torch.cuda.caching_allocator_delete(ptr)
 
     a, f = ALLOC(_alloc), FREE(_free)
-    _ALLOC_REFS = (a, f)
+    # kept for the life of the process: blocks made through them return to them when freed,
+    # whatever allocator is set by then
+    _ALLOC_REFS.append((a, f))
     lib.tls_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), None)
 
 

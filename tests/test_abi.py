@@ -63,16 +63,31 @@ def test_create_rejects_bad_shapes_without_device():
     assert st == 1
 
 
-def test_create_rejects_nan_inf_on_host():
-    A = np.ones((6, 2))
-    A[2, 1] = np.nan
-    st, ctx = _create(6, 2, A, np.ones(6))
-    assert st == 1 and not ctx.value
-    A[2, 1] = 1.0
-    b = np.ones(6)
-    b[0] = np.inf
-    st, _ = _create(6, 2, A, b)
-    assert st == 1
+@pytest.mark.gpu
+def test_create_rejects_nan_inf():
+    """NaN / Inf in A or b: TLS_ERR_ARG from the device-side check of the copy, for host and
+    device pointers, the single context and the packed batch; the pool keeps working after."""
+    import torch
+    A = np.ones((70, 5))
+    A[::3, 1] = 2.0
+    b = np.arange(70.0)
+    for where in ("A", "b"):
+        for bad in (np.nan, np.inf, -np.inf):
+            A2, b2 = A.copy(), b.copy()
+            if where == "A":
+                A2[69, 4] = bad
+            else:
+                b2[0] = bad
+            st, ctx = _create(70, 5, A2, b2)
+            assert st == 1 and not ctx.value
+            with pytest.raises(tls.TLSError) as ei:
+                tls.tls_create_dense(torch.from_numpy(A2).cuda(), torch.from_numpy(b2).cuda())
+            assert ei.value.status == 1
+            with pytest.raises(tls.TLSError) as ei:
+                tls.Batch([(A, b), (A2, b2)])
+            assert ei.value.status == 1
+    ctx = tls.tls_create_dense(A, b)        # a clean problem still creates
+    tls.tls_destroy(ctx)
 
 
 def test_csr_validation_on_host():
