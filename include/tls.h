@@ -135,7 +135,12 @@ tls_status tls_create_dense(tls_ctx** out, int64_t m, int64_t n, const double* A
  *   row_ptr   m + 1 int64 offsets, row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz;
  *   col_idx   nnz int32 column indices in [0, n), strictly increasing within each row;
  *   val       nnz FP64 values.
- * Host pointers only (on_device must be 0); the structure is validated on the host.
+ * Host pointers only (on_device must be 0). row_ptr[0] and row_ptr[m] are checked on the host;
+ * after the upload one kernel checks the rest of the structure and that val and b are finite
+ * (TLS_ERR_ARG), before anything indexes with col_idx. The column (CSC) index the A^T products
+ * gather through is then built on the device (a stable counting sort by column; entries of a
+ * column in increasing row order). n <= 51200 (TLS_ERR_ARG above: the per-warp column counters
+ * of that sort live in shared memory).
  */
 tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz,
                           const int64_t* row_ptr, const int32_t* col_idx, const double* val,

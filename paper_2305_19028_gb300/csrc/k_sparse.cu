@@ -9,6 +9,8 @@
 #include "tls_internal.h"
 #include "tls_device.cuh"
 
+#include <algorithm>
+
 namespace tls {
 
 namespace {
@@ -364,7 +366,202 @@ __global__ void __launch_bounds__(kT) csc_pcg_kernel(const int* __restrict__ cp,
 
 inline int nblk(int64_t count, int threads) { return (int)((count + threads - 1) / threads); }
 
+// ---------------------------------------------------------------------------------------
+// The column (CSC) index, built on the device from the uploaded CSR arrays: a stable counting
+// sort of the entries by column (entries of a column in increasing row order). The row ranges
+// are split over G CTAs of W warps, warp g of all G W taking rows [m g / (G W), m (g+1) / (G W)).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void warp_rows(int64_t m, int W, int64_t* r0, int64_t* r1) {
+  const int64_t g = (int64_t)blockIdx.x * W + (threadIdx.x >> 5);
+  const int64_t GW = (int64_t)gridDim.x * W;
+  *r0 = m * g / GW;
+  *r1 = m * (g + 1) / GW;
+}
+
+// Structure and value check, one warp per row: row offsets non-decreasing from 0 to nnz,
+// column indices in [0, n) and strictly increasing within the row, values and b finite. Writes
+// the 32-bit row offsets. *bad = 1 on any violation (nothing below runs on a bad structure).
+__global__ void __launch_bounds__(kT) csr_check_kernel(const int64_t* __restrict__ rp64,
+                                                       const int* __restrict__ ci,
+                                                       const double* __restrict__ v64,
+                                                       const double* __restrict__ b, int64_t m,
+                                                       int64_t n, int64_t nnz,
+                                                       int* __restrict__ rp32,
+                                                       int* __restrict__ bad) {
+  const int64_t r = (int64_t)blockIdx.x * kW + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= m) return;
+  const int64_t lo = rp64[r], hi = rp64[r + 1];
+  bool err = lo < 0 || hi < lo || hi > nnz;
+  if (!err) {
+    for (int64_t e = lo + lane; e < hi; e += 32) {
+      const int c = ci[e];
+      err |= c < 0 || c >= n || !isfinite(v64[e]) || (e > lo && ci[e - 1] >= c);
+    }
+  }
+  if (lane == 0) {
+    err |= !isfinite(b[r]);
+    rp32[r] = (int)lo;
+    if (r == m - 1) rp32[m] = (int)nnz;
+  }
+  if (__any_sync(0xffffffffu, err) && lane == 0) atomicOr(bad, 1);
+}
+
+// Column counts of each CTA's rows: cnt[blockIdx.x * npad + c]. Dynamic shared memory: W
+// counters of npad ints (one set per warp, summed at the end).
+__global__ void __launch_bounds__(kT) csc_count_kernel(const int* __restrict__ rp32,
+                                                       const int* __restrict__ ci, int64_t m,
+                                                       int64_t npad, int W,
+                                                       int* __restrict__ cnt) {
+  extern __shared__ int sc_cnt[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t k = threadIdx.x; k < (int64_t)W * npad; k += blockDim.x) sc_cnt[k] = 0;
+  __syncthreads();
+  if (warp < W) {
+    int64_t r0, r1;
+    warp_rows(m, W, &r0, &r1);
+    int* mine = sc_cnt + (int64_t)warp * npad;
+    for (int64_t e = rp32[r0] + lane; e < rp32[r1]; e += 32) atomicAdd(&mine[ci[e]], 1);
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < npad; c += blockDim.x) {
+    int t = 0;
+    for (int w = 0; w < W; ++w) t += sc_cnt[(int64_t)w * npad + c];
+    cnt[(int64_t)blockIdx.x * npad + c] = t;
+  }
+}
+
+// Per column: off[g * npad + c] = entries of column c in CTAs before g; tot[c] = all of them.
+__global__ void csc_colscan_kernel(const int* __restrict__ cnt, int G, int64_t npad,
+                                   int* __restrict__ off, int* __restrict__ tot) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= npad) return;
+  int run = 0;
+#pragma unroll 8
+  for (int g = 0; g < G; ++g) {
+    const int t = cnt[(int64_t)g * npad + c];
+    off[(int64_t)g * npad + c] = run;
+    run += t;
+  }
+  tot[c] = run;
+}
+
+// cp[0..npad] = exclusive prefix sums of tot (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) csc_ptr_kernel(const int* __restrict__ tot, int64_t npad,
+                                                       int* __restrict__ cp) {
+  __shared__ int wsums[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t per = (npad + 1023) / 1024;
+  const int64_t c0 = tid * per, c1 = min(npad, c0 + per);
+  int seg = 0;
+  for (int64_t c = c0; c < c1; ++c) seg += tot[c];
+  // exclusive scan of the segment sums over the block
+  int incl = seg;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsums[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += v;
+    }
+    wsums[lane] = w;
+  }
+  __syncthreads();
+  int run = incl - seg + (warp > 0 ? wsums[warp - 1] : 0);
+  for (int64_t c = c0; c < c1; ++c) {
+    cp[c] = run;
+    run += tot[c];
+  }
+  if (tid == 1023) cp[npad] = run;
+}
+
+// Scatter: each warp walks its rows in order and places row r's entries at the next free slot
+// of their columns, starting from cp[c] + off[cta][c] + the counts of the CTA's earlier warps.
+// (Columns are distinct within a row, so the lanes of one row never share a counter; the warp
+// synchronises between rows so that a later row sees the earlier rows' increments.)
+__global__ void __launch_bounds__(kT) csc_scatter_kernel(const int* __restrict__ rp32,
+                                                         const int* __restrict__ ci,
+                                                         const double* __restrict__ v64,
+                                                         int64_t m, int64_t npad, int64_t nnz,
+                                                         int W, const int* __restrict__ cp,
+                                                         const int* __restrict__ off,
+                                                         int* __restrict__ ri,
+                                                         double* __restrict__ cv) {
+  extern __shared__ int sc_cnt[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t k = threadIdx.x; k < (int64_t)W * npad; k += blockDim.x) sc_cnt[k] = 0;
+  __syncthreads();
+  int64_t r0 = 0, r1 = 0;
+  if (warp < W) {
+    warp_rows(m, W, &r0, &r1);
+    int* mine = sc_cnt + (int64_t)warp * npad;
+    for (int64_t e = rp32[r0] + lane; e < rp32[r1]; e += 32) atomicAdd(&mine[ci[e]], 1);
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < npad; c += blockDim.x) {
+    int run = cp[c] + off[(int64_t)blockIdx.x * npad + c];
+    for (int w = 0; w < W; ++w) {
+      const int t = sc_cnt[(int64_t)w * npad + c];
+      sc_cnt[(int64_t)w * npad + c] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  if (warp >= W) return;
+  int* next = sc_cnt + (int64_t)warp * npad;
+  for (int64_t r = r0; r < r1; ++r) {
+    const int lo = rp32[r], hi = rp32[r + 1];
+    for (int e = lo + lane; e < hi; e += 32) {
+      const int c = ci[e];
+      const int pos = next[c];
+      next[c] = pos + 1;
+      if (pos < nnz) {
+        ri[pos] = (int)r;
+        cv[pos] = v64[e];
+      }
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
+
+int csc_build_warps(int64_t npad) {
+  const int64_t w = (int64_t)(200 * 1024) / (npad * (int64_t)sizeof(int));
+  return (int)std::min<int64_t>(kW, w);
+}
+
+void csr_check(const int64_t* rp64, const int* ci, const double* v64, const double* b, int64_t m,
+               int64_t n, int64_t nnz, int* rp32, int* bad, cudaStream_t s) {
+  csr_check_kernel<<<nblk(m, kW), kT, 0, s>>>(rp64, ci, v64, b, m, n, nnz, rp32, bad);
+  count_launch();
+}
+
+void csc_build(const int* rp32, const int* ci, const double* v64, int64_t m, int64_t npad,
+               int64_t nnz, int G, int* cnt, int* off, int* tot, int* cp, int* ri, double* cv,
+               cudaStream_t s) {
+  const int W = csc_build_warps(npad);
+  const size_t smem = sizeof(int) * (size_t)W * (size_t)npad;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(csc_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(csc_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    return true;
+  }();
+  (void)attr;
+  csc_count_kernel<<<G, kT, smem, s>>>(rp32, ci, m, npad, W, cnt);
+  csc_colscan_kernel<<<nblk(npad, 256), 256, 0, s>>>(cnt, G, npad, off, tot);
+  csc_ptr_kernel<<<1, 1024, 0, s>>>(tot, npad, cp);
+  csc_scatter_kernel<<<G, kT, smem, s>>>(rp32, ci, v64, m, npad, nnz, W, cp, off, ri, cv);
+  count_launch(4);
+}
 
 // =========================================================================================
 void sparse_to_f32(const double* v64, float* v32, int64_t nnz, cudaStream_t s) {

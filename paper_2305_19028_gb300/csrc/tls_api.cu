@@ -190,11 +190,6 @@ T* alloc_t(tls_ctx* c, int64_t count) {
   return static_cast<T*>(dev_alloc(c, sizeof(T) * (size_t)count));
 }
 
-bool finite_all(const double* p, int64_t count) {
-  for (int64_t i = 0; i < count; ++i)
-    if (!std::isfinite(p[i])) return false;
-  return true;
-}
 
 tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->m = m;
@@ -1280,32 +1275,8 @@ tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz, cons
   if (nnz > 0 && (!col_idx || !val)) return TLS_ERR_ARG;
   if (nnz >= (int64_t)1 << 31 || m >= (int64_t)1 << 31) return TLS_ERR_ARG;
   if (row_ptr[0] != 0 || row_ptr[m] != nnz) return TLS_ERR_ARG;
-  if (!finite_all(b, m)) return TLS_ERR_ARG;
   const int64_t npad = tls::round_up(n, tls::kPad);
-  // validate, and build the column (CSC) index: a transpose of the sparsity structure, entries
-  // of each column in increasing row order
-  std::vector<int> rp32((size_t)m + 1), cp32((size_t)npad + 1, 0);
-  for (int64_t i = 0; i < m; ++i) {
-    if (row_ptr[i + 1] < row_ptr[i]) return TLS_ERR_ARG;
-    rp32[(size_t)i] = (int)row_ptr[i];
-    int64_t prev = -1;
-    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-      const int64_t c = col_idx[e];
-      if (c < 0 || c >= n || c <= prev || !std::isfinite(val[e])) return TLS_ERR_ARG;
-      prev = c;
-      cp32[(size_t)c + 1] += 1;
-    }
-  }
-  rp32[(size_t)m] = (int)nnz;
-  for (int64_t j = 0; j < npad; ++j) cp32[(size_t)j + 1] += cp32[(size_t)j];
-  std::vector<int> ri32((size_t)nnz), fill(cp32.begin(), cp32.end() - 1);
-  std::vector<double> cv((size_t)nnz);
-  for (int64_t i = 0; i < m; ++i)
-    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-      const int pos = fill[(size_t)col_idx[e]]++;
-      ri32[(size_t)pos] = (int)i;
-      cv[(size_t)pos] = val[e];
-    }
+  if (tls::csc_build_warps(npad) < 1) return TLS_ERR_ARG;   // n too large for the CSC build
   tls_ctx* ctx = new tls_ctx();
   tls_options o;
   tls_default_options(&o);
@@ -1315,6 +1286,7 @@ tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz, cons
   ctx->sparse = true;
   ctx->nnz = nnz;
   const int64_t nz = std::max<int64_t>(nnz, 1);
+  const int G = ctx->num_sms;
   ctx->rp = alloc_t<int>(ctx, m + 1);
   ctx->ci = alloc_t<int>(ctx, nz);
   ctx->v64 = alloc_t<double>(ctx, nz);
@@ -1324,20 +1296,39 @@ tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz, cons
   ctx->cv64 = alloc_t<double>(ctx, nz);
   ctx->cv32 = alloc_t<float>(ctx, nz);
   ctx->rbuf = alloc_t<double>(ctx, m);
+  // creation scratch (returned at the end): 64-bit row offsets, per-CTA column counts
+  int64_t* rp64 = alloc_t<int64_t>(ctx, m + 1);
+  int* work = alloc_t<int>(ctx, (int64_t)2 * G * npad + npad);
   if (!ctx->rp || !ctx->ci || !ctx->v64 || !ctx->v32 || !ctx->cp || !ctx->ri || !ctx->cv64 ||
-      !ctx->cv32 || !ctx->rbuf) {
+      !ctx->cv32 || !ctx->rbuf || !rp64 || !work) {
     destroy_ctx(ctx);
     return TLS_ERR_OOM;
   }
+  // upload; check the structure and the values on the device (the error word, zero until a
+  // solve, is the flag) before anything indexes with the column indices; then the column
+  // (CSC) index as a stable counting sort by column, also on the device
   cudaStream_t sm = ctx->stream;
-  cudaError_t e = cudaMemcpyAsync(ctx->rp, rp32.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, sm);
+  int bad = 0;
+  cudaError_t e = cudaMemcpyAsync(rp64, row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, sm);
   if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(ctx->ci, col_idx, sizeof(int) * nnz, cudaMemcpyHostToDevice, sm);
   if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(ctx->v64, val, sizeof(double) * nnz, cudaMemcpyHostToDevice, sm);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->cp, cp32.data(), sizeof(int) * (npad + 1), cudaMemcpyHostToDevice, sm);
-  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(ctx->ri, ri32.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, sm);
-  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(ctx->cv64, cv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, sm);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->b, b, sizeof(double) * m, cudaMemcpyHostToDevice, sm);
   if (e == cudaSuccess) {
+    tls::csr_check(rp64, ctx->ci, ctx->v64, ctx->b, m, n, nnz, ctx->rp, ctx->derr, sm);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, sm);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+  if (e == cudaSuccess && bad) {
+    destroy_ctx(ctx);
+    return TLS_ERR_ARG;   // malformed structure or NaN / Inf values
+  }
+  if (e == cudaSuccess) {
+    int* cnt = work;
+    int* off = work + (int64_t)G * npad;
+    int* tot = work + (int64_t)2 * G * npad;
+    tls::csc_build(ctx->rp, ctx->ci, ctx->v64, m, npad, nnz, G, cnt, off, tot, ctx->cp, ctx->ri,
+                   ctx->cv64, sm);
     tls::sparse_to_f32(ctx->v64, ctx->v32, nnz, sm);
     tls::sparse_to_f32(ctx->cv64, ctx->cv32, nnz, sm);
     e = cudaGetLastError();
@@ -1348,6 +1339,8 @@ tls_status tls_create_csr(tls_ctx** out, int64_t m, int64_t n, int64_t nnz, cons
     destroy_ctx(ctx);
     return s2;
   }
+  dev_free(ctx, work);
+  dev_free(ctx, rp64);
   *out = ctx;
   return TLS_OK;
 }

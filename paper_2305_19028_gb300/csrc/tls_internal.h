@@ -262,5 +262,16 @@ void sparse_pcg_pass(const int* rp, const int* ci, const T* val, const int* cp, 
                      T* w, T* y, const T* dinv, PcgScalars* sc, double* spart, double* sout,
                      unsigned int* counter, const int* done, cudaStream_t s);
 int sparse_grid_rows(int64_t m);
+// CSR check on the device: rp64 (m + 1 int64) non-decreasing from 0 to nnz, ci in [0, n) and
+// strictly increasing per row, v64 and b finite; writes rp32; *bad |= 1 on a violation.
+void csr_check(const int64_t* rp64, const int* ci, const double* v64, const double* b, int64_t m,
+               int64_t n, int64_t nnz, int* rp32, int* bad, cudaStream_t s);
+// CSC index of a checked CSR matrix (stable counting sort by column): cp (npad + 1), ri and cv
+// (nnz). G CTAs; scratch cnt and off (G x npad ints each), tot (npad ints). Needs
+// csc_build_warps(npad) >= 1 (npad <= 51200).
+int csc_build_warps(int64_t npad);
+void csc_build(const int* rp32, const int* ci, const double* v64, int64_t m, int64_t npad,
+               int64_t nnz, int G, int* cnt, int* off, int* tot, int* cp, int* ri, double* cv,
+               cudaStream_t s);
 
 }  // namespace tls

@@ -90,23 +90,56 @@ def test_create_rejects_nan_inf():
     tls.tls_destroy(ctx)
 
 
-def test_csr_validation_on_host():
+def _create_csr(m, n, rp, ci, va, b):
     lib = tls.load()
     ctx = C.c_void_p()
-    rp = np.array([0, 2, 3], dtype=np.int64)
-    ci = np.array([1, 0, 0], dtype=np.int32)          # not increasing in row 0
-    va = np.ones(3)
-    b = np.ones(2)
-    st = lib.tls_create_csr(C.byref(ctx), 2, 2, 3, rp.ctypes.data_as(C.c_void_p),
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    va = np.ascontiguousarray(va, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    st = lib.tls_create_csr(C.byref(ctx), m, n, int(rp[-1]), rp.ctypes.data_as(C.c_void_p),
                             ci.ctypes.data_as(C.c_void_p), va.ctypes.data_as(C.c_void_p),
                             b.ctypes.data_as(C.c_void_p), 0, None)
+    if st == 0:
+        lib.tls_destroy(ctx)
+    return st, ctx
+
+
+def test_csr_validation_on_host():
+    """The checks made before any device work: sizes and the two end offsets."""
+    va = np.ones(3)
+    st, ctx = _create_csr(2, 2, [1, 2, 3], [0, 1, 0], va, np.ones(2))      # row_ptr[0] != 0
     assert st == 1 and not ctx.value
+    st, _ = _create_csr(1, 2, [0, 3], [0, 1, 0], va, np.ones(1))           # m < n
+    assert st == 1
+    n = 60000                                                             # n above the limit
+    st, _ = _create_csr(n, n, np.zeros(n + 1), np.zeros(0), np.zeros(0), np.ones(n))
+    assert st == 1
 
 
-def test_null_context_calls_are_rejected():
-    lib = tls.load()
-    assert lib.tls_factor(None, 0, None) == 1
-    x = np.zeros(2)
-    s = C.c_double()
-    assert lib.tls_solve(None, 0.0, 5, x.ctypes.data_as(tls._dp), C.byref(s), None) == 1
-    lib.tls_destroy(None)
+@pytest.mark.gpu
+def test_csr_validation_on_device():
+    """Malformed structure or non-finite data: TLS_ERR_ARG from the device check, before the
+    column index is built; a well-formed matrix still creates afterwards."""
+    m, n = 5, 3
+    rp = [0, 2, 3, 5, 6, 7]
+    ci = [0, 2, 1, 0, 2, 1, 0]
+    va = np.arange(1.0, 8.0)
+    b = np.ones(m)
+    st, _ = _create_csr(m, n, rp, ci, va, b)
+    assert st == 0
+    bad_cases = {
+        "not increasing": (rp, [2, 0, 1, 0, 2, 1, 0], va, b),
+        "duplicate": (rp, [0, 0, 1, 0, 2, 1, 0], va, b),
+        "column >= n": (rp, [0, 3, 1, 0, 2, 1, 0], va, b),
+        "negative column": (rp, [-1, 2, 1, 0, 2, 1, 0], va, b),
+        "row_ptr decreasing": ([0, 2, 1, 5, 6, 7], ci, va, b),
+        "row_ptr beyond nnz": ([0, 2, 9, 5, 6, 7], ci, va, b),
+        "NaN value": (rp, ci, np.where(np.arange(7) == 4, np.nan, va), b),
+        "Inf in b": (rp, ci, va, np.where(np.arange(m) == 4, np.inf, b)),
+    }
+    for name, (rp2, ci2, va2, b2) in bad_cases.items():
+        st, ctx = _create_csr(m, n, rp2, ci2, va2, b2)
+        assert st == 1 and not ctx.value, name
+    st, _ = _create_csr(m, n, rp, ci, va, b)
+    assert st == 0

@@ -64,6 +64,42 @@ def test_sparse_residual_block_matches_oracle():
     assert abs(sc["psi"] - psio) <= 1e-6 * psio + 8 * fscale
 
 
+def test_sparse_column_index_with_long_and_empty_rows():
+    """The device-built column index on rows of 0 to 150 entries (several 32-entry chunks per
+    row; empty rows): the A^T products of the FP64 residual block and the column norms match
+    the dense expansion."""
+    rng = np.random.default_rng(11)
+    m, n = 3000, 150
+    lens = rng.integers(0, 13, size=m)
+    lens[rng.choice(m, 40, replace=False)] = rng.integers(33, n + 1, size=40)
+    lens[:n] = np.maximum(lens[:n], 1)
+    rows = [np.sort(rng.choice(n, k, replace=False)) for k in lens]
+    for i in range(n):                        # every column has an entry (diagonal)
+        if i not in rows[i]:
+            rows[i] = np.sort(np.append(rows[i][1:], i))
+    rp = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum([len(r) for r in rows], out=rp[1:])
+    ci = np.concatenate(rows).astype(np.int32)
+    va = rng.standard_normal(ci.size)
+    A = np.zeros((m, n))
+    for i in range(m):
+        A[i, rows[i]] = va[rp[i]:rp[i + 1]]
+    b = A @ rng.standard_normal(n) + 1e-3 * rng.standard_normal(m)
+    x = rng.standard_normal(n)
+    ctx = tls.tls_create_csr(m, n, rp, ci, va, b)
+    try:
+        f, sc = tls.tls_residual(ctx, x)
+        tls.tls_factor(ctx, "fp64", tls.tls_default_options(u="fp64"))
+        _, d, _ = tls.tls_export_factor(ctx)
+    finally:
+        tls.tls_destroy(ctx)
+    r, s2, fo, go, psio = O.residual_block(A, b, x)
+    fscale = m * U64 * (np.abs(A).T @ (np.abs(A) @ np.abs(x) + np.abs(b))).max()
+    assert np.max(np.abs(f - fo)) <= 8 * fscale
+    d_ref = np.linalg.norm(A, axis=0)
+    assert np.max(np.abs(d - d_ref) / d_ref) <= m * U64
+
+
 @pytest.mark.parametrize("u_f", ["bf16", "fp16"])
 def test_sparse_gram_matches_definition(u_f):
     p = synth.csr_problem(2000, 150, nnz_per_row=12, noise=1e-3, seed=7)
