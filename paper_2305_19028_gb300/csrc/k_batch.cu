@@ -1630,6 +1630,40 @@ void launch_count_active(const BArrays& a, const int* list, int cnt, int* out, i
   count_launch();
 }
 
+namespace {
+// grid (X, njobs): the warps of the X CTAs of job j take its rows in turn; a row is read and
+// written with consecutive lanes on consecutive columns.
+__global__ void __launch_bounds__(256) repack_kernel(double* __restrict__ A64,
+                                                     const RepackJob* __restrict__ jobs,
+                                                     int* __restrict__ bad) {
+  const RepackJob J = jobs[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t ws = (int64_t)gridDim.x * 8;
+  bool err = false;
+  for (int64_t i = w0; i < J.m; i += ws) {
+    const double* src = J.src + i * J.src_ld;
+    double* dst = A64 + J.dst + i * J.lda;
+    for (int64_t c = lane; c < J.n; c += 32) {
+      const double v = src[c];
+      err |= !isfinite(v);
+      dst[c] = v;
+    }
+  }
+  if (__syncthreads_or(err) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+}  // namespace
+
+void launch_repack(double* A64, const RepackJob* jobs, int njobs, int* bad, int num_sms,
+                   cudaStream_t s) {
+  for (int j0 = 0; j0 < njobs; j0 += 65535) {
+    const int nj = std::min(65535, njobs - j0);
+    const int X = std::max(1, (4 * num_sms + nj - 1) / nj);
+    repack_kernel<<<dim3((unsigned)X, (unsigned)nj), 256, 0, s>>>(A64, jobs + j0, bad);
+    count_launch();
+  }
+}
+
 template void launch_pass_pcg<float>(const BArrays&, const int*, const int*, int, int, cudaStream_t);
 template void launch_pass_pcg<double>(const BArrays&, const int*, const int*, int, int, cudaStream_t);
 template void launch_gram<float>(const BArrays&, const GTile*, int, const GTile*, int, void*,

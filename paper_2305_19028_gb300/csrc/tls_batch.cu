@@ -94,6 +94,17 @@ void* balloc(tls_batch* bt, size_t bytes) {
   return p;
 }
 
+// Return a device buffer of the batch once the work queued on its stream is done.
+void bfree(tls_batch* bt, void* p) {
+  cudaStreamSynchronize(bt->stream);
+  for (size_t i = 0; i < bt->bufs.size(); ++i)
+    if (bt->bufs[i].first == p) {
+      tls::hook_free(p, bt->bufs[i].second, bt->stream);
+      bt->bufs.erase(bt->bufs.begin() + (long)i);
+      return;
+    }
+}
+
 // Grow a device buffer owned by the batch to at least `bytes` (contents are not kept).
 bool ensure_cap(tls_batch* bt, void** p, size_t* cap, size_t bytes) {
   if (*p && *cap >= bytes) return true;
@@ -874,19 +885,64 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   if (e == cudaSuccess) e = cudaMemsetAsync(a.vq, 0, 2 * vbytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.x, 0, vbytes, st);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  for (int i = 0; i < count && e == cudaSuccess; ++i) {
-    const BProb& P = bt->hp[(size_t)i];
-    e = cudaMemcpy2DAsync(A64 + P.offA, sizeof(double) * P.lda, A[i], sizeof(double) * lda[i],
-                          sizeof(double) * P.n, P.m, kind, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(bb + P.offB, b[i], sizeof(double) * P.m, kind, st);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int i = 0; i < count && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(bb + bt->hp[(size_t)i].offB, b[i], sizeof(double) * m[i], kind, st);
+  // A into the padded layout: rows of a few hundred bytes make row-by-row (2D) copies slow, so
+  // each problem's block is copied whole (host data through a staging buffer, in chunks) and one
+  // kernel per chunk places the rows and checks them for NaN / Inf
+  {
+    std::vector<RepackJob> jobs;
+    RepackJob* djobs = nullptr;
+    double* stage = nullptr;
+    int64_t cap = 0;   // staging capacity (doubles)
+    if (!on_device) {
+      int64_t most = 0, total = 0;
+      for (int i = 0; i < count; ++i) {
+        const int64_t span = (m[i] - 1) * lda[i] + n[i];
+        most = std::max(most, span);
+        total += span;
+      }
+      cap = std::max(most, std::min<int64_t>(total, (int64_t)64 << 20));   // <= 512 MB
+      stage = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)cap));
+    }
+    djobs = static_cast<RepackJob*>(balloc(bt, sizeof(RepackJob) * (size_t)count));
+    if (!djobs || (!on_device && !stage)) e = cudaErrorMemoryAllocation;
+    int64_t used = 0;
+    auto flush = [&]() {
+      if (jobs.empty() || e != cudaSuccess) return;
+      e = cudaMemcpyAsync(djobs, jobs.data(), sizeof(RepackJob) * jobs.size(),
+                          cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) {
+        launch_repack(A64, djobs, (int)jobs.size(), bt->dcount, sms, st);
+        e = cudaGetLastError();
+      }
+      // the next chunk's copies into the staging buffer and its job list queue behind this
+      // kernel on the same stream (and the pageable job upload has read `jobs` on return)
+      jobs.clear();
+      used = 0;
+    };
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+      const BProb& P = bt->hp[(size_t)i];
+      const int64_t span = (m[i] - 1) * lda[i] + n[i];
+      const double* src = A[i];
+      if (!on_device) {
+        if (used + span > cap) flush();
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(stage + used, A[i], sizeof(double) * (size_t)span,
+                            cudaMemcpyHostToDevice, st);
+        src = stage + used;
+        used += span;
+      }
+      jobs.push_back({src, lda[i], P.offA, P.m, P.n, P.lda});
+    }
+    flush();
+    if (stage) bfree(bt, stage);
+    if (djobs) bfree(bt, djobs);
   }
-  // NaN / Inf check on the device copy (padding is zero): one read at copy bandwidth
   if (e == cudaSuccess) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    tls::launch_nonfinite(A64, offA, bt->dcount, sms, st);
     tls::launch_nonfinite(bb, offB, bt->dcount, sms, st);
     e = cudaGetLastError();
   }

@@ -108,7 +108,18 @@ struct SolveParams {
   double cg_tol;
 };
 
+// One problem's rows to place into A64: m x n FP64 at src (device, row stride src_ld) to
+// A64 + dst (row stride lda).
+struct RepackJob {
+  const double* src;
+  int64_t src_ld, dst, m, n, lda;
+};
+
 // ---- launchers (k_batch.cu) --------------------------------------------------------------
+// Copies the rows of each job into the padded layout of A64 (one pass; columns n .. lda-1 are
+// left as they are) and sets *bad = 1 if a copied value is NaN or infinite.
+void launch_repack(double* A64, const RepackJob* jobs, int njobs, int* bad, int num_sms,
+                   cudaStream_t s);
 void launch_pass_colnorm(const BArrays& a, int ntiles, cudaStream_t s);
 void launch_colnorm_post(const BArrays& a, const int* list, int cnt, cudaStream_t s);
 // Pass and per-problem kernels take a work list and its length: a device count with a

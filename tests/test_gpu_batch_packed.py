@@ -3,6 +3,8 @@ phase one launch for the whole batch. Each problem is compared with the FP64 ora
 same seeded input, with the tolerances of the single-problem parity tests."""
 from __future__ import annotations
 
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -145,3 +147,53 @@ def test_graph_replay_equals_eager_launches():
         assert np.array_equal(a, b) and np.array_equal(a, c)
     assert [i["rqi_steps"] for i in i1] == [i["rqi_steps"] for i in i3]
     assert prof["pcg_pass2"][0] > 0 and prof["resid_pass"][0] > 0
+
+
+def _batch_raw(arrays, on_device):
+    """tls_batch_create_dense through the C ABI with each A's own row stride."""
+    lib = tls.load()
+    k = len(arrays)
+    ms = (C.c_int64 * k)(*[A.shape[0] for A, _, _ in arrays])
+    ns = (C.c_int64 * k)(*[A.shape[1] for A, _, _ in arrays])
+    ld = (C.c_int64 * k)(*[ld_ for _, _, ld_ in arrays])
+    ptr = (lambda t: t.data_ptr()) if on_device else (lambda a: a.ctypes.data)
+    ap = (C.c_void_p * k)(*[ptr(A) for A, _, _ in arrays])
+    bp = (C.c_void_p * k)(*[ptr(b) for _, b, _ in arrays])
+    h = C.c_void_p()
+    st = lib.tls_batch_create_dense(C.byref(h), k, ms, ns, ap, ld, bp, int(on_device), None)
+    assert st == 0
+    bt = tls.Batch.__new__(tls.Batch)
+    bt.h, bt.k = h, k
+    bt.shapes = [tuple(A.shape) for A, _, _ in arrays]
+    return bt
+
+
+def test_strided_inputs_host_and_device_give_identical_results():
+    """Row strides wider than n on the host and on the device (the rows are copied whole and
+    placed by one kernel): bit-identical to the contiguous batch."""
+    torch = pytest.importorskip("torch")
+    probs = _mixed_problems()
+    with tls.Batch([(p.A, p.b) for p in probs]) as bt:
+        bt.factor("fp16", u="fp32")
+        x0, s0, _, _ = bt.solve(tol=0.0, max_rqi=12)
+    wide = []
+    for j, p in enumerate(probs):
+        m, n = p.A.shape
+        W = np.full((m, n + 3 + j % 5), np.nan)
+        W[:, :n] = p.A
+        wide.append((W, p.b))
+    host = [(W[:, :p.A.shape[1]], b, W.shape[1]) for (W, b), p in zip(wide, probs)]
+    dev = []
+    for (W, b), p in zip(wide, probs):
+        Wd = torch.from_numpy(W).cuda()
+        dev.append((Wd[:, :p.A.shape[1]], torch.from_numpy(b).cuda(), W.shape[1]))
+    for arrays, on_device in ((host, False), (dev, True)):
+        bt = _batch_raw(arrays, on_device)
+        try:
+            bt.factor("fp16", u="fp32")
+            x1, s1, _, _ = bt.solve(tol=0.0, max_rqi=12)
+        finally:
+            bt.close()
+        assert np.array_equal(s0, s1)
+        for a, b in zip(x0, x1):
+            assert np.array_equal(a, b)
