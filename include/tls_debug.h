@@ -92,6 +92,16 @@ tls_status tls_profile_enable(tls_ctx* ctx, int on);
  * residual pass and the PCGTLS pass respectively. TLS_ERR_STATE before tls_factor or for CSR.
  */
 tls_status tls_set_pass_variant(tls_ctx* ctx, int variant_fp64, int variant_u);
+
+/*
+ * tls_set_small_path -- the solver used for a dense problem small enough to be solved in one
+ * launch (u = FP64, n <= 64, mode A, fixed PCGTLS step counts, its rows of A and W in shared
+ * memory): 0 automatic (a thread-block cluster of up to 16 CTAs where one fits, else one CTA),
+ * 1 one CTA, 2 a cluster (tls_solve returns TLS_ERR_ARG when no cluster shape fits), 3 neither
+ * (the multi-kernel path of larger problems). Kept until changed. TLS_ERR_ARG for another
+ * value.
+ */
+tls_status tls_set_small_path(tls_ctx* ctx, int path);
 /* Launch count and summed device milliseconds of one class (TLS_PROF_*). */
 tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* ms);
 /* The same per-class timing for a packed batch (classes as above; PCG_REDUCE covers the

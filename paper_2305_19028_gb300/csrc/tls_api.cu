@@ -43,6 +43,7 @@ struct tls_ctx {
   // persistent work buffers, reused by every factor / solve while they are large enough (no
   // cudaMalloc / cudaFree, which synchronise the device, between repeated calls)
   DevBuf slots[24];
+  int small_path = 0;      // tls_set_small_path
   RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
 
   // problem data (device)
@@ -469,13 +470,20 @@ tls_status precond_apply(tls_ctx* ctx, const double* y) {
 // memory) with the default PCGTLS schedule: the whole solve in one CTA (k_small.cu).
 bool small_eligible(const tls_ctx* ctx) {
   const tls_options& o = ctx->opt;
-  return !ctx->sparse && ctx->u == Prec::FP64 && ctx->n <= 64 && o.mode_A != 0 &&
-         o.cg_fixed != 0 && !ctx->use_sel_tol &&
-         tls::small_solve_smem((int)ctx->m, (int)ctx->n) > 0 &&
-         tls::small_solve_smem((int)ctx->m, (int)ctx->n) <= tls::kSmallSmemMax;
+  if (ctx->small_path == 3 || ctx->sparse || ctx->u != Prec::FP64 || ctx->n > 64 ||
+      o.mode_A == 0 || o.cg_fixed == 0 || ctx->use_sel_tol)
+    return false;
+  const size_t one = tls::small_solve_smem((int)ctx->m, (int)ctx->n);
+  const bool one_fits = one > 0 && one <= tls::kSmallSmemMax;
+  const bool cluster_fits = tls::cluster_solve_fits((int)ctx->m, (int)ctx->n);
+  if (ctx->small_path == 1) return one_fits;
+  if (ctx->small_path == 2) return true;   // tls_solve reports when no cluster shape fits
+  return one_fits || cluster_fits;
 }
 
-tls_status small_solve(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, double* sigma_out) {
+tls_status small_solve(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, double* sigma_out,
+                       bool* handled) {
+  *handled = true;
   const tls_options& o = ctx->opt;
   cudaStream_t st = ctx->stream;
   TLS_CK(cudaEventRecord(ctx->ev0, st));
@@ -486,12 +494,26 @@ tls_status small_solve(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, do
   prm.ls_iters = std::max(1, o.ls_iters);
   prm.psi_rule_ge = o.psi_rule_ge;
   auto* dres = reinterpret_cast<tls::SmallResult*>(ctx->gpart);
+  int cluster = 0;   // cluster size of the launch, 0 for the one-CTA solve
   {
     Prof pr(ctx, TLS_PROF_VEC);
-    if (!tls::launch_small_solve(ctx->A64, ctx->npad, (int)ctx->m, (int)ctx->n, ctx->b,
-                                 ctx->dinv, static_cast<const double*>(ctx->W), ctx->npad,
-                                 ctx->norm2_A + ctx->norm2_b, prm, ctx->x_best, dres, st))
-      return TLS_ERR_ARG;
+    const double scale = ctx->norm2_A + ctx->norm2_b;
+    const double* W = static_cast<const double*>(ctx->W);
+    if (ctx->small_path != 1)
+      cluster = tls::launch_cluster_solve(ctx->A64, ctx->npad, (int)ctx->m, (int)ctx->n, ctx->b,
+                                          ctx->dinv, W, ctx->npad, scale, prm, ctx->x_best,
+                                          dres, st);
+    if (cluster == 0) {
+      if (ctx->small_path == 2) {
+        set_err(ctx, "no thread-block cluster shape fits this problem");
+        return TLS_ERR_ARG;
+      }
+      if (!tls::launch_small_solve(ctx->A64, ctx->npad, (int)ctx->m, (int)ctx->n, ctx->b,
+                                   ctx->dinv, W, ctx->npad, scale, prm, ctx->x_best, dres, st)) {
+        *handled = false;   // neither fits (no cluster could be launched): multi-kernel path
+        return TLS_OK;
+      }
+    }
   }
   TLS_CK_LAUNCH("small solve");
   tls::SmallResult r{};
@@ -522,8 +544,8 @@ tls_status small_solve(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, do
     info->t_factor_ms = ctx->t_factor_ms;
     info->t_solve_ms = ms;
     info->fail_pivot = (int)ctx->fail_pivot;
-    info->pass_variant[0] = -1;   // no pass kernels: the one-CTA solve
-    info->pass_variant[1] = -1;
+    info->pass_variant[0] = cluster ? -2 : -1;   // no pass kernels: the one-launch solve
+    info->pass_variant[1] = cluster ? cluster : 1;
     info->n_psi = r.n_psi;
     for (int i = 0; i < r.n_psi; ++i) info->psi_hist[i] = r.psi_hist[i];
   }
@@ -532,8 +554,13 @@ tls_status small_solve(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, do
 
 template <typename T>
 tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, double* sigma_out) {
-  if constexpr (std::is_same<T, double>::value)
-    if (small_eligible(ctx)) return small_solve(ctx, tol, max_rqi, info, sigma_out);
+  if constexpr (std::is_same<T, double>::value) {
+    if (small_eligible(ctx)) {
+      bool handled = true;
+      const tls_status ss = small_solve(ctx, tol, max_rqi, info, sigma_out, &handled);
+      if (handled) return ss;
+    }
+  }
   const tls_options& o = ctx->opt;
   const bool modeA = o.mode_A != 0;
   UVecs<T> v = uvecs<T>(ctx);
@@ -1522,6 +1549,13 @@ tls_status tls_export_factor(tls_ctx* ctx, double* R_host, double* d_host, doubl
     TLS_CK(cudaMemcpyAsync(d_host, ctx->d, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     TLS_CK(cudaStreamSynchronize(st));
   }
+  return TLS_OK;
+}
+
+tls_status tls_set_small_path(tls_ctx* ctx, int path) {
+  if (!ctx) return TLS_ERR_ARG;
+  if (path < 0 || path > 3) return TLS_ERR_ARG;
+  ctx->small_path = path;
   return TLS_OK;
 }
 

@@ -88,6 +88,14 @@ size_t small_solve_smem(int m, int n);
 bool launch_small_solve(const double* A, int64_t lda, int m, int n, const double* b,
                         const double* dinv, const double* W, int64_t ldw, double scale,
                         const SmallParams& prm, double* x_out, SmallResult* res, cudaStream_t s);
+// The same solve on a thread-block cluster (rows of A spread over up to 16 CTAs, one per SM);
+// returns the cluster size launched, or 0 when no cluster shape fits (nothing launched).
+// cluster_solve_fits: some cluster shape holds the problem (at least 16 rows per CTA).
+bool cluster_solve_fits(int m, int n);
+int launch_cluster_solve(const double* A, int64_t lda, int m, int n, const double* b,
+                         const double* dinv, const double* W, int64_t ldw, double scale,
+                         const SmallParams& prm, double* x_out, SmallResult* res,
+                         cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------
 // Factorisation kernels (k_factor.cu)

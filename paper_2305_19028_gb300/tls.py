@@ -37,7 +37,7 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_batch_profile_elems", "tls_mlp_forward", "tls_mlp_grad", "tls_mlp_adam",
            "tls_batch_set_selector", "tls_batch_features", "tls_set_pass_variant",
            "tls_set_selector", "tls_features", "tls_pool_enable", "tls_pool_trim",
-           "tls_pool_stats", "tls_pool_poison"]
+           "tls_pool_stats", "tls_pool_poison", "tls_set_small_path"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
@@ -142,6 +142,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
                                              C.POINTER(C.c_float)]),
         "tls_batch_features": (C.c_int, [v, C.POINTER(C.c_float)]),
         "tls_set_pass_variant": (C.c_int, [v, C.c_int, C.c_int]),
+        "tls_set_small_path": (C.c_int, [v, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

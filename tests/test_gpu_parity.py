@@ -204,6 +204,56 @@ def test_solve_matches_oracle(m, n, dlo, noise, u_f, u):
     assert info["stop_reason"] in (tls.STOP_PSI_UP, tls.STOP_TOL, tls.STOP_MAX_RQI)
 
 
+SMALL_CASES = [
+    # (m, n, d_lo, noise): dense FP64 problems solved in one launch
+    (400, 40, 1e-2, 1e-6),     # the all-FP64 400 x 40 workload (cluster of 16 CTAs)
+    (230, 7, 1e-3, 1e-5),      # ragged: 230 rows over 8 CTAs
+    (64, 64, 1e-1, 1e-3),      # square, 64 rows: cluster of 4
+    (24, 20, 1e-2, 1e-4),      # too few rows for a cluster: one CTA (path 2 refuses)
+    (2000, 64, 1e-3, 1e-4),    # 125 rows per CTA, n at the limit; too large for one CTA
+]
+
+
+@pytest.mark.parametrize("m,n,dlo,noise", SMALL_CASES)
+@pytest.mark.parametrize("path", [2, 1, 3])
+def test_small_paths_match_oracle(path, m, n, dlo, noise):
+    """The one-launch solves (on a thread-block cluster, path 2; in one CTA, path 1) and the
+    multi-kernel path (3) on the same problems, each against the oracle."""
+    p = synth.dense_problem(m, n, d_lo=dlo, noise=noise, seed=4)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    ctx = tls.tls_create_dense(p.A, p.b)
+    try:
+        assert tls.load().tls_set_small_path(ctx, path) == 0
+        tls.tls_factor(ctx, "fp64", tls.tls_default_options(u="fp64"))
+        if path == 2 and m // 2 < 16:
+            with pytest.raises(tls.TLSError):
+                tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+            return
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+    finally:
+        tls.tls_destroy(ctx)
+    one_cta_fits = m * n <= 20000
+    if path == 2:
+        assert info["pass_variant"][0] == -2 and info["pass_variant"][1] >= 2, info
+    elif path == 1 and one_cta_fits:
+        assert info["pass_variant"] == [-1, 1], info
+    else:
+        assert info["pass_variant"][0] >= 0, info
+    atol = 64 * U64 * (np.linalg.norm(p.A) + np.linalg.norm(p.b)) if m == n else 0.0
+    assert abs(sigma - so) <= 1e-10 * so + atol, (sigma, so, info)
+    assert _rel(x, xo) <= 1e-8, info
+
+
+def test_small_path_argument_checked():
+    p = synth.dense_problem(50, 5, seed=1)
+    ctx = tls.tls_create_dense(p.A, p.b)
+    try:
+        assert tls.load().tls_set_small_path(ctx, 4) == 1     # TLS_ERR_ARG
+        assert tls.load().tls_set_small_path(ctx, -1) == 1
+    finally:
+        tls.tls_destroy(ctx)
+
+
 def test_refactor_with_another_working_precision():
     # the column norms and the FP32 copy of A are computed once per context: a context factored
     # first for u = FP64 (no FP32 copy yet) and then for u = FP32 still solves correctly, and so
