@@ -205,7 +205,13 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int) -> dict:
+# DRAM bytes per launch of the FP64 residual pass (the pipelined kernel, n = 2048) per row of A,
+# from the ncu capture in profiles/resid_pass_dense_8192x2048.md (134.346 MB read + 0.067 MB
+# written at m = 8192; one read of A, so proportional to m)
+RESID_PIPE_TRAFFIC_PER_ROW = (134.346e6 + 0.067e6) / 8192
+
+
+def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int = -1) -> dict:
     cnt, ms = prof.get(cls, (0, 0.0))
     if cnt == 0:
         return {}
@@ -224,8 +230,10 @@ def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int) -> dict:
         # FP64 FMA-bound on this GPU: r = b - A x and A^T r are 2 FMA (4 flops) per entry of A
         flops = 4.0 * m * n
         ach = flops / avg_s / 1e12
+        traffic = RESID_PIPE_TRAFFIC_PER_ROW * m if (variant64 == 3 and n == 2048) else None
         return {"kernel": "resid_pass (FP64 r=b-Ax, A^T r)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK, "unit": "TFLOP/s", "frac": ach / FP64_PEAK, "traffic": None,
+                "peak": FP64_PEAK, "unit": "TFLOP/s", "frac": ach / FP64_PEAK, "traffic": traffic,
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                 "peak_source": "nominal FP64 rate (2 FMA/clk/SM x 152 SMs x 2.07 GHz)",
                 "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops,
                 "hbm_gbs": (m * n * 8 + m * 8) / avg_s / 1e9}
@@ -395,8 +403,9 @@ def run_ours(args, ws, rank, local):
     total = {k: v[1] for k, v in prof.items()}
     dom = max(total, key=total.get)
     share = {k: round(v / max(1e-9, sum(total.values())), 4) for k, v in total.items()}
-    roof = _roofline(prof, peaks, dom, M_ROWS, N_COLS) or _roofline(prof, peaks, "pcg_pass2",
-                                                                   M_ROWS, N_COLS)
+    v64 = infos[-1]["pass_variant"][0]
+    roof = _roofline(prof, peaks, dom, M_ROWS, N_COLS, v64) or _roofline(prof, peaks, "pcg_pass2",
+                                                                        M_ROWS, N_COLS)
     inner = _roofline(prof, peaks, "pcg_pass2", M_ROWS, N_COLS)
     value = ok / (ms * 1e-3)
     line = {
