@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(kST, 1) small_solve_kernel(
 // memory, with one cluster barrier.
 // ---------------------------------------------------------------------------------------
 constexpr int kCT = 256;
+constexpr int kMaxCluster = 16;
 
 // Completes the row sums over the CTAs of the cluster: every CTA publishes its partial (K
 // scalars, identical in all its threads, and nv x n values in vec) in its own exchange buffer;
@@ -435,15 +436,28 @@ struct ClusterComm {
       for (int k = 0; k < K; ++k) buf[k] = a[k];
     for (int e = threadIdx.x; e < nv * n; e += kCT) buf[4 + e] = vec[e];
     cl.sync();
-    const unsigned R = cl.num_blocks();
+    const int R = (int)cl.num_blocks();
+    // all remote loads first (one round trip), then the adds in rank order
     for (int e = threadIdx.x; e < nv * n; e += kCT) {
+      double val[kMaxCluster];
+#pragma unroll
+      for (int r = 0; r < kMaxCluster; ++r)
+        val[r] = (r < R) ? cl.map_shared_rank(buf, r)[4 + e] : 0.0;
       double t = 0.0;
-      for (unsigned r = 0; r < R; ++r) t += cl.map_shared_rank(buf, r)[4 + e];
+#pragma unroll
+      for (int r = 0; r < kMaxCluster; ++r)
+        if (r < R) t += val[r];
       vec[e] = t;
     }
     if (threadIdx.x < K) {
+      double val[kMaxCluster];
+#pragma unroll
+      for (int r = 0; r < kMaxCluster; ++r)
+        val[r] = (r < R) ? cl.map_shared_rank(buf, r)[threadIdx.x] : 0.0;
       double t = 0.0;
-      for (unsigned r = 0; r < R; ++r) t += cl.map_shared_rank(buf, r)[threadIdx.x];
+#pragma unroll
+      for (int r = 0; r < kMaxCluster; ++r)
+        if (r < R) t += val[r];
       tot[threadIdx.x] = t;
     }
     __syncthreads();
