@@ -24,6 +24,8 @@ template <typename T>
 struct Scratch {
   T rowk[kPB][kB];
   T Yk[kPB][kB];
+  T r11[kPB][kPB];   // FP64: the pivot block's factor, formed once per step
+  T rinv[kPB];
   int bad;
 };
 
@@ -32,8 +34,14 @@ struct Scratch {
 // row stride lds) holds the same rows with zeros below the diagonal. Returns the first
 // non-positive (or NaN) pivot + 1, or 0; the value is the same in every thread. Call with all
 // threads of a CTA of at least 136 threads (blockDim.x <= 1024).
+// nb (a multiple of kPB, at most kB): the block's rows and columns from nb on are the identity
+// padding of an order-n problem (identity on the diagonal, zero elsewhere), so only the leading
+// nb x nb part is factored; G keeps the padding as it is and S receives it.
+// FP64 (sizeof(T) == 8; FP64 arithmetic runs at a 64th of the FP32 rate): R11 is formed once per
+// step by one warp and shared, rather than by every column thread.
 template <typename T, typename Round>
-__device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Round rnd) {
+__device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Round rnd,
+                           int nb = kB) {
   const int tid = threadIdx.x;
   int tI = kTT, tJ = 0;
   if (tid < kTT * (kTT + 1) / 2) {
@@ -50,14 +58,83 @@ __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Rou
     for (int c = 0; c < 4; ++c)
       v[a][c] = (tI < kTT) ? G[(int64_t)(4 * tI + a) * ld + 4 * tJ + c] : T(0);
   if (tid == 0) sc.bad = 0;
-  for (int k = 0; k < kB; k += kPB) {
+  if (nb < kB)
+    for (int e = tid; e < kB * kB; e += blockDim.x) {
+      const int rr = e / kB, cc = e % kB;
+      if (rr >= nb || cc >= nb) S[rr * lds + cc] = (rr == cc) ? T(1) : T(0);
+    }
+  for (int k = 0; k < nb; k += kPB) {
     if (tI >= k / 4 && tI < (k + kPB) / 4)
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) sc.rowk[4 * tI - k + a][4 * tJ + c] = v[a][c];
     __syncthreads();
-    if (tid < kB && tid >= k) {
+    if constexpr (sizeof(T) == 8) {
+      if (tid < 32) {
+        T r[kPB][kPB], rinv[kPB];
+        int bad = 0;
+#pragma unroll
+        for (int t = 0; t < kPB; ++t) {
+          T dsum = sc.rowk[t][k + t];
+#pragma unroll
+          for (int q = 0; q < kPB; ++q)
+            if (q < t) dsum = fma(-r[q][t], r[q][t], dsum);
+          if (!(dsum > T(0))) {
+            bad = bad ? bad : (k + t + 1);
+            dsum = T(1);
+          }
+          const T rtt = sqrt(dsum);
+          const T inv = T(1) / rtt;
+          r[t][t] = rtt;
+          rinv[t] = inv;
+#pragma unroll
+          for (int u = 0; u < kPB; ++u) {
+            if (u > t) {
+              T e = sc.rowk[t][k + u];
+#pragma unroll
+              for (int q = 0; q < kPB; ++q)
+                if (q < t) e = fma(-r[q][t], r[q][u], e);
+              r[t][u] = e * inv;
+            }
+          }
+        }
+        if (tid == 0) {
+#pragma unroll
+          for (int t = 0; t < kPB; ++t) {
+            sc.rinv[t] = rinv[t];
+#pragma unroll
+            for (int u = 0; u < kPB; ++u) sc.r11[t][u] = (u >= t) ? r[t][u] : T(0);
+          }
+          if (bad) atomicCAS(&sc.bad, 0, bad);
+        }
+      }
+      __syncthreads();
+      if (tid < nb && tid >= k) {
+        const int c = tid;
+        T y[kPB];
+#pragma unroll
+        for (int t = 0; t < kPB; ++t) {
+          T e = sc.rowk[t][c];
+#pragma unroll
+          for (int q = 0; q < kPB; ++q)
+            if (q < t) e = fma(-sc.r11[q][t], y[q], e);
+          y[t] = (c - k < t) ? T(0) : e * sc.rinv[t];
+        }
+#pragma unroll
+        for (int t = 0; t < kPB; ++t) {
+          sc.Yk[t][c] = y[t];
+          if (c >= k + t) {
+            const T val = rnd(y[t]);
+            G[(int64_t)(k + t) * ld + c] = val;
+            S[(k + t) * lds + c] = val;
+          }
+        }
+      } else if (tid < kB && tid >= nb) {
+#pragma unroll
+        for (int t = 0; t < kPB; ++t) sc.Yk[t][tid] = T(0);   // padding columns
+      }
+    } else if (tid < kB && tid >= k) {
       // R11 = chol(S11) from the published upper entries
       T r[kPB][kPB], rinv[kPB];
       int bad = 0;
@@ -116,7 +193,7 @@ __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Rou
       if (bad && tid == k) atomicCAS(&sc.bad, 0, bad);
     }
     __syncthreads();
-    if (tI < kTT && tI >= (k + kPB) / 4) {
+    if (tI < kTT && tI >= (k + kPB) / 4 && tJ < nb / 4) {
       T yi[kPB][4], yj[kPB][4];
 #pragma unroll
       for (int t = 0; t < kPB; ++t)

@@ -577,21 +577,77 @@ __device__ __forceinline__ void inv_double_level(T (*S)[NB + 1], T (*X)[NB + 1],
   __syncthreads();
 }
 
+// FP64 level of the doubling inverse with the zero parts skipped (FP64 arithmetic runs at a
+// 64th of the FP32 rate, so the full-length sums of inv_double_level would cost real time):
+// k runs over the upper-triangular support of X_BB and X_AA only, and over the nb leading
+// (non-padding) rows and columns of the block; the padding part of X_AB is zero.
+template <int SB>
+__device__ __forceinline__ void inv_double_level_f64(double (*S)[NB + 1], double (*X)[NB + 1],
+                                                     int tid, int nb) {
+  constexpr int pairs = NB / (2 * SB), cnt = pairs * SB * SB;
+  for (int e = tid; e < cnt; e += 256) {
+    const int pr = e / (SB * SB), rem = e % (SB * SB), i = rem / SB, j = rem % SB;
+    const int a = 2 * pr * SB, nbB = nb - (a + SB);
+    double v = 0.0;
+    const int kmax = min(j + 1, nbB);
+    for (int k = 0; k < kmax; ++k) v = fma(S[a + i][a + SB + k], X[a + SB + k][a + SB + j], v);
+    S[a + SB + i][a + j] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < cnt; e += 256) {
+    const int pr = e / (SB * SB), rem = e % (SB * SB), i = rem / SB, j = rem % SB;
+    const int a = 2 * pr * SB, nbB = nb - (a + SB);
+    double v = 0.0;
+    if (j < nbB)
+      for (int k = i; k < SB; ++k) v = fma(X[a + i][a + k], S[a + SB + k][a + j], v);
+    X[a + i][a + SB + j] = -v;
+  }
+  __syncthreads();
+}
+
+// nb: the leading non-padding order of the block (a multiple of 8; NB unless this is the last
+// block of a problem whose n is not a multiple of 64); used by the FP64 factor only.
 template <typename T>
 __device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, int64_t kb,
-                                                    int* info, int prec, unsigned char* dsm) {
+                                                    int* info, int prec, unsigned char* dsm,
+                                                    int nb = NB) {
   T (*S)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm);
   T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
   const int tid = threadIdx.x;
   __shared__ chol64::Scratch<T> sc;
+  if constexpr (sizeof(T) != 8) nb = NB;
   const int bad = chol64::factor_block<T>(M + kb * npad + kb, npad, &S[0][0], NB + 1, sc,
-                                          [prec](T v) { return round_prec(v, prec); });
+                                          [prec](T v) { return round_prec(v, prec); }, nb);
   if (bad) {
     if (tid == 0) atomicCAS(info, 0, (int)kb + bad);
     return;   // uniform: every thread saw the same pivots
   }
   for (int e = tid; e < NB * NB; e += 256) X[e / NB][e % NB] = T(0);
   __syncthreads();
+  if constexpr (sizeof(T) == 8) {
+    // reciprocals of the diagonal once, then the 8 x 8 diagonal blocks by substitution with
+    // multiplications, then the levels with the zero parts skipped
+    T* rd = &sc.rowk[0][0];
+    if (tid < NB) rd[tid] = T(1) / S[tid][tid];
+    __syncthreads();
+    if (tid < 64) {
+      const int o = (tid >> 3) * 8, j = tid & 7;
+      for (int i = j; i >= 0; --i) {
+        T v = (i == j) ? T(1) : T(0);
+        for (int k = i + 1; k <= j; ++k) v = fma(-S[o + i][o + k], X[o + k][o + j], v);
+        X[o + i][o + j] = v * rd[o + i];
+      }
+    }
+    __syncthreads();
+    inv_double_level_f64<8>(S, X, tid, nb);
+    inv_double_level_f64<16>(S, X, tid, nb);
+    inv_double_level_f64<32>(S, X, tid, nb);
+    for (int e = tid; e < NB * NB; e += 256) {
+      const int r = e / NB, c = e % NB;
+      W[(kb + r) * npad + kb + c] = X[r][c];
+    }
+    return;
+  }
   // inverse by doubling: the eight 8 x 8 diagonal blocks by substitution (thread: one column,
   // chains of at most 8), then for s = 8, 16, 32 every pair of s-blocks A, B gets
   // X_AB = -X_AA (R_AB X_BB) as two small products; Tm = R_AB X_BB lives in the (zero, unused)
@@ -616,10 +672,10 @@ __device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, in
 
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_inv_diag_kernel(T* M, T* W, int64_t npad, int64_t kb,
-                                                             int* info, int prec) {
+                                                             int* info, int prec, int nb) {
   if (*(volatile int*)info != 0) return;
   extern __shared__ __align__(16) unsigned char dsm[];
-  potrf_inv_diag_body<T>(M, W, npad, kb, info, prec, dsm);
+  potrf_inv_diag_body<T>(M, W, npad, kb, info, prec, dsm, nb);
 }
 
 // Trailing update of block step K, H_22 -= R_K2^T R_K2 (upper 64 x 64 tiles), with the factor
@@ -990,7 +1046,11 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
     }();
     (void)attr2;
   }
-  potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, 0, info, (int)prec);
+  // leading non-padding order of the diagonal block at kb (multiple of 8, at most 64)
+  auto active = [n](int64_t kb) {
+    return (int)std::min<int64_t>(NB, std::max<int64_t>(8, (n - kb + 7) / 8 * 8));
+  };
+  potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, 0, info, (int)prec, active(0));
   count_launch();
   int64_t kb_from = npad;   // first block step with the panel folded into the update
   for (int64_t kb = 0; kb < npad; kb += NB) {
@@ -1036,7 +1096,8 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
       T* C = M + (kb + NB) * npad + kb + NB;
       gemm_simt<T, T, false, false>((int)n2, (int)n2, NB, P, npad, 0, P, npad, 0, C, npad, 0,
                                     T(-1), T(1), 1, 0, 1, s, info);
-      potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb + NB, info, (int)prec);
+      potrf_inv_diag_kernel<T><<<1, 256, dsmem, s>>>(M, Wd, npad, kb + NB, info, (int)prec,
+                                                     active(kb + NB));
       count_launch();
     }
   }

@@ -24,20 +24,32 @@ __device__ __forceinline__ double swsum(double v) {
   return v;
 }
 
-// Sums of K values over the CTA of NT threads; every thread receives the totals.
-// sh: NT / 32 * K doubles.
+// Sums of K values over the CTA of NT threads; every thread receives the totals. Only threads
+// [0, active) may hold nonzero values: the warps beyond skip their shuffles, and one warp adds
+// the per-warp sums (FP64 adds run at a 64th of the FP32 rate on this GPU, so a reduction
+// repeated by every warp costs as much as the products it sums). sh: (NT / 32 + 1) * K doubles.
 template <int K, int NT = kST>
-__device__ __forceinline__ void csum(double (&v)[K], double* sh) {
+__device__ __forceinline__ void csum(double (&v)[K], double* sh, int active = NT) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = min(NT / 32, (active + 31) / 32);
+  if (warp < nw) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = swsum(v[k]);
+    for (int k = 0; k < K; ++k) v[k] = swsum(v[k]);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
+  }
   __syncthreads();
-  if (lane == 0)
+  if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
+    for (int k = 0; k < K; ++k) {
+      const double t = swsum(lane < nw ? sh[lane * K + k] : 0.0);
+      if (lane == 0) sh[(NT / 32) * K + k] = t;
+    }
+  }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = swsum(lane < NT / 32 ? sh[lane * K + k] : 0.0);
+  for (int k = 0; k < K; ++k) v[k] = sh[(NT / 32) * K + k];
 }
 
 struct Small {
@@ -46,7 +58,7 @@ struct Small {
   const double* W;   // n x n upper triangular (row stride n)
   const double* dv;  // 1 / d
   int m, n;
-  double* red;       // kSW * 4
+  double* red;       // (threads / 32 + 1) * 4
   double* part;      // G x 2 x n partial column sums
   int G;             // row groups of the A^T products
 };
@@ -113,9 +125,11 @@ __device__ void mat_Wt(const Small& S, const double* y, double* v, int nr) {
   }
 }
 
+// State of the paired PCGTLS solves: one copy per CTA in shared memory; thread 0 computes the
+// FP64 scalars (divisions and square roots) once and the others read them after a barrier.
 struct Pcg {
-  double eta[2], eta0[2], beta[2];
-  int done[2], iters[2], not_spd[2];
+  double eta[2], eta0[2], beta[2], alpha[2], delta[2];
+  int done[2], iters[2], not_spd[2], ok[2];
 };
 
 // The rows of A may be spread over the CTAs of a cluster: every sum over rows (the m-vector dot
@@ -127,13 +141,13 @@ struct OneCta {
 };
 
 // Paired PCGTLS (Alg. 3, A-explicit operator) for RHS fin0 * s0 (r = 0) and fin1 (r = 1):
-// iterates in w (nr x n). Scratch vectors: y, s, p, q, v (nr x n each), t (nr x m).
+// iterates in w (nr x n). Scratch vectors: y, s, p, q, v (nr x n each), t (nr x m). st: shared.
 template <int NT, class Comm>
 __device__ void pcg(const Small& S, Comm& comm, int nr, const double* fin0, double s0,
                     const double* fin1, double sigma2, int steps, double* w, double* y,
                     double* s, double* p, double* q, double* v, double* t, Pcg& st) {
-  const int n = S.n;
-  for (int e = threadIdx.x; e < nr * n; e += NT) {
+  const int n = S.n, nn = nr * n;
+  for (int e = threadIdx.x; e < nn; e += NT) {
     const int r = e / n, j = e % n;
     const double f = (r == 0) ? s0 * fin0[j] : fin1[j];
     y[e] = f * S.dv[j];
@@ -145,33 +159,35 @@ __device__ void pcg(const Small& S, Comm& comm, int nr, const double* fin0, doub
   __syncthreads();
   {
     double a[2] = {0.0, 0.0};
-    for (int e = threadIdx.x; e < nr * n; e += NT) a[e / n] = fma(s[e], s[e], a[e / n]);
-    csum<2, NT>(a, S.red);
-    for (int r = 0; r < 2; ++r) {
-      st.eta[r] = a[r];
-      st.eta0[r] = a[r];
-      st.beta[r] = 0.0;
-      st.done[r] = (r < nr) ? (a[r] == 0.0 ? 1 : 0) : 1;
-      st.iters[r] = 0;
-      st.not_spd[r] = 0;
-    }
+    for (int e = threadIdx.x; e < nn; e += NT) a[e / n] = fma(s[e], s[e], a[e / n]);
+    csum<2, NT>(a, S.red, nn);
+    if (threadIdx.x == 0)
+      for (int r = 0; r < 2; ++r) {
+        st.eta[r] = a[r];
+        st.eta0[r] = a[r];
+        st.beta[r] = 0.0;
+        st.done[r] = (r < nr) ? (a[r] == 0.0 ? 1 : 0) : 1;
+        st.iters[r] = 0;
+        st.not_spd[r] = 0;
+      }
+    __syncthreads();
   }
   for (int it = 0; it < steps; ++it) {
     if (st.done[0] && st.done[1]) break;   // the remaining steps change nothing
     // p = s + beta p; q = D^{-1} W p
-    for (int e = threadIdx.x; e < nr * n; e += NT) p[e] = s[e] + st.beta[e / n] * p[e];
+    for (int e = threadIdx.x; e < nn; e += NT) p[e] = s[e] + st.beta[e / n] * p[e];
     __syncthreads();
     mat_W<NT>(S, p, q, nr);
     __syncthreads();
     mat_A<NT>(S, q, t, nr);
     __syncthreads();
     double a[4] = {0.0, 0.0, 0.0, 0.0};   // qq0, qq1, tt0, tt1
-    for (int e = threadIdx.x; e < nr * n; e += NT) a[e / n] = fma(q[e], q[e], a[e / n]);
+    for (int e = threadIdx.x; e < nn; e += NT) a[e / n] = fma(q[e], q[e], a[e / n]);
     for (int e = threadIdx.x; e < nr * S.m; e += NT) {
       const int r = e / S.m;
       a[2 + r] = fma(t[e], t[e], a[2 + r]);
     }
-    csum<4, NT>(a, S.red);
+    csum<4, NT>(a, S.red, max(nn, nr * S.m));
     mat_At<NT>(S, t, v, nr);
     __syncthreads();
     {
@@ -180,41 +196,43 @@ __device__ void pcg(const Small& S, Comm& comm, int nr, const double* fin0, doub
       a[2] = mt[0];
       a[3] = mt[1];
     }
-    double delta[2], alpha[2];
-    bool ok[2];
-    for (int r = 0; r < 2; ++r) {
-      delta[r] = a[2 + r] - sigma2 * a[r];
-      ok[r] = r < nr && !st.done[r] && delta[r] > 0.0;
-      alpha[r] = ok[r] ? st.eta[r] / delta[r] : 0.0;
-    }
-    for (int e = threadIdx.x; e < nr * n; e += NT) {
+    if (threadIdx.x == 0)
+      for (int r = 0; r < 2; ++r) {
+        st.delta[r] = a[2 + r] - sigma2 * a[r];
+        st.ok[r] = (r < nr && !st.done[r] && st.delta[r] > 0.0) ? 1 : 0;
+        st.alpha[r] = st.ok[r] ? st.eta[r] / st.delta[r] : 0.0;
+      }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn; e += NT) {
       const int r = e / n, j = e % n;
-      if (!ok[r]) continue;
-      w[e] = fma(alpha[r], q[e], w[e]);
+      if (!st.ok[r]) continue;
+      w[e] = fma(st.alpha[r], q[e], w[e]);
       y[e] = (v[e] - sigma2 * q[e]) * S.dv[j];
     }
     __syncthreads();
     mat_Wt<NT>(S, y, v, nr);
     __syncthreads();
     double ss[2] = {0.0, 0.0};
-    for (int e = threadIdx.x; e < nr * n; e += NT) {
+    for (int e = threadIdx.x; e < nn; e += NT) {
       const int r = e / n;
-      if (ok[r]) s[e] = s[e] - alpha[r] * v[e];
+      if (st.ok[r]) s[e] = s[e] - st.alpha[r] * v[e];
       ss[r] = fma(s[e], s[e], ss[r]);
     }
-    csum<2, NT>(ss, S.red);
-    for (int r = 0; r < nr; ++r) {
-      if (st.done[r]) continue;
-      if (!(delta[r] > 0.0)) {
-        st.done[r] = 1;
-        st.not_spd[r] = (delta[r] < 0.0) ? 1 : 0;
-      } else {
-        st.beta[r] = ss[r] / st.eta[r];
-        st.eta[r] = ss[r];
-        st.iters[r] += 1;
-        if (ss[r] == 0.0) st.done[r] = 1;
+    csum<2, NT>(ss, S.red, nn);
+    if (threadIdx.x == 0)
+      for (int r = 0; r < nr; ++r) {
+        if (st.done[r]) continue;
+        if (!(st.delta[r] > 0.0)) {
+          st.done[r] = 1;
+          st.not_spd[r] = (st.delta[r] < 0.0) ? 1 : 0;
+        } else {
+          st.beta[r] = ss[r] / st.eta[r];
+          st.eta[r] = ss[r];
+          st.iters[r] += 1;
+          if (ss[r] == 0.0) st.done[r] = 1;
+        }
       }
-    }
+    __syncthreads();
   }
   __syncthreads();
 }
@@ -224,10 +242,10 @@ struct Rq {
 };
 
 // r = b - A x, sigma^2 = ||r||^2 / (1 + ||x||^2), f = -A^T r - sigma^2 x, g = -b^T r + sigma^2,
-// psi (Alg. 2, Eq. (2), Eq. (4)); x, f: n; r: m scratch, v: n scratch
+// psi (Alg. 2, Eq. (2), Eq. (4)); x, f: n; r: m scratch, v: n scratch; q: shared
 template <int NT, class Comm>
-__device__ Rq resid(const Small& S, Comm& comm, const double* x, double xx, double* r, double* v,
-                    double* f) {
+__device__ void resid(const Small& S, Comm& comm, const double* x, double xx, double* r,
+                      double* v, double* f, Rq& q) {
   double a[2] = {0.0, 0.0};
   for (int i = threadIdx.x; i < S.m; i += NT) {
     const double* ai = S.A + (int64_t)i * S.n;
@@ -238,33 +256,38 @@ __device__ Rq resid(const Small& S, Comm& comm, const double* x, double xx, doub
     a[0] = fma(ri, ri, a[0]);
     a[1] = fma(S.b[i], ri, a[1]);
   }
-  csum<2, NT>(a, S.red);
+  csum<2, NT>(a, S.red, S.m);
   mat_At<NT>(S, r, v, 1);
   __syncthreads();
   comm.sum(a, v, 1);
-  Rq q;
-  q.rr = a[0];
-  q.br = a[1];
-  q.xx = xx;
-  q.sigma2 = a[0] / (1.0 + xx);
+  if (threadIdx.x == 0) {
+    q.rr = a[0];
+    q.br = a[1];
+    q.xx = xx;
+    q.sigma2 = a[0] / (1.0 + xx);
+    q.g = -q.br + q.sigma2;
+  }
+  __syncthreads();
+  const double sigma2 = q.sigma2;
   double ff[1] = {0.0};
   for (int j = threadIdx.x; j < S.n; j += NT) {
-    const double fj = -v[j] - q.sigma2 * x[j];
+    const double fj = -v[j] - sigma2 * x[j];
     f[j] = fj;
     ff[0] = fma(fj, fj, ff[0]);
   }
-  csum<1, NT>(ff, S.red);
-  q.ff = ff[0];
-  q.g = -q.br + q.sigma2;
-  q.psi = sqrt((q.ff + q.g * q.g) / (xx + 1.0));
-  return q;
+  csum<1, NT>(ff, S.red, S.n);
+  if (threadIdx.x == 0) {
+    q.ff = ff[0];
+    q.psi = sqrt((q.ff + q.g * q.g) / (xx + 1.0));
+  }
+  __syncthreads();
 }
 
 template <int NT>
 __device__ double norm2(const Small& S, const double* x) {
   double a[1] = {0.0};
   for (int j = threadIdx.x; j < S.n; j += NT) a[0] = fma(x[j], x[j], a[0]);
-  csum<1, NT>(a, S.red);
+  csum<1, NT>(a, S.red, S.n);
   return a[0];
 }
 
@@ -277,16 +300,18 @@ __device__ void rqi_solve(Small& S, Comm& comm, double scale, const SmallParams&
                           double* __restrict__ x_out, SmallResult* res) {
   const int n = S.n;
   const double* pdv = S.dv;
-  Pcg st;
+  __shared__ Pcg st;
+  __shared__ Rq rq;
+  __shared__ double betak_sh;
   // Alg. 2 line 1, LS start: residual at x = 0 (f = -A^T b), PCG with sigma^2 = 0
-  Rq rq = resid<NT>(S, comm, x, 0.0, t, v, f);
+  resid<NT>(S, comm, x, 0.0, t, v, f, rq);
   pcg<NT>(S, comm, 1, f, -1.0, nullptr, 0.0, prm.ls_iters, w, y, s, p, q, v, t, st);
   for (int j = threadIdx.x; j < n; j += NT) x[j] = w[j];
   __syncthreads();
   double xx = norm2<NT>(S, x);
   // lines 2-5: r_0, sigma_0^2, u_0 = (R^T R)^{-1} x_0 (one init step and one W product),
   // x_1 = x_0 + sigma_0^2 u_0
-  rq = resid<NT>(S, comm, x, xx, t, v, f);
+  resid<NT>(S, comm, x, xx, t, v, f, rq);
   for (int j = threadIdx.x; j < n; j += NT) y[j] = x[j] * pdv[j];
   __syncthreads();
   mat_Wt<NT>(S, y, s, 1);
@@ -301,7 +326,7 @@ __device__ void rqi_solve(Small& S, Comm& comm, double scale, const SmallParams&
   int k = 0, best_k = 0, stop = TLS_STOP_MAX_RQI, cg_total = 0, not_spd = 0, n_psi = 0;
   for (;;) {
     ++k;
-    rq = resid<NT>(S, comm, x, xx, t, v, f);
+    resid<NT>(S, comm, x, xx, t, v, f, rq);
     if (k > 1) {
       cg_total += st.iters[0] + st.iters[1];
       not_spd |= st.not_spd[0] | st.not_spd[1];
@@ -341,8 +366,10 @@ __device__ void rqi_solve(Small& S, Comm& comm, double scale, const SmallParams&
       a[0] = fma(z, f[j], a[0]);
       a[1] = fma(z, x[j], a[1]);
     }
-    csum<2, NT>(a, S.red);
-    const double betak = (a[0] - rq.g) / (a[1] + 1.0);
+    csum<2, NT>(a, S.red, n);
+    if (threadIdx.x == 0) betak_sh = (a[0] - rq.g) / (a[1] + 1.0);
+    __syncthreads();
+    const double betak = betak_sh;
     for (int j = threadIdx.x; j < n; j += NT) x[j] = fma(betak, w[n + j], x[j] + w[j]);
     __syncthreads();
     xx = norm2<NT>(S, x);
@@ -387,7 +414,7 @@ __global__ void __launch_bounds__(kST, 1) small_solve_kernel(
   double* v = q + 2 * n;
   double* t = v + 2 * n;    // 2m
   double* part = t + 2 * m; // G x 2 x n
-  double* red = part + (size_t)S.G * 2 * n;
+  double* red = part + (size_t)S.G * 2 * n;   // (kSW + 1) * 4
   S.A = pA;
   S.b = pb;
   S.W = pW;
@@ -497,7 +524,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_solve_kernel(
   double* t = v + 2 * n;      // 2 mmax
   double* part = t + 2 * mmax;
   double* red = part + (size_t)S.G * 2 * n;
-  double* xch0 = red + (kCT / 32) * 4;
+  double* xch0 = red + (kCT / 32 + 1) * 4;
   double* xch1 = xch0 + 4 + 2 * n;
   double* tot = xch1 + 4 + 2 * n;
   S.A = pA;
@@ -524,7 +551,7 @@ size_t cluster_solve_smem(int m, int n, int R) {
   if (n < 1 || n > 64 || R < 1) return 0;
   const int G = kCT / n, mm = cluster_rows(m, R);
   return sizeof(double) * ((size_t)mm * n + mm + (size_t)n * n + 4 * (size_t)n + 12 * (size_t)n +
-                           2 * (size_t)mm + (size_t)G * 2 * n + (kCT / 32) * 4 +
+                           2 * (size_t)mm + (size_t)G * 2 * n + (kCT / 32 + 1) * 4 +
                            2 * (4 + 2 * (size_t)n) + 4);
 }
 
@@ -587,7 +614,7 @@ size_t small_solve_smem(int m, int n) {
   if (n < 1 || n > 64) return 0;
   const int G = kST / n;
   return sizeof(double) * ((size_t)m * n + m + (size_t)n * n + 4 * (size_t)n + 12 * (size_t)n +
-                           2 * (size_t)m + (size_t)G * 2 * n + kSW * 4);
+                           2 * (size_t)m + (size_t)G * 2 * n + (kSW + 1) * 4);
 }
 
 bool launch_small_solve(const double* A, int64_t lda, int m, int n, const double* b,
