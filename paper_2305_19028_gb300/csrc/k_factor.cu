@@ -13,6 +13,19 @@ namespace tls {
 
 namespace {
 
+// Two FP32 fused multiply-adds in one instruction (the packed f32x2 form of sm_100 and later):
+// c.lo = fma(a.lo, b.lo, c.lo), c.hi = fma(a.hi, b.hi, c.hi), each rounded to nearest like
+// fmaf; halves the issue slots of the shared-memory-fed GEMM inner loops.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ void ffma2(unsigned long long& c, unsigned long long a,
+                                      unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
+__device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+
 __device__ __forceinline__ float load_f(const __half* p) { return __half2float(*p); }
 __device__ __forceinline__ float load_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 __device__ __forceinline__ float load_f(const float* p) { return *p; }
@@ -285,11 +298,11 @@ __device__ __forceinline__ void gemm_big_tile(
       *reinterpret_cast<float4*>(&Bs[buf][b_k][b_c]) = vb;
     }
   };
-  float acc[8][8];
+  unsigned long long acc2[8][4];   // packed pairs: columns 2q, 2q + 1 of the thread's row p
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < 4; ++b) acc2[a][b] = 0ull;
   if (k_lo < k_hi) {
     float4 va = load_a(k_lo), vb = load_b(k_lo);
     store(0, va, vb);
@@ -308,11 +321,14 @@ __device__ __forceinline__ void gemm_big_tile(
         const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
         const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const unsigned long long bp[4] = {pk2(b0.x, b0.y), pk2(b0.z, b0.w), pk2(b1.x, b1.y),
+                                          pk2(b1.z, b1.w)};
 #pragma unroll
-        for (int p = 0; p < 8; ++p)
+        for (int p = 0; p < 8; ++p) {
+          const unsigned long long ap = pk2(av[p], av[p]);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+          for (int q = 0; q < 4; ++q) ffma2(acc2[p][q], ap, bp[q]);
+        }
       }
       if (more) {
         store(buf ^ 1, va, vb);
@@ -330,7 +346,8 @@ __device__ __forceinline__ void gemm_big_tile(
       const int gj = j0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
       if (gj >= N || (upper && gi > gj)) continue;
       float* cp = C + (int64_t)gi * ldc + gj;
-      float v = alpha * acc[p][q];
+      const float a = (q & 1) ? hi2(acc2[p][q >> 1]) : lo2(acc2[p][q >> 1]);
+      float v = alpha * a;
       if (beta != 0.f) v += beta * (*cp);
       *cp = v;
       if (mirror && gi != gj) C[(int64_t)gj * ldc + gi] = v;
@@ -406,11 +423,11 @@ __device__ __forceinline__ void gemm_mid_tile(
       *reinterpret_cast<float4*>(&Bs[buf][b_k][b_c]) = vb;
     }
   };
-  float acc[4][4];
+  unsigned long long acc2[4][2];   // packed pairs: columns 2q, 2q + 1 of the thread's row p
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < 2; ++b) acc2[a][b] = 0ull;
   if (k_lo < k_hi) {
     float4 va = load_a(k_lo), vb = load_b(k_lo);
     store(0, va, vb);
@@ -427,11 +444,13 @@ __device__ __forceinline__ void gemm_mid_tile(
         const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
         const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
         const float av[4] = {a4.x, a4.y, a4.z, a4.w};
-        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+        const unsigned long long bp[2] = {pk2(b4.x, b4.y), pk2(b4.z, b4.w)};
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+        for (int p = 0; p < 4; ++p) {
+          const unsigned long long ap = pk2(av[p], av[p]);
+          ffma2(acc2[p][0], ap, bp[0]);
+          ffma2(acc2[p][1], ap, bp[1]);
+        }
       }
       if (more) {
         store(buf ^ 1, va, vb);
@@ -449,7 +468,7 @@ __device__ __forceinline__ void gemm_mid_tile(
       const int gj = j0 + tx * 4 + q;
       if (gj >= N || (upper && gi > gj)) continue;
       float* cp = C + (int64_t)gi * ldc + gj;
-      float v = alpha * acc[p][q];
+      float v = alpha * ((q & 1) ? hi2(acc2[p][q >> 1]) : lo2(acc2[p][q >> 1]));
       if (beta != 0.f) v += beta * (*cp);
       *cp = v;
       if (mirror && gi != gj) C[(int64_t)gj * ldc + gi] = v;
