@@ -15,7 +15,9 @@ namespace {
 
 // Two FP32 fused multiply-adds in one instruction (the packed f32x2 form of sm_100 and later):
 // c.lo = fma(a.lo, b.lo, c.lo), c.hi = fma(a.hi, b.hi, c.hi), each rounded to nearest like
-// fmaf; halves the issue slots of the shared-memory-fed GEMM inner loops.
+// fmaf; halves the FMA issue slots of the 8 x 8-per-thread GEMM tile. (In the 4 x 4-per-thread
+// tile the packing of the broadcast operands cost more than it saved: the inverse by doubling
+// took 0.37 ms instead of 0.25 ms at n = 2048, so that tile keeps scalar FMAs.)
 __device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
   return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
 }
@@ -423,11 +425,11 @@ __device__ __forceinline__ void gemm_mid_tile(
       *reinterpret_cast<float4*>(&Bs[buf][b_k][b_c]) = vb;
     }
   };
-  unsigned long long acc2[4][2];   // packed pairs: columns 2q, 2q + 1 of the thread's row p
+  float acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) acc2[a][b] = 0ull;
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
   if (k_lo < k_hi) {
     float4 va = load_a(k_lo), vb = load_b(k_lo);
     store(0, va, vb);
@@ -444,13 +446,11 @@ __device__ __forceinline__ void gemm_mid_tile(
         const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
         const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
         const float av[4] = {a4.x, a4.y, a4.z, a4.w};
-        const unsigned long long bp[2] = {pk2(b4.x, b4.y), pk2(b4.z, b4.w)};
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const unsigned long long ap = pk2(av[p], av[p]);
-          ffma2(acc2[p][0], ap, bp[0]);
-          ffma2(acc2[p][1], ap, bp[1]);
-        }
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
       }
       if (more) {
         store(buf ^ 1, va, vb);
@@ -468,7 +468,7 @@ __device__ __forceinline__ void gemm_mid_tile(
       const int gj = j0 + tx * 4 + q;
       if (gj >= N || (upper && gi > gj)) continue;
       float* cp = C + (int64_t)gi * ldc + gj;
-      float v = alpha * ((q & 1) ? hi2(acc2[p][q >> 1]) : lo2(acc2[p][q >> 1]));
+      float v = alpha * acc[p][q];
       if (beta != 0.f) v += beta * (*cp);
       *cp = v;
       if (mirror && gi != gj) C[(int64_t)gj * ldc + gi] = v;
