@@ -84,17 +84,6 @@ __device__ __forceinline__ void lds4(const double* p, double (&o)[4]) {
   o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
 }
 
-// Two FP32 fused multiply-adds in one instruction (the packed f32x2 form of sm_100 and later):
-// c.lo = fma(a.lo, b.lo, c.lo), c.hi = fma(a.hi, b.hi, c.hi), each rounded to nearest like
-// fmaf. Halves the issue slots of an FMA-bound loop whose operands come from shared memory.
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-}
-__device__ __forceinline__ void fma2(unsigned long long& c, unsigned long long a,
-                                     unsigned long long b) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
-}
-
 // rounding to the factor precision u_f (Table 2): FP16 / BF16 round to nearest even
 __device__ __forceinline__ float round_uf(float v, int prec) {
   if (prec == (int)Prec::FP16) return __half2float(__float2half_rn(v));
@@ -386,11 +375,6 @@ __global__ void __launch_bounds__(64) gram_kernel(BArrays a, const GTile* __rest
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = C(0);
-  unsigned long long acc2[8][4];   // FP32: packed pairs of acc (zero bits are 0.0f, 0.0f)
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc2[i][q] = 0ull;
   // this thread stages column tid of each block; its scale factor stays in a register
   const bool okA = c0 + tid < n, okB = c1 + tid < n;
   const C* Ab = GramSrc<C>::A(a) + P.offA;
@@ -418,51 +402,20 @@ __global__ void __launch_bounds__(64) gram_kernel(BArrays a, const GTile* __rest
     }
     __syncthreads();
     const C (*B)[kLd] = diag ? SA : SB;
-    if constexpr (sizeof(C) == 4) {
-      // FP32: the 64 products of a k step as 32 packed pair FMAs (acc2[i][q] holds columns
-      // 2q, 2q + 1 of row i)
 #pragma unroll 4
-      for (int k = 0; k < 32; ++k) {
-        C av[8], bv[8];
-        lds4(&SA[k][ty * 8], *reinterpret_cast<C(*)[4]>(av));
-        lds4(&SA[k][ty * 8 + 4], *reinterpret_cast<C(*)[4]>(av + 4));
-        lds4(&B[k][tx * 8], *reinterpret_cast<C(*)[4]>(bv));
-        lds4(&B[k][tx * 8 + 4], *reinterpret_cast<C(*)[4]>(bv + 4));
-        unsigned long long b2[4];
+    for (int k = 0; k < 32; ++k) {
+      // vector reads from shared memory: 4 loads (FP32) for 64 FMA
+      C av[8], bv[8];
+      lds4(&SA[k][ty * 8], *reinterpret_cast<C(*)[4]>(av));
+      lds4(&SA[k][ty * 8 + 4], *reinterpret_cast<C(*)[4]>(av + 4));
+      lds4(&B[k][tx * 8], *reinterpret_cast<C(*)[4]>(bv));
+      lds4(&B[k][tx * 8 + 4], *reinterpret_cast<C(*)[4]>(bv + 4));
 #pragma unroll
-        for (int q = 0; q < 4; ++q) b2[q] = pack2(bv[2 * q], bv[2 * q + 1]);
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const unsigned long long a2 = pack2(av[i], av[i]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) fma2(acc2[i][q], a2, b2[q]);
-        }
-      }
-    } else {
-#pragma unroll 4
-      for (int k = 0; k < 32; ++k) {
-        // vector reads from shared memory: 4 loads (FP32) for 64 FMA
-        C av[8], bv[8];
-        lds4(&SA[k][ty * 8], *reinterpret_cast<C(*)[4]>(av));
-        lds4(&SA[k][ty * 8 + 4], *reinterpret_cast<C(*)[4]>(av + 4));
-        lds4(&B[k][tx * 8], *reinterpret_cast<C(*)[4]>(bv));
-        lds4(&B[k][tx * 8 + 4], *reinterpret_cast<C(*)[4]>(bv + 4));
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
-      }
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
-  }
-  if constexpr (sizeof(C) == 4) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[i][2 * q] = __uint_as_float((unsigned)(acc2[i][q] & 0xffffffffull));
-        acc[i][2 * q + 1] = __uint_as_float((unsigned)(acc2[i][q] >> 32));
-      }
   }
   if (g.slot >= 0) {
     C* w = work + (int64_t)g.slot * kNB * kNB;

@@ -15,9 +15,8 @@ namespace {
 
 // Two FP32 fused multiply-adds in one instruction (the packed f32x2 form of sm_100 and later):
 // c.lo = fma(a.lo, b.lo, c.lo), c.hi = fma(a.hi, b.hi, c.hi), each rounded to nearest like
-// fmaf; halves the FMA issue slots of the 8 x 8-per-thread GEMM tile. (In the 4 x 4-per-thread
-// tile the packing of the broadcast operands cost more than it saved: the inverse by doubling
-// took 0.37 ms instead of 0.25 ms at n = 2048, so that tile keeps scalar FMAs.)
+// fmaf; halves the FMA issue slots of the 8 x 8-per-thread GEMM tile (measured faster there; in
+// the 4 x 4-per-thread tile the packing of the broadcast operand cost more than it saved).
 __device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
   return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
 }
