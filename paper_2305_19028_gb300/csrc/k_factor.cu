@@ -982,9 +982,11 @@ __global__ void gram_sum_kernel(const double* __restrict__ part, int chunks, int
 }
 
 int gram_split_chunks(int64_t npad, int64_t mpad) {
-  // an FP64 Gram of a few output tiles runs on a few SMs: split its rows into chunks of 32
+  // an FP64 Gram of a few output tiles runs on a few SMs: split its rows into chunks of at least
+  // 8 rows, up to one per SM (a chunk's tile is FP64-bound on its SM: 400 x 64 in 14 chunks of
+  // 32 rows took 48 us)
   if (npad > 128) return 1;
-  return (int)std::min<int64_t>(64, std::max<int64_t>(1, mpad / 32));
+  return (int)std::min<int64_t>(152, std::max<int64_t>(1, mpad / 8));
 }
 
 void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
