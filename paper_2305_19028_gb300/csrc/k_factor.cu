@@ -981,19 +981,22 @@ __global__ void gram_sum_kernel(const double* __restrict__ part, int chunks, int
   H[e] = a;
 }
 
-int gram_split_chunks(int64_t npad, int64_t mpad) {
+int gram_split_chunks(int64_t npad, int64_t mpad, int num_sms) {
   // an FP64 Gram of a few output tiles runs on a few SMs: split its rows into chunks of at least
   // 8 rows, up to one per SM (a chunk's tile is FP64-bound on its SM: 400 x 64 in 14 chunks of
-  // 32 rows took 48 us)
+  // 32 rows took 48 us). Each chunk writes a full npad x npad FP64 partial that the sum kernel
+  // reads back; the partials are capped at 32 MB in all so that they stay in L2 (npad <= 128
+  // gives at most 128 KB per chunk, so the cap only binds for unusually many SMs).
   if (npad > 128) return 1;
-  return (int)std::min<int64_t>(152, std::max<int64_t>(1, mpad / 8));
+  const int64_t by_rows = std::max<int64_t>(1, mpad / 8);
+  const int64_t by_bytes = std::max<int64_t>(1, (int64_t)(32u << 20) / (npad * npad * 8));
+  return (int)std::min<int64_t>(std::max(1, num_sms), std::min(by_rows, by_bytes));
 }
 
 void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
-                      void* H, cudaStream_t s, void* work) {
+                      void* H, cudaStream_t s, void* work, int chunks) {
   const int M = (int)npad, K = (int)mpad;
   if (prec == Prec::FP64 && work != nullptr) {
-    const int chunks = gram_split_chunks(npad, mpad);
     if (chunks > 1) {
       // chunk z: rows [z*kc, min(K, (z+1)*kc)) of A_s^T A_s (upper tiles) into work[z]
       const int kc = (int)(((int64_t)K + chunks - 1) / chunks);

@@ -899,10 +899,10 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
       }
       if (!tc) {
         void* gw = nullptr;
-        const int chunks = tls::gram_split_chunks(npad, mpad);
+        const int chunks = tls::gram_split_chunks(npad, mpad, ctx->num_sms);
         if (pf == Prec::FP64 && chunks > 1)
           gw = slot(ctx, kSlotGsplit, sizeof(double) * (size_t)chunks * npad * npad);
-        tls::launch_gram_simt(AsT, pf, n, npad, mpad, ctx->H, st, gw);
+        tls::launch_gram_simt(AsT, pf, n, npad, mpad, ctx->H, st, gw, gw ? chunks : 1);
       }
       ctx->gram_tc_used = tc;
     }

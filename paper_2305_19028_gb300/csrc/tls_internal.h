@@ -115,11 +115,13 @@ void launch_scale_cast_T(const void* A, bool a_is_fp64, int64_t lda, int64_t m, 
                          void* AsT, Prec prec, cudaStream_t s);
 // H (npad x npad, type T = float for FP16/BF16/FP32 input, double for FP64) = AsT AsT^T,
 // identity on the padded diagonal.
-// work (may be NULL): for an FP64 Gram of npad <= 128, gram_split_chunks(npad, mpad) partial
+// work (may be NULL): for an FP64 Gram of npad <= 128, `chunks` (gram_split_chunks) partial
 // npad x npad FP64 matrices (the rows are split over that many CTA sets, summed in fixed order).
 void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
-                      void* H, cudaStream_t s, void* work = nullptr);
-int gram_split_chunks(int64_t npad, int64_t mpad);
+                      void* H, cudaStream_t s, void* work = nullptr, int chunks = 1);
+// Row chunks of the split FP64 Gram: at least 8 rows each, at most one per SM (num_sms, the
+// device's multiprocessor count) and at most 32 MB of partials in all; 1 when npad > 128.
+int gram_split_chunks(int64_t npad, int64_t mpad, int num_sms);
 // tcgen05 (UMMA) Gram for FP16/BF16 input into FP32 H. Returns false if the shape is not
 // supported (falls back to nothing: the caller decides).
 bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,

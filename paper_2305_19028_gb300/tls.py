@@ -376,9 +376,41 @@ def tls_kernel_launches() -> int:
 
 def tls_residual_noalloc(A, b, x, f, scal, stream=None):
     """The residual block with caller-provided device buffers and no device allocation.
-    A (m, n), b (m,), x (n,), f (n,), scal (5,): torch CUDA float64 tensors (A row-major with
-    unit column stride). Returns the status code (0 on success); raises on error."""
+    A (m, n), b (m,), x (n,), f (n,), scal (5,): torch CUDA float64 tensors on the current
+    device (A row-major with unit column stride, any row stride >= n; the vectors contiguous).
+    Every tensor is checked before the call (dtype, device, shape, strides), so the kernels
+    never index past the end of a buffer; a mismatch raises TLSError (TLS_ERR_ARG). Returns the
+    status code (0 on success); raises on error."""
+    import torch
+
+    def bad(msg):
+        raise TLSError(1, "tls_residual_noalloc: " + msg)
+
+    named = {"A": A, "b": b, "x": x, "f": f, "scal": scal}
+    for nm, t in named.items():
+        if not isinstance(t, torch.Tensor):
+            bad(f"{nm} is not a torch tensor")
+        if t.dtype != torch.float64:
+            bad(f"{nm} has dtype {t.dtype}, float64 required")
+        if t.device.type != "cuda":
+            bad(f"{nm} is not on a CUDA device")
+    cur = torch.cuda.current_device()
+    for nm, t in named.items():
+        if t.device.index != cur:
+            bad(f"{nm} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    if A.dim() != 2:
+        bad("A must be 2-D")
     m, n = A.shape
+    if m < 1 or n < 1:
+        bad(f"A is {m} x {n}")
+    if A.stride(1) != 1 or A.stride(0) < n:
+        bad(f"A must be row-major with unit column stride and row stride >= n "
+            f"(strides {A.stride()})")
+    for nm, t, need in (("b", b, m), ("x", x, n), ("f", f, n)):
+        if not t.is_contiguous() or t.numel() != need:
+            bad(f"{nm} must be contiguous with {need} elements (got {t.numel()})")
+    if not scal.is_contiguous() or scal.numel() < 5:
+        bad("scal must be contiguous with at least 5 elements")
     st = C.c_void_p(stream) if stream else None
     status = load().tls_residual_noalloc(m, n, C.c_void_p(A.data_ptr()), A.stride(0),
                                          C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),

@@ -143,3 +143,18 @@ def test_csr_validation_on_device():
         assert st == 1 and not ctx.value, name
     st, _ = _create_csr(m, n, rp, ci, va, b)
     assert st == 0
+
+
+def test_noalloc_binding_refuses_host_and_mistyped_tensors():
+    # the binding checks dtype and device before it loads or calls the library
+    torch = pytest.importorskip("torch")
+    A = torch.zeros((8, 4), dtype=torch.float64)
+    v8 = torch.zeros(8, dtype=torch.float64)
+    v4 = torch.zeros(4, dtype=torch.float64)
+    s5 = torch.zeros(5, dtype=torch.float64)
+    with pytest.raises(tls.TLSError, match="float64 required"):
+        tls.tls_residual_noalloc(A.float(), v8, v4, v4, s5)
+    with pytest.raises(tls.TLSError, match="not on a CUDA device"):
+        tls.tls_residual_noalloc(A, v8, v4, v4, s5)
+    with pytest.raises(tls.TLSError, match="not a torch tensor"):
+        tls.tls_residual_noalloc(A.numpy(), v8, v4, v4, s5)

@@ -163,6 +163,66 @@ def test_pcgtls_matches_oracle(u_f, u, modeA):
     assert _rel(w0s, w0) <= tol
 
 
+def _precond_residual(A, R, sigma2, f, w):
+    # ||R^{-T}(f - (A^T A - sigma^2 I) w)|| in FP64: what Alg. 3's ||s_j|| stands for
+    r = f - (A.T @ (A @ w) - sigma2 * w)
+    return float(np.linalg.norm(sla.solve_triangular(R, r, trans="T", lower=False)))
+
+
+@pytest.mark.parametrize("u_f,u,tol", [("fp16", "fp32", 1e-4), ("bf16", "fp32", 1e-3),
+                                       ("fp64", "fp64", 1e-9)])
+def test_pcgtls_tolerance_mode_matches_oracle(u_f, u, tol):
+    """PCGTLS with a relative tolerance on ||s_j|| (cg_fixed = 0, the mode the selector's
+    tolerance output uses) against the oracle's cg_tol mode on the same factor: the stop step
+    agrees to within one step (the FP32 recurrence crosses the threshold at its own rounding),
+    the GPU iterate meets the tolerance, and it equals the oracle's iterate of the same step
+    count element by element at the bound of the fixed-step parity test."""
+    m, n = 900, 200
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=16)
+    rng = np.random.default_rng(8)
+    f0 = rng.standard_normal(n)
+    f1 = rng.standard_normal(n)
+    sigma2 = 0.3 * p.D[-1] ** 2
+    cap = 60
+    with Ctx(p.A, p.b, u_f=u_f, u=u, cg_fixed=0, cg_tol=tol, cg_max=cap) as ctx:
+        RH, d, _ = tls.tls_export_factor(ctx)
+        w0, w1, it, bad = tls.tls_pcgtls(ctx, sigma2, f0, f1, steps=cap, cg_tol=tol)
+    R = RH * d[None, :]
+    kap = np.linalg.cond(RH)
+    ueps = U32 if u == "fp32" else U64
+    assert bad == [0, 0]
+    for f, w, i_gpu in ((f0, w0, it[0]), (f1, w1, it[1])):
+        wo, i_or, bad_o = O.pcgtls(p.A, R, sigma2, f, 0, cg_tol=tol, cg_max=cap)
+        assert not bad_o and 1 <= i_gpu < cap
+        assert abs(i_gpu - i_or) <= 1, (i_gpu, i_or)
+        s0 = float(np.linalg.norm(sla.solve_triangular(R, f, trans="T", lower=False)))
+        # the GPU stopped once its ||s_j|| met the tolerance: the true preconditioned residual
+        # of its iterate is within the recurrence drift (a few kappa n u) of tol ||s_0||
+        assert _precond_residual(p.A, R, sigma2, f, w) <= (tol + 50 * kap * n * ueps) * s0
+        # element-wise against the oracle's iterate after the same number of steps
+        w_same, _, _ = O.pcgtls(p.A, R, sigma2, f, i_gpu - 1)
+        assert _rel(w, w_same) <= 50 * kap * n * ueps
+
+
+@pytest.mark.parametrize("m,n,u_f,u,cg_tol", [(1000, 130, "fp16", "fp32", 1e-3),
+                                              (2500, 300, "bf16", "fp32", 1e-2),
+                                              (400, 40, "fp64", "fp64", 1e-6),
+                                              (4096, 512, "fp16", "fp32", 1e-4)])
+def test_solve_tolerance_mode_matches_oracle(m, n, u_f, u, cg_tol):
+    """Full RQI-PCGTLS with the inner solves to a relative tolerance (cg_fixed = 0) against the
+    oracle's RQI-PCGTLS in its cg_tol mode: sigma rel <= 1e-10, x rel <= 1e-8."""
+    p = synth.dense_problem(m, n, d_lo=1e-3, noise=1e-4, seed=5)
+    with Ctx(p.A, p.b, u_f=u_f, u=u, cg_fixed=0, cg_tol=cg_tol, cg_max=40) as ctx:
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=15)
+    xo, so, io = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=15, cg_tol=cg_tol, cg_max=40)
+    assert abs(sigma - so) <= 1e-10 * so, (sigma, so, info)
+    assert _rel(x, xo) <= 1e-8, info
+    assert info["stop_reason"] in (tls.STOP_PSI_UP, tls.STOP_TOL)
+    # the inner solves ran to the tolerance, not the fixed k+1 schedule
+    fixed = sum(2 * (k + 1) for k in range(1, info["rqi_steps"]))
+    assert info["cg_iters"] != fixed or info["rqi_steps"] <= 2
+
+
 def test_pcgtls_flags_indefinite_shift():
     p = synth.dense_problem(300, 40, d_lo=1e-1, noise=1e-3, seed=7)
     with Ctx(p.A, p.b, u_f="fp32", u="fp32") as ctx:

@@ -205,6 +205,147 @@ def test_ls_solution_matches_lstsq():
 
 
 # ------------------------------------------------------------------------------------------
+# Alg. 3 with a relative tolerance on ||s_j|| (the inexact-solve option, Sec. 3): the stop
+# test and the accuracy it implies, from an independent recomputation of the residual
+# ------------------------------------------------------------------------------------------
+def _precond_residual(A, R, sigma2, f, w):
+    """||R^{-T}(f - (A^T A - sigma^2 I) w)||: the s_j that Alg. 3 carries is R^{-T} times the
+    residual of its iterate w_j (exact arithmetic), recomputed here from w alone."""
+    r = f - (A.T @ (A @ w) - sigma2 * w)
+    return float(np.linalg.norm(sla.solve_triangular(R, r, trans="T", lower=False)))
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-8])
+@pytest.mark.parametrize("mode", ["A", "R"])
+def test_pcgtls_tolerance_mode_stops_at_the_relative_residual(tol, mode):
+    p = synth.dense_problem(400, 60, d_lo=1e-2, noise=1e-3, seed=13)
+    R = O.r_factor_qr(p.A)
+    sigma2 = 0.5 * p.D[-1] ** 2        # preconditioned spectrum in [0.5, 1]
+    f = np.random.default_rng(3).standard_normal(60)
+    s0 = float(np.linalg.norm(sla.solve_triangular(R, f, trans="T", lower=False)))
+    w, it, bad = O.pcgtls(p.A, R, sigma2, f, l=0, mode=mode, cg_tol=tol, cg_max=200)
+    assert not bad and 1 <= it < 200
+    # the returned iterate meets the tolerance (up to the rounding of the recomputation) ...
+    assert _precond_residual(p.A, R, sigma2, f, w) <= tol * s0 * (1 + 1e-6) + 1e-12 * s0
+    # ... and the one before it does not (the loop stops at the first step that meets it)
+    w_prev, it_prev, _ = O.pcgtls(p.A, R, sigma2, f, l=0, mode=mode, cg_tol=tol, cg_max=it - 1)
+    assert it_prev == it - 1
+    assert _precond_residual(p.A, R, sigma2, f, w_prev) > tol * s0 * (1 - 1e-6)
+    # accuracy implied by the tolerance: ||R (w - w*)|| <= ||s|| / lambda_min(C) with the
+    # preconditioned matrix C = I - sigma^2 R^{-T} R^{-1}, lambda_min = 1 - sigma^2/sigma'_n^2
+    w_ref = np.linalg.solve(p.A.T @ p.A - sigma2 * np.eye(60), f)
+    lam = 1.0 - sigma2 / p.D[-1] ** 2
+    assert np.linalg.norm(R @ (w - w_ref)) <= tol * s0 / lam * (1 + 1e-6) + 1e-10 * s0
+
+
+def test_pcgtls_tolerance_mode_caps_at_cg_max():
+    p = synth.dense_problem(400, 60, d_lo=1e-3, noise=1e-3, seed=14)
+    R = O.r_factor_cholesky(p.A[:, :]) * (1.0 + 1e-3)   # an inexact factor: slow convergence
+    f = np.ones(60)
+    _, it, bad = O.pcgtls(p.A, R, 0.1 * p.D[-1] ** 2, f, l=0, cg_tol=1e-30, cg_max=7)
+    assert it == 7 and not bad
+
+
+# ------------------------------------------------------------------------------------------
+# the psi stop rule of Sec. 3 (strict) and its >= variant of Sec. 4.2, on a prescribed psi
+# sequence: the rule decides from the psi values alone
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("ge,stop_k,best_k", [(True, 3, 2), (False, 5, 4)])
+def test_psi_rule_on_prescribed_sequence(monkeypatch, ge, stop_k, best_k):
+    seq = [5.0, 4.0, 4.0, 3.0, 3.5, 1.0, 0.5]
+    real = O.residual_block
+    calls = []
+
+    def fake(A, b, x):
+        r, s2, f, g, _ = real(A, b, x)
+        calls.append(1)
+        return r, s2, f, g, seq[len(calls) - 1]
+
+    monkeypatch.setattr(O, "residual_block", fake)
+    p = synth.dense_problem(60, 5, d_lo=1e-1, noise=1e-3, seed=2)
+    _, _, info = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=20, psi_rule_ge=ge)
+    # Sec. 4.2 stops on psi_{k+1} >= psi_k: at the repeated 4.0 (k = 3), keeping k = 2;
+    # Sec. 3 stops on psi_{k+1} > psi_k: at 3.5 (k = 5), keeping the last non-increasing k = 4
+    assert info.stop_reason == O.STOP_PSI_UP
+    assert info.rqi_steps == stop_k and info.best_k == best_k
+    assert info.psi == seq[:stop_k]
+
+
+def test_psi_rule_ge_never_runs_longer_than_the_strict_rule():
+    for seed in range(4):
+        p = synth.dense_problem(300, 30, d_lo=1e-2, noise=1e-4, seed=seed)
+        _, s_ge, i_ge = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=15, psi_rule_ge=True)
+        _, s_gt, i_gt = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=15, psi_rule_ge=False)
+        assert i_ge.rqi_steps <= i_gt.rqi_steps
+        # both end at the TLS solution (the secular-equation closed form)
+        s_ref, _, _ = tls_by_secular(p)
+        assert abs(s_ge - s_ref) <= weyl_sigma_tol(p.A, p.b) + 1e-13 * s_ref
+
+
+# ------------------------------------------------------------------------------------------
+# the column-scaled Gram matrix and the Cholesky success bounds (Sec. 3.1)
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("m,n", [(50, 8), (300, 40)])
+def test_scaled_gram_is_the_gram_of_the_equilibrated_columns(m, n):
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-3, 2, size=n)
+    H, d = O.scaled_gram(A)
+    # D holds the column norms; H has a unit diagonal and is symmetric
+    assert np.allclose(d, np.linalg.norm(A, axis=0), rtol=1e-14)
+    assert np.allclose(np.diag(H), 1.0, rtol=0, atol=1e-14)
+    assert np.array_equal(H, H.T)
+    # its eigenvalues are the squared singular values of A D^{-1} (an SVD, not a Gram)
+    sv = np.linalg.svd(A / np.linalg.norm(A, axis=0), compute_uv=False)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(H)), np.sort(sv ** 2), rtol=1e-10, atol=1e-14)
+
+
+def _two_column_matrix(theta, c1, c2, m=6):
+    """Columns c1 e_1 and c2 (cos(theta) e_1 + sin(theta) e_2): the scaled Gram matrix is
+    [[1, cos theta], [cos theta, 1]], so lambda_min(H) = 1 - cos(theta) in closed form."""
+    A = np.zeros((m, 2))
+    A[0, 0] = c1
+    A[0, 1] = c2 * math.cos(theta)
+    A[1, 1] = c2 * math.sin(theta)
+    return A
+
+
+@pytest.mark.parametrize("theta", [0.3, 1.0, math.pi / 2])
+def test_cholesky_bounds_on_known_spectrum(theta):
+    A = _two_column_matrix(theta, 3.0, 0.02)
+    b = np.array([1.0, -2.0, 0.5, 0.25, 0.0, 1.0])
+    c = O.constraints(A, b)
+    lam = 1.0 - math.cos(theta)
+    n = 2
+    # scaled-Cholesky success bound of Sec. 3.1 at the closed-form lambda_min(H)
+    assert c["chol_scaled"] == pytest.approx(lam / ((2 * lam + n) * (n + 1)), rel=1e-12)
+    # Wilkinson's bound 1/(20 n^{3/2} kappa(A)^2) with kappa from the closed-form 2x2 Gram
+    G = np.array([[9.0, 3.0 * 0.02 * math.cos(theta)], [3.0 * 0.02 * math.cos(theta), 4e-4]])
+    ev = np.linalg.eigvalsh(G)
+    kappa = math.sqrt(ev[-1] / ev[0])
+    assert c["kappa"] == pytest.approx(kappa, rel=1e-9)
+    assert c["chol_wilkinson"] == pytest.approx(1.0 / (20 * n ** 1.5 * kappa ** 2), rel=1e-9)
+    # orthogonal columns (theta = pi/2): H = I, the bound is 1/((2 + n)(n + 1)) whatever the norms
+    if theta == math.pi / 2:
+        assert c["chol_scaled"] == pytest.approx(1.0 / 12.0, rel=1e-12)
+        assert c["kappa"] == pytest.approx(3.0 / 0.02, rel=1e-12)
+
+
+def test_van_huffel_scaled_gram_closed_form():
+    # unperturbed Sec. 4.5 matrix (n x (n-2)): A^T A = n^2 I - n J, diagonal n^2 - n, so
+    # H = (n I - J) / (n - 1) with eigenvalues n / (n - 1) (multiplicity n - 3) and
+    # (n - (n - 2)) / (n - 1) = 2 / (n - 1)
+    n = 40
+    p = synth.van_huffel_problem(n=n, eps=0.0)
+    H, _ = O.scaled_gram(p.A)
+    ev = np.linalg.eigvalsh(H)
+    assert ev[0] == pytest.approx(2.0 / (n - 1), rel=1e-12)
+    assert np.allclose(ev[1:], n / (n - 1), rtol=1e-12)
+    c = O.constraints(p.A, p.b)
+    lam = 2.0 / (n - 1)
+    assert c["chol_scaled"] == pytest.approx(lam / ((2 * lam + (n - 2)) * (n - 1)), rel=1e-12)
+
+
+# ------------------------------------------------------------------------------------------
 # printed values of the paper
 # ------------------------------------------------------------------------------------------
 def test_table2_unit_roundoffs():
@@ -369,3 +510,73 @@ def test_oracle_on_sparse_input_matches_dense_input():
     x2, s2, _ = O.rqi_pcgtls(A.toarray(), p.b, tol=0.0, max_rqi=12)
     assert abs(s1 - s2) <= 1e-12 * s2
     assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x2)
+
+
+# planted mistakes in the parts pinned above: each must fail one of those pins
+_ORIG_SCALED_GRAM = O.scaled_gram
+_ORIG_CONSTRAINTS = O.constraints
+_ORIG_PCGTLS = O.pcgtls
+_ORIG_RQI = O.rqi_pcgtls
+
+
+def _mut_one_sided_scaling(A):
+    G = A.T @ A
+    d = np.sqrt(np.diag(G))
+    return G / d[:, None] ** 2, d                  # D^{-2} G instead of D^{-1} G D^{-1}
+
+
+def _mut_lambda_max(A, b, n_plus_1_sigma=None):
+    c = _ORIG_CONSTRAINTS(A, b, n_plus_1_sigma)
+    n = A.shape[1]
+    H, _ = O.scaled_gram(A)
+    lam = np.linalg.eigvalsh(H)[-1]                # largest instead of smallest eigenvalue
+    c["chol_scaled"] = lam / ((2.0 * lam + n) * (n + 1))
+    return c
+
+
+def _mut_tol_on_eta(A, R, sigma2, f, l, mode="A", cg_tol=None, cg_max=None):
+    # compares eta = ||s||^2 with tol * ||s_0|| (a dropped square root)
+    return _ORIG_PCGTLS(A, R, sigma2, f, l, mode, None if cg_tol is None else cg_tol ** 2,
+                        cg_max)
+
+
+def _mut_ge_as_gt(*a, **k):
+    k["psi_rule_ge"] = False
+    return _ORIG_RQI(*a, **k)
+
+
+def _new_pins_pass(monkeypatch_fixture=None) -> bool:
+    try:
+        test_scaled_gram_is_the_gram_of_the_equilibrated_columns(50, 8)
+        test_cholesky_bounds_on_known_spectrum(0.3)
+        test_van_huffel_scaled_gram_closed_form()
+        test_pcgtls_tolerance_mode_stops_at_the_relative_residual(1e-3, "A")
+    except AssertionError:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("target,mutant", [
+    ("scaled_gram", _mut_one_sided_scaling), ("constraints", _mut_lambda_max),
+    ("pcgtls", _mut_tol_on_eta)])
+def test_planted_mistakes_in_scaling_bounds_and_tolerance_are_caught(monkeypatch, target, mutant):
+    assert _new_pins_pass()
+    monkeypatch.setattr(O, target, mutant)
+    assert not _new_pins_pass(), f"planted mistake in {target} went unnoticed"
+
+
+def test_planted_psi_rule_mistake_is_caught(monkeypatch):
+    # a >= rule that behaves like > must fail the prescribed-sequence pin
+    seq = [5.0, 4.0, 4.0, 3.0, 3.5, 1.0, 0.5]
+    real = O.residual_block
+    calls = []
+
+    def fake(A, b, x):
+        r, s2, f, g, _ = real(A, b, x)
+        calls.append(1)
+        return r, s2, f, g, seq[len(calls) - 1]
+
+    monkeypatch.setattr(O, "residual_block", fake)
+    p = synth.dense_problem(60, 5, d_lo=1e-1, noise=1e-3, seed=2)
+    _, _, info = _mut_ge_as_gt(p.A, p.b, tol=0.0, max_rqi=20, psi_rule_ge=True)
+    assert (info.rqi_steps, info.best_k) != (3, 2)
