@@ -71,6 +71,72 @@ def _oracle_solve(p):
     return O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=MAX_RQI)
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _timed_dense_oracle(seed: int):
+    """Pool worker: one FP64 oracle solve of the dense benchmark problem (seed), timed."""
+    p = _problem(seed)
+    t0 = time.perf_counter()
+    x, s, _ = _oracle_solve(p)
+    return x, s, time.perf_counter() - t0
+
+
+def _single_thread_pool(fn, items, procs):
+    """map(fn, items) on `procs` spawned single-threaded processes; (results, wall seconds)."""
+    import multiprocessing as mp
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(processes=procs) as pool:
+            res = pool.map(fn, items, chunksize=1)
+        dt = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return res, dt
+
+
+def _cpu_baseline_dense(seed: int):
+    """The CPU plan for the dense benchmark problem: single-core latency as the median of three
+    single-threaded solves (run side by side), and throughput as P = nproc single-threaded
+    solves run at once on all host cores (solves / wall time). Returns (baseline, (x, sigma))."""
+    nproc = os.cpu_count() or 1
+    lat, _ = _single_thread_pool(_timed_dense_oracle, [seed] * 3, 3)
+    thr, wall = _single_thread_pool(_timed_dense_oracle, [seed] * nproc, nproc)
+    times = sorted(t for _, _, t in lat)
+    x, s, _ = lat[0]
+    base = {"value": nproc / wall, "unit": "solves/s", "cores": nproc, "kind": "oracle",
+            "sample": f"{nproc} FP64 solves of the {M_ROWS}x{N_COLS} problem at once, one "
+                      f"single-threaded process per core ({wall:.1f} s wall)",
+            "latency_s_median": statistics.median(times), "latency_s": times,
+            "latency_sample": "3 single-threaded solves (one core each), median",
+            "nproc": nproc, "cpu_model": _cpu_model()}
+    return base, (x, s)
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
 
@@ -198,7 +264,9 @@ def run_reference(args, ws, rank):
         "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS, "d_lo": D_LO, "noise": NOISE,
                    "seed": 0, "solver": "FP64 CPU oracle (numpy/OpenBLAS), Householder QR R"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} full solves of the {M_ROWS}x{N_COLS} problem"},
+                         "sample": f"{args.steps} full solves of the {M_ROWS}x{N_COLS} problem "
+                                   f"(numpy/OpenBLAS threads)",
+                         "nproc": cores, "cpu_model": _cpu_model()},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -211,7 +279,46 @@ def run_reference(args, ws, rank):
 RESID_PIPE_TRAFFIC_PER_ROW = (134.346e6 + 0.067e6) / 8192
 
 
-def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int = -1) -> dict:
+def paired_iteration_bytes(m: int, n: int) -> int:
+    """Algorithmic bytes of one paired PCGTLS iteration (both right-hand sides): A_u in FP32
+    once (4 m n), the two triangular factors' products with R_H held in u_f = FP16
+    (2 x n (n + 1) / 2 x 2 B) and about 24 FP32 n-vectors (q, w, y, s, p and partial sums)."""
+    return 4 * m * n + 2 * n * (n + 1) + 24 * 4 * n
+
+
+def _inner_loop(prof: dict, units: dict, peaks: dict, m: int, n: int) -> dict:
+    """HBM roofline of the PCGTLS inner loop per paired iteration: the paired solves' device
+    time (one launch per solve: passes over A, reductions and W / W^T products of every step)
+    divided by the PCGTLS steps they ran."""
+    cnt, ms = prof.get("pcg_solve2", (0, 0.0))
+    it = units.get("pcg_solve2", 0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "measured" if peaks else "fallback"
+    byts = paired_iteration_bytes(m, n)
+    if cnt and it:
+        per = ms * 1e-3 / it
+        ach = byts / per / 1e9
+        return {"kernel": "pcg_fused_kernel (one launch per paired PCGTLS solve: t = A q, "
+                          "A^T t, reductions, W^T y, W p; FP32)",
+                "unit_of_work": "one paired PCGTLS iteration", "bound": "hbm", "achieved": ach,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "peak_source": src, "us_per_iteration": per * 1e6, "iterations": it,
+                "launches": cnt, "algorithmic_bytes": byts}
+    # multi-launch path: the pass launches plus the step-tail launches per iteration
+    c2, m2 = prof.get("pcg_pass2", (0, 0.0))
+    cr, mr = prof.get("pcg_reduce", (0, 0.0))
+    if not c2:
+        return {}
+    per = (m2 + mr * c2 / max(1, cr)) * 1e-3 / c2
+    ach = byts / per / 1e9
+    return {"kernel": "pass + step tail per paired iteration (multi-launch path)",
+            "unit_of_work": "one paired PCGTLS iteration", "bound": "hbm", "achieved": ach,
+            "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
+            "us_per_iteration": per * 1e6, "iterations": c2, "algorithmic_bytes": byts}
+
+
+def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int = -1,
+              units: dict | None = None) -> dict:
     cnt, ms = prof.get(cls, (0, 0.0))
     if cnt == 0:
         return {}
@@ -219,6 +326,8 @@ def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int 
     hbm = peaks.get("hbm_gbs", 6800.0)
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
     src = "measured" if peaks else "fallback"
+    if cls == "pcg_solve2":
+        return _inner_loop(prof, units or {}, peaks, m, n)
     if cls == "pcg_pass2":
         unit_bytes = m * n * 4 + 2 * n * 4 * 2          # A_u once + q in / partial out
         ach = unit_bytes / avg_s / 1e9
@@ -319,6 +428,7 @@ def run_ours(args, ws, rank, local):
         step()
     torch.cuda.synchronize()
     prof = tls.tls_profile_get(ctx)
+    units = tls.tls_profile_units(ctx)
     tls.tls_profile_enable(ctx, False)
     last_x, last_s = x, s
 
@@ -371,17 +481,15 @@ def run_ours(args, ws, rank, local):
                  "rqi_steps": ip["rqi_steps"], "cg_iters": ip["cg_iters"]}
     tls.tls_destroy(ctx)
 
-    # CPU oracle leg, then the accuracy of every result against it
+    # CPU oracle leg (rank 0 of a one-GPU run: the timed CPU baseline, whose first solve is
+    # also the accuracy reference; other ranks: one multi-threaded solve of their problem),
+    # then the accuracy of every result against it
     if not args.no_cpu:
-        t0 = time.perf_counter()
-        xo, so, io = _oracle_solve(p)
-        t_or = time.perf_counter() - t0
-        ref = (xo, so)
-        if rank == 0:
-            cpu = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(),
-                   "kind": "oracle",
-                   "sample": f"1 full FP64 solve of the {M_ROWS}x{N_COLS} problem "
-                             f"({t_or:.2f} s, numpy/OpenBLAS threads)"}
+        if rank == 0 and ws == 1:
+            cpu, ref = _cpu_baseline_dense(rank)
+        else:
+            xo, so, io = _oracle_solve(p)
+            ref = (xo, so)
     ok = _total(sum(int(accurate(x_, s_)) for x_, s_ in results), ws)
     err = None
     if ref is not None:
@@ -404,9 +512,9 @@ def run_ours(args, ws, rank, local):
     dom = max(total, key=total.get)
     share = {k: round(v / max(1e-9, sum(total.values())), 4) for k, v in total.items()}
     v64 = infos[-1]["pass_variant"][0]
-    roof = _roofline(prof, peaks, dom, M_ROWS, N_COLS, v64) or _roofline(prof, peaks, "pcg_pass2",
-                                                                        M_ROWS, N_COLS)
-    inner = _roofline(prof, peaks, "pcg_pass2", M_ROWS, N_COLS)
+    roof = (_roofline(prof, peaks, dom, M_ROWS, N_COLS, v64, units) or
+            _inner_loop(prof, units, peaks, M_ROWS, N_COLS))
+    inner = _inner_loop(prof, units, peaks, M_ROWS, N_COLS)
     value = ok / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -425,6 +533,7 @@ def run_ours(args, ws, rank, local):
         "roofline": roof, "inner_loop_roofline": inner,
         "kernel_share": share, "kernel_ms": {k: round(v, 4) for k, v in total.items()},
         "kernel_launches": {k: v[0] for k, v in prof.items()},
+        "kernel_units": {k: v for k, v in units.items() if v},
         "kernel_profile": "profiled steps after the timed region (every launch bracketed by "
                           "CUDA events on the context's stream)",
         "gpu_launches": int(launches),

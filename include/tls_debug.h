@@ -75,7 +75,10 @@ enum {
   TLS_PROF_PCG_REDUCE = 8,   /* PCGTLS partial reduction and w, y updates       */
   TLS_PROF_PCG_GEMV = 9,     /* products with W and W^T, s and p recurrences    */
   TLS_PROF_VEC = 10,         /* FP64 RQI vector updates                          */
-  TLS_PROF_NCLASSES = 11
+  TLS_PROF_PCG_SOLVE2 = 11,  /* a whole paired PCGTLS solve in one launch (passes, */
+                             /* reductions, W and W^T products of every step)    */
+  TLS_PROF_PCG_SOLVE1 = 12,  /* the same for one right-hand side (the LS start)  */
+  TLS_PROF_NCLASSES = 13
 };
 
 /*
@@ -104,6 +107,16 @@ tls_status tls_set_pass_variant(tls_ctx* ctx, int variant_fp64, int variant_u);
 tls_status tls_set_small_path(tls_ctx* ctx, int path);
 /* Launch count and summed device milliseconds of one class (TLS_PROF_*). */
 tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* ms);
+/* Units of work behind the timed launches of class cls: for TLS_PROF_PCG_SOLVE2 / SOLVE1 the
+ * PCGTLS steps (passes over A) those launches ran; 0 for the other classes. */
+tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units);
+/*
+ * tls_set_pcg_fused -- how dense FP32 PCGTLS solves (A-explicit operator) run: 0 automatic (one
+ * persistent cooperative launch per solve where the shape fits, else the multi-launch path),
+ * 1 the one-launch solve (TLS_ERR_ARG when the shape does not fit it), 2 the multi-launch path
+ * (a pass launch and a cooperative step-tail launch per step). Kept until changed.
+ */
+tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode);
 /* The same per-class timing for a packed batch (classes as above; PCG_REDUCE covers the
  * per-problem PCGTLS step including its W / W^T products; VEC the small per-problem kernels). */
 tls_status tls_batch_profile_enable(tls_batch* bt, int on);

@@ -44,6 +44,8 @@ struct tls_ctx {
   // cudaMalloc / cudaFree, which synchronise the device, between repeated calls)
   DevBuf slots[24];
   int small_path = 0;      // tls_set_small_path
+  int pcg_fused = 0;       // tls_set_pcg_fused
+  unsigned int* fbar = nullptr;   // grid barrier words of the one-launch PCGTLS solve (96)
   RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
 
   // problem data (device)
@@ -120,6 +122,8 @@ struct tls_ctx {
   int pused = 0;
   double prof_ms[TLS_PROF_NCLASSES] = {};
   int64_t prof_cnt[TLS_PROF_NCLASSES] = {};
+  int64_t prof_units[TLS_PROF_NCLASSES] = {};
+  bool last_pcg_fused = false;     // the last PCGTLS solve ran as one launch
 };
 
 namespace {
@@ -227,15 +231,18 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->sout = alloc_t<double>(ctx, 8);
   ctx->gpart = alloc_t<double>(ctx, 4096);
   ctx->counter = alloc_t<unsigned int>(ctx, 32);   // last-CTA counters; [4..22] PCGTLS step
+  ctx->fbar = alloc_t<unsigned int>(ctx, 96);
   ctx->derr = alloc_t<int>(ctx, 1);
   ctx->sc = alloc_t<PcgScalars>(ctx, 1);
   ctx->rs = alloc_t<RqiScalars>(ctx, 1);
   if (!ctx->b || !ctx->x || !ctx->x_best || !ctx->f || !ctx->d || !ctx->dinv || !ctx->sout ||
-      !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs || !ctx->derr || !ctx->dinv32) {
+      !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs || !ctx->derr || !ctx->dinv32 ||
+      !ctx->fbar) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
   TLS_CK(cudaMemsetAsync(ctx->counter, 0, 32 * sizeof(unsigned int), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->sc, 0, sizeof(PcgScalars), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->rs, 0, sizeof(RqiScalars), ctx->stream));
@@ -374,6 +381,36 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
                                        : reinterpret_cast<const T*>(ctx->A32);
   const T* W = static_cast<const T*>(ctx->W);
   const T* WT = static_cast<const T*>(ctx->WT);
+  if constexpr (std::is_same<T, float>::value) {
+  if (modeA && !ctx->sparse && steps > 0 && ctx->pcg_fused != 2 &&
+      tls::pcg_fused_supported(npad, nr)) {
+    // the whole solve in one persistent cooperative launch
+    cudaError_t e;
+    {
+      Prof pr(ctx, nr == 2 ? TLS_PROF_PCG_SOLVE2 : TLS_PROF_PCG_SOLVE1);
+      e = tls::launch_pcg_fused(
+          reinterpret_cast<const float*>(ctx->A32), ctx->m, ctx->n, npad, nr, fin0, s0, fin1,
+          ctx->dinv, ctx->dinv32, reinterpret_cast<const float*>(W),
+          reinterpret_cast<const float*>(WT), reinterpret_cast<float*>(v.w),
+          reinterpret_cast<float*>(v.y), reinterpret_cast<float*>(v.s),
+          reinterpret_cast<float*>(v.p0), reinterpret_cast<float*>(v.p1),
+          reinterpret_cast<float*>(v.q), static_cast<float*>(ctx->part), ctx->gpart, ctx->sc,
+          sigma2, cg_tol, steps, ctx->fbar, ctx->derr, ctx->num_sms, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+      ctx->last_pcg_fused = true;
+      if (ctx->prof_on && nr == 1) ctx->prof_units[TLS_PROF_PCG_SOLVE1] += steps;
+      return TLS_OK;
+    }
+    (void)cudaGetLastError();
+    if (ctx->pcg_fused == 1) {
+      set_err(ctx, std::string("one-launch PCGTLS solve failed: ") + cudaGetErrorString(e));
+      return TLS_ERR_CUDA;
+    }
+    ctx->pcg_fused = 2;   // not launchable here (e.g. no cooperative residency): multi-launch
+  }
+  }
+  ctx->last_pcg_fused = false;
   {
     Prof pr(ctx, TLS_PROF_PCG_GEMV);
     tls::launch_pcg_prep<T>(fin0, s0, fin1, nr, ctx->n, npad, ctx->dinv, v.y, v.w, v.p0, v.p1,
@@ -604,6 +641,8 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
       TLS_CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
     TLS_CK(cudaStreamSynchronize(st));
     if (k > 1) {
+      if (ctx->prof_on && ctx->last_pcg_fused)
+        ctx->prof_units[TLS_PROF_PCG_SOLVE2] += ctx->h_sc->passes;
       cg_total += ctx->h_sc->iters[0] + ctx->h_sc->iters[1];
       not_spd |= ctx->h_sc->not_spd[0] | ctx->h_sc->not_spd[1];
     }
@@ -664,6 +703,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   }
   if (herr != 0) {
     TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), st));
+    TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), st));
     set_err(ctx, "a bounded device wait expired (code " + std::to_string(herr) + ")");
     return TLS_ERR_TIMEOUT;
   }
@@ -1027,9 +1067,17 @@ static tls_status pcgtls_host(tls_ctx* ctx, int nr, double sigma2, const double*
   if (s != TLS_OK) return s;
   UVecs<T> v = uvecs<T>(ctx);
   std::vector<T> hw((size_t)2 * npad);
+  int herr = 0;
   TLS_CK(cudaMemcpyAsync(hw.data(), v.w, sizeof(T) * 2 * npad, cudaMemcpyDeviceToHost, st));
   TLS_CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaMemcpyAsync(&herr, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLS_CK(cudaStreamSynchronize(st));
+  if (herr != 0) {
+    TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), st));
+    TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), st));
+    set_err(ctx, "a bounded device wait expired (code " + std::to_string(herr) + ")");
+    return TLS_ERR_TIMEOUT;
+  }
   for (int64_t j = 0; j < n; ++j) {
     w0[j] = (double)hw[j];
     if (nr > 1 && w1) w1[j] = (double)hw[npad + j];
@@ -1585,6 +1633,7 @@ tls_status tls_profile_enable(tls_ctx* ctx, int on) {
   for (int i = 0; i < TLS_PROF_NCLASSES; ++i) {
     ctx->prof_ms[i] = 0.0;
     ctx->prof_cnt[i] = 0;
+    ctx->prof_units[i] = 0;
   }
   return TLS_OK;
 }
@@ -1593,6 +1642,19 @@ tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* 
   if (!ctx || cls < 0 || cls >= TLS_PROF_NCLASSES) return TLS_ERR_ARG;
   if (count) *count = ctx->prof_cnt[cls];
   if (ms) *ms = ctx->prof_ms[cls];
+  return TLS_OK;
+}
+
+tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units) {
+  if (!ctx || !units || cls < 0 || cls >= TLS_PROF_NCLASSES) return TLS_ERR_ARG;
+  *units = ctx->prof_units[cls];
+  return TLS_OK;
+}
+
+tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 2) return TLS_ERR_ARG;
+  if (mode == 1 && !tls::pcg_fused_supported(ctx->npad, 2)) return TLS_ERR_ARG;
+  ctx->pcg_fused = mode;
   return TLS_OK;
 }
 

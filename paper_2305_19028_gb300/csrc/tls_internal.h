@@ -51,7 +51,7 @@ struct PcgScalars {
   int not_spd[2];     // stopped on delta_j < 0
   int iters[2];       // completed steps
   int nr;             // number of right-hand sides (1 or 2)
-  int pad_;
+  int passes;         // passes over A run by the last one-launch solve
   unsigned int counter[4];   // last-block counters, always 0 between kernels
 };
 
@@ -201,6 +201,19 @@ bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* 
                      const T* dinv, PcgScalars* sc, const double* tt, const T* WT, const T* W,
                      T* s, const T* p_cur, T* p_next, double* gpart, bool next,
                      unsigned int* bar, int* err, int num_sms, cudaStream_t st);
+// A whole PCGTLS solve (A-explicit operator, FP32, nr right-hand sides fin0 * fin0_scale and
+// fin1, `steps` steps or fewer on the stop flags) in one persistent cooperative launch of
+// num_sms CTAs (k_pcg_fused.cu). Vectors nr x npad; part: num_sms x nr x npad floats; gpart: at
+// least 6 num_sms doubles; bar: 96 zero-initialised words (zero again after every launch unless
+// a bounded wait expired, which also records a code in *err). Writes w and the scalars in sc.
+bool pcg_fused_supported(int64_t npad, int nr);
+cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad, int nr,
+                             const double* fin0, double fin0_scale, const double* fin1,
+                             const double* dinv64, const float* dinv, const float* W,
+                             const float* WT, float* w, float* y, float* s, float* pa, float* pb,
+                             float* q, float* part, double* gpart, PcgScalars* sc, double sigma2,
+                             double cg_tol, int steps, unsigned int* bar, int* err, int num_sms,
+                             cudaStream_t st);
 // Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).
 template <typename T>
 void launch_pcg_reduce(const T* part, int P, int64_t npad, const T* q, T* w, T* y,

@@ -37,10 +37,11 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_batch_profile_elems", "tls_mlp_forward", "tls_mlp_grad", "tls_mlp_adam",
            "tls_batch_set_selector", "tls_batch_features", "tls_set_pass_variant",
            "tls_set_selector", "tls_features", "tls_pool_enable", "tls_pool_trim",
-           "tls_pool_stats", "tls_pool_poison", "tls_set_small_path"]
+           "tls_pool_stats", "tls_pool_poison", "tls_set_small_path", "tls_profile_units",
+           "tls_set_pcg_fused"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
-                "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec"]
+                "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec", "pcg_solve2", "pcg_solve1"]
 
 
 class tls_options(C.Structure):
@@ -143,6 +144,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_batch_features": (C.c_int, [v, C.POINTER(C.c_float)]),
         "tls_set_pass_variant": (C.c_int, [v, C.c_int, C.c_int]),
         "tls_set_small_path": (C.c_int, [v, C.c_int]),
+        "tls_profile_units": (C.c_int, [v, C.c_int, C.POINTER(i64)]),
+        "tls_set_pcg_fused": (C.c_int, [v, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -368,6 +371,21 @@ def tls_profile_get(ctx) -> dict:
         _check(load().tls_profile_get(ctx, i, C.byref(cnt), C.byref(ms)), ctx)
         out[name] = (cnt.value, ms.value)
     return out
+
+
+def tls_profile_units(ctx) -> dict:
+    """{class name: units of work behind its timed launches} (PCGTLS steps for pcg_solve*)."""
+    out = {}
+    for i, name in enumerate(PROF_CLASSES):
+        u = C.c_int64()
+        _check(load().tls_profile_units(ctx, i, C.byref(u)), ctx)
+        out[name] = u.value
+    return out
+
+
+def tls_set_pcg_fused(ctx, mode: int) -> None:
+    """0 automatic, 1 one persistent launch per PCGTLS solve, 2 the multi-launch path."""
+    _check(load().tls_set_pcg_fused(ctx, int(mode)), ctx)
 
 
 def tls_kernel_launches() -> int:

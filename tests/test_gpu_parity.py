@@ -28,8 +28,10 @@ def _rel(a, b):
 
 
 class Ctx:
-    def __init__(self, A, b, u_f="fp16", u="fp32", **opt):
+    def __init__(self, A, b, u_f="fp16", u="fp32", fused=0, **opt):
         self.ctx = tls.tls_create_dense(A, b)
+        if fused:
+            tls.tls_set_pcg_fused(self.ctx, fused)
         self.opt = tls.tls_default_options(u=u, **opt)
         tls.tls_factor(self.ctx, u_f, self.opt)
 
@@ -136,9 +138,12 @@ def test_precond_matches_oracle(u_f, u):
     assert _rel(uu, u_ref) <= 2 * tol * kap
 
 
-@pytest.mark.parametrize("u_f,u", [("fp16", "fp32"), ("fp64", "fp64")])
+@pytest.mark.parametrize("u_f,u,fused", [("fp16", "fp32", 1), ("fp16", "fp32", 2),
+                                         ("fp64", "fp64", 0)])
 @pytest.mark.parametrize("modeA", [1, 0])
-def test_pcgtls_matches_oracle(u_f, u, modeA):
+def test_pcgtls_matches_oracle(u_f, u, fused, modeA):
+    """Both FP32 forms of the A-explicit solve (one persistent launch per solve, fused = 1; a
+    pass launch and a step-tail launch per step, fused = 2) and Alg. 3 as printed (mode R)."""
     m, n = 900, 200
     p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=6)
     rng = np.random.default_rng(2)
@@ -146,7 +151,7 @@ def test_pcgtls_matches_oracle(u_f, u, modeA):
     f1 = rng.standard_normal(n)
     sigma2 = 0.3 * p.D[-1] ** 2
     steps = 4
-    with Ctx(p.A, p.b, u_f=u_f, u=u, mode_A=modeA) as ctx:
+    with Ctx(p.A, p.b, u_f=u_f, u=u, mode_A=modeA, fused=fused) as ctx:
         RH, d, _ = tls.tls_export_factor(ctx)
         w0, w1, it, bad = tls.tls_pcgtls(ctx, sigma2, f0, f1, steps=steps)
         w0s, _, it1, _ = tls.tls_pcgtls(ctx, sigma2, f0, None, steps=steps)
@@ -169,9 +174,9 @@ def _precond_residual(A, R, sigma2, f, w):
     return float(np.linalg.norm(sla.solve_triangular(R, r, trans="T", lower=False)))
 
 
-@pytest.mark.parametrize("u_f,u,tol", [("fp16", "fp32", 1e-4), ("bf16", "fp32", 1e-3),
-                                       ("fp64", "fp64", 1e-9)])
-def test_pcgtls_tolerance_mode_matches_oracle(u_f, u, tol):
+@pytest.mark.parametrize("u_f,u,tol,fused", [("fp16", "fp32", 1e-4, 1), ("fp16", "fp32", 1e-4, 2),
+                                             ("bf16", "fp32", 1e-3, 1), ("fp64", "fp64", 1e-9, 0)])
+def test_pcgtls_tolerance_mode_matches_oracle(u_f, u, tol, fused):
     """PCGTLS with a relative tolerance on ||s_j|| (cg_fixed = 0, the mode the selector's
     tolerance output uses) against the oracle's cg_tol mode on the same factor: the stop step
     agrees to within one step (the FP32 recurrence crosses the threshold at its own rounding),
@@ -184,7 +189,7 @@ def test_pcgtls_tolerance_mode_matches_oracle(u_f, u, tol):
     f1 = rng.standard_normal(n)
     sigma2 = 0.3 * p.D[-1] ** 2
     cap = 60
-    with Ctx(p.A, p.b, u_f=u_f, u=u, cg_fixed=0, cg_tol=tol, cg_max=cap) as ctx:
+    with Ctx(p.A, p.b, u_f=u_f, u=u, cg_fixed=0, cg_tol=tol, cg_max=cap, fused=fused) as ctx:
         RH, d, _ = tls.tls_export_factor(ctx)
         w0, w1, it, bad = tls.tls_pcgtls(ctx, sigma2, f0, f1, steps=cap, cg_tol=tol)
     R = RH * d[None, :]
@@ -221,6 +226,55 @@ def test_solve_tolerance_mode_matches_oracle(m, n, u_f, u, cg_tol):
     # the inner solves ran to the tolerance, not the fixed k+1 schedule
     fixed = sum(2 * (k + 1) for k in range(1, info["rqi_steps"]))
     assert info["cg_iters"] != fixed or info["rqi_steps"] <= 2
+
+
+FUSED_SHAPES = [
+    # (m, n): n_pad 64 (8 rows per tile), 704 and 2048 (4 rows), 2112 (2 rows, two float4
+    # groups per thread), 4160 (1 row, three groups); m leaves CTAs without rows (m < 152)
+    # or gives ragged last tiles
+    (100, 40), (3001, 700), (9000, 2048), (5003, 2100), (4500, 4100),
+]
+
+
+@pytest.mark.parametrize("m,n", FUSED_SHAPES)
+def test_one_launch_pcgtls_matches_multi_launch_and_oracle(m, n):
+    """The one-launch PCGTLS solve (every step's pass over A, reductions and W / W^T products in
+    one cooperative launch) against the multi-launch path and the oracle with the same factor,
+    for every ring geometry the kernel uses; and that it is the path that ran."""
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=17)
+    rng = np.random.default_rng(9)
+    f0, f1 = rng.standard_normal(n), rng.standard_normal(n)
+    sigma2 = 0.3 * p.D[-1] ** 2
+    steps = 6
+    out = {}
+    for fused in (1, 2):
+        with Ctx(p.A, p.b, u_f="fp16", u="fp32", fused=fused) as ctx:
+            RH, d, _ = tls.tls_export_factor(ctx)
+            tls.tls_profile_enable(ctx, True)
+            out[fused] = tls.tls_pcgtls(ctx, sigma2, f0, f1, steps=steps)
+            prof = tls.tls_profile_get(ctx)
+            tls.tls_profile_enable(ctx, False)
+        launched = prof["pcg_solve2"][0]
+        assert (launched == 1) if fused == 1 else (launched == 0), prof
+    R = RH * d[None, :]
+    kap = np.linalg.cond(RH)
+    tol = 50 * kap * n * U32
+    for f, k in ((f0, 0), (f1, 1)):
+        wo, _, _ = O.pcgtls(p.A, R, sigma2, f, steps - 1)
+        w_one, w_multi = out[1][k], out[2][k]
+        assert _rel(w_one, wo) <= tol
+        assert _rel(w_one, w_multi) <= tol
+    assert out[1][2] == [steps, steps] and out[1][3] == [0, 0]
+
+
+@pytest.mark.parametrize("fused", [1, 2])
+def test_solve_paths_match_oracle(fused):
+    p = synth.dense_problem(6000, 1000, d_lo=1e-3, noise=1e-4, seed=2)
+    with Ctx(p.A, p.b, u_f="fp16", u="fp32", fused=fused) as ctx:
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    assert abs(sigma - so) <= 1e-10 * so, (sigma, so, info)
+    assert _rel(x, xo) <= 1e-8, info
 
 
 def test_pcgtls_flags_indefinite_shift():
