@@ -1072,6 +1072,7 @@ static tls_status pcgtls_host(tls_ctx* ctx, int nr, double sigma2, const double*
   TLS_CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
   TLS_CK(cudaMemcpyAsync(&herr, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLS_CK(cudaStreamSynchronize(st));
+  prof_collect(ctx);
   if (herr != 0) {
     TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), st));
     TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), st));
