@@ -57,7 +57,21 @@ typedef enum {
 enum {
   TLS_STOP_TOL = 1,       /* psi_k <= tol * (||A||_F^2 + ||b||^2), tested from k = 2 on       */
   TLS_STOP_PSI_UP = 2,    /* psi_k > psi_{k-1} (or >= with psi_rule_ge), Sec. 3 after Eq. (4) */
-  TLS_STOP_MAX_RQI = 3    /* k reached max_rqi                                              */
+  TLS_STOP_MAX_RQI = 3,   /* k reached max_rqi                                              */
+  TLS_STOP_STALL = 4      /* a PCGTLS solve stalled or met delta_j <= 0 before psi reached  */
+                          /* the attainable level: the solve ended early for the precision  */
+                          /* fallback (tls_options.stall_fallback)                          */
+};
+
+/* Why the precision fallback of tls_solve refactored (tls_info.fallback_trigger). */
+enum {
+  TLS_TRIGGER_NONE = 0,
+  TLS_TRIGGER_MAX_RQI = 1,     /* the RQI loop ended on max_rqi                              */
+  TLS_TRIGGER_STALL = 2,       /* a PCGTLS solve reduced ||s|| by less than stall_ratio      */
+  TLS_TRIGGER_NOT_SPD = 3,     /* delta_j <= 0: the preconditioned operator lost positive    */
+                               /* definiteness (the requirement behind Eq. (9), Sec. 3.1)    */
+  TLS_TRIGGER_CONSTRAINT = 4   /* tls_factor: u_f above constr_guard x constraint 2 of the   */
+                               /* column-scaled matrix (Eq. (9) with sigma_{n+1} = 0)         */
 };
 
 typedef struct {
@@ -85,6 +99,20 @@ typedef struct {
                        /* one precision up (FP16/BF16 -> FP32 -> FP64) and solve again, at most  */
                        /* twice -- the precision fallback for a factor that violates the         */
                        /* stability constraints of Sec. 3.1; 0: return the max_rqi result       */
+  double constr_guard; /* > 0: tls_factor checks constraint 2 (Eq. (9), Sec. 3.1) on the column-  */
+                       /* scaled matrix the factor is built from, kappa_F(A D^{-1})^{-1} =      */
+                       /* 1 / (sqrt(n) ||R_H^{-1}||_F) (sigma_{n+1} taken as 0), and escalates  */
+                       /* an FP16/BF16 factor to the next precision when u_f > constr_guard x    */
+                       /* that bound (1: the paper's heuristic as printed); 0 (default): off     */
+  int stall_fallback;  /* 1 (default, with fallback): end the RQI loop early (TLS_STOP_STALL) and */
+                       /* fall back one precision when, at RQI step k >= 2 and psi still above   */
+                       /* the acceptance level, a PCGTLS solve reduced ||s_j|| / ||s_0|| by less  */
+                       /* than stall_ratio, met delta_j <= 0, or (tolerance mode) used cg_max    */
+                       /* steps without reaching cg_tol                                           */
+  double stall_ratio;  /* default 0.9                                                          */
+  int constraint_iters;/* > 0: tls_solve also estimates constraints 1 and 2 (Eq. (5), Eq. (9))   */
+                       /* as tls_condition does, with this many power iterations, into        */
+                       /* tls_info.constr1 / constr2; 0 (default): those fields are NaN         */
 } tls_options;
 
 typedef struct {
@@ -109,6 +137,13 @@ typedef struct {
   double psi_hist[24];   /* psi_k of the RQI loop, k = 1, 2, ... (first 24)                  */
   int fallbacks;         /* precision fallbacks taken (tls_options.fallback); the other       */
                          /* fields describe the final factor and solve                        */
+  int fallback_trigger;  /* TLS_TRIGGER_* of the last fallback or factor escalation           */
+  int escalations;       /* factor precisions skipped by the constraint guard                 */
+  double constr1;        /* constraint 1, kappa(A)^{-1} (Eq. (5)); NaN unless constraint_iters */
+  double constr2;        /* constraint 2, kappa_F(A)^{-1} (1 - sigma_{n+1}^2 / sigma'_n^2)     */
+                         /* (Eq. (9)) with this solve's sigma; NaN unless constraint_iters     */
+  double constr2_scaled; /* constraint 2 of the column-scaled matrix with sigma_{n+1} = 0 (the */
+                         /* guard's bound); NaN unless the guard or constraint_iters ran       */
 } tls_info;
 
 typedef struct tls_ctx tls_ctx;

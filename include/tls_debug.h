@@ -117,6 +117,17 @@ tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units);
  * (a pass launch and a cooperative step-tail launch per step). Kept until changed.
  */
 tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode);
+/*
+ * tls_trace_enable / tls_trace_get -- phase timestamps (global timer, ns) of the one-launch
+ * PCGTLS solve, recorded by CTA 0 into a device buffer of the context when on (the last solve
+ * overwrites them): out[0] the launch's start, out[1] the end of the initialisation, then ten
+ * words per step j (up to 64 steps) at 2 + 10 j: pass start, pass end, and the ends of grid
+ * barrier 1, the column reduction, barrier 2, the W^T product, barrier 3, the W product, barrier
+ * 4, and the nanoseconds CTA 0 waited for tiles of A in that pass. Unused words are 0. *count
+ * receives the number of words (0 before tls_trace_enable). Host buffer of cap words.
+ */
+tls_status tls_trace_enable(tls_ctx* ctx, int on);
+tls_status tls_trace_get(tls_ctx* ctx, uint64_t* out, int cap, int* count);
 /* The same per-class timing for a packed batch (classes as above; PCG_REDUCE covers the
  * per-problem PCGTLS step including its W / W^T products; VEC the small per-problem kernels). */
 tls_status tls_batch_profile_enable(tls_batch* bt, int on);

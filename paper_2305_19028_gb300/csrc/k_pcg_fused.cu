@@ -68,7 +68,15 @@ struct FusedArgs {
   double sigma2, cg_tol2;
   unsigned int* bar;     // [0] arrivals, [32] generation, [64] abort (zero between launches)
   int* err;
+  unsigned long long* trace;   // optional phase timestamps of CTA 0 (kFTraceCap words)
 };
+
+// Trace layout (global-timer nanoseconds, CTA 0, thread 0): [0] start, [1] initialisation done,
+// then per step j < kFTraceSteps, at 2 + kFTracePer * j: pass start, pass end, barrier 1 done,
+// reduce done, barrier 2 done, W^T done, barrier 3 done, W done, barrier 4 done, and the time
+// thread 0 spent waiting for tiles of that pass.
+constexpr int kFTracePer = 10;
+constexpr int kFTraceSteps = 64;
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
@@ -321,6 +329,11 @@ __device__ __forceinline__ void step_flags(FusedShared& sh, int r, double eta_ne
   if (eta_new == 0.0 || (tol2 > 0.0 && eta_new <= tol2 * sh.eta0[r])) sh.done[r] = 1;
 }
 
+__device__ __forceinline__ void trace_at(const FusedArgs& a, int idx) {
+  if (a.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && idx < 2 + kFTracePer * kFTraceSteps)
+    a.trace[idx] = ptx::global_ns();
+}
+
 template <int NR, int VPT, int RT>
 __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArgs a) {
   extern __shared__ __align__(128) unsigned char fsm[];
@@ -353,6 +366,7 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
     ptx::bulk_g2s_hint(ring + slot * stage_floats, a.A + row * npad, bytes, &sh.full[slot], pol);
   };
   int64_t issued = 0;                               // meaningful in thread 0
+  trace_at(a, 0);
   if (tid == 0) {
     for (int k = 0; k < S; ++k) ptx::mbar_init(&sh.full[k], 1);
     ptx::fence_mbar_init();
@@ -424,10 +438,14 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
   }
 
   // ---- the PCGTLS steps
+  trace_at(a, 1);
   int passes = 0;
   for (int j = 0; alive && j < a.steps; ++j) {
     if (sh.done[0] && (NR < 2 || sh.done[1])) break;
     ++passes;
+    const int tb = 2 + kFTracePer * j;
+    trace_at(a, tb);
+    unsigned long long tile_wait = 0;
     float* p_cur = (j & 1) ? a.pb : a.pa;
     float* p_next = (j & 1) ? a.pa : a.pb;
     // ---------------- pass over the CTA's rows: t = A q, partial A^T t, ||t||^2
@@ -445,7 +463,9 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
       float tt_acc = 0.f;          // warp 0, lane < NV: squares of the row values it totals
       for (int lt = 0; lt < T; ++lt, ++consumed) {
         const int slot = (int)(consumed % S);
+        const uint64_t tw0 = (a.trace != nullptr && tid == 0) ? ptx::global_ns() : 0;
         const bool got = ptx::mbar_wait(&sh.full[slot], (uint32_t)((consumed / S) & 1), a.err, 24);
+        if (a.trace != nullptr && tid == 0) tile_wait += ptx::global_ns() - tw0;
         const float* tile = ring + slot * stage_floats;
         const int rows = (int)min((int64_t)RT, r1 - (r0 + (int64_t)lt * RT));
         float4 av[RT][VPT];
@@ -528,7 +548,11 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
         }
       }
     }
+    trace_at(a, tb + 1);
+    if (a.trace != nullptr && blockIdx.x == 0 && tid == 0 && j < kFTraceSteps)
+      a.trace[tb + 9] = tile_wait;
     if (!(alive = grid_barrier(a.bar, a.err, fail))) break;
+    trace_at(a, tb + 2);
     // ---------------- delta_j, alpha_j (every CTA), column reduction, w and y
     if (warp == 0) grid_sum2(gp_tt, G, sh.sums);
     cons_sync();
@@ -568,7 +592,9 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
         cons_sync();
       }
     }
+    trace_at(a, tb + 3);
     if (!(alive = grid_barrier(a.bar, a.err, fail))) break;
+    trace_at(a, tb + 4);
     // ---------------- v = W^T y, s_{j+1} = s_j - alpha v, ||s_{j+1}||^2
     for (int64_t e = (int64_t)tid * 4; e < E; e += 4 * kFcThreads)
       *reinterpret_cast<float4*>(vs + e) = ldcg4(a.y + e);
@@ -578,7 +604,9 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
       wt_phase<NR>(a, vs, false, sh, ss);
       cta_publish2(ss[0], ss[1], sh.dred, gp_ss + 2 * blockIdx.x);
     }
+    trace_at(a, tb + 5);
     if (!(alive = grid_barrier(a.bar, a.err, fail))) break;
+    trace_at(a, tb + 6);
     if (warp == 0) grid_sum2(gp_ss, G, sh.sums);
     cons_sync();
     if (tid == 0)
@@ -601,7 +629,9 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
       w_phase<NR>(a, vs, qq);
       cta_publish2(qq[0], qq[1], sh.dred, gp_qq + 2 * blockIdx.x);
     }
+    trace_at(a, tb + 7);
     if (!(alive = grid_barrier(a.bar, a.err, fail))) break;
+    trace_at(a, tb + 8);
     if (warp == 0) grid_sum2(gp_qq, G, sh.sums);
     cons_sync();
     if (tid == 0) { sh.qq[0] = sh.sums[0]; sh.qq[1] = sh.sums[1]; }
@@ -669,6 +699,8 @@ static bool fused_geometry(int64_t npad, int nr, int* vpt, int* rt, int* stages,
   return true;
 }
 
+int pcg_fused_trace_words() { return 2 + kFTracePer * kFTraceSteps; }
+
 bool pcg_fused_supported(int64_t npad, int nr) {
   int v, r, s;
   size_t sm;
@@ -681,7 +713,7 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
                              const float* WT, float* w, float* y, float* s, float* pa, float* pb,
                              float* q, float* part, double* gpart, PcgScalars* sc, double sigma2,
                              double cg_tol, int steps, unsigned int* bar, int* err, int num_sms,
-                             cudaStream_t st) {
+                             cudaStream_t st, unsigned long long* trace) {
   int vpt, rt, stages;
   size_t smem;
   if (!fused_geometry(npad, nr, &vpt, &rt, &stages, &smem)) return cudaErrorInvalidValue;
@@ -690,7 +722,7 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
   a.tile_rows = rt; a.fin0 = fin0; a.fin0_scale = fin0_scale; a.fin1 = fin1;
   a.dinv64 = dinv64; a.dinv = dinv; a.W = W; a.WT = WT; a.w = w; a.y = y; a.s = s; a.pa = pa;
   a.pb = pb; a.q = q; a.part = part; a.gpart = gpart; a.sc = sc; a.sigma2 = sigma2;
-  a.cg_tol2 = cg_tol * cg_tol; a.bar = bar; a.err = err;
+  a.cg_tol2 = cg_tol * cg_tol; a.bar = bar; a.err = err; a.trace = trace;
   const int grid = num_sms;
   // the solution starts at zero (w_0 = 0)
   cudaError_t e = cudaMemsetAsync(w, 0, sizeof(float) * (size_t)nr * npad, st);

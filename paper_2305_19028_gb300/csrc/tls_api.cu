@@ -85,6 +85,9 @@ struct tls_ctx {
   double shift = 0.0;
   int64_t fail_pivot = -1;   // pivot index of the last breakdown (-1: none)
   double last_sigma2 = -1.0; // sigma^2 of the last successful tls_solve (-1: none yet)
+  double constr2_scaled = NAN;   // constraint 2 of A D^{-1} (sigma_{n+1} = 0) of the factor
+  int escalations = 0;       // factor precisions skipped by the constraint guard
+  int stall_trigger = 0;     // TLS_TRIGGER_* of the last TLS_STOP_STALL
   double t_factor_ms = 0.0;
   // selector network (tls_factor with TLS_AUTO)
   bool has_sel = false;
@@ -124,6 +127,8 @@ struct tls_ctx {
   int64_t prof_cnt[TLS_PROF_NCLASSES] = {};
   int64_t prof_units[TLS_PROF_NCLASSES] = {};
   bool last_pcg_fused = false;     // the last PCGTLS solve ran as one launch
+  bool trace_on = false;           // tls_trace_enable
+  unsigned long long* trace = nullptr;   // phase timestamps of the last one-launch solve
 };
 
 namespace {
@@ -395,7 +400,8 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
           reinterpret_cast<float*>(v.y), reinterpret_cast<float*>(v.s),
           reinterpret_cast<float*>(v.p0), reinterpret_cast<float*>(v.p1),
           reinterpret_cast<float*>(v.q), static_cast<float*>(ctx->part), ctx->gpart, ctx->sc,
-          sigma2, cg_tol, steps, ctx->fbar, ctx->derr, ctx->num_sms, ctx->stream);
+          sigma2, cg_tol, steps, ctx->fbar, ctx->derr, ctx->num_sms, ctx->stream,
+          ctx->trace_on ? ctx->trace : nullptr);
     }
     if (e == cudaSuccess) {
       ctx->last_pcg_fused = true;
@@ -585,6 +591,8 @@ tls_status small_solve(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, do
     info->pass_variant[1] = cluster ? cluster : 1;
     info->n_psi = r.n_psi;
     for (int i = 0; i < r.n_psi; ++i) info->psi_hist[i] = r.psi_hist[i];
+    info->escalations = ctx->escalations;
+    info->constr2_scaled = ctx->constr2_scaled;
   }
   return TLS_OK;
 }
@@ -628,7 +636,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   const double scale = ctx->norm2_A + ctx->norm2_b;
   double prev_psi = INFINITY;
   int stop = TLS_STOP_MAX_RQI;
-  int best_k = 0, k = 0, cg_total = 0, not_spd = 0;
+  int best_k = 0, k = 0, cg_total = 0, not_spd = 0, last_steps = 0;
   double best_psi = INFINITY, best_s2 = 0.0;
   double psi_hist[24];
   int n_psi = 0;
@@ -676,9 +684,26 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
       stop = TLS_STOP_MAX_RQI;
       break;
     }
+    // the precision fallback before max_rqi: the last pair of PCGTLS solves stalled or lost
+    // positive definiteness while psi is still above the attainable level
+    if (k > 1 && o.fallback && o.stall_fallback && ctx->uf_used != TLS_FP64 &&
+        best_psi > o.psi_accept * scale) {
+      const PcgScalars& h = *ctx->h_sc;
+      const double rel = (h.eta0[0] > 0.0) ? std::sqrt(h.eta[0] / h.eta0[0]) : 0.0;
+      int trig = TLS_TRIGGER_NONE;
+      if (h.not_spd[0] | h.not_spd[1]) trig = TLS_TRIGGER_NOT_SPD;
+      else if (o.cg_fixed && last_steps >= 3 && rel >= o.stall_ratio) trig = TLS_TRIGGER_STALL;
+      else if (!o.cg_fixed && !h.done[0] && h.iters[0] >= last_steps) trig = TLS_TRIGGER_STALL;
+      if (trig != TLS_TRIGGER_NONE) {
+        ctx->stall_trigger = trig;
+        stop = TLS_STOP_STALL;
+        break;
+      }
+    }
     prev_psi = psi;
     // two shifted solves (Alg. 4, PCGTLS with k+1 steps) and the x update
     const int steps = o.cg_fixed ? (k + 1) : std::max(1, o.cg_max);
+    last_steps = steps;
     const double cgt = ctx->use_sel_tol ? ctx->sel_cg_tol : o.cg_tol;
     stt = run_pcg<T>(ctx, 2, ctx->f, -1.0, ctx->x, s2, steps, o.cg_fixed ? 0.0 : cgt, modeA);
     if (stt != TLS_OK) return stt;
@@ -727,6 +752,8 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     info->pass_variant[1] = ctx->planU.variant;
     info->n_psi = n_psi;
     for (int i = 0; i < n_psi; ++i) info->psi_hist[i] = psi_hist[i];
+    info->escalations = ctx->escalations;
+    info->constr2_scaled = ctx->constr2_scaled;
   }
   return TLS_OK;
 }
@@ -829,6 +856,27 @@ tls_status ensure_solve_buffers(tls_ctx* ctx) {
   return TLS_OK;
 }
 
+// 1 / (sqrt(n) ||W||_F) with W = R_H^{-1} of the current factor (in the u type): constraint 2
+// of the column-scaled matrix with sigma_{n+1} = 0. Synchronises the stream.
+tls_status scaled_constraint2(tls_ctx* ctx, double* out) {
+  cudaStream_t st = ctx->stream;
+  int g;
+  if (ctx->u == Prec::FP64)
+    g = tls::launch_frob_dw<double>(static_cast<const double*>(ctx->W), ctx->n, ctx->npad,
+                                    nullptr, ctx->gpart, st);
+  else
+    g = tls::launch_frob_dw<float>(static_cast<const float*>(ctx->W), ctx->n, ctx->npad,
+                                   nullptr, ctx->gpart, st);
+  TLS_CK_LAUNCH("scaled constraint");
+  std::vector<double> h((size_t)g);
+  TLS_CK(cudaMemcpyAsync(h.data(), ctx->gpart, sizeof(double) * g, cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaStreamSynchronize(st));
+  double frob = 0.0;
+  for (double v : h) frob += v;
+  *out = (frob > 0.0) ? 1.0 / (std::sqrt((double)ctx->n) * std::sqrt(frob)) : 0.0;
+  return TLS_OK;
+}
+
 tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   cudaStream_t st = ctx->stream;
   const int64_t m = ctx->m, n = ctx->n, npad = ctx->npad, mpad = ctx->mpad;
@@ -885,6 +933,8 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   ctx->shifts = 0;
   ctx->shift = 0.0;
   ctx->fail_pivot = -1;
+  ctx->escalations = 0;
+  ctx->constr2_scaled = NAN;
   bool ok = false;
   for (tls_prec uf : ladder) {
     const Prec pf = to_prec(uf);
@@ -1029,6 +1079,18 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     TLS_CK_LAUNCH("triangular inverse");
     ctx->uf_used = uf;
     ctx->H_fp64 = chol64;
+    if (low && ctx->opt.constr_guard > 0.0 && uf != ladder.back()) {
+      // constraint 2 (Eq. (9), Sec. 3.1) of the column-scaled matrix A D^{-1} the factor is
+      // built from: kappa_F(A D^{-1}) = ||A D^{-1}||_F ||R_H^{-1}||_F = sqrt(n) ||W||_F (unit
+      // columns), with sigma_{n+1} = 0 before the solve
+      const tls_status gs = scaled_constraint2(ctx, &ctx->constr2_scaled);
+      if (gs != TLS_OK) return gs;
+      if (uf_round > ctx->opt.constr_guard * ctx->constr2_scaled) {
+        ctx->escalations += 1;
+        ok = false;
+        continue;
+      }
+    }
     break;
   }
   if (!ok) {
@@ -1266,6 +1328,10 @@ void tls_default_options(tls_options* opt) {
   opt->shift_first = 1;
   opt->psi_accept = 1e-15;
   opt->fallback = 1;
+  opt->constr_guard = 0.0;
+  opt->stall_fallback = 1;
+  opt->stall_ratio = 0.9;
+  opt->constraint_iters = 0;
 }
 
 const char* tls_status_str(tls_status s) {
@@ -1496,10 +1562,15 @@ static tls_status solve_common(tls_ctx* ctx, double tol, int max_rqi, double* si
     return TLS_ERR_STATE;
   }
   tls_info loc{};
+  int trigger = ctx->escalations ? TLS_TRIGGER_CONSTRAINT : TLS_TRIGGER_NONE;
   tls_status s = solve_once(ctx, tol, max_rqi, sigma, &loc);
   int fb = 0;
-  while (s == TLS_OK && ctx->opt.fallback && loc.stop_reason == TLS_STOP_MAX_RQI &&
+  // the precision fallback (FP16/BF16 -> FP32 -> FP64): on max_rqi, and earlier on a stalled or
+  // indefinite PCGTLS solve
+  while (s == TLS_OK && ctx->opt.fallback &&
+         (loc.stop_reason == TLS_STOP_MAX_RQI || loc.stop_reason == TLS_STOP_STALL) &&
          ctx->uf_used != TLS_FP64 && fb < 2) {
+    trigger = (loc.stop_reason == TLS_STOP_MAX_RQI) ? TLS_TRIGGER_MAX_RQI : ctx->stall_trigger;
     const tls_prec next = (ctx->uf_used == TLS_FP32) ? TLS_FP64 : TLS_FP32;
     const tls_options o = ctx->opt;
     s = tls_factor(ctx, next, &o);
@@ -1508,6 +1579,19 @@ static tls_status solve_common(tls_ctx* ctx, double tol, int max_rqi, double* si
     s = solve_once(ctx, tol, max_rqi, sigma, &loc);
   }
   loc.fallbacks = fb;
+  loc.fallback_trigger = trigger;
+  loc.constr1 = loc.constr2 = NAN;
+  if (s == TLS_OK && ctx->opt.constraint_iters > 0) {
+    // the paper's constraints 1 and 2 (Eq. (5), Eq. (9)) for A, with this solve's sigma
+    double c[9];
+    s = tls_condition(ctx, ctx->opt.constraint_iters, c);
+    if (s == TLS_OK) {
+      loc.constr1 = c[7];
+      loc.constr2 = c[8];
+      if (std::isnan(ctx->constr2_scaled)) s = scaled_constraint2(ctx, &ctx->constr2_scaled);
+      loc.constr2_scaled = ctx->constr2_scaled;
+    }
+  }
   if (info) *info = loc;
   return s;
 }
@@ -1649,6 +1733,32 @@ tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* 
 tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units) {
   if (!ctx || !units || cls < 0 || cls >= TLS_PROF_NCLASSES) return TLS_ERR_ARG;
   *units = ctx->prof_units[cls];
+  return TLS_OK;
+}
+
+tls_status tls_trace_enable(tls_ctx* ctx, int on) {
+  if (!ctx) return TLS_ERR_ARG;
+  if (on && !ctx->trace) {
+    ctx->trace = static_cast<unsigned long long*>(
+        dev_alloc(ctx, sizeof(unsigned long long) * (size_t)tls::pcg_fused_trace_words()));
+    if (!ctx->trace) return TLS_ERR_OOM;
+  }
+  if (ctx->trace)
+    TLS_CK(cudaMemsetAsync(ctx->trace, 0,
+                           sizeof(unsigned long long) * (size_t)tls::pcg_fused_trace_words(),
+                           ctx->stream));
+  ctx->trace_on = on != 0;
+  return TLS_OK;
+}
+
+tls_status tls_trace_get(tls_ctx* ctx, uint64_t* out, int cap, int* count) {
+  if (!ctx || !out || cap < 0) return TLS_ERR_ARG;
+  const int w = tls::pcg_fused_trace_words();
+  if (count) *count = ctx->trace ? w : 0;
+  if (!ctx->trace) return TLS_OK;
+  TLS_CK(cudaMemcpyAsync(out, ctx->trace, sizeof(uint64_t) * (size_t)std::min(cap, w),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+  TLS_CK(cudaStreamSynchronize(ctx->stream));
   return TLS_OK;
 }
 

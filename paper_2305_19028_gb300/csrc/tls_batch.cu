@@ -1093,6 +1093,8 @@ tls_status tls_batch_solve(tls_batch* bt, double tol, int max_rqi, double* const
       in.n_psi = std::min(S.n_psi, 24);
       for (int k = 0; k < in.n_psi; ++k) in.psi_hist[k] = S.psi_hist[k];
       in.fallbacks = bt->fallbacks[(size_t)i];
+      in.fallback_trigger = in.fallbacks ? TLS_TRIGGER_MAX_RQI : TLS_TRIGGER_NONE;
+      in.constr1 = in.constr2 = in.constr2_scaled = NAN;
     }
   }
   return first;

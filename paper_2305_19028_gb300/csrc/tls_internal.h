@@ -213,7 +213,9 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
                              const float* WT, float* w, float* y, float* s, float* pa, float* pb,
                              float* q, float* part, double* gpart, PcgScalars* sc, double sigma2,
                              double cg_tol, int steps, unsigned int* bar, int* err, int num_sms,
-                             cudaStream_t st);
+                             cudaStream_t st, unsigned long long* trace = nullptr);
+// Words of the optional phase trace of the one-launch PCGTLS solve (see k_pcg_fused.cu).
+int pcg_fused_trace_words();
 // Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).
 template <typename T>
 void launch_pcg_reduce(const T* part, int P, int64_t npad, const T* q, T* w, T* y,

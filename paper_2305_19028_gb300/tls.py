@@ -19,7 +19,8 @@ TLS_AUTO = 4
 PREC = {"fp16": TLS_FP16, "bf16": TLS_BF16, "fp32": TLS_FP32, "fp64": TLS_FP64, "auto": TLS_AUTO}
 MLP_PARAMS = 5508
 N_FEATURES = 16
-STOP_TOL, STOP_PSI_UP, STOP_MAX_RQI = 1, 2, 3
+STOP_TOL, STOP_PSI_UP, STOP_MAX_RQI, STOP_STALL = 1, 2, 3, 4
+TRIGGER_NONE, TRIGGER_MAX_RQI, TRIGGER_STALL, TRIGGER_NOT_SPD, TRIGGER_CONSTRAINT = 0, 1, 2, 3, 4
 
 STATUS = ["TLS_OK", "TLS_ERR_ARG", "TLS_ERR_CUDA", "TLS_ERR_OOM", "TLS_ERR_STATE",
           "TLS_ERR_FACTOR_BREAKDOWN", "TLS_ERR_NOT_SPD", "TLS_ERR_NOT_UNIQUE",
@@ -38,7 +39,7 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_batch_set_selector", "tls_batch_features", "tls_set_pass_variant",
            "tls_set_selector", "tls_features", "tls_pool_enable", "tls_pool_trim",
            "tls_pool_stats", "tls_pool_poison", "tls_set_small_path", "tls_profile_units",
-           "tls_set_pcg_fused"]
+           "tls_set_pcg_fused", "tls_trace_enable", "tls_trace_get"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec", "pcg_solve2", "pcg_solve1"]
@@ -48,7 +49,9 @@ class tls_options(C.Structure):
     _fields_ = [("u", C.c_int), ("mode_A", C.c_int), ("cg_fixed", C.c_int),
                 ("cg_tol", C.c_double), ("cg_max", C.c_int), ("psi_rule_ge", C.c_int),
                 ("ls_iters", C.c_int), ("max_shifts", C.c_int), ("gram_simt", C.c_int),
-                ("psi_accept", C.c_double), ("shift_first", C.c_int), ("fallback", C.c_int)]
+                ("psi_accept", C.c_double), ("shift_first", C.c_int), ("fallback", C.c_int),
+                ("constr_guard", C.c_double), ("stall_fallback", C.c_int),
+                ("stall_ratio", C.c_double), ("constraint_iters", C.c_int)]
 
 
 class tls_info(C.Structure):
@@ -57,7 +60,9 @@ class tls_info(C.Structure):
                 ("u_f_used", C.c_int), ("psi_final", C.c_double), ("sigma2", C.c_double),
                 ("shift", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("fail_pivot", C.c_int), ("pass_variant", C.c_int * 2), ("n_psi", C.c_int),
-                ("psi_hist", C.c_double * 24), ("fallbacks", C.c_int)]
+                ("psi_hist", C.c_double * 24), ("fallbacks", C.c_int),
+                ("fallback_trigger", C.c_int), ("escalations", C.c_int), ("constr1", C.c_double),
+                ("constr2", C.c_double), ("constr2_scaled", C.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("psi_hist", "pass_variant")}
@@ -146,6 +151,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_set_small_path": (C.c_int, [v, C.c_int]),
         "tls_profile_units": (C.c_int, [v, C.c_int, C.POINTER(i64)]),
         "tls_set_pcg_fused": (C.c_int, [v, C.c_int]),
+        "tls_trace_enable": (C.c_int, [v, C.c_int]),
+        "tls_trace_get": (C.c_int, [v, C.POINTER(C.c_uint64), C.c_int, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -386,6 +393,18 @@ def tls_profile_units(ctx) -> dict:
 def tls_set_pcg_fused(ctx, mode: int) -> None:
     """0 automatic, 1 one persistent launch per PCGTLS solve, 2 the multi-launch path."""
     _check(load().tls_set_pcg_fused(ctx, int(mode)), ctx)
+
+
+def tls_trace_enable(ctx, on: bool = True) -> None:
+    _check(load().tls_trace_enable(ctx, 1 if on else 0), ctx)
+
+
+def tls_trace_get(ctx) -> np.ndarray:
+    """Phase timestamps (ns) of the last one-launch PCGTLS solve (see tls_debug.h)."""
+    cnt = C.c_int()
+    buf = (C.c_uint64 * 1024)()
+    _check(load().tls_trace_get(ctx, buf, 1024, C.byref(cnt)), ctx)
+    return np.array(buf[:cnt.value], dtype=np.uint64)
 
 
 def tls_kernel_launches() -> int:

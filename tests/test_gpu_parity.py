@@ -506,3 +506,65 @@ def test_pass_variants_match_oracle(variant, m, n):
     tol = 50 * np.linalg.cond(RH) * n * U32
     assert it == [4, 4] and bad == [0, 0]
     assert _rel(w0, r0) <= tol and _rel(w1, r1) <= tol
+
+
+# ------------------------------------------------------------------------------------------
+# fallback triggers: the constraint guard of Sec. 3.1 (Eq. (9)) at factor time, and a stalled or
+# indefinite PCGTLS solve during RQI (the precision fallback before max_rqi)
+# ------------------------------------------------------------------------------------------
+def test_constraint_guard_escalates_a_factor_that_violates_constraint_2():
+    # Haar-random Y, Z with kappa(A) = 1e3: column scaling leaves kappa_F(A D^{-1}) near
+    # kappa_F(A), so 1 / (sqrt(n) ||R_H^{-1}||_F) falls below u_fp16 and the guard refactors
+    p = synth.dense_problem(2000, 200, d_lo=1e-3, noise=1e-4, seed=3, haar=True)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    with Ctx(p.A, p.b, u_f="fp16", u="fp32", constr_guard=1.0) as ctx:
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+    assert info["escalations"] >= 1 and info["u_f_used"] >= tls.TLS_FP32, info
+    assert info["fallback_trigger"] == tls.TRIGGER_CONSTRAINT, info
+    assert info["constr2_scaled"] < U16
+    assert abs(sigma - so) <= 1e-10 * so and _rel(x, xo) <= 1e-8, info
+
+
+def test_constraint_guard_keeps_a_factor_that_meets_constraint_2():
+    # the same size with a single reflector Z: the column scaling equilibrates A, the scaled
+    # constraint 2 is above u_fp16 and the FP16 factor stays
+    p = synth.dense_problem(2000, 200, d_lo=1e-3, noise=1e-4, seed=3)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    with Ctx(p.A, p.b, u_f="fp16", u="fp32", constr_guard=1.0) as ctx:
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+    assert info["escalations"] == 0 and info["u_f_used"] == tls.TLS_FP16, info
+    assert info["constr2_scaled"] > U16
+    assert info["fallback_trigger"] == tls.TRIGGER_NONE and info["fallbacks"] == 0
+    assert abs(sigma - so) <= 1e-10 * so and _rel(x, xo) <= 1e-8, info
+
+
+@pytest.mark.parametrize("stall", [1, 0])
+def test_stalled_inner_solve_falls_back_before_max_rqi(stall):
+    # kappa(A) = 1e4 with Haar Y, Z: the FP16 factor leaves PCGTLS with k + 1 steps making no
+    # progress. With stall_fallback the solve refactors in FP32 at the first stalled pair of
+    # solves (trigger STALL or NOT_SPD); without it only after max_rqi steps. Both end at the
+    # oracle's answer.
+    p = synth.dense_problem(2000, 200, d_lo=1e-4, noise=1e-4, seed=3, haar=True)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    with Ctx(p.A, p.b, u_f="fp16", u="fp32", stall_fallback=stall) as ctx:
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+    assert info["fallbacks"] >= 1 and info["u_f_used"] >= tls.TLS_FP32, info
+    if stall:
+        assert info["fallback_trigger"] in (tls.TRIGGER_STALL, tls.TRIGGER_NOT_SPD), info
+    else:
+        assert info["fallback_trigger"] == tls.TRIGGER_MAX_RQI, info
+    assert abs(sigma - so) <= 1e-10 * so and _rel(x, xo) <= 1e-8, info
+
+
+def test_info_reports_the_papers_constraints():
+    # Example 1 of Sec. 4 (U(0,1) 100 x 60): tls_info.constr1 / constr2 (Eq. (5), Eq. (9) with
+    # the solve's sigma) against the oracle's exact-SVD values
+    p = synth.random_matrix_problem(seed=0)
+    with Ctx(p.A, p.b, u_f="fp64", u="fp64", constraint_iters=60) as ctx:
+        _, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+    c = O.constraints(p.A, p.b)
+    assert c["constr1"] * (1 - 1e-9) <= info["constr1"] <= 2.0 * c["constr1"]
+    assert info["constr2"] == pytest.approx(c["constr2"], rel=0.5)
+    with Ctx(p.A, p.b, u_f="fp64", u="fp64") as ctx:
+        _, _, info0 = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+    assert np.isnan(info0["constr1"]) and np.isnan(info0["constr2"])
