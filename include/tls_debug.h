@@ -123,8 +123,10 @@ tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode);
  * overwrites them): out[0] the launch's start, out[1] the end of the initialisation, then ten
  * words per step j (up to 64 steps) at 2 + 10 j: pass start, pass end, and the ends of grid
  * barrier 1, the column reduction, barrier 2, the W^T product, barrier 3, the W product, barrier
- * 4, and the nanoseconds CTA 0 waited for tiles of A in that pass. Unused words are 0. *count
- * receives the number of words (0 before tls_trace_enable). Host buffer of cap words.
+ * 4, and the nanoseconds CTA 0 waited for tiles of A in that pass; then, at 642 + 5 t for
+ * the first 64 tiles t of step 0: tile ready, first barrier passed, refill issued, second
+ * barrier passed, tile done. Unused words are 0. *count receives the number of words (0 before
+ * tls_trace_enable). Host buffer of cap words.
  */
 tls_status tls_trace_enable(tls_ctx* ctx, int on);
 tls_status tls_trace_get(tls_ctx* ctx, uint64_t* out, int cap, int* count);

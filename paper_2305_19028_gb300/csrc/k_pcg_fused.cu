@@ -77,6 +77,10 @@ struct FusedArgs {
 // thread 0 spent waiting for tiles of that pass.
 constexpr int kFTracePer = 10;
 constexpr int kFTraceSteps = 64;
+// then, for the first kFTraceTiles tiles of step 0: tile data ready, first barrier passed, copy
+// issued, second barrier passed, tile done (5 words each)
+constexpr int kFTraceTiles = 64;
+constexpr int kFTraceTileBase = 2 + kFTracePer * kFTraceSteps;
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
@@ -173,12 +177,22 @@ __device__ bool grid_barrier(unsigned int* bar, int* err, volatile int* s_fail) 
 
 // Sum of the G per-CTA partials part[c * 2 + r] (r < 2) by warp 0, in one fixed order, so that
 // every CTA obtains bit-identical totals (and takes identical decisions from them).
+constexpr int kFMaxGrid = 256;   // CTAs of the launch at most (one per SM)
+
 __device__ __forceinline__ void grid_sum2(const double* part, int G, double* out2) {
   const int lane = threadIdx.x & 31;
+  // every load first (one round trip to L2), then the sums in a fixed order
+  double2 v[kFMaxGrid / 32];
+#pragma unroll
+  for (int u = 0; u < kFMaxGrid / 32; ++u) {
+    const int c = lane + 32 * u;
+    v[u] = (c < G) ? __ldcg(reinterpret_cast<const double2*>(part) + c) : make_double2(0.0, 0.0);
+  }
   double a0 = 0.0, a1 = 0.0;
-  for (int c = lane; c < G; c += 32) {
-    a0 += __ldcg(part + 2 * c);
-    a1 += __ldcg(part + 2 * c + 1);
+#pragma unroll
+  for (int u = 0; u < kFMaxGrid / 32; ++u) {
+    a0 += v[u].x;
+    a1 += v[u].y;
   }
   a0 = warp_sumd(a0);
   a1 = warp_sumd(a1);
@@ -330,7 +344,8 @@ __device__ __forceinline__ void step_flags(FusedShared& sh, int r, double eta_ne
 }
 
 __device__ __forceinline__ void trace_at(const FusedArgs& a, int idx) {
-  if (a.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && idx < 2 + kFTracePer * kFTraceSteps)
+  if (a.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0 &&
+      idx < kFTraceTileBase + 5 * kFTraceTiles)
     a.trace[idx] = ptx::global_ns();
 }
 
@@ -466,6 +481,8 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
         const uint64_t tw0 = (a.trace != nullptr && tid == 0) ? ptx::global_ns() : 0;
         const bool got = ptx::mbar_wait(&sh.full[slot], (uint32_t)((consumed / S) & 1), a.err, 24);
         if (a.trace != nullptr && tid == 0) tile_wait += ptx::global_ns() - tw0;
+        const bool tt_on = (j == 0 && lt < kFTraceTiles);
+        if (tt_on) trace_at(a, kFTraceTileBase + 5 * lt);
         const float* tile = ring + slot * stage_floats;
         const int rows = (int)min((int64_t)RT, r1 - (r0 + (int64_t)lt * RT));
         float4 av[RT][VPT];
@@ -500,8 +517,10 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
           }
           break;
         }
+        if (tt_on) trace_at(a, kFTraceTileBase + 5 * lt + 1);
         // every thread holds its part of the tile: refill the stage with tile consumed + S
         if (tid == 0 && issued < total) issue(issued++);
+        if (tt_on) trace_at(a, kFTraceTileBase + 5 * lt + 2);
         if (warp == 0 && lane < NV) {
           float t = 0.f;
 #pragma unroll
@@ -510,6 +529,7 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
           tt_acc = fmaf(t, t, tt_acc);             // rows beyond the block are zero
         }
         cons_sync();
+        if (tt_on) trace_at(a, kFTraceTileBase + 5 * lt + 3);
 #pragma unroll
         for (int rt = 0; rt < RT; ++rt) {
           if (rt >= rows) break;
@@ -525,6 +545,7 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
             }
           }
         }
+        if (tt_on) trace_at(a, kFTraceTileBase + 5 * lt + 4);
       }
       // this CTA's partial of A^T t and of ||t||^2
 #pragma unroll
@@ -573,8 +594,17 @@ __global__ void __launch_bounds__(kFcThreads, 1) pcg_fused_kernel(const FusedArg
       for (int64_t e0 = e_lo; e0 < e_hi; e0 += 32) {
         const int64_t e = e0 + lane;
         float t = 0.f;
-        if (e < e_hi)
-          for (int p = ps; p < G; p += kFcWarps) t += __ldcg(a.part + (int64_t)p * E + e);
+        if (e < e_hi) {
+          // all of this thread's partials in flight at once, then a fixed-order sum
+          float pv[kFMaxGrid / kFcWarps];
+#pragma unroll
+          for (int u = 0; u < kFMaxGrid / kFcWarps; ++u) {
+            const int p = ps + kFcWarps * u;
+            pv[u] = (p < G) ? __ldcg(a.part + (int64_t)p * E + e) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < kFMaxGrid / kFcWarps; ++u) t += pv[u];
+        }
         sh.red2[ps][lane] = t;
         cons_sync();
         if (warp == 0 && e < e_hi) {
@@ -699,7 +729,7 @@ static bool fused_geometry(int64_t npad, int nr, int* vpt, int* rt, int* stages,
   return true;
 }
 
-int pcg_fused_trace_words() { return 2 + kFTracePer * kFTraceSteps; }
+int pcg_fused_trace_words() { return kFTraceTileBase + 5 * kFTraceTiles; }
 
 bool pcg_fused_supported(int64_t npad, int nr) {
   int v, r, s;
@@ -724,6 +754,7 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
   a.pb = pb; a.q = q; a.part = part; a.gpart = gpart; a.sc = sc; a.sigma2 = sigma2;
   a.cg_tol2 = cg_tol * cg_tol; a.bar = bar; a.err = err; a.trace = trace;
   const int grid = num_sms;
+  if (grid > kFMaxGrid) return cudaErrorInvalidValue;
   // the solution starts at zero (w_0 = 0)
   cudaError_t e = cudaMemsetAsync(w, 0, sizeof(float) * (size_t)nr * npad, st);
   if (e != cudaSuccess) return e;
