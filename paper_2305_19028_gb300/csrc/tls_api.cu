@@ -45,7 +45,9 @@ struct tls_ctx {
   DevBuf slots[24];
   int small_path = 0;      // tls_set_small_path
   int pcg_fused = 0;       // tls_set_pcg_fused
-  unsigned int* fbar = nullptr;   // grid barrier words of the one-launch PCGTLS solve (96)
+  unsigned int* fbar = nullptr;   // abort word of the one-launch PCGTLS solve (96 words)
+  unsigned long long* fslots = nullptr;   // its flag-barrier slots
+  unsigned int fepoch = 8;        // tag counter of those barriers
   RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
 
   // problem data (device)
@@ -237,17 +239,19 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->gpart = alloc_t<double>(ctx, 4096);
   ctx->counter = alloc_t<unsigned int>(ctx, 32);   // last-CTA counters; [4..22] PCGTLS step
   ctx->fbar = alloc_t<unsigned int>(ctx, 96);
+  ctx->fslots = static_cast<unsigned long long*>(dev_alloc(ctx, tls::pcg_fused_slot_bytes()));
   ctx->derr = alloc_t<int>(ctx, 1);
   ctx->sc = alloc_t<PcgScalars>(ctx, 1);
   ctx->rs = alloc_t<RqiScalars>(ctx, 1);
   if (!ctx->b || !ctx->x || !ctx->x_best || !ctx->f || !ctx->d || !ctx->dinv || !ctx->sout ||
       !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs || !ctx->derr || !ctx->dinv32 ||
-      !ctx->fbar) {
+      !ctx->fbar || !ctx->fslots) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
   TLS_CK(cudaMemsetAsync(ctx->counter, 0, 32 * sizeof(unsigned int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->fslots, 0, tls::pcg_fused_slot_bytes(), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->sc, 0, sizeof(PcgScalars), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->rs, 0, sizeof(RqiScalars), ctx->stream));
@@ -388,7 +392,7 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
   const T* WT = static_cast<const T*>(ctx->WT);
   if constexpr (std::is_same<T, float>::value) {
   if (modeA && !ctx->sparse && steps > 0 && ctx->pcg_fused != 2 &&
-      tls::pcg_fused_supported(npad, nr)) {
+      tls::pcg_fused_supported(npad, nr, ctx->num_sms)) {
     // the whole solve in one persistent cooperative launch
     cudaError_t e;
     {
@@ -399,8 +403,9 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
           reinterpret_cast<const float*>(WT), reinterpret_cast<float*>(v.w),
           reinterpret_cast<float*>(v.y), reinterpret_cast<float*>(v.s),
           reinterpret_cast<float*>(v.p0), reinterpret_cast<float*>(v.p1),
-          reinterpret_cast<float*>(v.q), static_cast<float*>(ctx->part), ctx->gpart, ctx->sc,
-          sigma2, cg_tol, steps, ctx->fbar, ctx->derr, ctx->num_sms, ctx->stream,
+          reinterpret_cast<float*>(v.q), static_cast<float*>(ctx->part), ctx->fslots,
+          &ctx->fepoch, ctx->sc, sigma2, cg_tol, steps, ctx->fbar, ctx->derr, ctx->num_sms,
+          ctx->stream,
           ctx->trace_on ? ctx->trace : nullptr);
     }
     if (e == cudaSuccess) {
@@ -1764,7 +1769,7 @@ tls_status tls_trace_get(tls_ctx* ctx, uint64_t* out, int cap, int* count) {
 
 tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode) {
   if (!ctx || mode < 0 || mode > 2) return TLS_ERR_ARG;
-  if (mode == 1 && !tls::pcg_fused_supported(ctx->npad, 2)) return TLS_ERR_ARG;
+  if (mode == 1 && !tls::pcg_fused_supported(ctx->npad, 2, ctx->num_sms)) return TLS_ERR_ARG;
   ctx->pcg_fused = mode;
   return TLS_OK;
 }

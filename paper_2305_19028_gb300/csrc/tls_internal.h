@@ -203,17 +203,21 @@ bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* 
                      unsigned int* bar, int* err, int num_sms, cudaStream_t st);
 // A whole PCGTLS solve (A-explicit operator, FP32, nr right-hand sides fin0 * fin0_scale and
 // fin1, `steps` steps or fewer on the stop flags) in one persistent cooperative launch of
-// num_sms CTAs (k_pcg_fused.cu). Vectors nr x npad; part: num_sms x nr x npad floats; gpart: at
-// least 6 num_sms doubles; bar: 96 zero-initialised words (zero again after every launch unless
-// a bounded wait expired, which also records a code in *err). Writes w and the scalars in sc.
-bool pcg_fused_supported(int64_t npad, int nr);
+// num_sms CTAs (k_pcg_fused.cu). Vectors nr x npad; part: num_sms x nr x npad floats; slots:
+// pcg_fused_slot_bytes() zero-initialised bytes of flag-barrier words; *epoch: the tag counter of
+// those barriers (starts at 8, advanced by each launch); bar: 96 zero-initialised words (its
+// abort word stays zero unless a bounded wait expired, which also records a code in *err).
+// Writes w and the scalars in sc.
+bool pcg_fused_supported(int64_t npad, int nr, int num_sms);
+size_t pcg_fused_slot_bytes();
 cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad, int nr,
                              const double* fin0, double fin0_scale, const double* fin1,
                              const double* dinv64, const float* dinv, const float* W,
                              const float* WT, float* w, float* y, float* s, float* pa, float* pb,
-                             float* q, float* part, double* gpart, PcgScalars* sc, double sigma2,
-                             double cg_tol, int steps, unsigned int* bar, int* err, int num_sms,
-                             cudaStream_t st, unsigned long long* trace = nullptr);
+                             float* q, float* part, unsigned long long* slots,
+                             unsigned int* epoch, PcgScalars* sc, double sigma2, double cg_tol,
+                             int steps, unsigned int* bar, int* err, int num_sms, cudaStream_t st,
+                             unsigned long long* trace = nullptr);
 // Words of the optional phase trace of the one-launch PCGTLS solve (see k_pcg_fused.cu).
 int pcg_fused_trace_words();
 // Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).
