@@ -114,7 +114,9 @@ tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units);
  * tls_set_pcg_fused -- how dense FP32 PCGTLS solves (A-explicit operator) run: 0 automatic (one
  * persistent cooperative launch per solve where the shape fits, else the multi-launch path),
  * 1 the one-launch solve (TLS_ERR_ARG when the shape does not fit it), 2 the multi-launch path
- * (a pass launch and a cooperative step-tail launch per step). Kept until changed.
+ * (a pass launch and a cooperative step-tail launch per step); 3, 4, 5: the one-launch solve
+ * with tiles of A loaded by one bulk copy (TMA) per tile, one bulk copy per row, or 16-byte
+ * asynchronous copies by every thread (3 is the default loading). Kept until changed.
  */
 tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode);
 /*

@@ -77,6 +77,7 @@ struct FusedArgs {
   unsigned int* bar;     // [64] abort word (zero between launches)
   int* err;
   unsigned long long* trace;   // optional phase timestamps of CTA 0
+  int load_mode;         // how a tile reaches shared memory (see issue_tile)
 };
 
 // Trace layout (global-timer nanoseconds, CTA 0, thread 0): [0] start, [1] initialisation done,
@@ -92,13 +93,13 @@ __device__ __forceinline__ void trace_at(const FusedArgs& a, int idx) {
     a.trace[idx] = ptx::global_ns();
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ unsigned int ld_acquire32(const unsigned int* p) {
   unsigned int v;
@@ -171,11 +172,13 @@ struct alignas(16) FusedShared {
 };
 
 // Flag barrier over every CTA of the launch that also all-gathers two FP32 partial sums per CTA
-// (v0, v1): CTA c stores (v, tag) words in its slot with release semantics; warp 0 of every CTA
-// polls all slots with acquire loads until every tag is this barrier's, then adds the partials
-// in CTA order (FP64) into sh.sums. Slots alternate between two parities, so a CTA can only
-// overwrite a slot once every CTA has passed the barrier before. Returns false when abandoned
-// (deadline here, or the abort word raised elsewhere). All threads must call it.
+// (v0, v1): CTA c fences its writes and stores (v, tag) words in its slot; warp 0 of every CTA
+// polls all slots with relaxed loads (all in flight at once: an acquire load would order the
+// next one behind it) until every tag is this barrier's, fences (acquire side of the fence
+// pairing), then adds the partials in CTA order (FP64) into sh.sums. Slots alternate between two
+// parities, so a CTA can only overwrite a slot once every CTA has passed the barrier before.
+// Returns false when abandoned (deadline here, or the abort word raised elsewhere). All threads
+// must call it.
 __device__ __forceinline__ bool flag_barrier(const FusedArgs& a, FusedShared& sh, unsigned int tag, float v0,
                              float v1) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -185,8 +188,8 @@ __device__ __forceinline__ bool flag_barrier(const FusedArgs& a, FusedShared& sh
   if (tid == 0) {
     __threadfence();
     const unsigned long long t = (unsigned long long)tag << 32;
-    st_release64(base + 2 * blockIdx.x, t | __float_as_uint(v0));
-    st_release64(base + 2 * blockIdx.x + 1, t | __float_as_uint(v1));
+    st_relaxed64(base + 2 * blockIdx.x, t | __float_as_uint(v0));
+    st_relaxed64(base + 2 * blockIdx.x + 1, t | __float_as_uint(v1));
   }
   if (warp == 0) {
     constexpr int kU = kFMaxGrid / 32;
@@ -203,8 +206,8 @@ __device__ __forceinline__ bool flag_barrier(const FusedArgs& a, FusedShared& sh
       for (int u = 0; u < kU; ++u) {
         const int c = lane + 32 * u;
         if (c < G) {
-          const unsigned long long w0 = ld_acquire64(base + 2 * c);
-          const unsigned long long w1 = ld_acquire64(base + 2 * c + 1);
+          const unsigned long long w0 = ld_relaxed64(base + 2 * c);
+          const unsigned long long w1 = ld_relaxed64(base + 2 * c + 1);
           mine = mine && ((unsigned int)(w0 >> 32) == tag) && ((unsigned int)(w1 >> 32) == tag);
           s0 += (double)__uint_as_float((unsigned int)w0);
           s1 += (double)__uint_as_float((unsigned int)w1);
@@ -228,6 +231,7 @@ __device__ __forceinline__ bool flag_barrier(const FusedArgs& a, FusedShared& sh
         }
       }
     }
+    __threadfence();   // the slots were observed: later reads see what their writers fenced
     s0 = warp_sumd(s0);
     s1 = warp_sumd(s1);
     if (lane == 0) {
@@ -324,23 +328,51 @@ struct PassState {
   int64_t r0, r1;
   int T;
   int64_t npad, total;
-  int64_t consumed, issued;     // tiles consumed / copies issued (issued: thread 0)
+  int64_t consumed, issued;     // tiles consumed / copies issued
   unsigned long long tile_wait; // thread 0: ns spent waiting for tiles (trace)
   float tt_acc;                 // lane 0 of warps < NV: squares of the row values it summed
   bool gotall;
 };
 
-// Issues the bulk copy of the CTA's tile k (thread 0).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                   ptx::smem_u32(dst)),
+               "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(ptx::smem_u32(bar))
+               : "memory");
+}
+
+// Starts the copy of the CTA's tile k into its stage, completing on the stage's mbarrier. Every
+// thread calls it. load_mode 0: one 1-D bulk copy (TMA) of the tile by thread 0; 1: one bulk copy
+// per row by thread 0; 2: every thread copies 16-byte chunks with cp.async and arrives on the
+// mbarrier when its chunks have landed (the mbarrier then counts kT arrivals).
 template <int RT>
 __device__ __forceinline__ void issue_tile(const FusedArgs& a, FusedShared& sh, const PassState& ps,
                                            int64_t k, uint64_t pol) {
   const int slot = (int)(k % ps.S);
   const int64_t row = ps.r0 + (int64_t)(k % ps.T) * RT;
   const int rows = (int)min((int64_t)RT, ps.r1 - row);
+  float* dst = ps.ring + slot * ps.stage_floats;
+  const float* src = a.A + row * ps.npad;
+  if (a.load_mode == 2) {
+    const int64_t chunks = (int64_t)rows * ps.npad / 4;
+    for (int64_t c = threadIdx.x; c < chunks; c += kT) cp_async16(dst + 4 * c, src + 4 * c, pol);
+    cp_async_arrive(&sh.full[slot]);
+    return;
+  }
+  if (threadIdx.x != 0) return;
   const uint32_t bytes = (uint32_t)(rows * ps.npad * (int64_t)sizeof(float));
   ptx::mbar_expect_tx(&sh.full[slot], bytes);
-  ptx::bulk_g2s_hint(ps.ring + slot * ps.stage_floats, a.A + row * ps.npad, bytes,
-                     &sh.full[slot], pol);
+  if (a.load_mode == 0) {
+    ptx::bulk_g2s_hint(dst, src, bytes, &sh.full[slot], pol);
+  } else {
+    const uint32_t rb = (uint32_t)(ps.npad * sizeof(float));
+    for (int r = 0; r < rows; ++r)
+      ptx::bulk_g2s_hint(dst + r * ps.npad, src + r * ps.npad, rb, &sh.full[slot], pol);
+  }
 }
 
 // One tile step of the pipelined pass: the dot products of local tile lt (its rows into the
@@ -400,7 +432,7 @@ __device__ __forceinline__ bool pass_tile(const FusedArgs& a, FusedShared& sh, P
   }
   if (__syncthreads_or(!ps.gotall)) return false;
   // every thread holds tile lt in registers: refill its stage
-  if (tid == 0 && lt < ps.T && ps.issued < ps.total) issue_tile<RT>(a, sh, ps, ps.issued++, pol);
+  if (lt < ps.T && ps.issued < ps.total) issue_tile<RT>(a, sh, ps, ps.issued++, pol);
   if (lt >= 1) {
     const int b = (lt - 1) & 1;
     const int rows = (int)min((int64_t)RT, ps.r1 - (ps.r0 + (int64_t)(lt - 1) * RT));
@@ -451,12 +483,15 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
   // the CTA's tiles in sequence: tile k is local tile k % T of pass k / T
   const int64_t total = (int64_t)a.steps * T;
   const uint64_t pol = ptx::policy_evict_first();   // each row of A is read once per pass
-  int64_t issued = 0;                               // meaningful in thread 0
+  int64_t issued = 0;
   trace_at(a, 0);
   if (tid == 0) {
-    for (int k = 0; k < S; ++k) ptx::mbar_init(&sh.full[k], 1);
+    for (int k = 0; k < S; ++k) ptx::mbar_init(&sh.full[k], a.load_mode == 2 ? kT : 1);
     ptx::fence_mbar_init();
     sh.fail = 0;
+  }
+  __syncthreads();
+  {
     const PassState ps0{ring, stage_floats, S, r0, r1, T, npad, total, 0, 0, 0ull, 0.f, true};
     for (; issued < S && issued < total; ++issued) issue_tile<RT>(a, sh, ps0, issued, pol);
   }
@@ -781,9 +816,12 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
     sc->nr = NR;
     sc->passes = passes;
   }
-  if (tid == 0)
+  if (a.load_mode == 2) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (tid == 0) {
     for (int64_t kk = consumed; kk < issued; ++kk)
       ptx::mbar_wait(&sh.full[kk % S], (uint32_t)((kk / S) & 1), a.err, 23);
+  }
 }
 
 template <int NR, int VPT, int RT>
@@ -847,7 +885,7 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
                              float* q, float* part, unsigned long long* slots,
                              unsigned int* epoch, PcgScalars* sc, double sigma2, double cg_tol,
                              int steps, unsigned int* bar, int* err, int num_sms, cudaStream_t st,
-                             unsigned long long* trace) {
+                             unsigned long long* trace, int load_mode) {
   int vpt, rt, stages;
   size_t smem;
   if (!fused_geometry(npad, nr, num_sms, &vpt, &rt, &stages, &smem)) return cudaErrorInvalidValue;
@@ -857,6 +895,7 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
   a.dinv64 = dinv64; a.dinv = dinv; a.W = W; a.WT = WT; a.w = w; a.y = y; a.s = s; a.pa = pa;
   a.pb = pb; a.q = q; a.part = part; a.slots = slots; a.sc = sc; a.sigma2 = sigma2;
   a.cg_tol2 = cg_tol * cg_tol; a.bar = bar; a.err = err; a.trace = trace;
+  a.load_mode = (load_mode >= 0 && load_mode <= 2) ? load_mode : 0;
   // tags of this launch's barriers: epoch, epoch + 1, ... (at most 2 + 4 steps of them); the
   // next launch starts past them, so a slot never holds a matching tag from an earlier barrier
   a.epoch = *epoch;

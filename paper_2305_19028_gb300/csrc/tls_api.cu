@@ -45,6 +45,7 @@ struct tls_ctx {
   DevBuf slots[24];
   int small_path = 0;      // tls_set_small_path
   int pcg_fused = 0;       // tls_set_pcg_fused
+  int fused_load = 0;      // how the one-launch solve loads tiles of A (tls_set_pcg_fused)
   unsigned int* fbar = nullptr;   // abort word of the one-launch PCGTLS solve (96 words)
   unsigned long long* fslots = nullptr;   // its flag-barrier slots
   unsigned int fepoch = 8;        // tag counter of those barriers
@@ -405,8 +406,7 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
           reinterpret_cast<float*>(v.p0), reinterpret_cast<float*>(v.p1),
           reinterpret_cast<float*>(v.q), static_cast<float*>(ctx->part), ctx->fslots,
           &ctx->fepoch, ctx->sc, sigma2, cg_tol, steps, ctx->fbar, ctx->derr, ctx->num_sms,
-          ctx->stream,
-          ctx->trace_on ? ctx->trace : nullptr);
+          ctx->stream, ctx->trace_on ? ctx->trace : nullptr, ctx->fused_load);
     }
     if (e == cudaSuccess) {
       ctx->last_pcg_fused = true;
@@ -1502,7 +1502,8 @@ tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
   tls_default_options(&o);
   if (opt) o = *opt;
   if (o.u != TLS_FP32 && o.u != TLS_FP64) {
-    set_err(ctx, "u must be FP32 or FP64");
+    set_err(ctx, "u must be FP32 or FP64 (a half-precision PCGTLS working precision limits the "
+                 "attainable accuracy, Sec. 4.3)");
     return TLS_ERR_ARG;
   }
   const int64_t limit = (o.u == TLS_FP64) ? 4096 : 8192;
@@ -1768,9 +1769,11 @@ tls_status tls_trace_get(tls_ctx* ctx, uint64_t* out, int cap, int* count) {
 }
 
 tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode) {
-  if (!ctx || mode < 0 || mode > 2) return TLS_ERR_ARG;
-  if (mode == 1 && !tls::pcg_fused_supported(ctx->npad, 2, ctx->num_sms)) return TLS_ERR_ARG;
-  ctx->pcg_fused = mode;
+  if (!ctx || mode < 0 || mode > 5) return TLS_ERR_ARG;
+  if (mode != 0 && mode != 2 && !tls::pcg_fused_supported(ctx->npad, 2, ctx->num_sms))
+    return TLS_ERR_ARG;
+  ctx->pcg_fused = (mode >= 3) ? 1 : mode;
+  if (mode >= 3) ctx->fused_load = mode - 3;
   return TLS_OK;
 }
 
