@@ -541,11 +541,12 @@ def test_constraint_guard_keeps_a_factor_that_meets_constraint_2():
 
 @pytest.mark.parametrize("stall", [1, 0])
 def test_stalled_inner_solve_falls_back_before_max_rqi(stall):
-    # kappa(A) = 1e4 with Haar Y, Z: the FP16 factor leaves PCGTLS with k + 1 steps making no
-    # progress. With stall_fallback the solve refactors in FP32 at the first stalled pair of
-    # solves (trigger STALL or NOT_SPD); without it only after max_rqi steps. Both end at the
-    # oracle's answer.
-    p = synth.dense_problem(2000, 200, d_lo=1e-4, noise=1e-4, seed=3, haar=True)
+    # kappa(A) = 1e4 with Haar Y, Z (noise 1e-6: sigma_{n+1} / sigma'_n = 0.03, a well-posed
+    # TLS problem): the FP16 factor leaves PCGTLS with k + 1 steps making no progress (the
+    # preconditioned residual grows). With stall_fallback the solve refactors in FP32 at the
+    # first stalled pair of solves (trigger STALL or NOT_SPD); without it only after max_rqi
+    # steps. Both end at the oracle's answer.
+    p = synth.dense_problem(2000, 200, d_lo=1e-4, noise=1e-6, seed=3, haar=True)
     xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
     with Ctx(p.A, p.b, u_f="fp16", u="fp32", stall_fallback=stall) as ctx:
         x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
