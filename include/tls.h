@@ -77,7 +77,10 @@ enum {
 typedef struct {
   tls_prec u;          /* PCGTLS precision u_p: TLS_FP32 (mixed) or TLS_FP64 (plain)          */
   int mode_A;          /* 1: operator with A, delta = ||A q||^2 - sigma^2 ||q||^2 (default);    */
-                       /* 0: Alg. 3 as printed, delta = ||p||^2 - sigma^2 ||q||^2               */
+                       /* 0: Alg. 3 as printed, delta = ||p||^2 - sigma^2 ||q||^2 (no pass over */
+                       /* A: the operator is I - sigma^2 R^{-T} R^{-1}); 2: hybrid, the printed */
+                       /* form while psi falls by at least hybrid_ratio per RQI step, then the  */
+                       /* operator with A (dense contexts)                                      */
   int cg_fixed;        /* 1: k+1 PCGTLS steps in RQI step k (Alg. 4, default);                 */
                        /* 0: up to cg_max steps, stopping when ||s_j|| <= cg_tol ||s_0||        */
   double cg_tol;
@@ -113,6 +116,9 @@ typedef struct {
   int constraint_iters;/* > 0: tls_solve also estimates constraints 1 and 2 (Eq. (5), Eq. (9))   */
                        /* as tls_condition does, with this many power iterations, into        */
                        /* tls_info.constr1 / constr2; 0 (default): those fields are NaN         */
+  double hybrid_ratio; /* mode_A = 2: switch to the operator with A at the first RQI step whose  */
+                       /* psi exceeds hybrid_ratio x the previous psi, or whose solves met       */
+                       /* delta_j <= 0 (default 0.1)                                            */
 } tls_options;
 
 typedef struct {
@@ -144,6 +150,8 @@ typedef struct {
                          /* (Eq. (9)) with this solve's sigma; NaN unless constraint_iters     */
   double constr2_scaled; /* constraint 2 of the column-scaled matrix with sigma_{n+1} = 0 (the */
                          /* guard's bound); NaN unless the guard or constraint_iters ran       */
+  int mode_switch_k;     /* mode_A = 2: the RQI step k from which the operator with A was used */
+                         /* (0: never switched); -1 for the other modes                         */
 } tls_info;
 
 typedef struct tls_ctx tls_ctx;

@@ -320,7 +320,10 @@ __device__ __forceinline__ void step_flags(FusedShared& sh, int r, double eta_ne
   if (eta_new == 0.0 || (tol2 > 0.0 && eta_new <= tol2 * sh.eta0[r])) sh.done[r] = 1;
 }
 
-// State of a CTA's pass over its rows (shared by the tile steps below).
+// State of a CTA's pass over its rows (shared by the tile steps below). The ring positions are
+// kept as small counters (no 64-bit division per tile): c_slot / c_phase the stage and mbarrier
+// parity of the next tile to consume, i_slot / i_lt the stage and local tile index of the next
+// tile to issue.
 struct PassState {
   float* ring;
   int64_t stage_floats;
@@ -329,6 +332,8 @@ struct PassState {
   int T;
   int64_t npad, total;
   int64_t consumed, issued;     // tiles consumed / copies issued
+  int c_slot, i_slot, i_lt;
+  uint32_t c_phase;
   unsigned long long tile_wait; // thread 0: ns spent waiting for tiles (trace)
   float tt_acc;                 // lane 0 of warps < NV: squares of the row values it summed
   bool gotall;
@@ -345,21 +350,25 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
                : "memory");
 }
 
-// Starts the copy of the CTA's tile k into its stage, completing on the stage's mbarrier. Every
-// thread calls it. load_mode 0: one 1-D bulk copy (TMA) of the tile by thread 0; 1: one bulk copy
-// per row by thread 0; 2: every thread copies 16-byte chunks with cp.async and arrives on the
-// mbarrier when its chunks have landed (the mbarrier then counts kT arrivals).
+// Starts the copy of the CTA's next tile in sequence (stage ps.i_slot, local tile ps.i_lt) and
+// advances the issue position. Every thread calls it. load_mode 0: one 1-D bulk copy (TMA) of the
+// tile by thread 0; 1: one bulk copy per row by thread 0; 2: every thread copies 16-byte chunks
+// with cp.async and arrives on the mbarrier when its chunks have landed (the mbarrier then
+// counts kT arrivals).
 template <int RT>
-__device__ __forceinline__ void issue_tile(const FusedArgs& a, FusedShared& sh, const PassState& ps,
-                                           int64_t k, uint64_t pol) {
-  const int slot = (int)(k % ps.S);
-  const int64_t row = ps.r0 + (int64_t)(k % ps.T) * RT;
+__device__ __forceinline__ void issue_next(const FusedArgs& a, FusedShared& sh, PassState& ps,
+                                           uint64_t pol) {
+  const int slot = ps.i_slot;
+  const int64_t row = ps.r0 + (int64_t)ps.i_lt * RT;
   const int rows = (int)min((int64_t)RT, ps.r1 - row);
   float* dst = ps.ring + slot * ps.stage_floats;
   const float* src = a.A + row * ps.npad;
+  ++ps.issued;
+  if (++ps.i_slot == ps.S) ps.i_slot = 0;
+  if (++ps.i_lt == ps.T) ps.i_lt = 0;
   if (a.load_mode == 2) {
-    const int64_t chunks = (int64_t)rows * ps.npad / 4;
-    for (int64_t c = threadIdx.x; c < chunks; c += kT) cp_async16(dst + 4 * c, src + 4 * c, pol);
+    const int chunks = (int)((int64_t)rows * ps.npad / 4);
+    for (int c = threadIdx.x; c < chunks; c += kT) cp_async16(dst + 4 * c, src + 4 * c, pol);
     cp_async_arrive(&sh.full[slot]);
     return;
   }
@@ -387,13 +396,18 @@ __device__ __forceinline__ bool pass_tile(const FusedArgs& a, FusedShared& sh, P
   constexpr int NV = NR * RT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (lt < ps.T) {
-    const int slot = (int)(ps.consumed % ps.S);
+    const int slot = ps.c_slot;
     const uint64_t tw0 = (a.trace != nullptr && tid == 0) ? ptx::global_ns() : 0;
-    const bool got =
-        ptx::mbar_wait(&sh.full[slot], (uint32_t)((ps.consumed / ps.S) & 1), a.err, 24);
+    const bool got = ptx::mbar_wait(&sh.full[slot], ps.c_phase, a.err, 24);
     if (a.trace != nullptr && tid == 0) ps.tile_wait += ptx::global_ns() - tw0;
     ps.gotall = ps.gotall && got;
-    if (got) ++ps.consumed;   // a tile that never arrived stays in the drain at the end
+    if (got) {                 // a tile that never arrived stays in the drain at the end
+      ++ps.consumed;
+      if (++ps.c_slot == ps.S) {
+        ps.c_slot = 0;
+        ps.c_phase ^= 1u;
+      }
+    }
     const float* tile = ps.ring + slot * ps.stage_floats;
     const int rows = (int)min((int64_t)RT, ps.r1 - (ps.r0 + (int64_t)lt * RT));
 #pragma unroll
@@ -432,7 +446,7 @@ __device__ __forceinline__ bool pass_tile(const FusedArgs& a, FusedShared& sh, P
   }
   if (__syncthreads_or(!ps.gotall)) return false;
   // every thread holds tile lt in registers: refill its stage
-  if (lt < ps.T && ps.issued < ps.total) issue_tile<RT>(a, sh, ps, ps.issued++, pol);
+  if (lt < ps.T && ps.issued < ps.total) issue_next<RT>(a, sh, ps, pol);
   if (lt >= 1) {
     const int b = (lt - 1) & 1;
     const int rows = (int)min((int64_t)RT, ps.r1 - (ps.r0 + (int64_t)(lt - 1) * RT));
@@ -483,7 +497,6 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
   // the CTA's tiles in sequence: tile k is local tile k % T of pass k / T
   const int64_t total = (int64_t)a.steps * T;
   const uint64_t pol = ptx::policy_evict_first();   // each row of A is read once per pass
-  int64_t issued = 0;
   trace_at(a, 0);
   if (tid == 0) {
     for (int k = 0; k < S; ++k) ptx::mbar_init(&sh.full[k], a.load_mode == 2 ? kT : 1);
@@ -491,10 +504,8 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
     sh.fail = 0;
   }
   __syncthreads();
-  {
-    const PassState ps0{ring, stage_floats, S, r0, r1, T, npad, total, 0, 0, 0ull, 0.f, true};
-    for (; issued < S && issued < total; ++issued) issue_tile<RT>(a, sh, ps0, issued, pol);
-  }
+  PassState ps{ring, stage_floats, S, r0, r1, T, npad, total, 0, 0, 0, 0, 0, 0u, 0ull, 0.f, true};
+  while (ps.issued < S && ps.issued < total) issue_next<RT>(a, sh, ps, pol);
   for (int e = tid; e < nsl; e += kT) {
     sh.w_sl[e] = 0.f;
     sh.di_sl[e] = __ldg(a.dinv + (e_lo + e) % npad);
@@ -597,7 +608,6 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
   // ---- the PCGTLS steps
   trace_at(a, 1);
   int passes = 0;
-  int64_t consumed = 0;
   for (int j = 0; alive && j < a.steps; ++j) {
     __syncthreads();
     if (sh.done[0] && (NR < 2 || sh.done[1])) break;
@@ -627,15 +637,13 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
 #pragma unroll
         for (int v = 0; v < VPT; ++v) acc[r][v] = f4zero();
       float4 a0[RT][VPT], a1[RT][VPT];
-      PassState ps{ring, stage_floats, S, r0, r1, T, npad, total, consumed, issued, 0ull, 0.f,
-                   true};
+      ps.tile_wait = 0ull;
+      ps.tt_acc = 0.f;
       // one CTA barrier per tile: [dots(lt) | sums(lt - 1)] barrier [refill, axpy(lt - 1)]
       for (int lt = 0; ok && lt <= T; lt += 2) {
         ok = pass_tile<NR, VPT, RT>(a, sh, ps, qv, acc, a0, a1, lt, pol);
         if (ok && lt + 1 <= T) ok = pass_tile<NR, VPT, RT>(a, sh, ps, qv, acc, a1, a0, lt + 1, pol);
       }
-      consumed = ps.consumed;
-      issued = ps.issued;
       tile_wait = ps.tile_wait;
       tt_acc = ps.tt_acc;
       // this CTA's partial of A^T t
@@ -819,7 +827,7 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
   if (a.load_mode == 2) {
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (tid == 0) {
-    for (int64_t kk = consumed; kk < issued; ++kk)
+    for (int64_t kk = ps.consumed; kk < ps.issued; ++kk)
       ptx::mbar_wait(&sh.full[kk % S], (uint32_t)((kk / S) & 1), a.err, 23);
   }
 }

@@ -519,7 +519,7 @@ tls_status precond_apply(tls_ctx* ctx, const double* y) {
 bool small_eligible(const tls_ctx* ctx) {
   const tls_options& o = ctx->opt;
   if (ctx->small_path == 3 || ctx->sparse || ctx->u != Prec::FP64 || ctx->n > 64 ||
-      o.mode_A == 0 || o.cg_fixed == 0 || ctx->use_sel_tol)
+      o.mode_A != 1 || o.cg_fixed == 0 || ctx->use_sel_tol)
     return false;
   const size_t one = tls::small_solve_smem((int)ctx->m, (int)ctx->n);
   const bool one_fits = one > 0 && one <= tls::kSmallSmemMax;
@@ -598,6 +598,7 @@ tls_status small_solve(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, do
     for (int i = 0; i < r.n_psi; ++i) info->psi_hist[i] = r.psi_hist[i];
     info->escalations = ctx->escalations;
     info->constr2_scaled = ctx->constr2_scaled;
+    info->mode_switch_k = -1;
   }
   return TLS_OK;
 }
@@ -612,7 +613,12 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     }
   }
   const tls_options& o = ctx->opt;
-  const bool modeA = o.mode_A != 0;
+  // mode_A: 1 the A-explicit operator, 0 Alg. 3 as printed (operator R^T R), 2 the hybrid:
+  // the printed form while psi falls fast, the A-explicit operator from the first RQI step on
+  // whose psi is above hybrid_ratio times the previous one, or whose solves met delta_j <= 0
+  const bool hybrid = o.mode_A == 2;
+  bool modeA = o.mode_A == 1;
+  int switch_k = hybrid ? 0 : -1;
   UVecs<T> v = uvecs<T>(ctx);
   cudaStream_t st = ctx->stream;
   TLS_CK(cudaEventRecord(ctx->ev0, st));
@@ -642,6 +648,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   double prev_psi = INFINITY;
   int stop = TLS_STOP_MAX_RQI;
   int best_k = 0, k = 0, cg_total = 0, not_spd = 0, last_steps = 0;
+  bool continue_after_switch = false;
   double best_psi = INFINITY, best_s2 = 0.0;
   double psi_hist[24];
   int n_psi = 0;
@@ -689,10 +696,18 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
       stop = TLS_STOP_MAX_RQI;
       break;
     }
+    // the hybrid's switch to the A-explicit operator (the printed form stopped paying)
+    if (hybrid && !modeA && k > 1 &&
+        (psi > o.hybrid_ratio * prev_psi || (ctx->h_sc->not_spd[0] | ctx->h_sc->not_spd[1]))) {
+      modeA = true;
+      switch_k = k;
+      prev_psi = psi;
+      continue_after_switch = true;
+    }
     // the precision fallback before max_rqi: the last pair of PCGTLS solves stalled or lost
     // positive definiteness while psi is still above the attainable level
-    if (k > 1 && o.fallback && o.stall_fallback && ctx->uf_used != TLS_FP64 &&
-        best_psi > o.psi_accept * scale) {
+    if (k > 1 && !continue_after_switch && o.fallback && o.stall_fallback &&
+        ctx->uf_used != TLS_FP64 && best_psi > o.psi_accept * scale) {
       const PcgScalars& h = *ctx->h_sc;
       const double rel = (h.eta0[0] > 0.0) ? std::sqrt(h.eta[0] / h.eta0[0]) : 0.0;
       int trig = TLS_TRIGGER_NONE;
@@ -705,6 +720,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
         break;
       }
     }
+    continue_after_switch = false;
     prev_psi = psi;
     // two shifted solves (Alg. 4, PCGTLS with k+1 steps) and the x update
     const int steps = o.cg_fixed ? (k + 1) : std::max(1, o.cg_max);
@@ -759,6 +775,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     for (int i = 0; i < n_psi; ++i) info->psi_hist[i] = psi_hist[i];
     info->escalations = ctx->escalations;
     info->constr2_scaled = ctx->constr2_scaled;
+    info->mode_switch_k = switch_k;
   }
   return TLS_OK;
 }
@@ -1337,6 +1354,7 @@ void tls_default_options(tls_options* opt) {
   opt->stall_fallback = 1;
   opt->stall_ratio = 0.9;
   opt->constraint_iters = 0;
+  opt->hybrid_ratio = 0.1;
 }
 
 const char* tls_status_str(tls_status s) {
@@ -1501,6 +1519,10 @@ tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
   tls_options o;
   tls_default_options(&o);
   if (opt) o = *opt;
+  if (o.mode_A < 0 || o.mode_A > 2 || (o.mode_A == 2 && ctx->sparse)) {
+    set_err(ctx, "mode_A must be 0, 1 or 2 (2: dense contexts)");
+    return TLS_ERR_ARG;
+  }
   if (o.u != TLS_FP32 && o.u != TLS_FP64) {
     set_err(ctx, "u must be FP32 or FP64 (a half-precision PCGTLS working precision limits the "
                  "attainable accuracy, Sec. 4.3)");

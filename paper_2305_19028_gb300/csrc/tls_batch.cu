@@ -1095,6 +1095,7 @@ tls_status tls_batch_solve(tls_batch* bt, double tol, int max_rqi, double* const
       in.fallbacks = bt->fallbacks[(size_t)i];
       in.fallback_trigger = in.fallbacks ? TLS_TRIGGER_MAX_RQI : TLS_TRIGGER_NONE;
       in.constr1 = in.constr2 = in.constr2_scaled = NAN;
+      in.mode_switch_k = -1;
     }
   }
   return first;

@@ -51,7 +51,8 @@ class tls_options(C.Structure):
                 ("ls_iters", C.c_int), ("max_shifts", C.c_int), ("gram_simt", C.c_int),
                 ("psi_accept", C.c_double), ("shift_first", C.c_int), ("fallback", C.c_int),
                 ("constr_guard", C.c_double), ("stall_fallback", C.c_int),
-                ("stall_ratio", C.c_double), ("constraint_iters", C.c_int)]
+                ("stall_ratio", C.c_double), ("constraint_iters", C.c_int),
+                ("hybrid_ratio", C.c_double)]
 
 
 class tls_info(C.Structure):
@@ -62,7 +63,8 @@ class tls_info(C.Structure):
                 ("fail_pivot", C.c_int), ("pass_variant", C.c_int * 2), ("n_psi", C.c_int),
                 ("psi_hist", C.c_double * 24), ("fallbacks", C.c_int),
                 ("fallback_trigger", C.c_int), ("escalations", C.c_int), ("constr1", C.c_double),
-                ("constr2", C.c_double), ("constr2_scaled", C.c_double)]
+                ("constr2", C.c_double), ("constr2_scaled", C.c_double),
+                ("mode_switch_k", C.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("psi_hist", "pass_variant")}

@@ -570,3 +570,44 @@ def test_info_reports_the_papers_constraints():
     with Ctx(p.A, p.b, u_f="fp64", u="fp64") as ctx:
         _, _, info0 = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
     assert np.isnan(info0["constr1"]) and np.isnan(info0["constr2"])
+
+
+# ------------------------------------------------------------------------------------------
+# Alg. 3 as printed (mode R: the operator I - sigma^2 R^{-T} R^{-1}, no pass over A) as a full
+# solve, and the hybrid that starts in that form and switches to the operator with A
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("m,n,u", [(1000, 130, "fp64"), (3000, 300, "fp32"), (400, 40, "fp64")])
+def test_mode_R_solve_matches_oracle_mode_R(m, n, u):
+    # with an FP64 factor, R^T R = A^T A to rounding, and the printed form converges like the
+    # operator with A (Sec. 2): against the oracle's mode R run and the closed form
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-5, seed=11)
+    with Ctx(p.A, p.b, u_f="fp64", u=u, mode_A=0) as ctx:
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=15)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=15, mode="R")
+    assert abs(sigma - so) <= 1e-10 * so, (sigma, so, info)
+    assert _rel(x, xo) <= 1e-8, info
+    assert info["mode_switch_k"] == -1
+
+
+@pytest.mark.parametrize("u_f", ["fp16", "bf16"])
+def test_hybrid_solve_matches_oracle(u_f):
+    # u_f = FP16 / BF16: the printed form alone stalls short of the solution (its operator is
+    # R^T R, off by about u_f), the hybrid switches to the operator with A and converges
+    p = synth.dense_problem(4096, 512, d_lo=1e-3, noise=1e-4, seed=2)
+    with Ctx(p.A, p.b, u_f=u_f, u="fp32", mode_A=2) as ctx:
+        x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=20)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=20)
+    assert abs(sigma - so) <= 1e-10 * so, (sigma, so, info)
+    assert _rel(x, xo) <= 1e-8, info
+    assert info["mode_switch_k"] >= 2, info
+
+
+def test_mode_argument_checked():
+    p = synth.dense_problem(100, 10, seed=1)
+    ctx = tls.tls_create_dense(p.A, p.b)
+    try:
+        with pytest.raises(tls.TLSError) as e:
+            tls.tls_factor(ctx, "fp16", tls.tls_default_options(mode_A=3))
+        assert e.value.status == 1
+    finally:
+        tls.tls_destroy(ctx)
