@@ -120,6 +120,12 @@ tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units);
  */
 tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode);
 /*
+ * tls_set_pcg_l2_keep -- bytes of the FP32 copy of A that the one-launch PCGTLS solve loads with
+ * an L2 evict-last policy (the first tiles of every CTA's row block), so that they stay in L2
+ * from one step's pass to the next; the rest is loaded evict-first. 0 keeps none.
+ */
+tls_status tls_set_pcg_l2_keep(tls_ctx* ctx, int64_t bytes);
+/*
  * tls_trace_enable / tls_trace_get -- phase timestamps (global timer, ns) of the one-launch
  * PCGTLS solve, recorded by CTA 0 into a device buffer of the context when on (the last solve
  * overwrites them): out[0] the launch's start, out[1] the end of the initialisation, then ten

@@ -77,7 +77,10 @@ struct FusedArgs {
   unsigned int* bar;     // [64] abort word (zero between launches)
   int* err;
   unsigned long long* trace;   // optional phase timestamps of CTA 0
-  int load_mode;         // how a tile reaches shared memory (see issue_tile)
+  int load_mode;         // how a tile reaches shared memory (see issue_next)
+  int keep_tiles;        // the first keep_tiles tiles of every CTA's block are loaded with an
+                         // L2 evict-last policy (they stay resident across the steps), the rest
+                         // with evict-first
 };
 
 // Trace layout (global-timer nanoseconds, CTA 0, thread 0): [0] start, [1] initialisation done,
@@ -334,6 +337,7 @@ struct PassState {
   int64_t consumed, issued;     // tiles consumed / copies issued
   int c_slot, i_slot, i_lt;
   uint32_t c_phase;
+  uint64_t pol_keep;            // L2 policy of the tiles kept resident
   unsigned long long tile_wait; // thread 0: ns spent waiting for tiles (trace)
   float tt_acc;                 // lane 0 of warps < NV: squares of the row values it summed
   bool gotall;
@@ -357,7 +361,8 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
 // counts kT arrivals).
 template <int RT>
 __device__ __forceinline__ void issue_next(const FusedArgs& a, FusedShared& sh, PassState& ps,
-                                           uint64_t pol) {
+                                           uint64_t pol_stream) {
+  const uint64_t pol = (ps.i_lt < a.keep_tiles) ? ps.pol_keep : pol_stream;
   const int slot = ps.i_slot;
   const int64_t row = ps.r0 + (int64_t)ps.i_lt * RT;
   const int rows = (int)min((int64_t)RT, ps.r1 - row);
@@ -504,7 +509,10 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
     sh.fail = 0;
   }
   __syncthreads();
-  PassState ps{ring, stage_floats, S, r0, r1, T, npad, total, 0, 0, 0, 0, 0, 0u, 0ull, 0.f, true};
+  uint64_t pol_keep;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_keep));
+  PassState ps{ring, stage_floats, S, r0, r1, T, npad, total, 0, 0, 0, 0, 0, 0u, pol_keep, 0ull,
+               0.f, true};
   while (ps.issued < S && ps.issued < total) issue_next<RT>(a, sh, ps, pol);
   for (int e = tid; e < nsl; e += kT) {
     sh.w_sl[e] = 0.f;
@@ -893,7 +901,7 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
                              float* q, float* part, unsigned long long* slots,
                              unsigned int* epoch, PcgScalars* sc, double sigma2, double cg_tol,
                              int steps, unsigned int* bar, int* err, int num_sms, cudaStream_t st,
-                             unsigned long long* trace, int load_mode) {
+                             unsigned long long* trace, int load_mode, int64_t keep_bytes) {
   int vpt, rt, stages;
   size_t smem;
   if (!fused_geometry(npad, nr, num_sms, &vpt, &rt, &stages, &smem)) return cudaErrorInvalidValue;
@@ -904,6 +912,11 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
   a.pb = pb; a.q = q; a.part = part; a.slots = slots; a.sc = sc; a.sigma2 = sigma2;
   a.cg_tol2 = cg_tol * cg_tol; a.bar = bar; a.err = err; a.trace = trace;
   a.load_mode = (load_mode >= 0 && load_mode <= 2) ? load_mode : 0;
+  // tiles per CTA kept in L2 across the steps: keep_bytes over all CTAs (0: none)
+  a.keep_tiles = (keep_bytes > 0)
+                     ? (int)std::min<int64_t>(1 << 20, keep_bytes / num_sms /
+                                                           ((int64_t)rt * npad * (int64_t)sizeof(float)))
+                     : 0;
   // tags of this launch's barriers: epoch, epoch + 1, ... (at most 2 + 4 steps of them); the
   // next launch starts past them, so a slot never holds a matching tag from an earlier barrier
   a.epoch = *epoch;

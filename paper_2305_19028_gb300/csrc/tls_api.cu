@@ -46,6 +46,7 @@ struct tls_ctx {
   int small_path = 0;      // tls_set_small_path
   int pcg_fused = 0;       // tls_set_pcg_fused
   int fused_load = 0;      // how the one-launch solve loads tiles of A (tls_set_pcg_fused)
+  int64_t l2_keep = 0;     // bytes of A the one-launch solve keeps resident in L2
   unsigned int* fbar = nullptr;   // abort word of the one-launch PCGTLS solve (96 words)
   unsigned long long* fslots = nullptr;   // its flag-barrier slots
   unsigned int fepoch = 8;        // tag counter of those barriers
@@ -406,7 +407,7 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
           reinterpret_cast<float*>(v.p0), reinterpret_cast<float*>(v.p1),
           reinterpret_cast<float*>(v.q), static_cast<float*>(ctx->part), ctx->fslots,
           &ctx->fepoch, ctx->sc, sigma2, cg_tol, steps, ctx->fbar, ctx->derr, ctx->num_sms,
-          ctx->stream, ctx->trace_on ? ctx->trace : nullptr, ctx->fused_load);
+          ctx->stream, ctx->trace_on ? ctx->trace : nullptr, ctx->fused_load, ctx->l2_keep);
     }
     if (e == cudaSuccess) {
       ctx->last_pcg_fused = true;
@@ -1761,6 +1762,12 @@ tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* 
 tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units) {
   if (!ctx || !units || cls < 0 || cls >= TLS_PROF_NCLASSES) return TLS_ERR_ARG;
   *units = ctx->prof_units[cls];
+  return TLS_OK;
+}
+
+tls_status tls_set_pcg_l2_keep(tls_ctx* ctx, int64_t bytes) {
+  if (!ctx || bytes < 0) return TLS_ERR_ARG;
+  ctx->l2_keep = bytes;
   return TLS_OK;
 }
 

@@ -217,7 +217,8 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
                              float* q, float* part, unsigned long long* slots,
                              unsigned int* epoch, PcgScalars* sc, double sigma2, double cg_tol,
                              int steps, unsigned int* bar, int* err, int num_sms, cudaStream_t st,
-                             unsigned long long* trace = nullptr, int load_mode = 0);
+                             unsigned long long* trace = nullptr, int load_mode = 0,
+                             int64_t keep_bytes = 0);
 // Words of the optional phase trace of the one-launch PCGTLS solve (see k_pcg_fused.cu).
 int pcg_fused_trace_words();
 // Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).
