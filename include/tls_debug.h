@@ -67,7 +67,7 @@ enum {
   TLS_PROF_SCALE = 0,        /* column norms, FP32 copy, scaled cast of A       */
   TLS_PROF_GRAM = 1,         /* H = A_s^T A_s                                   */
   TLS_PROF_CHOL = 2,         /* blocked Cholesky (each attempt)                 */
-  TLS_PROF_TRTRI = 3,        /* rounding of R_H, W = R_H^{-1}, W^T             */
+  TLS_PROF_TRTRI = 3,        /* rounding of R_H, W = R_H^{-1}, W^T, (R^T R)^{-1} */
   TLS_PROF_RESID_PASS = 4,   /* FP64 pass over A of the RQI residual           */
   TLS_PROF_RESID_REDUCE = 5, /* its reduction: f, sigma^2, g, psi               */
   TLS_PROF_PCG_PASS2 = 6,    /* PCGTLS pass over A, two right-hand sides        */
@@ -116,7 +116,11 @@ tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units);
  * 1 the one-launch solve (TLS_ERR_ARG when the shape does not fit it), 2 the multi-launch path
  * (a pass launch and a cooperative step-tail launch per step); 3, 4, 5: the one-launch solve
  * with tiles of A loaded by one bulk copy (TMA) per tile, one bulk copy per row, or 16-byte
- * asynchronous copies by every thread (3 is the default loading). Kept until changed.
+ * asynchronous copies by every thread (3 is the default loading, as in 0 and 1; 5 runs the
+ * pass of 6); 6: the one-launch solve with one CTA barrier per tile of A and the tile held in
+ * registers across it (the default pass has no CTA barrier: each warp waits only for the row
+ * values it needs, and a tile stays in shared memory until every warp is done with it); 7: the
+ * default pass with smaller tiles and more stages. Kept until changed.
  */
 tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode);
 /*
@@ -129,12 +133,14 @@ tls_status tls_set_pcg_l2_keep(tls_ctx* ctx, int64_t bytes);
  * tls_trace_enable / tls_trace_get -- phase timestamps (global timer, ns) of the one-launch
  * PCGTLS solve, recorded by CTA 0 into a device buffer of the context when on (the last solve
  * overwrites them): out[0] the launch's start, out[1] the end of the initialisation, then ten
- * words per step j (up to 64 steps) at 2 + 10 j: pass start, pass end, and the ends of grid
- * barrier 1, the column reduction, barrier 2, the W^T product, barrier 3, the W product, barrier
- * 4, and the nanoseconds CTA 0 waited for tiles of A in that pass; then, at 642 + 5 t for
- * the first 64 tiles t of step 0: tile ready, first barrier passed, refill issued, second
- * barrier passed, tile done. Unused words are 0. *count receives the number of words (0 before
- * tls_trace_enable). Host buffer of cap words.
+ * words per step j (up to 64 steps) at 2 + 10 j: pass start, pass end, and the ends of
+ * grid barrier 1, the update of r and w, the same again (word 4 equals word 3), the
+ * M = (R^T R)^{-1} product, grid barrier 2, the new scalars, the next search direction, and the
+ * nanoseconds CTA 0 waited for tiles of A in that pass; then, for grid barrier b (0: the first,
+ * 2: the second) of step j < 8 (i = 3 j + b), the time CTA c arrived at it (642 + 256 i + c) and
+ * the time its arrival was counted (6786 + 256 i + c), and the times CTA 0 saw the last arrival
+ * and finished its acquire fence (12930 + 2 i, + 1). Unused words are 0. *count receives the
+ * number of words (0 before tls_trace_enable). Host buffer of cap words.
  */
 tls_status tls_trace_enable(tls_ctx* ctx, int on);
 tls_status tls_trace_get(tls_ctx* ctx, uint64_t* out, int cap, int* count);

@@ -18,7 +18,7 @@ in the paper's order and notation:
 * Sec. 3.1: the two constraints on the factorisation precision, Eq. (5) and Eq. (9), and the
   scaled-Cholesky success bound, evaluated from their definitions with an exact SVD.
 
-Readings of the paper taken here (each also recorded in the design notes):
+Readings of the paper taken here, where it is silent, garbled or ambiguous:
 
 * PCGTLS operator, "mode A" (default): delta_j = ||A q_j||^2 - sigma^2 ||q_j||^2 and
   s_{j+1} = s_j - alpha_j R^{-T}(A^T A q_j - sigma^2 q_j). Alg. 3 as printed ("mode R") uses

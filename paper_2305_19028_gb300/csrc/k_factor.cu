@@ -529,6 +529,15 @@ void gemm_simt(int M, int N, int K, const Tin* A, int64_t lda, int64_t sA, const
                                                          skip); count_launch();
 }
 
+// M_ij *= dinv_i dinv_j
+__global__ void scale_two_sided_kernel(float* __restrict__ M, const float* __restrict__ dinv,
+                                       int64_t npad) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npad * npad) return;
+  const int64_t i = e / npad, j = e - i * npad;
+  M[e] *= dinv[i] * dinv[j];
+}
+
 __global__ void set_identity_pad_kernel(void* M, int fp64, int64_t n, int64_t npad) {
   int64_t j = n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= npad) return;
@@ -1191,5 +1200,16 @@ template void launch_round_to<float>(float*, int64_t, Prec, cudaStream_t);
 template void launch_round_to<double>(double*, int64_t, Prec, cudaStream_t);
 template void launch_trtri<float>(const float*, float*, float*, float*, int64_t, bool, cudaStream_t);
 template void launch_trtri<double>(const double*, double*, double*, double*, int64_t, bool, cudaStream_t);
+
+// The PCGTLS preconditioner as one matrix: M = D^{-1} (W W^T) D^{-1}, W = R_H^{-1} upper
+// triangular (the product skips W's zero k-slabs; upper tiles, mirrored), FP32.
+void launch_precond_matrix(const float* W, const float* dinv, int64_t npad, float* M,
+                           cudaStream_t s) {
+  const int n = (int)npad;
+  gemm_simt<float, float, true, true>(n, n, n, W, npad, 0, W, npad, 0, M, npad, 0, 1.f, 0.f,
+                                      /*upper=*/1, /*mirror=*/1, 1, s, nullptr, /*kfrom_i=*/1, 0);
+  scale_two_sided_kernel<<<(unsigned)((npad * npad + 255) / 256), 256, 0, s>>>(M, dinv, npad);
+  count_launch();
+}
 
 }  // namespace tls

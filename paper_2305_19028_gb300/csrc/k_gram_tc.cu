@@ -14,6 +14,7 @@
 // Every mbarrier wait is bounded by a global-timer deadline: on expiry the kernel records an
 // error code, stops issuing work, frees its TMEM and returns (the host then falls back).
 #include "tls_internal.h"
+#include "tls_ptx.cuh"
 
 #include <cuda.h>
 
@@ -28,54 +29,12 @@ constexpr int TBM = 128, TBN = 128, TBK = 64;     // tile, K block (64 x 2 B = o
 constexpr int STAGES = 6;
 constexpr int STAGE_BYTES = TBM * TBK * 2;        // 16 KB per operand per stage
 constexpr int THREADS = 192;
-constexpr uint64_t WAIT_NS = 500ull * 1000 * 1000; // 0.5 s per wait, far above any real wait
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
-                   smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: returns false (after recording `code` in *err) if the phase did not complete
-// before the deadline.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > WAIT_NS) {
-      atomicCAS(err, 0, code);
-      return false;
-    }
-  }
-  return true;
-}
+// the mbarrier helpers (bounded waits) shared with the other TMA kernels
+using ptx::mbar_expect_tx;
+using ptx::mbar_init;
+using ptx::mbar_wait;
+using ptx::smem_u32;
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
@@ -170,7 +129,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     mbar_init(&acc_bar, 1);
     abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ptx::fence_mbar_init();
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(

@@ -46,10 +46,9 @@ struct tls_ctx {
   int small_path = 0;      // tls_set_small_path
   int pcg_fused = 0;       // tls_set_pcg_fused
   int fused_load = 0;      // how the one-launch solve loads tiles of A (tls_set_pcg_fused)
+  int fused_pass = 0;      // how its pass holds the tiles (tls_set_pcg_fused)
   int64_t l2_keep = 0;     // bytes of A the one-launch solve keeps resident in L2
-  unsigned int* fbar = nullptr;   // abort word of the one-launch PCGTLS solve (96 words)
-  unsigned long long* fslots = nullptr;   // its flag-barrier slots
-  unsigned int fepoch = 8;        // tag counter of those barriers
+  unsigned int* fbar = nullptr;   // barrier counter and abort word of the one-launch solve
   RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
 
   // problem data (device)
@@ -85,6 +84,8 @@ struct tls_ctx {
   void* R = nullptr;         // R_H rounded to u_f, stored in the u type (npad^2)
   void* W = nullptr;         // R_H^{-1} (u type)
   void* WT = nullptr;        // W^T (u type)
+  float* PM = nullptr;       // (R^T R)^{-1} = D^{-1} W W^T D^{-1} (FP32, for the one-launch solve)
+  bool pm_ready = false;     // PM belongs to the current factor
   int shifts = 0;
   double shift = 0.0;
   int64_t fail_pivot = -1;   // pivot index of the last breakdown (-1: none)
@@ -184,7 +185,8 @@ void dev_free(tls_ctx* c, void* p) {
 
 enum Slot : int {
   kSlotCpart, kSlotInfo, kSlotAsT, kSlotH, kSlotM, kSlotWc, kSlotR, kSlotW, kSlotWT, kSlotWork,
-  kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotFeat, kSlotGsplit, kSlotCount
+  kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotFeat, kSlotGsplit, kSlotPM,
+  kSlotCount
 };
 static_assert(kSlotCount <= 24, "slots");
 
@@ -241,19 +243,17 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->gpart = alloc_t<double>(ctx, 4096);
   ctx->counter = alloc_t<unsigned int>(ctx, 32);   // last-CTA counters; [4..22] PCGTLS step
   ctx->fbar = alloc_t<unsigned int>(ctx, 96);
-  ctx->fslots = static_cast<unsigned long long*>(dev_alloc(ctx, tls::pcg_fused_slot_bytes()));
   ctx->derr = alloc_t<int>(ctx, 1);
   ctx->sc = alloc_t<PcgScalars>(ctx, 1);
   ctx->rs = alloc_t<RqiScalars>(ctx, 1);
   if (!ctx->b || !ctx->x || !ctx->x_best || !ctx->f || !ctx->d || !ctx->dinv || !ctx->sout ||
       !ctx->gpart || !ctx->counter || !ctx->sc || !ctx->rs || !ctx->derr || !ctx->dinv32 ||
-      !ctx->fbar || !ctx->fslots) {
+      !ctx->fbar) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
   TLS_CK(cudaMemsetAsync(ctx->counter, 0, 32 * sizeof(unsigned int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), ctx->stream));
-  TLS_CK(cudaMemsetAsync(ctx->fslots, 0, tls::pcg_fused_slot_bytes(), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->sc, 0, sizeof(PcgScalars), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->rs, 0, sizeof(RqiScalars), ctx->stream));
@@ -395,19 +395,30 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
   if constexpr (std::is_same<T, float>::value) {
   if (modeA && !ctx->sparse && steps > 0 && ctx->pcg_fused != 2 &&
       tls::pcg_fused_supported(npad, nr, ctx->num_sms)) {
-    // the whole solve in one persistent cooperative launch
-    cudaError_t e;
-    {
+    // the whole solve in one persistent cooperative launch, preconditioned by the matrix
+    // (R^T R)^{-1} formed once per factor
+    cudaError_t e = cudaSuccess;
+    if (!ctx->pm_ready) {
+      ctx->PM = static_cast<float*>(slot(ctx, kSlotPM, sizeof(float) * (size_t)npad * npad));
+      if (!ctx->PM) {
+        set_err(ctx, "device allocation failed (preconditioner matrix)");
+        return TLS_ERR_OOM;
+      }
+      Prof pr(ctx, TLS_PROF_TRTRI);
+      tls::launch_precond_matrix(reinterpret_cast<const float*>(W), ctx->dinv32, npad, ctx->PM,
+                                 ctx->stream);
+      e = cudaGetLastError();
+      ctx->pm_ready = (e == cudaSuccess);
+    }
+    if (e == cudaSuccess) {
       Prof pr(ctx, nr == 2 ? TLS_PROF_PCG_SOLVE2 : TLS_PROF_PCG_SOLVE1);
       e = tls::launch_pcg_fused(
           reinterpret_cast<const float*>(ctx->A32), ctx->m, ctx->n, npad, nr, fin0, s0, fin1,
-          ctx->dinv, ctx->dinv32, reinterpret_cast<const float*>(W),
-          reinterpret_cast<const float*>(WT), reinterpret_cast<float*>(v.w),
-          reinterpret_cast<float*>(v.y), reinterpret_cast<float*>(v.s),
-          reinterpret_cast<float*>(v.p0), reinterpret_cast<float*>(v.p1),
-          reinterpret_cast<float*>(v.q), static_cast<float*>(ctx->part), ctx->fslots,
-          &ctx->fepoch, ctx->sc, sigma2, cg_tol, steps, ctx->fbar, ctx->derr, ctx->num_sms,
-          ctx->stream, ctx->trace_on ? ctx->trace : nullptr, ctx->fused_load, ctx->l2_keep);
+          ctx->PM, reinterpret_cast<float*>(v.w), reinterpret_cast<float*>(v.s),
+          reinterpret_cast<float*>(v.p0), ctx->sc, sigma2, cg_tol, steps, ctx->fbar, ctx->derr,
+          ctx->num_sms,
+          ctx->stream, ctx->trace_on ? ctx->trace : nullptr, ctx->fused_load, ctx->l2_keep,
+          ctx->fused_pass);
     }
     if (e == cudaSuccess) {
       ctx->last_pcg_fused = true;
@@ -1069,6 +1080,7 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     ctx->R = slot(ctx, kSlotR, us * (size_t)npad * (size_t)npad);
     ctx->W = slot(ctx, kSlotW, us * (size_t)npad * (size_t)npad);
     ctx->WT = slot(ctx, kSlotWT, us * (size_t)npad * (size_t)npad);
+    ctx->pm_ready = false;
     void* work = slot(ctx, kSlotWork, us * (size_t)npad * (size_t)npad);
     if (!ctx->R || !ctx->W || !ctx->WT || !work) {
       set_err(ctx, "device allocation failed (inverse factor)");
@@ -1798,11 +1810,12 @@ tls_status tls_trace_get(tls_ctx* ctx, uint64_t* out, int cap, int* count) {
 }
 
 tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode) {
-  if (!ctx || mode < 0 || mode > 5) return TLS_ERR_ARG;
+  if (!ctx || mode < 0 || mode > 7) return TLS_ERR_ARG;
   if (mode != 0 && mode != 2 && !tls::pcg_fused_supported(ctx->npad, 2, ctx->num_sms))
     return TLS_ERR_ARG;
   ctx->pcg_fused = (mode >= 3) ? 1 : mode;
-  if (mode >= 3) ctx->fused_load = mode - 3;
+  ctx->fused_load = (mode >= 3 && mode <= 5) ? mode - 3 : 0;
+  ctx->fused_pass = (mode == 5) ? 1 : (mode >= 6) ? mode - 5 : 0;
   return TLS_OK;
 }
 

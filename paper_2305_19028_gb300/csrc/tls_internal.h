@@ -203,22 +203,24 @@ bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* 
                      unsigned int* bar, int* err, int num_sms, cudaStream_t st);
 // A whole PCGTLS solve (A-explicit operator, FP32, nr right-hand sides fin0 * fin0_scale and
 // fin1, `steps` steps or fewer on the stop flags) in one persistent cooperative launch of
-// num_sms CTAs (k_pcg_fused.cu). Vectors nr x npad; part: num_sms x nr x npad floats; slots:
-// pcg_fused_slot_bytes() zero-initialised bytes of flag-barrier words; *epoch: the tag counter of
-// those barriers (starts at 8, advanced by each launch); bar: 96 zero-initialised words (its
-// abort word stays zero unless a bounded wait expired, which also records a code in *err).
-// Writes w and the scalars in sc.
+// num_sms CTAs (k_pcg_fused.cu), preconditioned by M = (R^T R)^{-1} (npad x npad, FP32). w, z:
+// nr x npad floats; atd: 2 x nr x npad floats (scratch); bar: 96 zero-initialised words (they
+// are zero again after the launch unless a bounded wait expired, which records a code in *err;
+// the caller then clears them). Writes w and the
+// scalars in sc. keep_bytes of A (leading tiles of every CTA's rows) are kept in L2. pass_kind:
+// 0 warps decoupled, tiles of A held in shared memory until every warp's axpy (the largest
+// tiles that leave three stages), 1 one CTA barrier per tile with the tile held in registers
+// across it (the only kind for load_mode 2), 2 as 0 with smaller tiles and five stages or more.
 bool pcg_fused_supported(int64_t npad, int nr, int num_sms);
-size_t pcg_fused_slot_bytes();
 cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad, int nr,
                              const double* fin0, double fin0_scale, const double* fin1,
-                             const double* dinv64, const float* dinv, const float* W,
-                             const float* WT, float* w, float* y, float* s, float* pa, float* pb,
-                             float* q, float* part, unsigned long long* slots,
-                             unsigned int* epoch, PcgScalars* sc, double sigma2, double cg_tol,
-                             int steps, unsigned int* bar, int* err, int num_sms, cudaStream_t st,
-                             unsigned long long* trace = nullptr, int load_mode = 0,
-                             int64_t keep_bytes = 0);
+                             const float* M, float* w, float* z, float* atd, PcgScalars* sc,
+                             double sigma2, double cg_tol, int steps, unsigned int* bar, int* err,
+                             int num_sms, cudaStream_t st, unsigned long long* trace = nullptr,
+                             int load_mode = 0, int64_t keep_bytes = 0, int pass_kind = 0);
+// M = D^{-1} W W^T D^{-1} (npad x npad, FP32) from W = R_H^{-1} (upper) and dinv = 1 / d.
+void launch_precond_matrix(const float* W, const float* dinv, int64_t npad, float* M,
+                           cudaStream_t s);
 // Words of the optional phase trace of the one-launch PCGTLS solve (see k_pcg_fused.cu).
 int pcg_fused_trace_words();
 // Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).

@@ -410,8 +410,8 @@ def tls_trace_enable(ctx, on: bool = True) -> None:
 def tls_trace_get(ctx) -> np.ndarray:
     """Phase timestamps (ns) of the last one-launch PCGTLS solve (see tls_debug.h)."""
     cnt = C.c_int()
-    buf = (C.c_uint64 * 4096)()
-    _check(load().tls_trace_get(ctx, buf, 4096, C.byref(cnt)), ctx)
+    buf = (C.c_uint64 * 16384)()
+    _check(load().tls_trace_get(ctx, buf, 16384, C.byref(cnt)), ctx)
     return np.array(buf[:cnt.value], dtype=np.uint64)
 
 

@@ -229,19 +229,20 @@ def test_solve_tolerance_mode_matches_oracle(m, n, u_f, u, cg_tol):
 
 
 FUSED_SHAPES = [
-    # (m, n): n_pad 64 (8 rows per tile), 704 and 2048 (4 rows), 2112 (2 rows, two float4
-    # groups per thread), 4160 (1 row, three groups); m leaves CTAs without rows (m < 152)
-    # or gives ragged last tiles
+    # (m, n): n_pad 64 and 704 (8 rows per tile held in shared memory, 4 in registers), 2048
+    # (4 rows), 2112 (two float4 groups per thread), 4160 (three groups); m leaves CTAs without
+    # rows (m < 152) or gives ragged last tiles
     (100, 40), (3001, 700), (9000, 2048), (5003, 2100), (4500, 4100),
 ]
 
 
-@pytest.mark.parametrize("load", [3, 4, 5])
+@pytest.mark.parametrize("load", [3, 4, 5, 6, 7])
 @pytest.mark.parametrize("m,n", FUSED_SHAPES)
 def test_one_launch_pcgtls_matches_multi_launch_and_oracle(m, n, load):
-    """The one-launch PCGTLS solve (every step's pass over A, reductions and W / W^T products in
-    one cooperative launch) against the multi-launch path and the oracle with the same factor,
-    for every ring geometry the kernel uses; and that it is the path that ran."""
+    """The one-launch PCGTLS solve (every step's pass over A, reductions and the product with
+    (R^T R)^{-1} in one cooperative launch) against the multi-launch path and the oracle with
+    the same factor, for every ring geometry, tile loading and tile holding the kernel has; and
+    that it is the path that ran."""
     p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=17)
     rng = np.random.default_rng(9)
     f0, f1 = rng.standard_normal(n), rng.standard_normal(n)
