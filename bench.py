@@ -364,6 +364,16 @@ def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int 
                 "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": None, "peak_source": src, "avg_launch_us": avg_s * 1e6,
                 "algorithmic_bytes": unit_bytes}
+    if cls == "resid_pass" and variant64 == 4:
+        # double-FP32 residual: A read once as the FP32 pair A32 + Alo (8 bytes per entry, the
+        # FP64 pass's traffic), x and b in, the per-CTA FP64 partials of A^T r out
+        unit_bytes = 8 * m * n + 8 * m + 8 * n + 152 * 8 * n
+        ach = unit_bytes / avg_s / 1e9
+        return {"kernel": "resid_df_kernel (r = b - A x, A^T r in double-FP32 arithmetic on "
+                          "A32 + Alo)", "bound": "hbm", "achieved": ach,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "peak_source": src, "avg_launch_us": avg_s * 1e6, "algorithmic_bytes": unit_bytes,
+                "fp64_equivalent_tflops": 4.0 * m * n / avg_s / 1e12}
     if cls == "resid_pass":
         # FP64 FMA-bound on this GPU: r = b - A x and A^T r are 2 FMA (4 flops) per entry of A
         flops = 4.0 * m * n

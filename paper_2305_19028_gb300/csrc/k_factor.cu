@@ -38,7 +38,8 @@ __device__ __forceinline__ double load_f(const double* p) { return *p; }
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) colnorm_kernel(const double* __restrict__ A, int64_t lda,
                                                       int64_t m, int64_t n, int64_t npad,
-                                                      float* __restrict__ A32, int64_t ldo,
+                                                      float* __restrict__ A32,
+                                                      float* __restrict__ Alo, int64_t ldo,
                                                       double* __restrict__ part) {
   const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int64_t rows_per = (m + gridDim.y - 1) / gridDim.y;
@@ -55,7 +56,13 @@ __global__ void __launch_bounds__(256) colnorm_kernel(const double* __restrict__
       for (int u = 0; u < U; ++u) v[u] = (c < n && i0 + u < r1) ? __ldcs(A + (i0 + u) * lda + c) : 0.0;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const float f = f64_to_f32_rn(v[u]);
+        float f, lo;
+        if (Alo != nullptr) {
+          f64_split_f32(v[u], f, lo);
+          if (i0 + u < r1) Alo[(i0 + u) * ldo + c] = lo;
+        } else {
+          f = f64_to_f32_rn(v[u]);
+        }
         if (i0 + u < r1) A32[(i0 + u) * ldo + c] = f;
         acc = fmaf(f, f, acc);
       }
@@ -238,7 +245,8 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(
 // each (two 4-row and two 4-column strips, read from shared memory as float4), the next k-slab
 // prefetched into registers while the current one is used (one barrier per slab).
 // Same layouts and flags as gemm_simt_kernel; in addition
-//   kfrom_i: the k range of a tile row block starts at i0 (A upper triangular: A(i,k) = 0, k < i)
+//   kfrom_i: 1: the k range of a tile row block starts at i0 (A upper triangular: A(i,k) = 0,
+//            k < i); 2: the k range of a tile starts at j0 (B(k,j) = 0 for k < j)
 //   kto_j:   the k range of a tile column block ends at j0 + 128 (B upper triangular).
 // Requires M, N multiples of 4, K a multiple of 8, lda, ldb multiples of 4 and 16-byte aligned
 // A, B (the dispatcher checks).
@@ -253,7 +261,7 @@ __device__ __forceinline__ void gemm_big_tile(
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int i0 = tile_i * BM, j0 = tile_j * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  int k_lo = kfrom_i ? (i0 / BK) * BK : 0;
+  int k_lo = (kfrom_i == 1) ? (i0 / BK) * BK : (kfrom_i == 2 ? (j0 / BK) * BK : 0);
   int k_hi = kto_j ? min(K, j0 + BN) : K;
   if (k_lo > K) k_lo = K;
   // global -> register slab loader: one float4 of A and one of B per thread
@@ -384,7 +392,7 @@ __device__ __forceinline__ void gemm_mid_tile(
   __shared__ __align__(16) float Bs[2][BK][LD];
   const int i0 = tile_i * BM, j0 = tile_j * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  int k_lo = kfrom_i ? (i0 / BK) * BK : 0;
+  int k_lo = (kfrom_i == 1) ? (i0 / BK) * BK : (kfrom_i == 2 ? (j0 / BK) * BK : 0);
   const int k_hi = kto_j ? min(K, j0 + BN) : K;
   if (k_lo > K) k_lo = K;
   // A: AK: row i = tid / 4, k = (tid & 3) * 4; else k = tid / 16, i = (tid & 15) * 4
@@ -926,11 +934,12 @@ void launch_nonfinite(const double* p, int64_t count, int* flag, int num_sms, cu
 
 // =========================================================================================
 void launch_colnorm(const double* A, int64_t lda, int64_t m, int64_t n, int64_t npad,
-                    float* A32, int64_t ldo, double* d_out, float* dinv32, double* dinv64,
-                    double* part, cudaStream_t s) {
+                    float* A32, float* Alo, int64_t ldo, double* d_out, float* dinv32,
+                    double* dinv64, double* part, cudaStream_t s) {
   const int P = (int)std::min<int64_t>(64, std::max<int64_t>(1, m / 64));
   dim3 grid((unsigned)((npad + 255) / 256), P);
-  colnorm_kernel<<<grid, 256, 0, s>>>(A, lda, m, n, npad, A32, ldo, part); count_launch();
+  colnorm_kernel<<<grid, 256, 0, s>>>(A, lda, m, n, npad, A32, A32 ? Alo : nullptr, ldo, part);
+  count_launch();
   colnorm_finish_kernel<<<blocks_for(npad, 256), 256, 0, s>>>(part, P, n, npad, d_out, dinv32,
                                                               dinv64); count_launch();
 }
@@ -1202,12 +1211,13 @@ template void launch_trtri<float>(const float*, float*, float*, float*, int64_t,
 template void launch_trtri<double>(const double*, double*, double*, double*, int64_t, bool, cudaStream_t);
 
 // The PCGTLS preconditioner as one matrix: M = D^{-1} (W W^T) D^{-1}, W = R_H^{-1} upper
-// triangular (the product skips W's zero k-slabs; upper tiles, mirrored), FP32.
+// triangular: (W W^T)_ij = sum over k >= max(i, j) of W_ik W_jk, so an upper tile (I <= J)
+// starts its k range at j0; mirrored to the lower triangle, FP32.
 void launch_precond_matrix(const float* W, const float* dinv, int64_t npad, float* M,
                            cudaStream_t s) {
   const int n = (int)npad;
   gemm_simt<float, float, true, true>(n, n, n, W, npad, 0, W, npad, 0, M, npad, 0, 1.f, 0.f,
-                                      /*upper=*/1, /*mirror=*/1, 1, s, nullptr, /*kfrom_i=*/1, 0);
+                                      /*upper=*/1, /*mirror=*/1, 1, s, nullptr, /*kfrom_i=*/2, 0);
   scale_two_sided_kernel<<<(unsigned)((npad * npad + 255) / 256), 256, 0, s>>>(M, dinv, npad);
   count_launch();
 }

@@ -11,6 +11,7 @@
 //  * FP64 RQI vector kernels: the x_{k+1} update of Alg. 2 and the inverse-iteration start.
 #include "tls_internal.h"
 #include "tls_ptx.cuh"
+#include "tls_device.cuh"
 
 #include <algorithm>
 
@@ -104,7 +105,7 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
 // for k < K lands in out[k] (written by thread 0). Used by the last CTA of a grid.
 template <int K>
 __device__ __forceinline__ void reduce_partials(const double* part, int P, double* out) {
-  __shared__ double sh[kWarps * K];
+  __shared__ double sh[32 * K];      // one slot per warp of the largest block (1024 threads)
   double v[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = 0.0;
@@ -1440,6 +1441,260 @@ void apass_dispatch(int vpt, dim3 grid, const T* A, int64_t lda, int64_t m, int6
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// RQI residual pass in double-FP32 arithmetic (Alg. 2, the u_r quantities r = b - A x,
+// A^T r, ||r||^2, b^T r). On this GPU an FP64 FMA issues at 1/64 of the FP32 rate, which makes
+// the FP64 pass (2 FMA per entry of A) arithmetic-bound at about 2.6 times its HBM time. Here
+// A is read as the FP32 pair A32 + Alo (A to 2^-48 relative, Alo = fl32(A - A32)), x as FP32
+// pairs, and every product a x is formed as the exact FP32 product of the leading parts
+// (TwoProd by FMA) plus the two cross terms, accumulated in unevaluated FP32 pairs (TwoSum);
+// the dropped a_lo x_lo term and the pair rounding keep each partial sum to about 2^-47 of the
+// sum of the magnitudes of its terms. r_i is formed as a pair from b_i; ||r||^2 and b^T r are
+// accumulated in FP64, and the per-CTA column partials of A^T r are written in FP64 for the
+// same reduction as the FP64 pass.
+// ---------------------------------------------------------------------------------------
+constexpr int kDfThreads = 512;
+constexpr int kDfWarps = kDfThreads / 32;
+constexpr int kDfMaxStages = 8;
+
+// (the _rn intrinsics keep the compiler from contracting a product into a later add, which
+// would break the error-free transforms)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += (ah + al) (xh + xl): ah xh exactly (FMA), the cross terms ah xl and al xh in
+// FP32, al xl (2^-48 of the product) dropped
+__device__ __forceinline__ void df_fma(float ah, float al, float xh, float xl, float& hi,
+                                       float& lo) {
+  const float p = __fmul_rn(ah, xh);
+  float e = __fmaf_rn(ah, xh, -p);
+  e = __fmaf_rn(ah, xl, e);
+  e = __fmaf_rn(al, xh, e);
+  float s, t;
+  two_sum(hi, p, s, t);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+
+// (hi, lo) += (bh, bl): the pair sum (TwoSum of the leading parts, the low parts added)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  hi = s;
+  lo = __fadd_rn(__fadd_rn(lo, bl), e);
+}
+
+// Warp sums of NV FP32 pairs by recursive halving (as warp_reduce_scatter): lane l returns the
+// warp total of pair l >> (5 - log2 NV).
+template <int NV>
+__device__ __forceinline__ void df_reduce_scatter(float (&h)[NV], float (&l)[NV], float& oh,
+                                                  float& ol) {
+  const int lane = threadIdx.x & 31;
+  int o = 16;
+#pragma unroll
+  for (int k = NV; k > 1; k >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < k / 2; ++i) {
+      const float kh = up ? h[k / 2 + i] : h[i], kl = up ? l[k / 2 + i] : l[i];
+      const float gh = up ? h[i] : h[k / 2 + i], gl = up ? l[i] : l[k / 2 + i];
+      const float rh = __shfl_xor_sync(0xffffffffu, gh, o);
+      const float rl = __shfl_xor_sync(0xffffffffu, gl, o);
+      h[i] = kh;
+      l[i] = kl;
+      df_add(h[i], l[i], rh, rl);
+    }
+  }
+  oh = h[0];
+  ol = l[0];
+  for (; o > 0; o >>= 1) {
+    const float rh = __shfl_xor_sync(0xffffffffu, oh, o);
+    const float rl = __shfl_xor_sync(0xffffffffu, ol, o);
+    df_add(oh, ol, rh, rl);
+  }
+}
+
+// One CTA per SM streams its block of rows of A32 and Alo through a ring of bulk-copy stages;
+// thread t owns the float4 column groups (v * 512 + t) of every row, for the row dot products
+// and for the axpy alike, so a tile is read from shared memory once and held in registers
+// across its CTA barrier. Per tile (RT rows): each thread's pair partials of the RT dot
+// products, a warp reduce-scatter, and the sums of tile t - 1 over the warps (warp rt adds row
+// rt's 16 warp shares in warp order and forms r_i = b_i - A_i x); one CTA barrier; then the
+// refill of tile t's stage and the axpy of tile t - 1.
+template <int RT, int VPT>
+__global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
+    const float* __restrict__ Ahi, const float* __restrict__ Alo, int64_t m, int64_t npad,
+    const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ part,
+    double* __restrict__ spart, double* __restrict__ sout, unsigned int* counter, int stages,
+    int* err) {
+  constexpr int kSh = (RT >= 16 ? 1 : (RT >= 8 ? 2 : (RT >= 4 ? 3 : (RT >= 2 ? 4 : 5))));
+  extern __shared__ __align__(128) unsigned char dsm[];
+  float* ring = reinterpret_cast<float*>(dsm);
+  __shared__ uint64_t full[kDfMaxStages];
+  __shared__ float2 red[2][kDfWarps][RT];      // per-warp pair shares of a tile's rows
+  __shared__ float2 rsm[2][RT];                // the tile's r_i as FP32 pairs
+  __shared__ double sred[kDfWarps][2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // the thread's x values as FP32 pairs
+  float xh[VPT * 4], xl[VPT * 4];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+      f64_split_f32(col < npad ? x[col + cc] : 0.0, xh[v * 4 + cc], xl[v * 4 + cc]);
+  }
+  float ach[VPT * 4], acl[VPT * 4];
+#pragma unroll
+  for (int e = 0; e < VPT * 4; ++e) ach[e] = acl[e] = 0.f;
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = min(m, (int64_t)blockIdx.x * per);
+  const int64_t r1 = min(m, r0 + per);
+  const int ntiles = (r1 > r0) ? (int)((r1 - r0 + RT - 1) / RT) : 0;
+  const int64_t half_floats = (int64_t)RT * npad;        // the A32 rows, then the Alo rows
+  const int64_t stage_floats = 2 * half_floats;
+  const uint64_t pol = ptx::policy_evict_first();
+  auto issue = [&](int t) {
+    const int64_t row = r0 + (int64_t)t * RT;
+    const int rows = (int)min((int64_t)RT, r1 - row);
+    const uint32_t bytes = (uint32_t)(rows * npad * (int64_t)sizeof(float));
+    uint64_t* bar = &full[t % stages];
+    float* dst = ring + (t % stages) * stage_floats;
+    ptx::mbar_expect_tx(bar, 2 * bytes);
+    ptx::bulk_g2s_hint(dst, Ahi + row * npad, bytes, bar, pol);
+    ptx::bulk_g2s_hint(dst + half_floats, Alo + row * npad, bytes, bar, pol);
+  };
+  if (tid == 0) {
+    for (int s2 = 0; s2 < stages; ++s2) ptx::mbar_init(&full[s2], 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int t = 0; t < stages && t < ntiles; ++t) issue(t);
+  double rr = 0.0, br = 0.0;      // lane 0 of warps < RT: its rows' ||r||^2 and b^T r
+  float4 ph[RT][VPT], pl[RT][VPT];  // the previous tile (its axpy follows the barrier)
+  for (int t = 0; t <= ntiles; ++t) {
+    float4 ch[RT][VPT], cl[RT][VPT];
+    if (t < ntiles) {
+      const int64_t i0 = r0 + (int64_t)t * RT;
+      ptx::mbar_wait(&full[t % stages], (uint32_t)((t / stages) & 1), err, 12);
+      const float* th = ring + (t % stages) * stage_floats;
+      const float* tl = th + half_floats;
+      const int rows = (int)min((int64_t)RT, r1 - i0);
+      float dh[RT], dl[RT];
+#pragma unroll
+      for (int rt = 0; rt < RT; ++rt) {
+        dh[rt] = dl[rt] = 0.f;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
+          const bool ok = rt < rows && col < npad;
+          ch[rt][v] = ok ? *reinterpret_cast<const float4*>(th + rt * npad + col)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+          cl[rt][v] = ok ? *reinterpret_cast<const float4*>(tl + rt * npad + col)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+          df_fma(ch[rt][v].x, cl[rt][v].x, xh[v * 4 + 0], xl[v * 4 + 0], dh[rt], dl[rt]);
+          df_fma(ch[rt][v].y, cl[rt][v].y, xh[v * 4 + 1], xl[v * 4 + 1], dh[rt], dl[rt]);
+          df_fma(ch[rt][v].z, cl[rt][v].z, xh[v * 4 + 2], xl[v * 4 + 2], dh[rt], dl[rt]);
+          df_fma(ch[rt][v].w, cl[rt][v].w, xh[v * 4 + 3], xl[v * 4 + 3], dh[rt], dl[rt]);
+        }
+      }
+      float oh, ol;
+      df_reduce_scatter<RT>(dh, dl, oh, ol);
+      if ((lane & ((1 << kSh) - 1)) == 0) red[t & 1][warp][lane >> kSh] = make_float2(oh, ol);
+    }
+    if (t >= 1 && warp < RT) {
+      // row `warp` of tile t - 1: the 16 warp shares in warp order, then r_i = b_i - A_i x
+      const int bb = (t - 1) & 1;
+      const int64_t row = r0 + (int64_t)(t - 1) * RT + warp;
+      float2 q = (lane < kDfWarps) ? red[bb][lane][warp] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int o = kDfWarps / 2; o > 0; o >>= 1) {
+        const float rh = __shfl_xor_sync(0xffffffffu, q.x, o);
+        const float rl = __shfl_xor_sync(0xffffffffu, q.y, o);
+        df_add(q.x, q.y, rh, rl);
+      }
+      if (lane == 0) {
+        float2 rv = make_float2(0.f, 0.f);
+        if (row < r1) {
+          float bh, bl;
+          f64_split_f32(b[row], bh, bl);
+          df_add(bh, bl, -q.x, -q.y);            // r = b - A_i x as a pair,
+          two_sum(bh, bl, rv.x, rv.y);           // renormalised for the products that follow
+          const double r = (double)rv.x + (double)rv.y;
+          rr = fma(r, r, rr);
+          br = fma(b[row], r, br);
+        }
+        rsm[bb][warp] = rv;
+      }
+    }
+    __syncthreads();
+    // every thread holds tile t in registers: refill its stage
+    if (tid == 0 && t < ntiles && t + stages < ntiles) {
+      ptx::fence_proxy_async();
+      issue(t + stages);
+    }
+    if (t >= 1) {
+      const int bb = (t - 1) & 1;
+      const int rows = (int)min((int64_t)RT, r1 - (r0 + (int64_t)(t - 1) * RT));
+#pragma unroll
+      for (int rt = 0; rt < RT; ++rt) {
+        if (rt >= rows) break;
+        const float2 rv = rsm[bb][rt];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          df_fma(ph[rt][v].x, pl[rt][v].x, rv.x, rv.y, ach[v * 4 + 0], acl[v * 4 + 0]);
+          df_fma(ph[rt][v].y, pl[rt][v].y, rv.x, rv.y, ach[v * 4 + 1], acl[v * 4 + 1]);
+          df_fma(ph[rt][v].z, pl[rt][v].z, rv.x, rv.y, ach[v * 4 + 2], acl[v * 4 + 2]);
+          df_fma(ph[rt][v].w, pl[rt][v].w, rv.x, rv.y, ach[v * 4 + 3], acl[v * 4 + 3]);
+        }
+      }
+    }
+    if (t < ntiles) {
+#pragma unroll
+      for (int rt = 0; rt < RT; ++rt)
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          ph[rt][v] = ch[rt][v];
+          pl[rt][v] = cl[rt][v];
+        }
+    }
+  }
+  // ---- the CTA's column partials of A^T r and its ||r||^2, b^T r (FP64)
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
+    if (col < npad) {
+      double2* dst = reinterpret_cast<double2*>(part + (int64_t)blockIdx.x * npad + col);
+      dst[0] = make_double2((double)ach[v * 4 + 0] + (double)acl[v * 4 + 0],
+                            (double)ach[v * 4 + 1] + (double)acl[v * 4 + 1]);
+      dst[1] = make_double2((double)ach[v * 4 + 2] + (double)acl[v * 4 + 2],
+                            (double)ach[v * 4 + 3] + (double)acl[v * 4 + 3]);
+    }
+  }
+  if (lane == 0) {
+    sred[warp][0] = rr;
+    sred[warp][1] = br;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int w = 0; w < RT && w < kDfWarps; ++w) {
+      a0 += sred[w][0];
+      a1 += sred[w][1];
+    }
+    spart[(int64_t)blockIdx.x * 2 + 0] = a0;
+    spart[(int64_t)blockIdx.x * 2 + 1] = a1;
+  }
+  if (arrive_last(counter)) {
+    reduce_partials<2>(spart, (int)gridDim.x, sout);
+    if (tid == 0) *counter = 0u;
+  }
+}
+
 }  // namespace
 
 // =========================================================================================
@@ -1654,5 +1909,41 @@ void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaS
 TLS_INST(float)
 TLS_INST(double)
 #undef TLS_INST
+
+// The RQI residual pass in double-FP32 arithmetic (resid_df_kernel): A as the pair A32 + Alo
+// (m x npad each, row-major, rows back to back), x and b FP64; per-CTA FP64 partials of A^T r
+// in part (grid x npad) and (||r||^2, b^T r) in spart, their totals in sout[0..1] by the last
+// CTA. Returns the grid (the number of partials), or 0 when npad is outside the kernel's range
+// (npad <= 8192, a multiple of 64) and nothing was launched.
+int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
+                    const double* x, const double* b, double* part, double* spart, double* sout,
+                    unsigned int* counter, int* err, int num_sms, cudaStream_t s) {
+  if (npad <= 0 || npad > 8192 || npad % 64 != 0 || m <= 0) return 0;
+  // float4 column groups per thread and rows per tile (RT * VPT <= 4: two tiles of both planes
+  // in registers)
+  const int vpt = (int)((npad + 4 * kDfThreads - 1) / (4 * kDfThreads));
+  const int rt = (vpt == 1) ? 4 : (vpt == 2 ? 2 : 1);
+  const size_t stage = (size_t)2 * rt * npad * sizeof(float);
+  const int stages = (int)std::min<size_t>(kDfMaxStages, (size_t)(200 * 1024) / stage);
+  if (stages < 2) return 0;
+  const int grid = (int)std::min<int64_t>((int64_t)num_sms, std::max<int64_t>(1, m / (2 * rt)));
+  const size_t smem = (size_t)stages * stage;
+#define TLS_DF(R, V)                                                                           \
+  {                                                                                            \
+    static const bool attr = [] {                                                              \
+      cudaFuncSetAttribute(resid_df_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           200 * 1024);                                                        \
+      return true;                                                                             \
+    }();                                                                                       \
+    (void)attr;                                                                                \
+    resid_df_kernel<R, V><<<grid, kDfThreads, smem, s>>>(Ahi, Alo, m, npad, x, b, part, spart, \
+                                                         sout, counter, stages, err);          \
+    count_launch();                                                                            \
+  }
+  if (vpt == 1) TLS_DF(4, 1) else if (vpt == 2) TLS_DF(2, 2) else if (vpt == 3) TLS_DF(1, 3)
+  else TLS_DF(1, 4)
+#undef TLS_DF
+  return grid;
+}
 
 }  // namespace tls

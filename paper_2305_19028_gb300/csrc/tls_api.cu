@@ -66,6 +66,7 @@ struct tls_ctx {
   double* A64 = nullptr;   // m x npad, zero padded columns
   double* b = nullptr;     // m
   float* A32 = nullptr;    // m x npad, made by tls_factor when u = FP32
+  float* Alo = nullptr;    // m x npad, fl32(A - A32): A32 + Alo is A to 2^-48 (residual pass)
   double norm2_A = 0.0, norm2_b = 0.0;
 
   // factor
@@ -116,6 +117,7 @@ struct tls_ctx {
   PcgScalars* sc = nullptr;
   RqiScalars* rs = nullptr;
   int P64 = 0, PU = 0;
+  bool resid_df = true;      // the residual pass in double-FP32 arithmetic where it applies
   tls::ApassPlan plan64{}, planU{};
   // pinned host mirrors
   RqiScalars* h_rs = nullptr;
@@ -331,6 +333,14 @@ void prof_collect(tls_ctx* c) {
 // ---------------------------------------------------------------------------------------
 // RQI residual block (FP64 pass over A): r, sigma^2, f, g, psi at ctx->x.
 // ---------------------------------------------------------------------------------------
+// The residual pass runs in double-FP32 arithmetic on A32 + Alo (k_solve.cu, resid_df_kernel)
+// for FP32 working precision once the pair exists and n_pad is in the kernel's range; the FP64
+// kernels otherwise (plain FP64 solves, CSR, or when turned off by tls_set_pass_variant).
+bool resid_df_active(const tls_ctx* ctx) {
+  return ctx->resid_df && !ctx->sparse && ctx->u == Prec::FP32 && ctx->A32 != nullptr &&
+         ctx->Alo != nullptr && ctx->a32_done && ctx->npad <= 8192 && ctx->npad % 64 == 0;
+}
+
 tls_status residual_pass(tls_ctx* ctx) {
   if (ctx->sparse) {
     Prof pr(ctx, TLS_PROF_RESID_PASS);
@@ -340,16 +350,28 @@ tls_status residual_pass(tls_ctx* ctx) {
     TLS_CK_LAUNCH("sparse residual pass");
     return TLS_OK;
   }
+  int P = 0;
   {
     Prof pr(ctx, TLS_PROF_RESID_PASS);
-    tls::launch_apass<double>(ctx->plan64, ctx->A64, ctx->npad, ctx->m, ctx->npad, 1, true,
-                              ctx->x, ctx->npad, ctx->b, ctx->part64, ctx->spart, ctx->sout,
-                              ctx->counter, nullptr, ctx->derr, ctx->stream);
+    if (resid_df_active(ctx))
+      P = tls::launch_resid_df(ctx->A32, ctx->Alo, ctx->m, ctx->npad, ctx->x, ctx->b,
+                               ctx->part64, ctx->spart, ctx->sout, ctx->counter, ctx->derr,
+                               ctx->num_sms, ctx->stream);
+    if (P == 0) {
+      if (ctx->npad > 4096) {
+        set_err(ctx, "the FP64 residual pass supports n_pad <= 4096");
+        return TLS_ERR_ARG;
+      }
+      tls::launch_apass<double>(ctx->plan64, ctx->A64, ctx->npad, ctx->m, ctx->npad, 1, true,
+                                ctx->x, ctx->npad, ctx->b, ctx->part64, ctx->spart, ctx->sout,
+                                ctx->counter, nullptr, ctx->derr, ctx->stream);
+      P = ctx->P64;
+    }
   }
   {
     Prof pr(ctx, TLS_PROF_RESID_REDUCE);
-    tls::launch_resid_reduce(ctx->part64, ctx->P64, ctx->npad, ctx->x, ctx->f, ctx->sout,
-                             ctx->rs, ctx->gpart, ctx->stream);
+    tls::launch_resid_reduce(ctx->part64, P, ctx->npad, ctx->x, ctx->f, ctx->sout, ctx->rs,
+                             ctx->gpart, ctx->stream);
   }
   TLS_CK_LAUNCH("residual pass");
   return TLS_OK;
@@ -781,7 +803,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     info->t_factor_ms = ctx->t_factor_ms;
     info->t_solve_ms = ms;
     info->fail_pivot = (int)ctx->fail_pivot;
-    info->pass_variant[0] = ctx->plan64.variant;
+    info->pass_variant[0] = resid_df_active(ctx) ? 4 : ctx->plan64.variant;
     info->pass_variant[1] = ctx->planU.variant;
     info->n_psi = n_psi;
     for (int i = 0; i < n_psi; ++i) info->psi_hist[i] = psi_hist[i];
@@ -913,12 +935,14 @@ tls_status scaled_constraint2(tls_ctx* ctx, double* out) {
 
 tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   cudaStream_t st = ctx->stream;
+  ctx->resid_df = true;
   const int64_t m = ctx->m, n = ctx->n, npad = ctx->npad, mpad = ctx->mpad;
   TLS_CK(cudaEventRecord(ctx->evf0, st));
   ctx->factored = false;
   if (!ctx->sparse && ctx->u == Prec::FP32 && ctx->A32 == nullptr) {
     ctx->A32 = alloc_t<float>(ctx, m * npad);
-    if (!ctx->A32) {
+    ctx->Alo = alloc_t<float>(ctx, m * npad);
+    if (!ctx->A32 || !ctx->Alo) {
       set_err(ctx, "device allocation failed (FP32 copy of A)");
       return TLS_ERR_OOM;
     }
@@ -937,8 +961,8 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
       tls::sparse_colnorm(ctx->cp, ctx->cv64, want32 ? ctx->cv32 : nullptr, n, npad, ctx->d,
                           ctx->dinv, ctx->dinv32, st);
     else
-      tls::launch_colnorm(ctx->A64, npad, m, n, npad, want32 ? ctx->A32 : nullptr, npad, ctx->d,
-                          ctx->dinv32, ctx->dinv, cpart, st);
+      tls::launch_colnorm(ctx->A64, npad, m, n, npad, want32 ? ctx->A32 : nullptr, ctx->Alo,
+                          npad, ctx->d, ctx->dinv32, ctx->dinv, cpart, st);
     TLS_CK_LAUNCH("column norms");
     ctx->colnorm_done = true;
     ctx->a32_done = ctx->a32_done || want32;
@@ -1735,9 +1759,27 @@ tls_status tls_set_small_path(tls_ctx* ctx, int path) {
 
 tls_status tls_set_pass_variant(tls_ctx* ctx, int variant_fp64, int variant_u) {
   if (!ctx || !ctx->factored || ctx->sparse) return TLS_ERR_STATE;
-  if (variant_fp64 < 0 || variant_fp64 >= tls::kApassVariants || variant_u < 0 ||
+  if (variant_fp64 < 0 || variant_fp64 > tls::kApassVariants || variant_u < 0 ||
       variant_u >= tls::kApassVariants)
     return TLS_ERR_ARG;
+  if (variant_fp64 == tls::kApassVariants) {
+    // the double-FP32 residual pass (FP32 working precision only)
+    const bool was = ctx->resid_df;
+    ctx->resid_df = true;
+    if (!resid_df_active(ctx)) {
+      ctx->resid_df = was;
+      return TLS_ERR_ARG;
+    }
+    const tls::ApassPlan pu = (ctx->u == Prec::FP64)
+                                  ? tls::plan_apass<double>(ctx->m, ctx->npad, 2, ctx->num_sms, variant_u)
+                                  : tls::plan_apass<float>(ctx->m, ctx->npad, 2, ctx->num_sms, variant_u);
+    if ((variant_u == 1 || variant_u == 2) && !pu.tma) return TLS_ERR_ARG;
+    ctx->planU = pu;
+    ctx->PU = pu.grid;
+    return TLS_OK;
+  }
+  if (ctx->npad > 4096) return TLS_ERR_ARG;   // the FP64 passes stop at n_pad = 4096
+  ctx->resid_df = false;
   const tls::ApassPlan p64 = tls::plan_apass<double>(ctx->m, ctx->npad, 1, ctx->num_sms, variant_fp64);
   const tls::ApassPlan pu = (ctx->u == Prec::FP64)
                                 ? tls::plan_apass<double>(ctx->m, ctx->npad, 2, ctx->num_sms, variant_u)

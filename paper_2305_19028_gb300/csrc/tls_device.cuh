@@ -40,4 +40,37 @@ static __device__ __forceinline__ float f64_to_f32_rn(double x) {
 }
 
 
+// a = hi + lo + e with hi = fl32(a) (round to nearest even, as f64_to_f32_rn) and
+// lo = fl32(a - hi), so |e| <= 2^-48 |a|: the FP64 value as an unevaluated pair of FP32 numbers.
+// Integer arithmetic only (no FP64 instruction): with a = sig 2^E (sig the 53-bit significand),
+// hi keeps the top 24 bits of sig rounded, and a - hi = D 2^E exactly with D = sig - 2^29 round(
+// sig / 2^29), |D| <= 2^28. lo = 0 where hi is not a normal FP32 number (|a| < 2^-126, overflow,
+// Inf, NaN): there the pair's error is below 2^-149 or the value is not finite in FP32 anyway.
+static __device__ __forceinline__ void f64_split_f32(double a, float& hi, float& lo) {
+  hi = f64_to_f32_rn(a);
+  lo = 0.f;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+  const int exp = (int)((bits >> 52) & 0x7FF);
+  const int e32 = exp - 1023 + 127;
+  if (exp == 0x7FF || e32 <= 0 || e32 >= 255) return;
+  const unsigned long long sig = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long q = sig >> 29;
+  const unsigned long long rem = sig & ((1ull << 29) - 1);
+  const unsigned long long half = 1ull << 28;
+  const bool up = rem > half || (rem == half && (q & 1));
+  const int D = up ? (int)rem - (1 << 29) : (int)rem;           // |D| <= 2^28
+  if (D == 0) return;
+  // lo = D 2^E, E = exp - 1075 in [-178, 75]: one exact power-of-two product, or two when 2^E
+  // is below the normal range
+  const int E = exp - 1075;
+  float v = __int2float_rn(D);
+  if (E >= -126) {
+    v *= __uint_as_float((unsigned int)(E + 127) << 23);
+  } else {
+    v *= __uint_as_float((unsigned int)(E + 64 + 127) << 23);
+    v *= __uint_as_float((unsigned int)(127 - 64) << 23);
+  }
+  lo = (bits >> 63) ? -v : v;
+}
+
 }  // namespace tls

@@ -103,11 +103,12 @@ int launch_cluster_solve(const double* A, int64_t lda, int m, int n, const doubl
 // *flag |= 1 when one of the `count` FP64 values at p (device, 16-byte aligned) is NaN or
 // infinite (the input check of the create calls, on the device copy).
 void launch_nonfinite(const double* p, int64_t count, int* flag, int num_sms, cudaStream_t s);
-// Column squared norms of A (m x n, row-major, lda) with an optional FP32 copy A32 (ld ldo).
+// Column squared norms of A (m x n, row-major, lda) with an optional FP32 copy A32 (ld ldo)
+// and, with it, the optional low parts Alo = fl32(A - A32) (so A32 + Alo carries A to 2^-48).
 // d_out[j] = sqrt(sum_i a_ij^2) (FP64 out). part: scratch of grid x ld doubles.
 void launch_colnorm(const double* A, int64_t lda, int64_t m, int64_t n, int64_t npad,
-                    float* A32, int64_t ldo, double* d_out, float* dinv32, double* dinv64,
-                    double* part, cudaStream_t s);
+                    float* A32, float* Alo, int64_t ldo, double* d_out, float* dinv32,
+                    double* dinv64, double* part, cudaStream_t s);
 // AsT[j][i] = fl_prec(A[i][j] / d[j]) (transposed, n x mpad, zero padded). A is FP32 (A32)
 // or FP64 (A64) row-major; prec selects the output element type.
 void launch_scale_cast_T(const void* A, bool a_is_fp64, int64_t lda, int64_t m, int64_t n,
@@ -201,6 +202,13 @@ bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* 
                      const T* dinv, PcgScalars* sc, const double* tt, const T* WT, const T* W,
                      T* s, const T* p_cur, T* p_next, double* gpart, bool next,
                      unsigned int* bar, int* err, int num_sms, cudaStream_t st);
+// The RQI residual pass in double-FP32 arithmetic on A = A32 + Alo (k_solve.cu): x, b FP64;
+// FP64 per-CTA partials of A^T r in part (grid x npad) and of (||r||^2, b^T r) in spart, their
+// totals in sout[0..1]; the same outputs as the FP64 pass. Returns the grid, 0 when npad is
+// outside its range (then nothing was launched).
+int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
+                    const double* x, const double* b, double* part, double* spart, double* sout,
+                    unsigned int* counter, int* err, int num_sms, cudaStream_t s);
 // A whole PCGTLS solve (A-explicit operator, FP32, nr right-hand sides fin0 * fin0_scale and
 // fin1, `steps` steps or fewer on the stop flags) in one persistent cooperative launch of
 // num_sms CTAs (k_pcg_fused.cu), preconditioned by M = (R^T R)^{-1} (npad x npad, FP32). w, z:

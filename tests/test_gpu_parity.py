@@ -65,6 +65,46 @@ def test_residual_block_matches_oracle(m, n):
     assert abs(sc["psi"] - psio) <= 1e-6 * psio + 8 * fscale
 
 
+U_DF = 2.0 ** -48     # the double-FP32 residual: A and x carried as FP32 pairs to 2^-48
+
+
+@pytest.mark.parametrize("m,n", [(64, 1), (3001, 40), (1000, 700), (5003, 2100), (4500, 4100),
+                                 (8100, 7900)])
+def test_double_fp32_residual_matches_oracle(m, n):
+    """The residual pass in double-FP32 arithmetic (FP32 working precision: A as A32 + Alo,
+    products by TwoProd, sums in FP32 pairs, r_i as a pair, ||r||^2 and b^T r in FP64) against
+    the FP64 oracle and against the FP64 pass on the same data. Error model: A and x carried to
+    2^-48, each product's dropped low-low term 2^-48, pair sums of a few dozen terms: the
+    entries of r within about 64 * 2^-48 of (|A||x| + |b|) plus the FP64 reductions' n u. Shapes
+    cover the tile sizes (4, 2 and 1 rows: n_pad up to 2048, 4096, 8192) and ragged row
+    blocks; above n_pad = 4096 no FP64 pass exists to compare with."""
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=m + 3 * n)
+    x = p.x_true + 1e-3 * np.random.default_rng(1).standard_normal(n)
+    npad = -(-n // 64) * 64
+    with Ctx(p.A, p.b, u_f="fp32", u="fp32") as ctx:
+        f, sc = tls.tls_residual(ctx, x)
+        x1, s1, info = tls.tls_solve(ctx, tol=0.0, max_rqi=1)
+        assert info["pass_variant"][0] == 4
+        if npad <= 4096:
+            assert tls.load().tls_set_pass_variant(ctx, 3, 0) == 0    # the FP64 pass
+            f64, sc64 = tls.tls_residual(ctx, x)
+        else:
+            assert tls.load().tls_set_pass_variant(ctx, 3, 0) == 1
+            f64, sc64 = f, sc
+    r, s2, fo, go, psio = O.residual_block(p.A, p.b, x)
+    u = 64 * U_DF + n * U64
+    ax = np.abs(p.A) @ np.abs(x) + np.abs(p.b)
+    scale_r = u * ax.max()
+    fscale = (64 * U_DF + m * U64) * (np.abs(p.A).T @ ax).max()
+    for ff, ss in ((f, sc), (f64, sc64)):
+        assert abs(ss["rr"] - r @ r) <= 4 * scale_r * np.linalg.norm(r) * np.sqrt(m) + 1e-300
+        assert abs(ss["sigma2"] - s2) <= 1e-10 * s2
+        assert np.max(np.abs(ff - fo)) <= 8 * fscale
+        assert abs(ss["g"] - go) <= 8 * (64 * U_DF + m * U64) * (np.abs(p.b) @ ax)
+        assert abs(ss["psi"] - psio) <= 1e-6 * psio + 8 * fscale
+    assert np.max(np.abs(f - f64)) <= 16 * fscale
+
+
 # ------------------------------------------------------------------------------------------
 # factor: column scaling, Gram of the u_f-rounded scaled matrix, Cholesky, R_H in u_f (Sec. 3.1)
 # ------------------------------------------------------------------------------------------
