@@ -119,6 +119,10 @@ typedef struct {
   double hybrid_ratio; /* mode_A = 2: switch to the operator with A at the first RQI step whose  */
                        /* psi exceeds hybrid_ratio x the previous psi, or whose solves met       */
                        /* delta_j <= 0 (default 0.1)                                            */
+  int reproducible;    /* 1 (default): bitwise reproducible results (every reduction in a fixed  */
+                       /* order); 0: the one-launch PCGTLS solve sums A^T t with float atomics  */
+                       /* (one grid barrier less per step; results may differ in the last bits  */
+                       /* from run to run)                                                       */
 } tls_options;
 
 typedef struct {

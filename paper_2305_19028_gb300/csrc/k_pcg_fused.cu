@@ -23,8 +23,11 @@
 //   next    eta_{j+1} = r^T z, beta_j and the stop flags (every CTA alike); d_{j+1} = z + beta d
 //
 // Every CTA adds the same numbers in the same order for each scalar, so all take identical
-// decisions without exchanging them; only A^T t (float atomics) is summed in an order that can
-// change from run to run. What keeps the step short on this GPU, where a dependent round trip to
+// decisions without exchanging them. A^T t is summed either in a fixed order (the default,
+// bitwise reproducible: each CTA writes its share, then after barrier 1 every CTA adds the
+// shares of its slice of the entries in CTA order, forms its slice of K d and its part of
+// d^T K d, and a second grid barrier follows) or with float vector atomics (one barrier less;
+// the order of the adds, and so the last bits, can change from run to run). What keeps the step short on this GPU, where a dependent round trip to
 // L2 costs about a microsecond and FP64 arithmetic is slow:
 //  * two grid barriers per step, each one atomic add and one polled word per CTA;
 //  * scalars in FP32, combined by warp shuffles (no FP64 on the critical path);
@@ -53,7 +56,7 @@ constexpr int kFMaxStages = 8;
 constexpr int kFMaxGrid = 256;                 // CTAs of the launch at most (one per SM)
 constexpr int kFMaxRows = 4;                   // rows of W / W^T per warp at most
 constexpr int kFMaxSlice = 256;                // entries of the column slice per CTA at most
-constexpr int kPre = 8;                        // float4 per lane of a prefetched W row
+constexpr int kPre = 8;                        // float4 per lane of a prefetched row of M
 constexpr uint64_t kFBarrierNs = 2000ull * 1000 * 1000;   // grid barrier deadline: 2 s
 
 struct FusedArgs {
@@ -66,8 +69,12 @@ struct FusedArgs {
   const float* M;        // the preconditioner (R^T R)^{-1} = D^{-1} W W^T D^{-1}, npad x npad
   float* w;              // solutions, nr x npad (written at the end)
   float* z;              // M r, nr x npad
-  float* atd;            // A^T t of the passes, 2 x nr x npad (alternating between steps,
-                         // accumulated by every CTA with vector atomics)
+  float* atd;            // atomic form: A^T t of the passes, 2 x nr x npad (alternating between
+                         // steps, accumulated by every CTA with vector atomics); fixed-order
+                         // form: K d, nr x npad
+  float* part;           // fixed-order form: the CTAs' shares of A^T t (G x nr x npad), then
+                         // their shares of d^T K d (G x 2)
+  int det;               // 1: the fixed-order form (bitwise reproducible, one more grid barrier)
   PcgScalars* sc;
   double sigma2, cg_tol2;
   unsigned int* bar;     // [0] grid-barrier counter, [64] abort word (both zero between launches)
@@ -153,6 +160,7 @@ struct alignas(16) FusedShared {
   int rcnt[2];                  // ... warps that published their share of tile k
   int ecnt[kFMaxStages];        // ... warps done with the tile in a stage
   float red[2][kW][16];         // per-warp row values of a tile (double-buffered)
+  float red2[kW][33];           // fixed-order form: partial sums of the slice reduction
   float tot[2][16];             // row values of a tile summed over the warps
   float cta2[kW][2];
   float w_sl[kFMaxSlice];       // this CTA's slice of w
@@ -600,7 +608,7 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
   __shared__ FusedShared sh;
   constexpr int NV = NR * RT;          // row values per tile
   static_assert(NV <= 16 && (NV & (NV - 1)) == 0, "row values per tile: a power of two <= 16");
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = (int)gridDim.x;
   const int64_t npad = a.npad, E = (int64_t)NR * npad;
   const int S = a.stages;
@@ -730,13 +738,26 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
         ok = pass_decoupled<NR, VPT, RT>(a, sh, ps, qv, acc, pol);
       }
       ok = !__syncthreads_or(!ok);
+      if (a.det) {
+        // the CTA's share of A^T t as its own partial (a CTA without rows writes zeros)
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const int64_t col = ((int64_t)v * kT + tid) * 4;
-        if (col < npad && T > 0)
+        for (int v = 0; v < VPT; ++v) {
+          const int64_t col = ((int64_t)v * kT + tid) * 4;
+          if (col < npad)
 #pragma unroll
-          for (int r = 0; r < NR; ++r)
-            atomicAdd(reinterpret_cast<float4*>(atd + r * npad + col), acc[r][v]);
+            for (int r = 0; r < NR; ++r)
+              *reinterpret_cast<float4*>(a.part + (int64_t)blockIdx.x * E + r * npad + col) =
+                  acc[r][v];
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          const int64_t col = ((int64_t)v * kT + tid) * 4;
+          if (col < npad && T > 0)
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+              atomicAdd(reinterpret_cast<float4*>(atd + r * npad + col), acc[r][v]);
+        }
       }
     }
     if (!ok && tid == 0) {
@@ -748,6 +769,49 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
       a.trace[tb + 9] = ps.tile_wait;
     if (!(alive = grid_sync(a, sh, 3 * j))) break;
     trace_at(a, tb + 2);
+    if (a.det) {
+      // fixed-order form: the CTA's slice of K d = (the partials summed in CTA order) - sigma^2 d
+      // into atd, and the slice's share of d^T K d; then a grid barrier
+      const float sig2f = (float)a.sigma2;
+      float* dpart = a.part + (int64_t)G * E;
+      float de0 = 0.f, de1 = 0.f;
+      for (int c0 = 0; c0 < nsl; c0 += 32) {
+        const int e = c0 + lane;
+        float t = 0.f;
+        if (e < nsl) {
+          float pv[kFMaxGrid / kW];
+#pragma unroll
+          for (int u = 0; u < kFMaxGrid / kW; ++u) {
+            const int pc = warp + kW * u;
+            pv[u] = (pc < G) ? __ldcg(a.part + (int64_t)pc * E + e_lo + e) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < kFMaxGrid / kW; ++u) t += pv[u];
+        }
+        sh.red2[warp][lane] = t;
+        __syncthreads();
+        if (warp == 0 && e < nsl) {
+          float at = 0.f;
+#pragma unroll
+          for (int k = 0; k < kW; ++k) at += sh.red2[k][lane];
+          const float dj = sh.d_sl[e];
+          const float kdv = fmaf(-sig2f, dj, at);
+          a.atd[e_lo + e] = kdv;
+          if ((e_lo + e) / npad == 0) de0 = fmaf(dj, kdv, de0);
+          else de1 = fmaf(dj, kdv, de1);
+        }
+        __syncthreads();
+      }
+      if (warp == 0) {
+        de0 = warp_sumf(de0);
+        de1 = warp_sumf(de1);
+        if (lane == 0) {
+          dpart[2 * blockIdx.x] = de0;
+          dpart[2 * blockIdx.x + 1] = de1;
+        }
+      }
+      if (!(alive = grid_sync(a, sh, 3 * j + 1))) break;
+    }
     // ---------------- K d = A^T t - sigma^2 d (the thread's columns, registers);
     // delta_j = d^T K d (= ||A d||^2 - sigma^2 ||d||^2), alpha_j = eta_j / delta_j (every CTA
     // alike, from the whole vectors); r -= alpha K d (every CTA the whole vector), w += alpha d
@@ -763,18 +827,45 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
         for (int r = 0; r < NR; ++r) {
           kd[r][v] = f4zero();
           if (col < npad) {
-            const float4 at = ldcg4(atd + r * npad + col);
-            const float4 q = qv[r][v];
-            kd[r][v] = make_float4(fmaf(-sig2f, q.x, at.x), fmaf(-sig2f, q.y, at.y),
-                                   fmaf(-sig2f, q.z, at.z), fmaf(-sig2f, q.w, at.w));
-            const float dk = dot4(q, kd[r][v], 0.f);
-            if (r == 0) de0 += dk; else de1 += dk;
+            if (a.det) {
+              kd[r][v] = ldcg4(a.atd + r * npad + col);
+            } else {
+              const float4 at = ldcg4(atd + r * npad + col);
+              const float4 q = qv[r][v];
+              kd[r][v] = make_float4(fmaf(-sig2f, q.x, at.x), fmaf(-sig2f, q.y, at.y),
+                                     fmaf(-sig2f, q.z, at.z), fmaf(-sig2f, q.w, at.w));
+              const float dk = dot4(q, kd[r][v], 0.f);
+              if (r == 0) de0 += dk; else de1 += dk;
+            }
           }
         }
       }
       // this warp's first row of M (needed after the update)
       if (gw < npad) prefetch_row(a.M + gw * npad, 0, npad, pre);
-      cta_sum2(de0, de1, sh);
+      if (a.det) {
+        // delta from the CTAs' shares in CTA order (each lane its CTAs, then a butterfly)
+        if (warp == 0) {
+          const float* dpart = a.part + (int64_t)G * E;
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int u = 0; u < kFMaxGrid / 32; ++u) {
+            const int c = lane + 32 * u;
+            if (c < G) {
+              s0 += __ldcg(dpart + 2 * c);
+              s1 += __ldcg(dpart + 2 * c + 1);
+            }
+          }
+          s0 = warp_sumf(s0);
+          s1 = warp_sumf(s1);
+          if (lane == 0) {
+            sh.sums[0] = s0;
+            sh.sums[1] = s1;
+          }
+        }
+        __syncthreads();
+      } else {
+        cta_sum2(de0, de1, sh);
+      }
       if (tid == 0)
         for (int r = 0; r < NR; ++r) {
           sh.ok[r] = 0;
@@ -805,7 +896,7 @@ __global__ void __launch_bounds__(kT, 1) pcg_fused_kernel(const FusedArgs a) {
       for (int e = tid; e < nsl; e += kT) {
         const int r = (int)((e_lo + e) / npad);
         if (sh.ok[r]) sh.w_sl[e] = fmaf(sh.alpha[r], sh.d_sl[e], sh.w_sl[e]);
-        atd_next[e_lo + e] = 0.f;
+        if (!a.det) atd_next[e_lo + e] = 0.f;
       }
     }
     __syncthreads();
@@ -965,7 +1056,8 @@ bool pcg_fused_supported(int64_t npad, int nr, int num_sms) {
 
 cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad, int nr,
                              const double* fin0, double fin0_scale, const double* fin1,
-                             const float* M, float* w, float* z, float* atd, PcgScalars* sc,
+                             const float* M, float* w, float* z, float* atd, float* part,
+                             int det, PcgScalars* sc,
                              double sigma2, double cg_tol, int steps, unsigned int* bar, int* err,
                              int num_sms, cudaStream_t st, unsigned long long* trace,
                              int load_mode, int64_t keep_bytes, int pass_kind) {
@@ -980,7 +1072,7 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
   FusedArgs a{};
   a.A = A; a.m = m; a.n = n; a.npad = npad; a.nr = nr; a.steps = steps; a.stages = stages;
   a.fin0 = fin0; a.fin0_scale = fin0_scale; a.fin1 = fin1; a.M = M; a.w = w; a.z = z;
-  a.atd = atd; a.sc = sc; a.sigma2 = sigma2;
+  a.atd = atd; a.part = part; a.det = det ? 1 : 0; a.sc = sc; a.sigma2 = sigma2;
   a.cg_tol2 = cg_tol * cg_tol; a.bar = bar; a.err = err; a.trace = trace;
   a.load_mode = (load_mode >= 0 && load_mode <= (hold ? 2 : 1)) ? load_mode : 0;
   // tiles per CTA kept in L2 across the steps: keep_bytes over all CTAs (0: none)

@@ -437,7 +437,9 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
       e = tls::launch_pcg_fused(
           reinterpret_cast<const float*>(ctx->A32), ctx->m, ctx->n, npad, nr, fin0, s0, fin1,
           ctx->PM, reinterpret_cast<float*>(v.w), reinterpret_cast<float*>(v.s),
-          reinterpret_cast<float*>(v.p0), ctx->sc, sigma2, cg_tol, steps, ctx->fbar, ctx->derr,
+          reinterpret_cast<float*>(v.p0), static_cast<float*>(ctx->part),
+          ctx->opt.reproducible != 0 ? 1 : 0, ctx->sc, sigma2, cg_tol, steps, ctx->fbar,
+          ctx->derr,
           ctx->num_sms,
           ctx->stream, ctx->trace_on ? ctx->trace : nullptr, ctx->fused_load, ctx->l2_keep,
           ctx->fused_pass);
@@ -1392,6 +1394,7 @@ void tls_default_options(tls_options* opt) {
   opt->stall_ratio = 0.9;
   opt->constraint_iters = 0;
   opt->hybrid_ratio = 0.1;
+  opt->reproducible = 1;
 }
 
 const char* tls_status_str(tls_status s) {

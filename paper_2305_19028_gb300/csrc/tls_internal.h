@@ -211,10 +211,12 @@ int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
                     unsigned int* counter, int* err, int num_sms, cudaStream_t s);
 // A whole PCGTLS solve (A-explicit operator, FP32, nr right-hand sides fin0 * fin0_scale and
 // fin1, `steps` steps or fewer on the stop flags) in one persistent cooperative launch of
-// num_sms CTAs (k_pcg_fused.cu), preconditioned by M = (R^T R)^{-1} (npad x npad, FP32). w, z:
-// nr x npad floats; atd: 2 x nr x npad floats (scratch); bar: 96 zero-initialised words (they
-// are zero again after the launch unless a bounded wait expired, which records a code in *err;
-// the caller then clears them). Writes w and the
+// num_sms CTAs (k_pcg_fused.cu), preconditioned by M = (R^T R)^{-1} (npad x npad, FP32).
+// w, z: nr x npad floats; atd: 2 x nr x npad floats (scratch); part: (num_sms + 1) x nr x npad
+// floats (scratch). det = 1: A^T t reduced in CTA order with one more grid barrier per step
+// (bitwise reproducible); det = 0: summed with float atomics (the order can change from run
+// to run). bar: 96 zero-initialised words (zero again after the launch unless a bounded wait
+// expired, which records a code in *err; the caller then clears them). Writes w and the
 // scalars in sc. keep_bytes of A (leading tiles of every CTA's rows) are kept in L2. pass_kind:
 // 0 warps decoupled, tiles of A held in shared memory until every warp's axpy (the largest
 // tiles that leave three stages), 1 one CTA barrier per tile with the tile held in registers
@@ -222,7 +224,8 @@ int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
 bool pcg_fused_supported(int64_t npad, int nr, int num_sms);
 cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad, int nr,
                              const double* fin0, double fin0_scale, const double* fin1,
-                             const float* M, float* w, float* z, float* atd, PcgScalars* sc,
+                             const float* M, float* w, float* z, float* atd, float* part,
+                             int det, PcgScalars* sc,
                              double sigma2, double cg_tol, int steps, unsigned int* bar, int* err,
                              int num_sms, cudaStream_t st, unsigned long long* trace = nullptr,
                              int load_mode = 0, int64_t keep_bytes = 0, int pass_kind = 0);

@@ -309,6 +309,32 @@ def test_one_launch_pcgtls_matches_multi_launch_and_oracle(m, n, load):
     assert out[load][2] == [steps, steps] and out[load][3] == [0, 0]
 
 
+def test_one_launch_atomic_form_matches_fixed_order_form():
+    """The one-launch solve with A^T t summed by float atomics (reproducible = 0, one grid
+    barrier less per step) against the fixed-order form and the oracle; the fixed-order form
+    repeats itself bit for bit."""
+    m, n = 9000, 2048
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=17)
+    rng = np.random.default_rng(9)
+    f0, f1 = rng.standard_normal(n), rng.standard_normal(n)
+    sigma2 = 0.3 * p.D[-1] ** 2
+    steps = 6
+    out = {}
+    for rep in (1, 0):
+        with Ctx(p.A, p.b, u_f="fp16", u="fp32", fused=1, reproducible=rep) as ctx:
+            RH, d, _ = tls.tls_export_factor(ctx)
+            out[rep] = tls.tls_pcgtls(ctx, sigma2, f0, f1, steps=steps)
+            if rep:
+                again = tls.tls_pcgtls(ctx, sigma2, f0, f1, steps=steps)
+                assert all(np.array_equal(a_, b_) for a_, b_ in zip(out[rep][:2], again[:2]))
+    R = RH * d[None, :]
+    tol = 50 * np.linalg.cond(RH) * n * U32
+    for f, k in ((f0, 0), (f1, 1)):
+        wo, _, _ = O.pcgtls(p.A, R, sigma2, f, steps - 1)
+        assert _rel(out[0][k], wo) <= tol and _rel(out[1][k], wo) <= tol
+        assert _rel(out[0][k], out[1][k]) <= tol
+
+
 @pytest.mark.parametrize("fused", [1, 2])
 def test_solve_paths_match_oracle(fused):
     p = synth.dense_problem(6000, 1000, d_lo=1e-3, noise=1e-4, seed=2)
