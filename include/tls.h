@@ -141,8 +141,7 @@ typedef struct {
   int fail_pivot;        /* pivot index of the last Cholesky breakdown before success (-1)   */
   int pass_variant[2];   /* autotuned kernel of the pass over A: [FP64 residual, PCGTLS];    */
                          /* 0 register kernel, 1 staged 256 threads, 2 staged 512 threads,   */
-                         /* 3 pipelined, 4 (residual) double-FP32 arithmetic on A32 + Alo,   */
-                         /* 5 the same without a CTA barrier per tile;                      */
+                         /* 3 pipelined, 4 (residual) double-FP32 arithmetic on A32 + Alo;   */
                          /* small FP64 problems solved in one launch: {-1, 1}                */
                          /* for the one-CTA solve, {-2, R} for the solve on a cluster of R   */
   int n_psi;             /* entries of psi_hist filled                                       */

@@ -94,8 +94,7 @@ tls_status tls_profile_enable(tls_ctx* ctx, int on);
  * where the staging fits: TLS_ERR_ARG otherwise), 3 pipelined register kernel, for the
  * residual pass (in FP64) and the PCGTLS pass respectively; variant_fp64 = 4: the residual pass
  * in double-FP32 arithmetic on the pair A32 + Alo (the default for FP32 working precision;
- * TLS_ERR_ARG for FP64 working precision), 5: the same with the warps decoupled (no CTA
- * barrier per tile). The FP64 residual passes stop at n_pad = 4096
+ * TLS_ERR_ARG for FP64 working precision). The FP64 residual passes stop at n_pad = 4096
  * (TLS_ERR_ARG above). TLS_ERR_STATE before tls_factor or for CSR.
  */
 tls_status tls_set_pass_variant(tls_ctx* ctx, int variant_fp64, int variant_u);

@@ -1695,223 +1695,6 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
   }
 }
 
-__device__ __forceinline__ void mbar_arrive_cta(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar))
-               : "memory");
-}
-
-// The same residual pass with the warps decoupled (no CTA barrier per tile): a tile stays in
-// its stage until every warp has done its axpy with it. Per tile k each warp forms its pair
-// partials of the RT row dot products and publishes its share (red[k & 1]); the warp that
-// publishes last adds the 16 shares of each row in warp order, forms r_i = b_i - A_i x as a pair
-// (and ||r||^2, b^T r in FP64) and arrives on totb[k & 1]; a warp does the axpy of tile k - 1
-// once totb says its r values are ready, and the last warp done with a stage refills it.
-template <int RT, int VPT>
-__global__ void __launch_bounds__(kDfThreads, 1) resid_dfd_kernel(
-    const float* __restrict__ Ahi, const float* __restrict__ Alo, int64_t m, int64_t npad,
-    const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ part,
-    double* __restrict__ spart, double* __restrict__ sout, unsigned int* counter, int stages,
-    int* err) {
-  constexpr int kSh = (RT >= 16 ? 1 : (RT >= 8 ? 2 : (RT >= 4 ? 3 : (RT >= 2 ? 4 : 5))));
-  extern __shared__ __align__(128) unsigned char dsm[];
-  float* ring = reinterpret_cast<float*>(dsm);
-  __shared__ uint64_t full[kDfMaxStages];
-  __shared__ uint64_t totb[2];
-  __shared__ int rcnt[2];
-  __shared__ int ecnt[kDfMaxStages];
-  __shared__ float2 red[2][kDfWarps][RT];
-  __shared__ float2 rsm[2][RT];
-  __shared__ double srr, sbr;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float xh[VPT * 4], xl[VPT * 4];
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) {
-    const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc)
-      f64_split_f32(col < npad ? x[col + cc] : 0.0, xh[v * 4 + cc], xl[v * 4 + cc]);
-  }
-  float ach[VPT * 4], acl[VPT * 4];
-#pragma unroll
-  for (int e = 0; e < VPT * 4; ++e) ach[e] = acl[e] = 0.f;
-  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = min(m, (int64_t)blockIdx.x * per);
-  const int64_t r1 = min(m, r0 + per);
-  const int ntiles = (r1 > r0) ? (int)((r1 - r0 + RT - 1) / RT) : 0;
-  const int64_t half_floats = (int64_t)RT * npad;
-  const int64_t stage_floats = 2 * half_floats;
-  const uint64_t pol = ptx::policy_evict_first();
-  auto issue = [&](int t) {
-    const int64_t row = r0 + (int64_t)t * RT;
-    const int rows = (int)min((int64_t)RT, r1 - row);
-    const uint32_t bytes = (uint32_t)(rows * npad * (int64_t)sizeof(float));
-    uint64_t* bar = &full[t % stages];
-    float* dst = ring + (t % stages) * stage_floats;
-    ptx::mbar_expect_tx(bar, 2 * bytes);
-    ptx::bulk_g2s_hint(dst, Ahi + row * npad, bytes, bar, pol);
-    ptx::bulk_g2s_hint(dst + half_floats, Alo + row * npad, bytes, bar, pol);
-  };
-  if (tid == 0) {
-    for (int s2 = 0; s2 < stages; ++s2) {
-      ptx::mbar_init(&full[s2], 1);
-      ecnt[s2] = 0;
-    }
-    for (int q = 0; q < 2; ++q) {
-      ptx::mbar_init(&totb[q], 1);
-      rcnt[q] = 0;
-    }
-    srr = 0.0;
-    sbr = 0.0;
-    ptx::fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0)
-    for (int t = 0; t < stages && t < ntiles; ++t) issue(t);
-  for (int t = 0; t <= ntiles; ++t) {
-    if (t < ntiles) {
-      const int64_t i0 = r0 + (int64_t)t * RT;
-      ptx::mbar_wait(&full[t % stages], (uint32_t)((t / stages) & 1), err, 12);
-      const float* th = ring + (t % stages) * stage_floats;
-      const float* tl = th + half_floats;
-      const int rows = (int)min((int64_t)RT, r1 - i0);
-      float dh[RT], dl[RT];
-#pragma unroll
-      for (int rt = 0; rt < RT; ++rt) {
-        dh[rt] = dl[rt] = 0.f;
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
-          if (rt < rows && col < npad) {
-            const float4 ah = *reinterpret_cast<const float4*>(th + rt * npad + col);
-            const float4 al = *reinterpret_cast<const float4*>(tl + rt * npad + col);
-            df_fma(ah.x, al.x, xh[v * 4 + 0], xl[v * 4 + 0], dh[rt], dl[rt]);
-            df_fma(ah.y, al.y, xh[v * 4 + 1], xl[v * 4 + 1], dh[rt], dl[rt]);
-            df_fma(ah.z, al.z, xh[v * 4 + 2], xl[v * 4 + 2], dh[rt], dl[rt]);
-            df_fma(ah.w, al.w, xh[v * 4 + 3], xl[v * 4 + 3], dh[rt], dl[rt]);
-          }
-        }
-      }
-      float oh, ol;
-      df_reduce_scatter<RT>(dh, dl, oh, ol);
-      const int bb = t & 1;
-      if ((lane & ((1 << kSh) - 1)) == 0) red[bb][warp][lane >> kSh] = make_float2(oh, ol);
-      __syncwarp();
-      int last = 0;
-      if (lane == 0) {
-        __threadfence_block();
-        last = (atomicAdd(&rcnt[bb], 1) == kDfWarps - 1) ? 1 : 0;
-      }
-      if (__shfl_sync(0xffffffffu, last, 0)) {
-        // this warp published last: the rows' totals in warp order, r_i = b_i - A_i x
-        __threadfence_block();
-        float2 q[RT];
-#pragma unroll
-        for (int rt = 0; rt < RT; ++rt)
-          q[rt] = (lane < kDfWarps) ? red[bb][lane][rt] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int o = kDfWarps / 2; o > 0; o >>= 1)
-#pragma unroll
-          for (int rt = 0; rt < RT; ++rt) {
-            const float rh = __shfl_xor_sync(0xffffffffu, q[rt].x, o);
-            const float rl = __shfl_xor_sync(0xffffffffu, q[rt].y, o);
-            df_add(q[rt].x, q[rt].y, rh, rl);
-          }
-        if (lane < RT) {
-          float qh = q[0].x, ql = q[0].y;
-#pragma unroll
-          for (int rt = 1; rt < RT; ++rt)
-            if (lane == rt) {
-              qh = q[rt].x;
-              ql = q[rt].y;
-            }
-          const int64_t row = i0 + lane;
-          float2 rv = make_float2(0.f, 0.f);
-          double r = 0.0, bi = 0.0;
-          if (row < r1) {
-            bi = b[row];
-            float bh, bl;
-            f64_split_f32(bi, bh, bl);
-            df_add(bh, bl, -qh, -ql);
-            two_sum(bh, bl, rv.x, rv.y);
-            r = (double)rv.x + (double)rv.y;
-          }
-          rsm[bb][lane] = rv;
-          // ||r||^2 and b^T r of the tile's rows, added in row order by lane 0
-          double rr = r * r, brr = bi * r;
-#pragma unroll
-          for (int o = 1; o < RT; o <<= 1) {
-            rr += __shfl_down_sync((1u << RT) - 1u, rr, o);
-            brr += __shfl_down_sync((1u << RT) - 1u, brr, o);
-          }
-          if (lane == 0) {
-            srr += rr;
-            sbr += brr;
-          }
-        }
-        __syncwarp();
-        if (lane == 0) {
-          rcnt[bb] = 0;
-          mbar_arrive_cta(&totb[bb]);
-        }
-      }
-    }
-    if (t >= 1) {
-      const int k = t - 1;
-      const int bb = k & 1;
-      ptx::mbar_wait(&totb[bb], (uint32_t)((k >> 1) & 1), err, 13);
-      const float* th = ring + (k % stages) * stage_floats;
-      const float* tl = th + half_floats;
-      const int rows = (int)min((int64_t)RT, r1 - (r0 + (int64_t)k * RT));
-#pragma unroll
-      for (int rt = 0; rt < RT; ++rt) {
-        if (rt >= rows) break;
-        const float2 rv = rsm[bb][rt];
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
-          if (col < npad) {
-            const float4 ah = *reinterpret_cast<const float4*>(th + rt * npad + col);
-            const float4 al = *reinterpret_cast<const float4*>(tl + rt * npad + col);
-            df_fma(ah.x, al.x, rv.x, rv.y, ach[v * 4 + 0], acl[v * 4 + 0]);
-            df_fma(ah.y, al.y, rv.x, rv.y, ach[v * 4 + 1], acl[v * 4 + 1]);
-            df_fma(ah.z, al.z, rv.x, rv.y, ach[v * 4 + 2], acl[v * 4 + 2]);
-            df_fma(ah.w, al.w, rv.x, rv.y, ach[v * 4 + 3], acl[v * 4 + 3]);
-          }
-        }
-      }
-      // the stage of tile k is free once every warp is past here: the last one refills it
-      __syncwarp();
-      if (lane == 0 && atomicAdd(&ecnt[k % stages], 1) == kDfWarps - 1) {
-        ecnt[k % stages] = 0;
-        if (k + stages < ntiles) {
-          ptx::fence_proxy_async();
-          issue(k + stages);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) {
-    const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
-    if (col < npad) {
-      double2* dst = reinterpret_cast<double2*>(part + (int64_t)blockIdx.x * npad + col);
-      dst[0] = make_double2((double)ach[v * 4 + 0] + (double)acl[v * 4 + 0],
-                            (double)ach[v * 4 + 1] + (double)acl[v * 4 + 1]);
-      dst[1] = make_double2((double)ach[v * 4 + 2] + (double)acl[v * 4 + 2],
-                            (double)ach[v * 4 + 3] + (double)acl[v * 4 + 3]);
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    spart[(int64_t)blockIdx.x * 2 + 0] = srr;
-    spart[(int64_t)blockIdx.x * 2 + 1] = sbr;
-  }
-  if (arrive_last(counter)) {
-    reduce_partials<2>(spart, (int)gridDim.x, sout);
-    if (tid == 0) *counter = 0u;
-  }
-}
-
 }  // namespace
 
 // =========================================================================================
@@ -2134,8 +1917,7 @@ TLS_INST(double)
 // (npad <= 8192, a multiple of 64) and nothing was launched.
 int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
                     const double* x, const double* b, double* part, double* spart, double* sout,
-                    unsigned int* counter, int* err, int num_sms, cudaStream_t s,
-                    bool decoupled) {
+                    unsigned int* counter, int* err, int num_sms, cudaStream_t s) {
   if (npad <= 0 || npad > 8192 || npad % 64 != 0 || m <= 0) return 0;
   // float4 column groups per thread and rows per tile (RT * VPT <= 4: two tiles of both planes
   // in registers)
@@ -2146,25 +1928,21 @@ int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
   if (stages < 2) return 0;
   const int grid = (int)std::min<int64_t>((int64_t)num_sms, std::max<int64_t>(1, m / (2 * rt)));
   const size_t smem = (size_t)stages * stage;
-#define TLS_DF_K(K, R, V)                                                                      \
+#define TLS_DF(R, V)                                                                           \
   {                                                                                            \
     static const bool attr = [] {                                                              \
-      cudaFuncSetAttribute(K<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);  \
+      cudaFuncSetAttribute(resid_df_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           200 * 1024);                                                        \
       return true;                                                                             \
     }();                                                                                       \
     (void)attr;                                                                                \
-    K<R, V><<<grid, kDfThreads, smem, s>>>(Ahi, Alo, m, npad, x, b, part, spart, sout, counter, \
-                                           stages, err);                                       \
+    resid_df_kernel<R, V><<<grid, kDfThreads, smem, s>>>(Ahi, Alo, m, npad, x, b, part, spart, \
+                                                         sout, counter, stages, err);          \
     count_launch();                                                                            \
-  }
-#define TLS_DF(R, V)                                                                           \
-  {                                                                                            \
-    if (decoupled) TLS_DF_K(resid_dfd_kernel, R, V) else TLS_DF_K(resid_df_kernel, R, V)       \
   }
   if (vpt == 1) TLS_DF(4, 1) else if (vpt == 2) TLS_DF(2, 2) else if (vpt == 3) TLS_DF(1, 3)
   else TLS_DF(1, 4)
 #undef TLS_DF
-#undef TLS_DF_K
   return grid;
 }
 

@@ -118,7 +118,6 @@ struct tls_ctx {
   RqiScalars* rs = nullptr;
   int P64 = 0, PU = 0;
   bool resid_df = true;      // the residual pass in double-FP32 arithmetic where it applies
-  bool resid_dfd = false;    // ... in its form without a CTA barrier per tile
   tls::ApassPlan plan64{}, planU{};
   // pinned host mirrors
   RqiScalars* h_rs = nullptr;
@@ -357,7 +356,7 @@ tls_status residual_pass(tls_ctx* ctx) {
     if (resid_df_active(ctx))
       P = tls::launch_resid_df(ctx->A32, ctx->Alo, ctx->m, ctx->npad, ctx->x, ctx->b,
                                ctx->part64, ctx->spart, ctx->sout, ctx->counter, ctx->derr,
-                               ctx->num_sms, ctx->stream, ctx->resid_dfd);
+                               ctx->num_sms, ctx->stream);
     if (P == 0) {
       if (ctx->npad > 4096) {
         set_err(ctx, "the FP64 residual pass supports n_pad <= 4096");
@@ -806,8 +805,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     info->t_factor_ms = ctx->t_factor_ms;
     info->t_solve_ms = ms;
     info->fail_pivot = (int)ctx->fail_pivot;
-    info->pass_variant[0] =
-        resid_df_active(ctx) ? (ctx->resid_dfd ? 5 : 4) : ctx->plan64.variant;
+    info->pass_variant[0] = resid_df_active(ctx) ? 4 : ctx->plan64.variant;
     info->pass_variant[1] = ctx->planU.variant;
     info->n_psi = n_psi;
     for (int i = 0; i < n_psi; ++i) info->psi_hist[i] = psi_hist[i];
@@ -940,7 +938,6 @@ tls_status scaled_constraint2(tls_ctx* ctx, double* out) {
 tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   cudaStream_t st = ctx->stream;
   ctx->resid_df = true;
-  ctx->resid_dfd = false;
   const int64_t m = ctx->m, n = ctx->n, npad = ctx->npad, mpad = ctx->mpad;
   TLS_CK(cudaEventRecord(ctx->evf0, st));
   ctx->factored = false;
@@ -1765,18 +1762,17 @@ tls_status tls_set_small_path(tls_ctx* ctx, int path) {
 
 tls_status tls_set_pass_variant(tls_ctx* ctx, int variant_fp64, int variant_u) {
   if (!ctx || !ctx->factored || ctx->sparse) return TLS_ERR_STATE;
-  if (variant_fp64 < 0 || variant_fp64 > tls::kApassVariants + 1 || variant_u < 0 ||
+  if (variant_fp64 < 0 || variant_fp64 > tls::kApassVariants || variant_u < 0 ||
       variant_u >= tls::kApassVariants)
     return TLS_ERR_ARG;
-  if (variant_fp64 >= tls::kApassVariants) {
-    // the double-FP32 residual pass (FP32 working precision only); 5: its decoupled form
+  if (variant_fp64 == tls::kApassVariants) {
+    // the double-FP32 residual pass (FP32 working precision only)
     const bool was = ctx->resid_df;
     ctx->resid_df = true;
     if (!resid_df_active(ctx)) {
       ctx->resid_df = was;
       return TLS_ERR_ARG;
     }
-    ctx->resid_dfd = (variant_fp64 == tls::kApassVariants + 1);
     const tls::ApassPlan pu = (ctx->u == Prec::FP64)
                                   ? tls::plan_apass<double>(ctx->m, ctx->npad, 2, ctx->num_sms, variant_u)
                                   : tls::plan_apass<float>(ctx->m, ctx->npad, 2, ctx->num_sms, variant_u);

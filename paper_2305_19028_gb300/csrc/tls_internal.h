@@ -204,13 +204,11 @@ bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* 
                      unsigned int* bar, int* err, int num_sms, cudaStream_t st);
 // The RQI residual pass in double-FP32 arithmetic on A = A32 + Alo (k_solve.cu): x, b FP64;
 // FP64 per-CTA partials of A^T r in part (grid x npad) and of (||r||^2, b^T r) in spart, their
-// totals in sout[0..1]; the same outputs as the FP64 pass. decoupled: the form without a CTA
-// barrier per tile. Returns the grid, 0 when npad is outside its range (then nothing was
-// launched).
+// totals in sout[0..1]; the same outputs as the FP64 pass. Returns the grid, 0 when npad is
+// outside its range (then nothing was launched).
 int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
                     const double* x, const double* b, double* part, double* spart, double* sout,
-                    unsigned int* counter, int* err, int num_sms, cudaStream_t s,
-                    bool decoupled);
+                    unsigned int* counter, int* err, int num_sms, cudaStream_t s);
 // A whole PCGTLS solve (A-explicit operator, FP32, nr right-hand sides fin0 * fin0_scale and
 // fin1, `steps` steps or fewer on the stop flags) in one persistent cooperative launch of
 // num_sms CTAs (k_pcg_fused.cu), preconditioned by M = (R^T R)^{-1} (npad x npad, FP32).
