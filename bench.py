@@ -277,6 +277,12 @@ def run_reference(args, ws, rank):
 # from the ncu capture in profiles/resid_pass_dense_8192x2048.md (134.346 MB read + 0.067 MB
 # written at m = 8192; one read of A, so proportional to m)
 RESID_PIPE_TRAFFIC_PER_ROW = (134.346e6 + 0.067e6) / 8192
+# DRAM bytes of the double-FP32 residual pass per launch at 16384 x 2048 (read + write, from the
+# ncu capture in profiles/resid_df_dense_16384x2048.md), and of the one-launch paired PCGTLS
+# solve per paired iteration at the same size (profiles/pcg_fused_dense_16384x2048.md: 419.96 MB
+# for a launch of 3 iterations)
+RESID_DF_TRAFFIC_C2 = 268.643584e6 + 3.102208e6
+PCG_FUSED_TRAFFIC_PER_ITER_C2 = (416.771072e6 + 3.188480e6) / 3
 
 
 def paired_iteration_bytes(m: int, n: int) -> int:
@@ -301,7 +307,9 @@ def _inner_loop(prof: dict, units: dict, peaks: dict, m: int, n: int) -> dict:
         return {"kernel": "pcg_fused_kernel (one launch per paired PCGTLS solve: t = A d, "
                           "A^T t by atomics, r and w updates, z = (R^T R)^{-1} r; FP32)",
                 "unit_of_work": "one paired PCGTLS iteration", "bound": "hbm", "achieved": ach,
-                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": PCG_FUSED_TRAFFIC_PER_ITER_C2 if (m, n) == (16384, 2048) else None,
+                "traffic_unit": "DRAM bytes per paired iteration (ncu, 3-step launch)",
                 "peak_source": src, "us_per_iteration": per * 1e6, "iterations": it,
                 "launches": cnt, "algorithmic_bytes": byts}
     # multi-launch path: the pass launches plus the step-tail launches per iteration
@@ -371,7 +379,9 @@ def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int 
         ach = unit_bytes / avg_s / 1e9
         return {"kernel": "resid_df_kernel (r = b - A x, A^T r in double-FP32 arithmetic on "
                           "A32 + Alo)", "bound": "hbm", "achieved": ach,
-                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": RESID_DF_TRAFFIC_C2 if (m, n) == (16384, 2048) else None,
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                 "peak_source": src, "avg_launch_us": avg_s * 1e6, "algorithmic_bytes": unit_bytes,
                 "fp64_equivalent_tflops": 4.0 * m * n / avg_s / 1e12}
     if cls == "resid_pass":
