@@ -305,7 +305,8 @@ def _inner_loop(prof: dict, units: dict, peaks: dict, m: int, n: int) -> dict:
         per = ms * 1e-3 / it
         ach = byts / per / 1e9
         return {"kernel": "pcg_fused_kernel (one launch per paired PCGTLS solve: t = A d, "
-                          "A^T t by atomics, r and w updates, z = (R^T R)^{-1} r; FP32)",
+                          "A^T t reduced in a fixed order, r and w updates, "
+                          "z = (R^T R)^{-1} r; FP32)",
                 "unit_of_work": "one paired PCGTLS iteration", "bound": "hbm", "achieved": ach,
                 "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": PCG_FUSED_TRAFFIC_PER_ITER_C2 if (m, n) == (16384, 2048) else None,
