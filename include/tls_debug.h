@@ -133,6 +133,13 @@ tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode);
  */
 tls_status tls_set_pcg_l2_keep(tls_ctx* ctx, int64_t bytes);
 /*
+ * tls_set_factor_chain -- c = 1 .. 4 (default 3): the block steps of an FP32 Cholesky factor
+ * whose trailing matrix fits run in one persistent cooperative launch of up to c CTAs per SM (a
+ * grid barrier between steps); 0: one launch per block step. The arithmetic is the same in
+ * all. Kept until changed.
+ */
+tls_status tls_set_factor_chain(tls_ctx* ctx, int on);
+/*
  * tls_trace_enable / tls_trace_get -- phase timestamps (global timer, ns) of the one-launch
  * PCGTLS solve, recorded by CTA 0 into a device buffer of the context when on (the last solve
  * overwrites them): out[0] the launch's start, out[1] the end of the initialisation, then ten

@@ -4,6 +4,7 @@
 // W = R_H^{-1} that the PCGTLS iteration applies as two triangular products per step.
 #include "tls_internal.h"
 #include "tls_device.cuh"
+#include "tls_ptx.cuh"
 #include "chol64.cuh"
 
 #include <algorithm>
@@ -765,14 +766,12 @@ __device__ __forceinline__ void tile_atb64(const float* As, const float* Bs, flo
 // factors and inverts the next diagonal block. One launch per block step instead of two (the
 // panel products are repeated by the CTAs of a tile row and column; the same arithmetic, in the
 // same order, as the separate panel and update products).
-__global__ void __launch_bounds__(256) chol_step_kernel(float* M, float* W, int64_t npad,
-                                                        int64_t kb, int* info, int prec) {
-  if (*(volatile int*)info != 0) return;
-  const int ti = blockIdx.y, tj = blockIdx.x;
-  if (ti > tj) return;
+// One trailing tile (ti, tj), ti <= tj, of block step kb (the body of chol_step_kernel; all
+// threads of the CTA; dsm: 3 x NB x LDT floats).
+__device__ __forceinline__ void chol_step_tile(float* M, const float* W, int64_t npad, int64_t kb,
+                                               int ti, int tj, unsigned char* dsm) {
   const bool diag = (ti == tj);
   const int64_t k2 = kb + NB;
-  extern __shared__ __align__(16) unsigned char dsm[];
   float* Wk = reinterpret_cast<float*>(dsm);
   float* Hi = Wk + NB * LDT;
   float* Hj = Hi + NB * LDT;
@@ -832,9 +831,112 @@ __global__ void __launch_bounds__(256) chol_step_kernel(float* M, float* W, int6
       float* cp = C + (int64_t)a * npad + b;
       *cp = -acc[p][q] + *cp;
     }
+}
+
+__global__ void __launch_bounds__(256) chol_step_kernel(float* M, float* W, int64_t npad,
+                                                        int64_t kb, int* info, int prec) {
+  if (*(volatile int*)info != 0) return;
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (ti > tj) return;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  chol_step_tile(M, W, npad, kb, ti, tj, dsm);
   if (ti != 0 || tj != 0) return;
   __syncthreads();   // the updated block (written by this CTA) before it is factored
-  potrf_inv_diag_body<float>(M, W, npad, k2, info, prec, dsm);
+  potrf_inv_diag_body<float>(M, W, npad, kb + NB, info, prec, dsm);
+}
+
+// Grid barrier of a cooperative launch on bar[0] (bar[1]: abort word): thread 0 of each CTA
+// fences and adds 1 (CTA 0 adds 2^31 - (G - 1)), so the top bit flips once every CTA has
+// arrived and the low bits return to their value; it polls until the bit differs from the one
+// its own add saw. Bounded by a 2 s deadline (then code 31 in *err and the abort word raised,
+// which the other CTAs see at their next poll). Returns false when abandoned. All threads call it.
+__device__ __forceinline__ bool chol_grid_sync(unsigned int* bar, int* err) {
+  __shared__ int fail;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fail = 0;
+    const unsigned int nb = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
+    __threadfence();
+    const unsigned int old = atomicAdd(bar, nb);
+    const uint64_t t0 = ptx::global_ns();
+    unsigned int it = 0;
+    while (((old ^ *(volatile unsigned int*)bar) & 0x80000000u) == 0u) {
+      if ((++it & 63u) == 0) {
+        if (*(volatile unsigned int*)(bar + 1) != 0u) {
+          fail = 1;
+          break;
+        }
+        if (ptx::global_ns() - t0 > 2000ull * 1000 * 1000) {
+          atomicCAS(err, 0, 31);
+          atomicExch(bar + 1, 1u);
+          fail = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return fail == 0;
+}
+
+// The block steps kb_from, kb_from + NB, ... of the FP32 factor in one persistent cooperative
+// launch, instead of one chol_step_kernel launch per step: per step, CTA 0 updates tile (0, 0)
+// and then factors and inverts the next diagonal block (the step's critical path), the other
+// CTAs take the remaining trailing tiles from a per-step queue (an atomic counter, so the load
+// balances itself), and a grid barrier separates the steps. CTAs on CTA 0's SM (its SM id is
+// published before the first step) take no tiles, so that the critical path has the SM to
+// itself. The arithmetic of every tile and block is chol_step_kernel's, in the same order.
+// bar: [0] barrier counter, [1] abort word, [2] CTA 0's SM id, [8 + s] the queue of step s
+// (s < 180; zeroed before the launch).
+__global__ void __launch_bounds__(256) chol_chain_kernel(float* M, float* W, int64_t npad,
+                                                         int64_t kb_from, int* info, int prec,
+                                                         unsigned int* bar, int* err,
+                                                         int num_sms,
+                                                         unsigned long long* trace) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ int claim;
+  const int c = (int)blockIdx.x;
+  unsigned int my_sm;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
+  if (c == 0 && threadIdx.x == 0) bar[2] = my_sm;
+  if (!chol_grid_sync(bar, err)) return;
+  const bool worker = (c != 0) && (*(volatile unsigned int*)(bar + 2) != my_sm);
+  (void)num_sms;
+  int step = 0;
+  for (int64_t kb = kb_from; kb + NB < npad; kb += NB, ++step) {
+    if (*(volatile int*)info != 0) return;   // uniform: read after the same barrier
+    const int nt = (int)((npad - kb - NB) / NB);
+    const int ntiles = nt * (nt + 1) / 2;
+    const bool tr = trace != nullptr && step < 64 && threadIdx.x == 0;
+    if (c == 0) {
+      if (tr) trace[4 * step] = ptx::global_ns();
+      chol_step_tile(M, W, npad, kb, 0, 0, dsm);
+      __syncthreads();   // the updated block (written by this CTA) before it is factored
+      if (tr) trace[4 * step + 1] = ptx::global_ns();
+      potrf_inv_diag_body<float>(M, W, npad, kb + NB, info, prec, dsm);
+      if (tr) trace[4 * step + 2] = ptx::global_ns();
+    } else if (worker) {
+      // tiles 1 .. ntiles - 1 in row-major order of the upper triangle, from the step's queue
+      unsigned int* q = bar + 8 + step;
+      int ti = 0, row_start = 0;
+      for (;;) {
+        if (threadIdx.x == 0) claim = 1 + (int)atomicAdd(q, 1u);
+        __syncthreads();
+        const int t = claim;
+        __syncthreads();
+        if (t >= ntiles) break;
+        while (t >= row_start + (nt - ti)) {
+          row_start += nt - ti;
+          ++ti;
+        }
+        chol_step_tile(M, W, npad, kb, ti, ti + (t - row_start), dsm);
+        __syncthreads();   // shared memory reused by the next tile
+      }
+      if (tr) atomicMax(trace + 4 * step + 3, (unsigned long long)ptx::global_ns());
+    }
+    if (!chol_grid_sync(bar, err)) return;
+  }
 }
 
 // Row blocks K >= kb_from kept their panels transposed below the diagonal (chol_step_kernel):
@@ -1067,7 +1169,10 @@ void launch_set_identity_pad(void* M, bool fp64, int64_t n, int64_t npad, cudaSt
 
 template <typename T>
 void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* Wd, Prec prec,
-                     cudaStream_t s) {
+                     cudaStream_t s, unsigned int* gbar, int* err, int num_sms,
+                     unsigned long long* trace, int chain_per_sm) {
+  // (chain_per_sm 3 measured best at n = 2048: 817 us per factor against 868, 851 and 817 us
+  // for 1, 2 and 4 CTAs per SM and 915 us with one launch per block step)
   if (shift != 0.0) { add_shift_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(M, n, npad, shift); count_launch(); }
   const size_t dsmem = 2 * sizeof(T) * NB * (NB + 1);
   static const bool attr = [dsmem] {   // thread-safe one-time initialisation
@@ -1105,10 +1210,35 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
         static const bool attr3 = [] {
           cudaFuncSetAttribute(chol_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(3 * NB * LDT * sizeof(float)));
+          cudaFuncSetAttribute(chol_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(3 * NB * LDT * sizeof(float)));
           return true;
         }();
         (void)attr3;
         if (kb_from == npad) kb_from = kb;
+        if (gbar != nullptr && num_sms > 1) {
+          // this and every later step in one persistent cooperative launch
+          int per_sm = 0;
+          const size_t cs = 3 * NB * LDT * sizeof(float);
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_chain_kernel, 256, cs) ==
+                  cudaSuccess &&
+              per_sm >= 1) {
+            float* Mf = reinterpret_cast<float*>(M);
+            float* Wf = reinterpret_cast<float*>(Wd);
+            int pr = (int)prec;
+            int64_t kbv = kb;
+            int64_t npv = npad;
+            int nsm = num_sms;
+            void* args[] = {&Mf, &Wf, &npv, &kbv, &info, &pr, &gbar, &err, &nsm, &trace};
+            const int grid = std::max(1, std::min(per_sm, chain_per_sm)) * num_sms;
+            cudaMemsetAsync(gbar + 2, 0, sizeof(unsigned int) * 190, s);   // SM id, queues
+            const cudaError_t e = cudaLaunchCooperativeKernel((const void*)chol_chain_kernel,
+                                                              grid, 256, args, cs, s);
+            count_launch();
+            if (e == cudaSuccess) break;
+            (void)cudaGetLastError();   // not launchable: one launch per step below
+          }
+        }
         chol_step_kernel<<<dim3((unsigned)nt, (unsigned)nt), 256, 3 * NB * LDT * sizeof(float),
                            s>>>(M, Wd, npad, kb, info, (int)prec);
         count_launch();
@@ -1203,8 +1333,12 @@ void launch_d2f(const double* in, float* out, int64_t count, cudaStream_t s) {
   d2f_kernel<<<blocks_for(count, 256), 256, 0, s>>>(in, out, count); count_launch();
 }
 
-template void launch_cholesky<float>(float*, int64_t, int64_t, double, int*, float*, Prec, cudaStream_t);
-template void launch_cholesky<double>(double*, int64_t, int64_t, double, int*, double*, Prec, cudaStream_t);
+template void launch_cholesky<float>(float*, int64_t, int64_t, double, int*, float*, Prec,
+                                     cudaStream_t, unsigned int*, int*, int, unsigned long long*,
+                                     int);
+template void launch_cholesky<double>(double*, int64_t, int64_t, double, int*, double*, Prec,
+                                      cudaStream_t, unsigned int*, int*, int, unsigned long long*,
+                                      int);
 template void launch_round_to<float>(float*, int64_t, Prec, cudaStream_t);
 template void launch_round_to<double>(double*, int64_t, Prec, cudaStream_t);
 template void launch_trtri<float>(const float*, float*, float*, float*, int64_t, bool, cudaStream_t);

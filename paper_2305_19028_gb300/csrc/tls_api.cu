@@ -33,6 +33,8 @@ struct DevBuf {
 
 }  // namespace
 
+constexpr int kBarWords = 320;   // the one-launch solve: [0, 128); the factor chain: [128, 320)
+
 struct tls_ctx {
   int64_t m = 0, n = 0, npad = 0, mpad = 0, nnz = -1;
   int device = 0, num_sms = 0;
@@ -48,7 +50,10 @@ struct tls_ctx {
   int fused_load = 0;      // how the one-launch solve loads tiles of A (tls_set_pcg_fused)
   int fused_pass = 0;      // how its pass holds the tiles (tls_set_pcg_fused)
   int64_t l2_keep = 0;     // bytes of A the one-launch solve keeps resident in L2
-  unsigned int* fbar = nullptr;   // barrier counter and abort word of the one-launch solve
+  unsigned int* fbar = nullptr;   // kBarWords barrier words: [0], [64] the one-launch solve's
+                                  // counter and abort word; from [128] the persistent Cholesky's
+  int chol_chain = 3;             // block steps of the FP32 factor in one persistent launch
+                                  // (up to this many CTAs per SM; 0: one launch per step)
   RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
 
   // problem data (device)
@@ -244,7 +249,7 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
   ctx->sout = alloc_t<double>(ctx, 8);
   ctx->gpart = alloc_t<double>(ctx, 4096);
   ctx->counter = alloc_t<unsigned int>(ctx, 32);   // last-CTA counters; [4..22] PCGTLS step
-  ctx->fbar = alloc_t<unsigned int>(ctx, 96);
+  ctx->fbar = alloc_t<unsigned int>(ctx, kBarWords);
   ctx->derr = alloc_t<int>(ctx, 1);
   ctx->sc = alloc_t<PcgScalars>(ctx, 1);
   ctx->rs = alloc_t<RqiScalars>(ctx, 1);
@@ -255,7 +260,7 @@ tls_status ctx_common_init(tls_ctx* ctx, int64_t m, int64_t n, void* stream) {
     return TLS_ERR_OOM;
   }
   TLS_CK(cudaMemsetAsync(ctx->counter, 0, 32 * sizeof(unsigned int), ctx->stream));
-  TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), ctx->stream));
+  TLS_CK(cudaMemsetAsync(ctx->fbar, 0, kBarWords * sizeof(unsigned int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->sc, 0, sizeof(PcgScalars), ctx->stream));
   TLS_CK(cudaMemsetAsync(ctx->rs, 0, sizeof(RqiScalars), ctx->stream));
@@ -785,7 +790,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   }
   if (herr != 0) {
     TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), st));
-    TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), st));
+    TLS_CK(cudaMemsetAsync(ctx->fbar, 0, kBarWords * sizeof(unsigned int), st));
     set_err(ctx, "a bounded device wait expired (code " + std::to_string(herr) + ")");
     return TLS_ERR_TIMEOUT;
   }
@@ -1083,12 +1088,23 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
                                        static_cast<double*>(Wc), pf, st);
         else
           tls::launch_cholesky<float>(static_cast<float*>(M), n, npad, shift, dinfo,
-                                      static_cast<float*>(Wc), pf, st);
+                                      static_cast<float*>(Wc), pf, st,
+                                      ctx->chol_chain ? ctx->fbar + 128 : nullptr, ctx->derr,
+                                      ctx->num_sms, ctx->trace_on ? ctx->trace : nullptr,
+                                      ctx->chol_chain);
       }
       TLS_CK_LAUNCH("cholesky");
-      int hinfo = 0;
+      int hinfo = 0, herr = 0;
       TLS_CK(cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TLS_CK(cudaMemcpyAsync(&herr, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
       TLS_CK(cudaStreamSynchronize(st));
+      if (herr != 0) {
+        TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), st));
+        TLS_CK(cudaMemsetAsync(ctx->fbar, 0, kBarWords * sizeof(unsigned int), st));
+        set_err(ctx, "a bounded device wait expired in the factor (code " +
+                         std::to_string(herr) + ")");
+        return TLS_ERR_TIMEOUT;
+      }
       read_norms();
       if (hinfo == 0) {
         ok = true;
@@ -1198,7 +1214,7 @@ static tls_status pcgtls_host(tls_ctx* ctx, int nr, double sigma2, const double*
   prof_collect(ctx);
   if (herr != 0) {
     TLS_CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), st));
-    TLS_CK(cudaMemsetAsync(ctx->fbar, 0, 96 * sizeof(unsigned int), st));
+    TLS_CK(cudaMemsetAsync(ctx->fbar, 0, kBarWords * sizeof(unsigned int), st));
     set_err(ctx, "a bounded device wait expired (code " + std::to_string(herr) + ")");
     return TLS_ERR_TIMEOUT;
   }
@@ -1819,6 +1835,12 @@ tls_status tls_profile_get(const tls_ctx* ctx, int cls, int64_t* count, double* 
 tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units) {
   if (!ctx || !units || cls < 0 || cls >= TLS_PROF_NCLASSES) return TLS_ERR_ARG;
   *units = ctx->prof_units[cls];
+  return TLS_OK;
+}
+
+tls_status tls_set_factor_chain(tls_ctx* ctx, int on) {
+  if (!ctx || on < 0 || on > 4) return TLS_ERR_ARG;
+  ctx->chol_chain = on;
   return TLS_OK;
 }
 

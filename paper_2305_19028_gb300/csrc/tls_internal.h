@@ -134,10 +134,18 @@ int gram_tc_error(int* err, cudaStream_t s);
 // Blocked upper Cholesky in place on M (npad x npad, T), with shift added to the first n
 // diagonal entries first; the rows of R are rounded to prec block by block and the inverses
 // of the 64 x 64 diagonal blocks are written to Wd (npad x npad, other entries untouched);
-// info[0] = first failing global pivot + 1 (0: success).
+// info[0] = first failing global pivot + 1 (0: success). gbar (192 words, the first two zero,
+// and zero again afterwards unless a bounded wait expired, which records code 31 in *err; the
+// others are cleared before use): with it, the
+// FP32 block steps whose trailing matrix fits run in one persistent cooperative launch of
+// chain_per_sm x num_sms CTAs instead of one launch per step. trace (optional, 256 zeroed words): per block
+// step s < 64 of that launch, at 4 s: CTA 0's start, its tile done, its diagonal block done,
+// the last tile worker done (global-timer ns).
 template <typename T>
 void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* Wd, Prec prec,
-                     cudaStream_t s);
+                     cudaStream_t s, unsigned int* gbar = nullptr, int* err = nullptr,
+                     int num_sms = 0, unsigned long long* trace = nullptr,
+                     int chain_per_sm = 3);
 // Round the upper triangle of R (T) to prec in place (FP16/BF16); no-op for FP32/FP64.
 template <typename T>
 void launch_round_to(T* R, int64_t npad, Prec prec, cudaStream_t s);

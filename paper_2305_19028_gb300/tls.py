@@ -39,7 +39,8 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_batch_set_selector", "tls_batch_features", "tls_set_pass_variant",
            "tls_set_selector", "tls_features", "tls_pool_enable", "tls_pool_trim",
            "tls_pool_stats", "tls_pool_poison", "tls_set_small_path", "tls_profile_units",
-           "tls_set_pcg_fused", "tls_trace_enable", "tls_trace_get", "tls_set_pcg_l2_keep"]
+           "tls_set_pcg_fused", "tls_trace_enable", "tls_trace_get", "tls_set_pcg_l2_keep",
+           "tls_set_factor_chain"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec", "pcg_solve2", "pcg_solve1"]
@@ -155,6 +156,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_set_pcg_fused": (C.c_int, [v, C.c_int]),
         "tls_trace_enable": (C.c_int, [v, C.c_int]),
         "tls_set_pcg_l2_keep": (C.c_int, [v, i64]),
+        "tls_set_factor_chain": (C.c_int, [v, C.c_int]),
         "tls_trace_get": (C.c_int, [v, C.POINTER(C.c_uint64), C.c_int, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -396,6 +398,12 @@ def tls_profile_units(ctx) -> dict:
 def tls_set_pcg_fused(ctx, mode: int) -> None:
     """0 automatic, 1 one persistent launch per PCGTLS solve, 2 the multi-launch path."""
     _check(load().tls_set_pcg_fused(ctx, int(mode)), ctx)
+
+
+def tls_set_factor_chain(ctx, per_sm: int) -> None:
+    """Block steps of the FP32 factor in one persistent launch of up to per_sm CTAs per SM
+    (default 3), or one launch each (0)."""
+    _check(load().tls_set_factor_chain(ctx, int(per_sm)), ctx)
 
 
 def tls_set_pcg_l2_keep(ctx, nbytes: int) -> None:

@@ -123,6 +123,24 @@ def _rounded_scaled(A, d, u_f):
     return As.astype(np.float64)
 
 
+@pytest.mark.parametrize("m,n", [(800, 130), (5000, 2100)])
+def test_factor_chain_matches_one_launch_per_step(m, n):
+    """The FP32 factor's block steps in one persistent launch give the same factor, bit for bit,
+    as one launch per block step (the same arithmetic in the same order)."""
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=5)
+    out = []
+    for chain in (1, 2, 0):
+        ctx = tls.tls_create_dense(p.A, p.b)
+        try:
+            tls.tls_set_factor_chain(ctx, chain)
+            tls.tls_factor(ctx, "fp16", tls.tls_default_options(u="fp32"))
+            out.append(tls.tls_export_factor(ctx))
+        finally:
+            tls.tls_destroy(ctx)
+    for a_, b_ in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a_), np.asarray(b_))
+
+
 @pytest.mark.parametrize("u_f,u", [("fp16", "fp32"), ("bf16", "fp32"), ("fp32", "fp32"),
                                    ("fp64", "fp64")])
 @pytest.mark.parametrize("m,n", [(300, 64), (777, 130)])
