@@ -1327,6 +1327,97 @@ __global__ void __launch_bounds__(1024) rqi_update_kernel(double* __restrict__ x
   }
 }
 
+// The same update over several CTAs (the FP64 arithmetic of one CTA on this GPU, at 2 lanes
+// per clock per SM, made the single-block form take about 20 us): rqi_dots_kernel forms the
+// CTAs' partials of z^T f and z^T x and the last CTA adds them in CTA order into beta_k;
+// xupd_kernel<T, 2> writes x_{k+1} and ||x_{k+1}||^2.
+template <typename T>
+__global__ void __launch_bounds__(256) rqi_dots_kernel(const double* __restrict__ x,
+                                                       const T* __restrict__ w,
+                                                       const double* __restrict__ f,
+                                                       RqiScalars* rs, int64_t n,
+                                                       double* __restrict__ part) {
+  __shared__ double sh[kWarps * 2];
+  double v[2] = {0.0, 0.0};
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double z = x[j] + (double)w[j];
+    v[0] = fma(z, f[j], v[0]);
+    v[1] = fma(z, x[j], v[1]);
+  }
+  block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = v[0];
+    part[2 * blockIdx.x + 1] = v[1];
+  }
+  if (arrive_last(&rs->counter[1])) {
+    if (threadIdx.x == 0) {
+      double zf = 0.0, zx = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        zf += __ldcg(part + 2 * b);
+        zx += __ldcg(part + 2 * b + 1);
+      }
+      rs->zf = zf;
+      rs->zx = zx;
+      rs->betak = (zf - rs->g) / (zx + 1.0);
+      rs->counter[1] = 0u;
+    }
+  }
+}
+
+// x updates with ||x||^2 over several CTAs (partials added in CTA order by the last CTA):
+// MODE 0: x = w (the LS start); 1: x = x + sigma^2 u (the inverse-iteration step);
+// 2: x = x + w + beta_k u (the RQI update). Any T for w and u.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) xupd_kernel(double* __restrict__ x,
+                                                   const T* __restrict__ w,
+                                                   const T* __restrict__ u, RqiScalars* rs,
+                                                   int64_t n, double* __restrict__ part) {
+  __shared__ double sh[kWarps];
+  const double c = (MODE == 1) ? rs->sigma2 : (MODE == 2 ? rs->betak : 0.0);
+  double xx[1] = {0.0};
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double xn;
+    if constexpr (MODE == 0) xn = (double)w[j];
+    else if constexpr (MODE == 1) xn = fma(c, (double)u[j], x[j]);
+    else xn = fma(c, (double)u[j], x[j] + (double)w[j]);
+    x[j] = xn;
+    xx[0] = fma(xn, xn, xx[0]);
+  }
+  block_sum<1>(xx, sh);
+  if (threadIdx.x == 0) part[64 + blockIdx.x] = xx[0];
+  if (arrive_last(&rs->counter[2])) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + 64 + b);
+      rs->xx = t;
+      rs->counter[2] = 0u;
+    }
+  }
+}
+
+// ||x||^2 over several CTAs (same partial scheme; x read only)
+__global__ void __launch_bounds__(256) xx_multi_kernel(const double* __restrict__ x,
+                                                       RqiScalars* rs, int64_t n,
+                                                       double* __restrict__ part) {
+  __shared__ double sh[kWarps];
+  double xx[1] = {0.0};
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    xx[0] = fma(x[j], x[j], xx[0]);
+  block_sum<1>(xx, sh);
+  if (threadIdx.x == 0) part[64 + blockIdx.x] = xx[0];
+  if (arrive_last(&rs->counter[2])) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + 64 + b);
+      rs->xx = t;
+      rs->counter[2] = 0u;
+    }
+  }
+}
+
 // x = x + sigma2 * u (Alg. 2, the inverse-iteration step before the loop)
 template <typename T>
 __global__ void __launch_bounds__(1024) inverse_step_kernel(double* __restrict__ x,
@@ -1857,22 +1948,45 @@ void launch_resid_reduce(const double* part, int P, int64_t npad, const double* 
 
 template <typename T>
 void launch_rqi_update(double* x, const T* w, const T* u, const double* f, RqiScalars* rs,
-                       int64_t n, cudaStream_t s) {
-  rqi_update_kernel<T><<<1, 1024, 0, s>>>(x, w, u, f, rs, n); count_launch();
+                       int64_t n, cudaStream_t s, double* part) {
+  if (part == nullptr) {
+    rqi_update_kernel<T><<<1, 1024, 0, s>>>(x, w, u, f, rs, n); count_launch();
+    return;
+  }
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(32, (n + 255) / 256));
+  rqi_dots_kernel<T><<<grid, 256, 0, s>>>(x, w, f, rs, n, part); count_launch();
+  xupd_kernel<T, 2><<<grid, 256, 0, s>>>(x, w, u, rs, n, part); count_launch();
 }
 
 template <typename T>
-void launch_inverse_step(double* x, const T* u, RqiScalars* rs, int64_t n, cudaStream_t s) {
-  inverse_step_kernel<T><<<1, 1024, 0, s>>>(x, u, rs, n); count_launch();
+void launch_inverse_step(double* x, const T* u, RqiScalars* rs, int64_t n, cudaStream_t s,
+                         double* part) {
+  if (part == nullptr) {
+    inverse_step_kernel<T><<<1, 1024, 0, s>>>(x, u, rs, n); count_launch();
+    return;
+  }
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(32, (n + 255) / 256));
+  xupd_kernel<T, 1><<<grid, 256, 0, s>>>(x, u, u, rs, n, part); count_launch();
 }
 
 template <typename T>
-void launch_copy_to_x(double* x, const T* w, RqiScalars* rs, int64_t n, cudaStream_t s) {
-  copy_to_x_kernel<T><<<1, 1024, 0, s>>>(x, w, rs, n); count_launch();
+void launch_copy_to_x(double* x, const T* w, RqiScalars* rs, int64_t n, cudaStream_t s,
+                      double* part) {
+  if (part == nullptr) {
+    copy_to_x_kernel<T><<<1, 1024, 0, s>>>(x, w, rs, n); count_launch();
+    return;
+  }
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(32, (n + 255) / 256));
+  xupd_kernel<T, 0><<<grid, 256, 0, s>>>(x, w, w, rs, n, part); count_launch();
 }
 
-void launch_xx(const double* x, RqiScalars* rs, int64_t n, cudaStream_t s) {
-  xx_kernel<<<1, 1024, 0, s>>>(x, rs, n); count_launch();
+void launch_xx(const double* x, RqiScalars* rs, int64_t n, cudaStream_t s, double* part) {
+  if (part == nullptr) {
+    xx_kernel<<<1, 1024, 0, s>>>(x, rs, n); count_launch();
+    return;
+  }
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(32, (n + 255) / 256));
+  xx_multi_kernel<<<grid, 256, 0, s>>>(x, rs, n, part); count_launch();
 }
 
 template <typename T>
@@ -1901,9 +2015,11 @@ void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaS
   template void launch_pcg_update_R<T>(const T*, T*, T*, const T*, PcgScalars*, int,           \
                                        int64_t, cudaStream_t);                                 \
   template void launch_rqi_update<T>(double*, const T*, const T*, const double*, RqiScalars*,  \
-                                     int64_t, cudaStream_t);                                   \
-  template void launch_inverse_step<T>(double*, const T*, RqiScalars*, int64_t, cudaStream_t); \
-  template void launch_copy_to_x<T>(double*, const T*, RqiScalars*, int64_t, cudaStream_t);    \
+                                     int64_t, cudaStream_t, double*);                          \
+  template void launch_inverse_step<T>(double*, const T*, RqiScalars*, int64_t, cudaStream_t,  \
+                                       double*);                                               \
+  template void launch_copy_to_x<T>(double*, const T*, RqiScalars*, int64_t, cudaStream_t,     \
+                                    double*);                                                  \
   template void launch_vec_convert<T>(const double*, T*, int64_t, int64_t, cudaStream_t);
 
 TLS_INST(float)

@@ -665,14 +665,14 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   TLS_CK(cudaEventRecord(ctx->ev0, st));
   // Alg. 2 line 1: LS start. Residual at x = 0 gives f = -A^T b; PCG with sigma^2 = 0.
   TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * ctx->npad, st));
-  tls::launch_xx(ctx->x, ctx->rs, ctx->n, st);
+  tls::launch_xx(ctx->x, ctx->rs, ctx->n, st, ctx->gpart + 2048);
   tls_status stt = residual_pass(ctx);
   if (stt != TLS_OK) return stt;
   stt = run_pcg<T>(ctx, 1, ctx->f, -1.0, nullptr, 0.0, std::max(1, o.ls_iters), 0.0, modeA);
   if (stt != TLS_OK) return stt;
   {
     Prof pr(ctx, TLS_PROF_VEC);
-    tls::launch_copy_to_x<T>(ctx->x, v.w, ctx->rs, ctx->n, st);
+    tls::launch_copy_to_x<T>(ctx->x, v.w, ctx->rs, ctx->n, st, ctx->gpart + 2048);
   }
   // lines 2-5: r_0, sigma_0^2, u_0 = (R^T R)^{-1} x_0, x_1 = x_0 + sigma_0^2 u_0
   stt = residual_pass(ctx);
@@ -681,7 +681,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   if (stt != TLS_OK) return stt;
   {
     Prof pr(ctx, TLS_PROF_VEC);
-    tls::launch_inverse_step<T>(ctx->x, v.q, ctx->rs, ctx->n, st);
+    tls::launch_inverse_step<T>(ctx->x, v.q, ctx->rs, ctx->n, st, ctx->gpart + 2048);
   }
   TLS_CK_LAUNCH("inverse step");
 
@@ -771,7 +771,8 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     if (stt != TLS_OK) return stt;
     {
       Prof pr(ctx, TLS_PROF_VEC);
-      tls::launch_rqi_update<T>(ctx->x, v.w, v.w + ctx->npad, ctx->f, ctx->rs, ctx->n, st);
+      tls::launch_rqi_update<T>(ctx->x, v.w, v.w + ctx->npad, ctx->f, ctx->rs, ctx->n, st,
+                                ctx->gpart + 2048);
     }
     TLS_CK_LAUNCH("rqi update");
   }
@@ -961,6 +962,8 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     set_err(ctx, "device allocation failed");
     return TLS_ERR_OOM;
   }
+  // (the completion counters of the norm kernels below start at zero)
+  TLS_CK(cudaMemsetAsync(dnorm, 0, 2 * sizeof(RqiScalars), st));
   const bool want32 = ctx->u == Prec::FP32;
   if (!ctx->colnorm_done || (want32 && !ctx->a32_done)) {
     Prof pr(ctx, TLS_PROF_SCALE);
@@ -977,8 +980,8 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   // ||A||_F^2 = sum of d_j^2 and ||b||^2 on the device; read back with the factor's first
   // synchronisation (no extra host round trip)
   TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * npad, st));
-  tls::launch_xx(ctx->d, dnorm, n, st);
-  tls::launch_xx(ctx->b, dnorm + 1, m, st);
+  tls::launch_xx(ctx->d, dnorm, n, st, ctx->gpart + 2048);
+  tls::launch_xx(ctx->b, dnorm + 1, m, st, ctx->gpart + 2048);
   TLS_CK(cudaMemcpyAsync(ctx->h_norm, dnorm, 2 * sizeof(RqiScalars), cudaMemcpyDeviceToHost, st));
   bool norms_read = false;
   auto read_norms = [&]() {
@@ -1913,7 +1916,7 @@ tls_status tls_residual(tls_ctx* ctx, const double* x_host, double* f_host, doub
   cudaStream_t st = ctx->stream;
   TLS_CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * ctx->npad, st));
   TLS_CK(cudaMemcpyAsync(ctx->x, x_host, sizeof(double) * ctx->n, cudaMemcpyHostToDevice, st));
-  tls::launch_xx(ctx->x, ctx->rs, ctx->n, st);
+  tls::launch_xx(ctx->x, ctx->rs, ctx->n, st, ctx->gpart + 2048);
   tls_status s = residual_pass(ctx);
   if (s != TLS_OK) return s;
   TLS_CK(cudaMemcpyAsync(ctx->h_rs, ctx->rs, sizeof(RqiScalars), cudaMemcpyDeviceToHost, st));

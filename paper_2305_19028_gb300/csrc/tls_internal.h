@@ -257,17 +257,21 @@ void launch_resid_reduce(const double* part, int P, int64_t npad, const double* 
 // x_{k+1} = z + beta_k u with z = x + w (Alg. 2), xx = ||x_{k+1}||^2.
 template <typename T>
 void launch_rqi_update(double* x, const T* w, const T* u, const double* f, RqiScalars* rs,
-                       int64_t n, cudaStream_t s);
+                       int64_t n, cudaStream_t s, double* part = nullptr);
 // x = x + sigma2 * u (Alg. 2 line 5), xx updated.
 template <typename T>
-void launch_inverse_step(double* x, const T* u, RqiScalars* rs, int64_t n, cudaStream_t s);
+void launch_inverse_step(double* x, const T* u, RqiScalars* rs, int64_t n, cudaStream_t s,
+                         double* part = nullptr);
 // x = (double) w, xx updated.
 template <typename T>
-void launch_copy_to_x(double* x, const T* w, RqiScalars* rs, int64_t n, cudaStream_t s);
+void launch_copy_to_x(double* x, const T* w, RqiScalars* rs, int64_t n, cudaStream_t s,
+                      double* part = nullptr);
 // Down-convert an FP64 vector (n) to T into a buffer of npad (zero padded).
 template <typename T>
 void launch_vec_convert(const double* in, T* out, int64_t n, int64_t npad, cudaStream_t s);
-void launch_xx(const double* x, RqiScalars* rs, int64_t n, cudaStream_t s);
+// (part: optional scratch of 96 doubles; with it these x kernels run on several CTAs and add
+// their partials in CTA order)
+void launch_xx(const double* x, RqiScalars* rs, int64_t n, cudaStream_t s, double* part = nullptr);
 
 // ---------------------------------------------------------------------------------------
 // Condition estimates (k_cond.cu)
