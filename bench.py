@@ -1153,8 +1153,9 @@ def main():
                     help="batch: let the trained selector network pick u_f per problem")
     args = ap.parse_args()
     if args.steps is None:
+        # (a timed region of at least half a second: three or more 200 ms clock samples)
         args.steps = (10 if args.impl == "reference" or args.workload == "batch"
-                      else 1000 if args.workload == "c1" else 100)
+                      else 1500 if args.workload == "c1" else 150)
     _set_size(args.m, args.n)
     ws, rank, local = _dist()
     if args.impl == "reference":

@@ -86,7 +86,7 @@ typedef struct {
   double cg_tol;
   int cg_max;
   int psi_rule_ge;     /* 1: stop on psi_k >= psi_{k-1} (the rule of Sec. 4.2)                 */
-  int ls_iters;        /* PCG steps (sigma^2 = 0) that produce the LS start x_0 (default 8)    */
+  int ls_iters;        /* PCG steps (sigma^2 = 0) that produce the LS start x_0 (default 6)    */
   int max_shifts;      /* Cholesky retries with H + s I, s = 2^-10 * 4^i before escalating u_f */
   int gram_simt;       /* 1: form H with the CUDA-core kernel even for FP16/BF16 (default 0:   */
                        /* tensor cores, tcgen05)                                             */

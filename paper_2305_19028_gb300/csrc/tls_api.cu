@@ -1402,7 +1402,7 @@ void tls_default_options(tls_options* opt) {
   opt->cg_tol = 1e-6;
   opt->cg_max = 50;
   opt->psi_rule_ge = 0;
-  opt->ls_iters = 8;
+  opt->ls_iters = 6;
   opt->max_shifts = 3;
   opt->gram_simt = 0;
   opt->shift_first = 1;
