@@ -133,7 +133,7 @@ tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode);
  */
 tls_status tls_set_pcg_l2_keep(tls_ctx* ctx, int64_t bytes);
 /*
- * tls_set_factor_chain -- c = 1 .. 4 (default 3): the block steps of an FP32 Cholesky factor
+ * tls_set_factor_chain -- c = 1 .. 4 (default 2): the block steps of an FP32 Cholesky factor
  * whose trailing matrix fits run in one persistent cooperative launch of up to c CTAs per SM (a
  * grid barrier between steps); 0: one launch per block step. The arithmetic is the same in
  * all. Kept until changed.

@@ -37,11 +37,14 @@ struct Scratch {
 // nb (a multiple of kPB, at most kB): the block's rows and columns from nb on are the identity
 // padding of an order-n problem (identity on the diagonal, zero elsewhere), so only the leading
 // nb x nb part is factored; G keeps the padding as it is and S receives it.
+// Gin, ldin (optional): read the block from there instead of from G (e.g. a copy in shared memory
+// that the caller has just updated); the rows of R still go to G. Gin is read before the first
+// barrier, so it may share storage with S.
 // FP64 (sizeof(T) == 8; FP64 arithmetic runs at a 64th of the FP32 rate): R11 is formed once per
 // step by one warp and shared, rather than by every column thread.
 template <typename T, typename Round>
 __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Round rnd,
-                           int nb = kB) {
+                           int nb = kB, const T* Gin = nullptr, int64_t ldin = 0) {
   const int tid = threadIdx.x;
   int tI = kTT, tJ = 0;
   if (tid < kTT * (kTT + 1) / 2) {
@@ -52,11 +55,13 @@ __device__ int factor_block(T* G, int64_t ld, T* S, int lds, Scratch<T>& sc, Rou
   }
   // (entries below the diagonal inside the diagonal tiles ride along and are never published)
   T v[4][4];
+  const T* src = Gin ? Gin : G;
+  const int64_t lsrc = Gin ? ldin : ld;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      v[a][c] = (tI < kTT) ? G[(int64_t)(4 * tI + a) * ld + 4 * tJ + c] : T(0);
+      v[a][c] = (tI < kTT) ? src[(int64_t)(4 * tI + a) * lsrc + 4 * tJ + c] : T(0);
   if (tid == 0) sc.bad = 0;
   if (nb < kB)
     for (int e = tid; e < kB * kB; e += blockDim.x) {

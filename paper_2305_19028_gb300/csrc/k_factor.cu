@@ -558,6 +558,7 @@ __global__ void set_identity_pad_kernel(void* M, int fp64, int64_t n, int64_t np
 // Cholesky pieces (upper, H = R^T R), block size 64.
 // ---------------------------------------------------------------------------------------
 constexpr int NB = 64;
+constexpr int LDT = 68;   // row stride (floats) of the 64 x 64 FP32 tiles staged in shared memory
 
 template <typename T>
 __global__ void add_shift_kernel(T* M, int64_t n, int64_t npad, double shift) {
@@ -643,20 +644,27 @@ __device__ __forceinline__ void inv_double_level_f64(double (*S)[NB + 1], double
 
 // nb: the leading non-padding order of the block (a multiple of 8; NB unless this is the last
 // block of a problem whose n is not a multiple of 64); used by the FP64 factor only.
+// Sbuf, Xbuf: NB x (NB + 1) each in shared memory. Gin, ldin (optional): the block's input, read
+// before the factor's first barrier (Xbuf may hold it). Wcopy (optional, FP32): the inverse also
+// goes there, row stride LDT, for the caller's next panel products. Returns the breakdown
+// (non-zero: the first bad pivot + 1, after which *info is set and nothing else is written).
 template <typename T>
-__device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, int64_t kb,
-                                                    int* info, int prec, unsigned char* dsm,
-                                                    int nb = NB) {
-  T (*S)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm);
-  T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+__device__ __forceinline__ int potrf_inv_diag_core(T* M, T* W, int64_t npad, int64_t kb,
+                                                   int* info, int prec, T* Sbuf, T* Xbuf,
+                                                   const T* Gin, int64_t ldin, T* Wcopy,
+                                                   int nb, unsigned long long* stamp = nullptr) {
+  T (*S)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(Sbuf);
+  T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(Xbuf);
   const int tid = threadIdx.x;
   __shared__ chol64::Scratch<T> sc;
   if constexpr (sizeof(T) != 8) nb = NB;
   const int bad = chol64::factor_block<T>(M + kb * npad + kb, npad, &S[0][0], NB + 1, sc,
-                                          [prec](T v) { return round_prec(v, prec); }, nb);
+                                          [prec](T v) { return round_prec(v, prec); }, nb,
+                                          Gin, ldin);
+  if (stamp != nullptr && tid == 0) *stamp = ptx::global_ns();
   if (bad) {
     if (tid == 0) atomicCAS(info, 0, (int)kb + bad);
-    return;   // uniform: every thread saw the same pivots
+    return bad;   // uniform: every thread saw the same pivots
   }
   for (int e = tid; e < NB * NB; e += 256) X[e / NB][e % NB] = T(0);
   __syncthreads();
@@ -682,7 +690,7 @@ __device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, in
       const int r = e / NB, c = e % NB;
       W[(kb + r) * npad + kb + c] = X[r][c];
     }
-    return;
+    return 0;
   }
   // inverse by doubling: the eight 8 x 8 diagonal blocks by substitution (thread: one column,
   // chains of at most 8), then for s = 8, 16, 32 every pair of s-blocks A, B gets
@@ -703,7 +711,18 @@ __device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, in
   for (int e = tid; e < NB * NB; e += 256) {
     const int r = e / NB, c = e % NB;
     W[(kb + r) * npad + kb + c] = X[r][c];
+    if (Wcopy) Wcopy[r * LDT + c] = X[r][c];
   }
+  return 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void potrf_inv_diag_body(T* M, T* W, int64_t npad, int64_t kb,
+                                                    int* info, int prec, unsigned char* dsm,
+                                                    int nb = NB) {
+  T* S = reinterpret_cast<T*>(dsm);
+  (void)potrf_inv_diag_core<T>(M, W, npad, kb, info, prec, S, S + NB * (NB + 1), nullptr, 0,
+                               nullptr, nb);
 }
 
 template <typename T>
@@ -743,7 +762,6 @@ __global__ void __launch_bounds__(256) chol_update_next_kernel(float* M, float* 
 // acc += As^T Bs over k < 64 for the 4 x 4 outputs of this thread (rows 4 ty .. +3, columns
 // 4 tx .. +3; tx = tid % 16, ty = tid / 16; 256 threads); As[k][i], Bs[k][j] in shared memory
 // with row stride LDT (float4 reads).
-constexpr int LDT = 68;
 __device__ __forceinline__ void tile_atb64(const float* As, const float* Bs, float (&acc)[4][4]) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll 8
@@ -779,16 +797,16 @@ __device__ __forceinline__ void chol_step_tile(float* M, const float* W, int64_t
   const float* Wsrc = W + kb * npad + kb;
   const float* Ri = M + kb * npad + k2 + (int64_t)ti * NB;
   const float* Rj = M + kb * npad + k2 + (int64_t)tj * NB;
-  for (int e = tid; e < NB * NB / 4; e += 256) {
-    const int r = e >> 4, c = (e & 15) * 4;
-    *reinterpret_cast<float4*>(Wk + r * LDT + c) =
-        *reinterpret_cast<const float4*>(Wsrc + (int64_t)r * npad + c);
-    *reinterpret_cast<float4*>(Hi + r * LDT + c) =
-        *reinterpret_cast<const float4*>(Ri + (int64_t)r * npad + c);
-    if (!diag)
-      *reinterpret_cast<float4*>(Hj + r * LDT + c) =
-          *reinterpret_cast<const float4*>(Rj + (int64_t)r * npad + c);
+  // every copy in flight before the first wait (one round trip, not one per row group)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = tid + 256 * i, r = e >> 4, c = (e & 15) * 4;
+    ptx::cp_async16(Wk + r * LDT + c, Wsrc + (int64_t)r * npad + c);
+    ptx::cp_async16(Hi + r * LDT + c, Ri + (int64_t)r * npad + c);
+    if (!diag) ptx::cp_async16(Hj + r * LDT + c, Rj + (int64_t)r * npad + c);
   }
+  ptx::cp_async_commit();
+  ptx::cp_async_wait_all();
   __syncthreads();
   float pi[4][4], pj[4][4];
 #pragma unroll
@@ -798,6 +816,13 @@ __device__ __forceinline__ void chol_step_tile(float* M, const float* W, int64_t
   tile_atb64(Wk, Hi, pi);
   if (!diag) tile_atb64(Wk, Hj, pj);
   __syncthreads();
+  // this thread's 4 x 4 entries of the tile into the W_KK area (read by no one from here on), in
+  // flight during the second product (no other CTA writes the tile during the step)
+  float* C = M + (k2 + (int64_t)ti * NB) * npad + k2 + (int64_t)tj * NB;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+    ptx::cp_async16(Wk + (4 * ty + p) * LDT + 4 * tx, C + (int64_t)(4 * ty + p) * npad + 4 * tx);
+  ptx::cp_async_commit();
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
     *reinterpret_cast<float4*>(Hi + (4 * ty + p) * LDT + 4 * tx) =
@@ -821,19 +846,25 @@ __device__ __forceinline__ void chol_step_tile(float* M, const float* W, int64_t
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
   tile_atb64(Hi, diag ? Hi : Hj, acc);
-  float* C = M + (k2 + (int64_t)ti * NB) * npad + k2 + (int64_t)tj * NB;
+  ptx::cp_async_wait_all();   // this thread's own copies of the tile
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int a = 4 * ty + p, b = 4 * tx + q;
-      if (diag && a > b) continue;
-      float* cp = C + (int64_t)a * npad + b;
-      *cp = -acc[p][q] + *cp;
+  for (int p = 0; p < 4; ++p) {
+    const float4 cv = *reinterpret_cast<const float4*>(Wk + (4 * ty + p) * LDT + 4 * tx);
+    const float4 o = make_float4(-acc[p][0] + cv.x, -acc[p][1] + cv.y, -acc[p][2] + cv.z,
+                                 -acc[p][3] + cv.w);
+    float* cp = C + (int64_t)(4 * ty + p) * npad + 4 * tx;
+    if (!diag || 4 * ty + p <= 4 * tx) {
+      *reinterpret_cast<float4*>(cp) = o;   // the whole row segment is on or above the diagonal
+    } else if (4 * ty + p <= 4 * tx + 3) {
+      const int a = 4 * ty + p;
+      if (a <= 4 * tx + 1) cp[1] = o.y;
+      if (a <= 4 * tx + 2) cp[2] = o.z;
+      cp[3] = o.w;
     }
+  }
 }
 
-__global__ void __launch_bounds__(256) chol_step_kernel(float* M, float* W, int64_t npad,
+__global__ void __launch_bounds__(256, 3) chol_step_kernel(float* M, float* W, int64_t npad,
                                                         int64_t kb, int* info, int prec) {
   if (*(volatile int*)info != 0) return;
   const int ti = blockIdx.y, tj = blockIdx.x;
@@ -843,6 +874,71 @@ __global__ void __launch_bounds__(256) chol_step_kernel(float* M, float* W, int6
   if (ti != 0 || tj != 0) return;
   __syncthreads();   // the updated block (written by this CTA) before it is factored
   potrf_inv_diag_body<float>(M, W, npad, kb + NB, info, prec, dsm);
+}
+
+// CTA 0's part of block step kb in the persistent chain: tile (0, 0) of the trailing matrix
+// (the next diagonal block), then that block's factor and inverse. The arithmetic and its order
+// are chol_step_tile's and potrf_inv_diag_body's; what differs is where the operands live:
+// W_KK stays in shared memory from the previous step's inverse (read from W on the first step
+// only), and the updated block goes to the factor through shared memory rather than through M.
+// Shared memory (floats): [0, NB LDT) W_KK; [NB LDT, 2 NB LDT) the panel block P, then the
+// updated block, then the inverse X; from 2 NB LDT the factor's S. Returns the factor's
+// breakdown code (0: none). tr, tf (optional): the times the update and the factor were done.
+__device__ __forceinline__ int chol_cta0_step(float* M, float* W, int64_t npad, int64_t kb,
+                                              int* info, int prec, unsigned char* dsm,
+                                              bool load_w, unsigned long long* tr,
+                                              unsigned long long* tf) {
+  const int64_t k2 = kb + NB;
+  float* Wk = reinterpret_cast<float*>(dsm);
+  float* R2 = Wk + NB * LDT;
+  float* R3 = R2 + NB * LDT;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float* Hsrc = M + kb * npad + k2;
+  const float* C = M + k2 * npad + k2;
+  // the panel block into R2, this thread's 4 x 4 entries of the block into R3 (free until the
+  // factor), W_KK on the first step
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = tid + 256 * i, r = e >> 4, c = (e & 15) * 4;
+    if (load_w) ptx::cp_async16(Wk + r * LDT + c, W + (kb + r) * npad + kb + c);
+    ptx::cp_async16(R2 + r * LDT + c, Hsrc + (int64_t)r * npad + c);
+    ptx::cp_async16(R3 + (4 * ty + i) * LDT + 4 * tx, C + (int64_t)(4 * ty + i) * npad + 4 * tx);
+  }
+  ptx::cp_async_commit();
+  ptx::cp_async_wait_all();
+  __syncthreads();
+  float pi[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pi[p][q] = 0.f;
+  tile_atb64(Wk, R2, pi);
+  __syncthreads();
+  float* low = M + k2 * npad + kb;   // P transposed below the diagonal (mirror_panels_kernel)
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    *reinterpret_cast<float4*>(R2 + (4 * ty + p) * LDT + 4 * tx) =
+        make_float4(pi[p][0], pi[p][1], pi[p][2], pi[p][3]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) low[(int64_t)(4 * tx + q) * npad + 4 * ty + p] = pi[p][q];
+  }
+  __syncthreads();
+  float acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+  tile_atb64(R2, R2, acc);
+  __syncthreads();   // every read of P done before the updated block replaces it
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float4 cv = *reinterpret_cast<const float4*>(R3 + (4 * ty + p) * LDT + 4 * tx);
+    *reinterpret_cast<float4*>(R2 + (4 * ty + p) * LDT + 4 * tx) =
+        make_float4(-acc[p][0] + cv.x, -acc[p][1] + cv.y, -acc[p][2] + cv.z, -acc[p][3] + cv.w);
+  }
+  __syncthreads();
+  if (tr != nullptr && tid == 0) *tr = ptx::global_ns();
+  return potrf_inv_diag_core<float>(M, W, npad, k2, info, prec, R3, R2, R2, LDT, Wk, NB, tf);
 }
 
 // Grid barrier of a cooperative launch on bar[0] (bar[1]: abort word): thread 0 of each CTA
@@ -882,56 +978,76 @@ __device__ __forceinline__ bool chol_grid_sync(unsigned int* bar, int* err) {
 
 // The block steps kb_from, kb_from + NB, ... of the FP32 factor in one persistent cooperative
 // launch, instead of one chol_step_kernel launch per step: per step, CTA 0 updates tile (0, 0)
-// and then factors and inverts the next diagonal block (the step's critical path), the other
-// CTAs take the remaining trailing tiles from a per-step queue (an atomic counter, so the load
-// balances itself), and a grid barrier separates the steps. CTAs on CTA 0's SM (its SM id is
+// and then factors and inverts the next diagonal block (the step's critical path;
+// chol_cta0_step), the other CTAs take the remaining trailing tiles from a per-step queue (an
+// atomic counter, so the load balances itself; each CTA claims its next tile while it works on
+// the current one), and a grid barrier separates the steps. CTAs on CTA 0's SM (its SM id is
 // published before the first step) take no tiles, so that the critical path has the SM to
-// itself. The arithmetic of every tile and block is chol_step_kernel's, in the same order.
-// bar: [0] barrier counter, [1] abort word, [2] CTA 0's SM id, [8 + s] the queue of step s
-// (s < 180; zeroed before the launch).
-__global__ void __launch_bounds__(256) chol_chain_kernel(float* M, float* W, int64_t npad,
+// itself. Every CTA also learns its rank among the CTAs of its SM; a step with few tiles is
+// left to the lower ranks, so that its tiles spread over the SMs instead of sharing some. The
+// arithmetic of every tile and block is chol_step_kernel's, in the same order.
+// bar: [0] barrier counter, [1] abort word, [2] CTA 0's SM id (one 128-byte line), [32 + s] the
+// queue of step s (s < 160), [192 + i] the CTA count of SM i (i < 256); all zeroed before the
+// launch.
+// trace (optional): per step s < 64, [4 s] its start, [4 s + 1] CTA 0's update done, [4 s + 2]
+// its factor and inverse done, [4 s + 3] the last worker done; [256 + 4 s] CTA 0's factor done.
+__global__ void __launch_bounds__(256, 3) chol_chain_kernel(float* M, float* W, int64_t npad,
                                                          int64_t kb_from, int* info, int prec,
                                                          unsigned int* bar, int* err,
                                                          int num_sms,
                                                          unsigned long long* trace) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ int claim;
+  __shared__ int claim, sm_rank;
   const int c = (int)blockIdx.x;
   unsigned int my_sm;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
-  if (c == 0 && threadIdx.x == 0) bar[2] = my_sm;
+  if (threadIdx.x == 0) {
+    if (c == 0) bar[2] = my_sm;
+    sm_rank = (my_sm < 256u) ? (int)atomicAdd(bar + 192 + my_sm, 1u) : 0;
+  }
   if (!chol_grid_sync(bar, err)) return;
   const bool worker = (c != 0) && (*(volatile unsigned int*)(bar + 2) != my_sm);
-  (void)num_sms;
+  const int rank = sm_rank;
+  const int worker_sms = max(1, num_sms - 1);
+  // CTA 0 is the only writer of *info during the launch: it reads the flag once and then keeps
+  // its own breakdown code; the others read the flag after every barrier
+  int bad0 = (c == 0) ? *(volatile int*)info : 0;
   int step = 0;
   for (int64_t kb = kb_from; kb + NB < npad; kb += NB, ++step) {
-    if (*(volatile int*)info != 0) return;   // uniform: read after the same barrier
+    if (c == 0 ? bad0 != 0 : *(volatile int*)info != 0) return;   // uniform across the grid
+    if (step >= 160) {   // more steps than queues (not reached: the chain starts at <= 34 tiles)
+      if (c == 0 && threadIdx.x == 0) atomicCAS(err, 0, 32);
+      return;
+    }
     const int nt = (int)((npad - kb - NB) / NB);
     const int ntiles = nt * (nt + 1) / 2;
     const bool tr = trace != nullptr && step < 64 && threadIdx.x == 0;
     if (c == 0) {
       if (tr) trace[4 * step] = ptx::global_ns();
-      chol_step_tile(M, W, npad, kb, 0, 0, dsm);
-      __syncthreads();   // the updated block (written by this CTA) before it is factored
-      if (tr) trace[4 * step + 1] = ptx::global_ns();
-      potrf_inv_diag_body<float>(M, W, npad, kb + NB, info, prec, dsm);
+      const bool trs = trace != nullptr && step < 64;
+      bad0 = chol_cta0_step(M, W, npad, kb, info, prec, dsm, step == 0,
+                            trs ? trace + 4 * step + 1 : nullptr,
+                            trs ? trace + 256 + 4 * step : nullptr);
       if (tr) trace[4 * step + 2] = ptx::global_ns();
-    } else if (worker) {
+    } else if (worker && rank < (ntiles - 1 + worker_sms - 1) / worker_sms) {
       // tiles 1 .. ntiles - 1 in row-major order of the upper triangle, from the step's queue
-      unsigned int* q = bar + 8 + step;
+      unsigned int* q = bar + 32 + step;
       int ti = 0, row_start = 0;
-      for (;;) {
-        if (threadIdx.x == 0) claim = 1 + (int)atomicAdd(q, 1u);
-        __syncthreads();
-        const int t = claim;
-        __syncthreads();
-        if (t >= ntiles) break;
+      if (threadIdx.x == 0) claim = 1 + (int)atomicAdd(q, 1u);
+      __syncthreads();
+      int t = claim;
+      while (t < ntiles) {   // t is the same in every thread
+        unsigned int nxt = 0u;
+        if (threadIdx.x == 0) nxt = atomicAdd(q, 1u);   // in flight during this tile
         while (t >= row_start + (nt - ti)) {
           row_start += nt - ti;
           ++ti;
         }
         chol_step_tile(M, W, npad, kb, ti, ti + (t - row_start), dsm);
-        __syncthreads();   // shared memory reused by the next tile
+        // (the tile's own barriers come after every thread's read of claim)
+        if (threadIdx.x == 0) claim = 1 + (int)nxt;
+        __syncthreads();   // claim published; shared memory reused by the next tile
+        t = claim;
       }
       if (tr) atomicMax(trace + 4 * step + 3, (unsigned long long)ptx::global_ns());
     }
@@ -1171,8 +1287,8 @@ template <typename T>
 void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* Wd, Prec prec,
                      cudaStream_t s, unsigned int* gbar, int* err, int num_sms,
                      unsigned long long* trace, int chain_per_sm) {
-  // (chain_per_sm 3 measured best at n = 2048: 817 us per factor against 868, 851 and 817 us
-  // for 1, 2 and 4 CTAs per SM and 915 us with one launch per block step)
+  // (chain_per_sm 2 measured best at n = 2048: 756 us per factor against 807 us for 3 or 4
+  // CTAs per SM and 838 us with one launch per block step)
   if (shift != 0.0) { add_shift_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(M, n, npad, shift); count_launch(); }
   const size_t dsmem = 2 * sizeof(T) * NB * (NB + 1);
   static const bool attr = [dsmem] {   // thread-safe one-time initialisation
@@ -1231,7 +1347,7 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
             int nsm = num_sms;
             void* args[] = {&Mf, &Wf, &npv, &kbv, &info, &pr, &gbar, &err, &nsm, &trace};
             const int grid = std::max(1, std::min(per_sm, chain_per_sm)) * num_sms;
-            cudaMemsetAsync(gbar + 2, 0, sizeof(unsigned int) * 190, s);   // SM id, queues
+            cudaMemsetAsync(gbar + 2, 0, sizeof(unsigned int) * 446, s);   // SM id, queues, ranks
             const cudaError_t e = cudaLaunchCooperativeKernel((const void*)chol_chain_kernel,
                                                               grid, 256, args, cs, s);
             count_launch();

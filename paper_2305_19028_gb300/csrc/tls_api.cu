@@ -33,7 +33,7 @@ struct DevBuf {
 
 }  // namespace
 
-constexpr int kBarWords = 320;   // the one-launch solve: [0, 128); the factor chain: [128, 320)
+constexpr int kBarWords = 640;   // the one-launch solve: [0, 128); the factor chain: [128, 640)
 
 struct tls_ctx {
   int64_t m = 0, n = 0, npad = 0, mpad = 0, nnz = -1;
@@ -52,7 +52,7 @@ struct tls_ctx {
   int64_t l2_keep = 0;     // bytes of A the one-launch solve keeps resident in L2
   unsigned int* fbar = nullptr;   // kBarWords barrier words: [0], [64] the one-launch solve's
                                   // counter and abort word; from [128] the persistent Cholesky's
-  int chol_chain = 3;             // block steps of the FP32 factor in one persistent launch
+  int chol_chain = 2;             // block steps of the FP32 factor in one persistent launch
                                   // (up to this many CTAs per SM; 0: one launch per step)
   RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
 

@@ -145,7 +145,7 @@ template <typename T>
 void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* Wd, Prec prec,
                      cudaStream_t s, unsigned int* gbar = nullptr, int* err = nullptr,
                      int num_sms = 0, unsigned long long* trace = nullptr,
-                     int chain_per_sm = 3);
+                     int chain_per_sm = 2);
 // Round the upper triangle of R (T) to prec in place (FP16/BF16); no-op for FP32/FP64.
 template <typename T>
 void launch_round_to(T* R, int64_t npad, Prec prec, cudaStream_t s);

@@ -402,7 +402,7 @@ def tls_set_pcg_fused(ctx, mode: int) -> None:
 
 def tls_set_factor_chain(ctx, per_sm: int) -> None:
     """Block steps of the FP32 factor in one persistent launch of up to per_sm CTAs per SM
-    (default 3), or one launch each (0)."""
+    (default 2), or one launch each (0)."""
     _check(load().tls_set_factor_chain(ctx, int(per_sm)), ctx)
 
 
