@@ -123,6 +123,14 @@ typedef struct {
                        /* order); 0: the one-launch PCGTLS solve sums A^T t with float atomics  */
                        /* (one grid barrier less per step; results may differ in the last bits  */
                        /* from run to run)                                                       */
+  int factor;          /* how R-hat is formed (dense contexts): 0 (default) the Cholesky factor */
+                       /* of the column-scaled Gram matrix (Sec. 3, on tensor cores); 1 the     */
+                       /* Householder QR of the column-scaled A in u_q = u_f (Alg. 4's         */
+                       /* "A = Q[R 0]^T", the paper's default; its constraint is kappa^-1 rather */
+                       /* than kappa^-2). With 1 no Gram matrix is formed, so tls_condition is   */
+                       /* unavailable (TLS_ERR_STATE) and tls_info.constr1/constr2 stay NaN;     */
+                       /* m is limited by the panel kernel (rows of a 32-column FP32 panel, or a */
+                       /* 16-column FP64 one, in the shared memory of one 16-CTA cluster)        */
 } tls_options;
 
 typedef struct {

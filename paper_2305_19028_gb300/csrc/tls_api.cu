@@ -193,7 +193,7 @@ void dev_free(tls_ctx* c, void* p) {
 enum Slot : int {
   kSlotCpart, kSlotInfo, kSlotAsT, kSlotH, kSlotM, kSlotWc, kSlotR, kSlotW, kSlotWT, kSlotWork,
   kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotFeat, kSlotGsplit, kSlotPM,
-  kSlotCount
+  kSlotQR, kSlotQRwork, kSlotCount
 };
 static_assert(kSlotCount <= 24, "slots");
 
@@ -1004,22 +1004,91 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
   ctx->escalations = 0;
   ctx->constr2_scaled = NAN;
   bool ok = false;
+  const bool qr = (ctx->opt.factor == 1) && !ctx->sparse;
   for (tls_prec uf : ladder) {
     const Prec pf = to_prec(uf);
     const bool chol64 = (pf == Prec::FP64);
     const size_t ce = chol64 ? 8 : 4;
+    const bool from64 = (ctx->u != Prec::FP32) || (pf == Prec::FP64);
+    // unit roundoff of the factor precision (Table 2; bf16: 2^-8)
+    const double uf_round = (pf == Prec::FP16) ? std::ldexp(1.0, -11)
+                            : (pf == Prec::BF16) ? std::ldexp(1.0, -8)
+                            : (pf == Prec::FP32) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    const bool low = (pf == Prec::FP16 || pf == Prec::BF16);
+    void* Wc = nullptr;
+    void* M = nullptr;
+    if (qr) {
+      // Alg. 4: R-hat from the Householder QR of A D^{-1} rounded to u_q (the same column
+      // scaling as the Cholesky route, so R-hat plays the part of R_H); no Gram matrix
+      ctx->H = nullptr;
+      M = slot(ctx, kSlotM, ce * (size_t)npad * (size_t)npad);
+      void* Aq = slot(ctx, kSlotQR, ce * (size_t)m * (size_t)npad);
+      const size_t qwe = (size_t)npad + (chol64 ? tls::qr_work_elems<double>(m, n, ctx->num_sms)
+                                                : tls::qr_work_elems<float>(m, n, ctx->num_sms));
+      void* qw = slot(ctx, kSlotQRwork, ce * qwe);
+      if (!M || !Aq || !qw) {
+        set_err(ctx, "device allocation failed (QR workspace)");
+        return TLS_ERR_OOM;
+      }
+      TLS_CK(cudaMemsetAsync(dinfo, 0, sizeof(int), st));
+      const void* src = from64 ? (const void*)ctx->A64 : (const void*)ctx->A32;
+      {
+        Prof pr(ctx, TLS_PROF_SCALE);
+        if (chol64)
+          tls::launch_qr_scale<double>(src, from64, npad, m, n, ctx->dinv, ctx->dinv32, pf,
+                                       static_cast<double*>(Aq), npad, st);
+        else
+          tls::launch_qr_scale<float>(src, from64, npad, m, n, ctx->dinv, ctx->dinv32, pf,
+                                      static_cast<float*>(Aq), npad, st);
+      }
+      int qrc;
+      {
+        Prof pr(ctx, TLS_PROF_CHOL);
+        if (chol64) {
+          double* q = static_cast<double*>(qw);
+          qrc = tls::launch_qr_r<double>(static_cast<double*>(Aq), npad, m, n, q, q + npad, dinfo,
+                                         ctx->num_sms, st);
+          if (qrc == 0)
+            tls::launch_qr_extract<double, double>(static_cast<double*>(Aq), npad, n, npad,
+                                                   static_cast<double*>(M), st);
+        } else {
+          float* q = static_cast<float*>(qw);
+          qrc = tls::launch_qr_r<float>(static_cast<float*>(Aq), npad, m, n, q, q + npad, dinfo,
+                                        ctx->num_sms, st);
+          if (qrc == 0)
+            tls::launch_qr_extract<float, float>(static_cast<float*>(Aq), npad, n, npad,
+                                                 static_cast<float*>(M), st);
+        }
+      }
+      if (qrc != 0) {
+        set_err(ctx, qrc == -3 ? "Householder QR: the panel kernel's cluster launch failed"
+                               : "Householder QR: m too large for the panel kernel (rows of a "
+                                 "panel are held in the shared memory of one 16-CTA cluster)");
+        return TLS_ERR_ARG;
+      }
+      TLS_CK_LAUNCH("householder qr");
+      int hinfo = 0;
+      TLS_CK(cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TLS_CK(cudaStreamSynchronize(st));
+      read_norms();
+      if (hinfo != 0) {
+        // a zero (or non-finite) diagonal entry of R-hat: rank deficient in u_q, escalate
+        ctx->fail_pivot = hinfo - 1;
+        continue;
+      }
+      ok = true;
+    } else {
     const size_t ae = (pf == Prec::FP64) ? 8 : (pf == Prec::FP32 ? 4 : 2);
     // dense: the scaled, rounded, transposed A_s; sparse: its values in CSR and CSC order
     void* AsT = ctx->sparse
                     ? slot(ctx, kSlotAsT, 2 * ce * (size_t)std::max<int64_t>(ctx->nnz, 1))
                     : slot(ctx, kSlotAsT, ae * (size_t)npad * (size_t)mpad);
     ctx->H = slot(ctx, kSlotH, ce * (size_t)npad * (size_t)npad);
-    void* M = slot(ctx, kSlotM, ce * (size_t)npad * (size_t)npad);
+    M = slot(ctx, kSlotM, ce * (size_t)npad * (size_t)npad);
     if (!AsT || !ctx->H || !M) {
       set_err(ctx, "device allocation failed (factor workspace)");
       return TLS_ERR_OOM;
     }
-    const bool from64 = (ctx->u != Prec::FP32) || (pf == Prec::FP64);
     if (ctx->sparse) {
       Prof pr(ctx, TLS_PROF_GRAM);
       const int64_t nz = std::max<int64_t>(ctx->nnz, 1);
@@ -1066,17 +1135,12 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     }
     }
     TLS_CK_LAUNCH("gram");
-    void* Wc = slot(ctx, kSlotWc, ce * (size_t)npad * (size_t)npad);   // diagonal-block inverses
+    Wc = slot(ctx, kSlotWc, ce * (size_t)npad * (size_t)npad);   // diagonal-block inverses
     if (!Wc) {
       set_err(ctx, "device allocation failed (factor workspace)");
       return TLS_ERR_OOM;
     }
     const int max_shift = std::max(0, ctx->opt.max_shifts);
-    // unit roundoff of the factor precision (Table 2; bf16: 2^-8)
-    const double uf_round = (pf == Prec::FP16) ? std::ldexp(1.0, -11)
-                            : (pf == Prec::BF16) ? std::ldexp(1.0, -8)
-                            : (pf == Prec::FP32) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
-    const bool low = (pf == Prec::FP16 || pf == Prec::BF16);
     const int first = (low && ctx->opt.shift_first) ? 1 : 0;
     for (int sh = first; sh <= max_shift + first; ++sh) {
       const double shift = (sh == 0) ? 0.0 : 2.0 * uf_round * std::pow(4.0, sh - 1);
@@ -1117,6 +1181,7 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
       ctx->shifts += 1;
       ctx->fail_pivot = hinfo - 1;
     }
+    }   // Cholesky route
     if (!ok) continue;
     // R_H rounded to u_f (the computed factor R-hat), then carried in the u type
     if (chol64) tls::launch_round_to<double>(static_cast<double*>(M), npad, pf, st);
@@ -1133,28 +1198,31 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     }
     const int64_t cnt = npad * npad;
     Prof pr(ctx, TLS_PROF_TRTRI);
+    // (the Cholesky route has the inverses of R-hat's 64 x 64 diagonal blocks in Wc already;
+    // the QR route leaves them to the triangular inverse)
+    const bool have_diag = (Wc != nullptr);
     if (ctx->u == Prec::FP64) {
       if (chol64) {
         TLS_CK(cudaMemcpyAsync(ctx->R, M, 8 * cnt, cudaMemcpyDeviceToDevice, st));
-        TLS_CK(cudaMemcpyAsync(ctx->W, Wc, 8 * cnt, cudaMemcpyDeviceToDevice, st));
+        if (have_diag) TLS_CK(cudaMemcpyAsync(ctx->W, Wc, 8 * cnt, cudaMemcpyDeviceToDevice, st));
       } else {
         tls::launch_f2d(static_cast<float*>(M), static_cast<double*>(ctx->R), cnt, st);
-        tls::launch_f2d(static_cast<float*>(Wc), static_cast<double*>(ctx->W), cnt, st);
+        if (have_diag) tls::launch_f2d(static_cast<float*>(Wc), static_cast<double*>(ctx->W), cnt, st);
       }
       tls::launch_trtri<double>(static_cast<double*>(ctx->R), static_cast<double*>(ctx->W),
                                 static_cast<double*>(ctx->WT), static_cast<double*>(work), npad,
-                                true, st);
+                                have_diag, st);
     } else {
       if (chol64) {
         tls::launch_d2f(static_cast<double*>(M), static_cast<float*>(ctx->R), cnt, st);
-        tls::launch_d2f(static_cast<double*>(Wc), static_cast<float*>(ctx->W), cnt, st);
+        if (have_diag) tls::launch_d2f(static_cast<double*>(Wc), static_cast<float*>(ctx->W), cnt, st);
       } else {
         TLS_CK(cudaMemcpyAsync(ctx->R, M, 4 * cnt, cudaMemcpyDeviceToDevice, st));
-        TLS_CK(cudaMemcpyAsync(ctx->W, Wc, 4 * cnt, cudaMemcpyDeviceToDevice, st));
+        if (have_diag) TLS_CK(cudaMemcpyAsync(ctx->W, Wc, 4 * cnt, cudaMemcpyDeviceToDevice, st));
       }
       tls::launch_trtri<float>(static_cast<float*>(ctx->R), static_cast<float*>(ctx->W),
                                static_cast<float*>(ctx->WT), static_cast<float*>(work), npad,
-                               true, st);
+                               have_diag, st);
     }
     TLS_CK_LAUNCH("triangular inverse");
     ctx->uf_used = uf;
@@ -1174,7 +1242,8 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     break;
   }
   if (!ok) {
-    set_err(ctx, "Cholesky breakdown at every shift and precision");
+    set_err(ctx, qr ? "Householder QR: a zero diagonal entry of R at every precision"
+                    : "Cholesky breakdown at every shift and precision");
     return TLS_ERR_FACTOR_BREAKDOWN;
   }
   tls_status s2 = ensure_solve_buffers(ctx);
@@ -1414,6 +1483,7 @@ void tls_default_options(tls_options* opt) {
   opt->constraint_iters = 0;
   opt->hybrid_ratio = 0.1;
   opt->reproducible = 1;
+  opt->factor = 0;
 }
 
 const char* tls_status_str(tls_status s) {
@@ -1587,6 +1657,11 @@ tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
                  "attainable accuracy, Sec. 4.3)");
     return TLS_ERR_ARG;
   }
+  if (o.factor < 0 || o.factor > 1 || (o.factor == 1 && ctx->sparse)) {
+    set_err(ctx, "factor must be 0 (Cholesky of the scaled Gram matrix) or 1 (Householder QR, "
+                 "dense contexts)");
+    return TLS_ERR_ARG;
+  }
   const int64_t limit = (o.u == TLS_FP64) ? 4096 : 8192;
   if (ctx->npad > limit) {
     set_err(ctx, "n too large for the dense path");
@@ -1671,8 +1746,10 @@ static tls_status solve_common(tls_ctx* ctx, double tol, int max_rqi, double* si
   if (s == TLS_OK && ctx->opt.constraint_iters > 0) {
     // the paper's constraints 1 and 2 (Eq. (5), Eq. (9)) for A, with this solve's sigma
     double c[9];
-    s = tls_condition(ctx, ctx->opt.constraint_iters, c);
-    if (s == TLS_OK) {
+    s = ctx->H ? tls_condition(ctx, ctx->opt.constraint_iters, c) : TLS_ERR_STATE;
+    if (s == TLS_ERR_STATE && !ctx->H) {
+      s = TLS_OK;   // QR factor: no Gram matrix, the constraint fields stay NaN
+    } else if (s == TLS_OK) {
       loc.constr1 = c[7];
       loc.constr2 = c[8];
       if (std::isnan(ctx->constr2_scaled)) s = scaled_constraint2(ctx, &ctx->constr2_scaled);
@@ -1894,6 +1971,11 @@ uint64_t tls_kernel_launches(void) { return tls::g_launches.load(); }
 tls_status tls_condition(tls_ctx* ctx, int iters, double* out) {
   if (!ctx || !out || iters < 1) return TLS_ERR_ARG;
   if (!ctx->factored) return TLS_ERR_STATE;
+  if (!ctx->H) {
+    set_err(ctx, "the condition estimate uses the scaled Gram matrix, which the QR factor does "
+                 "not form");
+    return TLS_ERR_STATE;
+  }
   if (ctx->H_fp64) {
     if (ctx->u == Prec::FP64) return condition_impl<double, double>(ctx, iters, out);
     return condition_impl<double, float>(ctx, iters, out);

@@ -160,6 +160,34 @@ void launch_d2f(const double* in, float* out, int64_t count, cudaStream_t s);
 void launch_set_identity_pad(void* M, bool fp64, int64_t n, int64_t npad, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------
+// Householder QR preconditioner (k_qr.cu)
+// ---------------------------------------------------------------------------------------
+// Panel width the cluster panel kernel can hold for m rows (32, 16 or 8; 0: m too large).
+template <typename T>
+int qr_panel_width(int64_t m);
+// Elements of T the QR's work buffer needs (T of a panel and the partial products V^T A).
+template <typename T>
+size_t qr_work_elems(int64_t m, int64_t n, int num_sms);
+// Aq (m x n, row stride ldq, T) = A D^{-1} rounded to prec, from the FP64 master or the FP32
+// working copy (row stride lda_src).
+template <typename T>
+int launch_qr_scale(const void* Asrc, bool from64, int64_t lda_src, int64_t m, int64_t n,
+                    const double* dinv, const float* dinv32, Prec prec, T* Aq, int64_t ldq,
+                    cudaStream_t s);
+// Blocked Householder QR of the m x n row-major A (lda), m >= n, in place: R in the upper
+// triangle of rows 0 .. n-1, the reflectors below; tau (n) their scalars. work: qr_work_elems.
+// *info = j + 1 for the first reflector whose diagonal entry is zero or not finite. Returns 0,
+// or < 0 when the problem does not fit the panel kernel (nothing launched).
+template <typename T>
+int launch_qr_r(T* A, int64_t lda, int64_t m, int64_t n, T* tau, T* work, int* info,
+                int num_sms, cudaStream_t s);
+// M (npad x npad) = R with a positive diagonal (rows scaled by sign(R_ii)), zero below, the
+// identity on the padding.
+template <typename T, typename Tout>
+void launch_qr_extract(const T* Aq, int64_t lda, int64_t n, int64_t npad, Tout* M,
+                       cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
 // Solve kernels (k_solve.cu)
 // ---------------------------------------------------------------------------------------
 struct ApassPlan {

@@ -53,7 +53,7 @@ class tls_options(C.Structure):
                 ("psi_accept", C.c_double), ("shift_first", C.c_int), ("fallback", C.c_int),
                 ("constr_guard", C.c_double), ("stall_fallback", C.c_int),
                 ("stall_ratio", C.c_double), ("constraint_iters", C.c_int),
-                ("hybrid_ratio", C.c_double), ("reproducible", C.c_int)]
+                ("hybrid_ratio", C.c_double), ("reproducible", C.c_int), ("factor", C.c_int)]
 
 
 class tls_info(C.Structure):

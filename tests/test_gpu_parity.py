@@ -137,8 +137,9 @@ def test_factor_chain_matches_one_launch_per_step(m, n):
             out.append(tls.tls_export_factor(ctx))
         finally:
             tls.tls_destroy(ctx)
-    for a_, b_ in zip(out[0], out[1]):
-        assert np.array_equal(np.asarray(a_), np.asarray(b_))
+    for chained in out[:2]:
+        for a_, b_ in zip(chained, out[2]):
+            assert np.array_equal(np.asarray(a_), np.asarray(b_))
 
 
 @pytest.mark.parametrize("u_f,u", [("fp16", "fp32"), ("bf16", "fp32"), ("fp32", "fp32"),
