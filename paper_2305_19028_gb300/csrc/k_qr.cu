@@ -59,65 +59,86 @@ __device__ __forceinline__ T rank_order_sum(cg::cluster_group& cl, T* buf, int e
   return t;
 }
 
-// The end of a panel (both panel kernels, all threads of every CTA): V^T V from the panel rows
-// in shared memory P (entry (a, b), a < b, sums V[r][a] V[r][b] over rows r >= k + b, with
-// V[k + b][b] = 1 and V[r][a] = P[r][a] below row k + a), summed over the cluster in rank order;
-// then T by the recurrence (one warp, lane = row); rank 0 writes T and the taus; every CTA
-// writes its rows of the panel back to A.
+// The end of a panel (both panel kernels, all threads of every CTA). With have_g false, first
+// V^T V from the panel rows in shared memory P (entry (a, b), a < b, sums V[r][a] V[r][b] over
+// rows r >= k + b, with V[k + b][b] = 1 and V[r][a] = P[r][a] below row k + a), summed over
+// the cluster in rank order, into the strict upper part of G. Then T by doubling: T_jj = tau_j,
+// and for every pair of neighbouring s-blocks A, B (s = 1, 2, 4, 8, 16),
+// T_AB = -T_AA (V_A^T V_B) T_BB, the compact WY form of Q_A Q_B. Rank 0 writes T and the taus;
+// every CTA writes its rows of the panel back to A.
 template <typename T>
 __device__ __forceinline__ void qr_panel_finish(cg::cluster_group& cl, const T* P, int ldp, int nr,
                                                 int bw, T* xch, const T* taus, T* G, T* Tl,
                                                 T* A, int64_t lda, int64_t k, int64_t r0,
-                                                T* tau_out, T* Tm, int* info, int bad) {
+                                                T* tau_out, T* Tm, int* info, int bad,
+                                                bool have_g) {
   const int R = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthr = blockDim.x, nw = nthr / 32;
   const int npairs = bw * (bw - 1) / 2;
-  for (int q = warp; q < npairs; q += nw) {
-    int a = 0, rem = q;
-    while (rem >= bw - 1 - a) {
-      rem -= bw - 1 - a;
-      ++a;
-    }
-    const int b = a + 1 + rem;
-    const int lb = (rank == 0) ? b : -1;
-    T acc = T(0);
-    for (int i = max(lb, 0) + lane; i < nr; i += 32) {
-      const T vb = (i == lb) ? T(1) : P[i * ldp + b];
-      acc = fma(P[i * ldp + a], vb, acc);
-    }
-    acc = warp_sum_q(acc);
-    if (lane == 0) xch[q] = acc;
-  }
-  cl.sync();
-  for (int q = tid; q < npairs; q += nthr) {
-    int a = 0, rem = q;
-    while (rem >= bw - 1 - a) {
-      rem -= bw - 1 - a;
-      ++a;
-    }
-    const int b = a + 1 + rem;
-    G[a * bw + b] = rank_order_sum(cl, xch, q, R);
-  }
-  __syncthreads();
-  if (warp == 0) {
-    // column j of T: T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j], T[j][j] = tau_j
-    for (int j = 0; j < bw; ++j) {
-      T val = T(0);
-      if (lane < j) {
-        for (int l = lane; l < j; ++l) val = fma(Tl[lane * bw + l], G[l * bw + j], val);
-        val = -taus[j] * val;
-      } else if (lane == j) {
-        val = taus[j];
+  if (!have_g) {
+    for (int q = warp; q < npairs; q += nw) {
+      int a = 0, rem = q;
+      while (rem >= bw - 1 - a) {
+        rem -= bw - 1 - a;
+        ++a;
       }
-      __syncwarp();
-      if (lane < bw) Tl[lane * bw + j] = val;
-      __syncwarp();
+      const int b = a + 1 + rem;
+      const int lb = (rank == 0) ? b : -1;
+      T acc = T(0);
+      for (int i = max(lb, 0) + lane; i < nr; i += 32) {
+        const T vb = (i == lb) ? T(1) : P[i * ldp + b];
+        acc = fma(P[i * ldp + a], vb, acc);
+      }
+      acc = warp_sum_q(acc);
+      if (lane == 0) xch[q] = acc;
+    }
+    cl.sync();
+    for (int q = tid; q < npairs; q += nthr) {
+      int a = 0, rem = q;
+      while (rem >= bw - 1 - a) {
+        rem -= bw - 1 - a;
+        ++a;
+      }
+      const int b = a + 1 + rem;
+      G[a * bw + b] = rank_order_sum(cl, xch, q, R);
     }
   }
+  for (int e = tid; e < bw * bw; e += nthr) {
+    const int i = e / bw, j = e - i * bw;
+    Tl[e] = (i == j) ? taus[i] : T(0);
+  }
   __syncthreads();
+  for (int sb = 1; sb < bw; sb *= 2) {
+    // Tm_AB = G_AB T_BB into the (zero, unused) lower part of Tl: entry (a, b) of the pair at o
+    // goes to Tl[o + sb + b][o + a]; then T_AB = -T_AA Tm_AB
+    const int pairs = (bw + 2 * sb - 1) / (2 * sb);
+    for (int e = tid; e < pairs * sb * sb; e += nthr) {
+      const int pr = e / (sb * sb), rem = e - pr * sb * sb, a = rem / sb, b = rem - a * sb;
+      const int o = 2 * pr * sb, ia = o + a, jb = o + sb + b;
+      if (jb < bw) {
+        T v = T(0);
+        for (int l = o + sb; l <= jb; ++l) v = fma(G[ia * bw + l], Tl[l * bw + jb], v);
+        Tl[jb * bw + ia] = v;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < pairs * sb * sb; e += nthr) {
+      const int pr = e / (sb * sb), rem = e - pr * sb * sb, a = rem / sb, b = rem - a * sb;
+      const int o = 2 * pr * sb, ia = o + a, jb = o + sb + b;
+      if (jb < bw) {
+        T v = T(0);
+        for (int l = ia; l < o + sb; ++l) v = fma(Tl[ia * bw + l], Tl[jb * bw + l], v);
+        Tl[ia * bw + jb] = -v;
+      }
+    }
+    __syncthreads();
+  }
   if (rank == 0) {
-    for (int e = tid; e < bw * bw; e += nthr) Tm[e] = Tl[e];
+    for (int e = tid; e < bw * bw; e += nthr) {
+      const int i = e / bw, j = e - i * bw;
+      Tm[e] = (j >= i) ? Tl[e] : T(0);
+    }
     for (int e = tid; e < bw; e += nthr) tau_out[k + e] = taus[e];
     if (tid == 0 && bad) atomicCAS(info, 0, (int)(k + bad));
   }
@@ -240,7 +261,7 @@ __global__ void __launch_bounds__(kQT, 1) qr_panel_kernel(T* __restrict__ A, int
     }
   }
   qr_panel_finish<T>(cl, P, ldp, nr, bw, xch, taus, G, Tl, A, lda, k, r0, tau_out, Tm, info,
-                     bad);
+                     bad, false);
 }
 
 // Sums over the 32 lanes of a warp of 32 values per lane at once: lane l ends with the total of
@@ -275,8 +296,8 @@ __host__ __device__ inline size_t qr_panel_reg_extra() {
 // then every CTA's partial pushed into its slot of every peer before one cluster barrier), the
 // reflector, then v^T a_c for the later columns (each lane's 32 partial products reduced over
 // the warp in one transposed pass, then over the warps, then over the cluster in rank order
-// the same way), and the rank-1 update in registers. The same arithmetic decisions as
-// qr_panel_kernel; V^T V, T and the write-back go through shared memory (qr_panel_finish).
+// the same way; the same exchange carries column j of V^T V), and the rank-1 update in
+// registers. T and the write-back go through shared memory (qr_panel_finish).
 template <int RPT>
 __global__ void __launch_bounds__(kQRT, 1) qr_panel_reg_kernel(float* __restrict__ A, int64_t lda,
                                                               int64_t m, int64_t k, int bw,
@@ -300,13 +321,18 @@ __global__ void __launch_bounds__(kQRT, 1) qr_panel_reg_kernel(float* __restrict
   float* Tl = G + BW * BW;
   const int64_t r0 = k + (int64_t)rank * rpc;
   const int nr = (int)max((int64_t)0, min(m, r0 + rpc) - r0);
+  // the rows through shared memory (coalesced loads), then into registers
+  for (int e = tid; e < nr * BW; e += kQRT) {
+    const int i = e / BW, c = e - i * BW;
+    P[i * ldp + c] = (c < bw) ? A[(r0 + i) * lda + k + c] : 0.f;
+  }
+  __syncthreads();
   float a[RPT][BW];
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int lr = tid + kQRT * q;
 #pragma unroll
-    for (int c = 0; c < BW; ++c)
-      a[q][c] = (lr < nr && c < bw) ? A[(r0 + lr) * lda + k + c] : 0.f;
+    for (int c = 0; c < BW; ++c) a[q][c] = (lr < nr) ? P[lr * ldp + c] : 0.f;
   }
   if (tid < BW) wtot[tid] = 0.f;
   cl.sync();   // every CTA of the cluster running before the first write into a peer's slots
@@ -358,8 +384,11 @@ __global__ void __launch_bounds__(kQRT, 1) qr_panel_reg_kernel(float* __restrict
         if (lr < nr && lr > lj) a[q][j] *= scal;
         if (lr == lj) a[q][j] = beta;
       }
-      if (j + 1 < bw) {
-        // (2) v^T a_c, c > j (v = 1 at the pivot, the scaled column below, 0 above)
+      {
+        // (2) sums v^T a_c over the rows from the pivot down (v = 1 at the pivot, the scaled
+        // column below, 0 above): for c > j the w_c of the update; for c < j the entry
+        // G[c][j] = v_c^T v_j of V^T V (every row here lies below pivot c, where column c holds
+        // v_c), so V^T V costs no extra exchange
         float d[BW];
 #pragma unroll
         for (int c = 0; c < BW; ++c) d[c] = 0.f;
@@ -368,32 +397,36 @@ __global__ void __launch_bounds__(kQRT, 1) qr_panel_reg_kernel(float* __restrict
           const int lr = tid + kQRT * q;
           const float v = (lr >= nr || lr < lj) ? 0.f : (lr == lj ? 1.f : a[q][j]);
 #pragma unroll
-          for (int c = j + 1; c < BW; ++c) d[c] = fmaf(v, a[q][c], d[c]);
+          for (int c = 0; c < BW; ++c)
+            if (c != j) d[c] = fmaf(v, a[q][c], d[c]);
         }
         const float wv = warp_transpose_sum32(d, lane);   // column `lane`, this warp's rows
         wsum[warp * (BW + 1) + lane] = wv;
         __syncthreads();
         float* set2 = slots + ph * kQMaxCl * SW;
         ph ^= 1;
-        if (tid > j && tid < bw) {
+        if (tid < bw && tid != j) {
           float t = 0.f;
           for (int w = 0; w < NW; ++w) t += wsum[w * (BW + 1) + tid];
           for (int r = 0; r < R; ++r) cl.map_shared_rank(set2 + rank * SW, r)[tid] = t;
         }
         cl.sync();
-        if (tid > j && tid < bw) {
+        if (tid < bw && tid != j) {
           float t = 0.f;
           for (int r = 0; r < R; ++r) t += set2[r * SW + tid];
-          wtot[tid] = tau * t;
+          if (tid > j) wtot[tid] = tau * t;
+          else G[tid * bw + j] = t;
         }
         __syncthreads();
-        // (3) a_c -= (tau w_c) v
+        if (j + 1 < bw) {
+          // (3) a_c -= (tau w_c) v
 #pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-          const int lr = tid + kQRT * q;
-          const float v = (lr >= nr || lr < lj) ? 0.f : (lr == lj ? 1.f : a[q][j]);
+          for (int q = 0; q < RPT; ++q) {
+            const int lr = tid + kQRT * q;
+            const float v = (lr >= nr || lr < lj) ? 0.f : (lr == lj ? 1.f : a[q][j]);
 #pragma unroll
-          for (int c = j + 1; c < BW; ++c) a[q][c] = fmaf(-wtot[c], v, a[q][c]);
+            for (int c = j + 1; c < BW; ++c) a[q][c] = fmaf(-wtot[c], v, a[q][c]);
+          }
         }
       }
     }
@@ -408,7 +441,7 @@ __global__ void __launch_bounds__(kQRT, 1) qr_panel_reg_kernel(float* __restrict
   }
   __syncthreads();
   qr_panel_finish<float>(cl, P, ldp, nr, bw, xch, taus, G, Tl, A, lda, k, r0, tau_out, Tm, info,
-                         bad);
+                         bad, true);
 }
 
 // V[r][i] of panel (k, bw): 1 at r = k + i, the stored entry below, 0 above
@@ -419,6 +452,17 @@ __device__ __forceinline__ T qr_v(const T* A, int64_t lda, int64_t k, int64_t r,
 }
 
 constexpr int kQCB = 128;   // columns of the trailing matrix per block of the update kernels
+
+// four consecutive shared elements in 16-byte reads (p 16-byte aligned)
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 u = *reinterpret_cast<const double2*>(p);
+  const double2 v = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = u.x; o[1] = u.y; o[2] = v.x; o[3] = v.y;
+}
 
 // Partial X_p = V[rows of chunk p]^T A_trail[rows, columns of block cb] (bw x kQCB), into
 // part[(p bw + i) nt + c]. Thread tile: X rows 4 (tid / 32) .. + 3, columns 4 (tid % 32) .. + 3
@@ -453,11 +497,8 @@ __global__ void __launch_bounds__(kQT, 4) qr_vta_kernel(const T* __restrict__ A,
 #pragma unroll 4
     for (int rr = 0; rr < kQChunk; ++rr) {
       T v[4], a[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        v[q] = Vs[rr][ig4 + q];
-        a[q] = As[rr][cg4 + q];
-      }
+      ld4(&Vs[rr][ig4], v);
+      ld4(&As[rr][cg4], a);
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -550,11 +591,8 @@ __global__ void __launch_bounds__(kQT, 4) qr_apply_kernel(T* __restrict__ A, int
 #pragma unroll 4
     for (int i = 0; i < kQMaxBw; ++i) {
       T v[4], yv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        v[q] = Vt[i][rg4 + q];
-        yv[q] = Ys[i][cg4 + q];
-      }
+      ld4(&Vt[i][rg4], v);
+      ld4(&Ys[i][cg4], yv);
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
