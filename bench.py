@@ -356,7 +356,7 @@ def _pass_only(tls, ctx, p, sigma) -> dict:
 
 
 def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int = -1,
-              units: dict | None = None) -> dict:
+              units: dict | None = None, qr: bool = False) -> dict:
     cnt, ms = prof.get(cls, (0, 0.0))
     if cnt == 0:
         return {}
@@ -403,6 +403,17 @@ def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int 
                 "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
                 "traffic": None, "peak_source": src + " (bf16 sustained; fp16 nominal rate equal)",
                 "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops}
+    if cls == "chol" and qr:
+        # the Householder QR of the scaled m x n matrix (R only): 2 m n^2 - 2 n^3 / 3 flops,
+        # FP32 on CUDA cores; bound by the per-column cluster exchanges of its panels
+        flops = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+        ach = flops / avg_s / 1e12
+        return {"kernel": "householder qr (R of A D^-1 in u_q; panel reflectors on a 16-CTA "
+                          "cluster, WY trailing updates, FP32 CUDA cores)", "bound": "alu",
+                "achieved": ach, "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": ach / FP32_PEAK,
+                "traffic": None,
+                "peak_source": "nominal FP32 rate (128 FMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops}
     if cls == "chol":
         # one launch-class entry per factor: the diagonal blocks (a chain of n pivots, one CTA
         # per 64-block) and the panel / trailing updates, FP32 on CUDA cores
@@ -428,7 +439,8 @@ def run_ours(args, ws, rank, local):
     p = _problem(rank)
     stream = torch.cuda.current_stream()
     ctx = tls.tls_create_dense(p.A, p.b, stream=stream.cuda_stream)
-    opt = tls.tls_default_options(u="fp32")
+    qr = args.factor == "qr"
+    opt = tls.tls_default_options(u="fp32", factor=1 if qr else 0)
 
     # the CPU oracle (accuracy reference and CPU baseline) runs after every GPU measurement,
     # so that its host threads cannot slow the launches being timed; results are kept and
@@ -563,7 +575,7 @@ def run_ours(args, ws, rank, local):
     dom = max(total, key=total.get)
     share = {k: round(v / max(1e-9, sum(total.values())), 4) for k, v in total.items()}
     v64 = infos[-1]["pass_variant"][0]
-    roof = (_roofline(prof, peaks, dom, M_ROWS, N_COLS, v64, units) or
+    roof = (_roofline(prof, peaks, dom, M_ROWS, N_COLS, v64, units, qr) or
             _inner_loop(prof, units, peaks, M_ROWS, N_COLS))
     inner = _inner_loop(prof, units, peaks, M_ROWS, N_COLS)
     if inner and pass_only:
@@ -576,8 +588,10 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS, "d_lo": D_LO, "noise": NOISE,
+        "config": {"workload": WORKLOAD + ("_householder_qr" if qr else ""), "m": M_ROWS,
+                   "n": N_COLS, "d_lo": D_LO, "noise": NOISE,
                    "seed": "rank", "u_f": "fp16", "u": "fp32", "u_r": "fp64",
+                   "factor": "householder_qr" if qr else "cholesky_of_scaled_gram",
                    "solve_tol": SOLVE_TOL, "max_rqi": MAX_RQI,
                    "l2": "inputs larger than L2 (A: 268 MB FP64 + 134 MB FP32 per step)",
                    "step": "tls_factor + tls_solve on resident A"},
@@ -1148,6 +1162,9 @@ def main():
     ap.add_argument("--m", type=int, default=None, help="rows (profiling a smaller case)")
     ap.add_argument("--n", type=int, default=None, help="columns (profiling a smaller case)")
     ap.add_argument("--workload", choices=["dense", "batch", "sparse", "c1"], default="dense")
+    ap.add_argument("--factor", choices=["cholesky", "qr"], default="cholesky",
+                    help="dense workload: R-hat from the Cholesky factor of the scaled Gram "
+                         "matrix (default) or from Householder QR (Alg. 4)")
     ap.add_argument("--batch", type=int, default=BATCH_K, help="problems in the packed batch")
     ap.add_argument("--selector", action="store_true",
                     help="batch: let the trained selector network pick u_f per problem")

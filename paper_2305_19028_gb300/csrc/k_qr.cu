@@ -181,9 +181,18 @@ __global__ void __launch_bounds__(kQT, 1) qr_panel_kernel(T* __restrict__ A, int
   T* Tl = G + bw * bw;                 // T, bw x bw
   const int64_t r0 = k + (int64_t)rank * rpc;
   const int nr = (int)max((int64_t)0, min(m, r0 + rpc) - r0);
-  for (int e = tid; e < nr * bw; e += kQT) {
-    const int i = e / bw, c = e - i * bw;
-    P[i * ldp + c] = A[(r0 + i) * lda + k + c];
+  for (int e0 = tid; e0 < nr * bw; e0 += 8 * kQT) {
+    T v[8];   // eight loads in flight per thread
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = e0 + t * kQT, i = e / bw, c = e - i * bw;
+      v[t] = (e < nr * bw) ? A[(r0 + i) * lda + k + c] : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = e0 + t * kQT, i = e / bw, c = e - i * bw;
+      if (e < nr * bw) P[i * ldp + c] = v[t];
+    }
   }
   cl.sync();   // every CTA of the cluster running before the first write into a peer's slots
   // the pivot row k + j lies in rank 0's rows (the host keeps rpc >= bw)
@@ -321,10 +330,20 @@ __global__ void __launch_bounds__(kQRT, 1) qr_panel_reg_kernel(float* __restrict
   float* Tl = G + BW * BW;
   const int64_t r0 = k + (int64_t)rank * rpc;
   const int nr = (int)max((int64_t)0, min(m, r0 + rpc) - r0);
-  // the rows through shared memory (coalesced loads), then into registers
-  for (int e = tid; e < nr * BW; e += kQRT) {
-    const int i = e / BW, c = e - i * BW;
-    P[i * ldp + c] = (c < bw) ? A[(r0 + i) * lda + k + c] : 0.f;
+  // the rows through shared memory (coalesced loads, eight in flight per thread), then into
+  // registers
+  for (int e0 = tid; e0 < nr * BW; e0 += 8 * kQRT) {
+    float v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = e0 + t * kQRT, i = e / BW, c = e - i * BW;
+      v[t] = (e < nr * BW && c < bw) ? A[(r0 + i) * lda + k + c] : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = e0 + t * kQRT, i = e / BW, c = e - i * BW;
+      if (e < nr * BW) P[i * ldp + c] = v[t];
+    }
   }
   __syncthreads();
   float a[RPT][BW];
@@ -468,32 +487,52 @@ __device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
 // part[(p bw + i) nt + c]. Thread tile: X rows 4 (tid / 32) .. + 3, columns 4 (tid % 32) .. + 3
 // (the V row part is the same in a warp, the A part consecutive).
 template <typename T>
-__global__ void __launch_bounds__(kQT, 4) qr_vta_kernel(const T* __restrict__ A, int64_t lda,
+__global__ void __launch_bounds__(kQT, 3) qr_vta_kernel(const T* __restrict__ A, int64_t lda,
                                                        int64_t m, int64_t k, int bw, int64_t nt,
                                                        int64_t rc, T* __restrict__ part) {
+  constexpr int NV = kQChunk * kQMaxBw / kQT, NA = kQChunk * kQCB / kQT;
   __shared__ __align__(16) T Vs[kQChunk][kQMaxBw + 4];
   __shared__ __align__(16) T As[kQChunk][kQCB + 4];
   const int tid = threadIdx.x, cg4 = 4 * (tid & 31), ig4 = 4 * (tid >> 5);
   const int64_t c0 = (int64_t)blockIdx.x * kQCB, p = blockIdx.y;
   const int64_t rbeg = k + p * rc, rend = min(m, rbeg + rc);
   const int64_t col0 = k + bw + c0;
+  // the next chunk's share of V and A in registers: every load of a chunk in flight at once,
+  // and during the previous chunk's products
+  T pv[NV], pa[NA];
+  auto fetch = [&](int64_t r) {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int e = tid + t * kQT, rr = e / kQMaxBw, i = e % kQMaxBw;
+      const int64_t g = r + rr;
+      pv[t] = (g < rend && i < bw) ? qr_v(A, lda, k, g, i) : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < NA; ++t) {
+      const int e = tid + t * kQT, rr = e / kQCB, cc = e % kQCB;
+      const int64_t g = r + rr;
+      pa[t] = (g < rend && c0 + cc < nt) ? A[g * lda + col0 + cc] : T(0);
+    }
+  };
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  if (rbeg < rend) fetch(rbeg);
   for (int64_t r = rbeg; r < rend; r += kQChunk) {
-    for (int e = tid; e < kQChunk * kQMaxBw; e += kQT) {
-      const int rr = e / kQMaxBw, i = e % kQMaxBw;
-      const int64_t g = r + rr;
-      Vs[rr][i] = (g < rend && i < bw) ? qr_v(A, lda, k, g, i) : T(0);
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int e = tid + t * kQT;
+      Vs[e / kQMaxBw][e % kQMaxBw] = pv[t];
     }
-    for (int e = tid; e < kQChunk * kQCB; e += kQT) {
-      const int rr = e / kQCB, cc = e % kQCB;
-      const int64_t g = r + rr;
-      As[rr][cc] = (g < rend && c0 + cc < nt) ? A[g * lda + col0 + cc] : T(0);
+#pragma unroll
+    for (int t = 0; t < NA; ++t) {
+      const int e = tid + t * kQT;
+      As[e / kQCB][e % kQCB] = pa[t];
     }
     __syncthreads();
+    if (r + kQChunk < rend) fetch(r + kQChunk);
 #pragma unroll 4
     for (int rr = 0; rr < kQChunk; ++rr) {
       T v[4], a[4];
@@ -532,14 +571,15 @@ __global__ void __launch_bounds__(kQT) qr_reduce_kernel(const T* __restrict__ pa
   if (i < bw && c < nt) {
     const T* src = part + (int64_t)i * nt + c;
     const int64_t stride = (int64_t)bw * nt;
-    for (int q0 = 0; q0 < P; q0 += 16) {
+    int q0 = 0;
+    for (; q0 + 16 <= P; q0 += 16) {
       T v[16];   // sixteen loads in flight, then the adds in chunk order
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = (q0 + q < P) ? src[(q0 + q) * stride] : T(0);
+      for (int q = 0; q < 16; ++q) v[q] = src[(q0 + q) * stride];
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q0 + q < P) sum += v[q];
+      for (int q = 0; q < 16; ++q) sum += v[q];
     }
+    for (; q0 < P; ++q0) sum += src[q0 * stride];
   }
   Xs[i][cc] = sum;
   __syncthreads();
@@ -554,35 +594,62 @@ __global__ void __launch_bounds__(kQT) qr_reduce_kernel(const T* __restrict__ pa
 // Thread tile: rows 4 (tid / 32) .. + 3 of each 32-row chunk, columns 4 (tid % 32) .. + 3; V
 // staged transposed (Vt[i][row]) so that both operands are 16-byte shared reads.
 template <typename T>
-__global__ void __launch_bounds__(kQT, 4) qr_apply_kernel(T* __restrict__ A, int64_t lda,
-                                                      int64_t m, int64_t k, int bw, int64_t nt,
-                                                      int64_t rc, const T* __restrict__ Y) {
+__global__ void __launch_bounds__(kQT, 3) qr_apply_kernel(T* __restrict__ A, int64_t lda,
+                                                         int64_t m, int64_t k, int bw, int64_t nt,
+                                                         int64_t rc, const T* __restrict__ Y) {
+  constexpr int NV = kQChunk * kQMaxBw / kQT;
   __shared__ __align__(16) T Ys[kQMaxBw][kQCB + 4];
   __shared__ __align__(16) T Vt[kQMaxBw][kQChunk + 4];
   const int tid = threadIdx.x, cg4 = 4 * (tid & 31), rg4 = 4 * (tid >> 5);
   const int64_t c0 = (int64_t)blockIdx.x * kQCB, p = blockIdx.y;
   const int64_t rbeg = k + p * rc, rend = min(m, rbeg + rc);
   const int64_t col0 = k + bw + c0;
-  for (int e = tid; e < kQMaxBw * kQCB; e += kQT) {
-    const int i = e / kQCB, cc = e % kQCB;
-    Ys[i][cc] = (i < bw && c0 + cc < nt) ? Y[(int64_t)i * nt + c0 + cc] : T(0);
+  {
+    constexpr int NY = kQMaxBw * kQCB / kQT;
+    T yv[NY];   // every load of Y's block in flight at once
+#pragma unroll
+    for (int t = 0; t < NY; ++t) {
+      const int e = tid + t * kQT, i = e / kQCB, cc = e % kQCB;
+      yv[t] = (i < bw && c0 + cc < nt) ? Y[(int64_t)i * nt + c0 + cc] : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < NY; ++t) {
+      const int e = tid + t * kQT;
+      Ys[e / kQCB][e % kQCB] = yv[t];
+    }
   }
-  for (int64_t r = rbeg; r < rend; r += kQChunk) {
-    // this thread's 4 x 4 entries of A and the chunk's V rows, every load before the barrier
-    T a[4][4];
+  // this thread's 4 x 4 entries of A and its share of the V rows for the next chunk, in flight
+  // during the current chunk's products
+  T pa[4][4], pv[NV];
+  auto fetch = [&](int64_t r) {
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
       const int64_t g = r + rg4 + x;
 #pragma unroll
       for (int y = 0; y < 4; ++y)
-        a[x][y] = (g < rend && c0 + cg4 + y < nt) ? A[g * lda + col0 + cg4 + y] : T(0);
+        pa[x][y] = (g < rend && c0 + cg4 + y < nt) ? A[g * lda + col0 + cg4 + y] : T(0);
     }
-    for (int e = tid; e < kQChunk * kQMaxBw; e += kQT) {
-      const int rr = e / kQMaxBw, i = e % kQMaxBw;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int e = tid + t * kQT, rr = e / kQMaxBw, i = e % kQMaxBw;
       const int64_t g = r + rr;
-      Vt[i][rr] = (g < rend && i < bw) ? qr_v(A, lda, k, g, i) : T(0);
+      pv[t] = (g < rend && i < bw) ? qr_v(A, lda, k, g, i) : T(0);
+    }
+  };
+  if (rbeg < rend) fetch(rbeg);
+  for (int64_t r = rbeg; r < rend; r += kQChunk) {
+    T a[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) a[x][y] = pa[x][y];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int e = tid + t * kQT;
+      Vt[e % kQMaxBw][e / kQMaxBw] = pv[t];
     }
     __syncthreads();
+    if (r + kQChunk < rend) fetch(r + kQChunk);
     T acc[4][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
