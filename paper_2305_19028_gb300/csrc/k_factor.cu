@@ -387,14 +387,16 @@ template <bool AK, bool BKM>
 __device__ __forceinline__ void gemm_mid_tile(
     int M, int N, int K, const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
     int64_t ldb, float* __restrict__ C, int64_t ldc, float alpha, float beta, int upper,
-    int mirror, int kfrom_i, int kto_j, int tile_i, int tile_j) {
+    int mirror, int kfrom_i, int kto_j, int tile_i, int tile_j, int kc_lo = 0,
+    int kc_hi = 1 << 30) {
   constexpr int BM = 64, BN = 64, BK = 16, LD = 68;
   __shared__ __align__(16) float As[2][BK][LD];
   __shared__ __align__(16) float Bs[2][BK][LD];
   const int i0 = tile_i * BM, j0 = tile_j * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   int k_lo = (kfrom_i == 1) ? (i0 / BK) * BK : (kfrom_i == 2 ? (j0 / BK) * BK : 0);
-  const int k_hi = kto_j ? min(K, j0 + BN) : K;
+  const int k_hi = min(kto_j ? min(K, j0 + BN) : K, kc_hi);   // (kc_*: one chunk of a split k)
+  k_lo = max(k_lo, kc_lo);
   if (k_lo > K) k_lo = K;
   // A: AK: row i = tid / 4, k = (tid & 3) * 4; else k = tid / 16, i = (tid & 15) * 4
   const int a_r = AK ? (tid >> 2) : ((tid & 15) * 4);
@@ -498,6 +500,72 @@ __global__ void __launch_bounds__(256) gemm_mid_kernel(
                          kfrom_i, kto_j, tile_i, tile_j);
 }
 
+// Split-k form of gemm_mid_kernel (FP32, beta = 0, no upper / mirror) for products with few
+// tiles and long k: chunk z of tile (I, J) of batch member b covers [k_lo + z kc, k_lo + (z+1) kc)
+// of the tile's own k range (k_lo, k_hi from kfrom_i / kto_j as in gemm_mid_tile); chunk 0 goes
+// to C, chunk z > 0 to part + (z - 1) pstride at C's offsets; gemm_splitk_reduce_kernel adds the
+// chunks in order and applies alpha. blockIdx.z = b nzc + z.
+template <bool AK, bool BKM>
+__global__ void __launch_bounds__(256) gemm_mid_splitk_kernel(
+    int M, int N, int K, const float* __restrict__ A, int64_t lda, int64_t sA,
+    const float* __restrict__ B, int64_t ldb, int64_t sB, float* __restrict__ C, int64_t ldc,
+    int64_t sC, float* __restrict__ part, int64_t pstride, int kc, int nzc, int kfrom_i,
+    int kto_j) {
+  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
+  const int b = blockIdx.z / nzc, z = blockIdx.z - b * nzc;
+  const int i0 = tile_i * 64, j0 = tile_j * 64;
+  const int klo = (kfrom_i == 1) ? i0 : (kfrom_i == 2 ? j0 : 0);
+  const int khi = kto_j ? min(K, j0 + 64) : K;
+  const int c0 = klo + z * kc;
+  if (c0 >= khi && z > 0) return;
+  float* out = (z == 0 ? C : part + (int64_t)(z - 1) * pstride) + (int64_t)b * sC;
+  gemm_mid_tile<AK, BKM>(M, N, K, A + (int64_t)b * sA, lda, B + (int64_t)b * sB, ldb, out, ldc,
+                         1.f, 0.f, 0, 0, kfrom_i, kto_j, tile_i, tile_j, c0, c0 + kc);
+}
+
+__global__ void gemm_splitk_reduce_kernel(int M, int N, int K, float* __restrict__ C, int64_t ldc,
+                                          int64_t sC, const float* __restrict__ part,
+                                          int64_t pstride, int kc, int kfrom_i, int kto_j,
+                                          float alpha) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (e >= (int64_t)M * N) return;
+  const int i = (int)(e / N), j = (int)(e - (int64_t)i * N);
+  const int i0 = (i / 64) * 64, j0 = (j / 64) * 64;
+  const int klo = (kfrom_i == 1) ? i0 : (kfrom_i == 2 ? j0 : 0);
+  const int khi = kto_j ? min(K, j0 + 64) : K;
+  const int nz = (khi > klo) ? (khi - klo + kc - 1) / kc : 1;
+  const int64_t off = (int64_t)b * sC + (int64_t)i * ldc + j;
+  float v = C[off];
+  for (int z = 1; z < nz; ++z) v += part[(int64_t)(z - 1) * pstride + off];
+  C[off] = alpha * v;
+}
+
+// C = alpha op(A) op(B) (beta = 0) through the split-k kernels when the grid of 64 x 64 tiles is
+// small and k long (part: kSplitChunks - 1 buffers of pstride floats, each covering C's extent);
+// returns false (nothing launched) when the product does not qualify.
+constexpr int kSplitChunks = 4;
+template <bool AK, bool BKM>
+bool gemm_splitk(int M, int N, int K, const float* A, int64_t lda, int64_t sA, const float* B,
+                 int64_t ldb, int64_t sB, float* C, int64_t ldc, int64_t sC, float alpha,
+                 int batch, int kfrom_i, int kto_j, float* part, int64_t pstride,
+                 cudaStream_t s) {
+  if (part == nullptr || M % 64 || N % 64 || K % 16 || lda % 4 || ldb % 4) return false;
+  const int64_t tiles = (int64_t)(M / 64) * (N / 64) * batch;
+  const int kc = std::max(256, (K / kSplitChunks + 63) / 64 * 64);
+  if (tiles >= 4 * 152 || K <= kc) return false;
+  const int nzc = (K + kc - 1) / kc;   // <= kSplitChunks
+  if ((int64_t)(batch - 1) * sC + (int64_t)(M - 1) * ldc + N > pstride) return false;
+  dim3 g((unsigned)(N / 64), (unsigned)(M / 64), (unsigned)(batch * nzc));
+  gemm_mid_splitk_kernel<AK, BKM><<<g, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC,
+                                                    part, pstride, kc, nzc, kfrom_i, kto_j);
+  dim3 gr((unsigned)(((int64_t)M * N + 255) / 256), (unsigned)batch);
+  gemm_splitk_reduce_kernel<<<gr, 256, 0, s>>>(M, N, K, C, ldc, sC, part, pstride, kc, kfrom_i,
+                                               kto_j, alpha);
+  count_launch(2);
+  return true;
+}
+
 template <typename Tin, typename Tc, bool AK, bool BKM>
 void gemm_simt(int M, int N, int K, const Tin* A, int64_t lda, int64_t sA, const Tin* B,
                int64_t ldb, int64_t sB, Tc* C, int64_t ldc, int64_t sC, Tc alpha, Tc beta,
@@ -558,6 +626,7 @@ __global__ void set_identity_pad_kernel(void* M, int fp64, int64_t n, int64_t np
 // Cholesky pieces (upper, H = R^T R), block size 64.
 // ---------------------------------------------------------------------------------------
 constexpr int NB = 64;
+constexpr int kPmChunks = 4;    // k chunks of the split preconditioner-matrix product
 constexpr int LDT = 68;   // row stride (floats) of the 64 x 64 FP32 tiles staged in shared memory
 
 template <typename T>
@@ -1405,7 +1474,7 @@ void launch_round_to(T* R, int64_t npad, Prec prec, cudaStream_t s) {
 
 template <typename T>
 void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, bool have_diag,
-                  cudaStream_t s) {
+                  cudaStream_t s, T* part) {
   if (!have_diag) {
     cudaMemsetAsync(W, 0, sizeof(T) * npad * npad, s);
     trtri_diag_kernel<T><<<(unsigned)(npad / NB), NB, 0, s>>>(R, W, npad); count_launch();
@@ -1417,13 +1486,26 @@ void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, bool have_diag
     if (full_pairs > 0) {
       // work_AB = R_AB W_BB ; W_AB = -W_AA work_AB   (batched over the full pairs)
       const int64_t st = 2 * sz * npad + 2 * sz;   // stride between pairs along the diagonal
-      // (W_BB and W_AA are upper triangular: the products skip their zero k-slabs)
-      gemm_simt<T, T, true, false>((int)sz, (int)sz, (int)sz, R + sz, npad, st, W + sz * npad + sz,
-                                   npad, st, work + sz, npad, st, T(1), T(0), 0, 0,
-                                   (int)full_pairs, s, nullptr, 0, 1);
-      gemm_simt<T, T, true, false>((int)sz, (int)sz, (int)sz, W, npad, st, work + sz, npad, st,
-                                   W + sz, npad, st, T(-1), T(0), 0, 0, (int)full_pairs, s,
-                                   nullptr, 1, 0);
+      // (W_BB and W_AA are upper triangular: the products skip their zero k-slabs; the top
+      // levels, with few tiles and long k, split k over more CTAs)
+      bool split = false;
+      if constexpr (std::is_same<T, float>::value)
+        split = gemm_splitk<true, false>((int)sz, (int)sz, (int)sz, R + sz, npad, st,
+                                         W + sz * npad + sz, npad, st, work + sz, npad, st, 1.f,
+                                         (int)full_pairs, 0, 1, part, npad * npad, s);
+      if (!split)
+        gemm_simt<T, T, true, false>((int)sz, (int)sz, (int)sz, R + sz, npad, st,
+                                     W + sz * npad + sz, npad, st, work + sz, npad, st, T(1),
+                                     T(0), 0, 0, (int)full_pairs, s, nullptr, 0, 1);
+      split = false;
+      if constexpr (std::is_same<T, float>::value)
+        split = gemm_splitk<true, false>((int)sz, (int)sz, (int)sz, W, npad, st, work + sz, npad,
+                                         st, W + sz, npad, st, -1.f, (int)full_pairs, 1, 0, part,
+                                         npad * npad, s);
+      if (!split)
+        gemm_simt<T, T, true, false>((int)sz, (int)sz, (int)sz, W, npad, st, work + sz, npad, st,
+                                     W + sz, npad, st, T(-1), T(0), 0, 0, (int)full_pairs, s,
+                                     nullptr, 1, 0);
     }
     const int64_t o = full_pairs * 2 * sz;
     const int64_t sB = npad - o - sz;
@@ -1457,19 +1539,65 @@ template void launch_cholesky<double>(double*, int64_t, int64_t, double, int*, d
                                       int);
 template void launch_round_to<float>(float*, int64_t, Prec, cudaStream_t);
 template void launch_round_to<double>(double*, int64_t, Prec, cudaStream_t);
-template void launch_trtri<float>(const float*, float*, float*, float*, int64_t, bool, cudaStream_t);
-template void launch_trtri<double>(const double*, double*, double*, double*, int64_t, bool, cudaStream_t);
+template void launch_trtri<float>(const float*, float*, float*, float*, int64_t, bool, cudaStream_t,
+                                  float*);
+template void launch_trtri<double>(const double*, double*, double*, double*, int64_t, bool,
+                                   cudaStream_t, double*);
 
 // The PCGTLS preconditioner as one matrix: M = D^{-1} (W W^T) D^{-1}, W = R_H^{-1} upper
 // triangular: (W W^T)_ij = sum over k >= max(i, j) of W_ik W_jk, so an upper tile (I <= J)
 // starts its k range at j0; mirrored to the lower triangle, FP32.
-void launch_precond_matrix(const float* W, const float* dinv, int64_t npad, float* M,
-                           cudaStream_t s) {
+// M = D^{-1} W W^T D^{-1} with the k sums split into chunks of kc (npad / kPmChunks rounded up
+// to 64, at least 512): upper 64 x 64 tile (I, J) sums over k >= 64 J (W upper triangular), so
+// the first tile columns carry sums of length n and the last of 64; chunk z of tile (I, J)
+// covers k in [64 J + z kc, + kc) (chunk 0 into M, chunk z > 0 into part[z - 1]), and
+// precond_reduce_kernel adds the chunks in order, scales by d_i^{-1} d_j^{-1} and mirrors. The
+// same products as one launch, the k sums regrouped by chunk.
+__global__ void __launch_bounds__(256) precond_splitk_kernel(const float* __restrict__ W,
+                                                             int64_t npad, float* __restrict__ M,
+                                                             float* __restrict__ part, int kc) {
+  const int tile_i = blockIdx.y, tile_j = blockIdx.x, z = blockIdx.z;
+  if (tile_i > tile_j) return;
+  const int k0 = tile_j * 64 + z * kc;
+  if (k0 >= npad) return;
+  float* out = (z == 0) ? M : part + (int64_t)(z - 1) * npad * npad;
   const int n = (int)npad;
-  gemm_simt<float, float, true, true>(n, n, n, W, npad, 0, W, npad, 0, M, npad, 0, 1.f, 0.f,
-                                      /*upper=*/1, /*mirror=*/1, 1, s, nullptr, /*kfrom_i=*/2, 0);
-  scale_two_sided_kernel<<<(unsigned)((npad * npad + 255) / 256), 256, 0, s>>>(M, dinv, npad);
-  count_launch();
+  gemm_mid_tile<true, true>(n, n, n, W, npad, W, npad, out, npad, 1.f, 0.f, /*upper=*/1,
+                            /*mirror=*/0, /*kfrom_i=*/2, 0, tile_i, tile_j, k0, k0 + kc);
+}
+
+__global__ void precond_reduce_kernel(float* __restrict__ M, const float* __restrict__ part,
+                                      const float* __restrict__ dinv, int64_t npad, int kc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npad * npad) return;
+  const int64_t i = e / npad, j = e - i * npad;
+  if (i > j) return;
+  const int64_t j0 = (j / 64) * 64;
+  const int nz = (int)((npad - j0 + kc - 1) / kc);
+  float v = M[e];
+  for (int z = 1; z < nz; ++z) v += part[(int64_t)(z - 1) * npad * npad + e];
+  v *= dinv[i] * dinv[j];
+  M[e] = v;
+  if (i != j) M[j * npad + i] = v;
+}
+
+void launch_precond_matrix(const float* W, const float* dinv, int64_t npad, float* M,
+                           cudaStream_t s, float* part) {
+  const int n = (int)npad;
+  const int kc = (int)std::max<int64_t>(512, (npad / kPmChunks + 63) / 64 * 64);
+  if (part == nullptr || npad <= kc) {
+    gemm_simt<float, float, true, true>(n, n, n, W, npad, 0, W, npad, 0, M, npad, 0, 1.f, 0.f,
+                                        /*upper=*/1, /*mirror=*/1, 1, s, nullptr, /*kfrom_i=*/2, 0);
+    scale_two_sided_kernel<<<(unsigned)((npad * npad + 255) / 256), 256, 0, s>>>(M, dinv, npad);
+    count_launch();
+    return;
+  }
+  const int nz = (int)((npad + kc - 1) / kc);   // <= kPmChunks: part holds kPmChunks - 1 matrices
+  dim3 g((unsigned)(npad / 64), (unsigned)(npad / 64), (unsigned)nz);
+  precond_splitk_kernel<<<g, 256, 0, s>>>(W, npad, M, part, kc);
+  precond_reduce_kernel<<<(unsigned)((npad * npad + 255) / 256), 256, 0, s>>>(M, part, dinv, npad,
+                                                                             kc);
+  count_launch(2);
 }
 
 }  // namespace tls

@@ -193,7 +193,7 @@ void dev_free(tls_ctx* c, void* p) {
 enum Slot : int {
   kSlotCpart, kSlotInfo, kSlotAsT, kSlotH, kSlotM, kSlotWc, kSlotR, kSlotW, kSlotWT, kSlotWork,
   kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotFeat, kSlotGsplit, kSlotPM,
-  kSlotQR, kSlotQRwork, kSlotCount
+  kSlotQR, kSlotQRwork, kSlotPMpart, kSlotCount
 };
 static_assert(kSlotCount <= 24, "slots");
 
@@ -431,9 +431,10 @@ tls_status run_pcg(tls_ctx* ctx, int nr, const double* fin0, double s0, const do
         set_err(ctx, "device allocation failed (preconditioner matrix)");
         return TLS_ERR_OOM;
       }
+      float* mpart = static_cast<float*>(slot(ctx, kSlotPMpart, sizeof(float) * 3 * (size_t)npad * npad));
       Prof pr(ctx, TLS_PROF_TRTRI);
       tls::launch_precond_matrix(reinterpret_cast<const float*>(W), ctx->dinv32, npad, ctx->PM,
-                                 ctx->stream);
+                                 ctx->stream, mpart);
       e = cudaGetLastError();
       ctx->pm_ready = (e == cudaSuccess);
     }
@@ -1220,9 +1221,11 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
         TLS_CK(cudaMemcpyAsync(ctx->R, M, 4 * cnt, cudaMemcpyDeviceToDevice, st));
         if (have_diag) TLS_CK(cudaMemcpyAsync(ctx->W, Wc, 4 * cnt, cudaMemcpyDeviceToDevice, st));
       }
+      float* tpart = static_cast<float*>(
+          slot(ctx, kSlotPMpart, sizeof(float) * 3 * (size_t)npad * (size_t)npad));
       tls::launch_trtri<float>(static_cast<float*>(ctx->R), static_cast<float*>(ctx->W),
                                static_cast<float*>(ctx->WT), static_cast<float*>(work), npad,
-                               have_diag, st);
+                               have_diag, st, tpart);
     }
     TLS_CK_LAUNCH("triangular inverse");
     ctx->uf_used = uf;

@@ -151,9 +151,10 @@ template <typename T>
 void launch_round_to(T* R, int64_t npad, Prec prec, cudaStream_t s);
 // W = R^{-1} (upper, npad x npad) and WT = W^T (row-major), both T. work: npad x npad T.
 // have_diag: W already holds the inverses of the 64 x 64 diagonal blocks and zeros elsewhere.
+// part (optional, FP32 only: 3 npad^2 elements): the top levels' long products split in k.
 template <typename T>
 void launch_trtri(const T* R, T* W, T* WT, T* work, int64_t npad, bool have_diag,
-                  cudaStream_t s);
+                  cudaStream_t s, T* part = nullptr);
 // Convert FP32 <-> FP64 square matrices (used for escalation / export).
 void launch_f2d(const float* in, double* out, int64_t count, cudaStream_t s);
 void launch_d2f(const double* in, float* out, int64_t count, cudaStream_t s);
@@ -266,8 +267,9 @@ cudaError_t launch_pcg_fused(const float* A, int64_t m, int64_t n, int64_t npad,
                              int num_sms, cudaStream_t st, unsigned long long* trace = nullptr,
                              int load_mode = 0, int64_t keep_bytes = 0, int pass_kind = 0);
 // M = D^{-1} W W^T D^{-1} (npad x npad, FP32) from W = R_H^{-1} (upper) and dinv = 1 / d.
+// part (optional, 3 npad^2 floats): the k sums split into up to four chunks over more CTAs.
 void launch_precond_matrix(const float* W, const float* dinv, int64_t npad, float* M,
-                           cudaStream_t s);
+                           cudaStream_t s, float* part = nullptr);
 // Words of the optional phase trace of the one-launch PCGTLS solve (see k_pcg_fused.cu).
 int pcg_fused_trace_words();
 // Reduction of the fused pass partials and the update w += alpha q, y = D^{-1}(A^T t - s2 q).
