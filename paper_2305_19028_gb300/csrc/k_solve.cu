@@ -1570,6 +1570,52 @@ __device__ __forceinline__ void df_fma(float ah, float al, float xh, float xl, f
   lo = __fadd_rn(lo, __fadd_rn(t, e));
 }
 
+// Two FP32 lanes per instruction (the packed f32x2 forms of sm_100 and later), each lane
+// rounded to nearest exactly as the scalar instruction: two independent double-FP32
+// accumulations for the issue slots of one. A lane pair is a 64-bit value, low lane first.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2pack(float lo, float hi) {
+  return ((f2_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float f2lo(f2_t v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
+__device__ __forceinline__ float f2hi(f2_t v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ f2_t f2add(f2_t a, f2_t b) {
+  f2_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t f2sub(f2_t a, f2_t b) {
+  f2_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t f2mul(f2_t a, f2_t b) {
+  f2_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t f2fma(f2_t a, f2_t b, f2_t c) {
+  f2_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f2_t f2neg(f2_t a) { return a ^ 0x8000000080000000ull; }
+
+// df_fma on both lanes, operation for operation: the product enters negated (pn = -p, exact),
+// so that e = fma(ah, xh, pn) and the TwoSum of hi and p = -pn are the scalar form's values
+__device__ __forceinline__ void df_fma2(f2_t ah, f2_t al, f2_t xh, f2_t xl, f2_t& hi,
+                                        f2_t& lo) {
+  const f2_t pn = f2mul(f2neg(ah), xh);
+  f2_t e = f2fma(ah, xh, pn);
+  e = f2fma(ah, xl, e);
+  e = f2fma(al, xh, e);
+  const f2_t sm = f2sub(hi, pn);                                   // hi + p
+  const f2_t bb = f2sub(sm, hi);
+  const f2_t t = f2sub(f2sub(hi, f2sub(sm, bb)), f2add(pn, bb));   // (hi - (s - bb)) + (p - bb)
+  hi = sm;
+  lo = f2add(lo, f2add(t, e));
+}
+
 // (hi, lo) += (bh, bl): the pair sum (TwoSum of the leading parts, the low parts added)
 __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
   float s, e;
@@ -1629,18 +1675,23 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
   __shared__ float2 rsm[2][RT];                // the tile's r_i as FP32 pairs
   __shared__ double sred[kDfWarps][2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // the thread's x values as FP32 pairs
-  float xh[VPT * 4], xl[VPT * 4];
+  // the thread's x values as FP32 pairs, packed by neighbouring columns (lanes: even, odd)
+  f2_t xh2[VPT * 2], xl2[VPT * 2];
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
     const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
+    float xh[4], xl[4];
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc)
-      f64_split_f32(col < npad ? x[col + cc] : 0.0, xh[v * 4 + cc], xl[v * 4 + cc]);
+    for (int cc = 0; cc < 4; ++cc) f64_split_f32(col < npad ? x[col + cc] : 0.0, xh[cc], xl[cc]);
+    xh2[2 * v] = f2pack(xh[0], xh[1]);
+    xh2[2 * v + 1] = f2pack(xh[2], xh[3]);
+    xl2[2 * v] = f2pack(xl[0], xl[1]);
+    xl2[2 * v + 1] = f2pack(xl[2], xl[3]);
   }
-  float ach[VPT * 4], acl[VPT * 4];
+  // the thread's column partials of A^T r, packed by neighbouring columns
+  f2_t ach2[VPT * 2], acl2[VPT * 2];
 #pragma unroll
-  for (int e = 0; e < VPT * 4; ++e) ach[e] = acl[e] = 0.f;
+  for (int e = 0; e < VPT * 2; ++e) ach2[e] = acl2[e] = 0ull;
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = min(m, (int64_t)blockIdx.x * per);
   const int64_t r1 = min(m, r0 + per);
@@ -1666,9 +1717,9 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
   if (tid == 0)
     for (int t = 0; t < stages && t < ntiles; ++t) issue(t);
   double rr = 0.0, br = 0.0;      // lane 0 of warps < RT: its rows' ||r||^2 and b^T r
-  float4 ph[RT][VPT], pl[RT][VPT];  // the previous tile (its axpy follows the barrier)
+  ulonglong2 ph[RT][VPT], pl[RT][VPT];  // the previous tile (its axpy follows the barrier)
   for (int t = 0; t <= ntiles; ++t) {
-    float4 ch[RT][VPT], cl[RT][VPT];
+    ulonglong2 ch[RT][VPT], cl[RT][VPT];   // four entries as two packed column pairs
     if (t < ntiles) {
       const int64_t i0 = r0 + (int64_t)t * RT;
       ptx::mbar_wait(&full[t % stages], (uint32_t)((t / stages) & 1), err, 12);
@@ -1678,20 +1729,22 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
       float dh[RT], dl[RT];
 #pragma unroll
       for (int rt = 0; rt < RT; ++rt) {
-        dh[rt] = dl[rt] = 0.f;
+        // the row's even and odd columns in the two lanes, the lanes added at the end
+        f2_t h2 = 0ull, l2 = 0ull;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
           const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
           const bool ok = rt < rows && col < npad;
-          ch[rt][v] = ok ? *reinterpret_cast<const float4*>(th + rt * npad + col)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-          cl[rt][v] = ok ? *reinterpret_cast<const float4*>(tl + rt * npad + col)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-          df_fma(ch[rt][v].x, cl[rt][v].x, xh[v * 4 + 0], xl[v * 4 + 0], dh[rt], dl[rt]);
-          df_fma(ch[rt][v].y, cl[rt][v].y, xh[v * 4 + 1], xl[v * 4 + 1], dh[rt], dl[rt]);
-          df_fma(ch[rt][v].z, cl[rt][v].z, xh[v * 4 + 2], xl[v * 4 + 2], dh[rt], dl[rt]);
-          df_fma(ch[rt][v].w, cl[rt][v].w, xh[v * 4 + 3], xl[v * 4 + 3], dh[rt], dl[rt]);
+          ch[rt][v] = ok ? *reinterpret_cast<const ulonglong2*>(th + rt * npad + col)
+                         : make_ulonglong2(0ull, 0ull);
+          cl[rt][v] = ok ? *reinterpret_cast<const ulonglong2*>(tl + rt * npad + col)
+                         : make_ulonglong2(0ull, 0ull);
+          df_fma2(ch[rt][v].x, cl[rt][v].x, xh2[2 * v], xl2[2 * v], h2, l2);
+          df_fma2(ch[rt][v].y, cl[rt][v].y, xh2[2 * v + 1], xl2[2 * v + 1], h2, l2);
         }
+        dh[rt] = f2lo(h2);
+        dl[rt] = f2lo(l2);
+        df_add(dh[rt], dl[rt], f2hi(h2), f2hi(l2));
       }
       float oh, ol;
       df_reduce_scatter<RT>(dh, dl, oh, ol);
@@ -1735,12 +1788,11 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
       for (int rt = 0; rt < RT; ++rt) {
         if (rt >= rows) break;
         const float2 rv = rsm[bb][rt];
+        const f2_t rh2 = f2pack(rv.x, rv.x), rl2 = f2pack(rv.y, rv.y);
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
-          df_fma(ph[rt][v].x, pl[rt][v].x, rv.x, rv.y, ach[v * 4 + 0], acl[v * 4 + 0]);
-          df_fma(ph[rt][v].y, pl[rt][v].y, rv.x, rv.y, ach[v * 4 + 1], acl[v * 4 + 1]);
-          df_fma(ph[rt][v].z, pl[rt][v].z, rv.x, rv.y, ach[v * 4 + 2], acl[v * 4 + 2]);
-          df_fma(ph[rt][v].w, pl[rt][v].w, rv.x, rv.y, ach[v * 4 + 3], acl[v * 4 + 3]);
+          df_fma2(ph[rt][v].x, pl[rt][v].x, rh2, rl2, ach2[2 * v], acl2[2 * v]);
+          df_fma2(ph[rt][v].y, pl[rt][v].y, rh2, rl2, ach2[2 * v + 1], acl2[2 * v + 1]);
         }
       }
     }
@@ -1760,10 +1812,9 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
     const int64_t col = ((int64_t)v * kDfThreads + tid) * 4;
     if (col < npad) {
       double2* dst = reinterpret_cast<double2*>(part + (int64_t)blockIdx.x * npad + col);
-      dst[0] = make_double2((double)ach[v * 4 + 0] + (double)acl[v * 4 + 0],
-                            (double)ach[v * 4 + 1] + (double)acl[v * 4 + 1]);
-      dst[1] = make_double2((double)ach[v * 4 + 2] + (double)acl[v * 4 + 2],
-                            (double)ach[v * 4 + 3] + (double)acl[v * 4 + 3]);
+      const f2_t h0 = ach2[2 * v], l0 = acl2[2 * v], h1 = ach2[2 * v + 1], l1 = acl2[2 * v + 1];
+      dst[0] = make_double2((double)f2lo(h0) + (double)f2lo(l0), (double)f2hi(h0) + (double)f2hi(l0));
+      dst[1] = make_double2((double)f2lo(h1) + (double)f2lo(l1), (double)f2hi(h1) + (double)f2hi(l1));
     }
   }
   if (lane == 0) {
