@@ -1718,7 +1718,13 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
     for (int t = 0; t < stages && t < ntiles; ++t) issue(t);
   double rr = 0.0, br = 0.0;      // lane 0 of warps < RT: its rows' ||r||^2 and b^T r
   ulonglong2 ph[RT][VPT], pl[RT][VPT];  // the previous tile (its axpy follows the barrier)
+  double bn = 0.0;   // lane 0 of warp w < RT: b of row w of the tile whose r comes next
   for (int t = 0; t <= ntiles; ++t) {
+    const double bc = bn;   // b of row `warp` of tile t - 1, loaded one tile ahead
+    if (lane == 0 && warp < RT && t < ntiles) {
+      const int64_t nrow = r0 + (int64_t)t * RT + warp;
+      bn = (nrow < r1) ? b[nrow] : 0.0;
+    }
     ulonglong2 ch[RT][VPT], cl[RT][VPT];   // four entries as two packed column pairs
     if (t < ntiles) {
       const int64_t i0 = r0 + (int64_t)t * RT;
@@ -1765,12 +1771,12 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
         float2 rv = make_float2(0.f, 0.f);
         if (row < r1) {
           float bh, bl;
-          f64_split_f32(b[row], bh, bl);
+          f64_split_f32(bc, bh, bl);
           df_add(bh, bl, -q.x, -q.y);            // r = b - A_i x as a pair,
           two_sum(bh, bl, rv.x, rv.y);           // renormalised for the products that follow
           const double r = (double)rv.x + (double)rv.y;
           rr = fma(r, r, rr);
-          br = fma(b[row], r, br);
+          br = fma(bc, r, br);
         }
         rsm[bb][warp] = rv;
       }
