@@ -281,7 +281,7 @@ RESID_PIPE_TRAFFIC_PER_ROW = (134.346e6 + 0.067e6) / 8192
 # ncu capture in profiles/resid_df_dense_16384x2048.md), and of the one-launch paired PCGTLS
 # solve per paired iteration at the same size (profiles/pcg_fused_dense_16384x2048.md: 419.96 MB
 # for a launch of 3 iterations)
-RESID_DF_TRAFFIC_C2 = 268.643584e6 + 3.102208e6
+RESID_DF_TRAFFIC_C2 = 268.641792e6 + 2.953216e6
 PCG_FUSED_TRAFFIC_PER_ITER_C2 = (416.771072e6 + 3.188480e6) / 3
 
 
