@@ -1113,9 +1113,14 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
     {
       Prof pr(ctx, TLS_PROF_GRAM);
       bool tc = false;
-      if ((pf == Prec::FP16 || pf == Prec::BF16) && !ctx->opt.gram_simt)
+      if ((pf == Prec::FP16 || pf == Prec::BF16) && !ctx->opt.gram_simt) {
+        // (the partial sums use the buffer of the preconditioner matrix's split products,
+        // free until the inverse)
+        float* gpart = static_cast<float*>(
+            slot(ctx, kSlotPMpart, sizeof(float) * 3 * (size_t)npad * (size_t)npad));
         tc = tls::launch_gram_tc(AsT, pf, n, npad, mpad, static_cast<float*>(ctx->H), ctx->derr,
-                                 st);
+                                 st, gpart);
+      }
       if (tc) {
         const int terr = tls::gram_tc_error(ctx->derr, st);   // synchronises the stream
         if (terr != 0) {

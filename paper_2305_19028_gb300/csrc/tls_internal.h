@@ -124,9 +124,10 @@ void launch_gram_simt(const void* AsT, Prec prec, int64_t n, int64_t npad, int64
 // device's multiprocessor count) and at most 32 MB of partials in all; 1 when npad > 128.
 int gram_split_chunks(int64_t npad, int64_t mpad, int num_sms);
 // tcgen05 (UMMA) Gram for FP16/BF16 input into FP32 H. Returns false if the shape is not
-// supported (falls back to nothing: the caller decides).
+// supported (falls back to nothing: the caller decides). part (optional, npad^2 floats): the
+// 128 x 256-tile form with the K range in two halves (npad a multiple of 256).
 bool launch_gram_tc(const void* AsT, Prec prec, int64_t n, int64_t npad, int64_t mpad,
-                    float* H, int* err, cudaStream_t s);
+                    float* H, int* err, cudaStream_t s, float* part = nullptr);
 // 1 if the tensor-core path can run on the current device (sm_103 and a tensor-map encoder).
 bool gram_tc_available();
 // Error code recorded in *err by a bounded wait of the tensor-core kernel (0: none); resets it.
