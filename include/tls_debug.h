@@ -140,6 +140,15 @@ tls_status tls_set_pcg_l2_keep(tls_ctx* ctx, int64_t bytes);
  */
 tls_status tls_set_factor_chain(tls_ctx* ctx, int on);
 /*
+ * tls_set_factor_tc -- 1 (default): for FP16 / BF16 factors, the trailing updates of the block
+ * steps that run before the persistent chain (trailing matrices of more than about four 64 x 64
+ * tiles per SM, i.e. n above about 2200) go to the tensor cores: the panel rows rounded to u_f
+ * (the rows of R-hat the factor keeps), tcgen05 MMAs with FP32 accumulation, the next diagonal
+ * block factored by the CTA of the first tile. 0: FP32 updates on the CUDA cores. Kept until
+ * changed.
+ */
+tls_status tls_set_factor_tc(tls_ctx* ctx, int on);
+/*
  * tls_trace_enable / tls_trace_get -- phase timestamps (global timer, ns) of the one-launch
  * PCGTLS solve, recorded by CTA 0 into a device buffer of the context when on (the last solve
  * overwrites them): out[0] the launch's start, out[1] the end of the initialisation, then ten

@@ -5,6 +5,7 @@
 #include "tls_internal.h"
 #include "tls_device.cuh"
 #include "tls_ptx.cuh"
+#include "tls_tc.cuh"
 #include "chol64.cuh"
 
 #include <algorithm>
@@ -828,6 +829,137 @@ __global__ void __launch_bounds__(256) chol_update_next_kernel(float* M, float* 
   potrf_inv_diag_body<float>(M, W, npad, k2, info, prec, dsm);
 }
 
+// ---------------------------------------------------------------------------------------
+// Trailing update on the tensor cores (FP16 / BF16 factors, block steps before the persistent
+// chain): H22 -= R_K2^T R_K2 with the panel rows R_K2 rounded to u_f, which are the rows of
+// R-hat that the factor keeps, accumulated in FP32 in TMEM.
+// ---------------------------------------------------------------------------------------
+// PT[j][k] = u_f(R_K2[k][j]) (j < n2, k < 64; rows n2 .. up to the next multiple of 64 zero):
+// the panel transposed, K-major for the MMA, through a 64 x 64 shared-memory tile.
+template <typename Tq>
+__global__ void __launch_bounds__(256) chol_pt_kernel(const float* __restrict__ M, int64_t npad,
+                                                      int64_t kb, int n2, Tq* __restrict__ PT) {
+  __shared__ float tl[NB][NB + 1];
+  const int j0 = blockIdx.x * NB, tid = threadIdx.x;
+  const float* P = M + kb * npad + kb + NB;
+  for (int e = tid; e < NB * NB; e += 256) {
+    const int k = e / NB, j = e % NB;
+    tl[k][j] = (j0 + j < n2) ? P[(int64_t)k * npad + j0 + j] : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += 256) {
+    const int j = e / NB, k = e % NB;
+    PT[(int64_t)(j0 + j) * NB + k] = cvt_out_f<Tq>(tl[k][j]);
+  }
+}
+
+// CTA (I, J), I <= J, of the 128 x 128 tiles of H22 (n2 x n2 at (k2, k2), k2 = kb + 64): one
+// TMA box of each 128-row strip of PT (64 wide, 128-byte swizzle), four MMAs (M = N = 128,
+// K = 16) into 128 TMEM columns, and the epilogue subtracts the tile from H22 on and above the
+// diagonal. The CTA of tile (0, 0), whose top left is the next diagonal block, then factors and
+// inverts that block as chol_update_next_kernel does. Waits are bounded (codes 21-23 in *err).
+constexpr int kTcThreads = 256;
+constexpr size_t kTcSmem = 2 * sizeof(float) * NB * (NB + 1) + 1024;   // >= 32 KB of strips
+__global__ void __launch_bounds__(kTcThreads, 1) chol_tc_update_kernel(
+    const __grid_constant__ CUtensorMap pt, float* M, float* W, int64_t npad, int64_t kb,
+    int n2, int* info, int prec, uint32_t idesc, int* err) {
+  if (*(volatile int*)info != 0) return;   // an earlier block broke down (uniform)
+  const int tile_i = blockIdx.y, tile_j = blockIdx.x;
+  if (tile_i > tile_j) return;
+  extern __shared__ __align__(1024) unsigned char dsm_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + 128 * NB * 2;
+  __shared__ uint64_t full_bar, acc_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const bool diag = (tile_i == tile_j);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k2 = kb + NB;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&full_bar, 1);
+    ptx::mbar_init(&acc_bar, 1);
+    abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     ptx::smem_u32(&tmem_base)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  if (warp == 0 && lane == 0) {
+    ptx::mbar_expect_tx(&full_bar, diag ? 128 * NB * 2 : 2 * 128 * NB * 2);
+    tc::tma_load_2d(sA, &pt, &full_bar, 0, tile_i * 128);
+    if (!diag) tc::tma_load_2d(sB, &pt, &full_bar, 0, tile_j * 128);
+    // the copies have landed before this CTA's shared memory is reused or released
+    if (!ptx::mbar_wait(&full_bar, 0, err, 21)) abort_flag = 1;
+  } else if (warp == 1 && lane == 0) {
+    const bool ok = ptx::mbar_wait(&full_bar, 0, err, 22);
+    if (ok) {
+      tc::tc_fence_after();
+      const uint32_t a0 = ptx::smem_u32(sA);
+      const uint32_t b0 = diag ? a0 : ptx::smem_u32(sB);
+#pragma unroll
+      for (int kk = 0; kk < NB / 16; ++kk)
+        tc::umma_f16(tmem, tc::sw128_desc(a0 + kk * 32), tc::sw128_desc(b0 + kk * 32), idesc,
+                     kk != 0 ? 1u : 0u);
+    } else {
+      abort_flag = 1;
+    }
+    tc::umma_commit(&acc_bar);
+  } else if (warp >= 2 && warp < 6) {
+    const int q = warp & 3;   // TMEM lane quadrant of this warp
+    const bool mine = ptx::mbar_wait(&acc_bar, 0, err, 23);
+    const bool ready = __all_sync(0xffffffffu, mine) && !*(volatile int*)&abort_flag;
+    tc::tc_fence_after();
+    if (ready) {
+      const int r = tile_i * 128 + q * 32 + lane;   // row of H22
+#pragma unroll 1
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        uint32_t acc[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, acc);
+        const int cb = tile_j * 128 + c0;
+        if (r < n2 && cb < n2 && cb + 31 >= r) {
+          float* dst = M + (k2 + r) * npad + k2 + cb;
+          if (cb >= r && cb + 31 < n2) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              float4 o = reinterpret_cast<float4*>(dst)[v];
+              o.x -= __uint_as_float(acc[4 * v]);
+              o.y -= __uint_as_float(acc[4 * v + 1]);
+              o.z -= __uint_as_float(acc[4 * v + 2]);
+              o.w -= __uint_as_float(acc[4 * v + 3]);
+              reinterpret_cast<float4*>(dst)[v] = o;
+            }
+          } else {
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc)
+              if (cb + cc >= r && cb + cc < n2) dst[cc] -= __uint_as_float(acc[cc]);
+          }
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc::tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
+                 : "memory");
+  }
+  if (tile_i != 0 || tile_j != 0 || abort_flag) return;
+  __syncthreads();   // the updated block (written by this CTA) before it is factored
+  potrf_inv_diag_body<float>(M, W, npad, k2, info, prec, smem);
+}
+
 // acc += As^T Bs over k < 64 for the 4 x 4 outputs of this thread (rows 4 ty .. +3, columns
 // 4 tx .. +3; tx = tid % 16, ty = tid / 16; 256 threads); As[k][i], Bs[k][j] in shared memory
 // with row stride LDT (float4 reads).
@@ -1355,7 +1487,7 @@ void launch_set_identity_pad(void* M, bool fp64, int64_t n, int64_t npad, cudaSt
 template <typename T>
 void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* Wd, Prec prec,
                      cudaStream_t s, unsigned int* gbar, int* err, int num_sms,
-                     unsigned long long* trace, int chain_per_sm) {
+                     unsigned long long* trace, int chain_per_sm, void* ptbuf) {
   // (chain_per_sm 2 measured best at n = 2048: 756 us per factor against 807 us for 3 or 4
   // CTAs per SM and 838 us with one launch per block step)
   if (shift != 0.0) { add_shift_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(M, n, npad, shift); count_launch(); }
@@ -1436,6 +1568,35 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
                                   0, T(1), T(0), 0, 0, 1, s, info);
     // trailing update H22 -= R_K2^T R_K2 (upper part), then the next diagonal block
     if constexpr (fused) {
+      if (ptbuf != nullptr && err != nullptr && (prec == Prec::FP16 || prec == Prec::BF16) &&
+          gram_tc_available()) {
+        // on the tensor cores: the panel rounded to u_f and transposed, then the update
+        const bool bf = (prec == Prec::BF16);
+        const int ntp = (int)((n2 + NB - 1) / NB);
+        if (bf)
+          chol_pt_kernel<__nv_bfloat16><<<ntp, 256, 0, s>>>(
+              reinterpret_cast<const float*>(M), npad, kb, (int)n2,
+              static_cast<__nv_bfloat16*>(ptbuf));
+        else
+          chol_pt_kernel<__half><<<ntp, 256, 0, s>>>(reinterpret_cast<const float*>(M), npad, kb,
+                                                     (int)n2, static_cast<__half*>(ptbuf));
+        CUtensorMap map;
+        if (tc::encode_kmajor_map(&map, ptbuf, bf, NB, (uint64_t)ntp * NB, NB * 2, NB, 128)) {
+          static const bool attr_tc = [] {
+            cudaFuncSetAttribute(chol_tc_update_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+            return true;
+          }();
+          (void)attr_tc;
+          const unsigned nt = (unsigned)((n2 + 127) / 128);
+          chol_tc_update_kernel<<<dim3(nt, nt), kTcThreads, kTcSmem, s>>>(
+              map, reinterpret_cast<float*>(M), reinterpret_cast<float*>(Wd), npad, kb, (int)n2,
+              info, (int)prec, tc::idesc_f16_mn(bf ? 1u : 0u, 128, 128), err);
+          count_launch(2);
+          continue;
+        }
+        count_launch();
+      }
       // 128 x 128 tiles once they still give about two CTAs per SM
       if (n2 >= 2048) {
         const unsigned nt = (unsigned)((n2 + 127) / 128);
@@ -1533,10 +1694,10 @@ void launch_d2f(const double* in, float* out, int64_t count, cudaStream_t s) {
 
 template void launch_cholesky<float>(float*, int64_t, int64_t, double, int*, float*, Prec,
                                      cudaStream_t, unsigned int*, int*, int, unsigned long long*,
-                                     int);
+                                     int, void*);
 template void launch_cholesky<double>(double*, int64_t, int64_t, double, int*, double*, Prec,
                                       cudaStream_t, unsigned int*, int*, int, unsigned long long*,
-                                      int);
+                                      int, void*);
 template void launch_round_to<float>(float*, int64_t, Prec, cudaStream_t);
 template void launch_round_to<double>(double*, int64_t, Prec, cudaStream_t);
 template void launch_trtri<float>(const float*, float*, float*, float*, int64_t, bool, cudaStream_t,

@@ -17,6 +17,7 @@
 // error code, stops issuing work, frees its TMEM and returns (the host then falls back).
 #include "tls_internal.h"
 #include "tls_ptx.cuh"
+#include "tls_tc.cuh"
 
 #include <cuda.h>
 
@@ -33,70 +34,19 @@ constexpr int STAGES = 6;
 constexpr int STAGE_BYTES = TBM * TBK * 2;        // 16 KB per operand per stage
 constexpr int THREADS = 192;
 
-// the mbarrier helpers (bounded waits) shared with the other TMA kernels
+// the mbarrier helpers (bounded waits) and the tcgen05 / TMA building blocks shared with the
+// other tensor-core kernels
 using ptx::mbar_expect_tx;
 using ptx::mbar_init;
 using ptx::mbar_wait;
 using ptx::smem_u32;
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
-  d |= (uint64_t)(16u >> 4) << 16;                    // leading byte offset (unused here)
-  d |= (uint64_t)(1024u >> 4) << 32;                  // stride byte offset
-  d |= (uint64_t)1 << 46;                             // descriptor version
-  d |= (uint64_t)2 << 61;                             // 128-byte swizzle
-  return d;
-}
-
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-      "%28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+using tc::sw128_desc;
+using tc::tc_fence_after;
+using tc::tc_fence_before;
+using tc::tma_load_2d;
+using tc::tmem_ld32;
+using tc::umma_commit;
+using tc::umma_f16;
 
 // Instruction descriptor for kind::f16: D = FP32, A/B = FP16 (fmt 0) or BF16 (fmt 1), both
 // K-major, M = 128, N = 128.
@@ -418,6 +368,24 @@ EncodeTiledFn get_encoder() {
 }
 
 }  // namespace
+
+namespace tc {
+bool encode_kmajor_map(CUtensorMap* map, const void* base, bool bf16, uint64_t k_extent,
+                       uint64_t rows, uint64_t row_bytes, uint32_t box_k, uint32_t box_rows) {
+  EncodeTiledFn enc = get_encoder();
+  if (enc == nullptr || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || row_bytes % 16 != 0)
+    return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)k_extent, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)row_bytes};
+  const cuuint32_t box[2] = {box_k, box_rows};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+             const_cast<void*>(base), gdim, gstride, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+}  // namespace tc
 
 bool gram_tc_available() {
   int dev = 0, major = 0, minor = 0;

@@ -52,6 +52,7 @@ struct tls_ctx {
   int64_t l2_keep = 0;     // bytes of A the one-launch solve keeps resident in L2
   unsigned int* fbar = nullptr;   // kBarWords barrier words: [0], [64] the one-launch solve's
                                   // counter and abort word; from [128] the persistent Cholesky's
+  int chol_tc = 1;                // trailing updates before the chain on the tensor cores
   int chol_chain = 2;             // block steps of the FP32 factor in one persistent launch
                                   // (up to this many CTAs per SM; 0: one launch per step)
   RqiScalars* h_norm = nullptr;   // pinned: ||A||_F^2 (xx) and ||b||^2 read back after the factor
@@ -193,7 +194,7 @@ void dev_free(tls_ctx* c, void* p) {
 enum Slot : int {
   kSlotCpart, kSlotInfo, kSlotAsT, kSlotH, kSlotM, kSlotWc, kSlotR, kSlotW, kSlotWT, kSlotWork,
   kSlotVbuf, kSlotPart, kSlotTbuf, kSlotCond, kSlotNorm, kSlotFeat, kSlotGsplit, kSlotPM,
-  kSlotQR, kSlotQRwork, kSlotPMpart, kSlotCount
+  kSlotQR, kSlotQRwork, kSlotPMpart, kSlotPT, kSlotCount
 };
 static_assert(kSlotCount <= 24, "slots");
 
@@ -1164,7 +1165,9 @@ tls_status factor_impl(tls_ctx* ctx, tls_prec uf_req) {
                                       static_cast<float*>(Wc), pf, st,
                                       ctx->chol_chain ? ctx->fbar + 128 : nullptr, ctx->derr,
                                       ctx->num_sms, ctx->trace_on ? ctx->trace : nullptr,
-                                      ctx->chol_chain);
+                                      ctx->chol_chain,
+                                      ctx->chol_tc ? slot(ctx, kSlotPT, 2 * 64 * (size_t)npad)
+                                                   : nullptr);
       }
       TLS_CK_LAUNCH("cholesky");
       int hinfo = 0, herr = 0;
@@ -1929,6 +1932,12 @@ tls_status tls_profile_units(const tls_ctx* ctx, int cls, int64_t* units) {
 tls_status tls_set_factor_chain(tls_ctx* ctx, int on) {
   if (!ctx || on < 0 || on > 4) return TLS_ERR_ARG;
   ctx->chol_chain = on;
+  return TLS_OK;
+}
+
+tls_status tls_set_factor_tc(tls_ctx* ctx, int on) {
+  if (!ctx || on < 0 || on > 1) return TLS_ERR_ARG;
+  ctx->chol_tc = on;
   return TLS_OK;
 }
 

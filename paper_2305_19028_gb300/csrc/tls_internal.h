@@ -142,11 +142,13 @@ int gram_tc_error(int* err, cudaStream_t s);
 // chain_per_sm x num_sms CTAs instead of one launch per step. trace (optional, 256 zeroed words): per block
 // step s < 64 of that launch, at 4 s: CTA 0's start, its tile done, its diagonal block done,
 // the last tile worker done (global-timer ns).
+// ptbuf (optional, npad x 64 halves): FP16 / BF16 factors run the trailing updates of the block
+// steps before the chain on the tensor cores (the panel rounded to u_f, FP32 accumulation).
 template <typename T>
 void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* Wd, Prec prec,
                      cudaStream_t s, unsigned int* gbar = nullptr, int* err = nullptr,
                      int num_sms = 0, unsigned long long* trace = nullptr,
-                     int chain_per_sm = 2);
+                     int chain_per_sm = 2, void* ptbuf = nullptr);
 // Round the upper triangle of R (T) to prec in place (FP16/BF16); no-op for FP32/FP64.
 template <typename T>
 void launch_round_to(T* R, int64_t npad, Prec prec, cudaStream_t s);

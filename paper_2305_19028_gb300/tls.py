@@ -40,7 +40,7 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_set_selector", "tls_features", "tls_pool_enable", "tls_pool_trim",
            "tls_pool_stats", "tls_pool_poison", "tls_set_small_path", "tls_profile_units",
            "tls_set_pcg_fused", "tls_trace_enable", "tls_trace_get", "tls_set_pcg_l2_keep",
-           "tls_set_factor_chain"]
+           "tls_set_factor_chain", "tls_set_factor_tc"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec", "pcg_solve2", "pcg_solve1"]
@@ -157,6 +157,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_trace_enable": (C.c_int, [v, C.c_int]),
         "tls_set_pcg_l2_keep": (C.c_int, [v, i64]),
         "tls_set_factor_chain": (C.c_int, [v, C.c_int]),
+        "tls_set_factor_tc": (C.c_int, [v, C.c_int]),
         "tls_trace_get": (C.c_int, [v, C.POINTER(C.c_uint64), C.c_int, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -404,6 +405,12 @@ def tls_set_factor_chain(ctx, per_sm: int) -> None:
     """Block steps of the FP32 factor in one persistent launch of up to per_sm CTAs per SM
     (default 2), or one launch each (0)."""
     _check(load().tls_set_factor_chain(ctx, int(per_sm)), ctx)
+
+
+def tls_set_factor_tc(ctx, on: int) -> None:
+    """Trailing updates of the wide block steps of an FP16/BF16 factor on the tensor cores (1,
+    default) or on the CUDA cores in FP32 (0)."""
+    _check(load().tls_set_factor_tc(ctx, int(on)), ctx)
 
 
 def tls_set_pcg_l2_keep(ctx, nbytes: int) -> None:

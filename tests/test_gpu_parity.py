@@ -142,6 +142,40 @@ def test_factor_chain_matches_one_launch_per_step(m, n):
             assert np.array_equal(np.asarray(a_), np.asarray(b_))
 
 
+@pytest.mark.parametrize("u_f", ["fp16", "bf16"])
+def test_tensor_core_trailing_updates_match_definitions(u_f):
+    """n = 2500 (n_pad = 2560): the first block steps, whose trailing matrices are too large for
+    the persistent chain, update on the tensor cores with the panel rows rounded to u_f (FP32
+    accumulation); the factor meets the same backward-error bound as the FP32 CUDA-core updates
+    (R_H^T R_H = H up to 4 u_f sqrt(n) + n u_32 of ||H||), is upper triangular and representable
+    in u_f, and its solve still reaches the oracle's answer."""
+    m, n = 3000, 2500
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=9)
+    ufac = {"fp16": U16, "bf16": UBF}[u_f]
+    res = {}
+    for tcu in (1, 0):
+        ctx = tls.tls_create_dense(p.A, p.b)
+        try:
+            tls.tls_set_factor_tc(ctx, tcu)
+            tls.tls_factor(ctx, u_f, tls.tls_default_options(u="fp32"))
+            R, d, H = tls.tls_export_factor(ctx)
+            x, sigma, info = tls.tls_solve(ctx, tol=0.0, max_rqi=12)
+        finally:
+            tls.tls_destroy(ctx)
+        res[tcu] = (R, H, x, sigma)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    for tcu, (R, H, x, sigma) in res.items():
+        assert np.array_equal(R, np.triu(R))
+        if u_f == "fp16":
+            assert np.array_equal(R, R.astype(np.float16).astype(np.float64))
+        berr = np.linalg.norm(R.T @ R - H) / np.linalg.norm(H)
+        assert berr <= 4 * ufac * np.sqrt(n) + n * U32, (tcu, berr)
+        assert abs(sigma - so) <= 1e-10 * so, (tcu, sigma, so)
+        assert _rel(x, xo) <= 1e-8, tcu
+    # the same Gram matrix enters both factors
+    assert np.array_equal(res[0][1], res[1][1])
+
+
 @pytest.mark.parametrize("u_f,u", [("fp16", "fp32"), ("bf16", "fp32"), ("fp32", "fp32"),
                                    ("fp64", "fp64")])
 @pytest.mark.parametrize("m,n", [(300, 64), (777, 130)])
