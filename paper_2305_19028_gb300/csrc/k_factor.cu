@@ -835,22 +835,28 @@ __global__ void __launch_bounds__(256) chol_update_next_kernel(float* M, float* 
 // R-hat that the factor keeps, accumulated in FP32 in TMEM.
 // ---------------------------------------------------------------------------------------
 // PT[j][k] = u_f(R_K2[k][j]) (j < n2, k < 64; rows n2 .. up to the next multiple of 64 zero):
-// the panel transposed, K-major for the MMA, through a 64 x 64 shared-memory tile.
+// the panel transposed, K-major for the MMA, through a 64 x 32 shared-memory tile per CTA (each
+// thread's eight loads in flight together).
 template <typename Tq>
 __global__ void __launch_bounds__(256) chol_pt_kernel(const float* __restrict__ M, int64_t npad,
                                                       int64_t kb, int n2, Tq* __restrict__ PT) {
-  __shared__ float tl[NB][NB + 1];
-  const int j0 = blockIdx.x * NB, tid = threadIdx.x;
+  __shared__ float tl[NB][33];
+  const int j0 = blockIdx.x * 32, tid = threadIdx.x, jj = tid & 31, k0 = tid >> 5;
   const float* P = M + kb * npad + kb + NB;
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int k = e / NB, j = e % NB;
-    tl[k][j] = (j0 + j < n2) ? P[(int64_t)k * npad + j0 + j] : 0.f;
+  float v[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int k = k0 + 8 * t;
+    v[t] = (j0 + jj < n2) ? P[(int64_t)k * npad + j0 + jj] : 0.f;
   }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) tl[k0 + 8 * t][jj] = v[t];
   __syncthreads();
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int j = e / NB, k = e % NB;
-    PT[(int64_t)(j0 + j) * NB + k] = cvt_out_f<Tq>(tl[k][j]);
-  }
+  // row j0 + j of PT: 64 values, 8 per thread of a 8-thread group
+  const int j = tid >> 3, kq = (tid & 7) * 8;
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    PT[(int64_t)(j0 + j) * NB + kq + t] = cvt_out_f<Tq>(tl[kq + t][j]);
 }
 
 // CTA (I, J), I <= J, of the 128 x 128 tiles of H22 (n2 x n2 at (k2, k2), k2 = kb + 64): one
@@ -1573,12 +1579,13 @@ void launch_cholesky(T* M, int64_t n, int64_t npad, double shift, int* info, T* 
         // on the tensor cores: the panel rounded to u_f and transposed, then the update
         const bool bf = (prec == Prec::BF16);
         const int ntp = (int)((n2 + NB - 1) / NB);
+        const unsigned gpt = (unsigned)(ntp * NB / 32);
         if (bf)
-          chol_pt_kernel<__nv_bfloat16><<<ntp, 256, 0, s>>>(
+          chol_pt_kernel<__nv_bfloat16><<<gpt, 256, 0, s>>>(
               reinterpret_cast<const float*>(M), npad, kb, (int)n2,
               static_cast<__nv_bfloat16*>(ptbuf));
         else
-          chol_pt_kernel<__half><<<ntp, 256, 0, s>>>(reinterpret_cast<const float*>(M), npad, kb,
+          chol_pt_kernel<__half><<<gpt, 256, 0, s>>>(reinterpret_cast<const float*>(M), npad, kb,
                                                      (int)n2, static_cast<__half*>(ptbuf));
         CUtensorMap map;
         if (tc::encode_kmajor_map(&map, ptbuf, bf, NB, (uint64_t)ntp * NB, NB * 2, NB, 128)) {
