@@ -61,6 +61,13 @@ tls_status tls_pcgtls(tls_ctx* ctx, int nr, double sigma2, const double* f0, con
  * y, s0, u: n values (host); s0 or u may be NULL.
  */
 tls_status tls_precond(tls_ctx* ctx, const double* y, double* s0, double* u);
+/*
+ * tls_precond_trsv -- the same two quantities by triangular solves with the factor itself
+ * (Alg. 3's R^{-T} and R^{-1}, R = R_H D): blocked substitution on R_H in precision u, one CTA,
+ * the reference for the products with the explicit inverse that the solve uses. n_pad is
+ * limited by one CTA's shared memory (8192 FP32, 4096 FP64 columns: TLS_ERR_ARG above).
+ */
+tls_status tls_precond_trsv(tls_ctx* ctx, const double* y, double* s0, double* u);
 
 /* Kernel classes timed by the profiler. */
 enum {

@@ -1330,6 +1330,30 @@ static tls_status precond_host(tls_ctx* ctx, const double* y, double* s0, double
   return TLS_OK;
 }
 
+template <typename T>
+static tls_status precond_trsv_host(tls_ctx* ctx, const double* y, double* s0, double* u) {
+  cudaStream_t st = ctx->stream;
+  const int64_t n = ctx->n, npad = ctx->npad;
+  TLS_CK(cudaMemsetAsync(ctx->f, 0, sizeof(double) * npad, st));
+  TLS_CK(cudaMemcpyAsync(ctx->f, y, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  UVecs<T> v = uvecs<T>(ctx);
+  const T* dinvT = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)ctx->dinv32
+                                                             : (const void*)ctx->dinv);
+  if (!tls::launch_trsv<T>(static_cast<const T*>(ctx->R), npad, n, dinvT, ctx->f, v.s, v.q, st)) {
+    set_err(ctx, "triangular solve: n too large for one CTA's shared memory");
+    return TLS_ERR_ARG;
+  }
+  std::vector<T> hs(npad), hq(npad);
+  TLS_CK(cudaMemcpyAsync(hs.data(), v.s, sizeof(T) * npad, cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaMemcpyAsync(hq.data(), v.q, sizeof(T) * npad, cudaMemcpyDeviceToHost, st));
+  TLS_CK(cudaStreamSynchronize(st));
+  for (int64_t j = 0; j < n; ++j) {
+    if (s0) s0[j] = (double)hs[j];
+    if (u) u[j] = (double)hq[j];
+  }
+  return TLS_OK;
+}
+
 template <typename TH, typename TU>
 static tls_status condition_impl(tls_ctx* ctx, int iters, double* out) {
   cudaStream_t st = ctx->stream;
@@ -2047,6 +2071,14 @@ tls_status tls_precond(tls_ctx* ctx, const double* y, double* s0, double* u) {
   if (!ctx->factored) return TLS_ERR_STATE;
   if (ctx->u == Prec::FP64) return precond_host<double>(ctx, y, s0, u);
   return precond_host<float>(ctx, y, s0, u);
+}
+
+tls_status tls_precond_trsv(tls_ctx* ctx, const double* y, double* s0, double* u) {
+  if (!ctx || !y) return TLS_ERR_ARG;
+  if (!ctx->factored) return TLS_ERR_STATE;
+  if (ctx->sparse && ctx->R == nullptr) return TLS_ERR_STATE;
+  if (ctx->u == Prec::FP64) return precond_trsv_host<double>(ctx, y, s0, u);
+  return precond_trsv_host<float>(ctx, y, s0, u);
 }
 
 }  // extern "C"

@@ -163,6 +163,13 @@ void launch_f2d(const float* in, double* out, int64_t count, cudaStream_t s);
 void launch_d2f(const double* in, float* out, int64_t count, cudaStream_t s);
 void launch_set_identity_pad(void* M, bool fp64, int64_t n, int64_t npad, cudaStream_t s);
 
+// Triangular solves with R = R_H D by blocked substitution on R_H (k_trsv.cu): s = R^{-T} y,
+// u = R^{-1} s (y: FP64 on the device, n values; s, u: npad values of T). One CTA; false when
+// the right-hand side does not fit its shared memory.
+template <typename T>
+bool launch_trsv(const T* R, int64_t npad, int64_t n, const T* dinv, const double* y, T* s_out,
+                 T* u_out, cudaStream_t s);
+
 // ---------------------------------------------------------------------------------------
 // Householder QR preconditioner (k_qr.cu)
 // ---------------------------------------------------------------------------------------

@@ -40,7 +40,7 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_set_selector", "tls_features", "tls_pool_enable", "tls_pool_trim",
            "tls_pool_stats", "tls_pool_poison", "tls_set_small_path", "tls_profile_units",
            "tls_set_pcg_fused", "tls_trace_enable", "tls_trace_get", "tls_set_pcg_l2_keep",
-           "tls_set_factor_chain", "tls_set_factor_tc"]
+           "tls_set_factor_chain", "tls_set_factor_tc", "tls_precond_trsv"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec", "pcg_solve2", "pcg_solve1"]
@@ -122,6 +122,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
         "tls_pcgtls": (C.c_int, [v, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp, _dp,
                                  _ip, _ip]),
         "tls_precond": (C.c_int, [v, _dp, _dp, _dp]),
+        "tls_precond_trsv": (C.c_int, [v, _dp, _dp, _dp]),
         "tls_profile_enable": (C.c_int, [v, C.c_int]),
         "tls_profile_get": (C.c_int, [v, C.c_int, C.POINTER(i64), _dp]),
         "tls_kernel_launches": (C.c_uint64, []),
@@ -368,6 +369,16 @@ def tls_precond(ctx, y):
     s0 = np.zeros(n)
     u = np.zeros(n)
     _check(load().tls_precond(ctx, _ptr(y), _ptr(s0), _ptr(u)), ctx)
+    return s0, u
+
+
+def tls_precond_trsv(ctx, y):
+    """s0 = R^{-T} y and u = R^{-1} s0 by triangular solves with the factor (not its inverse)."""
+    _, n, _ = tls_shape(ctx)
+    y = _f64(y)
+    s0 = np.zeros(n)
+    u = np.zeros(n)
+    _check(load().tls_precond_trsv(ctx, _ptr(y), _ptr(s0), _ptr(u)), ctx)
     return s0, u
 
 

@@ -231,6 +231,31 @@ def test_precond_matches_oracle(u_f, u):
     assert _rel(uu, u_ref) <= 2 * tol * kap
 
 
+@pytest.mark.parametrize("u_f,u,m,n", [("fp16", "fp32", 500, 150), ("fp16", "fp32", 3000, 2100),
+                                       ("fp64", "fp64", 500, 150), ("bf16", "fp32", 900, 1)])
+def test_triangular_solves_match_oracle_and_inverse_products(u_f, u, m, n):
+    """Alg. 3's R^{-T} and R^{-1} by blocked substitution on the factor (tls_precond_trsv)
+    against scipy's triangular solves with the same R = R_H D, and against the products with
+    the explicit inverse that the solve uses (tls_precond). Shapes: one block, 33 blocks with a
+    ragged last one, FP64, a single column."""
+    p = synth.dense_problem(m, n, d_lo=1e-2, noise=1e-3, seed=7)
+    y = np.random.default_rng(3).standard_normal(n)
+    with Ctx(p.A, p.b, u_f=u_f, u=u) as ctx:
+        RH, d, _ = tls.tls_export_factor(ctx)
+        st, ut = tls.tls_precond_trsv(ctx, y)
+        sw, uw = tls.tls_precond(ctx, y)
+    R = RH * d[None, :]
+    s_ref = sla.solve_triangular(R, y, trans="T", lower=False)
+    u_ref = sla.solve_triangular(R, s_ref, lower=False)
+    kap = np.linalg.cond(RH)
+    uu = U32 if u == "fp32" else U64
+    tol = 20 * kap * n * uu
+    assert _rel(st, s_ref) <= tol
+    assert _rel(ut, u_ref) <= 2 * tol * kap
+    assert _rel(st, sw) <= 2 * tol
+    assert _rel(ut, uw) <= 4 * tol * kap
+
+
 @pytest.mark.parametrize("u_f,u,fused", [("fp16", "fp32", 1), ("fp16", "fp32", 2),
                                          ("fp64", "fp64", 0)])
 @pytest.mark.parametrize("modeA", [1, 0])
