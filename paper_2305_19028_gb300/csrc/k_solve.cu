@@ -1654,6 +1654,40 @@ __device__ __forceinline__ void df_reduce_scatter(float (&h)[NV], float (&l)[NV]
   }
 }
 
+// Grid barrier of the cooperative residual launch (bar[0] counter, bar[1] abort word): thread 0
+// of each CTA fences and adds 1 (CTA 0 adds 2^31 - (G - 1)), so the top bit flips once every CTA
+// has arrived; it polls until the bit differs from the one its add saw. Bounded by a 2 s
+// deadline (then code 33 in *err and the abort word raised). Returns false when abandoned.
+__device__ __forceinline__ bool df_grid_sync(unsigned int* bar, int* err) {
+  __shared__ int fail;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fail = 0;
+    const unsigned int nb = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
+    __threadfence();
+    const unsigned int old = atomicAdd(bar, nb);
+    const uint64_t t0 = ptx::global_ns();
+    unsigned int it = 0;
+    while (((old ^ *(volatile unsigned int*)bar) & 0x80000000u) == 0u) {
+      if ((++it & 63u) == 0) {
+        if (*(volatile unsigned int*)(bar + 1) != 0u) {
+          fail = 1;
+          break;
+        }
+        if (ptx::global_ns() - t0 > 2000ull * 1000 * 1000) {
+          atomicCAS(err, 0, 33);
+          atomicExch(bar + 1, 1u);
+          fail = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return fail == 0;
+}
+
 // One CTA per SM streams its block of rows of A32 and Alo through a ring of bulk-copy stages;
 // thread t owns the float4 column groups (v * 512 + t) of every row, for the row dot products
 // and for the axpy alike, so a tile is read from shared memory once and held in registers
@@ -1661,12 +1695,17 @@ __device__ __forceinline__ void df_reduce_scatter(float (&h)[NV], float (&l)[NV]
 // products, a warp reduce-scatter, and the sums of tile t - 1 over the warps (warp rt adds row
 // rt's 16 warp shares in warp order and forms r_i = b_i - A_i x); one CTA barrier; then the
 // refill of tile t's stage and the axpy of tile t - 1.
+// With rs set (a cooperative launch), the reduction of resid_reduce_kernel follows in the same
+// launch: after a grid barrier every CTA adds the CTAs' partials of its slice of the columns
+// (lanes over the CTAs, a butterfly), forms f_j = -(A^T r)_j - sigma^2 x_j and its part of
+// ||f||^2, and the last CTA to finish forms sigma^2, g, ||f||^2 and psi into rs.
 template <int RT, int VPT>
 __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
     const float* __restrict__ Ahi, const float* __restrict__ Alo, int64_t m, int64_t npad,
     const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ part,
     double* __restrict__ spart, double* __restrict__ sout, unsigned int* counter, int stages,
-    int* err) {
+    int* err, RqiScalars* rs, double* __restrict__ f, double* __restrict__ fpart,
+    unsigned int* gbar) {
   constexpr int kSh = (RT >= 16 ? 1 : (RT >= 8 ? 2 : (RT >= 4 ? 3 : (RT >= 2 ? 4 : 5))));
   extern __shared__ __align__(128) unsigned char dsm[];
   float* ring = reinterpret_cast<float*>(dsm);
@@ -1840,6 +1879,46 @@ __global__ void __launch_bounds__(kDfThreads, 1) resid_df_kernel(
   if (arrive_last(counter)) {
     reduce_partials<2>(spart, (int)gridDim.x, sout);
     if (tid == 0) *counter = 0u;
+  }
+  if (rs == nullptr) return;
+  if (!df_grid_sync(gbar, err)) return;
+  const int G = (int)gridDim.x;
+  const double xx = rs->xx;
+  const double sigma2 = __ldcg(sout) / (1.0 + xx);
+  const int64_t per_c = (npad + G - 1) / G;
+  const int64_t c0 = min(npad, (int64_t)blockIdx.x * per_c), c1 = min(npad, c0 + per_c);
+  double ffl = 0.0;
+  for (int64_t j = c0 + warp; j < c1; j += kDfWarps) {
+    double t = 0.0;
+    for (int p = lane; p < G; p += 32) t += __ldcg(part + (int64_t)p * npad + j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    const double fj = -t - sigma2 * x[j];
+    if (lane == 0) f[j] = fj;
+    ffl = fma(fj, fj, ffl);
+  }
+  if (lane == 0) sred[warp][0] = ffl;
+  __syncthreads();
+  if (tid == 0) {
+    double a0 = 0.0;
+    for (int w = 0; w < kDfWarps; ++w) a0 += sred[w][0];
+    fpart[blockIdx.x] = a0;
+  }
+  if (arrive_last(&rs->counter[0])) {
+    __shared__ double tfs[1];
+    reduce_partials<1>(fpart, G, tfs);
+    if (tid == 0) {
+      const double tf = tfs[0];
+      const double rr = __ldcg(sout), br = __ldcg(sout + 1);
+      const double g = -br + sigma2;
+      rs->rr = rr;
+      rs->br = br;
+      rs->sigma2 = sigma2;
+      rs->g = g;
+      rs->ff = tf;
+      rs->psi = sqrt((tf + g * g) / (xx + 1.0));
+      rs->counter[0] = 0u;
+    }
   }
 }
 
@@ -2090,7 +2169,9 @@ TLS_INST(double)
 // (npad <= 8192, a multiple of 64) and nothing was launched.
 int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
                     const double* x, const double* b, double* part, double* spart, double* sout,
-                    unsigned int* counter, int* err, int num_sms, cudaStream_t s) {
+                    unsigned int* counter, int* err, int num_sms, cudaStream_t s,
+                    RqiScalars* rs, double* f, double* fpart, unsigned int* gbar, bool* fused) {
+  if (fused) *fused = false;
   if (npad <= 0 || npad > 8192 || npad % 64 != 0 || m <= 0) return 0;
   // float4 column groups per thread and rows per tile (RT * VPT <= 4: two tiles of both planes
   // in registers)
@@ -2109,8 +2190,26 @@ int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
       return true;                                                                             \
     }();                                                                                       \
     (void)attr;                                                                                \
-    resid_df_kernel<R, V><<<grid, kDfThreads, smem, s>>>(Ahi, Alo, m, npad, x, b, part, spart, \
-                                                         sout, counter, stages, err);          \
+    bool done = false;                                                                         \
+    if (rs != nullptr && fused != nullptr && gbar != nullptr) {                                \
+      /* the reduction in the same, cooperative launch */                                     \
+      RqiScalars* rs_ = rs;                                                                    \
+      double* f_ = f;                                                                          \
+      double* fp_ = fpart;                                                                     \
+      unsigned int* gb_ = gbar;                                                                \
+      int st_ = stages;                                                                        \
+      void* args[] = {(void*)&Ahi, (void*)&Alo, (void*)&m, (void*)&npad, (void*)&x, (void*)&b, \
+                      (void*)&part, (void*)&spart, (void*)&sout, (void*)&counter, (void*)&st_, \
+                      (void*)&err, (void*)&rs_, (void*)&f_, (void*)&fp_, (void*)&gb_};          \
+      done = cudaLaunchCooperativeKernel((const void*)resid_df_kernel<R, V>, grid, kDfThreads,  \
+                                         args, smem, s) == cudaSuccess;                        \
+      if (!done) (void)cudaGetLastError();                                                     \
+      *fused = done;                                                                           \
+    }                                                                                          \
+    if (!done)                                                                                 \
+      resid_df_kernel<R, V><<<grid, kDfThreads, smem, s>>>(Ahi, Alo, m, npad, x, b, part,      \
+                                                           spart, sout, counter, stages, err,  \
+                                                           nullptr, nullptr, nullptr, nullptr); \
     count_launch();                                                                            \
   }
   if (vpt == 1) TLS_DF(4, 1) else if (vpt == 2) TLS_DF(2, 2) else if (vpt == 3) TLS_DF(1, 3)

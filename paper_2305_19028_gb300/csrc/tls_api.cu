@@ -33,7 +33,8 @@ struct DevBuf {
 
 }  // namespace
 
-constexpr int kBarWords = 640;   // the one-launch solve: [0, 128); the factor chain: [128, 640)
+constexpr int kBarWords = 640;   // the one-launch solve: [0, 128); the factor chain: [128, 576);
+                                 // the cooperative residual pass: [576, 578)
 
 struct tls_ctx {
   int64_t m = 0, n = 0, npad = 0, mpad = 0, nnz = -1;
@@ -357,12 +358,16 @@ tls_status residual_pass(tls_ctx* ctx) {
     return TLS_OK;
   }
   int P = 0;
+  bool reduced = false;
   {
     Prof pr(ctx, TLS_PROF_RESID_PASS);
     if (resid_df_active(ctx))
+      // (the reduction to f, sigma^2, g, psi in the same cooperative launch, barrier words at
+      // fbar[576], clear of the one-launch solve's and the factor chain's)
       P = tls::launch_resid_df(ctx->A32, ctx->Alo, ctx->m, ctx->npad, ctx->x, ctx->b,
                                ctx->part64, ctx->spart, ctx->sout, ctx->counter, ctx->derr,
-                               ctx->num_sms, ctx->stream);
+                               ctx->num_sms, ctx->stream, ctx->rs, ctx->f, ctx->gpart,
+                               ctx->fbar + 576, &reduced);
     if (P == 0) {
       if (ctx->npad > 4096) {
         set_err(ctx, "the FP64 residual pass supports n_pad <= 4096");
@@ -374,7 +379,7 @@ tls_status residual_pass(tls_ctx* ctx) {
       P = ctx->P64;
     }
   }
-  {
+  if (!reduced) {
     Prof pr(ctx, TLS_PROF_RESID_REDUCE);
     tls::launch_resid_reduce(ctx->part64, P, ctx->npad, ctx->x, ctx->f, ctx->sout, ctx->rs,
                              ctx->gpart, ctx->stream);

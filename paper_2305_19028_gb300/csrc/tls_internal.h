@@ -255,7 +255,9 @@ bool launch_pcg_step(const T* part, int P, int nr, int64_t npad, T* q, T* w, T* 
 // outside its range (then nothing was launched).
 int launch_resid_df(const float* Ahi, const float* Alo, int64_t m, int64_t npad,
                     const double* x, const double* b, double* part, double* spart, double* sout,
-                    unsigned int* counter, int* err, int num_sms, cudaStream_t s);
+                    unsigned int* counter, int* err, int num_sms, cudaStream_t s,
+                    RqiScalars* rs = nullptr, double* f = nullptr, double* fpart = nullptr,
+                    unsigned int* gbar = nullptr, bool* fused = nullptr);
 // A whole PCGTLS solve (A-explicit operator, FP32, nr right-hand sides fin0 * fin0_scale and
 // fin1, `steps` steps or fewer on the stop flags) in one persistent cooperative launch of
 // num_sms CTAs (k_pcg_fused.cu), preconditioned by M = (R^T R)^{-1} (npad x npad, FP32).
