@@ -164,11 +164,16 @@ __device__ __forceinline__ void pass_body(const BArrays& a, const BProb& P, cons
           const int col = 4 * (gl + LR * c);
 #pragma unroll
           for (int e = 0; e < 4; ++e) acc[0][c][e] = fma(x[u][c][e], x[u][c][e], acc[0][c][e]);
-          // the FP32 working copy fl32(A) (round to nearest)
-          if (hv[u] && col < lda)
-            *reinterpret_cast<float4*>(a.A32 + P.offA + (int64_t)(t.row0 + rr[u]) * lda + col) =
-                make_float4(f64_to_f32_rn(x[u][c][0]), f64_to_f32_rn(x[u][c][1]),
-                            f64_to_f32_rn(x[u][c][2]), f64_to_f32_rn(x[u][c][3]));
+          // the FP32 working copy fl32(A) (round to nearest) and its low parts A - fl32(A)
+          if (hv[u] && col < lda) {
+            float hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) f64_split_f32((double)x[u][c][e], hi[e], lo[e]);
+            const int64_t off = P.offA + (int64_t)(t.row0 + rr[u]) * lda + col;
+            *reinterpret_cast<float4*>(a.A32 + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+            if (a.Alo != nullptr)
+              *reinterpret_cast<float4*>(a.Alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+          }
         }
     } else {
       TA d[RU][NR];
@@ -267,6 +272,137 @@ __device__ __forceinline__ void pass_body(const BArrays& a, const BProb& P, cons
   }
 }
 
+// The residual pass of one tile in double-FP32 arithmetic (FP32 working precision): A as the
+// pair A32 + Alo, x and b split into FP32 pairs, each row's dot product summed in pairs
+// (TwoProd, TwoSum) and reduced over the row's lanes, r_i = b_i - a_i^T x as a pair, the
+// axpy A^T r in pairs; the outputs in FP64 as the FP64 pass writes them (part64, spart).
+template <int LR, int CH>
+__device__ __forceinline__ void pass_body_df(const BArrays& a, const BProb& P, const BTile& t,
+                                             int tile, unsigned char* smem) {
+  constexpr int G = 32 / LR;
+  constexpr int NG = kPW * G;
+  constexpr int NC = 4 * LR * CH;
+  constexpr int RU = (CH >= 4) ? 1 : 4 / CH;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane & (LR - 1);
+  const int lda = (int)P.lda;
+  const float* Ah = a.A32 + P.offA + (int64_t)t.row0 * lda;
+  const float* Al = a.Alo + P.offA + (int64_t)t.row0 * lda;
+  const double* xv = a.x + P.offV;
+  float xh[CH][4], xl[CH][4], ach[CH][4], acl[CH][4];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = 4 * (gl + LR * c);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ach[c][e] = acl[c][e] = 0.f;
+      f64_split_f32(col < lda ? xv[col + e] : 0.0, xh[c][e], xl[c][e]);
+    }
+  }
+  double sc0 = 0.0, sc1 = 0.0;
+  for (int base = warp * G; base < t.rows; base += RU * NG) {   // warp-uniform trip count
+    int rr[RU];
+    bool hv[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      rr[u] = base + lane / LR + u * NG;
+      hv[u] = rr[u] < t.rows;
+    }
+    float ah[RU][CH][4], al[RU][CH][4];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int col = 4 * (gl + LR * c);
+        if (hv[u] && col < lda) {
+          const float4 vh = *reinterpret_cast<const float4*>(Ah + (int64_t)rr[u] * lda + col);
+          const float4 vl = *reinterpret_cast<const float4*>(Al + (int64_t)rr[u] * lda + col);
+          ah[u][c][0] = vh.x; ah[u][c][1] = vh.y; ah[u][c][2] = vh.z; ah[u][c][3] = vh.w;
+          al[u][c][0] = vl.x; al[u][c][1] = vl.y; al[u][c][2] = vl.z; al[u][c][3] = vl.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ah[u][c][e] = al[u][c][e] = 0.f;
+        }
+      }
+    float dh[RU], dl[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      dh[u] = dl[u] = 0.f;
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) df_fma(ah[u][c][e], al[u][c][e], xh[c][e], xl[c][e], dh[u], dl[u]);
+    }
+    // the row's lanes (a butterfly: TwoSum is symmetric, so every lane ends with the same pair)
+#pragma unroll
+    for (int o = LR / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const float rh = __shfl_xor_sync(0xffffffffu, dh[u], o);
+        const float rl = __shfl_xor_sync(0xffffffffu, dl[u], o);
+        df_add(dh[u], dl[u], rh, rl);
+      }
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const double bv = hv[u] ? a.b[P.offB + t.row0 + rr[u]] : 0.0;
+      float bh, bl, rh, rl;
+      f64_split_f32(bv, bh, bl);
+      df_add(bh, bl, -dh[u], -dl[u]);   // r = b - A_i x as a pair,
+      two_sum(bh, bl, rh, rl);          // renormalised for the products that follow
+      if (!hv[u]) rh = rl = 0.f;
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) df_fma(ah[u][c][e], al[u][c][e], rh, rl, ach[c][e], acl[c][e]);
+      if (gl == 0 && hv[u]) {
+        const double r = (double)rh + (double)rl;
+        sc0 = fma(r, r, sc0);
+        sc1 = fma(bv, r, sc1);
+      }
+    }
+  }
+  // the G groups of a warp cover the same columns
+#pragma unroll
+  for (int o = LR; o < 32; o <<= 1)
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float rh = __shfl_xor_sync(0xffffffffu, ach[c][e], o);
+        const float rl = __shfl_xor_sync(0xffffffffu, acl[c][e], o);
+        df_add(ach[c][e], acl[c][e], rh, rl);
+      }
+  double* red = reinterpret_cast<double*>(smem);   // [kPW][NC]
+  if (lane < LR)
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        red[warp * NC + 4 * (gl + LR * c) + e] = (double)ach[c][e] + (double)acl[c][e];
+  __shared__ double sred[kPW][2];
+  sc0 = wsum(sc0);
+  sc1 = wsum(sc1);
+  if (lane == 0) {
+    sred[warp][0] = sc0;
+    sred[warp][1] = sc1;
+  }
+  __syncthreads();
+  double* out = a.part64;
+  const int64_t slab = P.poff + (int64_t)(tile - P.tile0) * lda;
+  for (int e = threadIdx.x; e < lda; e += kPT) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kPW; ++w) s2 += red[w * NC + e];
+    out[slab + e] = s2;
+  }
+  if (threadIdx.x < 2) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kPW; ++w) s2 += sred[w][threadIdx.x];
+    a.spart[(int64_t)tile * 4 + threadIdx.x] = s2;
+  }
+}
+
 // ntile: device count of the tile list (a persistent grid loops over it), or NULL: one tile
 // per CTA (tlist NULL: tile = CTA index)
 template <typename TA, int NR, int MODE>
@@ -283,12 +419,22 @@ __global__ void __launch_bounds__(kPT, (sizeof(TA) == 8 && NR == 2) ? 1 : 2) pas
       if (st.done[0] && (NR < 2 || st.done[1])) continue;
     }
     const BProb P = a.probs[t.prob];
-    switch (P.cfg) {
-      case 0: pass_body<TA, NR, MODE, 8, 1>(a, P, t, tile, smem); break;
-      case 1: pass_body<TA, NR, MODE, 16, 1>(a, P, t, tile, smem); break;
-      case 2: pass_body<TA, NR, MODE, 32, 1>(a, P, t, tile, smem); break;
-      case 3: pass_body<TA, NR, MODE, 32, 2>(a, P, t, tile, smem); break;
-      default: pass_body<TA, NR, MODE, 32, 4>(a, P, t, tile, smem); break;
+    if constexpr (MODE == kResidDf) {
+      switch (P.cfg) {
+        case 0: pass_body_df<8, 1>(a, P, t, tile, smem); break;
+        case 1: pass_body_df<16, 1>(a, P, t, tile, smem); break;
+        case 2: pass_body_df<32, 1>(a, P, t, tile, smem); break;
+        case 3: pass_body_df<32, 2>(a, P, t, tile, smem); break;
+        default: pass_body_df<32, 4>(a, P, t, tile, smem); break;
+      }
+    } else {
+      switch (P.cfg) {
+        case 0: pass_body<TA, NR, MODE, 8, 1>(a, P, t, tile, smem); break;
+        case 1: pass_body<TA, NR, MODE, 16, 1>(a, P, t, tile, smem); break;
+        case 2: pass_body<TA, NR, MODE, 32, 1>(a, P, t, tile, smem); break;
+        case 3: pass_body<TA, NR, MODE, 32, 2>(a, P, t, tile, smem); break;
+        default: pass_body<TA, NR, MODE, 32, 4>(a, P, t, tile, smem); break;
+      }
     }
     __syncthreads();   // shared memory is reused by the next tile
   }
@@ -1477,6 +1623,16 @@ void launch_pass_colnorm(const BArrays& a, int ntiles, cudaStream_t s) {
 void launch_colnorm_post(const BArrays& a, const int* list, int cnt, cudaStream_t s) {
   if (cnt <= 0) return;
   colnorm_post_kernel<<<cnt, kCT, 0, s>>>(a, list);
+  count_launch();
+}
+
+void launch_pass_resid_df(const BArrays& a, const int* tlist, const int* ntile, int grid,
+                          cudaStream_t s) {
+  if (grid <= 0) return;
+  constexpr size_t sm = pass_smem<double, 1>();
+  static const bool once = [] { set_smem(pass_kernel<float, 1, kResidDf>, sm); return true; }();
+  (void)once;
+  pass_kernel<float, 1, kResidDf><<<grid, kPT, sm, s>>>(a, tlist, ntile);
   count_launch();
 }
 

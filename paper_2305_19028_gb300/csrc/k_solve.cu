@@ -1548,28 +1548,6 @@ constexpr int kDfThreads = 512;
 constexpr int kDfWarps = kDfThreads / 32;
 constexpr int kDfMaxStages = 8;
 
-// (the _rn intrinsics keep the compiler from contracting a product into a later add, which
-// would break the error-free transforms)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// (hi, lo) += (ah + al) (xh + xl): ah xh exactly (FMA), the cross terms ah xl and al xh in
-// FP32, al xl (2^-48 of the product) dropped
-__device__ __forceinline__ void df_fma(float ah, float al, float xh, float xl, float& hi,
-                                       float& lo) {
-  const float p = __fmul_rn(ah, xh);
-  float e = __fmaf_rn(ah, xh, -p);
-  e = __fmaf_rn(ah, xl, e);
-  e = __fmaf_rn(al, xh, e);
-  float s, t;
-  two_sum(hi, p, s, t);
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(t, e));
-}
-
 // Two FP32 lanes per instruction (the packed f32x2 forms of sm_100 and later), each lane
 // rounded to nearest exactly as the scalar instruction: two independent double-FP32
 // accumulations for the issue slots of one. A lane pair is a 64-bit value, low lane first.
@@ -1616,13 +1594,6 @@ __device__ __forceinline__ void df_fma2(f2_t ah, f2_t al, f2_t xh, f2_t xl, f2_t
   lo = f2add(lo, f2add(t, e));
 }
 
-// (hi, lo) += (bh, bl): the pair sum (TwoSum of the leading parts, the low parts added)
-__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
-  float s, e;
-  two_sum(hi, bh, s, e);
-  hi = s;
-  lo = __fadd_rn(__fadd_rn(lo, bl), e);
-}
 
 // Warp sums of NV FP32 pairs by recursive halving (as warp_reduce_scatter): lane l returns the
 // warp total of pair l >> (5 - log2 NV).

@@ -476,7 +476,11 @@ void issue_solve(tls_batch* bt, int cnt, const SolveParams& sp, const SolveGrid&
   auto resid = [&](int mode) {
     {
       BProfScope pr(bt, TLS_PROF_RESID_PASS);
-      launch_pass_resid(a, tl, n_tile, g.pass, st);
+      // FP32 working precision: the residual in double-FP32 arithmetic on A32 + Alo
+      if (std::is_same<T, float>::value && a.Alo != nullptr)
+        launch_pass_resid_df(a, tl, n_tile, g.pass, st);
+      else
+        launch_pass_resid(a, tl, n_tile, g.pass, st);
       if (bt->prof) bt->prof_elems[TLS_PROF_RESID_PASS] += elems;
     }
     BProfScope pr(bt, TLS_PROF_RESID_REDUCE);
@@ -618,8 +622,14 @@ tls_status tune_tiles(tls_batch* bt) {
       BT_CK(cudaMemcpyAsync(bt->dact_tiles, tl.data(), sizeof(int) * tl.size(),
                             cudaMemcpyHostToDevice, st));
       const int nt = (int)tl.size();
+      auto resid_pass = [&]() {
+        if (std::is_same<T, float>::value && bt->a.Alo != nullptr)
+          launch_pass_resid_df(bt->a, bt->dact_tiles, nullptr, nt, st);
+        else
+          launch_pass_resid(bt->a, bt->dact_tiles, nullptr, nt, st);
+      };
       launch_pass_pcg<T>(bt->a, bt->dact_tiles, nullptr, nt, 2, st);   // warm-up
-      launch_pass_resid(bt->a, bt->dact_tiles, nullptr, nt, st);
+      resid_pass();
       BT_CK(cudaEventRecord(bt->ev0, st));
       for (int r = 0; r < 3; ++r) launch_pass_pcg<T>(bt->a, bt->dact_tiles, nullptr, nt, 2, st);
       BT_CK(cudaEventRecord(bt->ev1, st));
@@ -627,7 +637,7 @@ tls_status tune_tiles(tls_batch* bt) {
       float ms_p = 0.f, ms_r = 0.f;
       cudaEventElapsedTime(&ms_p, bt->ev0, bt->ev1);
       BT_CK(cudaEventRecord(bt->ev0, st));
-      launch_pass_resid(bt->a, bt->dact_tiles, nullptr, nt, st);
+      resid_pass();
       BT_CK(cudaEventRecord(bt->ev1, st));
       BT_CK(cudaEventSynchronize(bt->ev1));
       cudaEventElapsedTime(&ms_r, bt->ev0, bt->ev1);
@@ -837,6 +847,7 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   bt->dcgtol = static_cast<double*>(balloc(bt, sizeof(double) * count));
   double* A64 = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)offA));
   a.A32 = static_cast<float*>(balloc(bt, sizeof(float) * (size_t)offA));
+  a.Alo = static_cast<float*>(balloc(bt, sizeof(float) * (size_t)offA));
   double* bb = static_cast<double*>(balloc(bt, sizeof(double) * (size_t)offB));
   a.d = static_cast<double*>(balloc(bt, vbytes));
   a.dinv = static_cast<double*>(balloc(bt, vbytes));
@@ -858,7 +869,8 @@ tls_status tls_batch_create_dense(tls_batch** out, int count, const int64_t* m, 
   if (!bt->dprobs || !bt->dtiles || !bt->dst || !bt->dlist || !bt->dshift ||
       !bt->dact_probs || !bt->dact_tiles || !bt->dsel || !bt->dF || !bt->dnet || !bt->dfint ||
       !bt->dcgtol ||
-      !bt->dinfo || !bt->dcount || !A64 || !a.A32 || !bb || !a.d || !a.dinv || !a.dinv32 ||
+      !bt->dinfo || !bt->dcount || !A64 || !a.A32 || !a.Alo || !bb || !a.d || !a.dinv ||
+      !a.dinv32 ||
       !a.x || !a.xbest || !a.f || !a.vw || !a.vs || !a.vp || !a.vq || !a.H || !a.R || !a.W ||
       !a.WT || !a.partU || !a.part64 || !a.spart) {
     destroy(bt);

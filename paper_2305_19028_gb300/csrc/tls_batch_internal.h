@@ -85,6 +85,7 @@ struct BArrays {
   BState* st;
   const double* A64;
   float* A32;
+  float* Alo;           // A - A32 rounded to FP32 (the low parts for the double-FP32 residual)
   const double* b;
   double *d, *dinv;
   float* dinv32;
@@ -99,7 +100,7 @@ struct BArrays {
   const double* cg_tol; // per-problem PCGTLS tolerance (selector), or NULL: the solve's own
 };
 
-enum PassMode : int { kColnorm = 0, kResid = 1, kPcg = 2 };
+enum PassMode : int { kColnorm = 0, kResid = 1, kPcg = 2, kResidDf = 3 };
 enum ResidMode : int { kResidLs = 0, kResidStart = 1, kResidRqi = 2 };
 
 struct SolveParams {
@@ -125,6 +126,10 @@ void launch_colnorm_post(const BArrays& a, const int* list, int cnt, cudaStream_
 // Pass and per-problem kernels take a work list and its length: a device count with a
 // persistent grid that loops over the list (graph-capturable: no host knowledge of the count),
 // or NULL with one list entry per CTA (grid = the list length).
+// The residual pass in double-FP32 arithmetic on A32 + Alo (FP32 working precision; the same
+// FP64 outputs as launch_pass_resid).
+void launch_pass_resid_df(const BArrays& a, const int* tlist, const int* ntile, int grid,
+                          cudaStream_t s);
 void launch_pass_resid(const BArrays& a, const int* tlist, const int* ntile, int grid,
                        cudaStream_t s);
 template <typename T>

@@ -73,4 +73,38 @@ static __device__ __forceinline__ void f64_split_f32(double a, float& hi, float&
   lo = (bits >> 63) ? -v : v;
 }
 
+
+// ---- double-FP32 arithmetic (error-free transforms on FP32 pairs), shared by the dense and
+// batched residual passes
+// (the _rn intrinsics keep the compiler from contracting a product into a later add, which
+// would break the error-free transforms)
+static __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += (ah + al) (xh + xl): ah xh exactly (FMA), the cross terms ah xl and al xh in
+// FP32, al xl (2^-48 of the product) dropped
+static __device__ __forceinline__ void df_fma(float ah, float al, float xh, float xl, float& hi,
+                                       float& lo) {
+  const float p = __fmul_rn(ah, xh);
+  float e = __fmaf_rn(ah, xh, -p);
+  e = __fmaf_rn(ah, xl, e);
+  e = __fmaf_rn(al, xh, e);
+  float s, t;
+  two_sum(hi, p, s, t);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+
+
+// (hi, lo) += (bh, bl): the pair sum (TwoSum of the leading parts, the low parts added)
+static __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  hi = s;
+  lo = __fadd_rn(__fadd_rn(lo, bl), e);
+}
+
 }  // namespace tls
