@@ -107,7 +107,8 @@ __global__ void colnorm_finish_kernel(const double* __restrict__ part, int P, in
 }
 
 // ---------------------------------------------------------------------------------------
-// AsT[j][i] = fl(A[i][j] / d_j): scaled, rounded and transposed (n x mpad), via 32x32 tiles
+// AsT[j][i] = fl(A[i][j] / d_j): scaled, rounded and transposed (n x mpad), via 32x32 tiles (FP64
+// input) or 64x64 tiles (the FP32 working copy)
 // ---------------------------------------------------------------------------------------
 template <typename Tout> __device__ __forceinline__ Tout cvt_out(double v);
 template <> __device__ __forceinline__ __half cvt_out<__half>(double v) { return __double2half(v); }
@@ -125,24 +126,57 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_out_f<__nv_bfloat16>(fl
 template <> __device__ __forceinline__ float cvt_out_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ double cvt_out_f<double>(float v) { return (double)v; }
 
-// FP32 input (the working copy of A): A_s = fl(fl32(A32 * dinv32)), all in FP32 arithmetic
+// two neighbouring entries of a row of A_s^T as one packed store (the pair starts at an even
+// column of an even-length row, so it is aligned to its own size)
+template <typename Tout> __device__ __forceinline__ void store_pair(Tout* p, float a, float b);
+template <> __device__ __forceinline__ void store_pair<__half>(__half* p, float a, float b) {
+  *reinterpret_cast<__half2*>(p) = __halves2half2(__float2half_rn(a), __float2half_rn(b));
+}
+template <> __device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* p, float a,
+                                                                      float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) =
+      __halves2bfloat162(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+}
+template <> __device__ __forceinline__ void store_pair<float>(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+
+// FP32 input (the working copy of A): A_s = fl(fl32(A32 * dinv32)), all in FP32 arithmetic.
+// 64 x 64 tiles, 256 threads: warp w reads rows 8w..8w+7 of the tile, each lane two
+// neighbouring columns per row (all eight loads of a thread issued before the first is used),
+// and writes rows 8w..8w+7 of the transposed tile, each lane two neighbouring entries as one
+// packed word. m_pad and n_pad are multiples of 64, lda is even.
 template <typename Tout>
-__global__ void scale_cast_T32_kernel(const float* __restrict__ A, int64_t lda, int64_t m,
-                                      int64_t n, int64_t npad, int64_t mpad,
-                                      const float* __restrict__ dinv, Tout* __restrict__ AsT) {
-  __shared__ float tile[32][33];
-  const int64_t i0 = (int64_t)blockIdx.x * 32;
-  const int64_t j0 = (int64_t)blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int64_t i = i0 + r, j = j0 + threadIdx.x;
-    float v = 0.f;
-    if (i < m && j < n) v = A[i * lda + j] * dinv[j];
-    tile[r][threadIdx.x] = v;
+__global__ void __launch_bounds__(256) scale_cast_T32_kernel(
+    const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, int64_t npad, int64_t mpad,
+    const float* __restrict__ dinv, Tout* __restrict__ AsT) {
+  __shared__ float tile[64][65];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * 64;   // rows of A (columns of AsT)
+  const int64_t j0 = (int64_t)blockIdx.y * 64;   // columns of A (rows of AsT)
+  const int64_t j = j0 + 2 * lane;
+  const bool c0 = j < n, c1 = j + 1 < n;
+  const float d0 = c0 ? dinv[j] : 0.f, d1 = c1 ? dinv[j + 1] : 0.f;
+  float2 a[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int64_t i = i0 + warp * 8 + t;
+    a[t] = (i < m && c0) ? *reinterpret_cast<const float2*>(A + i * lda + j)
+                         : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int r = warp * 8 + t;
+    const bool row = i0 + r < m;
+    tile[r][2 * lane] = (row && c0) ? a[t].x * d0 : 0.f;
+    tile[r][2 * lane + 1] = (row && c1) ? a[t].y * d1 : 0.f;
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int64_t j = j0 + r, i = i0 + threadIdx.x;
-    if (j < npad && i < mpad) AsT[j * mpad + i] = cvt_out_f<Tout>(tile[threadIdx.x][r]);
+  const int64_t i = i0 + 2 * lane;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int c = warp * 8 + t;
+    store_pair<Tout>(AsT + (j0 + c) * mpad + i, tile[2 * lane][c], tile[2 * lane + 1][c]);
   }
 }
 
@@ -1376,6 +1410,8 @@ void launch_scale_cast_T(const void* A, bool a_is_fp64, int64_t lda, int64_t m, 
   dim3 block(32, 8);
   if (!a_is_fp64 && dinv32 != nullptr && prec != Prec::FP64) {
     const float* Af = static_cast<const float*>(A);
+    grid = dim3((unsigned)(mpad / 64), (unsigned)(npad / 64));
+    block = dim3(256);
     switch (prec) {
       case Prec::FP16:
         scale_cast_T32_kernel<__half><<<grid, block, 0, s>>>(Af, lda, m, n, npad, mpad, dinv32, static_cast<__half*>(AsT));

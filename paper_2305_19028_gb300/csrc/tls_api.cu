@@ -696,7 +696,7 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
   double prev_psi = INFINITY;
   int stop = TLS_STOP_MAX_RQI;
   int best_k = 0, k = 0, cg_total = 0, not_spd = 0, last_steps = 0;
-  bool continue_after_switch = false;
+  bool continue_after_switch = false, save_best = false;
   double best_psi = INFINITY, best_s2 = 0.0;
   double psi_hist[24];
   int n_psi = 0;
@@ -731,8 +731,9 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
       best_k = k;
       best_psi = psi;
       best_s2 = s2;
-      TLS_CK(cudaMemcpyAsync(ctx->x_best, ctx->x, sizeof(double) * ctx->npad,
-                             cudaMemcpyDeviceToDevice, st));
+      // x_k is copied to x_best after the next solves are queued (they only read x), so
+      // the copy is not between the host's decision and the GPU's next launch
+      save_best = true;
     }
     // the tolerance test from the second RQI step on: psi_1 is taken at the inverse-iteration
     // start x_1, whose error is only first order in psi_1
@@ -776,6 +777,11 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     const double cgt = ctx->use_sel_tol ? ctx->sel_cg_tol : o.cg_tol;
     stt = run_pcg<T>(ctx, 2, ctx->f, -1.0, ctx->x, s2, steps, o.cg_fixed ? 0.0 : cgt, modeA);
     if (stt != TLS_OK) return stt;
+    if (save_best) {
+      TLS_CK(cudaMemcpyAsync(ctx->x_best, ctx->x, sizeof(double) * ctx->npad,
+                             cudaMemcpyDeviceToDevice, st));
+      save_best = false;
+    }
     {
       Prof pr(ctx, TLS_PROF_VEC);
       tls::launch_rqi_update<T>(ctx->x, v.w, v.w + ctx->npad, ctx->f, ctx->rs, ctx->n, st,
@@ -783,6 +789,9 @@ tls_status solve_impl(tls_ctx* ctx, double tol, int max_rqi, tls_info* info, dou
     }
     TLS_CK_LAUNCH("rqi update");
   }
+  if (save_best)
+    TLS_CK(cudaMemcpyAsync(ctx->x_best, ctx->x, sizeof(double) * ctx->npad,
+                           cudaMemcpyDeviceToDevice, st));
   TLS_CK(cudaEventRecord(ctx->ev1, st));
   int herr = 0;
   TLS_CK(cudaMemcpyAsync(&herr, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
