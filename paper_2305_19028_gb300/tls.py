@@ -185,6 +185,61 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
 
 
+def _arg_error(fn: str, msg: str):
+    raise TLSError(1, f"{fn}: {msg}")
+
+
+def _host_vec(fn: str, name: str, a, need: int) -> np.ndarray:
+    """A contiguous float64 copy (or view) of a host vector with exactly `need` entries: the
+    library reads that many, so a shorter array would be read past its end."""
+    v = _f64(a)
+    if v.size != need:
+        _arg_error(fn, f"{name} has {v.size} entries, {need} required")
+    return v
+
+
+def _host_dense(fn: str, A, b) -> tuple[np.ndarray, np.ndarray]:
+    A = _f64(A)
+    if A.ndim != 2:
+        _arg_error(fn, f"A must be 2-D (got {A.ndim}-D)")
+    return A, _host_vec(fn, "b", b, A.shape[0])
+
+
+def _check_device_tensors(fn: str, named: dict) -> None:
+    """Every tensor a float64 torch tensor on the current CUDA device (the library reads
+    device pointers as float64 arrays of the stated sizes and cannot check them itself)."""
+    import torch
+
+    for nm, t in named.items():
+        if not isinstance(t, torch.Tensor):
+            _arg_error(fn, f"{nm} is not a torch tensor")
+        if t.dtype != torch.float64:
+            _arg_error(fn, f"{nm} has dtype {t.dtype}, float64 required")
+        if t.device.type != "cuda":
+            _arg_error(fn, f"{nm} is not on a CUDA device")
+    cur = torch.cuda.current_device()
+    for nm, t in named.items():
+        if t.device.index != cur:
+            _arg_error(fn, f"{nm} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+
+
+def _device_dense(fn: str, A, b) -> tuple[int, int, int]:
+    """(m, n, row stride) of a device problem: A (m, n) row-major with unit column stride and
+    row stride >= n, b contiguous with m entries."""
+    _check_device_tensors(fn, {"A": A, "b": b})
+    if A.dim() != 2:
+        _arg_error(fn, f"A must be 2-D (got {A.dim()}-D)")
+    m, n = A.shape
+    if m < 1 or n < 1:
+        _arg_error(fn, f"A is {m} x {n}")
+    if (n > 1 and A.stride(1) != 1) or A.stride(0) < n:
+        _arg_error(fn, f"A must be row-major with unit column stride and row stride >= n "
+                       f"(strides {A.stride()})")
+    if not b.is_contiguous() or b.numel() != m:
+        _arg_error(fn, f"b must be contiguous with {m} entries (got {b.numel()})")
+    return m, n, A.stride(0)
+
+
 def tls_default_options(**overrides) -> tls_options:
     o = tls_options()
     load().tls_default_options(C.byref(o))
@@ -201,13 +256,11 @@ def tls_create_dense(A, b, stream=None) -> C.c_void_p:
     ctx = C.c_void_p()
     st = C.c_void_p(stream) if stream else None
     if hasattr(A, "is_cuda") and A.is_cuda:
-        m, n = A.shape
-        lda = A.stride(0)
+        m, n, lda = _device_dense("tls_create_dense", A, b)
         _check(lib.tls_create_dense(C.byref(ctx), m, n, C.c_void_p(A.data_ptr()), lda,
                                     C.c_void_p(b.data_ptr()), 1, st))
     else:
-        A = _f64(A)
-        b = _f64(b)
+        A, b = _host_dense("tls_create_dense", A, b)
         m, n = A.shape
         _check(lib.tls_create_dense(C.byref(ctx), m, n, A.ctypes.data_as(C.c_void_p), n,
                                     b.ctypes.data_as(C.c_void_p), 0, st))
@@ -218,11 +271,19 @@ def tls_create_csr(m: int, n: int, row_ptr, col_idx, val, b, stream=None) -> C.c
     lib = load()
     ctx = C.c_void_p()
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    fn = "tls_create_csr"
+    if rp.ndim != 1 or rp.size != m + 1:
+        _arg_error(fn, f"row_ptr has {rp.size} entries, m + 1 = {m + 1} required")
+    nnz = int(rp[-1])
     ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    if ci.size < nnz:
+        _arg_error(fn, f"col_idx has {ci.size} entries, row_ptr[m] = {nnz} required")
     va = _f64(val)
-    bb = _f64(b)
+    if va.size < nnz:
+        _arg_error(fn, f"val has {va.size} entries, row_ptr[m] = {nnz} required")
+    bb = _host_vec(fn, "b", b, m)
     st = C.c_void_p(stream) if stream else None
-    _check(lib.tls_create_csr(C.byref(ctx), m, n, int(rp[-1]), rp.ctypes.data_as(C.c_void_p),
+    _check(lib.tls_create_csr(C.byref(ctx), m, n, nnz, rp.ctypes.data_as(C.c_void_p),
                               ci.ctypes.data_as(C.c_void_p), va.ctypes.data_as(C.c_void_p),
                               bb.ctypes.data_as(C.c_void_p), 0, st))
     return ctx
@@ -342,7 +403,7 @@ def tls_export_working_copy(ctx):
 
 def tls_residual(ctx, x):
     _, n, _ = tls_shape(ctx)
-    x = _f64(x)
+    x = _host_vec("tls_residual", "x", x, n)
     f = np.zeros(n)
     sc = np.zeros(5)
     _check(load().tls_residual(ctx, _ptr(x), _ptr(f), _ptr(sc)), ctx)
@@ -352,8 +413,8 @@ def tls_residual(ctx, x):
 def tls_pcgtls(ctx, sigma2: float, f0, f1=None, steps: int = 1, cg_tol: float = 0.0):
     _, n, _ = tls_shape(ctx)
     nr = 1 if f1 is None else 2
-    f0 = _f64(f0)
-    f1a = _f64(f1) if f1 is not None else np.zeros(n)
+    f0 = _host_vec("tls_pcgtls", "f0", f0, n)
+    f1a = _host_vec("tls_pcgtls", "f1", f1, n) if f1 is not None else np.zeros(n)
     w0 = np.zeros(n)
     w1 = np.zeros(n)
     it = (C.c_int * 2)()
@@ -365,7 +426,7 @@ def tls_pcgtls(ctx, sigma2: float, f0, f1=None, steps: int = 1, cg_tol: float = 
 
 def tls_precond(ctx, y):
     _, n, _ = tls_shape(ctx)
-    y = _f64(y)
+    y = _host_vec("tls_precond", "y", y, n)
     s0 = np.zeros(n)
     u = np.zeros(n)
     _check(load().tls_precond(ctx, _ptr(y), _ptr(s0), _ptr(u)), ctx)
@@ -375,7 +436,7 @@ def tls_precond(ctx, y):
 def tls_precond_trsv(ctx, y):
     """s0 = R^{-T} y and u = R^{-1} s0 by triangular solves with the factor (not its inverse)."""
     _, n, _ = tls_shape(ctx)
-    y = _f64(y)
+    y = _host_vec("tls_precond_trsv", "y", y, n)
     s0 = np.zeros(n)
     u = np.zeros(n)
     _check(load().tls_precond_trsv(ctx, _ptr(y), _ptr(s0), _ptr(u)), ctx)
@@ -452,23 +513,11 @@ def tls_residual_noalloc(A, b, x, f, scal, stream=None):
     Every tensor is checked before the call (dtype, device, shape, strides), so the kernels
     never index past the end of a buffer; a mismatch raises TLSError (TLS_ERR_ARG). Returns the
     status code (0 on success); raises on error."""
-    import torch
 
     def bad(msg):
-        raise TLSError(1, "tls_residual_noalloc: " + msg)
+        _arg_error("tls_residual_noalloc", msg)
 
-    named = {"A": A, "b": b, "x": x, "f": f, "scal": scal}
-    for nm, t in named.items():
-        if not isinstance(t, torch.Tensor):
-            bad(f"{nm} is not a torch tensor")
-        if t.dtype != torch.float64:
-            bad(f"{nm} has dtype {t.dtype}, float64 required")
-        if t.device.type != "cuda":
-            bad(f"{nm} is not on a CUDA device")
-    cur = torch.cuda.current_device()
-    for nm, t in named.items():
-        if t.device.index != cur:
-            bad(f"{nm} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    _check_device_tensors("tls_residual_noalloc", {"A": A, "b": b, "x": x, "f": f, "scal": scal})
     if A.dim() != 2:
         bad("A must be 2-D")
     m, n = A.shape
@@ -556,15 +605,18 @@ class Batch:
         ld = (C.c_int64 * k)()
         ap = (C.c_void_p * k)()
         bp = (C.c_void_p * k)()
-        on_dev = 0
+        # one flag covers every problem's pointers: all on the device or all on the host
+        on_dev = 1 if k and hasattr(problems[0][0], "is_cuda") and problems[0][0].is_cuda else 0
         for i, (A, b) in enumerate(problems):
-            if hasattr(A, "is_cuda") and A.is_cuda:
-                on_dev = 1
-                m, n = A.shape
-                ms[i], ns[i], ld[i] = m, n, A.stride(0)
+            fn = f"tls_batch_create_dense (problem {i})"
+            if bool(hasattr(A, "is_cuda") and A.is_cuda) != bool(on_dev):
+                _arg_error(fn, "problems must be all on the device or all on the host")
+            if on_dev:
+                m, n, lda = _device_dense(fn, A, b)
+                ms[i], ns[i], ld[i] = m, n, lda
                 ap[i], bp[i] = A.data_ptr(), b.data_ptr()
             else:
-                A, b = _f64(A), _f64(b)
+                A, b = _host_dense(fn, A, b)
                 m, n = A.shape
                 ms[i], ns[i], ld[i] = m, n, n
                 ap[i], bp[i] = A.ctypes.data, b.ctypes.data

@@ -158,3 +158,49 @@ def test_noalloc_binding_refuses_host_and_mistyped_tensors():
         tls.tls_residual_noalloc(A, v8, v4, v4, s5)
     with pytest.raises(tls.TLSError, match="not a torch tensor"):
         tls.tls_residual_noalloc(A.numpy(), v8, v4, v4, s5)
+
+
+def test_binding_checks_host_lengths_before_the_library_reads():
+    """The library reads m, n or nnz entries from host pointers; the binding refuses arrays
+    that are shorter (or longer) before the call, so nothing is read past an array's end."""
+    A = np.ones((10, 3))
+    with pytest.raises(tls.TLSError, match="b has 9 entries, 10 required"):
+        tls.tls_create_dense(A, np.ones(9))
+    with pytest.raises(tls.TLSError, match="A must be 2-D"):
+        tls.tls_create_dense(np.ones(10), np.ones(10))
+    rp, ci, va = [0, 1, 2, 3], [0, 1, 0], np.ones(3)
+    with pytest.raises(tls.TLSError, match="row_ptr has 4 entries"):
+        tls.tls_create_csr(4, 2, rp, ci, va, np.ones(4))
+    with pytest.raises(tls.TLSError, match="col_idx has 2 entries"):
+        tls.tls_create_csr(3, 2, rp, ci[:2], va, np.ones(3))
+    with pytest.raises(tls.TLSError, match="val has 1 entries"):
+        tls.tls_create_csr(3, 2, rp, ci, va[:1], np.ones(3))
+    with pytest.raises(tls.TLSError, match="b has 2 entries"):
+        tls.tls_create_csr(3, 2, rp, ci, va, np.ones(2))
+    with pytest.raises(tls.TLSError, match="problem 1"):
+        tls.Batch([(A, np.ones(10)), (A, np.ones(3))])
+    with pytest.raises(tls.TLSError, match="y has 4 entries, 3 required"):
+        tls._host_vec("tls_precond", "y", np.ones(4), 3)
+
+
+def test_binding_checks_device_tensors_before_the_library_reads():
+    """Device pointers are read as float64 arrays of the stated shape: dtype, placement,
+    layout and lengths are checked in the binding (here on CPU tensors and stand-ins, so the
+    checks run without a GPU)."""
+    torch = pytest.importorskip("torch")
+    A = torch.zeros((8, 4), dtype=torch.float64)
+    b = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(tls.TLSError, match="float64 required"):
+        tls._device_dense("f", A.float(), b)
+    with pytest.raises(tls.TLSError, match="not on a CUDA device"):
+        tls._device_dense("f", A, b)
+    with pytest.raises(tls.TLSError, match="not a torch tensor"):
+        tls._device_dense("f", A.numpy(), b)
+
+    class OnDevice:   # looks like a CUDA tensor to the placement test, is not a tensor
+        is_cuda = True
+
+    with pytest.raises(tls.TLSError, match="all on the device or all on the host"):
+        tls.Batch([(np.ones((10, 3)), np.ones(10)), (OnDevice(), OnDevice())])
+    with pytest.raises(tls.TLSError, match="not a torch tensor"):
+        tls.Batch([(OnDevice(), OnDevice())])
