@@ -229,8 +229,9 @@ tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt);
 tls_status tls_solve(tls_ctx* ctx, double tol, int max_rqi, double* x, double* sigma,
                      tls_info* info);
 
-/* x on the device instead of the host (n FP64 values, device pointer); sigma and info on the
- * host as in tls_solve. */
+/* x on the device instead of the host (n FP64 values, device pointer on the context's
+ * device; the library cannot check its size); sigma and info on the host as in tls_solve. The
+ * copy into x_dev is issued on the context's stream and complete when the call returns. */
 tls_status tls_solve_device(tls_ctx* ctx, double tol, int max_rqi, double* x_dev,
                             double* sigma, tls_info* info);
 

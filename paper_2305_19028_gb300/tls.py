@@ -310,10 +310,23 @@ def tls_solve(ctx, tol: float = 0.0, max_rqi: int = 10):
     return x, sigma.value, info.as_dict()
 
 
-def tls_solve_device(ctx, x_dev_ptr: int, tol: float = 0.0, max_rqi: int = 10):
+def tls_solve_device(ctx, x_dev, tol: float = 0.0, max_rqi: int = 10):
+    """tls_solve with x written to device memory. x_dev: a float64 torch CUDA tensor on the
+    current device, contiguous with n entries (checked), or a raw device address (an int) of
+    n float64 values, which the caller vouches for. The copy is ordered on the context's
+    stream and finished when this returns. Returns (sigma, info dict)."""
+    if isinstance(x_dev, int):
+        ptr = x_dev
+    else:
+        _, n, _ = tls_shape(ctx)
+        _check_device_tensors("tls_solve_device", {"x": x_dev})
+        if not x_dev.is_contiguous() or x_dev.numel() != n:
+            _arg_error("tls_solve_device",
+                       f"x must be contiguous with {n} entries (got {x_dev.numel()})")
+        ptr = x_dev.data_ptr()
     sigma = C.c_double()
     info = tls_info()
-    _check(load().tls_solve_device(ctx, tol, max_rqi, C.c_void_p(x_dev_ptr), C.byref(sigma),
+    _check(load().tls_solve_device(ctx, tol, max_rqi, C.c_void_p(ptr), C.byref(sigma),
                                    C.byref(info)), ctx)
     return sigma.value, info.as_dict()
 

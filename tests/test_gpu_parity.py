@@ -542,6 +542,25 @@ def test_solve_before_factor_is_a_state_error():
         tls.tls_destroy(ctx)
 
 
+def test_solve_to_device_memory_matches_oracle():
+    """tls_solve_device writes all n entries of x into a torch CUDA tensor (NaN before the
+    solve), and that x is the oracle's; a tensor of another length is refused before the call.
+    The problem is one of the host-output cases above."""
+    import torch
+    p = synth.dense_problem(1000, 130, d_lo=1e-3, noise=1e-4, seed=0)
+    xo, so, _ = O.rqi_pcgtls(p.A, p.b, tol=0.0, max_rqi=12)
+    with Ctx(p.A, p.b, u_f="fp16", u="fp32") as ctx:
+        xd = torch.full((130,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()   # the fill runs on torch's stream, the solve on the context's
+        sigma, info = tls.tls_solve_device(ctx, xd, tol=0.0, max_rqi=12)
+        with pytest.raises(tls.TLSError, match="130 entries"):
+            tls.tls_solve_device(ctx, torch.zeros(131, dtype=torch.float64, device="cuda"))
+    x = xd.cpu().numpy()
+    assert np.all(np.isfinite(x))
+    assert abs(sigma - so) <= 1e-10 * so, (sigma, so, info)
+    assert _rel(x, xo) <= 1e-8, info
+
+
 @pytest.mark.parametrize("shift_first", [0, 1])
 def test_zero_column_breaks_down_then_shifts(shift_first):
     # A zero column makes H singular: the pivot at that column is 0. Started unshifted, the
