@@ -1,0 +1,57 @@
+"""Host logic of bench.py that needs no GPU: the algorithmic units behind its roofline fields
+and the arithmetic that turns event times into achieved rates and fractions of the peak."""
+from __future__ import annotations
+
+import pytest
+
+import bench
+
+M, N = 16384, 2048
+
+
+def test_paired_iteration_bytes_at_the_dense_workload():
+    # A_u in FP32 once, the triangle of R_H in FP16 for each of the two triangular products,
+    # about 24 FP32 n-vectors: 142.8 MB at 16384 x 2048
+    assert bench.paired_iteration_bytes(M, N) == 4 * M * N + 2 * N * (N + 1) + 24 * 4 * N
+    assert bench.paired_iteration_bytes(M, N) == 142_807_040
+
+
+def test_inner_loop_rate_from_event_time_and_iterations():
+    peaks = {"hbm_gbs": 6800.0}
+    prof = {"pcg_solve2": (30, 5.7811)}              # launches, device ms
+    units = {"pcg_solve2": 135}                      # paired iterations in those launches
+    r = bench._inner_loop(prof, units, peaks, M, N)
+    per_s = 5.7811e-3 / 135
+    assert r["us_per_iteration"] == pytest.approx(per_s * 1e6, rel=1e-12)
+    assert r["achieved"] == pytest.approx(142_807_040 / per_s / 1e9, rel=1e-12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.0, rel=1e-12)
+    assert r["peak_source"] == "measured" and r["bound"] == "hbm"
+    # ncu traffic belongs to the size it was captured at only
+    assert r["traffic"] == bench.PCG_FUSED_TRAFFIC_PER_ITER_C2
+    assert bench._inner_loop(prof, units, peaks, 8192, N)["traffic"] is None
+    # no launches timed: no roofline
+    assert bench._inner_loop({}, {}, peaks, M, N) == {}
+
+
+def test_residual_and_gram_units():
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops_sustained": 1700.0}
+    avg_ms = 0.078
+    r = bench._roofline({"resid_pass": (9, 9 * avg_ms)}, peaks, "resid_pass", M, N, variant64=4)
+    # the pair A32 + Alo read once (8 B per entry of A), x and b in, per-SM FP64 partials out
+    byts = 8 * M * N + 8 * M + 8 * N + 152 * 8 * N
+    assert r["algorithmic_bytes"] == byts
+    assert r["achieved"] == pytest.approx(byts / (avg_ms * 1e-3) / 1e9, rel=1e-12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.0, rel=1e-12)
+    # the FP64 pass is bounded by the FP64 FMA rate: 4 flops per entry of A
+    r = bench._roofline({"resid_pass": (1, 0.152)}, peaks, "resid_pass", M, N, variant64=3)
+    assert r["bound"] == "alu" and r["algorithmic_flops"] == 4.0 * M * N
+    assert r["frac"] == pytest.approx(4.0 * M * N / 0.152e-3 / 1e12 / bench.FP64_PEAK)
+    # the Gram: n(n+1)/2 entries of 2m flops each, against the sustained bf16 peak
+    r = bench._roofline({"gram": (1, 0.08)}, peaks, "gram", M, N)
+    assert r["algorithmic_flops"] == M * N * (N + 1)
+    assert r["frac"] == pytest.approx(M * N * (N + 1) / 0.08e-3 / 1e12 / 1700.0)
+
+
+def test_fallback_peaks_are_named_as_such():
+    r = bench._roofline({"gram": (1, 0.08)}, {}, "gram", M, N)
+    assert r["peak"] == 1700.0 and r["peak_source"].startswith("fallback")
