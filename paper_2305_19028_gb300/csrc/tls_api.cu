@@ -2090,7 +2090,7 @@ tls_status tls_precond(tls_ctx* ctx, const double* y, double* s0, double* u) {
 tls_status tls_precond_trsv(tls_ctx* ctx, const double* y, double* s0, double* u) {
   if (!ctx || !y) return TLS_ERR_ARG;
   if (!ctx->factored) return TLS_ERR_STATE;
-  if (ctx->sparse && ctx->R == nullptr) return TLS_ERR_STATE;
+  if (ctx->R == nullptr) return TLS_ERR_STATE;
   if (ctx->u == Prec::FP64) return precond_trsv_host<double>(ctx, y, s0, u);
   return precond_trsv_host<float>(ctx, y, s0, u);
 }
