@@ -277,11 +277,10 @@ def run_reference(args, ws, rank):
 # from the ncu capture in profiles/resid_pass_dense_8192x2048.md (134.346 MB read + 0.067 MB
 # written at m = 8192; one read of A, so proportional to m)
 RESID_PIPE_TRAFFIC_PER_ROW = (134.346e6 + 0.067e6) / 8192
-# DRAM bytes of the double-FP32 residual pass per launch at 16384 x 2048 (read + write, from the
-# ncu capture in profiles/resid_df_dense_16384x2048.md), and of the one-launch paired PCGTLS
-# solve per paired iteration at the same size (profiles/pcg_fused_dense_16384x2048.md: 419.96 MB
-# for a launch of 3 iterations)
-RESID_DF_TRAFFIC_C2 = 268.641792e6 + 2.953216e6
+# DRAM bytes of the one-launch paired PCGTLS solve per paired iteration at 16384 x 2048 (read +
+# write, from the ncu capture in profiles/pcg_fused_dense_16384x2048.md: 419.96 MB for a launch
+# of 3 iterations). The double-FP32 residual pass has no current figure: its capture predates
+# the column reduction it now runs after a grid barrier in the same launch.
 PCG_FUSED_TRAFFIC_PER_ITER_C2 = (416.771072e6 + 3.188480e6) / 3
 
 
@@ -381,8 +380,7 @@ def _roofline(prof: dict, peaks: dict, cls: str, m: int, n: int, variant64: int 
         return {"kernel": "resid_df_kernel (r = b - A x, A^T r in double-FP32 arithmetic on "
                           "A32 + Alo)", "bound": "hbm", "achieved": ach,
                 "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": RESID_DF_TRAFFIC_C2 if (m, n) == (16384, 2048) else None,
-                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                "traffic": None,
                 "peak_source": src, "avg_launch_us": avg_s * 1e6, "algorithmic_bytes": unit_bytes,
                 "fp64_equivalent_tflops": 4.0 * m * n / avg_s / 1e12}
     if cls == "resid_pass":
