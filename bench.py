@@ -965,7 +965,10 @@ def _oracle_pool(ids, procs):
     return {i: (x, s) for i, x, s in res}, dt
 
 
-def _batch_roofline(prof: dict, peaks: dict, cls: str) -> dict:
+def _batch_roofline(prof: dict, peaks: dict, cls: str, u64: bool = False) -> dict:
+    """Roofline of one kernel class of the packed batch from its profiled launches (count,
+    device ms, entries of A of the active problems). u64: the FP64 working precision (FP64
+    residual passes); otherwise the residual passes run in double-FP32 on A32 + Alo."""
     cnt, ms, elems = prof.get(cls, (0, 0.0, 0))
     if cnt == 0 or ms <= 0:
         return {}
@@ -979,6 +982,15 @@ def _batch_roofline(prof: dict, peaks: dict, cls: str) -> dict:
                 "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": None, "peak_source": src,
                 "avg_launch_us": ms / cnt * 1e3, "algorithmic_bytes_per_launch": byts / cnt}
+    if cls == "resid_pass" and not u64:
+        # double-FP32: the pair A32 + Alo read once (8 bytes per entry of A)
+        byts = 8.0 * elems
+        ach = byts / (ms * 1e-3) / 1e9
+        return {"kernel": "resid_pass (batched r = b - A x, A^T r in double-FP32 arithmetic on "
+                          "A32 + Alo)", "bound": "hbm", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "avg_launch_us": ms / cnt * 1e3, "algorithmic_bytes_per_launch": byts / cnt,
+                "fp64_equivalent_tflops": 4.0 * elems / (ms * 1e-3) / 1e12}
     if cls == "resid_pass":
         # FP64 FMA-bound: 2 FMA (4 flops) per entry of A; peak 1.25 TFLOP/s FP64 (nominal)
         flops = 4.0 * elems

@@ -55,3 +55,15 @@ def test_residual_and_gram_units():
 def test_fallback_peaks_are_named_as_such():
     r = bench._roofline({"gram": (1, 0.08)}, {}, "gram", M, N)
     assert r["peak"] == 1700.0 and r["peak_source"].startswith("fallback")
+
+
+def test_batch_residual_roofline_follows_the_working_precision():
+    peaks = {"hbm_gbs": 6800.0}
+    prof = {"resid_pass": (10, 20.0, 10 * 2.2e8)}    # launches, device ms, entries of A
+    r = bench._batch_roofline(prof, peaks, "resid_pass")
+    assert r["bound"] == "hbm" and "double-FP32" in r["kernel"]
+    assert r["achieved"] == pytest.approx(8.0 * 2.2e9 / 20e-3 / 1e9, rel=1e-12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.0, rel=1e-12)
+    r = bench._batch_roofline(prof, peaks, "resid_pass", u64=True)
+    assert r["bound"] == "alu" and r["peak"] == bench.FP64_PEAK
+    assert r["achieved"] == pytest.approx(4.0 * 2.2e9 / 20e-3 / 1e12, rel=1e-12)
