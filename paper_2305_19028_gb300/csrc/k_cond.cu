@@ -128,10 +128,12 @@ __global__ void __launch_bounds__(256) feat_gemv_kernel(const T* __restrict__ M,
 }
 
 // One CTA. mode 0: x = ones on the first n entries (zero padding). mode 1: out = sqrt(|y|^2 /
-// |x|^2) (the estimate after a product y = W x). mode 2: x = z / |z|. Sums in FP64.
+// |x|^2) (the estimate after a product y = W x). mode 2: x = z / |z|. Sums in FP64. z may be x
+// itself (mode 2 normalises x in place, each thread reading and writing only its own entries),
+// so x and z carry no __restrict__.
 template <typename T>
-__global__ void __launch_bounds__(1024) feat_power_kernel(T* __restrict__ x, const T* __restrict__ y,
-                                                          const T* __restrict__ z, int64_t n,
+__global__ void __launch_bounds__(1024) feat_power_kernel(T* x, const T* __restrict__ y,
+                                                          const T* z, int64_t n,
                                                           int64_t npad, int mode,
                                                           double* __restrict__ out) {
   __shared__ double sh[2][32];

@@ -123,8 +123,6 @@ template <> __device__ __forceinline__ __half cvt_out_f<__half>(float v) { retur
 template <> __device__ __forceinline__ __nv_bfloat16 cvt_out_f<__nv_bfloat16>(float v) {
   return __float2bfloat16_rn(v);
 }
-template <> __device__ __forceinline__ float cvt_out_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ double cvt_out_f<double>(float v) { return (double)v; }
 
 // two neighbouring entries of a row of A_s^T as one packed store (the pair starts at an even
 // column of an even-length row, so it is aligned to its own size)

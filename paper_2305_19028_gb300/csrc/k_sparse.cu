@@ -111,7 +111,6 @@ template <> __device__ __forceinline__ float round_to<float>(float v, int prec) 
   if (prec == (int)Prec::BF16) return __bfloat162float(__float2bfloat16_rn(v));
   return v;
 }
-template <> __device__ __forceinline__ double round_to<double>(double v, int prec) { return v; }
 
 // scaled, rounded values in CSR order: as[k] = fl_uf(a_k / d_col(k))
 template <typename T>
