@@ -503,13 +503,19 @@ def run_ours(args, ws, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e2e_res = []
-        e0.record(stream)
-        for _ in range(ne):
+
+        def e2e_step():
             c2 = tls.tls_create_dense(A_pin, b_pin, stream=stream.cuda_stream)
             tls.tls_factor(c2, "fp16", opt)
             x2, s2, _ = tls.tls_solve(c2, tol=SOLVE_TOL, max_rqi=MAX_RQI)
             tls.tls_destroy(c2)
-            e2e_res.append((x2, s2))
+            return x2, s2
+
+        e2e_step()   # warm-up: the first context's buffers come from cudaMalloc, later ones from the block cache
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ne):
+            e2e_res.append(e2e_step())
         e1.record(stream)
         torch.cuda.synchronize()
         ems = _barrier_max(e0.elapsed_time(e1), ws)
@@ -691,13 +697,19 @@ def run_c1(args, ws, rank, local):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     oke = 0
-    e0.record(stream)
-    for _ in range(args.steps):
+
+    def e2e_step():
         c2 = tls.tls_create_dense(A_pin, b_pin, stream=stream.cuda_stream)
         tls.tls_factor(c2, "fp64", opt)
         x2, s2, _ = tls.tls_solve(c2, tol=1e-12, max_rqi=10)
         tls.tls_destroy(c2)
-        oke += int(accurate(x2, s2))
+        return x2, s2
+
+    e2e_step()   # warm-up: the first context's buffers come from cudaMalloc, later ones from the block cache
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        oke += int(accurate(*e2e_step()))
     e1.record(stream)
     torch.cuda.synchronize()
     ems = _barrier_max(e0.elapsed_time(e1), ws)
@@ -846,13 +858,19 @@ def run_sparse(args, ws, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e2e_res = []
-        e0.record(stream)
-        for _ in range(ne):
+
+        def e2e_step():
             c2 = tls.tls_create_csr(p.m, p.n, *pins, stream=stream.cuda_stream)
             tls.tls_factor(c2, "bf16", opt)
             x2, s2, _ = tls.tls_solve(c2, tol=SOLVE_TOL, max_rqi=MAX_RQI)
             tls.tls_destroy(c2)
-            e2e_res.append((x2, s2))
+            return x2, s2
+
+        e2e_step()   # warm-up: the first context's buffers come from cudaMalloc, later ones from the block cache
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ne):
+            e2e_res.append(e2e_step())
         e1.record(stream)
         torch.cuda.synchronize()
         ems = _barrier_max(e0.elapsed_time(e1), ws)
@@ -1083,14 +1101,20 @@ def run_batch(args, ws, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         okc = 0
-        e0.record(stream)
-        for _ in range(ne):
+
+        def e2e_step():
             with tls.Batch(pins, stream=stream.cuda_stream) as b2:
                 if model is not None:
                     b2.set_selector(*model)
                 b2.factor(uf, u="fp32")
                 x2, s2, _, _ = b2.solve(tol=SOLVE_TOL, max_rqi=MAX_RQI)
-            okc += count_ok(x2, s2)
+            return x2, s2
+
+        e2e_step()   # warm-up: the first batch's buffers come from cudaMalloc, later ones from the block cache
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ne):
+            okc += count_ok(*e2e_step())
         e1.record(stream)
         torch.cuda.synchronize()
         ems = _barrier_max(e0.elapsed_time(e1), ws)
