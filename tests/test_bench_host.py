@@ -67,3 +67,43 @@ def test_batch_residual_roofline_follows_the_working_precision():
     r = bench._batch_roofline(prof, peaks, "resid_pass", u64=True)
     assert r["bound"] == "alu" and r["peak"] == bench.FP64_PEAK
     assert r["achieved"] == pytest.approx(4.0 * 2.2e9 / 20e-3 / 1e12, rel=1e-12)
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"),
+                        *args], capture_output=True, text=True, timeout=300, env=env)
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return r.returncode, [json.loads(ln) for ln in lines], r.stderr
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`--impl reference` times the FP64 oracle on the host cores (here on a small case) and
+    prints one JSON line with the keys the benchmark contract names."""
+    rc, lines, err = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1",
+                                 "--m", "600", "--n", "60"])
+    assert rc == 0, err
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["unit"] == "solves/s" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "dense_600x60_uf16_u32_ur64"
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    rc, lines, err = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1",
+                                 "--m", "600", "--n", "60"],
+                                {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
+    assert rc == 0, err
+    assert lines == []
