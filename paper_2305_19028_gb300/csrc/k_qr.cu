@@ -838,7 +838,10 @@ int launch_qr_r(T* A, int64_t lda, int64_t m, int64_t n, T* tau, T* work, int* i
     } else {
       le = cudaLaunchKernelEx(&cfg, qr_panel_kernel<T>, A, lda, m, k, bw, rpc, tau, Tm, info);
     }
-    if (le != cudaSuccess) return -3;
+    if (le != cudaSuccess) {
+      (void)cudaGetLastError();   // a refused launch: clear it so later checks see only their own
+      return -3;
+    }
     count_launch();
     const int64_t nt = n - k - bw;
     if (nt <= 0) break;
