@@ -173,6 +173,13 @@ typedef struct tls_ctx tls_ctx;
  * 3 shifts, tensor-core Gram. */
 void tls_default_options(tls_options* opt);
 
+/* NULL when every field of *opt is in its range, else a static string saying which is not
+ * (switches 0 or 1; cg_max in [1, 100000], ls_iters and constraint_iters in [0, 100000],
+ * max_shifts in [0, 30]; cg_tol, constr_guard, stall_ratio, hybrid_ratio finite and >= 0;
+ * psi_accept >= 0). tls_factor and tls_batch_factor apply the same check (TLS_ERR_ARG) plus the
+ * rules that depend on the context. Host only: needs no GPU. */
+const char* tls_options_check(const tls_options* opt);
+
 /*
  * tls_create_dense -- a TLS problem [A, b] with dense A (Sec. 1: min ||[E, r]||_F subject to
  * (A + E) x = b + r).

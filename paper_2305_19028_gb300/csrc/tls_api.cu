@@ -3,6 +3,7 @@
 #include "../../include/tls.h"
 #include "../../include/tls_debug.h"
 #include "tls_internal.h"
+#include "tls_options.h"
 
 #include <cmath>
 #include <map>
@@ -1512,6 +1513,11 @@ tls_status factor_auto_ctx(tls_ctx* ctx) {
 
 extern "C" {
 
+const char* tls_options_check(const tls_options* opt) {
+  if (!opt) return "no options given";
+  return tls::options_error(*opt);
+}
+
 void tls_default_options(tls_options* opt) {
   if (!opt) return;
   opt->u = TLS_FP32;
@@ -1709,6 +1715,10 @@ tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt) {
   if (o.factor < 0 || o.factor > 1 || (o.factor == 1 && ctx->sparse)) {
     set_err(ctx, "factor must be 0 (Cholesky of the scaled Gram matrix) or 1 (Householder QR, "
                  "dense contexts)");
+    return TLS_ERR_ARG;
+  }
+  if (const char* why = tls::options_error(o)) {
+    set_err(ctx, why);
     return TLS_ERR_ARG;
   }
   const int64_t limit = (o.u == TLS_FP64) ? 4096 : 8192;

@@ -5,6 +5,7 @@
 #include "../../include/tls.h"
 #include "../../include/tls_debug.h"
 #include "tls_batch_internal.h"
+#include "tls_options.h"
 
 #include <algorithm>
 #include <map>
@@ -1011,6 +1012,10 @@ tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt)
   if (o.u != TLS_FP32 && o.u != TLS_FP64) return TLS_ERR_ARG;
   if (!o.mode_A) {
     set_err(bt, "the packed batch implements the A-explicit PCGTLS operator (mode_A = 1)");
+    return TLS_ERR_ARG;
+  }
+  if (const char* why = tls::options_error(o)) {
+    set_err(bt, why);
     return TLS_ERR_ARG;
   }
   bt->opt = o;

@@ -40,7 +40,7 @@ EXPORTS = ["tls_default_options", "tls_create_dense", "tls_create_csr", "tls_fac
            "tls_set_selector", "tls_features", "tls_pool_enable", "tls_pool_trim",
            "tls_pool_stats", "tls_pool_poison", "tls_set_small_path", "tls_profile_units",
            "tls_set_pcg_fused", "tls_trace_enable", "tls_trace_get", "tls_set_pcg_l2_keep",
-           "tls_set_factor_chain", "tls_set_factor_tc", "tls_precond_trsv"]
+           "tls_set_factor_chain", "tls_set_factor_tc", "tls_precond_trsv", "tls_options_check"]
 
 PROF_CLASSES = ["scale", "gram", "chol", "trtri", "resid_pass", "resid_reduce", "pcg_pass2",
                 "pcg_pass1", "pcg_reduce", "pcg_gemv", "vec", "pcg_solve2", "pcg_solve1"]
@@ -101,6 +101,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     v, vp, i64 = C.c_void_p, C.POINTER(C.c_void_p), C.c_int64
     sig = {
         "tls_default_options": (None, [C.POINTER(tls_options)]),
+        "tls_options_check": (C.c_char_p, [C.POINTER(tls_options)]),
         "tls_create_dense": (C.c_int, [vp, i64, i64, v, i64, v, C.c_int, v]),
         "tls_create_csr": (C.c_int, [vp, i64, i64, i64, v, v, v, v, C.c_int, v]),
         "tls_factor": (C.c_int, [v, C.c_int, C.POINTER(tls_options)]),
@@ -287,6 +288,12 @@ def tls_create_csr(m: int, n: int, row_ptr, col_idx, val, b, stream=None) -> C.c
                               ci.ctypes.data_as(C.c_void_p), va.ctypes.data_as(C.c_void_p),
                               bb.ctypes.data_as(C.c_void_p), 0, st))
     return ctx
+
+
+def tls_options_check(opt: tls_options) -> str | None:
+    """None when every field of opt is in range, else what is not (host only, no GPU)."""
+    why = load().tls_options_check(C.byref(opt))
+    return why.decode() if why else None
 
 
 def tls_factor(ctx, u_f="fp16", opt: tls_options | None = None):

@@ -204,3 +204,21 @@ def test_binding_checks_device_tensors_before_the_library_reads():
         tls.Batch([(np.ones((10, 3)), np.ones(10)), (OnDevice(), OnDevice())])
     with pytest.raises(tls.TLSError, match="not a torch tensor"):
         tls.Batch([(OnDevice(), OnDevice())])
+
+
+def test_option_ranges_are_checked_on_the_host():
+    """tls_options_check (the check tls_factor and tls_batch_factor apply before any device
+    work): the defaults pass; a switch outside {0, 1}, an unbounded count or a non-finite or
+    negative real is named."""
+    assert tls.tls_options_check(tls.tls_default_options()) is None
+    assert tls.tls_options_check(tls.tls_default_options(u="fp64", mode_A=2, factor=1,
+                                                         cg_fixed=0, cg_max=100000,
+                                                         max_shifts=30, psi_accept=float("inf"),
+                                                         constraint_iters=60)) is None
+    bad = {"u": 0, "mode_A": 3, "factor": 2, "cg_fixed": 2, "reproducible": -1, "cg_max": 0,
+           "ls_iters": -1, "max_shifts": 31, "constraint_iters": 100001,
+           "cg_tol": float("nan"), "psi_accept": -1.0, "constr_guard": float("inf"),
+           "stall_ratio": -0.5, "hybrid_ratio": float("nan")}
+    for field, value in bad.items():
+        why = tls.tls_options_check(tls.tls_default_options(**{field: value}))
+        assert why is not None and field in why, (field, value, why)
