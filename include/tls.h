@@ -227,7 +227,8 @@ tls_status tls_factor(tls_ctx* ctx, tls_prec u_f, const tls_options* opt);
  * from the LS start and return the iterate with the smallest psi_k (Eq. (4)).
  *   tol      stop when psi_k <= tol * (||A||_F^2 + ||b||^2) (a normwise backward error of
  *            the eigenpair of Eq. (1)); 0 leaves only the psi-increase rule and max_rqi.
- *   max_rqi  maximum number of RQI updates.
+ *   max_rqi  maximum number of RQI updates, 0 ... 1000 (RQI step k runs k + 1 PCGTLS steps
+ *            per solve, so the cap bounds the work of one call; TLS_ERR_ARG above it).
  *   x        n FP64 values, host memory, written on success.
  *   sigma    host, sigma = sqrt(sigma_k^2) of the returned iterate.
  *   info     host, may be NULL.
@@ -278,7 +279,8 @@ tls_status tls_solve_batched(int count, tls_ctx* const* ctxs, double tol, int ma
  * tls_batch_solve -- RQI-PCGTLS for every problem, same stopping rules as tls_solve and the
  *   same precision fallback (tls_options.fallback) applied per problem. x[i] (host, n[i]
  *   doubles; a NULL entry skips the copy), sigma[i], infos[i] (NULL: none), per_problem[i]
- *   (NULL: none). t_factor_ms / t_solve_ms of every info are the batch's times.
+ *   (NULL: none). t_factor_ms / t_solve_ms of every info are the batch's times. max_rqi
+ *   0 ... 100 (the captured graph holds every RQI step; TLS_ERR_ARG above it).
  *   Returns TLS_ERR_STATE before a successful factor, else the first non-OK per-problem status.
  */
 #define TLS_BATCH_MAX_N 512

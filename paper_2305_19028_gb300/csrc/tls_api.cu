@@ -1775,9 +1775,16 @@ static tls_status solve_once(tls_ctx* ctx, double tol, int max_rqi, double* sigm
 // Solve; when the RQI loop ends on max_rqi without converging and the factor precision is
 // below FP64, refactor one precision up and solve again (the precision fallback for a factor
 // that violates the stability constraints of Sec. 3.1).
+constexpr int kMaxRqi = 1000;
+
 static tls_status solve_common(tls_ctx* ctx, double tol, int max_rqi, double* sigma,
                                tls_info* info) {
   if (!ctx || !sigma || max_rqi < 0 || !(tol >= 0.0)) return TLS_ERR_ARG;
+  if (max_rqi > kMaxRqi) {
+    // RQI step k runs k + 1 PCGTLS steps per solve: the cap bounds the work of one call
+    set_err(ctx, "max_rqi must be in [0, " + std::to_string(kMaxRqi) + "]");
+    return TLS_ERR_ARG;
+  }
   if (!ctx->factored) {
     set_err(ctx, "tls_solve called before a successful tls_factor");
     return TLS_ERR_STATE;

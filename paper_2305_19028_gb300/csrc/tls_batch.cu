@@ -1062,6 +1062,11 @@ tls_status tls_batch_factor(tls_batch* bt, tls_prec u_f, const tls_options* opt)
 tls_status tls_batch_solve(tls_batch* bt, double tol, int max_rqi, double* const* x,
                            double* sigma, tls_info* infos, tls_status* per_problem) {
   if (!bt || !x || !sigma || max_rqi < 0 || !(tol >= 0.0)) return TLS_ERR_ARG;
+  if (max_rqi > 100) {
+    // the captured graph holds every RQI step up to max_rqi + 1 with its k + 1 PCGTLS steps
+    set_err(bt, "max_rqi must be in [0, 100] for the packed batch");
+    return TLS_ERR_ARG;
+  }
   if (!bt->factored) {
     set_err(bt, "tls_batch_solve called before tls_batch_factor");
     return TLS_ERR_STATE;
