@@ -333,7 +333,7 @@ tls_status tls_mlp_adam(float* params, const float* grad, float* m, float* v, in
  * tls_condition -- estimates behind the two constraints on the factor precision (Sec. 3.1):
  * constraint 1, u_q <~ kappa(A)^{-1} (Eq. (5)), and constraint 2,
  * u_q <~ kappa_F(A)^{-1} (1 - sigma_{n+1}^2 / sigma'_n^2) (Eq. (9)).
- * Power iterations (iters steps each) give sigma'_1 (on A^T A through the Gram matrix) and
+ * Power iterations (iters steps each, 1 ... 100000) give sigma'_1 (on A^T A through the Gram matrix) and
  * sigma'_n (on (R^T R)^{-1} through the factor's triangular products, so the estimate is that
  * of the computed factor, shift included); ||A^+||_F is taken as ||R^{-1}||_F.
  * out (host, 9 values): sigma'_1, sigma'_n, kappa(A), ||A||_F, ||A^+||_F, kappa_F(A),

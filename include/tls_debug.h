@@ -47,8 +47,9 @@ tls_status tls_residual(tls_ctx* ctx, const double* x_host, double* f_host, doub
 
 /*
  * tls_pcgtls -- PCGTLS (Alg. 3) for (A^T A - sigma2 I) w = f in the context's precision u, for
- * nr = 1 or 2 right-hand sides f0 (and f1) sharing each pass over A: `steps` steps, or fewer
- * when ||s_j|| <= cg_tol ||s_0|| (cg_tol > 0) or delta_j <= 0. w0 (and w1): n values each.
+ * nr = 1 or 2 right-hand sides f0 (and f1) sharing each pass over A: `steps` steps (0 ...
+ * 100000), or fewer when ||s_j|| <= cg_tol ||s_0|| (cg_tol > 0; NaN is refused) or
+ * delta_j <= 0. w0 (and w1): n values each.
  * iters[2], not_spd[2] (may be NULL): per right-hand side. Host pointers.
  */
 tls_status tls_pcgtls(tls_ctx* ctx, int nr, double sigma2, const double* f0, const double* f1,

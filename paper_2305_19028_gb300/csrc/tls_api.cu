@@ -2041,7 +2041,7 @@ tls_status tls_set_pcg_fused(tls_ctx* ctx, int mode) {
 uint64_t tls_kernel_launches(void) { return tls::g_launches.load(); }
 
 tls_status tls_condition(tls_ctx* ctx, int iters, double* out) {
-  if (!ctx || !out || iters < 1) return TLS_ERR_ARG;
+  if (!ctx || !out || iters < 1 || iters > 100000) return TLS_ERR_ARG;
   if (!ctx->factored) return TLS_ERR_STATE;
   if (!ctx->H) {
     set_err(ctx, "the condition estimate uses the scaled Gram matrix, which the QR factor does "
@@ -2090,7 +2090,9 @@ tls_status tls_residual(tls_ctx* ctx, const double* x_host, double* f_host, doub
 tls_status tls_pcgtls(tls_ctx* ctx, int nr, double sigma2, const double* f0, const double* f1,
                       int steps, double cg_tol, double* w0, double* w1, int* iters,
                       int* not_spd) {
-  if (!ctx || !f0 || !w0 || nr < 1 || nr > 2 || steps < 0 || (nr == 2 && !f1)) return TLS_ERR_ARG;
+  if (!ctx || !f0 || !w0 || nr < 1 || nr > 2 || steps < 0 || steps > 100000 ||
+      (nr == 2 && !f1) || std::isnan(cg_tol))
+    return TLS_ERR_ARG;
   if (!ctx->factored) return TLS_ERR_STATE;
   if (ctx->u == Prec::FP64)
     return pcgtls_host<double>(ctx, nr, sigma2, f0, f1, steps, cg_tol, w0, w1, iters, not_spd);
