@@ -317,6 +317,8 @@ const char* tls_batch_last_error(const tls_batch* bt);
  * tls_mlp_grad    -- mean loss and gradient over the samples idx[0..nsamp) of X (idx NULL: the
  *   first nsamp rows): cross-entropy of the logits against ycls plus
  *   lambda * ymask * (out[3] - ytol)^2; scratch holds nsamp * (TLS_MLP_PARAMS + 1) floats.
+ *   The caller guarantees that every idx value indexes a row of X (and of ycls, ytol, ymask)
+ *   and that every ycls value is 0, 1 or 2; the Python trainer checks both.
  * tls_mlp_adam    -- one Adam step (step >= 1) of params with gradient grad and moments m, v.
  */
 #define TLS_MLP_PARAMS 5508

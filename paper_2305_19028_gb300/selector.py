@@ -64,9 +64,37 @@ class Trainer:
         self.t = 0
         self.scratch = None
 
+    def _check_X(self, fn: str, X) -> int:
+        """X: float32 (rows, 16) contiguous on the current CUDA device; returns rows."""
+        tls._check_device_tensors(fn, {"X": X}, self.torch.float32)
+        if X.dim() != 2 or X.shape[1] != tls.N_FEATURES or not X.is_contiguous():
+            tls._arg_error(fn, f"X must be contiguous (rows, {tls.N_FEATURES}), got "
+                               f"{tuple(X.shape)}")
+        return int(X.shape[0])
+
     def grad(self, X, ycls, ytol, ymask, idx=None, lam: float = 0.1):
+        """Mean loss and gradient over the rows idx of X (all rows when idx is None). Every
+        tensor is checked first (dtype, device, shape, index and label ranges): the kernel reads
+        them by device pointer."""
         torch = self.torch
-        n = int(idx.numel()) if idx is not None else int(X.shape[0])
+        fn = "tls_mlp_grad"
+        rows = self._check_X(fn, X)
+        tls._check_device_tensors(fn, {"ycls": ycls}, torch.int32)
+        tls._check_device_tensors(fn, {"ytol": ytol, "ymask": ymask}, torch.float32)
+        for nm, t in (("ycls", ycls), ("ytol", ytol), ("ymask", ymask)):
+            if not t.is_contiguous() or t.numel() != rows:
+                tls._arg_error(fn, f"{nm} must be contiguous with {rows} entries")
+        if rows and (int(ycls.min()) < 0 or int(ycls.max()) > 2):
+            tls._arg_error(fn, "ycls must hold class indices 0, 1 or 2")
+        if idx is not None:
+            tls._check_device_tensors(fn, {"idx": idx}, torch.int32)
+            if idx.dim() != 1 or not idx.is_contiguous():
+                tls._arg_error(fn, "idx must be a contiguous 1-D tensor")
+            if idx.numel() and (int(idx.min()) < 0 or int(idx.max()) >= rows):
+                tls._arg_error(fn, f"idx must index the {rows} rows of X")
+        n = int(idx.numel()) if idx is not None else rows
+        if n < 1:
+            tls._arg_error(fn, "no samples")
         need = n * (tls.MLP_PARAMS + 1)
         if self.scratch is None or self.scratch.numel() < need:
             self.scratch = torch.empty(need, dtype=torch.float32, device=self.P.device)
@@ -88,6 +116,7 @@ class Trainer:
             raise tls.TLSError(r, "tls_mlp_adam")
 
     def forward(self, X):
+        self._check_X("tls_mlp_forward", X)
         out = self.torch.empty((X.shape[0], 4), dtype=self.torch.float32, device=self.P.device)
         st = self.torch.cuda.current_stream().cuda_stream
         r = tls.load().tls_mlp_forward(_ptr(self.P), int(X.shape[0]), _ptr(X), _ptr(out),

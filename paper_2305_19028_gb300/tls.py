@@ -206,16 +206,18 @@ def _host_dense(fn: str, A, b) -> tuple[np.ndarray, np.ndarray]:
     return A, _host_vec(fn, "b", b, A.shape[0])
 
 
-def _check_device_tensors(fn: str, named: dict) -> None:
-    """Every tensor a float64 torch tensor on the current CUDA device (the library reads
-    device pointers as float64 arrays of the stated sizes and cannot check them itself)."""
+def _check_device_tensors(fn: str, named: dict, dtype=None) -> None:
+    """Every tensor a torch tensor of `dtype` (default float64) on the current CUDA device (the
+    library reads device pointers as arrays of the stated type and sizes and cannot check them
+    itself)."""
     import torch
 
+    dtype = torch.float64 if dtype is None else dtype
     for nm, t in named.items():
         if not isinstance(t, torch.Tensor):
             _arg_error(fn, f"{nm} is not a torch tensor")
-        if t.dtype != torch.float64:
-            _arg_error(fn, f"{nm} has dtype {t.dtype}, float64 required")
+        if t.dtype != dtype:
+            _arg_error(fn, f"{nm} has dtype {t.dtype}, {str(dtype).replace('torch.', '')} required")
         if t.device.type != "cuda":
             _arg_error(fn, f"{nm} is not on a CUDA device")
     cur = torch.cuda.current_device()

@@ -222,3 +222,21 @@ def test_option_ranges_are_checked_on_the_host():
     for field, value in bad.items():
         why = tls.tls_options_check(tls.tls_default_options(**{field: value}))
         assert why is not None and field in why, (field, value, why)
+
+
+def test_selector_trainer_checks_its_tensors_before_the_kernels():
+    """The training kernels read X, labels and indices by device pointer: the trainer refuses
+    a wrong dtype, shape or placement before any call (checked here without a GPU)."""
+    torch = pytest.importorskip("torch")
+    from paper_2305_19028_gb300 import selector
+    tr = selector.Trainer.__new__(selector.Trainer)   # no device parameters needed for the checks
+    tr.torch = torch
+    X = torch.zeros((5, 16), dtype=torch.float32)
+    with pytest.raises(tls.TLSError, match="not on a CUDA device"):
+        tr._check_X("f", X)
+    with pytest.raises(tls.TLSError, match="float32 required"):
+        tr._check_X("f", X.double())
+    with pytest.raises(tls.TLSError, match="not a torch tensor"):
+        tr.grad(X.numpy(), None, None, None)
+    with pytest.raises(tls.TLSError, match="not on a CUDA device"):
+        tr.forward(X)
