@@ -240,3 +240,25 @@ def test_selector_trainer_checks_its_tensors_before_the_kernels():
         tr.grad(X.numpy(), None, None, None)
     with pytest.raises(tls.TLSError, match="not on a CUDA device"):
         tr.forward(X)
+
+
+def test_no_device_means_an_error_not_a_fallback():
+    """Without a GPU the library reports the CUDA failure (a non-zero status, TLSError in the
+    binding) instead of computing on the host; without libtls.so the binding raises at load."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    p_A = np.random.default_rng(0).standard_normal((50, 5))
+    with pytest.raises(tls.TLSError) as ei:
+        tls.tls_create_dense(p_A, np.ones(50))
+    assert ei.value.status != 0
+    import subprocess
+    import sys
+    code = ("from paper_2305_19028_gb300 import tls\n"
+            "try:\n"
+            "    tls.load(path='/nonexistent/libtls.so', build_if_missing=False)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT,
+                       timeout=120)
+    assert "raised: libtls.so not found" in r.stdout, r.stdout + r.stderr
